@@ -1,0 +1,105 @@
+"""Seeded synthetic inputs: density fields and particle sets.
+
+This module holds no solver arithmetic.  It only draws random numbers and
+shapes them into the inputs the solver and the oracle both consume:
+
+* Gaussian random fields with a power-law spectrum P(k) ~ k^slope
+  (white noise -> rFFT -> multiply by sqrt(P) -> irFFT -> scale to sigma),
+* lognormal densities rho = exp(g - sigma^2/2), renormalised to mean 1
+  (rho~ has mean 1 in the paper's code units, Sec. III.A),
+* Zel'dovich-displaced particle lattices (displacement s = IFFT(i k / k^2 g^)),
+* the point-mass field of Sec. VI.A.2 (Eq. point_mass).
+
+Seeds follow seed = 1000 * config + field index.  numpy only.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _kgrid(shape):
+    """Integer wavenumbers for an rFFT of a (n2, n1, n0) array."""
+    n2, n1, n0 = shape
+    kz = np.fft.fftfreq(n2, d=1.0 / n2)
+    ky = np.fft.fftfreq(n1, d=1.0 / n1)
+    kx = np.fft.rfftfreq(n0, d=1.0 / n0)
+    return np.meshgrid(kz, ky, kx, indexing="ij")
+
+
+def gaussian_random_field(shape, seed, sigma=1.0, slope=-1.5, dtype=np.float64):
+    """Zero-mean Gaussian field with P(k) ~ |k|^slope (k in grid units), k = 0
+    removed, normalised to standard deviation ``sigma`` per cell."""
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal(shape)
+    wk = np.fft.rfftn(white)
+    del white
+    kz, ky, kx = _kgrid(shape)
+    k2 = kz * kz + ky * ky + kx * kx
+    del kz, ky, kx
+    k2[0, 0, 0] = 1.0
+    amp = k2 ** (slope / 4.0)  # sqrt(P) = |k|^(slope/2)
+    amp[0, 0, 0] = 0.0
+    wk *= amp
+    del amp, k2
+    g = np.fft.irfftn(wk, s=shape, axes=(0, 1, 2))
+    del wk
+    g -= g.mean()
+    std = g.std()
+    if std > 0:
+        g *= sigma / std
+    return g.astype(dtype, copy=False)
+
+
+def lognormal_density(shape, seed, sigma=1.0, slope=-1.5):
+    """rho = exp(g - sigma^2/2) renormalised to an exact mean of 1 (FP64)."""
+    g = gaussian_random_field(shape, seed, sigma=sigma, slope=slope)
+    g -= 0.5 * sigma * sigma
+    np.exp(g, out=g)
+    g /= g.mean()
+    return g
+
+
+def point_mass_density(n):
+    """Eq. (point_mass), Sec. VI.A.2: contrast 1e-4 (N^3 - 1) in cell (0,0,0) and
+    -1e-4 elsewhere; returned as rho~ = 1 + contrast."""
+    rho = np.full((n, n, n), 1.0 - 1e-4)
+    rho[0, 0, 0] = 1.0 + 1e-4 * (n ** 3 - 1)
+    return rho
+
+
+def zeldovich_positions(n, seed, amplitude, slope=-1.5):
+    """n^3 particles on a cell-centred lattice displaced by amplitude * s(q),
+    s = IFFT(i k / k^2 g^) with g a unit-variance field of spectrum k^slope.
+    Positions are in box units, wrapped into [0, 1); shape (n^3, 3) as (x, y, z)."""
+    shape = (n, n, n)
+    g = gaussian_random_field(shape, seed, sigma=1.0, slope=slope)
+    gk = np.fft.rfftn(g)
+    del g
+    kz, ky, kx = _kgrid(shape)
+    k2 = kz * kz + ky * ky + kx * kx
+    k2[0, 0, 0] = 1.0
+    disp = []
+    for kd in (kx, ky, kz):
+        sk = 1j * kd / k2 * gk
+        sk[0, 0, 0] = 0.0
+        disp.append(np.fft.irfftn(sk, s=shape, axes=(0, 1, 2)) / n)  # grid units -> box units
+    del gk, kz, ky, kx, k2
+    q = (np.arange(n) + 0.5) / n
+    qz, qy, qx = np.meshgrid(q, q, q, indexing="ij")
+    pos = np.empty((n ** 3, 3))
+    for d, qd in enumerate((qx, qy, qz)):
+        x = qd + amplitude * disp[d]
+        pos[:, d] = np.mod(x, 1.0).ravel()
+    # np.mod can return exactly 1.0 for tiny negative inputs
+    pos[pos >= 1.0] = 0.0
+    return pos
+
+
+# Zel'dovich amplitude for the 128^3, seed-2000 particle set of the CIC workload,
+# chosen (oracle/calibrate_zeldovich.py) so that max(rho~ - 1) is about 100.
+ZELDOVICH_AMPLITUDE_128 = None
+
+
+def uniform_positions(np_, seed):
+    rng = np.random.default_rng(seed)
+    return rng.random((np_, 3))
