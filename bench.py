@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark: f(R) FAS multigrid solve, cells/s to converge (rms L(u) <= 1e-8).
+
+Workload (one "step"): one full solve from u0 = 0 of a 512^3 periodic grid,
+box 256 Mpc/h, a = 1, Omega_m = 0.24, |f_R0| = 1e-5, lognormal density with
+sigma = 2.0 (P(k) ~ k^-1.5), V(2,2) cycles, mixed FP32/FP64 precision.  The
+same workload is also solved in plain FP64 on the GPU for the comparison the
+metric asks for ("mixed vs FP64 at equal residual").
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the workload (see cpu_baseline).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 512
+PHYS = dict(box=256.0, a=1.0, omega_m=0.24, fr0=1e-5)
+SIGMA = 2.0
+SEED = 3000
+TOL = 1e-8
+WORKLOAD = (f"{N}^3 periodic, box 256 Mpc/h, a=1, Om=0.24, |f_R0|=1e-5, lognormal sigma=2.0 "
+            f"P(k)~k^-1.5 seed {SEED}, u0=0, V(2,2) red-black NGS, rms tol 1e-8")
+# CPU oracle sample: same cell size (0.5 Mpc/h), sigma, |f_R0| and a on a 64^3 box
+SAMPLE_N = 64
+SAMPLE_PHYS = dict(box=32.0, a=1.0, omega_m=0.24, fr0=1e-5)
+
+# Algorithmic bytes per cell of the grid a launch covers (minimum traffic of
+# the operation: each array read or written once).
+ALG_BYTES = {
+    "smooth_f32@fine": 6.0,          # half-sweep: (read u, read rhs, write u) / 2 colours, 4 B
+    "smooth_f64@fine": 12.0,
+    "resid_restrict_f32@fine": 10.0,  # read u, rhs (8 B) + 4 coarse words / 8 cells
+    "resid_restrict_f64@fine": 20.0,
+    "prolong_f32@fine": 9.0,         # read/write u (8 B) + 2 coarse words / 8 cells
+    "prolong_f64@fine": 18.0,
+    "residual_f64@fine": 24.0,       # read u, rho, write d (FP64 defect)
+    "residual_f32@fine": 12.0,
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(budget_s=12.0):
+    """FP64 CPU oracle, as it stands, on a bounded sample: full solves of a 64^3
+    box with the workload's cell size, sigma, a and |f_R0|, single thread."""
+    from oracle import oracle as O
+    from paper_1110_1379_gb300 import synth
+    rho = synth.lognormal_density((SAMPLE_N,) * 3, SEED, sigma=SIGMA)
+    cells = 0
+    t0 = time.perf_counter()
+    solves = 0
+    while True:
+        r = O.solve(rho, tol=TOL, **SAMPLE_PHYS)
+        assert r.converged
+        cells += SAMPLE_N ** 3
+        solves += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": f"{solves} full oracle solves (rms<=1e-8) of a {SAMPLE_N}^3 box, "
+                      f"box 32 Mpc/h (same 0.5 Mpc/h cells), sigma 2.0, |f_R0|=1e-5, a=1, "
+                      f"seed {SEED}; {dt:.1f} s on 1 core"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1110_1379_gb300 import synth
+    rho = synth.lognormal_density((SAMPLE_N,) * 3, SEED, sigma=SIGMA)
+    for _ in range(args.warmup):
+        O.solve(rho, tol=TOL, **SAMPLE_PHYS)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = O.solve(rho, tol=TOL, **SAMPLE_PHYS)
+        times.append(time.perf_counter() - t0)
+        assert r.converged
+    tot = sum(times)
+    value = args.steps * SAMPLE_N ** 3 / tot
+    line = {
+        "impl": "reference", "metric": "f(R) MG solve: cells/s to converge (rms <= 1e-8)",
+        "value": value, "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"bounded sample of [{WORKLOAD}]: {SAMPLE_N}^3 box 32 Mpc/h "
+                               f"(same cell size)", "parallelism": "none (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step one full oracle solve of the {SAMPLE_N}^3 sample"},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def grad_error(u_test, u_ref, ubar, h):
+    """Relative error of the fifth-force gradient: central differences of
+    f~_R = -exp(u + ubar) in code units; max and rms over all cells/axes."""
+    import torch
+    mx = 0.0
+    sq = 0.0
+    ref_max = 0.0
+    n = 0
+    for ax in range(3):
+        def g(u):
+            f = -torch.exp(u + ubar)
+            return (torch.roll(f, -1, ax) - torch.roll(f, 1, ax)) / (2 * h)
+        gr = g(u_ref)
+        dg = g(u_test) - gr
+        mx = max(mx, float(dg.abs().max()))
+        sq += float((dg * dg).sum())
+        ref_max = max(ref_max, float(gr.abs().max()))
+        n += dg.numel()
+    return {"max_rel": mx / ref_max, "rms_rel": (sq / n) ** 0.5 / ref_max}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1110_1379_gb300 import frmg, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n = args.n
+    shape = (n, n, n)
+    cells = n ** 3
+    # one independent field per rank (replicas: a single field does not shard)
+    rho_np = synth.lognormal_density(shape, SEED + rank, sigma=SIGMA)
+    rho = torch.from_numpy(rho_np).cuda()
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    ctx = frmg.Context(local)
+    stream = torch.cuda.current_stream()
+
+    def solve(prec, profile=False):
+        u.zero_()
+        st, s = ctx.solve(rho, u, tol=TOL, prec=prec, stream=stream, **PHYS)
+        if st != frmg.FR_OK:
+            raise RuntimeError(f"solve failed: status {st} {s.as_dict()}")
+        return s
+
+    for _ in range(args.warmup):
+        solve("mixed")
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile(True)
+    l0 = ctx.launches
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        stats.append(solve("mixed"))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launches - l0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * cells * args.steps / (ms / 1e3)
+    u_mixed = u.clone()
+
+    # plain FP64 GPU solve of the same field (equal residual)
+    solve("fp64")
+    torch.cuda.synchronize()
+    t64 = []
+    s64 = None
+    for _ in range(args.fp64_steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64 = solve("fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64.append(e0.elapsed_time(e1))
+    fp64_value = cells / (statistics.median(t64) / 1e3)
+    du = float((u_mixed - u).abs().max())
+    du_rms = float(((u_mixed - u) ** 2).mean().sqrt())
+    alpha, beta, gamma, ct, fbar, ubar = frmg.constants(PHYS["box"], n, PHYS["a"],
+                                                         PHYS["omega_m"], PHYS["fr0"])
+    gerr = grad_error(u_mixed, u, ubar, 1.0 / n)
+
+    # roofline of the dominant kernel family during the timed mixed steps
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_cnt, dom_ms) = dom
+    avg_ms = dom_ms / dom_cnt
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "of measured" if hbm else "of fallback"
+    hbm = hbm or 6800.0
+    if dom_name in ALG_BYTES:
+        traffic_alg = ALG_BYTES[dom_name] * cells
+        achieved = traffic_alg / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "alg_bytes_per_launch": traffic_alg, "avg_launch_ms": avg_ms,
+                "launches": dom_cnt, "peak_source": peak_src}
+    else:
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None, "avg_launch_ms": avg_ms, "launches": dom_cnt,
+                "peak_source": peak_src}
+
+    # end to end through the public API with pinned host buffers
+    rho_h = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+    rho_h.copy_(torch.from_numpy(rho_np))
+    u_h = torch.zeros(shape, dtype=torch.float64, pin_memory=True)
+    e2e_t = []
+    for it in range(1 + min(args.steps, 3)):
+        u_h.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, s = ctx.solve(rho_h, u_h, tol=TOL, prec="mixed", stream=stream, **PHYS)
+        t1 = time.perf_counter()
+        if it > 0:
+            e2e_t.append(t1 - t0)
+    e2e = {"value": world * cells / statistics.median(e2e_t), "unit": "cells/s",
+           "h2d_bytes_per_step": 2 * 8 * cells, "d2h_bytes_per_step": 8 * cells}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline()
+    s0 = stats[-1]
+    line = {
+        "metric": "f(R) MG solve: cells/s to converge (rms <= 1e-8), mixed FP32/FP64",
+        "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
+                   "parallelism": f"replicas x{world} (one field per GPU)",
+                   "l2": "inputs larger than L2 (1 GiB per FP64 field)"},
+        "fp64": {"value": fp64_value, "unit": "cells/s", "ms_per_solve": statistics.median(t64),
+                 "vcycles": s64.vcycles, "res_rms": s64.res_rms},
+        "mixed_vs_fp64_speedup": value / world / fp64_value,
+        "mixed": {"vcycles": s0.vcycles, "outer": s0.outer, "res_rms": s0.res_rms,
+                  "res_max": s0.res_max},
+        "accuracy_vs_fp64_gpu": {"max_abs_du": du, "rms_du": du_rms,
+                                 "grad_fR_max_rel": gerr["max_rel"],
+                                 "grad_fR_rms_rel": gerr["rms_rel"]},
+        "roofline": roof,
+        "kernels_ms": {k: {"launches": c, "total_ms": t} for k, (c, t) in sorted(prof.items())},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

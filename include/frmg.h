@@ -1,0 +1,209 @@
+/*
+ * frmg.h -- C ABI of the GB300 (sm_103a) FAS multigrid solver for the
+ * Hu-Sawicki f(R) scalaron equation (n = 1), after Li, Zhao, Teyssier &
+ * Koyama, "ECOSMOG" (arXiv:1110.1379).
+ *
+ * Equation (Sec. IV, Eq. discrete_fR, multiplied by c~^2 as in Sec. V.B.1,
+ * Eq. bc_modified_fR_op), written in u = ln(f_R / fbar_R(a)):
+ *
+ *   L_i(u) = (alpha/2) sum_{6 faces j} (e^{u_i} + e^{u_j}) (u_j - u_i)
+ *            + beta (e^{-u_i/2} - 1) - gamma (rho_i - 1)            = 0
+ *
+ *   alpha = c~^2 |fbar~_R(a)| / h^2,  beta = Om a^4 (a^-3 + 4 OL/Om),
+ *   gamma = Om a,  c~ = c/(B H0),  OL = 1 - Om,
+ *   |fbar~_R(a)| = a^2 xi / (3 (a^-3 + 4 OL/Om))^2  (Sec. VI.A.1),
+ *   xi = |f_R0| (3 (1 + 4 OL/Om))^2.
+ *
+ * h is the cell size in code units (box side 1): h = 1/dims[0] on the domain
+ * grid, halved per refinement level.  The solution returned in u is
+ * u = ln(f_R/fbar_R); f_R = fbar_R(a) e^u with fbar_R(a) = -|fbar~_R(a)|/a^2.
+ *
+ * Conventions for every entry point:
+ *  - Grids are [n2][n1][n0] with x (dims[0]) fastest; dims must be even and >= 2.
+ *  - Pointers may be CUDA device memory or host memory.  Host arrays are
+ *    staged through library-owned device buffers (copies in both directions
+ *    are part of the call).  The caller keeps ownership of every array.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *    is synchronous on return: results and stats are valid when it returns.
+ *  - Return values are fr_status codes.  On FR_ENOCONV / FR_EDIVERGED the last
+ *    iterate is still written to u.  fr_status_string() names a code;
+ *    fr_last_error() returns a message for the last failing call on the
+ *    calling thread.
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef FRMG_H
+#define FRMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct frmg_ctx frmg_ctx;
+
+typedef enum {
+    FR_OK = 0,
+    FR_EINVAL = 1,     /* invalid argument (dims, a, |f_R0|, density, patch nesting) */
+    FR_ENOMEM = 2,     /* device or pinned host allocation failed */
+    FR_ECUDA = 3,      /* a CUDA call failed */
+    FR_ENOCONV = 4,    /* max_vcycles reached before tol */
+    FR_EDIVERGED = 5,  /* NaN/Inf or a residual growing for several cycles */
+    FR_ETIMEOUT = 6    /* a bounded device-side wait ran out */
+} fr_status;
+
+typedef enum {
+    FR_FP64 = 0,  /* every step in FP64 (the plain method) */
+    FR_MIXED = 1  /* FP32 smoothing and coarse levels inside an FP64 defect /
+                     update / convergence loop (iterative refinement) */
+} fr_precision;
+
+typedef struct {
+    double tol;             /* rms of L(u) on the finest grid; 1e-8 */
+    int max_vcycles;        /* cap on V-cycles (FP64) or on inner V-cycles (mixed); 100 */
+    int pre, post;          /* NGS sweeps before / after the coarse correction; 2, 2 */
+    fr_precision prec;      /* FR_FP64 */
+    double newton_step_cap; /* |du| per Newton-Gauss-Seidel update; 1.0 */
+    int inner_cycles;       /* mixed: FP32 V-cycles per FP64 defect after the first; 2 */
+    int max_outer;          /* mixed: cap on FP64 defect evaluations; 40 */
+    int allow_negative_density; /* 0: reject rho < 0 (the paper's sine test needs 1) */
+    int use_graph;          /* capture repeated V-cycles in CUDA graphs; 1 */
+} fr_opts;
+
+typedef struct {
+    int vcycles;      /* V-cycles on the finest grid (all precisions) */
+    int outer;        /* mixed: FP64 defect evaluations; FP64: 0 */
+    double res0_rms;  /* rms of L(u0) */
+    double res_rms;   /* rms of L(u) on return (FP64 evaluation) */
+    double res_max;   /* max |L(u)| on return */
+    double seconds;   /* wall time of the call */
+} fr_stats;
+
+/* Refinement patch (Sec. V.A.1, V.B.1, VI.B): a box of fine cells at twice the
+ * resolution of its parent, with Dirichlet boundary values interpolated from
+ * the parent solution.  The footprint plus one parent cell on every side must
+ * lie inside a patch parent; a domain-grid parent wraps periodically. */
+typedef struct {
+    int parent;          /* -1: the domain grid; else index of an earlier patch */
+    int origin[3];       /* lower corner in parent cells (x, y, z) */
+    int n[3];            /* fine cells (x, y, z); even, >= 4 */
+    const double *density; /* rho~ on the patch cells, [n2][n1][n0] */
+    double *u;           /* out: patch solution, [n2][n1][n0] */
+} fr_patch;
+
+void fr_opts_default(fr_opts *opts);
+const char *fr_status_string(int status);
+const char *fr_last_error(void);
+
+/* Library-owned context: device, workspace, streams, captured graphs. */
+int fr_ctx_create(frmg_ctx **out, int device);
+void fr_ctx_destroy(frmg_ctx *ctx);
+
+/* Derived constants {alpha(h = 1/n0), beta, gamma, c~, |fbar~_R(a)|, ubar} for
+ * one grid; out has 6 doubles (host). */
+int fr_constants(double box_mpc_h, int n0, double a, double omega_m, double fr0_abs,
+                 double *out6);
+
+/*
+ * Solve one periodic domain grid: FAS V-cycles of red-black Newton-Gauss-Seidel
+ * (Sec. V.B) from the initial guess in u_inout until rms(L(u)) <= tol.
+ * density: rho~ (mean ~1, Sec. III.A), [n2][n1][n0] FP64.
+ * u_inout: in the initial guess, out the solution, FP64.
+ * opts NULL = defaults (tol from the argument overrides opts->tol);
+ * stats may be NULL.
+ * Errors: FR_EINVAL for odd/small dims, a <= 0, |f_R0| <= 0, Om outside
+ * (0,1), box <= 0, NaN density or (unless allowed) negative density.
+ */
+int fr_solve(frmg_ctx *ctx, const double *density, const int dims[3], double box_mpc_h,
+             double a, double omega_m, double fr0_abs, double tol, double *u_inout,
+             const fr_opts *opts, fr_stats *stats, void *stream);
+
+/*
+ * Domain grid plus nested refinement patches, solved one way coarse to fine
+ * (Sec. V.A.1: boundary values come from the parent solution; Sec. VI.B).
+ * Patches must be ordered so that every parent precedes its children.  For
+ * each patch: the initial u and the ghost values are the trilinear (27/9/3/1)
+ * interpolation of the parent's solution, u_b = (ghost + first interior)/2 is
+ * fixed, and the patch is solved with FAS V-cycles to tol_patch.
+ * per_grid (optional, 1 + npatch entries): stats of the domain then each patch.
+ */
+int fr_solve_levels(frmg_ctx *ctx, const double *density, const int dims[3], double box_mpc_h,
+                    double a, double omega_m, double fr0_abs, double tol, double tol_patch,
+                    double *u_inout, fr_patch *patches, int npatch, const fr_opts *opts,
+                    fr_stats *per_grid, void *stream);
+
+/*
+ * Many independent periodic fields solved together: every kernel launch of a
+ * V-cycle level covers all fields still iterating (a field drops out once its
+ * rms(L(u)) <= tol).  Arrays of nfields entries; density[i] and u_inout[i]
+ * must all be device pointers or all host pointers.  omega_m and tol are
+ * shared.  stats (optional) has nfields entries.
+ */
+int fr_solve_batch(frmg_ctx *ctx, int nfields, const double *const *density,
+                   const int (*dims)[3], const double *box_mpc_h, const double *a,
+                   const double *fr0_abs, double omega_m, double tol, double *const *u_inout,
+                   const fr_opts *opts, fr_stats *stats, void *stream);
+
+/*
+ * Cloud-in-cell density assignment (Sec. VI.C): np particles at pos[np][3]
+ * (x, y, z in box units, [0, 1)), each of mass n0 n1 n2 / np, spread over the 8
+ * nearest cell centres with weights prod_d (1 - |x_d - x_c,d| / h_d), periodic.
+ * density_out: [n2][n1][n0] FP64, overwritten; its mean is 1 (Sec. VI.C).
+ */
+int fr_cic_assign(frmg_ctx *ctx, const double *pos, long long np, const int dims[3],
+                  double *density_out, void *stream);
+
+/* ---- Single-step entry points (one level, FP64, the same kernels as the
+ *      solver uses); parity checks call these step by step. ---- */
+
+/* nsweeps red-black Newton-Gauss-Seidel sweeps (red = (i+j+k) even first) on
+ * L(u) = f (f NULL = 0); cell size h; ub NULL = periodic, else the six packed
+ * boundary faces (-x,+x,-y,+y,-z,+z; face normal to axis a indexed by the other
+ * axes p < q as c[q]*n[p] + c[p]). */
+int fr_smooth(frmg_ctx *ctx, double *u, const double *density, const double *f,
+              const int dims[3], double h, double box_mpc_h, double a, double omega_m,
+              double fr0_abs, const double *ub, int nsweeps, double step_cap, void *stream);
+
+/* d = L(u) - f on one level (arguments as fr_smooth). */
+int fr_residual(frmg_ctx *ctx, const double *u, const double *density, const double *f,
+                const int dims[3], double h, double box_mpc_h, double a, double omega_m,
+                double fr0_abs, const double *ub, double *d, void *stream);
+
+/* coarse = average of the 8 children of each coarse cell (full weighting on a
+ * cell-centred grid); fine dims even. */
+int fr_restrict(frmg_ctx *ctx, const double *fine, const int dims_fine[3], double *coarse,
+                void *stream);
+
+/* u_fine += P(uH - uR), trilinear 27/9/3/1 over 64 (Sec. V.A.3, V.B.3);
+ * dirichlet != 0: coarse neighbours outside the grid contribute 0. */
+int fr_prolong_correct(frmg_ctx *ctx, double *u_fine, const int dims_fine[3], const double *uH,
+                       const double *uR, int dirichlet, void *stream);
+
+/* Patch boundary set-up: u_init (patch cells) and ub (packed faces) from the
+ * parent solution uparent (dims_parent; periodic != 0 wraps). */
+int fr_patch_bc(frmg_ctx *ctx, const double *uparent, const int dims_parent[3], int periodic,
+                const int origin[3], const int n[3], double *u_init, double *ub, void *stream);
+
+/* Run exactly ncycles FAS V-cycles (no convergence test) on one periodic grid
+ * in the given precision; stats->res_rms is the FP64 residual afterwards. */
+int fr_vcycles(frmg_ctx *ctx, const double *density, const int dims[3], double box_mpc_h,
+               double a, double omega_m, double fr0_abs, double *u_inout, int ncycles,
+               const fr_opts *opts, fr_stats *stats, void *stream);
+
+/* Number of kernel launches this context issued since it was created. */
+long long fr_launch_count(const frmg_ctx *ctx);
+
+/* Per-kernel timing: when enabled, every launch is bracketed by CUDA events
+ * recorded on its own stream and the elapsed times are accumulated per kernel
+ * family.  fr_profile(ctx, 1) enables and clears, fr_profile(ctx, 0) disables
+ * and clears.  fr_profile_entry reads entry idx (FR_EINVAL past the end):
+ * name (NUL-terminated, truncated to namelen), launch count, total ms. */
+int fr_profile(frmg_ctx *ctx, int enable);
+int fr_profile_entry(frmg_ctx *ctx, int idx, char *name, int namelen, long long *count,
+                     double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRMG_H */

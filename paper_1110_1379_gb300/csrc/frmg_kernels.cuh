@@ -1,0 +1,484 @@
+// frmg_kernels.cuh -- device code of the f(R) FAS multigrid solver (sm_103a).
+//
+// Operator (Sec. IV Eq. discrete_fR times c~^2, Sec. V.B.1 Eq. bc_modified_fR_op)
+// in u = ln(f_R/fbar_R), as a nonlinear operator A with right-hand side f:
+//
+//   A_i(u) = (alpha/2) sum_j (e^{u_i} + e^{u_j}) (u_j - u_i) + beta (e^{-u_i/2} - 1)
+//   finest level:  A(u) = gamma (rho - 1);  coarse levels: A^H(u^H) = f^H (FAS).
+//
+// Two evaluation modes share one code path:
+//  * plain (BG = false): u is the unknown itself.  Cache x = expm1(u), so
+//    B = e^u = 1 + x.
+//  * background (BG = true, FP32 inside the mixed-precision loop): the unknown
+//    is a correction delta on a fixed FP32 background ub (E = e^{ub}), and the
+//    kernels evaluate N(delta) = A(ub + delta) - A(ub) in a form where every
+//    term carries a factor of delta:
+//      (alpha/2) sum_j [ (E_i x_i + E_j x_j)(ub_j - ub_i) + (B_i + B_j)(d_j - d_i) ]
+//      + beta e^{-ub_i/2} (e^{-d_i/2} - 1),    x = expm1(delta), B = E (1 + x).
+//    so that FP32 rounding is relative to the correction, not to u.
+// Both modes give the same Newton derivative (Eq. bc_modified_fR_dop):
+//   dA_i/du_i = (alpha/2) sum_j [ B_i (u_j - u_i) - (B_i + B_j) ] - (beta/2) e^{-u_i/2}.
+//
+// Refinement patches: a ghost neighbour outside the patch takes
+//   u_g = u_b - r u_b + r u_i with r = -1, b_g = exp(u_g)     (Eq. u_i-1jk),
+// so its face contributes (B_i + B_g)(u_g - u_i) and, because u_g depends on
+// u_i, (B_i - B_g)(u_g - u_i) - 2 (B_i + B_g) to the derivative.
+//
+// Red-black ordering: colour = (i + j + k) & 1, red (0) first.
+// Layout: [n2][n1][n0], x fastest.  Packed boundary faces: -x,+x,-y,+y,-z,+z,
+// face normal to axis a indexed by the other axes p < q as c[q]*n[p] + c[p].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace frmg {
+
+template <typename T>
+struct Grid {
+  T *u;            // unknown (delta in background mode)
+  T *x;            // cache: expm1(u)
+  const T *f;      // right-hand side storage; f_i = fs * (f[i] - fo); null = 0
+  T *uR;           // R u^h saved for the FAS correction (coarse levels)
+  const float *ubg;  // background (BG mode), null otherwise
+  const float *Ebg;  // exp(background)
+  const T *bnd;    // packed Dirichlet faces (null: periodic)
+  long long foff[6];
+  long long ncell;
+  int n0, n1, n2;
+  int field;       // index into the active-flag array
+  T ah;            // alpha / 2
+  T beta;
+  T fs, fo;
+  T cap;           // Newton step cap
+};
+
+// ----------------------------------------------------------------------------
+// math wrappers (library functions; no re-derived constants)
+__device__ __forceinline__ float m_exp(float v) { return expf(v); }
+__device__ __forceinline__ double m_exp(double v) { return exp(v); }
+__device__ __forceinline__ float m_expm1(float v) { return expm1f(v); }
+__device__ __forceinline__ double m_expm1(double v) { return expm1(v); }
+__device__ __forceinline__ float m_sqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double m_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float m_rsqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double m_rsqrt(double v) { return rsqrt(v); }
+
+__device__ __forceinline__ int find_grid(const int *off, int ngrid, int b) {
+  int lo = 0, hi = ngrid;  // off[lo] <= b < off[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= b)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool grid_active(const int *active, int field) {
+  return active == nullptr || active[field] != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ long long idx3(const Grid<T> &G, int i, int j, int k) {
+  return ((long long)k * G.n1 + j) * G.n0 + i;
+}
+
+// Boundary value of the face f (0..5) at the boundary cell (i,j,k).
+template <typename T>
+__device__ __forceinline__ T face_value(const Grid<T> &G, int f, int i, int j, int k) {
+  long long o;
+  if (f < 2)
+    o = (long long)k * G.n1 + j;
+  else if (f < 4)
+    o = (long long)k * G.n0 + i;
+  else
+    o = (long long)j * G.n0 + i;
+  return G.bnd[G.foff[f] + o];
+}
+
+template <typename T, bool BG>
+__device__ __forceinline__ void face_regular(const Grid<T> &G, long long cj, T di, T Ei, T xi,
+                                             T Bi, T ubi, T &acc, T &dacc) {
+  T dj = G.u[cj];
+  T xj = G.x[cj];
+  T Ej = BG ? (T)G.Ebg[cj] : T(1);
+  T Bj = BG ? Ej + Ej * xj : T(1) + xj;
+  T dd = dj - di;
+  T w;
+  if (BG) {
+    T gd = (T)G.ubg[cj] - ubi;
+    acc += (Ei * xi + Ej * xj) * gd + (Bi + Bj) * dd;
+    w = gd + dd;
+  } else {
+    acc += (Bi + Bj) * dd;
+    w = dd;
+  }
+  dacc += Bi * w - (Bi + Bj);
+}
+
+template <typename T, bool BG>
+__device__ __forceinline__ void face_ghost(T ubf, T di, T Ei, T xi, T Bi, T ubi, T &acc,
+                                           T &dacc) {
+  T w, Bg;
+  if (BG) {
+    T ubgh = T(2) * ubf - ubi;   // background ghost
+    T Eg = m_exp(ubgh);
+    T xg = -xi / (T(1) + xi);    // expm1(-delta_i)
+    T gd = ubgh - ubi;
+    T dd = T(-2) * di;           // delta_g - delta_i
+    Bg = Eg + Eg * xg;
+    acc += (Ei * xi + Eg * xg) * gd + (Bi + Bg) * dd;
+    w = gd + dd;
+  } else {
+    T ug = T(2) * ubf - di;
+    Bg = m_exp(ug);
+    w = ug - di;
+    acc += (Bi + Bg) * w;
+  }
+  dacc += (Bi - Bg) * w - T(2) * (Bi + Bg);
+}
+
+// A_i (or N_i) and its derivative at cell (i,j,k).
+template <typename T, bool BG>
+__device__ __forceinline__ void cell_eval(const Grid<T> &G, int i, int j, int k, long long c,
+                                          T &N, T &dN) {
+  T di = G.u[c];
+  T xi = G.x[c];
+  T Ei = BG ? (T)G.Ebg[c] : T(1);
+  T ubi = BG ? (T)G.ubg[c] : T(0);
+  T Bi = BG ? Ei + Ei * xi : T(1) + xi;
+  T acc = T(0), dacc = T(0);
+  const bool dir = G.bnd != nullptr;
+  const long long sx = 1, sy = G.n0, sz = (long long)G.n0 * G.n1;
+  // -x, +x
+  if (i > 0)
+    face_regular<T, BG>(G, c - sx, di, Ei, xi, Bi, ubi, acc, dacc);
+  else if (!dir)
+    face_regular<T, BG>(G, c + (G.n0 - 1) * sx, di, Ei, xi, Bi, ubi, acc, dacc);
+  else
+    face_ghost<T, BG>(face_value(G, 0, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
+  if (i < G.n0 - 1)
+    face_regular<T, BG>(G, c + sx, di, Ei, xi, Bi, ubi, acc, dacc);
+  else if (!dir)
+    face_regular<T, BG>(G, c - (G.n0 - 1) * sx, di, Ei, xi, Bi, ubi, acc, dacc);
+  else
+    face_ghost<T, BG>(face_value(G, 1, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
+  // -y, +y
+  if (j > 0)
+    face_regular<T, BG>(G, c - sy, di, Ei, xi, Bi, ubi, acc, dacc);
+  else if (!dir)
+    face_regular<T, BG>(G, c + (G.n1 - 1) * sy, di, Ei, xi, Bi, ubi, acc, dacc);
+  else
+    face_ghost<T, BG>(face_value(G, 2, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
+  if (j < G.n1 - 1)
+    face_regular<T, BG>(G, c + sy, di, Ei, xi, Bi, ubi, acc, dacc);
+  else if (!dir)
+    face_regular<T, BG>(G, c - (G.n1 - 1) * sy, di, Ei, xi, Bi, ubi, acc, dacc);
+  else
+    face_ghost<T, BG>(face_value(G, 3, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
+  // -z, +z
+  if (k > 0)
+    face_regular<T, BG>(G, c - sz, di, Ei, xi, Bi, ubi, acc, dacc);
+  else if (!dir)
+    face_regular<T, BG>(G, c + (G.n2 - 1) * sz, di, Ei, xi, Bi, ubi, acc, dacc);
+  else
+    face_ghost<T, BG>(face_value(G, 4, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
+  if (k < G.n2 - 1)
+    face_regular<T, BG>(G, c + sz, di, Ei, xi, Bi, ubi, acc, dacc);
+  else if (!dir)
+    face_regular<T, BG>(G, c - (G.n2 - 1) * sz, di, Ei, xi, Bi, ubi, acc, dacc);
+  else
+    face_ghost<T, BG>(face_value(G, 5, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
+  // mass term: beta F (e^{-d/2} - 1) with F = e^{-ub/2}; s = e^{d/2}
+  T B1 = T(1) + xi;
+  T s = m_sqrt(B1);
+  T y = -xi / (B1 + s);
+  T F = BG ? m_rsqrt(Ei) : T(1);
+  N = G.ah * acc + G.beta * F * y;
+  dN = G.ah * dacc - T(0.5) * G.beta * F / s;
+}
+
+template <typename T>
+__device__ __forceinline__ T rhs_at(const Grid<T> &G, long long c) {
+  return G.f ? G.fs * (G.f[c] - G.fo) : T(0);
+}
+
+template <typename T, bool BG>
+__device__ __forceinline__ void ngs_update(const Grid<T> &G, int i, int j, int k) {
+  long long c = idx3(G, i, j, k);
+  T N, dN;
+  cell_eval<T, BG>(G, i, j, k, c, N, dN);
+  T du = -(N - rhs_at(G, c)) / dN;
+  du = du > G.cap ? G.cap : (du < -G.cap ? -G.cap : du);
+  T unew = G.u[c] + du;
+  G.u[c] = unew;
+  G.x[c] = m_expm1(unew);
+}
+
+// ---------------------------------------------------------------------------
+// One colour of a red-black Newton-Gauss-Seidel sweep; one thread per cell of
+// that colour.  off[] maps blocks to grids (n0/2 * n1 * n2 threads per grid).
+template <typename T, bool BG>
+__global__ void k_smooth(const Grid<T> *grids, const int *off, int ngrid, int colour,
+                         const int *active) {
+  int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<T> G = grids[g];
+  if (!grid_active(active, G.field)) return;
+  long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
+  int hx = G.n0 >> 1;
+  if (t >= (long long)hx * G.n1 * G.n2) return;
+  int ih = (int)(t % hx);
+  long long r = t / hx;
+  int j = (int)(r % G.n1);
+  int k = (int)(r / G.n1);
+  int i = 2 * ih + ((j + k + colour) & 1);
+  ngs_update<T, BG>(G, i, j, k);
+}
+
+// Block-level (sum of squares, max |v|) partials, one pair per block.
+template <int NT>
+__device__ __forceinline__ void block_reduce2(double s, double m, double *out_s, double *out_m) {
+  __shared__ double ss[NT / 32], sm[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  }
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    ss[w] = s;
+    sm[w] = m;
+  }
+  __syncthreads();
+  if (w == 0) {
+    s = (l < NT / 32) ? ss[l] : 0.0;
+    m = (l < NT / 32) ? sm[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_down_sync(0xffffffffu, s, o);
+      m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    if (l == 0) {
+      *out_s = s;
+      *out_m = m;
+    }
+  }
+}
+
+// d = A(u) - f over every cell; optional output array and per-block partial
+// norms (partial[2*block], partial[2*block+1]).  One thread per cell.
+template <typename T, bool BG, int NT>
+__global__ void __launch_bounds__(NT) k_residual(const Grid<T> *grids, const int *off, int ngrid,
+                                                 T *const *dout, double *partial,
+                                                 const int *active) {
+  int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<T> G = grids[g];
+  double s = 0.0, m = 0.0;
+  long long t = (long long)(blockIdx.x - off[g]) * NT + threadIdx.x;
+  if (grid_active(active, G.field) && t < G.ncell) {
+    int i = (int)(t % G.n0);
+    long long r = t / G.n0;
+    int j = (int)(r % G.n1);
+    int k = (int)(r / G.n1);
+    T N, dN;
+    cell_eval<T, BG>(G, i, j, k, t, N, dN);
+    T d = N - rhs_at(G, t);
+    if (dout && dout[g]) dout[g][t] = d;
+    s = (double)d * (double)d;
+    m = fabs((double)d);
+  }
+  if (partial) block_reduce2<NT>(s, m, &partial[2 * blockIdx.x], &partial[2 * blockIdx.x + 1]);
+}
+
+// Per-grid sums of the block partials: out[2g] = sum of squares, out[2g+1] = max.
+__global__ void k_reduce_partials(const double *partial, const int *off, int ngrid, double *out) {
+  int g = blockIdx.x;
+  if (g >= ngrid) return;
+  double s = 0.0, m = 0.0;
+  for (int b = off[g] + threadIdx.x; b < off[g + 1]; b += blockDim.x) {
+    s += partial[2 * b];
+    m = fmax(m, partial[2 * b + 1]);
+  }
+  block_reduce2<256>(s, m, &out[2 * g], &out[2 * g + 1]);
+}
+
+// Fused residual + restriction (Sec. V.B.2): for each coarse cell, the 8 fine
+// children give  u^H = uR = mean(u^h),  x^H = expm1(u^H),  f^H <- mean(d^h)
+// (the coarse operator is added by k_fas_rhs).  One thread per coarse cell.
+template <typename T, bool BG>
+__global__ void k_resid_restrict(const Grid<T> *fine, const Grid<T> *coarse, const int *off,
+                                 int ngrid, const int *active) {
+  int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<T> F = fine[g];
+  const Grid<T> C = coarse[g];
+  if (!grid_active(active, F.field)) return;
+  long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
+  if (t >= C.ncell) return;
+  int I = (int)(t % C.n0);
+  long long r = t / C.n0;
+  int J = (int)(r % C.n1);
+  int K = (int)(r / C.n1);
+  T su = T(0), sd = T(0);
+#pragma unroll
+  for (int cz = 0; cz < 2; cz++)
+#pragma unroll
+    for (int cy = 0; cy < 2; cy++)
+#pragma unroll
+      for (int cx = 0; cx < 2; cx++) {
+        int i = 2 * I + cx, j = 2 * J + cy, k = 2 * K + cz;
+        long long c = idx3(F, i, j, k);
+        T N, dN;
+        cell_eval<T, BG>(F, i, j, k, c, N, dN);
+        sd += N - rhs_at(F, c);
+        su += F.u[c];
+      }
+  T uh = su * T(0.125);
+  C.uR[t] = uh;
+  C.u[t] = uh;
+  C.x[t] = m_expm1(uh);
+  const_cast<T *>(C.f)[t] = sd * T(0.125);
+}
+
+// f^H = A^H(R u^h) - R d^h, in place over the R d^h stored in f (fs = 1, fo = 0).
+template <typename T, bool BG>
+__global__ void k_fas_rhs(const Grid<T> *grids, const int *off, int ngrid, const int *active) {
+  int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<T> G = grids[g];
+  if (!grid_active(active, G.field)) return;
+  long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
+  if (t >= G.ncell) return;
+  int i = (int)(t % G.n0);
+  long long r = t / G.n0;
+  int j = (int)(r % G.n1);
+  int k = (int)(r / G.n1);
+  T N, dN;
+  cell_eval<T, BG>(G, i, j, k, t, N, dN);
+  T *f = const_cast<T *>(G.f);
+  f[t] = N - f[t];
+}
+
+// u^h += P (u^H - R u^h), trilinear 27/9/3/1 over 64 (Sec. V.A.3); x^h refreshed.
+// Patches: coarse neighbours outside the grid contribute 0.
+template <typename T>
+__global__ void k_prolong(const Grid<T> *fine, const Grid<T> *coarse, const int *off, int ngrid,
+                          const int *active) {
+  int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<T> F = fine[g];
+  const Grid<T> C = coarse[g];
+  if (!grid_active(active, F.field)) return;
+  long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
+  if (t >= F.ncell) return;
+  int i = (int)(t % F.n0);
+  long long r = t / F.n0;
+  int j = (int)(r % F.n1);
+  int k = (int)(r / F.n1);
+  const bool dir = F.bnd != nullptr;
+  int pc[3] = {i >> 1, j >> 1, k >> 1};
+  int oc[3] = {pc[0] + ((i & 1) ? 1 : -1), pc[1] + ((j & 1) ? 1 : -1), pc[2] + ((k & 1) ? 1 : -1)};
+  const int nc[3] = {C.n0, C.n1, C.n2};
+  T s = T(0);
+#pragma unroll
+  for (int sel = 0; sel < 8; sel++) {
+    int cc[3];
+    T w = T(1);
+    bool valid = true;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      bool other = (sel >> d) & 1;
+      cc[d] = other ? oc[d] : pc[d];
+      w *= other ? T(1) : T(3);
+      if (cc[d] < 0 || cc[d] >= nc[d]) {
+        if (dir) valid = false;
+        cc[d] = cc[d] < 0 ? cc[d] + nc[d] : cc[d] - nc[d];
+      }
+    }
+    if (valid) {
+      long long cidx = ((long long)cc[2] * C.n1 + cc[1]) * C.n0 + cc[0];
+      s += (w * T(1.0 / 64.0)) * (C.u[cidx] - C.uR[cidx]);
+    }
+  }
+  T unew = F.u[t] + s;
+  F.u[t] = unew;
+  F.x[t] = m_expm1(unew);
+}
+
+// Coarsest level: one block per grid, Newton-Gauss-Seidel sweeps until
+// rms <= max(rel * rms0, abs_floor) (at least one sweep, at most maxit);
+// stop_on_stall also stops once a sweep reduces the rms by less than 5%.
+template <typename T, bool BG, int NT>
+__global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid, double rel,
+                                                 double abs_floor, int maxit, int stop_on_stall,
+                                                 const int *active) {
+  int g = blockIdx.x;
+  if (g >= ngrid) return;
+  const Grid<T> G = grids[g];
+  if (!grid_active(active, G.field)) return;
+  __shared__ double red_s, red_m;
+  __shared__ int stop;
+  const long long n = G.ncell;
+  const int hx = G.n0 >> 1;
+  const long long nh = (long long)hx * G.n1 * G.n2;
+  double thr = 0.0, prev = 0.0;
+  for (int it = -1; it < maxit; it++) {
+    if (it >= 0) {
+      for (int colour = 0; colour < 2; colour++) {
+        for (long long t = threadIdx.x; t < nh; t += NT) {
+          int ih = (int)(t % hx);
+          long long r = t / hx;
+          int j = (int)(r % G.n1);
+          int k = (int)(r / G.n1);
+          ngs_update<T, BG>(G, 2 * ih + ((j + k + colour) & 1), j, k);
+        }
+        __syncthreads();
+      }
+    }
+    double s = 0.0;
+    for (long long t = threadIdx.x; t < n; t += NT) {
+      int i = (int)(t % G.n0);
+      long long r = t / G.n0;
+      int j = (int)(r % G.n1);
+      int k = (int)(r / G.n1);
+      T N, dN;
+      cell_eval<T, BG>(G, i, j, k, t, N, dN);
+      double d = (double)(N - rhs_at(G, t));
+      s += d * d;
+    }
+    block_reduce2<NT>(s, 0.0, &red_s, &red_m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double rms = sqrt(red_s / (double)n);
+      int st = 0;
+      if (it < 0) {
+        thr = fmax(rel * rms, abs_floor);
+      } else {
+        if (rms <= thr) st = 1;
+        if (stop_on_stall && rms > 0.95 * prev) st = 1;
+      }
+      prev = rms;
+      stop = st;
+    }
+    __syncthreads();
+    if (stop) break;
+  }
+}
+
+// Generic 8-child average (full weighting on cell-centred grids).
+template <typename T>
+__global__ void k_restrict_avg(const T *fine, int nf0, int nf1, int nf2, T *coarse) {
+  int nc0 = nf0 >> 1, nc1 = nf1 >> 1, nc2 = nf2 >> 1;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nc0 * nc1 * nc2) return;
+  int I = (int)(t % nc0);
+  long long r = t / nc0;
+  int J = (int)(r % nc1);
+  int K = (int)(r / nc1);
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
+    s += fine[((long long)k * nf1 + j) * nf0 + i];
+  }
+  coarse[t] = s * T(0.125);
+}
+
+}  // namespace frmg

@@ -1,0 +1,1512 @@
+// frmg_solver.cu -- host driver and C ABI of the f(R) FAS multigrid solver.
+//
+// Method: Li, Zhao, Teyssier & Koyama (arXiv:1110.1379), Sec. V.B: FAS
+// V-cycles of red-black Newton-Gauss-Seidel relaxation on the domain grid and
+// on refinement patches whose Dirichlet boundary values come from the parent
+// solution.  Everything that touches a grid cell runs in the kernels of
+// frmg_kernels.cuh; this file builds level hierarchies, launches kernels and
+// reads back per-grid residual norms.
+//
+// Precisions:
+//  * FR_FP64: the plain method in FP64 (V-cycle, then an FP64 residual norm).
+//  * FR_MIXED: iterative refinement.  Outer loop in FP64: d = A(u) - f
+//    (the fine-grid defect and the convergence test), then FP32 FAS V-cycles
+//    solve N(delta) = -d for a correction on the FP32 background fp32(u),
+//    then u += delta in FP64.
+// Batching: every launch covers all grids (fields or patches) at one depth of
+// their hierarchies; a per-field active flag drops converged fields.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "frmg.h"
+#include "frmg_internal.h"
+#include "frmg_kernels.cuh"
+
+using namespace frmg;
+
+// ---------------------------------------------------------------------------
+// errors
+static thread_local std::string g_last_error;
+
+void frmg_set_error(const std::string &s) { g_last_error = s; }
+
+struct FrError {
+  int status;
+  std::string msg;
+};
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw FrError{FR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};      \
+  } while (0)
+
+#define CK_LAUNCH(ctx)                                                                  \
+  do {                                                                                  \
+    (ctx)->launches++;                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess)                                                              \
+      throw FrError{FR_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)}; \
+  } while (0)
+
+static void einval(const std::string &m) { throw FrError{FR_EINVAL, m}; }
+
+// ---------------------------------------------------------------------------
+// context: device, caching allocator, pinned readback buffer
+struct ProfPending {
+  const char *name;
+  cudaEvent_t a, b;
+};
+
+struct frmg_ctx {
+  int device = 0;
+  long long launches = 0;
+  std::multimap<size_t, void *> free_blocks;
+  std::map<void *, size_t> sizes;
+  double *pinned = nullptr;
+  size_t pinned_n = 0;
+  // optional per-kernel timing with CUDA events on the launch stream
+  bool prof = false;
+  std::vector<ProfPending> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::string> prof_names;
+  std::vector<long long> prof_count;
+  std::vector<double> prof_ms;
+};
+
+static cudaEvent_t ev_get(frmg_ctx *c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Accumulates the finished events (call after a stream synchronisation).
+static void prof_harvest(frmg_ctx *c) {
+  for (auto &p : c->pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(p.b);
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    size_t i = 0;
+    for (; i < c->prof_names.size(); i++)
+      if (c->prof_names[i] == p.name) break;
+    if (i == c->prof_names.size()) {
+      c->prof_names.push_back(p.name);
+      c->prof_count.push_back(0);
+      c->prof_ms.push_back(0.0);
+    }
+    c->prof_count[i]++;
+    c->prof_ms[i] += ms;
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+// Brackets one kernel launch with events when profiling is on.
+struct ProfScope {
+  frmg_ctx *c;
+  cudaStream_t st;
+  const char *name;
+  cudaEvent_t a = nullptr;
+  ProfScope(frmg_ctx *c_, cudaStream_t st_, const char *n) : c(c_), st(st_), name(n) {
+    if (c->prof && (a = ev_get(c)) != nullptr) cudaEventRecord(a, st);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = ev_get(c);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    c->pending.push_back({name, a, b});
+  }
+};
+#define PROF(name) ProfScope prof_scope_(ctx, st, name)
+
+long long &frmg_launch_counter(frmg_ctx *c) { return c->launches; }
+
+static size_t round_bytes(size_t b) { return (b + 4095) & ~(size_t)4095; }
+
+void *frmg_alloc(frmg_ctx *c, size_t bytes) {
+  bytes = round_bytes(std::max<size_t>(bytes, 1));
+  auto it = c->free_blocks.find(bytes);
+  if (it != c->free_blocks.end()) {
+    void *p = it->second;
+    c->free_blocks.erase(it);
+    return p;
+  }
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    // drop the cache and retry once
+    for (auto &kv : c->free_blocks) {
+      cudaFree(kv.second);
+      c->sizes.erase(kv.second);
+    }
+    c->free_blocks.clear();
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw FrError{FR_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+    }
+  }
+  c->sizes[p] = bytes;
+  return p;
+}
+
+void frmg_release(frmg_ctx *c, void *p) {
+  if (!p) return;
+  auto it = c->sizes.find(p);
+  if (it == c->sizes.end()) return;
+  c->free_blocks.emplace(it->second, p);
+}
+
+static double *pinned_buf(frmg_ctx *c, size_t n) {
+  if (c->pinned_n < n) {
+    if (c->pinned) cudaFreeHost(c->pinned);
+    c->pinned = nullptr;
+    c->pinned_n = 0;
+    if (cudaMallocHost((void **)&c->pinned, n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      throw FrError{FR_ENOMEM, "cudaMallocHost failed"};
+    }
+    c->pinned_n = n;
+  }
+  return c->pinned;
+}
+
+// Allocations of one call, returned to the cache on scope exit.
+struct Scope {
+  frmg_ctx *c;
+  std::vector<void *> ptrs;
+  explicit Scope(frmg_ctx *c_) : c(c_) {}
+  template <typename T>
+  T *get(size_t n) {
+    void *p = frmg_alloc(c, n * sizeof(T));
+    ptrs.push_back(p);
+    return (T *)p;
+  }
+  ~Scope() {
+    for (void *p : ptrs) frmg_release(c, p);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// model constants (Sec. II, III.A, VI.A.1), n = 1, flat background
+struct Consts {
+  double alpha, beta, gamma, ct, fbar, ubar;
+};
+
+static Consts model_consts(double box, double h, double a, double om, double fr0) {
+  Consts k;
+  double ol = 1.0 - om;
+  k.ct = 299792.458 / (100.0 * box);
+  double K = 1.0 / (a * a * a) + 4.0 * ol / om;
+  double K1 = 1.0 + 4.0 * ol / om;
+  double xi = fr0 * (3.0 * K1) * (3.0 * K1);
+  k.fbar = a * a * xi / ((3.0 * K) * (3.0 * K));
+  k.alpha = k.ct * k.ct * k.fbar / (h * h);
+  k.beta = om * a * a * a * a * K;
+  k.gamma = om * a;
+  k.ubar = std::log(k.fbar);
+  return k;
+}
+
+static void check_dims(const int n[3], int minn = 2) {
+  for (int d = 0; d < 3; d++)
+    if (n[d] < minn || (n[d] & 1)) einval("dims must be even and >= " + std::to_string(minn));
+}
+
+static void check_model(double box, double a, double om, double fr0) {
+  if (!(box > 0) || !(a > 0) || !(fr0 > 0) || !(om > 0 && om < 1))
+    einval("box, a and |f_R0| must be > 0 and 0 < Omega_m < 1");
+}
+
+// Reading of the level count (the paper does not fix it): halve while every
+// next size is even and >= 4.
+static int count_levels(const int n[3]) {
+  int m[3] = {n[0], n[1], n[2]};
+  int nl = 1;
+  for (;;) {
+    bool ok = true;
+    for (int d = 0; d < 3; d++) {
+      if (m[d] & 1) ok = false;
+      int nx = m[d] / 2;
+      if (nx < 4 || (nx & 1)) ok = false;
+    }
+    if (!ok) break;
+    for (int d = 0; d < 3; d++) m[d] /= 2;
+    nl++;
+  }
+  return nl;
+}
+
+static long long face_total(const int n[3]) {
+  return 2LL * n[1] * n[2] + 2LL * n[0] * n[2] + 2LL * n[0] * n[1];
+}
+
+static void face_offsets(const int n[3], long long off[6]) {
+  long long sz[6] = {(long long)n[1] * n[2], (long long)n[1] * n[2], (long long)n[0] * n[2],
+                     (long long)n[0] * n[2], (long long)n[0] * n[1], (long long)n[0] * n[1]};
+  long long o = 0;
+  for (int f = 0; f < 6; f++) {
+    off[f] = o;
+    o += sz[f];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// small kernels used only by the host driver
+template <typename T>
+__global__ void k_fill(T *p, long long n, T v) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) p[t] = v;
+}
+
+template <typename T>
+__global__ void k_expm1(const T *u, T *x, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) x[t] = m_expm1(u[t]);
+}
+
+template <typename S, typename D>
+__global__ void k_convert(const S *s, D *d, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) d[t] = (D)s[t];
+}
+
+__global__ void k_expf(const float *u, float *e, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) e[t] = expf(u[t]);
+}
+
+// Mixed precision: from the FP64 defect d, the inner right-hand side -d and the
+// FP32 background fp32(u) with e^{fp32(u)}; the correction restarts at 0.
+__global__ void k_prep_inner(const double *d64, const double *u64, float *r32, float *ub32,
+                             float *E32, float *delta, float *x32, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  r32[t] = (float)(-d64[t]);
+  float ub = (float)u64[t];
+  ub32[t] = ub;
+  E32[t] = expf(ub);
+  delta[t] = 0.0f;
+  x32[t] = 0.0f;
+}
+
+// u += delta in FP64, x = expm1(u).
+__global__ void k_update64(double *u64, double *x64, const float *delta, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double u = u64[t] + (double)delta[t];
+  u64[t] = u;
+  x64[t] = expm1(u);
+}
+
+// Restriction of packed boundary faces: a coarse face value is the mean of the
+// 4 fine face values covering it (reading of Sec. V.B.2, "u_B taken as those
+// in the corresponding AMR cells").
+template <typename T>
+__global__ void k_restrict_faces(const T *fine, int nf0, int nf1, int nf2, T *coarse) {
+  int nf[3] = {nf0, nf1, nf2};
+  int nc[3] = {nf0 / 2, nf1 / 2, nf2 / 2};
+  long long tot = 2LL * nc[1] * nc[2] + 2LL * nc[0] * nc[2] + 2LL * nc[0] * nc[1];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  long long offc = 0, offf = 0;
+  for (int f = 0; f < 6; f++) {
+    int ax = f / 2;
+    int p = ax == 0 ? 1 : 0, q = ax == 2 ? 1 : 2;
+    long long szc = (long long)nc[p] * nc[q], szf = (long long)nf[p] * nf[q];
+    if (t < offc + szc) {
+      long long r = t - offc;
+      int P = (int)(r % nc[p]), Q = (int)(r / nc[p]);
+      T s = T(0);
+      for (int b = 0; b < 2; b++)
+        for (int a = 0; a < 2; a++) s += fine[offf + (long long)(2 * Q + b) * nf[p] + 2 * P + a];
+      coarse[t] = s * T(0.25);
+      return;
+    }
+    offc += szc;
+    offf += szf;
+  }
+}
+
+static int nblocks(long long n, int nt = 256) { return (int)((n + nt - 1) / nt); }
+
+// ---------------------------------------------------------------------------
+// problems and level hierarchies
+struct Problem {
+  int n[3];
+  double h, box, a, om, fr0;
+  const double *rho;  // device
+  double *u;          // device, in/out
+  const double *bnd;  // device packed faces (patches) or null
+  Consts k;
+  int nl;
+};
+
+template <typename T>
+struct LevelSet {
+  std::vector<Grid<T>> h;
+  Grid<T> *d = nullptr;
+  std::vector<int> off_half, off_full;
+  int *d_off_half = nullptr, *d_off_full = nullptr;
+  int nblk_half = 0, nblk_full = 0;
+  double *partial = nullptr;  // per-block norm partials
+  double *red = nullptr;      // per-grid (sum of squares, max)
+  T **d_dout = nullptr;       // per-grid residual output pointers
+  bool empty() const { return h.empty(); }
+  int size() const { return (int)h.size(); }
+};
+
+template <typename T>
+static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st) {
+  if (ls.empty()) return;
+  int ng = ls.size();
+  ls.off_half.assign(ng + 1, 0);
+  ls.off_full.assign(ng + 1, 0);
+  for (int g = 0; g < ng; g++) {
+    long long half = (long long)(ls.h[g].n0 / 2) * ls.h[g].n1 * ls.h[g].n2;
+    ls.off_half[g + 1] = ls.off_half[g] + nblocks(half);
+    ls.off_full[g + 1] = ls.off_full[g] + nblocks(ls.h[g].ncell);
+  }
+  ls.nblk_half = ls.off_half[ng];
+  ls.nblk_full = ls.off_full[ng];
+  ls.d = S.get<Grid<T>>(ng);
+  ls.d_off_half = S.get<int>(ng + 1);
+  ls.d_off_full = S.get<int>(ng + 1);
+  CK(cudaMemcpyAsync(ls.d, ls.h.data(), ng * sizeof(Grid<T>), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ls.d_off_half, ls.off_half.data(), (ng + 1) * sizeof(int),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ls.d_off_full, ls.off_full.data(), (ng + 1) * sizeof(int),
+                     cudaMemcpyHostToDevice, st));
+  ls.partial = S.get<double>(2 * (size_t)ls.nblk_full);
+  ls.red = S.get<double>(2 * (size_t)ng);
+  ls.d_dout = S.get<T *>(ng);
+  // host vectors must stay alive until the copies finished
+  CK(cudaStreamSynchronize(st));
+}
+
+// Level hierarchy of a batch of problems in precision T.  BG: background mode
+// (the FP32 inner solve of the mixed loop).
+template <typename T>
+struct Hier {
+  int depth = 0;
+  std::vector<std::vector<Grid<T>>> lev;  // lev[p][l]
+  std::vector<LevelSet<T>> cont, next, coarsest, all;
+  std::vector<float *> bg_u, bg_E;        // fine-level background arrays per problem
+};
+
+template <typename T, bool BG>
+static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap,
+                       cudaStream_t st, frmg_ctx *ctx) {
+  int np = (int)P.size();
+  H.lev.assign(np, {});
+  H.depth = 0;
+  for (auto &p : P) H.depth = std::max(H.depth, p.nl);
+  H.bg_u.assign(np, nullptr);
+  H.bg_E.assign(np, nullptr);
+  for (int pi = 0; pi < np; pi++) {
+    Problem &p = P[pi];
+    int n[3] = {p.n[0], p.n[1], p.n[2]};
+    double h = p.h;
+    const T *bnd_prev = nullptr;
+    for (int l = 0; l < p.nl; l++) {
+      Grid<T> G;
+      memset(&G, 0, sizeof(G));
+      G.n0 = n[0];
+      G.n1 = n[1];
+      G.n2 = n[2];
+      G.ncell = (long long)n[0] * n[1] * n[2];
+      G.field = pi;
+      Consts k = model_consts(p.box, h, p.a, p.om, p.fr0);
+      G.ah = (T)(0.5 * k.alpha);
+      G.beta = (T)k.beta;
+      G.cap = (T)cap;
+      face_offsets(n, G.foff);
+      bool fine_fp64_plain = (l == 0 && !BG && sizeof(T) == 8);
+      if (fine_fp64_plain) {
+        G.u = (T *)p.u;
+        G.f = (const T *)p.rho;
+        G.fs = (T)k.gamma;
+        G.fo = T(1);
+      } else {
+        G.u = S.get<T>(G.ncell);
+        T *f = S.get<T>(G.ncell);
+        G.f = f;
+        G.fs = T(1);
+        G.fo = T(0);
+      }
+      G.x = S.get<T>(G.ncell);
+      if (l > 0) G.uR = S.get<T>(G.ncell);
+      if (BG) {
+        float *ub = S.get<float>(G.ncell);
+        float *E = S.get<float>(G.ncell);
+        G.ubg = ub;
+        G.Ebg = E;
+        if (l == 0) {
+          H.bg_u[pi] = ub;
+          H.bg_E[pi] = E;
+        }
+      }
+      if (p.bnd) {
+        long long nf = face_total(n);
+        T *b = S.get<T>(nf);
+        if (l == 0) {
+          if (sizeof(T) == 8)
+            CK(cudaMemcpyAsync(b, p.bnd, nf * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          else {
+            k_convert<double, float><<<nblocks(nf), 256, 0, st>>>(p.bnd, (float *)b, nf);
+            CK_LAUNCH(ctx);
+          }
+        } else {
+          int nfp[3] = {n[0] * 2, n[1] * 2, n[2] * 2};
+          k_restrict_faces<T><<<nblocks(nf), 256, 0, st>>>(bnd_prev, nfp[0], nfp[1], nfp[2], b);
+          CK_LAUNCH(ctx);
+        }
+        G.bnd = b;
+        bnd_prev = b;
+      }
+      H.lev[pi].push_back(G);
+      for (int d = 0; d < 3; d++) n[d] /= 2;
+      h *= 2.0;
+    }
+  }
+  H.cont.assign(H.depth, {});
+  H.next.assign(H.depth, {});
+  H.coarsest.assign(H.depth, {});
+  H.all.assign(H.depth, {});
+  for (int pi = 0; pi < np; pi++) {
+    int nl = P[pi].nl;
+    for (int l = 0; l < nl; l++) {
+      H.all[l].h.push_back(H.lev[pi][l]);
+      if (l < nl - 1) {
+        H.cont[l].h.push_back(H.lev[pi][l]);
+        H.next[l].h.push_back(H.lev[pi][l + 1]);
+      } else {
+        H.coarsest[l].h.push_back(H.lev[pi][l]);
+      }
+    }
+  }
+  for (int l = 0; l < H.depth; l++) {
+    upload_set(S, H.cont[l], st);
+    upload_set(S, H.next[l], st);
+    upload_set(S, H.coarsest[l], st);
+    upload_set(S, H.all[l], st);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle (Sec. V.B.2), batched over the grids of each depth
+struct CycleOpts {
+  int pre, post;
+  double crs_rel, crs_abs;
+  int crs_maxit, crs_stall;
+};
+
+// Profiling names: kernel family, precision, fine (depth 0) or coarse level.
+static const char *pname(const char *kind, bool f64, bool fine) {
+  static const char *tab[][4] = {
+      {"smooth_f64@fine", "smooth_f64@coarse", "smooth_f32@fine", "smooth_f32@coarse"},
+      {"resid_restrict_f64@fine", "resid_restrict_f64@coarse", "resid_restrict_f32@fine",
+       "resid_restrict_f32@coarse"},
+      {"prolong_f64@fine", "prolong_f64@coarse", "prolong_f32@fine", "prolong_f32@coarse"},
+      {"fas_rhs_f64@coarse", "fas_rhs_f64@coarse", "fas_rhs_f32@coarse", "fas_rhs_f32@coarse"},
+      {"residual_f64@fine", "residual_f64@coarse", "residual_f32@fine", "residual_f32@coarse"}};
+  int row = 0;
+  if (!strcmp(kind, "resid_restrict")) row = 1;
+  else if (!strcmp(kind, "prolong")) row = 2;
+  else if (!strcmp(kind, "fas_rhs")) row = 3;
+  else if (!strcmp(kind, "residual")) row = 4;
+  return tab[row][(f64 ? 0 : 2) + (fine ? 0 : 1)];
+}
+
+template <typename T, bool BG>
+static void smooth_set(frmg_ctx *ctx, LevelSet<T> &s, int sweeps, const int *active,
+                       cudaStream_t st, bool fine = true) {
+  if (s.empty()) return;
+  for (int it = 0; it < sweeps; it++)
+    for (int colour = 0; colour < 2; colour++) {
+      PROF(pname("smooth", sizeof(T) == 8, fine));
+      k_smooth<T, BG><<<s.nblk_half, 256, 0, st>>>(s.d, s.d_off_half, s.size(), colour, active);
+      CK_LAUNCH(ctx);
+    }
+}
+
+template <typename T, bool BG>
+static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const int *active,
+                   cudaStream_t st) {
+  if (!H.coarsest[l].empty()) {
+    auto &c = H.coarsest[l];
+    PROF(sizeof(T) == 8 ? "coarsest_f64" : "coarsest_f32");
+    k_coarsest<T, BG, 256><<<c.size(), 256, 0, st>>>(c.d, c.size(), o.crs_rel, o.crs_abs,
+                                                     o.crs_maxit, o.crs_stall, active);
+    CK_LAUNCH(ctx);
+  }
+  if (H.cont[l].empty()) return;
+  auto &F = H.cont[l];
+  auto &C = H.next[l];
+  smooth_set<T, BG>(ctx, F, o.pre, active, st, l == 0);
+  {
+    PROF(pname("resid_restrict", sizeof(T) == 8, l == 0));
+    k_resid_restrict<T, BG><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, C.size(),
+                                                         active);
+    CK_LAUNCH(ctx);
+  }
+  {
+    PROF(pname("fas_rhs", sizeof(T) == 8, false));
+    k_fas_rhs<T, BG><<<C.nblk_full, 256, 0, st>>>(C.d, C.d_off_full, C.size(), active);
+    CK_LAUNCH(ctx);
+  }
+  vcycle<T, BG>(ctx, H, l + 1, o, active, st);
+  {
+    PROF(pname("prolong", sizeof(T) == 8, l == 0));
+    k_prolong<T><<<F.nblk_full, 256, 0, st>>>(F.d, C.d, F.d_off_full, F.size(), active);
+    CK_LAUNCH(ctx);
+  }
+  smooth_set<T, BG>(ctx, F, o.post, active, st, l == 0);
+}
+
+// Residual norms of every grid of a level set: out[2g] = rms, out[2g+1] = max.
+// dout (host array of ng device pointers, entries may be null) receives d.
+template <typename T, bool BG>
+static void level_norms(frmg_ctx *ctx, LevelSet<T> &s, T *const *dout, const int *active,
+                        cudaStream_t st, std::vector<double> &out) {
+  int ng = s.size();
+  if (dout)
+    CK(cudaMemcpyAsync(s.d_dout, dout, ng * sizeof(T *), cudaMemcpyHostToDevice, st));
+  {
+    PROF(pname("residual", sizeof(T) == 8, true));
+    k_residual<T, BG, 256><<<s.nblk_full, 256, 0, st>>>(s.d, s.d_off_full, ng,
+                                                        dout ? s.d_dout : nullptr, s.partial,
+                                                        active);
+    CK_LAUNCH(ctx);
+  }
+  k_reduce_partials<<<ng, 256, 0, st>>>(s.partial, s.d_off_full, ng, s.red);
+  CK_LAUNCH(ctx);
+  double *hp = pinned_buf(ctx, 2 * (size_t)ng);
+  CK(cudaMemcpyAsync(hp, s.red, 2 * ng * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  prof_harvest(ctx);
+  out.assign(2 * ng, 0.0);
+  for (int g = 0; g < ng; g++) {
+    out[2 * g] = std::sqrt(hp[2 * g] / (double)s.h[g].ncell);
+    out[2 * g + 1] = hp[2 * g + 1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// solve loops
+struct SolveCfg {
+  double tol;
+  int max_vcycles, pre, post;
+  double cap;
+  int inner_cycles, max_outer;
+  int fixed_cycles;  // > 0: exactly this many (FP64 only), no convergence test
+};
+
+static bool bad(double v) { return !(v == v) || std::isinf(v); }
+
+// Plain FP64: V-cycles until every problem has rms <= tol.
+static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &cfg,
+                       std::vector<fr_stats> &stats, cudaStream_t st) {
+  Scope S(ctx);
+  int np = (int)P.size();
+  Hier<double> H;
+  build_hier<double, false>(S, H, P, cfg.cap, st, ctx);
+  for (int pi = 0; pi < np; pi++) {
+    Grid<double> &G = H.lev[pi][0];
+    k_expm1<double><<<nblocks(G.ncell), 256, 0, st>>>(G.u, G.x, G.ncell);
+    CK_LAUNCH(ctx);
+  }
+  int *active = S.get<int>(np);
+  std::vector<int> act(np, 1);
+  CycleOpts co{cfg.pre, cfg.post, 1e-3, 0.1 * cfg.tol, 500, 0};
+  std::vector<double> nr;
+  level_norms<double, false>(ctx, H.all[0], nullptr, nullptr, st, nr);
+  std::vector<double> prev(np);
+  std::vector<int> grow(np, 0);
+  for (int pi = 0; pi < np; pi++) {
+    stats[pi].res0_rms = nr[2 * pi];
+    stats[pi].res_rms = nr[2 * pi];
+    stats[pi].res_max = nr[2 * pi + 1];
+    stats[pi].vcycles = 0;
+    prev[pi] = nr[2 * pi];
+    if (cfg.fixed_cycles <= 0 && nr[2 * pi] <= cfg.tol) act[pi] = 0;
+    if (bad(nr[2 * pi])) throw FrError{FR_EDIVERGED, "non-finite initial residual"};
+  }
+  int maxc = cfg.fixed_cycles > 0 ? cfg.fixed_cycles : cfg.max_vcycles;
+  for (int cyc = 0; cyc < maxc; cyc++) {
+    int nact = 0;
+    for (int v : act) nact += v;
+    if (nact == 0) break;
+    CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    vcycle<double, false>(ctx, H, 0, co, active, st);
+    level_norms<double, false>(ctx, H.all[0], nullptr, nullptr, st, nr);
+    for (int pi = 0; pi < np; pi++) {
+      if (!act[pi]) continue;
+      stats[pi].vcycles++;
+      stats[pi].res_rms = nr[2 * pi];
+      stats[pi].res_max = nr[2 * pi + 1];
+      if (bad(nr[2 * pi])) throw FrError{FR_EDIVERGED, "non-finite residual"};
+      grow[pi] = nr[2 * pi] > prev[pi] ? grow[pi] + 1 : 0;
+      if (grow[pi] >= 5) throw FrError{FR_EDIVERGED, "residual grew for 5 cycles"};
+      prev[pi] = nr[2 * pi];
+      if (cfg.fixed_cycles <= 0 && nr[2 * pi] <= cfg.tol) act[pi] = 0;
+    }
+  }
+}
+
+// Mixed: FP64 defect / update / test around FP32 background-mode V-cycles.
+static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &cfg,
+                        std::vector<fr_stats> &stats, cudaStream_t st) {
+  Scope S(ctx);
+  int np = (int)P.size();
+  Hier<double> H64;  // FP64 fine levels only (defect); coarse levels unused
+  std::vector<Problem> P1 = P;
+  for (auto &p : P1) p.nl = 1;
+  build_hier<double, false>(S, H64, P1, cfg.cap, st, ctx);
+  Hier<float> H;
+  build_hier<float, true>(S, H, P, cfg.cap, st, ctx);
+  std::vector<double *> d64(np);
+  for (int pi = 0; pi < np; pi++) {
+    Grid<double> &G = H64.lev[pi][0];
+    d64[pi] = S.get<double>(G.ncell);
+    k_expm1<double><<<nblocks(G.ncell), 256, 0, st>>>(G.u, G.x, G.ncell);
+    CK_LAUNCH(ctx);
+  }
+  int *active = S.get<int>(np);
+  std::vector<int> act(np, 1);
+  CycleOpts co{cfg.pre, cfg.post, 1e-3, 0.0, 500, 1};
+  std::vector<double> nr, inr;
+  std::vector<double> prev(np, 0.0);
+  std::vector<int> grow(np, 0);
+  for (int pi = 0; pi < np; pi++) {
+    stats[pi].vcycles = 0;
+    stats[pi].outer = 0;
+  }
+  for (int outer = 0; outer < cfg.max_outer; outer++) {
+    // FP64 defect and convergence test
+    CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    level_norms<double, false>(ctx, H64.all[0], d64.data(), active, st, nr);
+    int nact = 0;
+    for (int pi = 0; pi < np; pi++) {
+      if (!act[pi]) continue;
+      stats[pi].outer++;
+      if (outer == 0) stats[pi].res0_rms = nr[2 * pi];
+      stats[pi].res_rms = nr[2 * pi];
+      stats[pi].res_max = nr[2 * pi + 1];
+      if (bad(nr[2 * pi])) throw FrError{FR_EDIVERGED, "non-finite residual"};
+      if (outer > 0) {
+        grow[pi] = nr[2 * pi] > prev[pi] ? grow[pi] + 1 : 0;
+        if (grow[pi] >= 3) throw FrError{FR_EDIVERGED, "FP64 defect grew for 3 outer steps"};
+      }
+      prev[pi] = nr[2 * pi];
+      if (nr[2 * pi] <= cfg.tol)
+        act[pi] = 0;
+      else
+        nact++;
+    }
+    if (nact == 0) return;
+    bool any_left = false;
+    for (int pi = 0; pi < np; pi++)
+      if (act[pi] && stats[pi].vcycles < cfg.max_vcycles) any_left = true;
+    if (!any_left) return;
+    CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    // inner problem set-up: rhs, background on every level, zero correction
+    for (int pi = 0; pi < np; pi++) {
+      if (!act[pi]) continue;
+      Grid<float> &G = H.lev[pi][0];
+      Grid<double> &G64 = H64.lev[pi][0];
+      PROF("prep_inner");
+      k_prep_inner<<<nblocks(G.ncell), 256, 0, st>>>(d64[pi], G64.u, const_cast<float *>(G.f),
+                                                     H.bg_u[pi], H.bg_E[pi], G.u, G.x, G.ncell);
+      CK_LAUNCH(ctx);
+      for (size_t l = 1; l < H.lev[pi].size(); l++) {
+        Grid<float> &F = H.lev[pi][l - 1];
+        Grid<float> &C = H.lev[pi][l];
+        k_restrict_avg<float><<<nblocks(C.ncell), 256, 0, st>>>(F.ubg, F.n0, F.n1, F.n2,
+                                                                const_cast<float *>(C.ubg));
+        CK_LAUNCH(ctx);
+        k_expf<<<nblocks(C.ncell), 256, 0, st>>>(C.ubg, const_cast<float *>(C.Ebg), C.ncell);
+        CK_LAUNCH(ctx);
+      }
+    }
+    // inner FP32 V-cycles: the first outer step runs until the FP32 residual
+    // stops falling; later ones run inner_cycles
+    int kmax = outer == 0 ? 30 : cfg.inner_cycles;
+    std::vector<double> r0;
+    if (outer == 0) level_norms<float, true>(ctx, H.all[0], nullptr, active, st, r0);
+    std::vector<double> rp = r0;
+    for (int k = 0; k < kmax; k++) {
+      vcycle<float, true>(ctx, H, 0, co, active, st);
+      for (int pi = 0; pi < np; pi++)
+        if (act[pi]) stats[pi].vcycles++;
+      if (outer == 0) {
+        level_norms<float, true>(ctx, H.all[0], nullptr, active, st, inr);
+        bool go = false;
+        for (int pi = 0; pi < np; pi++) {
+          if (!act[pi]) continue;
+          double r = inr[2 * pi];
+          if (r > 1e-6 * r0[2 * pi] && r < 0.5 * rp[2 * pi] && r > 0.3 * cfg.tol) go = true;
+          rp[2 * pi] = r;
+        }
+        if (!go) break;
+      }
+    }
+    // u += delta (FP64)
+    for (int pi = 0; pi < np; pi++) {
+      if (!act[pi]) continue;
+      Grid<double> &G64 = H64.lev[pi][0];
+      PROF("update64");
+      k_update64<<<nblocks(G64.ncell), 256, 0, st>>>(G64.u, G64.x, H.lev[pi][0].u, G64.ncell);
+      CK_LAUNCH(ctx);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host/device staging
+static bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Staged {
+  void *dev = nullptr;
+  const void *host_src = nullptr;
+  void *host_dst = nullptr;
+  size_t bytes = 0;
+};
+
+// Returns a device view of p; host memory is copied in (and back if `out`).
+template <typename T>
+static T *stage(Scope &S, std::vector<Staged> &back, const T *p, size_t n, bool in, bool out,
+                cudaStream_t st) {
+  if (!p) return nullptr;
+  if (is_device_ptr(p)) return const_cast<T *>(p);
+  T *d = S.get<T>(n);
+  if (in) CK(cudaMemcpyAsync(d, p, n * sizeof(T), cudaMemcpyHostToDevice, st));
+  if (out) back.push_back({d, p, const_cast<T *>(p), n * sizeof(T)});
+  return d;
+}
+
+static void unstage(std::vector<Staged> &back, cudaStream_t st) {
+  for (auto &s : back) CK(cudaMemcpyAsync(s.host_dst, s.dev, s.bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+}
+
+static void finish(frmg_ctx *ctx, std::vector<Staged> &back, cudaStream_t st) {
+  unstage(back, st);
+  prof_harvest(ctx);
+}
+
+// density validation (NaN always rejected; negative unless allowed)
+__global__ void k_check_density(const double *rho, long long n, int allow_neg, int *bad) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double v = rho[t];
+  if (!(v == v) || isinf(v) || (!allow_neg && v < 0.0)) atomicExch(bad, 1);
+}
+
+static void validate_density(frmg_ctx *ctx, Scope &S, const double *rho, long long n,
+                             int allow_neg, cudaStream_t st) {
+  int *bad = S.get<int>(1);
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  k_check_density<<<nblocks(n), 256, 0, st>>>(rho, n, allow_neg, bad);
+  CK_LAUNCH(ctx);
+  int hb = 0;
+  CK(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hb) einval("density has NaN/Inf or negative values");
+}
+
+static fr_opts resolve_opts(const fr_opts *o) {
+  fr_opts r;
+  fr_opts_default(&r);
+  if (o) r = *o;
+  return r;
+}
+
+static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &o, double tol,
+                         std::vector<fr_stats> &stats, cudaStream_t st, int fixed = 0) {
+  SolveCfg cfg{tol, o.max_vcycles, o.pre, o.post, o.newton_step_cap, o.inner_cycles,
+               o.max_outer, fixed};
+  if (o.pre < 0 || o.post < 0 || o.max_vcycles < 0 || !(o.newton_step_cap > 0) ||
+      !(tol >= 0) || o.inner_cycles < 1 || o.max_outer < 1)
+    einval("invalid options");
+  for (auto &p : P) {
+    p.nl = count_levels(p.n);
+    p.k = model_consts(p.box, p.h, p.a, p.om, p.fr0);
+  }
+  if (o.prec == FR_MIXED && fixed <= 0)
+    solve_mixed(ctx, P, cfg, stats, st);
+  else
+    solve_fp64(ctx, P, cfg, stats, st);
+}
+
+static int status_from_stats(const std::vector<fr_stats> &stats, double tol) {
+  for (auto &s : stats)
+    if (!(s.res_rms <= tol)) return FR_ENOCONV;
+  return FR_OK;
+}
+
+template <typename F>
+static int guard(F &&f) {
+  try {
+    return f();
+  } catch (FrError &e) {
+    g_last_error = e.msg;
+    return e.status;
+  } catch (std::exception &e) {
+    g_last_error = e.what();
+    return FR_ENOMEM;
+  }
+}
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// ---------------------------------------------------------------------------
+// patch boundary set-up kernel (Sec. V.A.1, V.B.1, VI.B): trilinear value of
+// the parent at a fine cell g (relative to the patch corner; may be -1 or n
+// for ghosts).  Returns false if the stencil leaves a non-periodic parent.
+__device__ bool parent_interp(const double *up, int p0, int p1, int p2, int periodic,
+                              const int org[3], const int g[3], double *val) {
+  const int np_[3] = {p0, p1, p2};
+  int par[3], oth[3];
+  for (int d = 0; d < 3; d++) {
+    int fg = 2 * org[d] + g[d];
+    int pc = fg >= 0 ? fg / 2 : -((-fg + 1) / 2);
+    par[d] = pc;
+    oth[d] = pc + ((fg - 2 * pc == 0) ? -1 : 1);
+  }
+  double s = 0.0;
+  for (int sel = 0; sel < 8; sel++) {
+    int cc[3];
+    double w = 1.0;
+    for (int d = 0; d < 3; d++) {
+      int o = (sel >> d) & 1;
+      cc[d] = o ? oth[d] : par[d];
+      w *= o ? 1.0 : 3.0;
+      if (cc[d] < 0 || cc[d] >= np_[d]) {
+        if (!periodic) return false;
+        cc[d] = ((cc[d] % np_[d]) + np_[d]) % np_[d];
+      }
+    }
+    s += (w / 64.0) * up[((long long)cc[2] * p1 + cc[1]) * p0 + cc[0]];
+  }
+  *val = s;
+  return true;
+}
+
+__global__ void k_patch_init(const double *up, int p0, int p1, int p2, int periodic, int o0, int o1,
+                             int o2, int n0, int n1, int n2, double *u_init, int *bad) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n0 * n1 * n2) return;
+  int g[3] = {(int)(t % n0), (int)((t / n0) % n1), (int)(t / ((long long)n0 * n1))};
+  int org[3] = {o0, o1, o2};
+  double v = 0.0;
+  if (!parent_interp(up, p0, p1, p2, periodic, org, g, &v)) atomicExch(bad, 1);
+  u_init[t] = v;
+}
+
+__global__ void k_patch_faces(const double *up, int p0, int p1, int p2, int periodic, int o0,
+                              int o1, int o2, int n0, int n1, int n2, const double *u_init,
+                              double *ub, int *bad) {
+  const int n[3] = {n0, n1, n2};
+  long long tot = 2LL * n1 * n2 + 2LL * n0 * n2 + 2LL * n0 * n1;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  long long off = 0;
+  int org[3] = {o0, o1, o2};
+  for (int f = 0; f < 6; f++) {
+    int ax = f / 2;
+    int p = ax == 0 ? 1 : 0, q = ax == 2 ? 1 : 2;
+    long long sz = (long long)n[p] * n[q];
+    if (t < off + sz) {
+      long long r = t - off;
+      int P = (int)(r % n[p]), Q = (int)(r / n[p]);
+      int inner[3], ghost[3];
+      inner[p] = ghost[p] = P;
+      inner[q] = ghost[q] = Q;
+      inner[ax] = (f & 1) ? n[ax] - 1 : 0;
+      ghost[ax] = (f & 1) ? n[ax] : -1;
+      double ug = 0.0;
+      if (!parent_interp(up, p0, p1, p2, periodic, org, ghost, &ug)) atomicExch(bad, 1);
+      double ui = u_init[((long long)inner[2] * n1 + inner[1]) * n0 + inner[0]];
+      ub[t] = 0.5 * (ug + ui);
+      return;
+    }
+    off += sz;
+  }
+}
+
+static void patch_bc_dev(frmg_ctx *ctx, Scope &S, const double *up, const int np_[3], int periodic,
+                         const int org[3], const int n[3], double *u_init, double *ub,
+                         cudaStream_t st) {
+  int *bad = S.get<int>(1);
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  long long nc = (long long)n[0] * n[1] * n[2];
+  k_patch_init<<<nblocks(nc), 256, 0, st>>>(up, np_[0], np_[1], np_[2], periodic, org[0], org[1],
+                                            org[2], n[0], n[1], n[2], u_init, bad);
+  CK_LAUNCH(ctx);
+  long long nf = face_total(n);
+  k_patch_faces<<<nblocks(nf), 256, 0, st>>>(up, np_[0], np_[1], np_[2], periodic, org[0],
+                                             org[1], org[2], n[0], n[1], n[2], u_init, ub, bad);
+  CK_LAUNCH(ctx);
+  int hb = 0;
+  CK(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hb) einval("patch interpolation stencil leaves its parent (needs a 1-parent-cell margin)");
+}
+
+// y += s * x
+__global__ void k_axpy(double *y, const double *x, double s, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] += s * x[t];
+}
+
+void frmg_axpy(double *y, const double *x, double s, long long n, cudaStream_t st,
+               frmg_ctx *ctx) {
+  k_axpy<<<nblocks(n), 256, 0, st>>>(y, x, s, n);
+  CK_LAUNCH(ctx);
+}
+
+// ===========================================================================
+// C ABI
+extern "C" {
+
+void fr_opts_default(fr_opts *o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->max_vcycles = 100;
+  o->pre = 2;
+  o->post = 2;
+  o->prec = FR_FP64;
+  o->newton_step_cap = 1.0;
+  o->inner_cycles = 2;
+  o->max_outer = 40;
+  o->allow_negative_density = 0;
+  o->use_graph = 1;
+}
+
+const char *fr_status_string(int s) {
+  switch (s) {
+    case FR_OK: return "FR_OK";
+    case FR_EINVAL: return "FR_EINVAL: invalid argument";
+    case FR_ENOMEM: return "FR_ENOMEM: allocation failed";
+    case FR_ECUDA: return "FR_ECUDA: CUDA error";
+    case FR_ENOCONV: return "FR_ENOCONV: tolerance not reached";
+    case FR_EDIVERGED: return "FR_EDIVERGED: iteration diverged";
+    case FR_ETIMEOUT: return "FR_ETIMEOUT: device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char *fr_last_error(void) { return g_last_error.c_str(); }
+
+int fr_ctx_create(frmg_ctx **out, int device) {
+  return guard([&]() {
+    if (!out) einval("out is NULL");
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) einval("no such device");
+    CK(cudaSetDevice(device));
+    frmg_ctx *c = new frmg_ctx();
+    c->device = device;
+    *out = c;
+    return FR_OK;
+  });
+}
+
+void fr_ctx_destroy(frmg_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  prof_harvest(c);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  for (auto &kv : c->sizes) cudaFree(kv.first);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+}
+
+long long fr_launch_count(const frmg_ctx *c) { return c ? c->launches : 0; }
+
+int fr_profile(frmg_ctx *c, int enable) {
+  if (!c) return FR_EINVAL;
+  prof_harvest(c);
+  c->prof = enable != 0;
+  c->prof_names.clear();
+  c->prof_count.clear();
+  c->prof_ms.clear();
+  return FR_OK;
+}
+
+int fr_profile_entry(frmg_ctx *c, int idx, char *name, int namelen, long long *count,
+                     double *total_ms) {
+  if (!c || idx < 0) return FR_EINVAL;
+  prof_harvest(c);
+  if (idx >= (int)c->prof_names.size()) return FR_EINVAL;
+  if (name && namelen > 0) {
+    strncpy(name, c->prof_names[idx].c_str(), (size_t)namelen - 1);
+    name[namelen - 1] = 0;
+  }
+  if (count) *count = c->prof_count[idx];
+  if (total_ms) *total_ms = c->prof_ms[idx];
+  return FR_OK;
+}
+
+int fr_constants(double box, int n0, double a, double om, double fr0, double *out6) {
+  return guard([&]() {
+    check_model(box, a, om, fr0);
+    if (n0 <= 0 || !out6) einval("n0 <= 0 or out NULL");
+    Consts k = model_consts(box, 1.0 / n0, a, om, fr0);
+    out6[0] = k.alpha;
+    out6[1] = k.beta;
+    out6[2] = k.gamma;
+    out6[3] = k.ct;
+    out6[4] = k.fbar;
+    out6[5] = k.ubar;
+    return FR_OK;
+  });
+}
+
+static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], double box,
+                      double a, double om, double fr0, double tol, double *u, const fr_opts *opts,
+                      fr_stats *stats, void *stream, int fixed) {
+  double t0 = now_s();
+  return guard([&]() {
+    if (!ctx || !density || !dims || !u) einval("NULL argument");
+    check_dims(dims);
+    check_model(box, a, om, fr0);
+    fr_opts o = resolve_opts(opts);
+    if (fixed > 0 && o.prec != FR_FP64) einval("fixed cycle counts are FP64 only");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Scope S(ctx);
+    std::vector<Staged> back;
+    long long nc = (long long)dims[0] * dims[1] * dims[2];
+    const double *drho = stage(S, back, density, nc, true, false, st);
+    double *du = stage(S, back, u, nc, true, true, st);
+    validate_density(ctx, S, drho, nc, o.allow_negative_density, st);
+    Problem p;
+    memset(&p, 0, sizeof(p));
+    for (int d = 0; d < 3; d++) p.n[d] = dims[d];
+    p.h = 1.0 / dims[0];
+    p.box = box;
+    p.a = a;
+    p.om = om;
+    p.fr0 = fr0;
+    p.rho = drho;
+    p.u = du;
+    std::vector<Problem> P{p};
+    std::vector<fr_stats> sv(1);
+    memset(sv.data(), 0, sizeof(fr_stats));
+    int status = FR_OK;
+    try {
+      run_problems(ctx, P, o, tol, sv, st, fixed);
+      status = fixed > 0 ? FR_OK : status_from_stats(sv, tol);
+    } catch (FrError &e) {
+      if (e.status != FR_EDIVERGED) throw;
+      status = e.status;
+      g_last_error = e.msg;
+    }
+    finish(ctx, back, st);
+    sv[0].seconds = now_s() - t0;
+    if (stats) *stats = sv[0];
+    return status;
+  });
+}
+
+int fr_solve(frmg_ctx *ctx, const double *density, const int dims[3], double box, double a,
+             double om, double fr0, double tol, double *u, const fr_opts *opts, fr_stats *stats,
+             void *stream) {
+  return solve_impl(ctx, density, dims, box, a, om, fr0, tol, u, opts, stats, stream, 0);
+}
+
+int fr_vcycles(frmg_ctx *ctx, const double *density, const int dims[3], double box, double a,
+               double om, double fr0, double *u, int ncycles, const fr_opts *opts,
+               fr_stats *stats, void *stream) {
+  if (ncycles <= 0) {
+    g_last_error = "ncycles must be > 0";
+    return FR_EINVAL;
+  }
+  return solve_impl(ctx, density, dims, box, a, om, fr0, 0.0, u, opts, stats, stream, ncycles);
+}
+
+int fr_solve_batch(frmg_ctx *ctx, int nfields, const double *const *density, const int (*dims)[3],
+                   const double *box, const double *a, const double *fr0, double om, double tol,
+                   double *const *u, const fr_opts *opts, fr_stats *stats, void *stream) {
+  double t0 = now_s();
+  return guard([&]() {
+    if (!ctx || nfields <= 0 || !density || !dims || !box || !a || !fr0 || !u)
+      einval("NULL argument or nfields <= 0");
+    fr_opts o = resolve_opts(opts);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Scope S(ctx);
+    std::vector<Staged> back;
+    std::vector<Problem> P(nfields);
+    for (int i = 0; i < nfields; i++) {
+      if (!density[i] || !u[i]) einval("NULL field pointer");
+      check_dims(dims[i]);
+      check_model(box[i], a[i], om, fr0[i]);
+      long long nc = (long long)dims[i][0] * dims[i][1] * dims[i][2];
+      Problem &p = P[i];
+      memset(&p, 0, sizeof(p));
+      for (int d = 0; d < 3; d++) p.n[d] = dims[i][d];
+      p.h = 1.0 / dims[i][0];
+      p.box = box[i];
+      p.a = a[i];
+      p.om = om;
+      p.fr0 = fr0[i];
+      p.rho = stage(S, back, density[i], nc, true, false, st);
+      p.u = stage(S, back, u[i], nc, true, true, st);
+      validate_density(ctx, S, p.rho, nc, o.allow_negative_density, st);
+    }
+    std::vector<fr_stats> sv(nfields);
+    memset(sv.data(), 0, nfields * sizeof(fr_stats));
+    int status = FR_OK;
+    try {
+      run_problems(ctx, P, o, tol, sv, st);
+      status = status_from_stats(sv, tol);
+    } catch (FrError &e) {
+      if (e.status != FR_EDIVERGED) throw;
+      status = e.status;
+      g_last_error = e.msg;
+    }
+    finish(ctx, back, st);
+    double dt = now_s() - t0;
+    if (stats)
+      for (int i = 0; i < nfields; i++) {
+        stats[i] = sv[i];
+        stats[i].seconds = dt;
+      }
+    return status;
+  });
+}
+
+int fr_solve_levels(frmg_ctx *ctx, const double *density, const int dims[3], double box, double a,
+                    double om, double fr0, double tol, double tol_patch, double *u,
+                    fr_patch *patches, int npatch, const fr_opts *opts, fr_stats *per_grid,
+                    void *stream) {
+  double t0 = now_s();
+  return guard([&]() {
+    if (!ctx || !density || !dims || !u || (npatch > 0 && !patches) || npatch < 0)
+      einval("NULL argument");
+    check_dims(dims);
+    check_model(box, a, om, fr0);
+    fr_opts o = resolve_opts(opts);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Scope S(ctx);
+    std::vector<Staged> back;
+    // validate nesting on the host
+    std::vector<int> level(npatch, 0);
+    std::vector<std::array<int, 3>> pdims(npatch);
+    for (int i = 0; i < npatch; i++) {
+      fr_patch &pp = patches[i];
+      if (pp.parent >= i || pp.parent < -1) einval("patch parent must precede the patch");
+      if (!pp.density || !pp.u) einval("NULL patch pointer");
+      check_dims(pp.n, 4);
+      const int *par = pp.parent < 0 ? dims : pdims[pp.parent].data();
+      level[i] = pp.parent < 0 ? 1 : level[pp.parent] + 1;
+      for (int d = 0; d < 3; d++) {
+        pdims[i][d] = pp.n[d];
+        if (pp.parent >= 0) {
+          // footprint + 1 parent cell must lie inside the parent patch
+          if (pp.origin[d] < 1 || pp.origin[d] + pp.n[d] / 2 + 1 > par[d])
+            einval("patch " + std::to_string(i) + " not nested with a 1-cell margin");
+        } else if (pp.n[d] / 2 > par[d]) {
+          einval("patch larger than the domain");
+        }
+      }
+    }
+    long long nc = (long long)dims[0] * dims[1] * dims[2];
+    const double *drho = stage(S, back, density, nc, true, false, st);
+    double *du = stage(S, back, u, nc, true, true, st);
+    validate_density(ctx, S, drho, nc, o.allow_negative_density, st);
+    std::vector<fr_stats> all(1 + npatch);
+    memset(all.data(), 0, all.size() * sizeof(fr_stats));
+    int status = FR_OK;
+    auto run = [&](std::vector<Problem> &P, std::vector<fr_stats> &sv, double tl) {
+      try {
+        run_problems(ctx, P, o, tl, sv, st);
+        int s2 = status_from_stats(sv, tl);
+        if (s2 != FR_OK && status == FR_OK) status = s2;
+      } catch (FrError &e) {
+        if (e.status != FR_EDIVERGED) throw;
+        status = e.status;
+        g_last_error = e.msg;
+      }
+    };
+    {
+      Problem p;
+      memset(&p, 0, sizeof(p));
+      for (int d = 0; d < 3; d++) p.n[d] = dims[d];
+      p.h = 1.0 / dims[0];
+      p.box = box;
+      p.a = a;
+      p.om = om;
+      p.fr0 = fr0;
+      p.rho = drho;
+      p.u = du;
+      std::vector<Problem> P{p};
+      std::vector<fr_stats> sv(1);
+      memset(sv.data(), 0, sizeof(fr_stats));
+      run(P, sv, tol);
+      all[0] = sv[0];
+    }
+    // patches level by level (one batched solve per refinement level)
+    std::vector<double *> pu(npatch, nullptr);
+    std::vector<double> ph(npatch, 0.0);
+    int maxlev = 0;
+    for (int i = 0; i < npatch; i++) maxlev = std::max(maxlev, level[i]);
+    for (int lv = 1; lv <= maxlev; lv++) {
+      std::vector<Problem> P;
+      std::vector<int> ids;
+      for (int i = 0; i < npatch; i++) {
+        if (level[i] != lv) continue;
+        fr_patch &pp = patches[i];
+        long long pn = (long long)pp.n[0] * pp.n[1] * pp.n[2];
+        const double *prho = stage(S, back, pp.density, pn, true, false, st);
+        pu[i] = stage(S, back, pp.u, pn, false, true, st);
+        validate_density(ctx, S, prho, pn, o.allow_negative_density, st);
+        double *ub = S.get<double>(face_total(pp.n));
+        const double *up = pp.parent < 0 ? du : pu[pp.parent];
+        const int *pdim = pp.parent < 0 ? dims : pdims[pp.parent].data();
+        double hpar = pp.parent < 0 ? 1.0 / dims[0] : ph[pp.parent];
+        patch_bc_dev(ctx, S, up, pdim, pp.parent < 0, pp.origin, pp.n, pu[i], ub, st);
+        ph[i] = 0.5 * hpar;
+        Problem p;
+        memset(&p, 0, sizeof(p));
+        for (int d = 0; d < 3; d++) p.n[d] = pp.n[d];
+        p.h = ph[i];
+        p.box = box;
+        p.a = a;
+        p.om = om;
+        p.fr0 = fr0;
+        p.rho = prho;
+        p.u = pu[i];
+        p.bnd = ub;
+        P.push_back(p);
+        ids.push_back(i);
+      }
+      std::vector<fr_stats> sv(P.size());
+      memset(sv.data(), 0, sv.size() * sizeof(fr_stats));
+      run(P, sv, tol_patch);
+      for (size_t j = 0; j < ids.size(); j++) all[1 + ids[j]] = sv[j];
+    }
+    finish(ctx, back, st);
+    double dt = now_s() - t0;
+    if (per_grid)
+      for (int i = 0; i <= npatch; i++) {
+        per_grid[i] = all[i];
+        per_grid[i].seconds = dt;
+      }
+    return status;
+  });
+}
+
+// ---- single-step entry points ----
+static Problem one_level(const int dims[3], double h, double box, double a, double om,
+                         double fr0) {
+  check_dims(dims);
+  check_model(box, a, om, fr0);
+  if (!(h > 0)) einval("h must be > 0");
+  Problem p;
+  memset(&p, 0, sizeof(p));
+  for (int d = 0; d < 3; d++) p.n[d] = dims[d];
+  p.h = h;
+  p.box = box;
+  p.a = a;
+  p.om = om;
+  p.fr0 = fr0;
+  p.nl = 1;
+  return p;
+}
+
+// One FP64 level whose right-hand side is gamma(rho-1) + f.
+static Grid<double> single_grid(Scope &S, frmg_ctx *ctx, Problem &p, double *u, const double *rho,
+                                const double *f, const double *ub, double cap, cudaStream_t st) {
+  Consts k = model_consts(p.box, p.h, p.a, p.om, p.fr0);
+  Grid<double> G;
+  memset(&G, 0, sizeof(G));
+  G.n0 = p.n[0];
+  G.n1 = p.n[1];
+  G.n2 = p.n[2];
+  G.ncell = (long long)p.n[0] * p.n[1] * p.n[2];
+  G.ah = 0.5 * k.alpha;
+  G.beta = k.beta;
+  G.cap = cap;
+  G.u = u;
+  G.x = S.get<double>(G.ncell);
+  face_offsets(p.n, G.foff);
+  G.bnd = ub;
+  // right-hand side gamma (rho - 1) + f, stored as rho + f/gamma with fs = gamma, fo = 1
+  double *ft = S.get<double>(G.ncell);
+  k_convert<double, double><<<nblocks(G.ncell), 256, 0, st>>>(rho, ft, G.ncell);
+  CK_LAUNCH(ctx);
+  G.f = ft;
+  G.fs = k.gamma;
+  G.fo = 1.0;
+  if (f) frmg_axpy(ft, f, 1.0 / k.gamma, G.ncell, st, ctx);
+  k_expm1<double><<<nblocks(G.ncell), 256, 0, st>>>(G.u, G.x, G.ncell);
+  CK_LAUNCH(ctx);
+  return G;
+}
+
+int fr_smooth(frmg_ctx *ctx, double *u, const double *density, const double *f, const int dims[3],
+              double h, double box, double a, double om, double fr0, const double *ub, int nsweeps,
+              double cap, void *stream) {
+  return guard([&]() {
+    if (!ctx || !u || !density || !dims || nsweeps < 0 || !(cap > 0)) einval("bad argument");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Problem p = one_level(dims, h, box, a, om, fr0);
+    Scope S(ctx);
+    std::vector<Staged> back;
+    long long nc = (long long)dims[0] * dims[1] * dims[2];
+    double *du = stage(S, back, u, nc, true, true, st);
+    const double *dr = stage(S, back, density, nc, true, false, st);
+    const double *df = stage(S, back, f, nc, true, false, st);
+    const double *dub = stage(S, back, ub, ub ? face_total(dims) : 0, true, false, st);
+    LevelSet<double> ls;
+    ls.h.push_back(single_grid(S, ctx, p, du, dr, df, dub, cap, st));
+    upload_set(S, ls, st);
+    smooth_set<double, false>(ctx, ls, nsweeps, nullptr, st);
+    finish(ctx, back, st);
+    return FR_OK;
+  });
+}
+
+int fr_residual(frmg_ctx *ctx, const double *u, const double *density, const double *f,
+                const int dims[3], double h, double box, double a, double om, double fr0,
+                const double *ub, double *d, void *stream) {
+  return guard([&]() {
+    if (!ctx || !u || !density || !dims || !d) einval("bad argument");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Problem p = one_level(dims, h, box, a, om, fr0);
+    Scope S(ctx);
+    std::vector<Staged> back;
+    long long nc = (long long)dims[0] * dims[1] * dims[2];
+    double *du = S.get<double>(nc);
+    const double *su = stage(S, back, u, nc, true, false, st);
+    CK(cudaMemcpyAsync(du, su, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    const double *dr = stage(S, back, density, nc, true, false, st);
+    const double *df = stage(S, back, f, nc, true, false, st);
+    const double *dub = stage(S, back, ub, ub ? face_total(dims) : 0, true, false, st);
+    double *dd = stage(S, back, d, nc, false, true, st);
+    LevelSet<double> ls;
+    ls.h.push_back(single_grid(S, ctx, p, du, dr, df, dub, 1.0, st));
+    upload_set(S, ls, st);
+    std::vector<double> nr;
+    double *outs[1] = {dd};
+    level_norms<double, false>(ctx, ls, outs, nullptr, st, nr);
+    finish(ctx, back, st);
+    return FR_OK;
+  });
+}
+
+int fr_restrict(frmg_ctx *ctx, const double *fine, const int dims[3], double *coarse,
+                void *stream) {
+  return guard([&]() {
+    if (!ctx || !fine || !dims || !coarse) einval("bad argument");
+    check_dims(dims);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Scope S(ctx);
+    std::vector<Staged> back;
+    long long nf = (long long)dims[0] * dims[1] * dims[2];
+    const double *df = stage(S, back, fine, nf, true, false, st);
+    double *dc = stage(S, back, coarse, nf / 8, false, true, st);
+    k_restrict_avg<double><<<nblocks(nf / 8), 256, 0, st>>>(df, dims[0], dims[1], dims[2], dc);
+    CK_LAUNCH(ctx);
+    finish(ctx, back, st);
+    return FR_OK;
+  });
+}
+
+int fr_prolong_correct(frmg_ctx *ctx, double *uf, const int dims[3], const double *uH,
+                       const double *uR, int dirichlet, void *stream) {
+  return guard([&]() {
+    if (!ctx || !uf || !dims || !uH || !uR) einval("bad argument");
+    check_dims(dims);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Scope S(ctx);
+    std::vector<Staged> back;
+    long long nf = (long long)dims[0] * dims[1] * dims[2];
+    Grid<double> F, C;
+    memset(&F, 0, sizeof(F));
+    memset(&C, 0, sizeof(C));
+    F.n0 = dims[0];
+    F.n1 = dims[1];
+    F.n2 = dims[2];
+    F.ncell = nf;
+    F.u = stage(S, back, uf, nf, true, true, st);
+    F.x = S.get<double>(nf);
+    // a non-null bnd marks the grid as a patch (the values are not read)
+    F.bnd = dirichlet ? F.x : nullptr;
+    C.n0 = dims[0] / 2;
+    C.n1 = dims[1] / 2;
+    C.n2 = dims[2] / 2;
+    C.ncell = nf / 8;
+    C.u = const_cast<double *>(stage(S, back, uH, nf / 8, true, false, st));
+    C.uR = const_cast<double *>(stage(S, back, uR, nf / 8, true, false, st));
+    LevelSet<double> lf, lc;
+    lf.h.push_back(F);
+    lc.h.push_back(C);
+    upload_set(S, lf, st);
+    upload_set(S, lc, st);
+    k_prolong<double><<<lf.nblk_full, 256, 0, st>>>(lf.d, lc.d, lf.d_off_full, 1, nullptr);
+    CK_LAUNCH(ctx);
+    finish(ctx, back, st);
+    return FR_OK;
+  });
+}
+
+int fr_patch_bc(frmg_ctx *ctx, const double *uparent, const int dims_parent[3], int periodic,
+                const int origin[3], const int n[3], double *u_init, double *ub, void *stream) {
+  return guard([&]() {
+    if (!ctx || !uparent || !dims_parent || !origin || !n || !u_init || !ub)
+      einval("bad argument");
+    check_dims(n);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Scope S(ctx);
+    std::vector<Staged> back;
+    long long npar = (long long)dims_parent[0] * dims_parent[1] * dims_parent[2];
+    long long nc = (long long)n[0] * n[1] * n[2];
+    const double *dp = stage(S, back, uparent, npar, true, false, st);
+    double *di = stage(S, back, u_init, nc, false, true, st);
+    double *db = stage(S, back, ub, face_total(n), false, true, st);
+    patch_bc_dev(ctx, S, dp, dims_parent, periodic, origin, n, di, db, st);
+    finish(ctx, back, st);
+    return FR_OK;
+  });
+}
+
+}  // extern "C"
+

@@ -1,0 +1,236 @@
+"""GPU (CUDA, C ABI) against the FP64 oracle, step by step and end to end.
+
+Tolerances:
+* one FP64 step (sweep, residual, restriction, prolongation, boundary set-up):
+  the two sides evaluate the same formulas in a different rounding order, so
+  they agree to ~1e-12 relative; tests use 1e-10 (absolute in u, relative to
+  the largest term for residuals).
+* a converged solve at rms residual <= 1e-8: both sides sit within
+  tol / (beta/2) ~ 1e-8 of the unique discrete solution, so |u_gpu - u_oracle|
+  <= 1e-6 (the stated target) with a large margin.
+"""
+import numpy as np
+import pytest
+
+import paper_fields as PF
+from gpu_common import ctx, dev, host, local_block, torch  # noqa: F401
+from oracle import oracle as O
+from paper_1110_1379_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CFG1 = dict(box=64.0, a=1.0, omega_m=0.24, fr0=1e-5)
+
+
+@pytest.fixture(scope="module")
+def C():
+    return ctx()
+
+
+def _field(shape, seed, sigma=1.0):
+    return synth.lognormal_density(shape, seed, sigma=sigma)
+
+
+# ------------------------------------------------------------------ single steps
+@pytest.mark.parametrize("shape", [(32, 32, 32), (12, 20, 36), (4, 4, 4), (2, 2, 2)])
+@pytest.mark.parametrize("nsweeps", [1, 3])
+def test_smooth_matches_oracle(C, shape, nsweeps):
+    rho = _field(shape, 11, sigma=1.5)
+    rng = np.random.default_rng(2)
+    u0 = rng.uniform(-0.5, 0.3, shape)
+    f = rng.standard_normal(shape) * 0.1
+    h = 1.0 / shape[2]
+    ref = O.smooth(u0, rho, nsweeps, h=h, f=f, **CFG1)
+    u = dev(u0)
+    C.smooth(u, dev(rho), nsweeps, h=h, f=dev(f), **CFG1)
+    assert np.abs(host(u) - ref).max() < 1e-10
+
+
+def test_smooth_patch_faces_match_oracle(C):
+    shape = (10, 8, 12)
+    rho = _field(shape, 3)
+    rng = np.random.default_rng(5)
+    u0 = rng.uniform(-0.5, 0.3, shape)
+    ub = rng.uniform(-0.8, 0.4, sum(O.face_sizes(shape)))
+    h = 1.0 / 64
+    ref = O.smooth(u0, rho, 2, h=h, ub=ub, **CFG1)
+    u = dev(u0)
+    C.smooth(u, dev(rho), 2, h=h, ub=dev(ub), **CFG1)
+    assert np.abs(host(u) - ref).max() < 1e-10
+
+
+@pytest.mark.parametrize("with_faces", [False, True])
+def test_residual_matches_oracle(C, with_faces):
+    shape = (16, 12, 20)
+    rho = _field(shape, 8, sigma=2.0)
+    rng = np.random.default_rng(9)
+    u0 = rng.uniform(-2.0, 0.5, shape)
+    f = rng.standard_normal(shape)
+    ub = rng.uniform(-1, 0.5, sum(O.face_sizes(shape))) if with_faces else None
+    P = dict(h=1.0 / 40, f=f, ub=ub, **CFG1)
+    ref = O.residual(u0, rho, **P)
+    d = torch.empty(shape, dtype=torch.float64, device="cuda")
+    C.residual(dev(u0), dev(rho), d, h=P["h"], f=dev(f),
+               ub=None if ub is None else dev(ub), **CFG1)
+    scale = np.abs(ref).max()
+    assert np.abs(host(d) - ref).max() < 1e-12 * max(scale, 1.0)
+
+
+def test_restrict_and_prolong_match_oracle(C):
+    rng = np.random.default_rng(4)
+    fine = rng.standard_normal((12, 8, 16))
+    c = torch.empty((6, 4, 8), dtype=torch.float64, device="cuda")
+    C.restrict(dev(fine), c)
+    assert np.abs(host(c) - O.restrict(fine)).max() < 1e-15
+    uH = rng.standard_normal((6, 4, 8))
+    uR = rng.standard_normal((6, 4, 8))
+    for dirichlet in (False, True):
+        uf = dev(fine)
+        C.prolong_correct(uf, dev(uH), dev(uR), dirichlet=dirichlet)
+        ref = O.prolong_correct(fine, uH, uR, dirichlet=dirichlet)
+        assert np.abs(host(uf) - ref).max() < 1e-14
+
+
+@pytest.mark.parametrize("periodic,origin", [(True, (0, 3, 14)), (False, (2, 3, 4))])
+def test_patch_bc_matches_oracle(C, periodic, origin):
+    rng = np.random.default_rng(6)
+    up = rng.standard_normal((14, 12, 16))
+    n = (6, 8, 10)
+    ui_ref, ub_ref = O.patch_bc(up, origin, n, parent_periodic=periodic)
+    ui = torch.empty(n, dtype=torch.float64, device="cuda")
+    ub = torch.empty(sum(O.face_sizes(n)), dtype=torch.float64, device="cuda")
+    C.patch_bc(dev(up), origin, ui, ub, periodic=periodic)
+    assert np.abs(host(ui) - ui_ref).max() < 1e-14
+    assert np.abs(host(ub) - ub_ref).max() < 1e-14
+
+
+# ------------------------------------------------------------------ V-cycles
+@pytest.mark.parametrize("shape", [(32, 32, 32), (40, 24, 48), (48, 48, 48)])
+@pytest.mark.parametrize("ncyc", [1, 3])
+def test_fp64_vcycles_match_oracle(C, shape, ncyc):
+    """Identical V-cycles (same ordering, restriction, coarsest rule) give the
+    same iterate up to rounding."""
+    rho = _field(shape, 1000, sigma=1.0)
+    P = dict(box=64.0 * shape[2] / 32, a=1.0, omega_m=0.24, fr0=1e-5)
+    ref = O.solve(rho, ncycles=ncyc, **P)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    s = C.vcycles(dev(rho), u, ncyc, **P)
+    assert np.abs(host(u) - ref.u).max() < 1e-10
+    assert s.res_rms == pytest.approx(ref.hist[-1], rel=1e-6, abs=1e-13)
+
+
+# ------------------------------------------------------------------ full solves
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_config1_matches_oracle(C, prec):
+    shape = (32, 32, 32)
+    rho = _field(shape, 1000, sigma=1.0)
+    ref = O.solve(rho, tol=1e-8, **CFG1)
+    assert ref.converged
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s = C.solve(dev(rho), u, tol=1e-8, prec=prec, **CFG1)
+    assert st == 0
+    assert s.res_rms <= 1e-8
+    assert np.abs(host(u) - ref.u).max() <= 1e-6
+    if prec == "fp64":
+        assert s.vcycles == ref.cycles
+        assert np.abs(host(u) - ref.u).max() <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("fr0,box,sigma", [(1e-4, 256.0, 2.0), (1e-6, 256.0, 2.0),
+                                           (1e-5, 128.0, 2.5)])
+def test_solve_screened_regimes_match_oracle(C, prec, fr0, box, sigma):
+    shape = (48, 48, 48)
+    rho = _field(shape, 3000 + int(-np.log10(fr0)), sigma=sigma)
+    P = dict(box=box, a=1.0, omega_m=0.24, fr0=fr0)
+    ref = O.solve(rho, tol=1e-8, **P)
+    assert ref.converged
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s = C.solve(dev(rho), u, tol=1e-8, prec=prec, **P)
+    assert st == 0 and s.res_rms <= 1e-8
+    assert np.abs(host(u) - ref.u).max() <= 1e-6
+
+
+@pytest.mark.parametrize("a", [0.5, 1.0])
+def test_solve_cic_config_matches_oracle(C, a):
+    """Particles -> CIC density -> solve, both sides from the same positions."""
+    n = 32
+    pos = synth.zeldovich_positions(n, 2000, amplitude=0.02)
+    rho_ref = O.cic(pos, (n, n, n))
+    rho = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    C.cic(dev(pos), rho)
+    assert np.abs(host(rho) - rho_ref).max() < 1e-12 * rho_ref.max()
+    P = dict(box=32.0, a=a, omega_m=0.24, fr0=1e-5)
+    ref = O.solve(rho_ref, tol=1e-8, **P)
+    u = torch.zeros_like(rho)
+    st, s = C.solve(rho, u, tol=1e-8, **P)
+    assert st == 0
+    assert np.abs(host(u) - ref.u).max() <= 1e-6
+
+
+def test_sine_closed_form_on_gpu(C):
+    """Sec. VI.A.3 on the GPU: same second-order approach to the closed form."""
+    P = dict(box=256.0, a=1.0, omega_m=0.24, fr0=1e-5)
+    errs = []
+    for n in (32, 64):
+        rho, ue = PF.sine_field(n, **P)
+        u = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+        st, _ = C.solve(dev(rho), u, tol=1e-11, allow_negative_density=1, **P)
+        assert st == 0
+        errs.append(np.abs(host(u) - ue).max())
+    assert 1.9 < np.log2(errs[0] / errs[1]) < 2.1
+
+
+# ------------------------------------------------------------------ host memory path
+def test_host_pointers_same_as_device(C):
+    shape = (16, 16, 16)
+    rho = _field(shape, 5)
+    u_host = np.zeros(shape)
+    st, _ = C.solve(rho, u_host, tol=1e-9, **CFG1)
+    assert st == 0
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    C.solve(dev(rho), u, tol=1e-9, **CFG1)
+    assert np.abs(host(u) - u_host).max() < 1e-14
+
+
+# ------------------------------------------------------------------ edge cases
+def test_invalid_arguments(C):
+    from paper_1110_1379_gb300 import frmg
+    rho = torch.ones((8, 8, 7), dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(rho)
+    with pytest.raises(frmg.FRError) as e:
+        C.solve(rho, u, **CFG1)
+    assert e.value.status == frmg.FR_EINVAL
+    rho = torch.ones((8, 8, 8), dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(rho)
+    rho[1, 2, 3] = float("nan")
+    with pytest.raises(frmg.FRError):
+        C.solve(rho, u, **CFG1)
+    rho[1, 2, 3] = -0.5
+    with pytest.raises(frmg.FRError):
+        C.solve(rho, u, **CFG1)
+    st, _ = C.solve(rho, u, allow_negative_density=1, **CFG1)
+    assert st == 0
+    with pytest.raises(frmg.FRError):
+        C.solve(torch.ones_like(rho), u, box=64.0, a=-1.0, omega_m=0.24, fr0=1e-5)
+
+
+def test_no_convergence_reports_and_writes_u(C):
+    from paper_1110_1379_gb300 import frmg
+    shape = (16, 16, 16)
+    rho = _field(shape, 7, sigma=1.5)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s = C.solve(dev(rho), u, tol=1e-12, max_vcycles=1, **CFG1)
+    assert st == frmg.FR_ENOCONV
+    assert s.vcycles == 1
+    ref = O.solve(rho, ncycles=1, **CFG1)
+    assert np.abs(host(u) - ref.u).max() < 1e-10
+
+
+def test_homogeneous_and_tiny_grids(C):
+    for shape in [(2, 2, 2), (4, 4, 4), (6, 6, 6)]:
+        rng = np.random.default_rng(1)
+        u = dev(rng.uniform(-1, 1, shape))
+        st, s = C.solve(dev(np.ones(shape)), u, tol=1e-12, **CFG1)
+        assert st == 0
+        assert np.abs(host(u)).max() < 1e-10
