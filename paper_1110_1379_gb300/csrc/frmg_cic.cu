@@ -31,10 +31,18 @@ __global__ void k_cic(const double *__restrict__ pos, long long np, int n0, int 
   const int n[3] = {n0, n1, n2};
   int i0[3];
   double t[3];
+  // positions outside [0, 1) (or NaN) are reported and not deposited
 #pragma unroll
   for (int d = 0; d < 3; d++) {
     double x = pos[3 * p + d];
-    if (!(x >= 0.0 && x < 1.0)) atomicExch(bad, 1);
+    if (!(x >= 0.0 && x < 1.0)) {
+      atomicExch(bad, 1);
+      return;
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    double x = pos[3 * p + d];
     double xc = x * n[d] - 0.5;  // position in cell-centre units
     double fl = floor(xc);
     i0[d] = (int)fl;
