@@ -76,8 +76,8 @@ bool is_dev(const void *p) {
 
 }  // namespace
 
-extern "C" int fr_cic_assign(frmg_ctx *ctx, const double *pos, long long np, const int dims[3],
-                             double *density_out, void *stream) {
+static int cic_impl(frmg_ctx *ctx, const double *pos, long long np, const int dims[3],
+                    double *density_out, void *stream) {
   if (!ctx || !pos || !dims || !density_out || np <= 0) {
     frmg_set_error("bad argument");
     return FR_EINVAL;
@@ -135,4 +135,14 @@ extern "C" int fr_cic_assign(frmg_ctx *ctx, const double *pos, long long np, con
   frmg_release(ctx, tmp_rho);
   frmg_release(ctx, bad);
   return status;
+}
+
+extern "C" int fr_cic_assign(frmg_ctx *ctx, const double *pos, long long np, const int dims[3],
+                             double *density_out, void *stream) {
+  try {
+    return cic_impl(ctx, pos, np, dims, density_out, stream);
+  } catch (...) {
+    frmg_set_error("allocation failed");
+    return FR_ENOMEM;
+  }
 }
