@@ -164,6 +164,16 @@ int fr_smooth(frmg_ctx *ctx, double *u, const double *density, const double *f,
               const int dims[3], double h, double box_mpc_h, double a, double omega_m,
               double fr0_abs, const double *ub, int nsweeps, double step_cap, void *stream);
 
+/* FP32 smoothing as the mixed path runs it, on one level: nsweeps red-black
+ * sweeps of A(u) = f (f NULL = 0, no density term) in FP32.  bg NULL: u is the
+ * unknown.  bg non-NULL: u is a correction delta on the FP32 background bg and
+ * the equation is A(bg + delta) - A(bg) = f.  tiled != 0 selects the
+ * shared-memory temporally blocked kernel (grids of at least 16 cells a side),
+ * 0 the one-colour-per-launch kernel; both give the same sweeps. */
+int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, const int dims[3],
+                  double h, double box_mpc_h, double a, double omega_m, double fr0_abs,
+                  const float *ub, int nsweeps, double step_cap, int tiled, void *stream);
+
 /* d = L(u) - f on one level (arguments as fr_smooth). */
 int fr_residual(frmg_ctx *ctx, const double *u, const double *density, const double *f,
                 const int dims[3], double h, double box_mpc_h, double a, double omega_m,

@@ -36,7 +36,9 @@ namespace frmg {
 
 template <typename T>
 struct Grid {
-  T *u;            // unknown (delta in background mode)
+  T *u;            // unknown (delta in background mode), buffer 0
+  T *u2;           // buffer 1: the tiled smoother reads one buffer and writes the other
+  int pad_;
   T *x;            // cache: expm1(u)
   const T *f;      // right-hand side storage; f_i = fs * (f[i] - fo); null = 0
   T *uR;           // R u^h saved for the FAS correction (coarse levels)
@@ -76,6 +78,14 @@ __device__ __forceinline__ int find_grid(const int *off, int ngrid, int b) {
   return lo;
 }
 
+// Grid view whose u is the current buffer (par selects buffer 0 or 1).
+template <typename T>
+__device__ __forceinline__ Grid<T> view(const Grid<T> *grids, int g, int par) {
+  Grid<T> G = grids[g];
+  if (par) G.u = G.u2;
+  return G;
+}
+
 __device__ __forceinline__ bool grid_active(const int *active, int field) {
   return active == nullptr || active[field] != 0;
 }
@@ -98,17 +108,15 @@ __device__ __forceinline__ T face_value(const Grid<T> &G, int f, int i, int j, i
   return G.bnd[G.foff[f] + o];
 }
 
+// Contribution of one regular face (neighbour values given).
 template <typename T, bool BG>
-__device__ __forceinline__ void face_regular(const Grid<T> &G, long long cj, T di, T Ei, T xi,
-                                             T Bi, T ubi, T &acc, T &dacc) {
-  T dj = G.u[cj];
-  T xj = G.x[cj];
-  T Ej = BG ? (T)G.Ebg[cj] : T(1);
+__device__ __forceinline__ void face_vals(T dj, T xj, T ubj, T Ej, T di, T Ei, T xi, T Bi, T ubi,
+                                          T &acc, T &dacc) {
   T Bj = BG ? Ej + Ej * xj : T(1) + xj;
   T dd = dj - di;
   T w;
   if (BG) {
-    T gd = (T)G.ubg[cj] - ubi;
+    T gd = ubj - ubi;
     acc += (Ei * xi + Ej * xj) * gd + (Bi + Bj) * dd;
     w = gd + dd;
   } else {
@@ -116,6 +124,13 @@ __device__ __forceinline__ void face_regular(const Grid<T> &G, long long cj, T d
     w = dd;
   }
   dacc += Bi * w - (Bi + Bj);
+}
+
+template <typename T, bool BG>
+__device__ __forceinline__ void face_regular(const Grid<T> &G, long long cj, T di, T Ei, T xi,
+                                             T Bi, T ubi, T &acc, T &dacc) {
+  face_vals<T, BG>(G.u[cj], G.x[cj], BG ? (T)G.ubg[cj] : T(0), BG ? (T)G.Ebg[cj] : T(1), di, Ei,
+                   xi, Bi, ubi, acc, dacc);
 }
 
 template <typename T, bool BG>
@@ -140,7 +155,37 @@ __device__ __forceinline__ void face_ghost(T ubf, T di, T Ei, T xi, T Bi, T ubi,
   dacc += (Bi - Bg) * w - T(2) * (Bi + Bg);
 }
 
-// A_i (or N_i) and its derivative at cell (i,j,k).
+// Mass term and final assembly:  N = (alpha/2) acc + beta F (e^{-d/2} - 1),
+// dN = (alpha/2) dacc - (beta/2) F e^{-d/2},  F = e^{-ub/2}.
+// FP64 uses IEEE sqrt and division; FP32 uses the SFU reciprocal square root
+// and reciprocal (the same expression in every FP32 kernel, so all of them
+// see one and the same discrete operator).
+__device__ __forceinline__ void finish_op(double xi, double Ei, double acc, double dacc,
+                                          double ah, double beta, bool bg, double &N,
+                                          double &dN) {
+  double B1 = 1.0 + xi;
+  double s = sqrt(B1);
+  double y = -xi / (B1 + s);
+  double F = bg ? rsqrt(Ei) : 1.0;
+  N = ah * acc + beta * F * y;
+  dN = ah * dacc - 0.5 * beta * F / s;
+}
+
+__device__ __forceinline__ void finish_op(float xi, float Ei, float acc, float dacc, float ah,
+                                          float beta, bool bg, float &N, float &dN) {
+  float B1 = 1.0f + xi;
+  float rs = rsqrtf(B1);  // e^{-d/2}
+  float s = B1 * rs;      // e^{d/2}
+  float y = __fdividef(-xi, B1 + s);
+  float F = bg ? rsqrtf(Ei) : 1.0f;
+  N = ah * acc + beta * F * y;
+  dN = ah * dacc - 0.5f * beta * F * rs;
+}
+
+__device__ __forceinline__ double newton_step(double r, double dN) { return -r / dN; }
+__device__ __forceinline__ float newton_step(float r, float dN) { return __fdividef(-r, dN); }
+
+// A_i (or N_i) and its derivative at cell (i,j,k) from global memory.
 template <typename T, bool BG>
 __device__ __forceinline__ void cell_eval(const Grid<T> &G, int i, int j, int k, long long c,
                                           T &N, T &dN) {
@@ -191,13 +236,7 @@ __device__ __forceinline__ void cell_eval(const Grid<T> &G, int i, int j, int k,
     face_regular<T, BG>(G, c - (G.n2 - 1) * sz, di, Ei, xi, Bi, ubi, acc, dacc);
   else
     face_ghost<T, BG>(face_value(G, 5, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
-  // mass term: beta F (e^{-d/2} - 1) with F = e^{-ub/2}; s = e^{d/2}
-  T B1 = T(1) + xi;
-  T s = m_sqrt(B1);
-  T y = -xi / (B1 + s);
-  T F = BG ? m_rsqrt(Ei) : T(1);
-  N = G.ah * acc + G.beta * F * y;
-  dN = G.ah * dacc - T(0.5) * G.beta * F / s;
+  finish_op(xi, Ei, acc, dacc, G.ah, G.beta, BG, N, dN);
 }
 
 template <typename T>
@@ -210,7 +249,7 @@ __device__ __forceinline__ void ngs_update(const Grid<T> &G, int i, int j, int k
   long long c = idx3(G, i, j, k);
   T N, dN;
   cell_eval<T, BG>(G, i, j, k, c, N, dN);
-  T du = -(N - rhs_at(G, c)) / dN;
+  T du = newton_step(N - rhs_at(G, c), dN);
   du = du > G.cap ? G.cap : (du < -G.cap ? -G.cap : du);
   T unew = G.u[c] + du;
   G.u[c] = unew;
@@ -222,9 +261,9 @@ __device__ __forceinline__ void ngs_update(const Grid<T> &G, int i, int j, int k
 // that colour.  off[] maps blocks to grids (n0/2 * n1 * n2 threads per grid).
 template <typename T, bool BG>
 __global__ void k_smooth(const Grid<T> *grids, const int *off, int ngrid, int colour,
-                         const int *active) {
+                         const int *active, int par) {
   int g = find_grid(off, ngrid, blockIdx.x);
-  const Grid<T> G = grids[g];
+  const Grid<T> G = view(grids, g, par);
   if (!grid_active(active, G.field)) return;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
   int hx = G.n0 >> 1;
@@ -270,9 +309,9 @@ __device__ __forceinline__ void block_reduce2(double s, double m, double *out_s,
 template <typename T, bool BG, int NT>
 __global__ void __launch_bounds__(NT) k_residual(const Grid<T> *grids, const int *off, int ngrid,
                                                  T *const *dout, double *partial,
-                                                 const int *active) {
+                                                 const int *active, int par) {
   int g = find_grid(off, ngrid, blockIdx.x);
-  const Grid<T> G = grids[g];
+  const Grid<T> G = view(grids, g, par);
   double s = 0.0, m = 0.0;
   long long t = (long long)(blockIdx.x - off[g]) * NT + threadIdx.x;
   if (grid_active(active, G.field) && t < G.ncell) {
@@ -307,10 +346,10 @@ __global__ void k_reduce_partials(const double *partial, const int *off, int ngr
 // (the coarse operator is added by k_fas_rhs).  One thread per coarse cell.
 template <typename T, bool BG>
 __global__ void k_resid_restrict(const Grid<T> *fine, const Grid<T> *coarse, const int *off,
-                                 int ngrid, const int *active) {
+                                 int ngrid, const int *active, int fpar, int cpar) {
   int g = find_grid(off, ngrid, blockIdx.x);
-  const Grid<T> F = fine[g];
-  const Grid<T> C = coarse[g];
+  const Grid<T> F = view(fine, g, fpar);
+  const Grid<T> C = view(coarse, g, cpar);
   if (!grid_active(active, F.field)) return;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
   if (t >= C.ncell) return;
@@ -341,9 +380,10 @@ __global__ void k_resid_restrict(const Grid<T> *fine, const Grid<T> *coarse, con
 
 // f^H = A^H(R u^h) - R d^h, in place over the R d^h stored in f (fs = 1, fo = 0).
 template <typename T, bool BG>
-__global__ void k_fas_rhs(const Grid<T> *grids, const int *off, int ngrid, const int *active) {
+__global__ void k_fas_rhs(const Grid<T> *grids, const int *off, int ngrid, const int *active,
+                          int par) {
   int g = find_grid(off, ngrid, blockIdx.x);
-  const Grid<T> G = grids[g];
+  const Grid<T> G = view(grids, g, par);
   if (!grid_active(active, G.field)) return;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
   if (t >= G.ncell) return;
@@ -361,10 +401,10 @@ __global__ void k_fas_rhs(const Grid<T> *grids, const int *off, int ngrid, const
 // Patches: coarse neighbours outside the grid contribute 0.
 template <typename T>
 __global__ void k_prolong(const Grid<T> *fine, const Grid<T> *coarse, const int *off, int ngrid,
-                          const int *active) {
+                          const int *active, int fpar, int cpar) {
   int g = find_grid(off, ngrid, blockIdx.x);
-  const Grid<T> F = fine[g];
-  const Grid<T> C = coarse[g];
+  const Grid<T> F = view(fine, g, fpar);
+  const Grid<T> C = view(coarse, g, cpar);
   if (!grid_active(active, F.field)) return;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
   if (t >= F.ncell) return;
@@ -408,10 +448,10 @@ __global__ void k_prolong(const Grid<T> *fine, const Grid<T> *coarse, const int 
 template <typename T, bool BG, int NT>
 __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid, double rel,
                                                  double abs_floor, int maxit, int stop_on_stall,
-                                                 const int *active) {
+                                                 const int *active, int par) {
   int g = blockIdx.x;
   if (g >= ngrid) return;
-  const Grid<T> G = grids[g];
+  const Grid<T> G = view(grids, g, par);
   if (!grid_active(active, G.field)) return;
   __shared__ double red_s, red_m;
   __shared__ int stop;
@@ -479,6 +519,167 @@ __global__ void k_restrict_avg(const T *fine, int nf0, int nf1, int nf2, T *coar
     s += fine[((long long)k * nf1 + j) * nf0 + i];
   }
   coarse[t] = s * T(0.125);
+}
+
+// ---------------------------------------------------------------------------
+// Tiled FP32 smoother with temporal blocking: S full red-black sweeps per pass.
+//
+// A block owns a TX x TY tile of one grid and a chunk of zc planes; it marches
+// along z with a ring of 2S+2 planes (tile plus a halo of 2S cells in x and y)
+// in shared memory.  At the step that loads plane p, stage q (q = 0 .. 2S-1,
+// colour q & 1: red first) updates plane p-1-q on the tile grown by 2S-1-q
+// cells, so that plane p-2S is final and its tile cells are written out.
+// Halo cells are updated redundantly by neighbouring blocks from identical
+// inputs; a pass reads the current buffer and writes the other one (blocks
+// load their halos from the unmodified input), which makes the result equal to
+// S sweeps of k_smooth.  x = expm1(u) is recomputed from u on load and written
+// in place for the kernels that follow.
+template <int S, int TX, int TY>
+struct TileCfg {
+  static constexpr int H = 2 * S;
+  static constexpr int LX = TX + 2 * H, LY = TY + 2 * H, PL = LX * LY, NS = 2 * S + 2;
+  static constexpr size_t smem(bool bg) { return (size_t)NS * PL * sizeof(float) * (bg ? 4 : 2); }
+};
+
+__device__ __forceinline__ int wrapmod(int v, int n) {
+  int r = v % n;
+  return r < 0 ? r + n : r;
+}
+
+template <bool BG, int S, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_smooth_tiled(const Grid<float> *grids, const int *off,
+                                                     int ngrid, int zc, const int *active,
+                                                     int par) {
+  using C = TileCfg<S, TX, TY>;
+  constexpr int H = C::H, LX = C::LX, PL = C::PL, NS = C::NS;
+  extern __shared__ float smem[];
+  float *sd = smem;
+  float *sx = smem + NS * PL;
+  float *sub = smem + 2 * NS * PL;
+  float *sE = smem + 3 * NS * PL;
+  const int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<float> G = view(grids, g, par);
+  if (!grid_active(active, G.field)) return;
+  float *__restrict__ uout = par ? grids[g].u : grids[g].u2;
+  const int n0 = G.n0, n1 = G.n1, n2 = G.n2;
+  const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
+  int b = blockIdx.x - off[g];
+  const int X0 = (b % ntx) * TX;
+  b /= ntx;
+  const int Y0 = (b % nty) * TY;
+  b /= nty;
+  const int Z0 = b * zc;
+  const int Z1 = min(Z0 + zc, n2);
+  const bool dir = G.bnd != nullptr;
+
+  for (int p = Z0 - H; p < Z1 + H; p++) {
+    // ---- load plane p (raw input values)
+    if (!dir || (p >= 0 && p < n2)) {
+      const int sl = wrapmod(p, NS);
+      const int gz = wrapmod(p, n2);
+      for (int c = threadIdx.x; c < PL; c += NT) {
+        const int ly = c / LX, lx = c - ly * LX;
+        const int gx = X0 - H + lx, gy = Y0 - H + ly;
+        if (dir && (gx < 0 || gx >= n0 || gy < 0 || gy >= n1)) continue;
+        const long long gi = ((long long)gz * n1 + wrapmod(gy, n1)) * n0 + wrapmod(gx, n0);
+        const float d = G.u[gi];
+        sd[sl * PL + c] = d;
+        sx[sl * PL + c] = m_expm1(d);
+        if (BG) {
+          sub[sl * PL + c] = G.ubg[gi];
+          sE[sl * PL + c] = G.Ebg[gi];
+        }
+      }
+    }
+    __syncthreads();
+    // ---- 2S wavefront stages
+#pragma unroll
+    for (int q = 0; q < 2 * S; q++) {
+      const int m = p - 1 - q;
+      const int R = 2 * S - 1 - q;
+      const int colour = q & 1;
+      const bool zok = m >= Z0 - R && m < Z1 + R && (!dir || (m >= 0 && m < n2));
+      if (zok) {
+        int xs = X0 - R, xe = X0 + TX + R, ys = Y0 - R, ye = Y0 + TY + R;
+        if (dir) {
+          xs = max(xs, 0);
+          xe = min(xe, n0);
+          ys = max(ys, 0);
+          ye = min(ye, n1);
+        }
+        const int W = xe - xs, nr = ye - ys;
+        const int per = (W + 1) >> 1;
+        const int sl = wrapmod(m, NS), slm = wrapmod(m - 1, NS), slp = wrapmod(m + 1, NS);
+        const int gzw = wrapmod(m, n2);
+        for (int c = threadIdx.x; c < per * nr; c += NT) {
+          const int row = c / per, k2 = c - row * per;
+          const int gy = ys + row;
+          const int gx = xs + ((xs + gy + m + colour) & 1) + 2 * k2;
+          if (gx >= xe) continue;
+          const int li = (gy - (Y0 - H)) * LX + (gx - (X0 - H));
+          const int o = sl * PL + li;
+          const float di = sd[o], xi = sx[o];
+          const float Ei = BG ? sE[o] : 1.0f;
+          const float ubi = BG ? sub[o] : 0.0f;
+          const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
+          float acc = 0.0f, dacc = 0.0f;
+#define FR_NB(OFF)                                                                          \
+  face_vals<float, BG>(sd[OFF], sx[OFF], BG ? sub[OFF] : 0.0f, BG ? sE[OFF] : 1.0f, di, Ei, \
+                       xi, Bi, ubi, acc, dacc)
+          if (dir && gx == 0)
+            face_ghost<float, BG>(face_value(G, 0, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
+          else
+            FR_NB(o - 1);
+          if (dir && gx == n0 - 1)
+            face_ghost<float, BG>(face_value(G, 1, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
+          else
+            FR_NB(o + 1);
+          if (dir && gy == 0)
+            face_ghost<float, BG>(face_value(G, 2, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
+          else
+            FR_NB(o - LX);
+          if (dir && gy == n1 - 1)
+            face_ghost<float, BG>(face_value(G, 3, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
+          else
+            FR_NB(o + LX);
+          if (dir && m == 0)
+            face_ghost<float, BG>(face_value(G, 4, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
+          else
+            FR_NB(slm * PL + li);
+          if (dir && m == n2 - 1)
+            face_ghost<float, BG>(face_value(G, 5, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
+          else
+            FR_NB(slp * PL + li);
+#undef FR_NB
+          float N, dN;
+          finish_op(xi, Ei, acc, dacc, G.ah, G.beta, BG, N, dN);
+          const long long gi = ((long long)gzw * n1 + wrapmod(gy, n1)) * n0 + wrapmod(gx, n0);
+          const float f = G.f ? G.fs * (G.f[gi] - G.fo) : 0.0f;
+          float du = newton_step(N - f, dN);
+          du = du > G.cap ? G.cap : (du < -G.cap ? -G.cap : du);
+          const float dn = di + du;
+          sd[o] = dn;
+          sx[o] = m_expm1(dn);
+        }
+      }
+      __syncthreads();
+    }
+    // ---- plane p - 2S is final: write the tile cells
+    const int w = p - H;
+    if (w >= Z0 && w < Z1) {
+      const int sl = wrapmod(w, NS);
+      for (int c = threadIdx.x; c < TX * TY; c += NT) {
+        const int ty = c / TX, tx = c - ty * TX;
+        const int gx = X0 + tx, gy = Y0 + ty;
+        if (gx < n0 && gy < n1) {
+          const int o = sl * PL + (ty + H) * LX + tx + H;
+          const long long gi = ((long long)w * n1 + gy) * n0 + gx;
+          uout[gi] = sd[o];
+          G.x[gi] = sx[o];
+        }
+      }
+    }
+  }
 }
 
 }  // namespace frmg

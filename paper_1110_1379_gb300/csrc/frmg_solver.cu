@@ -358,6 +358,9 @@ struct Problem {
   int nl;
 };
 
+// tile of the tiled smoother
+constexpr int kTX = 64, kTY = 16, kTNT = 256;
+
 template <typename T>
 struct LevelSet {
   std::vector<Grid<T>> h;
@@ -365,6 +368,12 @@ struct LevelSet {
   std::vector<int> off_half, off_full;
   int *d_off_half = nullptr, *d_off_full = nullptr;
   int nblk_half = 0, nblk_full = 0;
+  // tiled FP32 smoother: blocks per grid for TX x TY tiles and zc-plane chunks
+  bool tiled = false;
+  int zc = 0;
+  std::vector<int> off_tile;
+  int *d_off_tile = nullptr;
+  int nblk_tile = 0;
   double *partial = nullptr;  // per-block norm partials
   double *red = nullptr;      // per-grid (sum of squares, max)
   T **d_dout = nullptr;       // per-grid residual output pointers
@@ -393,6 +402,32 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st) {
                      cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ls.d_off_full, ls.off_full.data(), (ng + 1) * sizeof(int),
                      cudaMemcpyHostToDevice, st));
+  // tiled smoother for FP32 sets whose grids are all at least 16 cells a side
+  ls.tiled = sizeof(T) == 4;
+  int maxn2 = 0;
+  long long txy = 0;
+  for (int g = 0; g < ng; g++) {
+    const Grid<T> &G = ls.h[g];
+    if (std::min(G.n0, std::min(G.n1, G.n2)) < 16) ls.tiled = false;
+    maxn2 = std::max(maxn2, G.n2);
+    txy += (long long)((G.n0 + kTX - 1) / kTX) * ((G.n1 + kTY - 1) / kTY);
+  }
+  if (ls.tiled) {
+    // aim at ~8 resident blocks per SM-pair wave: chunks of z so that the set
+    // yields about 1216 blocks, never thinner than 32 planes
+    long long nz = std::max<long long>(1, (1216 + txy - 1) / txy);
+    ls.zc = (int)std::max<long long>(std::min(32, maxn2), (maxn2 + nz - 1) / nz);
+    ls.off_tile.assign(ng + 1, 0);
+    for (int g = 0; g < ng; g++) {
+      const Grid<T> &G = ls.h[g];
+      int nt = ((G.n0 + kTX - 1) / kTX) * ((G.n1 + kTY - 1) / kTY) * ((G.n2 + ls.zc - 1) / ls.zc);
+      ls.off_tile[g + 1] = ls.off_tile[g] + nt;
+    }
+    ls.nblk_tile = ls.off_tile[ng];
+    ls.d_off_tile = S.get<int>(ng + 1);
+    CK(cudaMemcpyAsync(ls.d_off_tile, ls.off_tile.data(), (ng + 1) * sizeof(int),
+                       cudaMemcpyHostToDevice, st));
+  }
   ls.partial = S.get<double>(2 * (size_t)ls.nblk_full);
   ls.red = S.get<double>(2 * (size_t)ng);
   ls.d_dout = S.get<T *>(ng);
@@ -408,6 +443,8 @@ struct Hier {
   std::vector<std::vector<Grid<T>>> lev;  // lev[p][l]
   std::vector<LevelSet<T>> cont, next, coarsest, all;
   std::vector<float *> bg_u, bg_E;        // fine-level background arrays per problem
+  std::vector<int> par;                   // current u buffer (0/1) per depth
+  T *cur_u(int pi, int l) const { return par[l] ? lev[pi][l].u2 : lev[pi][l].u; }
 };
 
 template <typename T, bool BG>
@@ -451,6 +488,7 @@ static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap
         G.fo = T(0);
       }
       G.x = S.get<T>(G.ncell);
+      if (sizeof(T) == 4) G.u2 = S.get<T>(G.ncell);
       if (l > 0) G.uR = S.get<T>(G.ncell);
       if (BG) {
         float *ub = S.get<float>(G.ncell);
@@ -485,6 +523,7 @@ static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap
       h *= 2.0;
     }
   }
+  H.par.assign(H.depth, 0);
   H.cont.assign(H.depth, {});
   H.next.assign(H.depth, {});
   H.coarsest.assign(H.depth, {});
@@ -534,14 +573,71 @@ static const char *pname(const char *kind, bool f64, bool fine) {
   return tab[row][(f64 ? 0 : 2) + (fine ? 0 : 1)];
 }
 
+template <bool BG, int S>
+static void launch_tiled(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
+                         cudaStream_t st) {
+  size_t sm = TileCfg<S, kTX, kTY>::smem(BG);
+  static bool attr_set = false;
+  if (!attr_set) {
+    CK(cudaFuncSetAttribute(k_smooth_tiled<BG, S, kTX, kTY, kTNT>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_set = true;
+  }
+  k_smooth_tiled<BG, S, kTX, kTY, kTNT><<<s.nblk_tile, kTNT, sm, st>>>(s.d, s.d_off_tile, s.size(),
+                                                                      s.zc, active, par);
+}
+
+// Passes of the tiled smoother (sweeps per pass) for the pre- and post-smoothing
+// of one V-cycle level.  The total number of passes must be even so that the
+// level's data is back in its starting buffer when the coarser V-cycle reads it
+// (grids whose coarsest level is this depth are not smoothed here).  Returns
+// false if no even plan exists (then the in-place kernel is used).
+static bool plan_passes(int pre, int post, std::vector<int> &a, std::vector<int> &b) {
+  auto split = [](int n, std::vector<int> &v) {
+    v.clear();
+    while (n >= 2) {
+      v.push_back(2);
+      n -= 2;
+    }
+    if (n) v.push_back(1);
+  };
+  split(pre, a);
+  split(post, b);
+  if ((a.size() + b.size()) % 2 == 0) return true;
+  for (auto *v : {&b, &a}) {
+    auto it = std::find(v->begin(), v->end(), 2);
+    if (it != v->end()) {
+      *it = 1;
+      v->insert(it, 1);
+      return true;
+    }
+  }
+  return false;
+}
+
 template <typename T, bool BG>
-static void smooth_set(frmg_ctx *ctx, LevelSet<T> &s, int sweeps, const int *active,
-                       cudaStream_t st, bool fine = true) {
-  if (s.empty()) return;
+static void smooth_set(frmg_ctx *ctx, LevelSet<T> &s, int sweeps, const std::vector<int> *plan,
+                       const int *active, int &par, cudaStream_t st, bool fine = true) {
+  if (s.empty() || sweeps <= 0) return;
+  if constexpr (sizeof(T) == 4) {
+    if (s.tiled && plan) {
+      for (int S : *plan) {
+        PROF(pname("smooth", false, fine));
+        if (S == 2)
+          launch_tiled<BG, 2>(ctx, s, active, par, st);
+        else
+          launch_tiled<BG, 1>(ctx, s, active, par, st);
+        CK_LAUNCH(ctx);
+        par ^= 1;
+      }
+      return;
+    }
+  }
   for (int it = 0; it < sweeps; it++)
     for (int colour = 0; colour < 2; colour++) {
       PROF(pname("smooth", sizeof(T) == 8, fine));
-      k_smooth<T, BG><<<s.nblk_half, 256, 0, st>>>(s.d, s.d_off_half, s.size(), colour, active);
+      k_smooth<T, BG><<<s.nblk_half, 256, 0, st>>>(s.d, s.d_off_half, s.size(), colour, active,
+                                                   par);
       CK_LAUNCH(ctx);
     }
 }
@@ -553,38 +649,42 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
     auto &c = H.coarsest[l];
     PROF(sizeof(T) == 8 ? "coarsest_f64" : "coarsest_f32");
     k_coarsest<T, BG, 256><<<c.size(), 256, 0, st>>>(c.d, c.size(), o.crs_rel, o.crs_abs,
-                                                     o.crs_maxit, o.crs_stall, active);
+                                                     o.crs_maxit, o.crs_stall, active, H.par[l]);
     CK_LAUNCH(ctx);
   }
   if (H.cont[l].empty()) return;
   auto &F = H.cont[l];
   auto &C = H.next[l];
-  smooth_set<T, BG>(ctx, F, o.pre, active, st, l == 0);
+  std::vector<int> plan_pre, plan_post;
+  bool even = plan_passes(o.pre, o.post, plan_pre, plan_post);
+  smooth_set<T, BG>(ctx, F, o.pre, even ? &plan_pre : nullptr, active, H.par[l], st, l == 0);
   {
     PROF(pname("resid_restrict", sizeof(T) == 8, l == 0));
     k_resid_restrict<T, BG><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, C.size(),
-                                                         active);
+                                                         active, H.par[l], H.par[l + 1]);
     CK_LAUNCH(ctx);
   }
   {
     PROF(pname("fas_rhs", sizeof(T) == 8, false));
-    k_fas_rhs<T, BG><<<C.nblk_full, 256, 0, st>>>(C.d, C.d_off_full, C.size(), active);
+    k_fas_rhs<T, BG><<<C.nblk_full, 256, 0, st>>>(C.d, C.d_off_full, C.size(), active,
+                                                  H.par[l + 1]);
     CK_LAUNCH(ctx);
   }
   vcycle<T, BG>(ctx, H, l + 1, o, active, st);
   {
     PROF(pname("prolong", sizeof(T) == 8, l == 0));
-    k_prolong<T><<<F.nblk_full, 256, 0, st>>>(F.d, C.d, F.d_off_full, F.size(), active);
+    k_prolong<T><<<F.nblk_full, 256, 0, st>>>(F.d, C.d, F.d_off_full, F.size(), active,
+                                              H.par[l], H.par[l + 1]);
     CK_LAUNCH(ctx);
   }
-  smooth_set<T, BG>(ctx, F, o.post, active, st, l == 0);
+  smooth_set<T, BG>(ctx, F, o.post, even ? &plan_post : nullptr, active, H.par[l], st, l == 0);
 }
 
 // Residual norms of every grid of a level set: out[2g] = rms, out[2g+1] = max.
 // dout (host array of ng device pointers, entries may be null) receives d.
 template <typename T, bool BG>
 static void level_norms(frmg_ctx *ctx, LevelSet<T> &s, T *const *dout, const int *active,
-                        cudaStream_t st, std::vector<double> &out) {
+                        cudaStream_t st, std::vector<double> &out, int par = 0) {
   int ng = s.size();
   if (dout)
     CK(cudaMemcpyAsync(s.d_dout, dout, ng * sizeof(T *), cudaMemcpyHostToDevice, st));
@@ -592,7 +692,7 @@ static void level_norms(frmg_ctx *ctx, LevelSet<T> &s, T *const *dout, const int
     PROF(pname("residual", sizeof(T) == 8, true));
     k_residual<T, BG, 256><<<s.nblk_full, 256, 0, st>>>(s.d, s.d_off_full, ng,
                                                         dout ? s.d_dout : nullptr, s.partial,
-                                                        active);
+                                                        active, par);
     CK_LAUNCH(ctx);
   }
   k_reduce_partials<<<ng, 256, 0, st>>>(s.partial, s.d_off_full, ng, s.red);
@@ -733,7 +833,8 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
       Grid<double> &G64 = H64.lev[pi][0];
       PROF("prep_inner");
       k_prep_inner<<<nblocks(G.ncell), 256, 0, st>>>(d64[pi], G64.u, const_cast<float *>(G.f),
-                                                     H.bg_u[pi], H.bg_E[pi], G.u, G.x, G.ncell);
+                                                     H.bg_u[pi], H.bg_E[pi], H.cur_u(pi, 0), G.x,
+                                                     G.ncell);
       CK_LAUNCH(ctx);
       for (size_t l = 1; l < H.lev[pi].size(); l++) {
         Grid<float> &F = H.lev[pi][l - 1];
@@ -749,14 +850,14 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
     // stops falling; later ones run inner_cycles
     int kmax = outer == 0 ? 30 : cfg.inner_cycles;
     std::vector<double> r0;
-    if (outer == 0) level_norms<float, true>(ctx, H.all[0], nullptr, active, st, r0);
+    if (outer == 0) level_norms<float, true>(ctx, H.all[0], nullptr, active, st, r0, H.par[0]);
     std::vector<double> rp = r0;
     for (int k = 0; k < kmax; k++) {
       vcycle<float, true>(ctx, H, 0, co, active, st);
       for (int pi = 0; pi < np; pi++)
         if (act[pi]) stats[pi].vcycles++;
       if (outer == 0) {
-        level_norms<float, true>(ctx, H.all[0], nullptr, active, st, inr);
+        level_norms<float, true>(ctx, H.all[0], nullptr, active, st, inr, H.par[0]);
         bool go = false;
         for (int pi = 0; pi < np; pi++) {
           if (!act[pi]) continue;
@@ -772,7 +873,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
       if (!act[pi]) continue;
       Grid<double> &G64 = H64.lev[pi][0];
       PROF("update64");
-      k_update64<<<nblocks(G64.ncell), 256, 0, st>>>(G64.u, G64.x, H.lev[pi][0].u, G64.ncell);
+      k_update64<<<nblocks(G64.ncell), 256, 0, st>>>(G64.u, G64.x, H.cur_u(pi, 0), G64.ncell);
       CK_LAUNCH(ctx);
     }
   }
@@ -1394,7 +1495,66 @@ int fr_smooth(frmg_ctx *ctx, double *u, const double *density, const double *f, 
     LevelSet<double> ls;
     ls.h.push_back(single_grid(S, ctx, p, du, dr, df, dub, cap, st));
     upload_set(S, ls, st);
-    smooth_set<double, false>(ctx, ls, nsweeps, nullptr, st);
+    int par = 0;
+    smooth_set<double, false>(ctx, ls, nsweeps, nullptr, nullptr, par, st);
+    finish(ctx, back, st);
+    return FR_OK;
+  });
+}
+
+int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, const int dims[3],
+                  double h, double box, double a, double om, double fr0, const float *ub,
+                  int nsweeps, double cap, int tiled, void *stream) {
+  return guard([&]() {
+    if (!ctx || !u || !dims || nsweeps < 0 || !(cap > 0)) einval("bad argument");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Problem p = one_level(dims, h, box, a, om, fr0);
+    Scope S(ctx);
+    std::vector<Staged> back;
+    long long nc = (long long)dims[0] * dims[1] * dims[2];
+    Consts k = model_consts(box, h, a, om, fr0);
+    Grid<float> G;
+    memset(&G, 0, sizeof(G));
+    G.n0 = dims[0];
+    G.n1 = dims[1];
+    G.n2 = dims[2];
+    G.ncell = nc;
+    G.ah = (float)(0.5 * k.alpha);
+    G.beta = (float)k.beta;
+    G.cap = (float)cap;
+    G.fs = 1.0f;
+    G.fo = 0.0f;
+    face_offsets(dims, G.foff);
+    float *du = stage(S, back, u, nc, true, true, st);
+    G.u = S.get<float>(nc);
+    G.u2 = S.get<float>(nc);
+    CK(cudaMemcpyAsync(G.u, du, nc * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    G.x = S.get<float>(nc);
+    k_expm1<float><<<nblocks(nc), 256, 0, st>>>(G.u, G.x, nc);
+    CK_LAUNCH(ctx);
+    G.f = stage(S, back, f, nc, true, false, st);
+    G.bnd = stage(S, back, ub, ub ? face_total(dims) : 0, true, false, st);
+    if (bg) {
+      G.ubg = stage(S, back, bg, nc, true, false, st);
+      float *E = S.get<float>(nc);
+      k_expf<<<nblocks(nc), 256, 0, st>>>(G.ubg, E, nc);
+      CK_LAUNCH(ctx);
+      G.Ebg = E;
+    }
+    LevelSet<float> ls;
+    ls.h.push_back(G);
+    upload_set(S, ls, st);
+    if (tiled && !ls.tiled) einval("tiled smoothing needs at least 16 cells a side");
+    if (!tiled) ls.tiled = false;
+    std::vector<int> plan;
+    for (int n = nsweeps; n > 0; n -= 2) plan.push_back(n >= 2 ? 2 : 1);
+    int par = 0;
+    if (bg)
+      smooth_set<float, true>(ctx, ls, nsweeps, &plan, nullptr, par, st);
+    else
+      smooth_set<float, false>(ctx, ls, nsweeps, &plan, nullptr, par, st);
+    CK(cudaMemcpyAsync(du, par ? G.u2 : G.u, nc * sizeof(float), cudaMemcpyDeviceToDevice, st));
     finish(ctx, back, st);
     return FR_OK;
   });
@@ -1480,7 +1640,7 @@ int fr_prolong_correct(frmg_ctx *ctx, double *uf, const int dims[3], const doubl
     lc.h.push_back(C);
     upload_set(S, lf, st);
     upload_set(S, lc, st);
-    k_prolong<double><<<lf.nblk_full, 256, 0, st>>>(lf.d, lc.d, lf.d_off_full, 1, nullptr);
+    k_prolong<double><<<lf.nblk_full, 256, 0, st>>>(lf.d, lc.d, lf.d_off_full, 1, nullptr, 0, 0);
     CK_LAUNCH(ctx);
     finish(ctx, back, st);
     return FR_OK;

@@ -47,7 +47,7 @@ class fr_patch(ctypes.Structure):
 EXPORTS = ["fr_opts_default", "fr_status_string", "fr_last_error", "fr_ctx_create",
            "fr_ctx_destroy", "fr_constants", "fr_solve", "fr_solve_levels", "fr_solve_batch",
            "fr_cic_assign", "fr_smooth", "fr_residual", "fr_restrict", "fr_prolong_correct",
-           "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry"]
+           "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32"]
 
 
 def lib_path():
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = False):
             "fr_patch_bc": (I, [P, P, P, I, P, P, P, P, P]),
             "fr_launch_count": (L, [P]),
             "fr_profile": (I, [P, I]),
+            "fr_smooth_f32": (I, [P, P, P, P, P, D, D, D, D, D, P, I, D, I, P]),
             "fr_profile_entry": (I, [P, I, P, I, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -283,6 +284,14 @@ class Context:
         st = self.lib.fr_smooth(self._h, _ptr(u), _ptr(density), _ptr(f), _dims(u.shape), h, box,
                                 a, omega_m, fr0, _ptr(ub), nsweeps, cap, _stream(stream))
         self._raise(st, "fr_smooth")
+
+    def smooth_f32(self, u, nsweeps, *, box, a, omega_m, fr0, h=None, bg=None, f=None, ub=None,
+                   cap=1.0, tiled=True, stream=None):
+        h = 1.0 / u.shape[2] if h is None else h
+        st = self.lib.fr_smooth_f32(self._h, _ptr(u), _ptr(bg), _ptr(f), _dims(u.shape), h, box,
+                                    a, omega_m, fr0, _ptr(ub), nsweeps, cap, int(tiled),
+                                    _stream(stream))
+        self._raise(st, "fr_smooth_f32")
 
     def residual(self, u, density, d, *, box, a, omega_m, fr0, h=None, f=None, ub=None,
                  stream=None):

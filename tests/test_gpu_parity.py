@@ -234,3 +234,63 @@ def test_homogeneous_and_tiny_grids(C):
         st, s = C.solve(dev(np.ones(shape)), u, tol=1e-12, **CFG1)
         assert st == 0
         assert np.abs(host(u)).max() < 1e-10
+
+
+# ------------------------------------------------------------------ FP32 smoothing (mixed path)
+def _f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+F32_SHAPES = [(32, 32, 32), (20, 36, 70), (16, 18, 130)]
+
+
+@pytest.mark.parametrize("shape", F32_SHAPES)
+@pytest.mark.parametrize("bg", [False, True])
+@pytest.mark.parametrize("faces", [False, True])
+@pytest.mark.parametrize("nsweeps", [1, 2, 3])
+def test_f32_tiled_smoother_equals_simple(C, shape, bg, faces, nsweeps):
+    """The shared-memory temporally blocked kernel performs the same sweeps as
+    the one-colour-per-launch kernel (same formulas; FP32 rounding only)."""
+    rng = np.random.default_rng(17)
+    u0 = rng.uniform(-0.3, 0.3, shape) if bg else rng.uniform(-1.5, 0.3, shape)
+    f = rng.standard_normal(shape) * 0.3
+    b = rng.uniform(-1.5, 0.3, shape) if bg else None
+    ub = rng.uniform(-1.5, 0.3, sum(O.face_sizes(shape))) if faces else None
+    P = dict(box=128.0, a=0.9, omega_m=0.24, fr0=1e-5, h=1.0 / 48)
+    outs = []
+    for tiled in (False, True):
+        u = _f32(u0)
+        C.smooth_f32(u, nsweeps, bg=None if b is None else _f32(b), f=_f32(f),
+                     ub=None if ub is None else _f32(ub), tiled=tiled, **P)
+        outs.append(host(u).astype(np.float64))
+    assert np.abs(outs[0] - outs[1]).max() < 2e-6
+
+
+@pytest.mark.parametrize("bg", [False, True])
+@pytest.mark.parametrize("faces", [False, True])
+def test_f32_smoother_matches_oracle(C, bg, faces):
+    """FP32 sweeps (plain, and in the correction form on a background) track
+    the FP64 oracle's sweeps of the same full-variable equation."""
+    shape = (24, 20, 36)
+    rng = np.random.default_rng(23)
+    P = dict(box=128.0, a=1.0, omega_m=0.24, fr0=1e-5, h=1.0 / 40)
+    ub = rng.uniform(-1.2, 0.3, sum(O.face_sizes(shape))) if faces else None
+    ones = np.ones(shape)
+    if bg:
+        b = rng.uniform(-1.2, 0.3, shape).astype(np.float32).astype(np.float64)
+        d0 = rng.uniform(-0.05, 0.05, shape).astype(np.float32).astype(np.float64)
+        r = (rng.standard_normal(shape) * 0.05).astype(np.float32).astype(np.float64)
+        # full-variable equation A(u) = r + A(bg) with u0 = bg + d0
+        Abg = O.residual(b, ones, ub=ub, **P)
+        ref = O.smooth(b + d0, ones, 2, f=r + Abg, ub=ub, **P)
+        u = _f32(d0)
+        C.smooth_f32(u, 2, bg=_f32(b), f=_f32(r), ub=None if ub is None else _f32(ub), **P)
+        got = b + host(u).astype(np.float64)
+    else:
+        u0 = rng.uniform(-1.2, 0.3, shape).astype(np.float32).astype(np.float64)
+        f = (rng.standard_normal(shape) * 0.3).astype(np.float32).astype(np.float64)
+        ref = O.smooth(u0, ones, 2, f=f, ub=ub, **P)
+        u = _f32(u0)
+        C.smooth_f32(u, 2, f=_f32(f), ub=None if ub is None else _f32(ub), **P)
+        got = host(u).astype(np.float64)
+    assert np.abs(got - ref).max() < 2e-5
