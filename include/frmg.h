@@ -68,6 +68,8 @@ typedef struct {
     int max_outer;          /* mixed: cap on FP64 defect evaluations; 40 */
     int allow_negative_density; /* 0: reject rho < 0 (the paper's sine test needs 1) */
     int use_graph;          /* capture repeated V-cycles in CUDA graphs; 1 */
+    int temporal_depth;     /* FP32 sweeps per pass of the tiled smoother: 1 or 2;
+                               0 = library default */
 } fr_opts;
 
 typedef struct {

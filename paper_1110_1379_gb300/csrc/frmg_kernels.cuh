@@ -32,6 +32,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace frmg {
 
 template <typename T>
@@ -59,7 +61,16 @@ struct Grid {
 // math wrappers (library functions; no re-derived constants)
 __device__ __forceinline__ float m_exp(float v) { return expf(v); }
 __device__ __forceinline__ double m_exp(double v) { return exp(v); }
-__device__ __forceinline__ float m_expm1(float v) { return expm1f(v); }
+// FP32 e^d - 1 used by every FP32 kernel (so all of them see the same cache
+// values): the Taylor series to degree 6 for |d| < 1/16 (truncation below
+// 1e-12 relative, which keeps small corrections exact to FP32 rounding), and
+// the SFU exponential minus one otherwise.
+__device__ __forceinline__ float m_expm1(float d) {
+  if (fabsf(d) < 0.0625f)
+    return d * (1.0f + d * (0.5f + d * (1.0f / 6.0f + d * (1.0f / 24.0f +
+                                       d * (1.0f / 120.0f + d * (1.0f / 720.0f))))));
+  return __expf(d) - 1.0f;
+}
 __device__ __forceinline__ double m_expm1(double v) { return expm1(v); }
 __device__ __forceinline__ float m_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double m_sqrt(double v) { return sqrt(v); }
@@ -343,39 +354,47 @@ __global__ void k_reduce_partials(const double *partial, const int *off, int ngr
 
 // Fused residual + restriction (Sec. V.B.2): for each coarse cell, the 8 fine
 // children give  u^H = uR = mean(u^h),  x^H = expm1(u^H),  f^H <- mean(d^h)
-// (the coarse operator is added by k_fas_rhs).  One thread per coarse cell.
+// (the coarse operator is added by k_fas_rhs).  One thread per coarse cell;
+// optionally accumulates per-block (sum d^2, max |d|) of the fine residual.
 template <typename T, bool BG>
-__global__ void k_resid_restrict(const Grid<T> *fine, const Grid<T> *coarse, const int *off,
-                                 int ngrid, const int *active, int fpar, int cpar) {
+__global__ void __launch_bounds__(256)
+    k_resid_restrict(const Grid<T> *fine, const Grid<T> *coarse, const int *off, int ngrid,
+                     const int *active, int fpar, int cpar, double *partial) {
   int g = find_grid(off, ngrid, blockIdx.x);
   const Grid<T> F = view(fine, g, fpar);
   const Grid<T> C = view(coarse, g, cpar);
-  if (!grid_active(active, F.field)) return;
+  double ss = 0.0, mx = 0.0;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
-  if (t >= C.ncell) return;
-  int I = (int)(t % C.n0);
-  long long r = t / C.n0;
-  int J = (int)(r % C.n1);
-  int K = (int)(r / C.n1);
-  T su = T(0), sd = T(0);
+  if (grid_active(active, F.field) && t < C.ncell) {
+    int I = (int)(t % C.n0);
+    long long r = t / C.n0;
+    int J = (int)(r % C.n1);
+    int K = (int)(r / C.n1);
+    T su = T(0), sd = T(0);
 #pragma unroll
-  for (int cz = 0; cz < 2; cz++)
+    for (int cz = 0; cz < 2; cz++)
 #pragma unroll
-    for (int cy = 0; cy < 2; cy++)
+      for (int cy = 0; cy < 2; cy++)
 #pragma unroll
-      for (int cx = 0; cx < 2; cx++) {
-        int i = 2 * I + cx, j = 2 * J + cy, k = 2 * K + cz;
-        long long c = idx3(F, i, j, k);
-        T N, dN;
-        cell_eval<T, BG>(F, i, j, k, c, N, dN);
-        sd += N - rhs_at(F, c);
-        su += F.u[c];
-      }
-  T uh = su * T(0.125);
-  C.uR[t] = uh;
-  C.u[t] = uh;
-  C.x[t] = m_expm1(uh);
-  const_cast<T *>(C.f)[t] = sd * T(0.125);
+        for (int cx = 0; cx < 2; cx++) {
+          int i = 2 * I + cx, j = 2 * J + cy, k = 2 * K + cz;
+          long long c = idx3(F, i, j, k);
+          T N, dN;
+          cell_eval<T, BG>(F, i, j, k, c, N, dN);
+          T d = N - rhs_at(F, c);
+          sd += d;
+          ss += (double)d * (double)d;
+          mx = fmax(mx, fabs((double)d));
+          su += F.u[c];
+        }
+    T uh = su * T(0.125);
+    C.uR[t] = uh;
+    C.u[t] = uh;
+    C.x[t] = m_expm1(uh);
+    const_cast<T *>(C.f)[t] = sd * T(0.125);
+  }
+  // fine-grid residual norm partials (the residual after pre-smoothing)
+  if (partial) block_reduce2<256>(ss, mx, &partial[2 * blockIdx.x], &partial[2 * blockIdx.x + 1]);
 }
 
 // f^H = A^H(R u^h) - R d^h, in place over the R d^h stored in f (fs = 1, fo = 0).
@@ -398,48 +417,86 @@ __global__ void k_fas_rhs(const Grid<T> *grids, const int *off, int ngrid, const
 }
 
 // u^h += P (u^H - R u^h), trilinear 27/9/3/1 over 64 (Sec. V.A.3); x^h refreshed.
+// One thread per coarse cell writes its 8 children: the correction
+// e = u^H - R u^h of the 3x3x3 coarse neighbourhood is interpolated separably
+// (weights 3/4 for the containing cell, 1/4 for the neighbour on the child's
+// side, per axis; their products are the paper's 27/9/3/1 over 64).
 // Patches: coarse neighbours outside the grid contribute 0.
 template <typename T>
-__global__ void k_prolong(const Grid<T> *fine, const Grid<T> *coarse, const int *off, int ngrid,
-                          const int *active, int fpar, int cpar) {
+__global__ void __launch_bounds__(256) k_prolong(const Grid<T> *fine, const Grid<T> *coarse,
+                                                 const int *off, int ngrid, const int *active,
+                                                 int fpar, int cpar) {
   int g = find_grid(off, ngrid, blockIdx.x);
-  const Grid<T> F = view(fine, g, fpar);
-  const Grid<T> C = view(coarse, g, cpar);
-  if (!grid_active(active, F.field)) return;
+  const Grid<T> &Fg = fine[g];
+  const Grid<T> &Cg = coarse[g];
+  if (!grid_active(active, Fg.field)) return;
+  const int c0 = Cg.n0, c1 = Cg.n1, c2 = Cg.n2;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
-  if (t >= F.ncell) return;
-  int i = (int)(t % F.n0);
-  long long r = t / F.n0;
-  int j = (int)(r % F.n1);
-  int k = (int)(r / F.n1);
-  const bool dir = F.bnd != nullptr;
-  int pc[3] = {i >> 1, j >> 1, k >> 1};
-  int oc[3] = {pc[0] + ((i & 1) ? 1 : -1), pc[1] + ((j & 1) ? 1 : -1), pc[2] + ((k & 1) ? 1 : -1)};
-  const int nc[3] = {C.n0, C.n1, C.n2};
-  T s = T(0);
+  if (t >= (long long)c0 * c1 * c2) return;
+  const T *__restrict__ uH = cpar ? Cg.u2 : Cg.u;
+  const T *__restrict__ uR = Cg.uR;
+  T *__restrict__ uf = fpar ? Fg.u2 : Fg.u;
+  T *__restrict__ xf = Fg.x;
+  const bool dir = Fg.bnd != nullptr;
+  const int I = (int)(t % c0);
+  long long r = t / c0;
+  const int J = (int)(r % c1);
+  const int K = (int)(r / c1);
+  // e over the 3x3x3 neighbourhood, index [dz][dy][dx] with d = -1, 0, 1
+  T e[3][3][3];
 #pragma unroll
-  for (int sel = 0; sel < 8; sel++) {
-    int cc[3];
-    T w = T(1);
-    bool valid = true;
+  for (int dz = 0; dz < 3; dz++) {
+    int kk = K + dz - 1;
+    bool vz = kk >= 0 && kk < c2;
+    kk = kk < 0 ? kk + c2 : (kk >= c2 ? kk - c2 : kk);
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-      bool other = (sel >> d) & 1;
-      cc[d] = other ? oc[d] : pc[d];
-      w *= other ? T(1) : T(3);
-      if (cc[d] < 0 || cc[d] >= nc[d]) {
-        if (dir) valid = false;
-        cc[d] = cc[d] < 0 ? cc[d] + nc[d] : cc[d] - nc[d];
+    for (int dy = 0; dy < 3; dy++) {
+      int jj = J + dy - 1;
+      bool vy = jj >= 0 && jj < c1;
+      jj = jj < 0 ? jj + c1 : (jj >= c1 ? jj - c1 : jj);
+#pragma unroll
+      for (int dx = 0; dx < 3; dx++) {
+        int ii = I + dx - 1;
+        bool vx = ii >= 0 && ii < c0;
+        ii = ii < 0 ? ii + c0 : (ii >= c0 ? ii - c0 : ii);
+        long long ci = ((long long)kk * c1 + jj) * c0 + ii;
+        bool valid = !dir || (vx && vy && vz);
+        e[dz][dy][dx] = valid ? uH[ci] - uR[ci] : T(0);
       }
     }
-    if (valid) {
-      long long cidx = ((long long)cc[2] * C.n1 + cc[1]) * C.n0 + cc[0];
-      s += (w * T(1.0 / 64.0)) * (C.u[cidx] - C.uR[cidx]);
-    }
   }
-  T unew = F.u[t] + s;
-  F.u[t] = unew;
-  F.x[t] = m_expm1(unew);
+  const T w3 = T(0.75), w1 = T(0.25);
+  // along x: child a = 0 uses (dx = 1, 0), a = 1 uses (dx = 1, 2)
+  T ex[2][3][3];
+#pragma unroll
+  for (int dz = 0; dz < 3; dz++)
+#pragma unroll
+    for (int dy = 0; dy < 3; dy++) {
+      ex[0][dz][dy] = w3 * e[dz][dy][1] + w1 * e[dz][dy][0];
+      ex[1][dz][dy] = w3 * e[dz][dy][1] + w1 * e[dz][dy][2];
+    }
+  T exy[2][2][3];
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int dz = 0; dz < 3; dz++) {
+      exy[a][0][dz] = w3 * ex[a][dz][1] + w1 * ex[a][dz][0];
+      exy[a][1][dz] = w3 * ex[a][dz][1] + w1 * ex[a][dz][2];
+    }
+  const int f0 = Fg.n0, f1 = Fg.n1;
+#pragma unroll
+  for (int cz = 0; cz < 2; cz++)
+#pragma unroll
+    for (int cy = 0; cy < 2; cy++) {
+      const long long fi = ((long long)(2 * K + cz) * f1 + (2 * J + cy)) * f0 + 2 * I;
+#pragma unroll
+      for (int a = 0; a < 2; a++) {
+        const T corr = w3 * exy[a][cy][1] + w1 * exy[a][cy][cz == 0 ? 0 : 2];
+        const T un = uf[fi + a] + corr;
+        uf[fi + a] = un;
+        xf[fi + a] = m_expm1(un);
+      }
+    }
 }
 
 // Coarsest level: one block per grid, Newton-Gauss-Seidel sweeps until
@@ -536,9 +593,13 @@ __global__ void k_restrict_avg(const T *fine, int nf0, int nf1, int nf2, T *coar
 // in place for the kernels that follow.
 template <int S, int TX, int TY>
 struct TileCfg {
-  static constexpr int H = 2 * S;
+  static constexpr int H = 2 * S;                   // halo
   static constexpr int LX = TX + 2 * H, LY = TY + 2 * H, PL = LX * LY, NS = 2 * S + 2;
-  static constexpr size_t smem(bool bg) { return (size_t)NS * PL * sizeof(float) * (bg ? 4 : 2); }
+  static constexpr int PX = LX / 2;                 // x-pairs per row
+  static constexpr int RPT = 2;                     // rows per thread (independent updates)
+  static constexpr int NT = PX * LY / RPT;          // threads per block
+  static constexpr size_t smem(bool bg) { return (size_t)NS * PL * sizeof(float) * (bg ? 5 : 3); }
+  static_assert(LY % RPT == 0, "rows must split evenly over threads");
 };
 
 __device__ __forceinline__ int wrapmod(int v, int n) {
@@ -546,22 +607,55 @@ __device__ __forceinline__ int wrapmod(int v, int n) {
   return r < 0 ? r + n : r;
 }
 
-template <bool BG, int S, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_smooth_tiled(const Grid<float> *grids, const int *off,
-                                                     int ngrid, int zc, const int *active,
-                                                     int par) {
+// ---------------------------------------------------------------------------
+// Tiled FP32 smoother with temporal blocking: S full red-black sweeps per pass.
+//
+// A block owns a TX x TY tile of one grid and a chunk of zc planes; it marches
+// along z with a ring of 2S+2 planes (tile plus a halo of 2S cells in x and y)
+// in shared memory.  At the step that loads plane p, stage q (q = 0 .. 2S-1,
+// colour q & 1: red first) updates plane p-1-q on the tile grown by 2S-1-q
+// cells, so that plane p-2S is final and its tile cells are written out.
+// Halo cells are updated redundantly by neighbouring blocks from identical
+// inputs; a pass reads the current buffer and writes the other one (blocks
+// load their halos from the unmodified input), which makes the result equal to
+// S sweeps of k_smooth.
+//
+// Each thread owns one x-pair in each of RPT rows (LY/RPT rows apart) for the
+// whole pass: it loads and stores its pairs with 8-byte accesses (x-pairs
+// start at even x, and n0 is even, so a pair never straddles the periodic
+// seam), and at every stage it updates, in each of its rows, the one cell of
+// its pair that has the stage's colour if that cell lies in the stage's
+// region; the RPT updates are independent, which gives the scheduler
+// instruction-level parallelism.  x = expm1(u) is recomputed from u on load
+// and written in place for the kernels that follow; the right-hand side is
+// kept in shared memory with the plane.  The global loads of plane p+1 are
+// issued into registers before the stages of step p and stored to shared
+// memory after them.
+template <bool BG, int S, int TX, int TY>
+__global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
+    k_smooth_tiled(const Grid<float> *grids, const int *off, int ngrid, int zc, const int *active,
+                   int par) {
   using C = TileCfg<S, TX, TY>;
-  constexpr int H = C::H, LX = C::LX, PL = C::PL, NS = C::NS;
+  constexpr int H = C::H, LX = C::LX, LY = C::LY, PL = C::PL, NS = C::NS, PX = C::PX;
+  constexpr int RPT = C::RPT;
   extern __shared__ float smem[];
   float *sd = smem;
   float *sx = smem + NS * PL;
-  float *sub = smem + 2 * NS * PL;
-  float *sE = smem + 3 * NS * PL;
+  float *sf = smem + 2 * NS * PL;
+  float *sub = smem + 3 * NS * PL;
+  float *sE = smem + 4 * NS * PL;
   const int g = find_grid(off, ngrid, blockIdx.x);
-  const Grid<float> G = view(grids, g, par);
-  if (!grid_active(active, G.field)) return;
-  float *__restrict__ uout = par ? grids[g].u : grids[g].u2;
-  const int n0 = G.n0, n1 = G.n1, n2 = G.n2;
+  const Grid<float> &Gg = grids[g];
+  if (!grid_active(active, Gg.field)) return;
+  const float *__restrict__ uin = par ? Gg.u2 : Gg.u;
+  float *__restrict__ uout = par ? Gg.u : Gg.u2;
+  float *__restrict__ xout = Gg.x;
+  const float *__restrict__ fin = Gg.f;
+  const float *__restrict__ ubin = Gg.ubg;
+  const float *__restrict__ Ein = Gg.Ebg;
+  const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap;
+  const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
+  const bool dir = Gg.bnd != nullptr;
   const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
   int b = blockIdx.x - off[g];
   const int X0 = (b % ntx) * TX;
@@ -570,115 +664,159 @@ __global__ void __launch_bounds__(NT) k_smooth_tiled(const Grid<float> *grids, c
   b /= nty;
   const int Z0 = b * zc;
   const int Z1 = min(Z0 + zc, n2);
-  const bool dir = G.bnd != nullptr;
 
-  for (int p = Z0 - H; p < Z1 + H; p++) {
-    // ---- load plane p (raw input values)
-    if (!dir || (p >= 0 && p < n2)) {
-      const int sl = wrapmod(p, NS);
-      const int gz = wrapmod(p, n2);
-      for (int c = threadIdx.x; c < PL; c += NT) {
-        const int ly = c / LX, lx = c - ly * LX;
-        const int gx = X0 - H + lx, gy = Y0 - H + ly;
-        if (dir && (gx < 0 || gx >= n0 || gy < 0 || gy >= n1)) continue;
-        const long long gi = ((long long)gz * n1 + wrapmod(gy, n1)) * n0 + wrapmod(gx, n0);
-        const float d = G.u[gi];
-        sd[sl * PL + c] = d;
-        sx[sl * PL + c] = m_expm1(d);
-        if (BG) {
-          sub[sl * PL + c] = G.ubg[gi];
-          sE[sl * PL + c] = G.Ebg[gi];
-        }
+  const int ly0 = threadIdx.x / PX;
+  const int lx0 = 2 * (threadIdx.x - ly0 * PX);
+  const int gx0 = X0 - H + lx0;
+  int gxw0;
+  if (dir)
+    gxw0 = (gx0 < 0 || gx0 >= n0) ? -1 : gx0;
+  else
+    gxw0 = wrapmod(gx0, n0);
+  int ly[RPT], gy[RPT], gyw[RPT], rowo[RPT];
+  bool mine[RPT], writer[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; r++) {
+    ly[r] = ly0 + r * (LY / RPT);
+    gy[r] = Y0 - H + ly[r];
+    if (dir)
+      gyw[r] = (gy[r] < 0 || gy[r] >= n1) ? -1 : gy[r];
+    else
+      gyw[r] = wrapmod(gy[r], n1);
+    mine[r] = gyw[r] >= 0 && gxw0 >= 0;
+    rowo[r] = ly[r] * LX + lx0;
+    writer[r] = mine[r] && ly[r] >= H && ly[r] < H + TY && lx0 >= H && lx0 < H + TX &&
+                gx0 < n0 && gy[r] < n1;
+  }
+
+  float2 pd[RPT], pf[RPT], pu[RPT], pE[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; r++) {
+    pd[r] = make_float2(0.f, 0.f);
+    pf[r] = pd[r];
+    pu[r] = pd[r];
+    pE[r] = make_float2(1.f, 1.f);
+  }
+  auto fetch = [&](int p) {
+    if (dir && (p < 0 || p >= n2)) return;
+    const long long zo = (long long)wrapmod(p, n2) * n1;
+#pragma unroll
+    for (int r = 0; r < RPT; r++) {
+      if (!mine[r]) continue;
+      const long long gi = (zo + gyw[r]) * n0 + gxw0;
+      pd[r] = *reinterpret_cast<const float2 *>(uin + gi);
+      if (fin) {
+        const float2 fv = *reinterpret_cast<const float2 *>(fin + gi);
+        pf[r] = make_float2(fs * (fv.x - fo), fs * (fv.y - fo));
+      }
+      if (BG) {
+        pu[r] = *reinterpret_cast<const float2 *>(ubin + gi);
+        pE[r] = *reinterpret_cast<const float2 *>(Ein + gi);
       }
     }
-    __syncthreads();
-    // ---- 2S wavefront stages
+  };
+  auto commit = [&](int p) {
+    const int base = wrapmod(p, NS) * PL;
 #pragma unroll
-    for (int q = 0; q < 2 * S; q++) {
-      const int m = p - 1 - q;
-      const int R = 2 * S - 1 - q;
-      const int colour = q & 1;
-      const bool zok = m >= Z0 - R && m < Z1 + R && (!dir || (m >= 0 && m < n2));
-      if (zok) {
-        int xs = X0 - R, xe = X0 + TX + R, ys = Y0 - R, ye = Y0 + TY + R;
-        if (dir) {
-          xs = max(xs, 0);
-          xe = min(xe, n0);
-          ys = max(ys, 0);
-          ye = min(ye, n1);
-        }
-        const int W = xe - xs, nr = ye - ys;
-        const int per = (W + 1) >> 1;
-        const int sl = wrapmod(m, NS), slm = wrapmod(m - 1, NS), slp = wrapmod(m + 1, NS);
-        const int gzw = wrapmod(m, n2);
-        for (int c = threadIdx.x; c < per * nr; c += NT) {
-          const int row = c / per, k2 = c - row * per;
-          const int gy = ys + row;
-          const int gx = xs + ((xs + gy + m + colour) & 1) + 2 * k2;
-          if (gx >= xe) continue;
-          const int li = (gy - (Y0 - H)) * LX + (gx - (X0 - H));
-          const int o = sl * PL + li;
-          const float di = sd[o], xi = sx[o];
-          const float Ei = BG ? sE[o] : 1.0f;
-          const float ubi = BG ? sub[o] : 0.0f;
-          const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
-          float acc = 0.0f, dacc = 0.0f;
+    for (int r = 0; r < RPT; r++) {
+      const int o = base + rowo[r];
+      sd[o] = pd[r].x;
+      sd[o + 1] = pd[r].y;
+      sx[o] = m_expm1(pd[r].x);
+      sx[o + 1] = m_expm1(pd[r].y);
+      sf[o] = pf[r].x;
+      sf[o + 1] = pf[r].y;
+      if (BG) {
+        sub[o] = pu[r].x;
+        sub[o + 1] = pu[r].y;
+        sE[o] = pE[r].x;
+        sE[o + 1] = pE[r].y;
+      }
+    }
+  };
+  auto stage = [&](int p, int q) {
+    const int m = p - 1 - q;
+    const int R = 2 * S - 1 - q;
+    const int colour = q & 1;
+    if (m < Z0 - R || m >= Z1 + R || (dir && (m < 0 || m >= n2))) return;
+    const int sl = wrapmod(m, NS), slm = wrapmod(m - 1, NS), slp = wrapmod(m + 1, NS);
+#pragma unroll
+    for (int r = 0; r < RPT; r++) {
+      const int par01 = (X0 - H + gy[r] + m + colour) & 1;
+      const int lx = lx0 + par01;
+      if (!mine[r] || ly[r] < H - R || ly[r] >= H + TY + R || lx < H - R || lx >= H + TX + R)
+        continue;
+      const int li = rowo[r] + par01;
+      const int o = sl * PL + li;
+      const float di = sd[o], xi = sx[o];
+      const float Ei = BG ? sE[o] : 1.0f;
+      const float ubi = BG ? sub[o] : 0.0f;
+      const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
+      float acc = 0.0f, dacc = 0.0f;
+      const int gxw = gxw0 + par01, gyr = gyw[r];
 #define FR_NB(OFF)                                                                          \
   face_vals<float, BG>(sd[OFF], sx[OFF], BG ? sub[OFF] : 0.0f, BG ? sE[OFF] : 1.0f, di, Ei, \
                        xi, Bi, ubi, acc, dacc)
-          if (dir && gx == 0)
-            face_ghost<float, BG>(face_value(G, 0, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
-          else
-            FR_NB(o - 1);
-          if (dir && gx == n0 - 1)
-            face_ghost<float, BG>(face_value(G, 1, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
-          else
-            FR_NB(o + 1);
-          if (dir && gy == 0)
-            face_ghost<float, BG>(face_value(G, 2, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
-          else
-            FR_NB(o - LX);
-          if (dir && gy == n1 - 1)
-            face_ghost<float, BG>(face_value(G, 3, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
-          else
-            FR_NB(o + LX);
-          if (dir && m == 0)
-            face_ghost<float, BG>(face_value(G, 4, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
-          else
-            FR_NB(slm * PL + li);
-          if (dir && m == n2 - 1)
-            face_ghost<float, BG>(face_value(G, 5, gx, gy, m), di, Ei, xi, Bi, ubi, acc, dacc);
-          else
-            FR_NB(slp * PL + li);
+      if (dir && gxw == 0)
+        face_ghost<float, BG>(face_value(Gg, 0, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+      else
+        FR_NB(o - 1);
+      if (dir && gxw == n0 - 1)
+        face_ghost<float, BG>(face_value(Gg, 1, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+      else
+        FR_NB(o + 1);
+      if (dir && gyr == 0)
+        face_ghost<float, BG>(face_value(Gg, 2, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+      else
+        FR_NB(o - LX);
+      if (dir && gyr == n1 - 1)
+        face_ghost<float, BG>(face_value(Gg, 3, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+      else
+        FR_NB(o + LX);
+      if (dir && m == 0)
+        face_ghost<float, BG>(face_value(Gg, 4, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+      else
+        FR_NB(slm * PL + li);
+      if (dir && m == n2 - 1)
+        face_ghost<float, BG>(face_value(Gg, 5, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+      else
+        FR_NB(slp * PL + li);
 #undef FR_NB
-          float N, dN;
-          finish_op(xi, Ei, acc, dacc, G.ah, G.beta, BG, N, dN);
-          const long long gi = ((long long)gzw * n1 + wrapmod(gy, n1)) * n0 + wrapmod(gx, n0);
-          const float f = G.f ? G.fs * (G.f[gi] - G.fo) : 0.0f;
-          float du = newton_step(N - f, dN);
-          du = du > G.cap ? G.cap : (du < -G.cap ? -G.cap : du);
-          const float dn = di + du;
-          sd[o] = dn;
-          sx[o] = m_expm1(dn);
-        }
-      }
+      float N, dN;
+      finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
+      float du = newton_step(N - sf[o], dN);
+      du = fminf(fmaxf(du, -cap), cap);
+      const float dn = di + du;
+      sd[o] = dn;
+      sx[o] = m_expm1(dn);
+    }
+  };
+
+  fetch(Z0 - H);
+  commit(Z0 - H);
+  __syncthreads();
+  for (int p = Z0 - H; p < Z1 + H; p++) {
+    const bool more = p + 1 < Z1 + H;
+    if (more) fetch(p + 1);
+#pragma unroll
+    for (int q = 0; q < 2 * S; q++) {
+      stage(p, q);
       __syncthreads();
     }
-    // ---- plane p - 2S is final: write the tile cells
     const int w = p - H;
     if (w >= Z0 && w < Z1) {
-      const int sl = wrapmod(w, NS);
-      for (int c = threadIdx.x; c < TX * TY; c += NT) {
-        const int ty = c / TX, tx = c - ty * TX;
-        const int gx = X0 + tx, gy = Y0 + ty;
-        if (gx < n0 && gy < n1) {
-          const int o = sl * PL + (ty + H) * LX + tx + H;
-          const long long gi = ((long long)w * n1 + gy) * n0 + gx;
-          uout[gi] = sd[o];
-          G.x[gi] = sx[o];
-        }
+      const int base = wrapmod(w, NS) * PL;
+#pragma unroll
+      for (int r = 0; r < RPT; r++) {
+        if (!writer[r]) continue;
+        const int o = base + rowo[r];
+        const long long gi = ((long long)w * n1 + gy[r]) * n0 + gx0;
+        *reinterpret_cast<float2 *>(uout + gi) = make_float2(sd[o], sd[o + 1]);
+        *reinterpret_cast<float2 *>(xout + gi) = make_float2(sx[o], sx[o + 1]);
       }
     }
+    if (more) commit(p + 1);
+    __syncthreads();
   }
 }
 

@@ -306,6 +306,31 @@ __global__ void k_prep_inner(const double *d64, const double *u64, float *r32, f
   x32[t] = 0.0f;
 }
 
+// Zero-start set-up of the mixed loop: the first inner solve works on the full
+// variable, u32 = 0 with right-hand side fp32(gamma (rho - 1)).
+// Block partials of (sum r^2, max |r|) go to partial[2 (base + block)]: the
+// initial residual is A(0) - gamma (rho - 1) = -r.
+__global__ void __launch_bounds__(256) k_prep_zero(const double *rho, double gamma, float *r32,
+                                                   float *u32, float *x32, long long n,
+                                                   double *partial, int base) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0.0, m = 0.0;
+  if (t < n) {
+    double r = gamma * (rho[t] - 1.0);
+    r32[t] = (float)r;
+    u32[t] = 0.0f;
+    x32[t] = 0.0f;
+    s = r * r;
+    m = fabs(r);
+  }
+  block_reduce2<256>(s, m, &partial[2 * (base + blockIdx.x)], &partial[2 * (base + blockIdx.x) + 1]);
+}
+
+__global__ void k_any_nonzero(const double *u, long long n, int *flag) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n && u[t] != 0.0) atomicExch(flag, 1);
+}
+
 // u += delta in FP64, x = expm1(u).
 __global__ void k_update64(double *u64, double *x64, const float *delta, long long n) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,8 +383,8 @@ struct Problem {
   int nl;
 };
 
-// tile of the tiled smoother
-constexpr int kTX = 64, kTY = 16, kTNT = 256;
+// tile of the tiled smoother (x by y cells; S = 1 and S = 2 sweeps per pass)
+constexpr int kTX = 64, kTY = 16;
 
 template <typename T>
 struct LevelSet {
@@ -369,7 +394,8 @@ struct LevelSet {
   int *d_off_half = nullptr, *d_off_full = nullptr;
   int nblk_half = 0, nblk_full = 0;
   // tiled FP32 smoother: blocks per grid for TX x TY tiles and zc-plane chunks
-  bool tiled = false;
+  bool tiled = false;     // the tiled smoother is used for this set
+  bool tiled_ok = false;  // it could be used (every grid >= 16 cells a side)
   int zc = 0;
   std::vector<int> off_tile;
   int *d_off_tile = nullptr;
@@ -413,10 +439,15 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st) {
     txy += (long long)((G.n0 + kTX - 1) / kTX) * ((G.n1 + kTY - 1) / kTY);
   }
   if (ls.tiled) {
-    // aim at ~8 resident blocks per SM-pair wave: chunks of z so that the set
-    // yields about 1216 blocks, never thinner than 32 planes
+    // chunks of z so that the set yields about 1216 blocks (several waves of
+    // resident blocks), never thinner than 32 planes; sets too small to fill
+    // the GPU with such blocks use the one-thread-per-cell kernel instead
     long long nz = std::max<long long>(1, (1216 + txy - 1) / txy);
     ls.zc = (int)std::max<long long>(std::min(32, maxn2), (maxn2 + nz - 1) / nz);
+    ls.tiled_ok = true;
+    if (txy * ((maxn2 + ls.zc - 1) / ls.zc) < 304) ls.tiled = false;
+  }
+  if (ls.tiled_ok) {
     ls.off_tile.assign(ng + 1, 0);
     for (int g = 0; g < ng; g++) {
       const Grid<T> &G = ls.h[g];
@@ -552,6 +583,7 @@ static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap
 // V-cycle (Sec. V.B.2), batched over the grids of each depth
 struct CycleOpts {
   int pre, post;
+  int tdepth;  // sweeps per tiled pass (1 or 2)
   double crs_rel, crs_abs;
   int crs_maxit, crs_stall;
 };
@@ -576,15 +608,16 @@ static const char *pname(const char *kind, bool f64, bool fine) {
 template <bool BG, int S>
 static void launch_tiled(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
                          cudaStream_t st) {
-  size_t sm = TileCfg<S, kTX, kTY>::smem(BG);
+  using TC = TileCfg<S, kTX, kTY>;
+  size_t sm = TC::smem(BG);
   static bool attr_set = false;
   if (!attr_set) {
-    CK(cudaFuncSetAttribute(k_smooth_tiled<BG, S, kTX, kTY, kTNT>,
+    CK(cudaFuncSetAttribute(k_smooth_tiled<BG, S, kTX, kTY>,
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
-  k_smooth_tiled<BG, S, kTX, kTY, kTNT><<<s.nblk_tile, kTNT, sm, st>>>(s.d, s.d_off_tile, s.size(),
-                                                                      s.zc, active, par);
+  k_smooth_tiled<BG, S, kTX, kTY><<<s.nblk_tile, TC::NT, sm, st>>>(s.d, s.d_off_tile, s.size(),
+                                                                   s.zc, active, par);
 }
 
 // Passes of the tiled smoother (sweeps per pass) for the pre- and post-smoothing
@@ -592,14 +625,17 @@ static void launch_tiled(frmg_ctx *ctx, LevelSet<float> &s, const int *active, i
 // level's data is back in its starting buffer when the coarser V-cycle reads it
 // (grids whose coarsest level is this depth are not smoothed here).  Returns
 // false if no even plan exists (then the in-place kernel is used).
-static bool plan_passes(int pre, int post, std::vector<int> &a, std::vector<int> &b) {
-  auto split = [](int n, std::vector<int> &v) {
+static bool plan_passes(int pre, int post, int depth, std::vector<int> &a, std::vector<int> &b) {
+  auto split = [depth](int n, std::vector<int> &v) {
     v.clear();
-    while (n >= 2) {
+    while (n >= 2 && depth >= 2) {
       v.push_back(2);
       n -= 2;
     }
-    if (n) v.push_back(1);
+    while (n > 0) {
+      v.push_back(1);
+      n -= 1;
+    }
   };
   split(pre, a);
   split(post, b);
@@ -656,12 +692,13 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
   auto &F = H.cont[l];
   auto &C = H.next[l];
   std::vector<int> plan_pre, plan_post;
-  bool even = plan_passes(o.pre, o.post, plan_pre, plan_post);
+  bool even = plan_passes(o.pre, o.post, o.tdepth, plan_pre, plan_post);
   smooth_set<T, BG>(ctx, F, o.pre, even ? &plan_pre : nullptr, active, H.par[l], st, l == 0);
   {
     PROF(pname("resid_restrict", sizeof(T) == 8, l == 0));
     k_resid_restrict<T, BG><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, C.size(),
-                                                         active, H.par[l], H.par[l + 1]);
+                                                         active, H.par[l], H.par[l + 1],
+                                                         l == 0 ? C.partial : nullptr);
     CK_LAUNCH(ctx);
   }
   {
@@ -673,7 +710,7 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
   vcycle<T, BG>(ctx, H, l + 1, o, active, st);
   {
     PROF(pname("prolong", sizeof(T) == 8, l == 0));
-    k_prolong<T><<<F.nblk_full, 256, 0, st>>>(F.d, C.d, F.d_off_full, F.size(), active,
+    k_prolong<T><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, F.size(), active,
                                               H.par[l], H.par[l + 1]);
     CK_LAUNCH(ctx);
   }
@@ -708,6 +745,28 @@ static void level_norms(frmg_ctx *ctx, LevelSet<T> &s, T *const *dout, const int
   }
 }
 
+// Fine-grid residual norms accumulated by the last depth-0 residual+restriction
+// (after pre-smoothing of the last V-cycle); out[p] = rms per problem (NaN for
+// problems without a coarser level).
+template <typename T>
+static void fused_fine_norms(frmg_ctx *ctx, Hier<T> &H, int np, cudaStream_t st,
+                             std::vector<double> &out) {
+  out.assign(np, std::nan(""));
+  LevelSet<T> &C = H.next[0];
+  if (C.empty()) return;
+  int ng = C.size();
+  k_reduce_partials<<<ng, 256, 0, st>>>(C.partial, C.d_off_full, ng, C.red);
+  CK_LAUNCH(ctx);
+  double *hp = pinned_buf(ctx, 2 * (size_t)ng);
+  CK(cudaMemcpyAsync(hp, C.red, 2 * ng * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  prof_harvest(ctx);
+  for (int g = 0; g < ng; g++) {
+    const Grid<T> &F = H.cont[0].h[g];
+    out[F.field] = std::sqrt(hp[2 * g] / (double)F.ncell);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // solve loops
 struct SolveCfg {
@@ -716,6 +775,7 @@ struct SolveCfg {
   double cap;
   int inner_cycles, max_outer;
   int fixed_cycles;  // > 0: exactly this many (FP64 only), no convergence test
+  int tdepth;
 };
 
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
@@ -734,7 +794,7 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
   }
   int *active = S.get<int>(np);
   std::vector<int> act(np, 1);
-  CycleOpts co{cfg.pre, cfg.post, 1e-3, 0.1 * cfg.tol, 500, 0};
+  CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.1 * cfg.tol, 500, 0};
   std::vector<double> nr;
   level_norms<double, false>(ctx, H.all[0], nullptr, nullptr, st, nr);
   std::vector<double> prev(np);
@@ -770,33 +830,114 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
   }
 }
 
-// Mixed: FP64 defect / update / test around FP32 background-mode V-cycles.
+// Mixed: FP64 defect / update / test around FP32 V-cycles.
+// Zero initial guess: the first inner solve is a full-variable FP32 FAS solve
+// (no FP64 defect needed, r = gamma (rho - 1)) run until its residual stops
+// falling.  Every later inner solve is a correction solve in background mode
+// on the FP32 background fp32(u), stopped once its residual is below a
+// fraction of tol or stops falling.
 static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &cfg,
                         std::vector<fr_stats> &stats, cudaStream_t st) {
   Scope S(ctx);
   int np = (int)P.size();
-  Hier<double> H64;  // FP64 fine levels only (defect); coarse levels unused
+  Hier<double> H64;  // FP64 fine levels only (defect)
   std::vector<Problem> P1 = P;
   for (auto &p : P1) p.nl = 1;
   build_hier<double, false>(S, H64, P1, cfg.cap, st, ctx);
   Hier<float> H;
   build_hier<float, true>(S, H, P, cfg.cap, st, ctx);
   std::vector<double *> d64(np);
+  int *flag = S.get<int>(1);
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
   for (int pi = 0; pi < np; pi++) {
     Grid<double> &G = H64.lev[pi][0];
     d64[pi] = S.get<double>(G.ncell);
-    k_expm1<double><<<nblocks(G.ncell), 256, 0, st>>>(G.u, G.x, G.ncell);
+    k_any_nonzero<<<nblocks(G.ncell), 256, 0, st>>>(G.u, G.ncell, flag);
     CK_LAUNCH(ctx);
   }
+  int nonzero = 0;
+  CK(cudaMemcpyAsync(&nonzero, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   int *active = S.get<int>(np);
   std::vector<int> act(np, 1);
-  CycleOpts co{cfg.pre, cfg.post, 1e-3, 0.0, 500, 1};
+  CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.0, 500, 1};
   std::vector<double> nr, inr;
   std::vector<double> prev(np, 0.0);
   std::vector<int> grow(np, 0);
   for (int pi = 0; pi < np; pi++) {
     stats[pi].vcycles = 0;
     stats[pi].outer = 0;
+  }
+  auto update = [&]() {
+    for (int pi = 0; pi < np; pi++) {
+      if (!act[pi]) continue;
+      Grid<double> &G64 = H64.lev[pi][0];
+      PROF("update64");
+      k_update64<<<nblocks(G64.ncell), 256, 0, st>>>(G64.u, G64.x, H.cur_u(pi, 0), G64.ncell);
+      CK_LAUNCH(ctx);
+    }
+  };
+  // inner V-cycles with the fused fine-residual norm as the stopping signal
+  auto inner = [&](bool bg, const std::vector<double> &r0, double floor_rel, int kmax) {
+    std::vector<double> rp = r0;
+    for (int k = 0; k < kmax; k++) {
+      if (bg)
+        vcycle<float, true>(ctx, H, 0, co, active, st);
+      else
+        vcycle<float, false>(ctx, H, 0, co, active, st);
+      bool go = false;
+      for (int pi = 0; pi < np; pi++)
+        if (act[pi]) {
+          stats[pi].vcycles++;
+          if (stats[pi].vcycles < cfg.max_vcycles) go = true;
+        }
+      if (!go) break;
+      fused_fine_norms(ctx, H, np, st, inr);
+      go = false;
+      for (int pi = 0; pi < np; pi++) {
+        if (!act[pi]) continue;
+        double r = inr[pi];
+        if (!(r == r)) continue;  // single-level grid: one coarsest solve per cycle
+        if (r < 0.5 * rp[pi] && r > floor_rel * r0[pi] && r > 0.3 * cfg.tol) go = true;
+        rp[pi] = r;
+      }
+      if (!go) break;
+    }
+  };
+  if (!nonzero) {
+    // full-variable FP32 phase from u = 0
+    for (int pi = 0; pi < np; pi++) {
+      Grid<float> &G = H.lev[pi][0];
+      Grid<double> &G64 = H64.lev[pi][0];
+      PROF("prep_inner");
+      LevelSet<double> &A0 = H64.all[0];
+      k_prep_zero<<<nblocks(G.ncell), 256, 0, st>>>(G64.f, P[pi].k.gamma,
+                                                    const_cast<float *>(G.f), H.cur_u(pi, 0),
+                                                    G.x, G.ncell, A0.partial, A0.off_full[pi]);
+      CK_LAUNCH(ctx);
+    }
+    CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<double> r0(np, 0.0);
+    {
+      LevelSet<double> &A0 = H64.all[0];
+      k_reduce_partials<<<np, 256, 0, st>>>(A0.partial, A0.d_off_full, np, A0.red);
+      CK_LAUNCH(ctx);
+      double *hp = pinned_buf(ctx, 2 * (size_t)np);
+      CK(cudaMemcpyAsync(hp, A0.red, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int pi = 0; pi < np; pi++) {
+        r0[pi] = std::sqrt(hp[2 * pi] / (double)A0.h[pi].ncell);
+        stats[pi].res0_rms = r0[pi];
+      }
+    }
+    inner(false, r0, 1e-7, 40);
+    update();
+  } else {
+    for (int pi = 0; pi < np; pi++) {
+      Grid<double> &G = H64.lev[pi][0];
+      k_expm1<double><<<nblocks(G.ncell), 256, 0, st>>>(G.u, G.x, G.ncell);
+      CK_LAUNCH(ctx);
+    }
   }
   for (int outer = 0; outer < cfg.max_outer; outer++) {
     // FP64 defect and convergence test
@@ -806,7 +947,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
     for (int pi = 0; pi < np; pi++) {
       if (!act[pi]) continue;
       stats[pi].outer++;
-      if (outer == 0) stats[pi].res0_rms = nr[2 * pi];
+      if (outer == 0 && nonzero) stats[pi].res0_rms = nr[2 * pi];
       stats[pi].res_rms = nr[2 * pi];
       stats[pi].res_max = nr[2 * pi + 1];
       if (bad(nr[2 * pi])) throw FrError{FR_EDIVERGED, "non-finite residual"};
@@ -815,27 +956,27 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
         if (grow[pi] >= 3) throw FrError{FR_EDIVERGED, "FP64 defect grew for 3 outer steps"};
       }
       prev[pi] = nr[2 * pi];
-      if (nr[2 * pi] <= cfg.tol)
+      if (nr[2 * pi] <= cfg.tol || stats[pi].vcycles >= cfg.max_vcycles)
         act[pi] = 0;
       else
         nact++;
     }
     if (nact == 0) return;
-    bool any_left = false;
-    for (int pi = 0; pi < np; pi++)
-      if (act[pi] && stats[pi].vcycles < cfg.max_vcycles) any_left = true;
-    if (!any_left) return;
     CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
-    // inner problem set-up: rhs, background on every level, zero correction
+    // correction problem: rhs -d, background fp32(u) on every level, delta = 0
+    std::vector<double> r0(np, 0.0);
     for (int pi = 0; pi < np; pi++) {
       if (!act[pi]) continue;
+      r0[pi] = nr[2 * pi];
       Grid<float> &G = H.lev[pi][0];
       Grid<double> &G64 = H64.lev[pi][0];
-      PROF("prep_inner");
-      k_prep_inner<<<nblocks(G.ncell), 256, 0, st>>>(d64[pi], G64.u, const_cast<float *>(G.f),
-                                                     H.bg_u[pi], H.bg_E[pi], H.cur_u(pi, 0), G.x,
-                                                     G.ncell);
-      CK_LAUNCH(ctx);
+      {
+        PROF("prep_inner");
+        k_prep_inner<<<nblocks(G.ncell), 256, 0, st>>>(d64[pi], G64.u, const_cast<float *>(G.f),
+                                                       H.bg_u[pi], H.bg_E[pi], H.cur_u(pi, 0),
+                                                       G.x, G.ncell);
+        CK_LAUNCH(ctx);
+      }
       for (size_t l = 1; l < H.lev[pi].size(); l++) {
         Grid<float> &F = H.lev[pi][l - 1];
         Grid<float> &C = H.lev[pi][l];
@@ -846,36 +987,8 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
         CK_LAUNCH(ctx);
       }
     }
-    // inner FP32 V-cycles: the first outer step runs until the FP32 residual
-    // stops falling; later ones run inner_cycles
-    int kmax = outer == 0 ? 30 : cfg.inner_cycles;
-    std::vector<double> r0;
-    if (outer == 0) level_norms<float, true>(ctx, H.all[0], nullptr, active, st, r0, H.par[0]);
-    std::vector<double> rp = r0;
-    for (int k = 0; k < kmax; k++) {
-      vcycle<float, true>(ctx, H, 0, co, active, st);
-      for (int pi = 0; pi < np; pi++)
-        if (act[pi]) stats[pi].vcycles++;
-      if (outer == 0) {
-        level_norms<float, true>(ctx, H.all[0], nullptr, active, st, inr, H.par[0]);
-        bool go = false;
-        for (int pi = 0; pi < np; pi++) {
-          if (!act[pi]) continue;
-          double r = inr[2 * pi];
-          if (r > 1e-6 * r0[2 * pi] && r < 0.5 * rp[2 * pi] && r > 0.3 * cfg.tol) go = true;
-          rp[2 * pi] = r;
-        }
-        if (!go) break;
-      }
-    }
-    // u += delta (FP64)
-    for (int pi = 0; pi < np; pi++) {
-      if (!act[pi]) continue;
-      Grid<double> &G64 = H64.lev[pi][0];
-      PROF("update64");
-      k_update64<<<nblocks(G64.ncell), 256, 0, st>>>(G64.u, G64.x, H.cur_u(pi, 0), G64.ncell);
-      CK_LAUNCH(ctx);
-    }
+    inner(true, r0, 1e-6, std::max(cfg.inner_cycles, 12));
+    update();
   }
 }
 
@@ -950,7 +1063,8 @@ static fr_opts resolve_opts(const fr_opts *o) {
 static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &o, double tol,
                          std::vector<fr_stats> &stats, cudaStream_t st, int fixed = 0) {
   SolveCfg cfg{tol, o.max_vcycles, o.pre, o.post, o.newton_step_cap, o.inner_cycles,
-               o.max_outer, fixed};
+               o.max_outer, fixed, o.temporal_depth <= 0 ? 1 : o.temporal_depth};
+  if (cfg.tdepth > 2) einval("temporal_depth must be 0, 1 or 2");
   if (o.pre < 0 || o.post < 0 || o.max_vcycles < 0 || !(o.newton_step_cap > 0) ||
       !(tol >= 0) || o.inner_cycles < 1 || o.max_outer < 1)
     einval("invalid options");
@@ -1110,6 +1224,7 @@ void fr_opts_default(fr_opts *o) {
   o->max_outer = 40;
   o->allow_negative_density = 0;
   o->use_graph = 1;
+  o->temporal_depth = 0;
 }
 
 const char *fr_status_string(int s) {
@@ -1545,8 +1660,8 @@ int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, cons
     LevelSet<float> ls;
     ls.h.push_back(G);
     upload_set(S, ls, st);
-    if (tiled && !ls.tiled) einval("tiled smoothing needs at least 16 cells a side");
-    if (!tiled) ls.tiled = false;
+    if (tiled && !ls.tiled_ok) einval("tiled smoothing needs at least 16 cells a side");
+    ls.tiled = tiled != 0;
     std::vector<int> plan;
     for (int n = nsweeps; n > 0; n -= 2) plan.push_back(n >= 2 ? 2 : 1);
     int par = 0;
@@ -1640,7 +1755,7 @@ int fr_prolong_correct(frmg_ctx *ctx, double *uf, const int dims[3], const doubl
     lc.h.push_back(C);
     upload_set(S, lf, st);
     upload_set(S, lc, st);
-    k_prolong<double><<<lf.nblk_full, 256, 0, st>>>(lf.d, lc.d, lf.d_off_full, 1, nullptr, 0, 0);
+    k_prolong<double><<<lc.nblk_full, 256, 0, st>>>(lf.d, lc.d, lc.d_off_full, 1, nullptr, 0, 0);
     CK_LAUNCH(ctx);
     finish(ctx, back, st);
     return FR_OK;

@@ -27,7 +27,7 @@ class fr_opts(ctypes.Structure):
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("prec", ctypes.c_int),
                 ("newton_step_cap", ctypes.c_double), ("inner_cycles", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("allow_negative_density", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("temporal_depth", ctypes.c_int)]
 
 
 class fr_stats(ctypes.Structure):
