@@ -70,15 +70,27 @@ typedef struct {
     int use_graph;          /* capture repeated V-cycles in CUDA graphs; 1 */
     int temporal_depth;     /* FP32 sweeps per pass of the tiled smoother: 1 or 2;
                                0 = library default */
+    int tiling;             /* FP32 shared-memory kernels: 0 = where the grids fill the
+                               GPU, 1 = wherever possible (grids >= 16 a side), -1 = never */
+    int defect_precision;   /* mixed: arithmetic of the fine-grid defect, the update of u
+                               and the convergence test: 0 = double-float (pairs of FP32
+                               values, ~48-bit significands, on the FP32 pipes),
+                               1 = native FP64 */
 } fr_opts;
 
+#define FR_HIST 64
 typedef struct {
     int vcycles;      /* V-cycles on the finest grid (all precisions) */
-    int outer;        /* mixed: FP64 defect evaluations; FP64: 0 */
+    int outer;        /* mixed: FP64-accurate defect evaluations; FP64: 0 */
     double res0_rms;  /* rms of L(u0) */
-    double res_rms;   /* rms of L(u) on return (FP64 evaluation) */
+    double res_rms;   /* rms of L(u) on return (FP64-accurate evaluation) */
     double res_max;   /* max |L(u)| on return */
     double seconds;   /* wall time of the call */
+    int nhist;        /* entries in hist (at most FR_HIST) */
+    double hist[FR_HIST]; /* residual rms per V-cycle: FP64 mode, after each cycle;
+                             mixed, the fine residual after pre-smoothing of each
+                             FP32 cycle, and the FP64-accurate defect (negated)
+                             at each outer step */
 } fr_stats;
 
 /* Refinement patch (Sec. V.A.1, V.B.1, VI.B): a box of fine cells at twice the
@@ -180,6 +192,14 @@ int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, cons
 int fr_residual(frmg_ctx *ctx, const double *u, const double *density, const double *f,
                 const int dims[3], double h, double box_mpc_h, double a, double omega_m,
                 double fr0_abs, const double *ub, double *d, void *stream);
+
+/* d = L(u) - f (f = 0) evaluated as the mixed-precision loop evaluates its
+ * fine-grid defect: in double-float arithmetic (FP32 pairs, ~48-bit
+ * significands) from u split into a double-float pair; arguments as
+ * fr_residual.  Lets callers compare it with an FP64 evaluation. */
+int fr_residual_df(frmg_ctx *ctx, const double *u, const double *density, const int dims[3],
+                   double h, double box_mpc_h, double a, double omega_m, double fr0_abs,
+                   const double *ub, double *d, void *stream);
 
 /* coarse = average of the 8 children of each coarse cell (full weighting on a
  * cell-centred grid); fine dims even. */

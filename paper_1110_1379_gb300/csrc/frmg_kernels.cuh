@@ -40,7 +40,7 @@ template <typename T>
 struct Grid {
   T *u;            // unknown (delta in background mode), buffer 0
   T *u2;           // buffer 1: the tiled smoother reads one buffer and writes the other
-  int pad_;
+  T *x2;           // buffer 1 of the x cache (ping-pongs with u)
   T *x;            // cache: expm1(u)
   const T *f;      // right-hand side storage; f_i = fs * (f[i] - fo); null = 0
   T *uR;           // R u^h saved for the FAS correction (coarse levels)
@@ -64,12 +64,14 @@ __device__ __forceinline__ double m_exp(double v) { return exp(v); }
 // FP32 e^d - 1 used by every FP32 kernel (so all of them see the same cache
 // values): the Taylor series to degree 6 for |d| < 1/16 (truncation below
 // 1e-12 relative, which keeps small corrections exact to FP32 rounding), and
-// the SFU exponential minus one otherwise.
+// the correctly rounded-to-1-ulp exponential minus one otherwise (strongly
+// screened cells reach |u| ~ 10, where the SFU approximation's error of a few
+// ulp per unit of |u| would set the FP32 residual floor).
 __device__ __forceinline__ float m_expm1(float d) {
   if (fabsf(d) < 0.0625f)
     return d * (1.0f + d * (0.5f + d * (1.0f / 6.0f + d * (1.0f / 24.0f +
                                        d * (1.0f / 120.0f + d * (1.0f / 720.0f))))));
-  return __expf(d) - 1.0f;
+  return expf(d) - 1.0f;
 }
 __device__ __forceinline__ double m_expm1(double v) { return expm1(v); }
 __device__ __forceinline__ float m_sqrt(float v) { return sqrtf(v); }
@@ -93,7 +95,10 @@ __device__ __forceinline__ int find_grid(const int *off, int ngrid, int b) {
 template <typename T>
 __device__ __forceinline__ Grid<T> view(const Grid<T> *grids, int g, int par) {
   Grid<T> G = grids[g];
-  if (par) G.u = G.u2;
+  if (par) {
+    G.u = G.u2;
+    G.x = G.x2;
+  }
   return G;
 }
 
@@ -166,6 +171,57 @@ __device__ __forceinline__ void face_ghost(T ubf, T di, T Ei, T xi, T Bi, T ubi,
   dacc += (Bi - Bg) * w - T(2) * (Bi + Bg);
 }
 
+// Face-sum accumulator of one cell: own values at construction, one call per
+// face (regular neighbour or patch ghost), then the two sums
+//   acc  = sum_faces (flux term),   dacc = sum_faces d(flux term)/du_i.
+// The generic form adds (B_i + B_j)(u_j - u_i) face by face.  The plain FP32
+// form (the bulk of the mixed-precision work) regroups the same sum as
+//   acc  = (B_i + 1) S1 + S2,   dacc = B_i S1 - n (B_i + 1) - S3,
+//   S1 = sum (u_j - u_i),  S2 = sum x_j (u_j - u_i),  S3 = sum x_j,
+// over the n regular faces (B_j = 1 + x_j), four operations per face instead
+// of six; every FP32 kernel uses this one accumulator, so all of them evaluate
+// the same discrete operator.
+template <typename T, bool BG>
+struct OpAcc {
+  T di, Ei, xi, Bi, ubi;
+  T acc = T(0), dacc = T(0);
+  __device__ __forceinline__ OpAcc(T d, T E, T x, T B, T ub) : di(d), Ei(E), xi(x), Bi(B), ubi(ub) {}
+  __device__ __forceinline__ void reg(T dj, T xj, T ubj, T Ej) {
+    face_vals<T, BG>(dj, xj, ubj, Ej, di, Ei, xi, Bi, ubi, acc, dacc);
+  }
+  __device__ __forceinline__ void ghost(T ubf) {
+    face_ghost<T, BG>(ubf, di, Ei, xi, Bi, ubi, acc, dacc);
+  }
+  __device__ __forceinline__ void done(T &a, T &da) const {
+    a = acc;
+    da = dacc;
+  }
+};
+
+template <>
+struct OpAcc<float, false> {
+  float di, Ei, xi, Bi, ubi;
+  float S1 = 0.f, S2 = 0.f, S3 = 0.f, ga = 0.f, gd = 0.f;
+  int n = 0;
+  __device__ __forceinline__ OpAcc(float d, float E, float x, float B, float ub)
+      : di(d), Ei(E), xi(x), Bi(B), ubi(ub) {}
+  __device__ __forceinline__ void reg(float dj, float xj, float, float) {
+    const float dd = dj - di;
+    S1 += dd;
+    S2 = fmaf(xj, dd, S2);
+    S3 += xj;
+    n++;
+  }
+  __device__ __forceinline__ void ghost(float ubf) {
+    face_ghost<float, false>(ubf, di, Ei, xi, Bi, ubi, ga, gd);
+  }
+  __device__ __forceinline__ void done(float &a, float &da) const {
+    const float nf = (float)n;
+    a = fmaf(Bi + 1.0f, S1, S2) + ga;
+    da = fmaf(Bi, S1, -nf * (Bi + 1.0f)) - S3 + gd;
+  }
+};
+
 // Mass term and final assembly:  N = (alpha/2) acc + beta F (e^{-d/2} - 1),
 // dN = (alpha/2) dacc - (beta/2) F e^{-d/2},  F = e^{-ub/2}.
 // FP64 uses IEEE sqrt and division; FP32 uses the SFU reciprocal square root
@@ -200,53 +256,40 @@ __device__ __forceinline__ float newton_step(float r, float dN) { return __fdivi
 template <typename T, bool BG>
 __device__ __forceinline__ void cell_eval(const Grid<T> &G, int i, int j, int k, long long c,
                                           T &N, T &dN) {
-  T di = G.u[c];
-  T xi = G.x[c];
-  T Ei = BG ? (T)G.Ebg[c] : T(1);
-  T ubi = BG ? (T)G.ubg[c] : T(0);
-  T Bi = BG ? Ei + Ei * xi : T(1) + xi;
-  T acc = T(0), dacc = T(0);
+  const T di = G.u[c];
+  const T xi = G.x[c];
+  const T Ei = BG ? (T)G.Ebg[c] : T(1);
+  const T ubi = BG ? (T)G.ubg[c] : T(0);
+  const T Bi = BG ? Ei + Ei * xi : T(1) + xi;
+  OpAcc<T, BG> A(di, Ei, xi, Bi, ubi);
   const bool dir = G.bnd != nullptr;
   const long long sx = 1, sy = G.n0, sz = (long long)G.n0 * G.n1;
+  auto nb = [&](long long cj) {
+    A.reg(G.u[cj], G.x[cj], BG ? (T)G.ubg[cj] : T(0), BG ? (T)G.Ebg[cj] : T(1));
+  };
   // -x, +x
-  if (i > 0)
-    face_regular<T, BG>(G, c - sx, di, Ei, xi, Bi, ubi, acc, dacc);
-  else if (!dir)
-    face_regular<T, BG>(G, c + (G.n0 - 1) * sx, di, Ei, xi, Bi, ubi, acc, dacc);
-  else
-    face_ghost<T, BG>(face_value(G, 0, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
-  if (i < G.n0 - 1)
-    face_regular<T, BG>(G, c + sx, di, Ei, xi, Bi, ubi, acc, dacc);
-  else if (!dir)
-    face_regular<T, BG>(G, c - (G.n0 - 1) * sx, di, Ei, xi, Bi, ubi, acc, dacc);
-  else
-    face_ghost<T, BG>(face_value(G, 1, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
+  if (i > 0) nb(c - sx);
+  else if (!dir) nb(c + (G.n0 - 1) * sx);
+  else A.ghost(face_value(G, 0, i, j, k));
+  if (i < G.n0 - 1) nb(c + sx);
+  else if (!dir) nb(c - (G.n0 - 1) * sx);
+  else A.ghost(face_value(G, 1, i, j, k));
   // -y, +y
-  if (j > 0)
-    face_regular<T, BG>(G, c - sy, di, Ei, xi, Bi, ubi, acc, dacc);
-  else if (!dir)
-    face_regular<T, BG>(G, c + (G.n1 - 1) * sy, di, Ei, xi, Bi, ubi, acc, dacc);
-  else
-    face_ghost<T, BG>(face_value(G, 2, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
-  if (j < G.n1 - 1)
-    face_regular<T, BG>(G, c + sy, di, Ei, xi, Bi, ubi, acc, dacc);
-  else if (!dir)
-    face_regular<T, BG>(G, c - (G.n1 - 1) * sy, di, Ei, xi, Bi, ubi, acc, dacc);
-  else
-    face_ghost<T, BG>(face_value(G, 3, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
+  if (j > 0) nb(c - sy);
+  else if (!dir) nb(c + (G.n1 - 1) * sy);
+  else A.ghost(face_value(G, 2, i, j, k));
+  if (j < G.n1 - 1) nb(c + sy);
+  else if (!dir) nb(c - (G.n1 - 1) * sy);
+  else A.ghost(face_value(G, 3, i, j, k));
   // -z, +z
-  if (k > 0)
-    face_regular<T, BG>(G, c - sz, di, Ei, xi, Bi, ubi, acc, dacc);
-  else if (!dir)
-    face_regular<T, BG>(G, c + (G.n2 - 1) * sz, di, Ei, xi, Bi, ubi, acc, dacc);
-  else
-    face_ghost<T, BG>(face_value(G, 4, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
-  if (k < G.n2 - 1)
-    face_regular<T, BG>(G, c + sz, di, Ei, xi, Bi, ubi, acc, dacc);
-  else if (!dir)
-    face_regular<T, BG>(G, c - (G.n2 - 1) * sz, di, Ei, xi, Bi, ubi, acc, dacc);
-  else
-    face_ghost<T, BG>(face_value(G, 5, i, j, k), di, Ei, xi, Bi, ubi, acc, dacc);
+  if (k > 0) nb(c - sz);
+  else if (!dir) nb(c + (G.n2 - 1) * sz);
+  else A.ghost(face_value(G, 4, i, j, k));
+  if (k < G.n2 - 1) nb(c + sz);
+  else if (!dir) nb(c - (G.n2 - 1) * sz);
+  else A.ghost(face_value(G, 5, i, j, k));
+  T acc, dacc;
+  A.done(acc, dacc);
   finish_op(xi, Ei, acc, dacc, G.ah, G.beta, BG, N, dN);
 }
 
@@ -315,6 +358,36 @@ __device__ __forceinline__ void block_reduce2(double s, double m, double *out_s,
   }
 }
 
+// Block-level (sum of squares, max |v|) from FP32 per-thread values, reduced in
+// FP32 (relative error ~1e-6, ample for a stopping criterion) and written as
+// FP64 once per block: FP64 arithmetic runs at 1/64 of the FP32 rate here.
+template <int NT>
+__device__ __forceinline__ void block_reduce2f(float s, float m, double *out_s, double *out_m) {
+  __shared__ float ssf[NT / 32], smf[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  }
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    ssf[w] = s;
+    smf[w] = m;
+  }
+  __syncthreads();
+  if (w == 0) {
+    s = (l < NT / 32) ? ssf[l] : 0.0f;
+    m = (l < NT / 32) ? smf[l] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_down_sync(0xffffffffu, s, o);
+      m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    if (l == 0) {
+      *out_s = (double)s;
+      *out_m = (double)m;
+    }
+  }
+}
+
 // d = A(u) - f over every cell; optional output array and per-block partial
 // norms (partial[2*block], partial[2*block+1]).  One thread per cell.
 template <typename T, bool BG, int NT>
@@ -323,7 +396,7 @@ __global__ void __launch_bounds__(NT) k_residual(const Grid<T> *grids, const int
                                                  const int *active, int par) {
   int g = find_grid(off, ngrid, blockIdx.x);
   const Grid<T> G = view(grids, g, par);
-  double s = 0.0, m = 0.0;
+  float s = 0.0f, m = 0.0f;
   long long t = (long long)(blockIdx.x - off[g]) * NT + threadIdx.x;
   if (grid_active(active, G.field) && t < G.ncell) {
     int i = (int)(t % G.n0);
@@ -334,10 +407,11 @@ __global__ void __launch_bounds__(NT) k_residual(const Grid<T> *grids, const int
     cell_eval<T, BG>(G, i, j, k, t, N, dN);
     T d = N - rhs_at(G, t);
     if (dout && dout[g]) dout[g][t] = d;
-    s = (double)d * (double)d;
-    m = fabs((double)d);
+    const float df_ = (float)d;
+    s = df_ * df_;
+    m = fabsf(df_);
   }
-  if (partial) block_reduce2<NT>(s, m, &partial[2 * blockIdx.x], &partial[2 * blockIdx.x + 1]);
+  if (partial) block_reduce2f<NT>(s, m, &partial[2 * blockIdx.x], &partial[2 * blockIdx.x + 1]);
 }
 
 // Per-grid sums of the block partials: out[2g] = sum of squares, out[2g+1] = max.
@@ -363,7 +437,7 @@ __global__ void __launch_bounds__(256)
   int g = find_grid(off, ngrid, blockIdx.x);
   const Grid<T> F = view(fine, g, fpar);
   const Grid<T> C = view(coarse, g, cpar);
-  double ss = 0.0, mx = 0.0;
+  float ss = 0.0f, mx = 0.0f;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
   if (grid_active(active, F.field) && t < C.ncell) {
     int I = (int)(t % C.n0);
@@ -383,8 +457,9 @@ __global__ void __launch_bounds__(256)
           cell_eval<T, BG>(F, i, j, k, c, N, dN);
           T d = N - rhs_at(F, c);
           sd += d;
-          ss += (double)d * (double)d;
-          mx = fmax(mx, fabs((double)d));
+          const float df_ = (float)d;
+          ss = fmaf(df_, df_, ss);
+          mx = fmaxf(mx, fabsf(df_));
           su += F.u[c];
         }
     T uh = su * T(0.125);
@@ -394,7 +469,7 @@ __global__ void __launch_bounds__(256)
     const_cast<T *>(C.f)[t] = sd * T(0.125);
   }
   // fine-grid residual norm partials (the residual after pre-smoothing)
-  if (partial) block_reduce2<256>(ss, mx, &partial[2 * blockIdx.x], &partial[2 * blockIdx.x + 1]);
+  if (partial) block_reduce2f<256>(ss, mx, &partial[2 * blockIdx.x], &partial[2 * blockIdx.x + 1]);
 }
 
 // f^H = A^H(R u^h) - R d^h, in place over the R d^h stored in f (fs = 1, fo = 0).
@@ -436,7 +511,7 @@ __global__ void __launch_bounds__(256) k_prolong(const Grid<T> *fine, const Grid
   const T *__restrict__ uH = cpar ? Cg.u2 : Cg.u;
   const T *__restrict__ uR = Cg.uR;
   T *__restrict__ uf = fpar ? Fg.u2 : Fg.u;
-  T *__restrict__ xf = Fg.x;
+  T *__restrict__ xf = fpar ? Fg.x2 : Fg.x;
   const bool dir = Fg.bnd != nullptr;
   const int I = (int)(t % c0);
   long long r = t / c0;
@@ -618,7 +693,7 @@ __device__ __forceinline__ int wrapmod(int v, int n) {
 // Halo cells are updated redundantly by neighbouring blocks from identical
 // inputs; a pass reads the current buffer and writes the other one (blocks
 // load their halos from the unmodified input), which makes the result equal to
-// S sweeps of k_smooth.
+// S sweeps of k_smooth.  The x = expm1(u) cache ping-pongs with u.
 //
 // Each thread owns one x-pair in each of RPT rows (LY/RPT rows apart) for the
 // whole pass: it loads and stores its pairs with 8-byte accesses (x-pairs
@@ -626,12 +701,11 @@ __device__ __forceinline__ int wrapmod(int v, int n) {
 // seam), and at every stage it updates, in each of its rows, the one cell of
 // its pair that has the stage's colour if that cell lies in the stage's
 // region; the RPT updates are independent, which gives the scheduler
-// instruction-level parallelism.  x = expm1(u) is recomputed from u on load
-// and written in place for the kernels that follow; the right-hand side is
-// kept in shared memory with the plane.  The global loads of plane p+1 are
+// instruction-level parallelism.  The right-hand side is kept in shared memory
+// with the plane.  The global loads of plane p+1 are
 // issued into registers before the stages of step p and stored to shared
 // memory after them.
-template <bool BG, int S, int TX, int TY>
+template <bool BG, bool DIR, int S, int TX, int TY>
 __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
     k_smooth_tiled(const Grid<float> *grids, const int *off, int ngrid, int zc, const int *active,
                    int par) {
@@ -649,13 +723,14 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
   if (!grid_active(active, Gg.field)) return;
   const float *__restrict__ uin = par ? Gg.u2 : Gg.u;
   float *__restrict__ uout = par ? Gg.u : Gg.u2;
-  float *__restrict__ xout = Gg.x;
+  const float *__restrict__ xin = par ? Gg.x2 : Gg.x;
+  float *__restrict__ xout = par ? Gg.x : Gg.x2;
   const float *__restrict__ fin = Gg.f;
   const float *__restrict__ ubin = Gg.ubg;
   const float *__restrict__ Ein = Gg.Ebg;
   const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap;
   const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
-  const bool dir = Gg.bnd != nullptr;
+  constexpr bool dir = DIR;  // patch (Dirichlet faces) or periodic grid
   const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
   int b = blockIdx.x - off[g];
   const int X0 = (b % ntx) * TX;
@@ -689,10 +764,11 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
                 gx0 < n0 && gy[r] < n1;
   }
 
-  float2 pd[RPT], pf[RPT], pu[RPT], pE[RPT];
+  float2 pd[RPT], px[RPT], pf[RPT], pu[RPT], pE[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; r++) {
     pd[r] = make_float2(0.f, 0.f);
+    px[r] = pd[r];
     pf[r] = pd[r];
     pu[r] = pd[r];
     pE[r] = make_float2(1.f, 1.f);
@@ -705,6 +781,7 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
       if (!mine[r]) continue;
       const long long gi = (zo + gyw[r]) * n0 + gxw0;
       pd[r] = *reinterpret_cast<const float2 *>(uin + gi);
+      px[r] = *reinterpret_cast<const float2 *>(xin + gi);
       if (fin) {
         const float2 fv = *reinterpret_cast<const float2 *>(fin + gi);
         pf[r] = make_float2(fs * (fv.x - fo), fs * (fv.y - fo));
@@ -722,8 +799,8 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
       const int o = base + rowo[r];
       sd[o] = pd[r].x;
       sd[o + 1] = pd[r].y;
-      sx[o] = m_expm1(pd[r].x);
-      sx[o + 1] = m_expm1(pd[r].y);
+      sx[o] = px[r].x;
+      sx[o + 1] = px[r].y;
       sf[o] = pf[r].x;
       sf[o + 1] = pf[r].y;
       if (BG) {
@@ -752,36 +829,36 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
       const float Ei = BG ? sE[o] : 1.0f;
       const float ubi = BG ? sub[o] : 0.0f;
       const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
-      float acc = 0.0f, dacc = 0.0f;
+      OpAcc<float, BG> A(di, Ei, xi, Bi, ubi);
       const int gxw = gxw0 + par01, gyr = gyw[r];
-#define FR_NB(OFF)                                                                          \
-  face_vals<float, BG>(sd[OFF], sx[OFF], BG ? sub[OFF] : 0.0f, BG ? sE[OFF] : 1.0f, di, Ei, \
-                       xi, Bi, ubi, acc, dacc)
+#define FR_NB(OFF) A.reg(sd[OFF], sx[OFF], BG ? sub[OFF] : 0.0f, BG ? sE[OFF] : 1.0f)
       if (dir && gxw == 0)
-        face_ghost<float, BG>(face_value(Gg, 0, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+        A.ghost(face_value(Gg, 0, gxw, gyr, m));
       else
         FR_NB(o - 1);
       if (dir && gxw == n0 - 1)
-        face_ghost<float, BG>(face_value(Gg, 1, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+        A.ghost(face_value(Gg, 1, gxw, gyr, m));
       else
         FR_NB(o + 1);
       if (dir && gyr == 0)
-        face_ghost<float, BG>(face_value(Gg, 2, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+        A.ghost(face_value(Gg, 2, gxw, gyr, m));
       else
         FR_NB(o - LX);
       if (dir && gyr == n1 - 1)
-        face_ghost<float, BG>(face_value(Gg, 3, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+        A.ghost(face_value(Gg, 3, gxw, gyr, m));
       else
         FR_NB(o + LX);
       if (dir && m == 0)
-        face_ghost<float, BG>(face_value(Gg, 4, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+        A.ghost(face_value(Gg, 4, gxw, gyr, m));
       else
         FR_NB(slm * PL + li);
       if (dir && m == n2 - 1)
-        face_ghost<float, BG>(face_value(Gg, 5, gxw, gyr, m), di, Ei, xi, Bi, ubi, acc, dacc);
+        A.ghost(face_value(Gg, 5, gxw, gyr, m));
       else
         FR_NB(slp * PL + li);
 #undef FR_NB
+      float acc, dacc;
+      A.done(acc, dacc);
       float N, dN;
       finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
       float du = newton_step(N - sf[o], dN);
@@ -818,6 +895,199 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
     if (more) commit(p + 1);
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled FP32 residual + restriction (same result as k_resid_restrict).
+// A block owns a TX x TY fine tile and an even chunk of zc fine planes, marches
+// along z with a ring of 4 planes (tile plus a halo of 2 cells in x, so that
+// 8-byte x-pairs stay aligned, and 1 in y) in shared memory, and each thread
+// owns one coarse column of the tile: per fine plane it evaluates the residual
+// of its 2x2 fine cells from shared memory, and after every second plane it
+// writes its coarse cell (u^H = uR = mean u^h, x^H = expm1(u^H),
+// f^H <- mean d^h) and accumulates the fine residual norm.  Plane m+2 is
+// fetched into registers while plane m is evaluated.
+template <int TX, int TY>
+struct RRCfg {
+  static constexpr int LX = TX + 4, LY = TY + 2, PL = LX * LY, NS = 4;
+  static constexpr int PXR = LX / 2, NPAIR = PXR * LY;
+  static constexpr int CX = TX / 2, NT = (TX / 2) * (TY / 2);
+  static constexpr int K = (NPAIR + NT - 1) / NT;
+  static constexpr size_t smem(bool bg) { return (size_t)NS * PL * sizeof(float) * (bg ? 5 : 3); }
+};
+
+template <bool BG, bool DIR, int TX, int TY>
+__global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
+    k_resid_restrict_tiled(const Grid<float> *fine, const Grid<float> *coarse, const int *off,
+                           int ngrid, int zc, const int *active, int fpar, int cpar,
+                           double *partial) {
+  using C = RRCfg<TX, TY>;
+  constexpr int LX = C::LX, PL = C::PL, NS = C::NS, NT = C::NT, CX = C::CX;
+  constexpr int PXR = C::PXR, NPAIR = C::NPAIR, K = C::K;
+  extern __shared__ float smem[];
+  float *sd = smem;
+  float *sx = smem + NS * PL;
+  float *sf = smem + 2 * NS * PL;
+  float *sub = smem + 3 * NS * PL;
+  float *sE = smem + 4 * NS * PL;
+  const int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<float> &Fg = fine[g];
+  const Grid<float> &Cg = coarse[g];
+  float ss = 0.0f, mx = 0.0f;
+  if (grid_active(active, Fg.field)) {
+    const float *__restrict__ uin = fpar ? Fg.u2 : Fg.u;
+    const float *__restrict__ xin = fpar ? Fg.x2 : Fg.x;
+    const float *__restrict__ fin = Fg.f;
+    const float *__restrict__ ubin = Fg.ubg;
+    const float *__restrict__ Ein = Fg.Ebg;
+    const float fs = Fg.fs, fo = Fg.fo, ah = Fg.ah, beta = Fg.beta;
+    const int n0 = Fg.n0, n1 = Fg.n1, n2 = Fg.n2;
+    const int c0 = Cg.n0, c1 = Cg.n1;
+    float *__restrict__ cu = cpar ? Cg.u2 : Cg.u;
+    float *__restrict__ cR = Cg.uR;
+    float *__restrict__ cx = cpar ? Cg.x2 : Cg.x;
+    float *__restrict__ cf = const_cast<float *>(Cg.f);
+    const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
+    int b = blockIdx.x - off[g];
+    const int X0 = (b % ntx) * TX;
+    b /= ntx;
+    const int Y0 = (b % nty) * TY;
+    b /= nty;
+    const int Z0 = b * zc;
+    const int Z1 = min(Z0 + zc, n2);
+    // the pairs this thread loads: global pair start (wrapped) per slot, -1 if none
+    long long pg[K];
+    int po[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      const int c = threadIdx.x + k * NT;
+      pg[k] = -1;
+      po[k] = 0;
+      if (c < NPAIR) {
+        const int yy = c / PXR, px = c - yy * PXR;
+        int gxx = X0 - 2 + 2 * px, gyy = Y0 - 1 + yy;
+        po[k] = yy * LX + 2 * px;
+        bool in = true;
+        if (DIR) {
+          in = gxx >= 0 && gxx < n0 && gyy >= 0 && gyy < n1;
+        } else {
+          gxx = gxx < 0 ? gxx + n0 : (gxx >= n0 ? gxx - n0 : gxx);
+          gyy = wrapmod(gyy, n1);
+        }
+        if (in) pg[k] = (long long)gyy * n0 + gxx;
+      }
+    }
+    float2 rd[K], rx[K], rf[K], ru[K], rE[K];
+    auto fetch = [&](int p) {
+      if (DIR && (p < 0 || p >= n2)) return;
+      const long long zo = (long long)wrapmod(p, n2) * n1 * n0;
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        if (pg[k] < 0) continue;
+        const long long gi = zo + pg[k];
+        rd[k] = *reinterpret_cast<const float2 *>(uin + gi);
+        rx[k] = *reinterpret_cast<const float2 *>(xin + gi);
+        if (fin) {
+          const float2 fv = *reinterpret_cast<const float2 *>(fin + gi);
+          rf[k] = make_float2(fs * (fv.x - fo), fs * (fv.y - fo));
+        } else {
+          rf[k] = make_float2(0.f, 0.f);
+        }
+        if (BG) {
+          ru[k] = *reinterpret_cast<const float2 *>(ubin + gi);
+          rE[k] = *reinterpret_cast<const float2 *>(Ein + gi);
+        }
+      }
+    };
+    auto commit = [&](int p) {
+      if (DIR && (p < 0 || p >= n2)) return;
+      const int base = wrapmod(p, NS) * PL;
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        if (pg[k] < 0) continue;
+        const int o = base + po[k];
+        sd[o] = rd[k].x;
+        sd[o + 1] = rd[k].y;
+        sx[o] = rx[k].x;
+        sx[o + 1] = rx[k].y;
+        sf[o] = rf[k].x;
+        sf[o + 1] = rf[k].y;
+        if (BG) {
+          sub[o] = ru[k].x;
+          sub[o + 1] = ru[k].y;
+          sE[o] = rE[k].x;
+          sE[o + 1] = rE[k].y;
+        }
+      }
+    };
+    const int ci = threadIdx.x % CX, cj = threadIdx.x / CX;
+    const int lx = 2 + 2 * ci, ly = 1 + 2 * cj;
+    const int gx = X0 + 2 * ci, gy = Y0 + 2 * cj;
+    const bool valid = gx < n0 && gy < n1;
+    float su = 0.f, sdd = 0.f;
+    fetch(Z0 - 1);
+    commit(Z0 - 1);
+    fetch(Z0);
+    commit(Z0);
+    fetch(Z0 + 1);
+    commit(Z0 + 1);
+    __syncthreads();
+    for (int m = Z0; m < Z1; m++) {
+      const bool more = m + 2 <= Z1;
+      if (more) fetch(m + 2);
+      if (valid) {
+        const int sl = wrapmod(m, NS), slm = wrapmod(m - 1, NS), slp = wrapmod(m + 1, NS);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int ax = q & 1, ay = q >> 1;
+          const int li = (ly + ay) * LX + lx + ax;
+          const int o = sl * PL + li;
+          const int gxq = gx + ax, gyq = gy + ay;
+          const float di = sd[o], xi = sx[o];
+          const float Ei = BG ? sE[o] : 1.0f;
+          const float ubi = BG ? sub[o] : 0.0f;
+          const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
+          OpAcc<float, BG> A(di, Ei, xi, Bi, ubi);
+#define FR_NB(OFF) A.reg(sd[OFF], sx[OFF], BG ? sub[OFF] : 0.0f, BG ? sE[OFF] : 1.0f)
+          if (DIR && gxq == 0) A.ghost(face_value(Fg, 0, gxq, gyq, m));
+          else FR_NB(o - 1);
+          if (DIR && gxq == n0 - 1) A.ghost(face_value(Fg, 1, gxq, gyq, m));
+          else FR_NB(o + 1);
+          if (DIR && gyq == 0) A.ghost(face_value(Fg, 2, gxq, gyq, m));
+          else FR_NB(o - LX);
+          if (DIR && gyq == n1 - 1) A.ghost(face_value(Fg, 3, gxq, gyq, m));
+          else FR_NB(o + LX);
+          if (DIR && m == 0) A.ghost(face_value(Fg, 4, gxq, gyq, m));
+          else FR_NB(slm * PL + li);
+          if (DIR && m == n2 - 1) A.ghost(face_value(Fg, 5, gxq, gyq, m));
+          else FR_NB(slp * PL + li);
+#undef FR_NB
+          float acc, dacc, N, dN;
+          A.done(acc, dacc);
+          finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
+          const float d = N - sf[o];
+          sdd += d;
+          su += di;
+          ss = fmaf(d, d, ss);
+          mx = fmaxf(mx, fabsf(d));
+        }
+        if ((m - Z0) & 1) {
+          const long long cidx = ((long long)(m >> 1) * c1 + (gy >> 1)) * c0 + (gx >> 1);
+          const float uh = su * 0.125f;
+          cR[cidx] = uh;
+          cu[cidx] = uh;
+          cx[cidx] = m_expm1(uh);
+          cf[cidx] = sdd * 0.125f;
+          su = 0.f;
+          sdd = 0.f;
+        }
+      }
+      // plane m+2 goes into the slot of plane m-2, which iteration m does not read
+      if (more) commit(m + 2);
+      __syncthreads();
+    }
+  }
+  if (partial) block_reduce2f<NT>(ss, mx, &partial[2 * blockIdx.x], &partial[2 * blockIdx.x + 1]);
 }
 
 }  // namespace frmg

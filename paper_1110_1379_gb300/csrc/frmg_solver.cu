@@ -30,6 +30,7 @@
 #include "frmg.h"
 #include "frmg_internal.h"
 #include "frmg_kernels.cuh"
+#include "frmg_df.cuh"
 
 using namespace frmg;
 
@@ -314,16 +315,16 @@ __global__ void __launch_bounds__(256) k_prep_zero(const double *rho, double gam
                                                    float *u32, float *x32, long long n,
                                                    double *partial, int base) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double s = 0.0, m = 0.0;
+  float s = 0.0f, m = 0.0f;
   if (t < n) {
-    double r = gamma * (rho[t] - 1.0);
-    r32[t] = (float)r;
+    float r = (float)(gamma * (rho[t] - 1.0));
+    r32[t] = r;
     u32[t] = 0.0f;
     x32[t] = 0.0f;
     s = r * r;
-    m = fabs(r);
+    m = fabsf(r);
   }
-  block_reduce2<256>(s, m, &partial[2 * (base + blockIdx.x)], &partial[2 * (base + blockIdx.x) + 1]);
+  block_reduce2f<256>(s, m, &partial[2 * (base + blockIdx.x)], &partial[2 * (base + blockIdx.x) + 1]);
 }
 
 __global__ void k_any_nonzero(const double *u, long long n, int *flag) {
@@ -396,10 +397,17 @@ struct LevelSet {
   // tiled FP32 smoother: blocks per grid for TX x TY tiles and zc-plane chunks
   bool tiled = false;     // the tiled smoother is used for this set
   bool tiled_ok = false;  // it could be used (every grid >= 16 cells a side)
+  bool dirichlet = false; // patches (all grids of a set are patches or all periodic)
   int zc = 0;
   std::vector<int> off_tile;
   int *d_off_tile = nullptr;
   int nblk_tile = 0;
+  // tiled residual + restriction (fine side of a V-cycle level)
+  bool rr_tiled = false;
+  int zc_rr = 0;
+  std::vector<int> off_rr;
+  int *d_off_rr = nullptr;
+  int nblk_rr = 0;
   double *partial = nullptr;  // per-block norm partials
   double *red = nullptr;      // per-grid (sum of squares, max)
   T **d_dout = nullptr;       // per-grid residual output pointers
@@ -408,7 +416,7 @@ struct LevelSet {
 };
 
 template <typename T>
-static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st) {
+static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 0) {
   if (ls.empty()) return;
   int ng = ls.size();
   ls.off_half.assign(ng + 1, 0);
@@ -428,6 +436,10 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st) {
                      cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ls.d_off_full, ls.off_full.data(), (ng + 1) * sizeof(int),
                      cudaMemcpyHostToDevice, st));
+  ls.dirichlet = ls.h[0].bnd != nullptr;
+  for (int g = 1; g < ng; g++)
+    if ((ls.h[g].bnd != nullptr) != ls.dirichlet)
+      throw FrError{FR_EINVAL, "a level set mixes patches and periodic grids"};
   // tiled smoother for FP32 sets whose grids are all at least 16 cells a side
   ls.tiled = sizeof(T) == 4;
   int maxn2 = 0;
@@ -445,7 +457,8 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st) {
     long long nz = std::max<long long>(1, (1216 + txy - 1) / txy);
     ls.zc = (int)std::max<long long>(std::min(32, maxn2), (maxn2 + nz - 1) / nz);
     ls.tiled_ok = true;
-    if (txy * ((maxn2 + ls.zc - 1) / ls.zc) < 304) ls.tiled = false;
+    if (tiling == 0 && txy * ((maxn2 + ls.zc - 1) / ls.zc) < 304) ls.tiled = false;
+    if (tiling < 0) ls.tiled = false;
   }
   if (ls.tiled_ok) {
     ls.off_tile.assign(ng + 1, 0);
@@ -459,7 +472,25 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st) {
     CK(cudaMemcpyAsync(ls.d_off_tile, ls.off_tile.data(), (ng + 1) * sizeof(int),
                        cudaMemcpyHostToDevice, st));
   }
-  ls.partial = S.get<double>(2 * (size_t)ls.nblk_full);
+  if (ls.tiled) {
+    // tiled residual + restriction: even z-chunks (coarse planes stay whole)
+    long long nz = std::max<long long>(1, (1216 + txy - 1) / txy);
+    int zc = (int)std::max<long long>(std::min(32, maxn2), (maxn2 + nz - 1) / nz);
+    ls.zc_rr = (zc + 1) & ~1;
+    ls.off_rr.assign(ng + 1, 0);
+    for (int g = 0; g < ng; g++) {
+      const Grid<T> &G = ls.h[g];
+      int nt = ((G.n0 + kTX - 1) / kTX) * ((G.n1 + kTY - 1) / kTY) *
+               ((G.n2 + ls.zc_rr - 1) / ls.zc_rr);
+      ls.off_rr[g + 1] = ls.off_rr[g] + nt;
+    }
+    ls.nblk_rr = ls.off_rr[ng];
+    ls.d_off_rr = S.get<int>(ng + 1);
+    CK(cudaMemcpyAsync(ls.d_off_rr, ls.off_rr.data(), (ng + 1) * sizeof(int),
+                       cudaMemcpyHostToDevice, st));
+    ls.rr_tiled = true;
+  }
+  ls.partial = S.get<double>(2 * (size_t)std::max(ls.nblk_full, ls.nblk_rr));
   ls.red = S.get<double>(2 * (size_t)ng);
   ls.d_dout = S.get<T *>(ng);
   // host vectors must stay alive until the copies finished
@@ -476,11 +507,12 @@ struct Hier {
   std::vector<float *> bg_u, bg_E;        // fine-level background arrays per problem
   std::vector<int> par;                   // current u buffer (0/1) per depth
   T *cur_u(int pi, int l) const { return par[l] ? lev[pi][l].u2 : lev[pi][l].u; }
+  T *cur_x(int pi, int l) const { return par[l] ? lev[pi][l].x2 : lev[pi][l].x; }
 };
 
 template <typename T, bool BG>
 static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap,
-                       cudaStream_t st, frmg_ctx *ctx) {
+                       cudaStream_t st, frmg_ctx *ctx, int tiling = 0) {
   int np = (int)P.size();
   H.lev.assign(np, {});
   H.depth = 0;
@@ -519,7 +551,10 @@ static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap
         G.fo = T(0);
       }
       G.x = S.get<T>(G.ncell);
-      if (sizeof(T) == 4) G.u2 = S.get<T>(G.ncell);
+      if (sizeof(T) == 4) {
+        G.u2 = S.get<T>(G.ncell);
+        G.x2 = S.get<T>(G.ncell);
+      }
       if (l > 0) G.uR = S.get<T>(G.ncell);
       if (BG) {
         float *ub = S.get<float>(G.ncell);
@@ -572,10 +607,10 @@ static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap
     }
   }
   for (int l = 0; l < H.depth; l++) {
-    upload_set(S, H.cont[l], st);
-    upload_set(S, H.next[l], st);
-    upload_set(S, H.coarsest[l], st);
-    upload_set(S, H.all[l], st);
+    upload_set(S, H.cont[l], st, tiling);
+    upload_set(S, H.next[l], st, tiling);
+    upload_set(S, H.coarsest[l], st, tiling);
+    upload_set(S, H.all[l], st, tiling);
   }
 }
 
@@ -605,19 +640,53 @@ static const char *pname(const char *kind, bool f64, bool fine) {
   return tab[row][(f64 ? 0 : 2) + (fine ? 0 : 1)];
 }
 
-template <bool BG, int S>
-static void launch_tiled(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
-                         cudaStream_t st) {
+template <bool BG, bool DIR, int S>
+static void launch_tiled_k(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
+                           cudaStream_t st) {
   using TC = TileCfg<S, kTX, kTY>;
   size_t sm = TC::smem(BG);
   static bool attr_set = false;
   if (!attr_set) {
-    CK(cudaFuncSetAttribute(k_smooth_tiled<BG, S, kTX, kTY>,
+    CK(cudaFuncSetAttribute(k_smooth_tiled<BG, DIR, S, kTX, kTY>,
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
-  k_smooth_tiled<BG, S, kTX, kTY><<<s.nblk_tile, TC::NT, sm, st>>>(s.d, s.d_off_tile, s.size(),
-                                                                   s.zc, active, par);
+  k_smooth_tiled<BG, DIR, S, kTX, kTY><<<s.nblk_tile, TC::NT, sm, st>>>(s.d, s.d_off_tile,
+                                                                        s.size(), s.zc, active, par);
+}
+
+template <bool BG, bool DIR>
+static void launch_rr_k(frmg_ctx *ctx, LevelSet<float> &F, LevelSet<float> &C, const int *active,
+                        int fpar, int cpar, double *partial, cudaStream_t st) {
+  using RC = RRCfg<kTX, kTY>;
+  size_t sm = RC::smem(BG);
+  static bool attr_set = false;
+  if (!attr_set) {
+    CK(cudaFuncSetAttribute(k_resid_restrict_tiled<BG, DIR, kTX, kTY>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_set = true;
+  }
+  k_resid_restrict_tiled<BG, DIR, kTX, kTY><<<F.nblk_rr, RC::NT, sm, st>>>(
+      F.d, C.d, F.d_off_rr, F.size(), F.zc_rr, active, fpar, cpar, partial);
+}
+
+template <bool BG>
+static void launch_rr_tiled(frmg_ctx *ctx, LevelSet<float> &F, LevelSet<float> &C,
+                            const int *active, int fpar, int cpar, double *partial,
+                            cudaStream_t st) {
+  if (F.dirichlet)
+    launch_rr_k<BG, true>(ctx, F, C, active, fpar, cpar, partial, st);
+  else
+    launch_rr_k<BG, false>(ctx, F, C, active, fpar, cpar, partial, st);
+}
+
+template <bool BG, int S>
+static void launch_tiled(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
+                         cudaStream_t st) {
+  if (s.dirichlet)
+    launch_tiled_k<BG, true, S>(ctx, s, active, par, st);
+  else
+    launch_tiled_k<BG, false, S>(ctx, s, active, par, st);
 }
 
 // Passes of the tiled smoother (sweeps per pass) for the pre- and post-smoothing
@@ -696,9 +765,20 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
   smooth_set<T, BG>(ctx, F, o.pre, even ? &plan_pre : nullptr, active, H.par[l], st, l == 0);
   {
     PROF(pname("resid_restrict", sizeof(T) == 8, l == 0));
-    k_resid_restrict<T, BG><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, C.size(),
-                                                         active, H.par[l], H.par[l + 1],
-                                                         l == 0 ? C.partial : nullptr);
+    if constexpr (sizeof(T) == 4) {
+      if (F.rr_tiled) {
+        launch_rr_tiled<BG>(ctx, F, C, active, H.par[l], H.par[l + 1],
+                            l == 0 ? C.partial : nullptr, st);
+      } else {
+        k_resid_restrict<T, BG><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, C.size(),
+                                                             active, H.par[l], H.par[l + 1],
+                                                             l == 0 ? C.partial : nullptr);
+      }
+    } else {
+      k_resid_restrict<T, BG><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, C.size(),
+                                                           active, H.par[l], H.par[l + 1],
+                                                           l == 0 ? C.partial : nullptr);
+    }
     CK_LAUNCH(ctx);
   }
   {
@@ -755,7 +835,8 @@ static void fused_fine_norms(frmg_ctx *ctx, Hier<T> &H, int np, cudaStream_t st,
   LevelSet<T> &C = H.next[0];
   if (C.empty()) return;
   int ng = C.size();
-  k_reduce_partials<<<ng, 256, 0, st>>>(C.partial, C.d_off_full, ng, C.red);
+  const int *offs = H.cont[0].rr_tiled ? H.cont[0].d_off_rr : C.d_off_full;
+  k_reduce_partials<<<ng, 256, 0, st>>>(C.partial, offs, ng, C.red);
   CK_LAUNCH(ctx);
   double *hp = pinned_buf(ctx, 2 * (size_t)ng);
   CK(cudaMemcpyAsync(hp, C.red, 2 * ng * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -776,9 +857,15 @@ struct SolveCfg {
   int inner_cycles, max_outer;
   int fixed_cycles;  // > 0: exactly this many (FP64 only), no convergence test
   int tdepth;
+  int tiling;
+  int defect_fp64;   // mixed: 1 = native FP64 defect/update, 0 = double-float
 };
 
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
+
+static void hist_push(fr_stats &s, double v) {
+  if (s.nhist < FR_HIST) s.hist[s.nhist++] = v;
+}
 
 // Plain FP64: V-cycles until every problem has rms <= tol.
 static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &cfg,
@@ -821,6 +908,7 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
       stats[pi].vcycles++;
       stats[pi].res_rms = nr[2 * pi];
       stats[pi].res_max = nr[2 * pi + 1];
+      hist_push(stats[pi], nr[2 * pi]);
       if (bad(nr[2 * pi])) throw FrError{FR_EDIVERGED, "non-finite residual"};
       grow[pi] = nr[2 * pi] > prev[pi] ? grow[pi] + 1 : 0;
       if (grow[pi] >= 5) throw FrError{FR_EDIVERGED, "residual grew for 5 cycles"};
@@ -845,7 +933,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
   for (auto &p : P1) p.nl = 1;
   build_hier<double, false>(S, H64, P1, cfg.cap, st, ctx);
   Hier<float> H;
-  build_hier<float, true>(S, H, P, cfg.cap, st, ctx);
+  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling);
   std::vector<double *> d64(np);
   int *flag = S.get<int>(1);
   CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
@@ -878,8 +966,14 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
     }
   };
   // inner V-cycles with the fused fine-residual norm as the stopping signal
+  // Stopping signal: the fine residual after pre-smoothing of each cycle (fused
+  // into the residual + restriction kernel).  Successive values are compared
+  // (the first cycle always runs); a ratio above 0.75 means FP32 rounding has
+  // taken over.  A correction solve stops once the residual at the end of the
+  // cycle, predicted as mid * sqrt(mid / previous mid) (the rest of the cycle
+  // does about half of a cycle's contraction), is below 0.7 tol.
   auto inner = [&](bool bg, const std::vector<double> &r0, double floor_rel, int kmax) {
-    std::vector<double> rp = r0;
+    std::vector<double> rp(np, HUGE_VAL);
     for (int k = 0; k < kmax; k++) {
       if (bg)
         vcycle<float, true>(ctx, H, 0, co, active, st);
@@ -898,7 +992,10 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
         if (!act[pi]) continue;
         double r = inr[pi];
         if (!(r == r)) continue;  // single-level grid: one coarsest solve per cycle
-        if (r < 0.5 * rp[pi] && r > floor_rel * r0[pi] && r > 0.3 * cfg.tol) go = true;
+        hist_push(stats[pi], r);
+        const double pred = rp[pi] < HUGE_VAL ? r * std::sqrt(r / rp[pi]) : r;
+        if (r < 0.75 * rp[pi] && r > floor_rel * r0[pi] && pred > (bg ? 0.7 : 0.3) * cfg.tol)
+          go = true;
         rp[pi] = r;
       }
       if (!go) break;
@@ -913,7 +1010,8 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
       LevelSet<double> &A0 = H64.all[0];
       k_prep_zero<<<nblocks(G.ncell), 256, 0, st>>>(G64.f, P[pi].k.gamma,
                                                     const_cast<float *>(G.f), H.cur_u(pi, 0),
-                                                    G.x, G.ncell, A0.partial, A0.off_full[pi]);
+                                                    H.cur_x(pi, 0), G.ncell, A0.partial,
+                                                    A0.off_full[pi]);
       CK_LAUNCH(ctx);
     }
     CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -930,7 +1028,8 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
         stats[pi].res0_rms = r0[pi];
       }
     }
-    inner(false, r0, 1e-7, 40);
+    // stop well above the FP32 rounding floor; the correction solves finish
+    inner(false, r0, 1e-4, 40);
     update();
   } else {
     for (int pi = 0; pi < np; pi++) {
@@ -974,7 +1073,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
         PROF("prep_inner");
         k_prep_inner<<<nblocks(G.ncell), 256, 0, st>>>(d64[pi], G64.u, const_cast<float *>(G.f),
                                                        H.bg_u[pi], H.bg_E[pi], H.cur_u(pi, 0),
-                                                       G.x, G.ncell);
+                                                       H.cur_x(pi, 0), G.ncell);
         CK_LAUNCH(ctx);
       }
       for (size_t l = 1; l < H.lev[pi].size(); l++) {
@@ -990,6 +1089,233 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
     inner(true, r0, 1e-6, std::max(cfg.inner_cycles, 12));
     update();
   }
+}
+
+// Zero-start set-up of the double-float loop: the FP32 right-hand side is the
+// high part of gamma (rho - 1); block partials of its norm as k_prep_zero.
+__global__ void __launch_bounds__(256) k_prep_zero_df(const float *rh, float *r32, float *u32,
+                                                      float *x32, long long n, double *partial,
+                                                      int base) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float s = 0.0f, m = 0.0f;
+  if (t < n) {
+    float r = rh[t];
+    r32[t] = r;
+    u32[t] = 0.0f;
+    x32[t] = 0.0f;
+    s = r * r;
+    m = fabsf(r);
+  }
+  block_reduce2f<256>(s, m, &partial[2 * (base + blockIdx.x)], &partial[2 * (base + blockIdx.x) + 1]);
+}
+
+static void split_host(double v, float &h, float &l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+// Mixed precision with the FP64-accurate quantities in double-float (see
+// frmg_df.cuh): the same outer loop as solve_mixed, with the defect, the
+// update and the convergence test evaluated on FP32 pipes at ~48-bit accuracy.
+static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &cfg,
+                           std::vector<fr_stats> &stats, cudaStream_t st) {
+  Scope S(ctx);
+  const int np = (int)P.size();
+  Hier<float> H;
+  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling);
+  const double ln2 = std::log(2.0);
+  float ln2h, ln2l;
+  split_host(ln2, ln2h, ln2l);
+  std::vector<DFGrid> D(np);
+  std::vector<int> boff(np + 1, 0);
+  for (int pi = 0; pi < np; pi++) {
+    DFGrid &g = D[pi];
+    memset(&g, 0, sizeof(g));
+    g.n0 = P[pi].n[0];
+    g.n1 = P[pi].n[1];
+    g.n2 = P[pi].n[2];
+    g.ncell = (long long)g.n0 * g.n1 * g.n2;
+    g.uh = S.get<float>(g.ncell);
+    g.ul = S.get<float>(g.ncell);
+    g.Bh = S.get<float>(g.ncell);
+    g.Bl = S.get<float>(g.ncell);
+    g.rh = S.get<float>(g.ncell);
+    g.rl = S.get<float>(g.ncell);
+    g.bnd = P[pi].bnd;
+    face_offsets(P[pi].n, g.foff);
+    split_host(0.5 * P[pi].k.alpha, g.ahh, g.ahl);
+    split_host(P[pi].k.beta, g.beh, g.bel);
+    boff[pi + 1] = boff[pi] + nblocks(g.ncell);
+  }
+  double *partial = S.get<double>(2 * (size_t)boff[np]);
+  double *red = S.get<double>(2 * (size_t)np);
+  int *d_boff = S.get<int>(np + 1);
+  CK(cudaMemcpyAsync(d_boff, boff.data(), (np + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  int *flag = S.get<int>(1);
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  for (int pi = 0; pi < np; pi++) {
+    k_any_nonzero<<<nblocks(D[pi].ncell), 256, 0, st>>>(P[pi].u, D[pi].ncell, flag);
+    CK_LAUNCH(ctx);
+  }
+  int nonzero = 0;
+  CK(cudaMemcpyAsync(&nonzero, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int pi = 0; pi < np; pi++) {
+    PROF("df_init");
+    k_df_init<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], P[pi].u, P[pi].rho, P[pi].k.gamma,
+                                                    !nonzero, ln2h, ln2l);
+    CK_LAUNCH(ctx);
+  }
+  auto read_norms = [&](std::vector<double> &out) {
+    k_reduce_partials<<<np, 256, 0, st>>>(partial, d_boff, np, red);
+    CK_LAUNCH(ctx);
+    double *hp = pinned_buf(ctx, 2 * (size_t)np);
+    CK(cudaMemcpyAsync(hp, red, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    prof_harvest(ctx);
+    out.assign(2 * np, 0.0);
+    for (int pi = 0; pi < np; pi++) {
+      out[2 * pi] = std::sqrt(hp[2 * pi] / (double)D[pi].ncell);
+      out[2 * pi + 1] = hp[2 * pi + 1];
+    }
+  };
+  auto finalize = [&]() {
+    for (int pi = 0; pi < np; pi++) {
+      k_df_final<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], P[pi].u);
+      CK_LAUNCH(ctx);
+    }
+  };
+  int *active = S.get<int>(np);
+  std::vector<int> act(np, 1);
+  CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.0, 500, 1};
+  std::vector<double> nr, inr;
+  std::vector<double> prev(np, 0.0);
+  std::vector<int> grow(np, 0);
+  for (int pi = 0; pi < np; pi++) {
+    stats[pi].vcycles = 0;
+    stats[pi].outer = 0;
+  }
+  auto update = [&]() {
+    for (int pi = 0; pi < np; pi++) {
+      if (!act[pi]) continue;
+      PROF("df_update");
+      k_df_update<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], H.cur_u(pi, 0), ln2h, ln2l);
+      CK_LAUNCH(ctx);
+    }
+  };
+  // Stopping signal: the fine residual after pre-smoothing of each cycle (fused
+  // into the residual + restriction kernel).  Successive values are compared
+  // (the first cycle always runs); a ratio above 0.75 means FP32 rounding has
+  // taken over.  A correction solve stops once the residual at the end of the
+  // cycle, predicted as mid * sqrt(mid / previous mid) (the rest of the cycle
+  // does about half of a cycle's contraction), is below 0.7 tol.
+  auto inner = [&](bool bg, const std::vector<double> &r0, double floor_rel, int kmax) {
+    std::vector<double> rp(np, HUGE_VAL);
+    for (int k = 0; k < kmax; k++) {
+      if (bg)
+        vcycle<float, true>(ctx, H, 0, co, active, st);
+      else
+        vcycle<float, false>(ctx, H, 0, co, active, st);
+      bool go = false;
+      for (int pi = 0; pi < np; pi++)
+        if (act[pi]) {
+          stats[pi].vcycles++;
+          if (stats[pi].vcycles < cfg.max_vcycles) go = true;
+        }
+      if (!go) break;
+      fused_fine_norms(ctx, H, np, st, inr);
+      go = false;
+      for (int pi = 0; pi < np; pi++) {
+        if (!act[pi]) continue;
+        double r = inr[pi];
+        if (!(r == r)) continue;
+        hist_push(stats[pi], r);
+        const double pred = rp[pi] < HUGE_VAL ? r * std::sqrt(r / rp[pi]) : r;
+        if (r < 0.75 * rp[pi] && r > floor_rel * r0[pi] && pred > (bg ? 0.7 : 0.3) * cfg.tol)
+          go = true;
+        rp[pi] = r;
+      }
+      if (!go) break;
+    }
+  };
+  try {
+    CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!nonzero) {
+      for (int pi = 0; pi < np; pi++) {
+        Grid<float> &G = H.lev[pi][0];
+        PROF("prep_inner");
+        k_prep_zero_df<<<nblocks(G.ncell), 256, 0, st>>>(D[pi].rh, const_cast<float *>(G.f),
+                                                         H.cur_u(pi, 0), H.cur_x(pi, 0),
+                                                         G.ncell, partial, boff[pi]);
+        CK_LAUNCH(ctx);
+      }
+      read_norms(nr);
+      std::vector<double> r0(np);
+      for (int pi = 0; pi < np; pi++) {
+        r0[pi] = nr[2 * pi];
+        stats[pi].res0_rms = nr[2 * pi];
+      }
+      // stop well above the FP32 rounding floor; the correction solves finish
+      inner(false, r0, 1e-4, 40);
+      update();
+    }
+    for (int outer = 0; outer < cfg.max_outer; outer++) {
+      CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+      for (int pi = 0; pi < np; pi++) {
+        if (!act[pi]) continue;
+        Grid<float> &G = H.lev[pi][0];
+        PROF("df_defect");
+        k_df_defect<<<nblocks(G.ncell), 256, 0, st>>>(D[pi], const_cast<float *>(G.f),
+                                                      H.bg_u[pi], H.bg_E[pi], H.cur_u(pi, 0),
+                                                      H.cur_x(pi, 0), partial, boff[pi], ln2h,
+                                                      ln2l);
+        CK_LAUNCH(ctx);
+      }
+      read_norms(nr);
+      int nact = 0;
+      for (int pi = 0; pi < np; pi++) {
+        if (!act[pi]) continue;
+        stats[pi].outer++;
+        if (outer == 0 && nonzero) stats[pi].res0_rms = nr[2 * pi];
+        stats[pi].res_rms = nr[2 * pi];
+        stats[pi].res_max = nr[2 * pi + 1];
+        hist_push(stats[pi], -nr[2 * pi]);
+        if (bad(nr[2 * pi])) throw FrError{FR_EDIVERGED, "non-finite residual"};
+        if (outer > 0) {
+          grow[pi] = nr[2 * pi] > prev[pi] ? grow[pi] + 1 : 0;
+          if (grow[pi] >= 3) throw FrError{FR_EDIVERGED, "defect grew for 3 outer steps"};
+        }
+        prev[pi] = nr[2 * pi];
+        if (nr[2 * pi] <= cfg.tol || stats[pi].vcycles >= cfg.max_vcycles)
+          act[pi] = 0;
+        else
+          nact++;
+      }
+      if (nact == 0) break;
+      CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+      std::vector<double> r0(np, 0.0);
+      for (int pi = 0; pi < np; pi++) {
+        if (!act[pi]) continue;
+        r0[pi] = nr[2 * pi];
+        for (size_t l = 1; l < H.lev[pi].size(); l++) {
+          Grid<float> &F = H.lev[pi][l - 1];
+          Grid<float> &C = H.lev[pi][l];
+          k_restrict_avg<float><<<nblocks(C.ncell), 256, 0, st>>>(F.ubg, F.n0, F.n1, F.n2,
+                                                                  const_cast<float *>(C.ubg));
+          CK_LAUNCH(ctx);
+          k_expf<<<nblocks(C.ncell), 256, 0, st>>>(C.ubg, const_cast<float *>(C.Ebg), C.ncell);
+          CK_LAUNCH(ctx);
+        }
+      }
+      inner(true, r0, 1e-6, std::max(cfg.inner_cycles, 12));
+      update();
+    }
+  } catch (...) {
+    finalize();
+    cudaStreamSynchronize(st);
+    throw;
+  }
+  finalize();
 }
 
 // ---------------------------------------------------------------------------
@@ -1063,7 +1389,9 @@ static fr_opts resolve_opts(const fr_opts *o) {
 static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &o, double tol,
                          std::vector<fr_stats> &stats, cudaStream_t st, int fixed = 0) {
   SolveCfg cfg{tol, o.max_vcycles, o.pre, o.post, o.newton_step_cap, o.inner_cycles,
-               o.max_outer, fixed, o.temporal_depth <= 0 ? 1 : o.temporal_depth};
+               o.max_outer, fixed, o.temporal_depth <= 0 ? 1 : o.temporal_depth, o.tiling,
+               o.defect_precision};
+  if (o.defect_precision < 0 || o.defect_precision > 1) einval("defect_precision must be 0 or 1");
   if (cfg.tdepth > 2) einval("temporal_depth must be 0, 1 or 2");
   if (o.pre < 0 || o.post < 0 || o.max_vcycles < 0 || !(o.newton_step_cap > 0) ||
       !(tol >= 0) || o.inner_cycles < 1 || o.max_outer < 1)
@@ -1072,8 +1400,12 @@ static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &
     p.nl = count_levels(p.n);
     p.k = model_consts(p.box, p.h, p.a, p.om, p.fr0);
   }
-  if (o.prec == FR_MIXED && fixed <= 0)
-    solve_mixed(ctx, P, cfg, stats, st);
+  if (o.prec == FR_MIXED && fixed <= 0) {
+    if (cfg.defect_fp64)
+      solve_mixed(ctx, P, cfg, stats, st);
+    else
+      solve_mixed_df(ctx, P, cfg, stats, st);
+  }
   else
     solve_fp64(ctx, P, cfg, stats, st);
 }
@@ -1225,6 +1557,8 @@ void fr_opts_default(fr_opts *o) {
   o->allow_negative_density = 0;
   o->use_graph = 1;
   o->temporal_depth = 0;
+  o->tiling = 0;
+  o->defect_precision = 0;
 }
 
 const char *fr_status_string(int s) {
@@ -1644,6 +1978,7 @@ int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, cons
     float *du = stage(S, back, u, nc, true, true, st);
     G.u = S.get<float>(nc);
     G.u2 = S.get<float>(nc);
+    G.x2 = S.get<float>(nc);
     CK(cudaMemcpyAsync(G.u, du, nc * sizeof(float), cudaMemcpyDeviceToDevice, st));
     G.x = S.get<float>(nc);
     k_expm1<float><<<nblocks(nc), 256, 0, st>>>(G.u, G.x, nc);
@@ -1699,6 +2034,54 @@ int fr_residual(frmg_ctx *ctx, const double *u, const double *density, const dou
     std::vector<double> nr;
     double *outs[1] = {dd};
     level_norms<double, false>(ctx, ls, outs, nullptr, st, nr);
+    finish(ctx, back, st);
+    return FR_OK;
+  });
+}
+
+int fr_residual_df(frmg_ctx *ctx, const double *u, const double *density, const int dims[3],
+                   double h, double box, double a, double om, double fr0, const double *ub,
+                   double *d, void *stream) {
+  return guard([&]() {
+    if (!ctx || !u || !density || !dims || !d) einval("bad argument");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Problem p = one_level(dims, h, box, a, om, fr0);
+    Consts k = model_consts(box, h, a, om, fr0);
+    Scope S(ctx);
+    std::vector<Staged> back;
+    long long nc = (long long)dims[0] * dims[1] * dims[2];
+    const double *du = stage(S, back, u, nc, true, false, st);
+    const double *dr = stage(S, back, density, nc, true, false, st);
+    const double *dub = stage(S, back, ub, ub ? face_total(dims) : 0, true, false, st);
+    double *dd = stage(S, back, d, nc, false, true, st);
+    DFGrid g;
+    memset(&g, 0, sizeof(g));
+    g.n0 = dims[0];
+    g.n1 = dims[1];
+    g.n2 = dims[2];
+    g.ncell = nc;
+    g.uh = S.get<float>(nc);
+    g.ul = S.get<float>(nc);
+    g.Bh = S.get<float>(nc);
+    g.Bl = S.get<float>(nc);
+    g.rh = S.get<float>(nc);
+    g.rl = S.get<float>(nc);
+    g.bnd = dub;
+    face_offsets(dims, g.foff);
+    split_host(0.5 * k.alpha, g.ahh, g.ahl);
+    split_host(k.beta, g.beh, g.bel);
+    float ln2h, ln2l;
+    split_host(std::log(2.0), ln2h, ln2l);
+    (void)p;
+    k_df_init<<<nblocks(nc), 256, 0, st>>>(g, du, dr, k.gamma, 0, ln2h, ln2l);
+    CK_LAUNCH(ctx);
+    float *scratch = S.get<float>(5 * (size_t)nc);
+    double *partial = S.get<double>(2 * (size_t)nblocks(nc));
+    k_df_defect<<<nblocks(nc), 256, 0, st>>>(g, scratch, scratch + nc, scratch + 2 * nc,
+                                             scratch + 3 * nc, scratch + 4 * nc, partial, 0,
+                                             ln2h, ln2l, dd);
+    CK_LAUNCH(ctx);
     finish(ctx, back, st);
     return FR_OK;
   });

@@ -27,16 +27,23 @@ class fr_opts(ctypes.Structure):
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("prec", ctypes.c_int),
                 ("newton_step_cap", ctypes.c_double), ("inner_cycles", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("allow_negative_density", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("temporal_depth", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("temporal_depth", ctypes.c_int),
+                ("tiling", ctypes.c_int), ("defect_precision", ctypes.c_int)]
+
+
+FR_HIST = 64
 
 
 class fr_stats(ctypes.Structure):
     _fields_ = [("vcycles", ctypes.c_int), ("outer", ctypes.c_int),
                 ("res0_rms", ctypes.c_double), ("res_rms", ctypes.c_double),
-                ("res_max", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("res_max", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("nhist", ctypes.c_int), ("hist", ctypes.c_double * FR_HIST)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}
+        d["hist"] = list(self.hist[: self.nhist])
+        return d
 
 
 class fr_patch(ctypes.Structure):
@@ -47,7 +54,7 @@ class fr_patch(ctypes.Structure):
 EXPORTS = ["fr_opts_default", "fr_status_string", "fr_last_error", "fr_ctx_create",
            "fr_ctx_destroy", "fr_constants", "fr_solve", "fr_solve_levels", "fr_solve_batch",
            "fr_cic_assign", "fr_smooth", "fr_residual", "fr_restrict", "fr_prolong_correct",
-           "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32"]
+           "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32", "fr_residual_df"]
 
 
 def lib_path():
@@ -88,6 +95,7 @@ def load(build_if_missing: bool = False):
             "fr_launch_count": (L, [P]),
             "fr_profile": (I, [P, I]),
             "fr_smooth_f32": (I, [P, P, P, P, P, D, D, D, D, D, P, I, D, I, P]),
+            "fr_residual_df": (I, [P, P, P, P, D, D, D, D, D, P, P, P]),
             "fr_profile_entry": (I, [P, I, P, I, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -299,6 +307,12 @@ class Context:
         st = self.lib.fr_residual(self._h, _ptr(u), _ptr(density), _ptr(f), _dims(u.shape), h,
                                   box, a, omega_m, fr0, _ptr(ub), _ptr(d), _stream(stream))
         self._raise(st, "fr_residual")
+
+    def residual_df(self, u, density, d, *, box, a, omega_m, fr0, h=None, ub=None, stream=None):
+        h = 1.0 / u.shape[2] if h is None else h
+        st = self.lib.fr_residual_df(self._h, _ptr(u), _ptr(density), _dims(u.shape), h, box, a,
+                                     omega_m, fr0, _ptr(ub), _ptr(d), _stream(stream))
+        self._raise(st, "fr_residual_df")
 
     def restrict(self, fine, coarse, stream=None):
         st = self.lib.fr_restrict(self._h, _ptr(fine), _dims(fine.shape), _ptr(coarse),

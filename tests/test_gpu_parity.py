@@ -116,7 +116,8 @@ def test_fp64_vcycles_match_oracle(C, shape, ncyc):
     u = torch.zeros(shape, dtype=torch.float64, device="cuda")
     s = C.vcycles(dev(rho), u, ncyc, **P)
     assert np.abs(host(u) - ref.u).max() < 1e-10
-    assert s.res_rms == pytest.approx(ref.hist[-1], rel=1e-6, abs=1e-13)
+    # the library reduces norms in FP32 per block (a stopping signal): 1e-5 relative
+    assert s.res_rms == pytest.approx(ref.hist[-1], rel=1e-5, abs=1e-13)
 
 
 # ------------------------------------------------------------------ full solves
@@ -294,3 +295,59 @@ def test_f32_smoother_matches_oracle(C, bg, faces):
         C.smooth_f32(u, 2, f=_f32(f), ub=None if ub is None else _f32(ub), **P)
         got = host(u).astype(np.float64)
     assert np.abs(got - ref).max() < 2e-5
+
+
+@pytest.mark.parametrize("tiling", [-1, 1])
+@pytest.mark.parametrize("tdepth", [1, 2])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 40, 96)])
+def test_mixed_tiled_and_plain_kernels_match_oracle(C, tiling, tdepth, shape):
+    """The shared-memory FP32 kernels (smoother with 1 or 2 sweeps per pass,
+    residual + restriction) and the one-thread-per-cell kernels both drive the
+    mixed solve to the oracle's solution."""
+    rho = _field(shape, 4000, sigma=2.0)
+    P = dict(box=2.0 * shape[2], a=1.0, omega_m=0.24, fr0=1e-5)
+    ref = O.solve(rho, tol=1e-8, **P)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s = C.solve(dev(rho), u, tol=1e-8, prec="mixed", tiling=tiling, temporal_depth=tdepth,
+                    **P)
+    assert st == 0 and s.res_rms <= 1e-8
+    assert np.abs(host(u) - ref.u).max() <= 1e-6
+    assert s.vcycles <= 2 * ref.cycles + 4
+
+
+# ------------------------------------------------------------------ double-float defect
+@pytest.mark.parametrize("fr0,box", [(1e-4, 256.0), (1e-5, 128.0), (1e-6, 64.0)])
+@pytest.mark.parametrize("faces", [False, True])
+def test_double_float_defect_matches_fp64(C, fr0, box, faces):
+    """The mixed loop's defect in double-float arithmetic agrees with the FP64
+    oracle residual to ~1e-13 of the size of the operator's terms, both for a
+    random u (large residual) and at a converged solution (the cancellation
+    the convergence test depends on)."""
+    shape = (24, 20, 32)
+    rho = _field(shape, 77, sigma=2.0)
+    P = dict(box=box, a=1.0, omega_m=0.24, fr0=fr0)
+    rng = np.random.default_rng(8)
+    ub = rng.uniform(-2.0, 0.5, sum(O.face_sizes(shape))) if faces else None
+    alpha, beta, gamma = PF.coefficients(box, shape[2], 1.0, 0.24, fr0)
+    sol = O.solve(rho, tol=1e-12, ub=ub, h=1.0 / shape[2], **P)
+    for u in (rng.uniform(-3.0, 0.8, shape), sol.u):
+        ref = O.residual(u, rho, ub=ub, **P)
+        d = torch.empty(shape, dtype=torch.float64, device="cuda")
+        C.residual_df(dev(u), dev(rho), d, ub=None if ub is None else dev(ub), **P)
+        # size of the largest flux term, alpha e^u |du| with |du| up to ~4
+        term = alpha * np.exp(np.abs(u).max()) * 4.0
+        assert np.abs(host(d) - ref).max() < 2e-13 * term + 1e-12
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 40, 96)])
+def test_mixed_defect_precisions_agree(C, shape):
+    """Double-float and FP64 defects drive the mixed loop to the same solution."""
+    rho = _field(shape, 5000, sigma=2.0)
+    P = dict(box=2.0 * shape[2], a=1.0, omega_m=0.24, fr0=1e-5)
+    outs = []
+    for dp in (0, 1):
+        u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        st, s = C.solve(dev(rho), u, tol=1e-10, prec="mixed", defect_precision=dp, **P)
+        assert st == 0 and s.res_rms <= 1e-10
+        outs.append(host(u))
+    assert np.abs(outs[0] - outs[1]).max() < 1e-9
