@@ -222,6 +222,29 @@ int fr_vcycles(frmg_ctx *ctx, const double *density, const int dims[3], double b
                double a, double omega_m, double fr0_abs, double *u_inout, int ncycles,
                const fr_opts *opts, fr_stats *stats, void *stream);
 
+/*
+ * Residual norm of one grid without allocating anything (no cudaMalloc,
+ * cudaFree or allocating library call), for callers that cannot allocate
+ * device memory at that point: code recording a CUDA stream capture, code
+ * whose device memory is owned by another allocator, loops that cannot afford
+ * the synchronisation of an allocation.  The paper has no counterpart; this is
+ * a service entry point of the library.
+ * out2 (device) receives {rms of L(u) over the cells, max |L(u)|}; u, density,
+ * ub (optional patch faces, as fr_smooth) and out2 must be device pointers;
+ * no context is needed.  Grids are limited to 33,554,432 cells (FR_EINVAL
+ * beyond, with a message in fr_last_error()).  The call is asynchronous on
+ * `stream`: out2 is valid once the stream reaches it.
+ * Scratch: a fixed 16 KB array of this library's module on each GPU that
+ * loads the library, held until the process exits and shared by every call on
+ * that GPU; each call overwrites all of it before reading it, but calls that
+ * overlap on the GPU (different streams, no ordering) race on it.  The first
+ * call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture begins.
+ */
+int fr_residual_norm_noalloc(const double *u, const double *density, const int dims[3],
+                             double h, double box_mpc_h, double a, double omega_m,
+                             double fr0_abs, const double *ub, double *out2, void *stream);
+
 /* Number of kernel launches this context issued since it was created. */
 long long fr_launch_count(const frmg_ctx *ctx);
 

@@ -54,7 +54,8 @@ class fr_patch(ctypes.Structure):
 EXPORTS = ["fr_opts_default", "fr_status_string", "fr_last_error", "fr_ctx_create",
            "fr_ctx_destroy", "fr_constants", "fr_solve", "fr_solve_levels", "fr_solve_batch",
            "fr_cic_assign", "fr_smooth", "fr_residual", "fr_restrict", "fr_prolong_correct",
-           "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32", "fr_residual_df"]
+           "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32", "fr_residual_df",
+           "fr_residual_norm_noalloc"]
 
 
 def lib_path():
@@ -96,6 +97,7 @@ def load(build_if_missing: bool = False):
             "fr_profile": (I, [P, I]),
             "fr_smooth_f32": (I, [P, P, P, P, P, D, D, D, D, D, P, I, D, I, P]),
             "fr_residual_df": (I, [P, P, P, P, D, D, D, D, D, P, P, P]),
+            "fr_residual_norm_noalloc": (I, [P, P, P, D, D, D, D, D, P, P, P]),
             "fr_profile_entry": (I, [P, I, P, I, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -153,6 +155,16 @@ def _stream(stream):
     if hasattr(stream, "cuda_stream"):
         return ctypes.c_void_p(stream.cuda_stream)
     return ctypes.c_void_p(int(stream))
+
+
+def residual_norm_noalloc(u, density, out2, *, box, a, omega_m, fr0, h=None, ub=None,
+                          stream=None):
+    """Allocation-free residual norm: out2 (device, 2 doubles) <- (rms, max) of
+    L(u); asynchronous on the stream.  Returns the status code."""
+    h = 1.0 / u.shape[2] if h is None else h
+    lib = load()
+    return lib.fr_residual_norm_noalloc(_ptr(u), _ptr(density), _dims(u.shape), h, box, a,
+                                        omega_m, fr0, _ptr(ub), _ptr(out2), _stream(stream))
 
 
 def constants(box, n0, a, omega_m, fr0):
