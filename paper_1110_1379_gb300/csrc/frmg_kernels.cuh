@@ -574,13 +574,43 @@ __global__ void __launch_bounds__(256) k_prolong(const Grid<T> *fine, const Grid
     }
 }
 
+// Block sum of two values (all threads get the result).
+template <int NT>
+__device__ __forceinline__ void block_sum2(double a, double b, double &ra, double &rb) {
+  __shared__ double sa[NT / 32], sb[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  double ta = 0.0, tb = 0.0;
+  for (int q = 0; q < NT / 32; q++) {
+    ta += sa[q];
+    tb += sb[q];
+  }
+  ra = ta;
+  rb = tb;
+}
+
 // Coarsest level: one block per grid, Newton-Gauss-Seidel sweeps until
-// rms <= max(rel * rms0, abs_floor) (at least one sweep, at most maxit);
-// stop_on_stall also stops once a sweep reduces the rms by less than 5%.
+// rms <= max(rel * rms0, abs_floor) (at least one sweep, at most maxit).
+// stop_on_stall also stops when a sweep does not lower the rms.
+// meanfix (periodic grids): after every sweep, one Newton step on a constant
+// shift c of the whole grid.  On a periodic grid the flux terms telescope, so
+// sum_i (N_i - f_i) depends on c only through the mass term, whose derivative
+// is -(beta/2) sum_i F_i e^{-d_i/2}; the step removes the error of the
+// constant mode, which plain relaxation damps by only ~beta/(12 alpha) per
+// sweep when the Laplacian dominates (stiff coarsest problems).
 template <typename T, bool BG, int NT>
 __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid, double rel,
                                                  double abs_floor, int maxit, int stop_on_stall,
-                                                 const int *active, int par) {
+                                                 const int *active, int par, int meanfix) {
   int g = blockIdx.x;
   if (g >= ngrid) return;
   const Grid<T> G = view(grids, g, par);
@@ -590,6 +620,7 @@ __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid
   const long long n = G.ncell;
   const int hx = G.n0 >> 1;
   const long long nh = (long long)hx * G.n1 * G.n2;
+  const bool shift = meanfix && G.bnd == nullptr;
   double thr = 0.0, prev = 0.0;
   for (int it = -1; it < maxit; it++) {
     if (it >= 0) {
@@ -600,6 +631,33 @@ __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid
           int j = (int)(r % G.n1);
           int k = (int)(r / G.n1);
           ngs_update<T, BG>(G, 2 * ih + ((j + k + colour) & 1), j, k);
+        }
+        __syncthreads();
+      }
+      if (shift) {
+        double S = 0.0, D = 0.0;
+        for (long long t = threadIdx.x; t < n; t += NT) {
+          int i = (int)(t % G.n0);
+          long long r = t / G.n0;
+          int j = (int)(r % G.n1);
+          int k = (int)(r / G.n1);
+          T N, dN;
+          cell_eval<T, BG>(G, i, j, k, t, N, dN);
+          S += (double)(N - rhs_at(G, t));
+          const T Ei = BG ? (T)G.Ebg[t] : T(1);
+          const T F = BG ? m_rsqrt(Ei) : T(1);
+          D += 0.5 * (double)G.beta * (double)(F * m_rsqrt(T(1) + G.x[t]));
+        }
+        double St, Dt;
+        block_sum2<NT>(S, D, St, Dt);
+        double c = Dt > 0.0 ? St / Dt : 0.0;
+        const double cap = (double)G.cap;
+        c = c > cap ? cap : (c < -cap ? -cap : c);
+        __syncthreads();
+        for (long long t = threadIdx.x; t < n; t += NT) {
+          const T un = G.u[t] + (T)c;
+          G.u[t] = un;
+          G.x[t] = m_expm1(un);
         }
         __syncthreads();
       }
@@ -622,9 +680,10 @@ __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid
       int st = 0;
       if (it < 0) {
         thr = fmax(rel * rms, abs_floor);
+        if (rms <= thr) st = 1;
       } else {
         if (rms <= thr) st = 1;
-        if (stop_on_stall && rms > 0.95 * prev) st = 1;
+        if (stop_on_stall && rms >= prev) st = 1;
       }
       prev = rms;
       stop = st;

@@ -621,6 +621,7 @@ struct CycleOpts {
   int tdepth;  // sweeps per tiled pass (1 or 2)
   double crs_rel, crs_abs;
   int crs_maxit, crs_stall;
+  int crs_meanfix;  // constant-mode Newton step in periodic coarsest solves
 };
 
 // Profiling names: kernel family, precision, fine (depth 0) or coarse level.
@@ -754,7 +755,8 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
     auto &c = H.coarsest[l];
     PROF(sizeof(T) == 8 ? "coarsest_f64" : "coarsest_f32");
     k_coarsest<T, BG, 256><<<c.size(), 256, 0, st>>>(c.d, c.size(), o.crs_rel, o.crs_abs,
-                                                     o.crs_maxit, o.crs_stall, active, H.par[l]);
+                                                     o.crs_maxit, o.crs_stall, active, H.par[l],
+                                                     o.crs_meanfix);
     CK_LAUNCH(ctx);
   }
   if (H.cont[l].empty()) return;
@@ -881,7 +883,7 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
   }
   int *active = S.get<int>(np);
   std::vector<int> act(np, 1);
-  CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.1 * cfg.tol, 500, 0};
+  CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.1 * cfg.tol, 500, 0, 0};
   std::vector<double> nr;
   level_norms<double, false>(ctx, H.all[0], nullptr, nullptr, st, nr);
   std::vector<double> prev(np);
@@ -948,7 +950,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
   CK(cudaStreamSynchronize(st));
   int *active = S.get<int>(np);
   std::vector<int> act(np, 1);
-  CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.0, 500, 1};
+  CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.0, 500, 1, 1};
   std::vector<double> nr, inr;
   std::vector<double> prev(np, 0.0);
   std::vector<int> grow(np, 0);
@@ -974,6 +976,10 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
   // does about half of a cycle's contraction), is below 0.7 tol.
   auto inner = [&](bool bg, const std::vector<double> &r0, double floor_rel, int kmax) {
     std::vector<double> rp(np, HUGE_VAL);
+    // fields leave the inner solve one by one (their active flag drops until
+    // the next outer step), so a batch does not run every field as long as
+    // its slowest one
+    std::vector<int> iact = act;
     for (int k = 0; k < kmax; k++) {
       if (bg)
         vcycle<float, true>(ctx, H, 0, co, active, st);
@@ -981,25 +987,30 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
         vcycle<float, false>(ctx, H, 0, co, active, st);
       bool go = false;
       for (int pi = 0; pi < np; pi++)
-        if (act[pi]) {
+        if (iact[pi]) {
           stats[pi].vcycles++;
-          if (stats[pi].vcycles < cfg.max_vcycles) go = true;
+          if (stats[pi].vcycles >= cfg.max_vcycles) iact[pi] = 0;
+          else go = true;
         }
       if (!go) break;
       fused_fine_norms(ctx, H, np, st, inr);
       go = false;
       for (int pi = 0; pi < np; pi++) {
-        if (!act[pi]) continue;
+        if (!iact[pi]) continue;
         double r = inr[pi];
-        if (!(r == r)) continue;  // single-level grid: one coarsest solve per cycle
+        if (!(r == r)) { go = true; continue; }  // single-level grid: one coarsest solve per cycle
         hist_push(stats[pi], r);
         const double pred = rp[pi] < HUGE_VAL ? r * std::sqrt(r / rp[pi]) : r;
         if (r < 0.75 * rp[pi] && r > floor_rel * r0[pi] && pred > (bg ? 0.7 : 0.3) * cfg.tol)
           go = true;
+        else
+          iact[pi] = 0;
         rp[pi] = r;
       }
       if (!go) break;
+      CK(cudaMemcpyAsync(active, iact.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
     }
+    CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
   };
   if (!nonzero) {
     // full-variable FP32 phase from u = 0
@@ -1187,7 +1198,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   };
   int *active = S.get<int>(np);
   std::vector<int> act(np, 1);
-  CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.0, 500, 1};
+  CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.0, 500, 1, 1};
   std::vector<double> nr, inr;
   std::vector<double> prev(np, 0.0);
   std::vector<int> grow(np, 0);
@@ -1211,6 +1222,10 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   // does about half of a cycle's contraction), is below 0.7 tol.
   auto inner = [&](bool bg, const std::vector<double> &r0, double floor_rel, int kmax) {
     std::vector<double> rp(np, HUGE_VAL);
+    // fields leave the inner solve one by one (their active flag drops until
+    // the next outer step), so a batch does not run every field as long as
+    // its slowest one
+    std::vector<int> iact = act;
     for (int k = 0; k < kmax; k++) {
       if (bg)
         vcycle<float, true>(ctx, H, 0, co, active, st);
@@ -1218,25 +1233,30 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
         vcycle<float, false>(ctx, H, 0, co, active, st);
       bool go = false;
       for (int pi = 0; pi < np; pi++)
-        if (act[pi]) {
+        if (iact[pi]) {
           stats[pi].vcycles++;
-          if (stats[pi].vcycles < cfg.max_vcycles) go = true;
+          if (stats[pi].vcycles >= cfg.max_vcycles) iact[pi] = 0;
+          else go = true;
         }
       if (!go) break;
       fused_fine_norms(ctx, H, np, st, inr);
       go = false;
       for (int pi = 0; pi < np; pi++) {
-        if (!act[pi]) continue;
+        if (!iact[pi]) continue;
         double r = inr[pi];
-        if (!(r == r)) continue;
+        if (!(r == r)) { go = true; continue; }
         hist_push(stats[pi], r);
         const double pred = rp[pi] < HUGE_VAL ? r * std::sqrt(r / rp[pi]) : r;
         if (r < 0.75 * rp[pi] && r > floor_rel * r0[pi] && pred > (bg ? 0.7 : 0.3) * cfg.tol)
           go = true;
+        else
+          iact[pi] = 0;
         rp[pi] = r;
       }
       if (!go) break;
+      CK(cudaMemcpyAsync(active, iact.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
     }
+    CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
   };
   try {
     CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));

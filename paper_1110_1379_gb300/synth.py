@@ -103,3 +103,66 @@ ZELDOVICH_AMPLITUDE_128 = None
 def uniform_positions(np_, seed):
     rng = np.random.default_rng(seed)
     return rng.random((np_, 3))
+
+
+def batch_specs(nfields=96, seed=5000):
+    """Many independent fields of uneven size: N from {32, 48, 64, 96, 128},
+    |f_R0| from {1e-4, 1e-5, 1e-6}, a ~ U[0.3, 1], lognormal sigma ~ U[0.5, 2.5],
+    box = N Mpc/h (cell 1 Mpc/h); field i uses density seed seed + i."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nfields):
+        n = int(rng.choice([32, 48, 64, 96, 128]))
+        out.append(dict(n=n, fr0=float(rng.choice([1e-4, 1e-5, 1e-6])),
+                        a=float(rng.uniform(0.3, 1.0)), sigma=float(rng.uniform(0.5, 2.5)),
+                        box=float(n), seed=seed + i))
+    return out
+
+
+def refine_density(parent_block, seed, sigma=0.5):
+    """Density of a refinement patch over a block of parent cells: each parent
+    cell splits into 2x2x2 children whose values are the parent value times a
+    seeded lognormal modulation normalised to mean 1 over the 8 children, so
+    the children average exactly to their parent (mass-consistent)."""
+    rng = np.random.default_rng(seed)
+    p = np.asarray(parent_block, dtype=np.float64)
+    mod = np.exp(sigma * rng.standard_normal((2 * p.shape[0], 2 * p.shape[1], 2 * p.shape[2])))
+    m = mod.reshape(p.shape[0], 2, p.shape[1], 2, p.shape[2], 2)
+    m = m / m.mean(axis=(1, 3, 5), keepdims=True)
+    child = m * p[:, None, :, None, :, None]
+    return child.reshape(2 * p.shape[0], 2 * p.shape[1], 2 * p.shape[2])
+
+
+def patch_layout(rho, sizes, count, seed, margin=1, parent_box=None):
+    """Greedy placement of `count` cubic patches of fine sizes drawn from `sizes`
+    over the densest cells of the parent grid rho (n2, n1, n0): each patch's
+    footprint (size/2 parent cells) plus `margin` parent cells stays inside the
+    parent (or inside parent_box = (lo, hi) per axis) and does not overlap
+    earlier patches.  Returns a list of (origin (x, y, z), size)."""
+    rng = np.random.default_rng(seed)
+    n2, n1, n0 = rho.shape
+    order = np.argsort(rho, axis=None)[::-1]
+    taken = np.zeros(rho.shape, dtype=bool)
+    out = []
+    lo = np.array([margin, margin, margin])
+    hi = np.array([n0, n1, n2]) - margin
+    if parent_box is not None:
+        lo = np.maximum(lo, np.array(parent_box[0]) + margin)
+        hi = np.minimum(hi, np.array(parent_box[1]) - margin)
+    for flat in order:
+        if len(out) >= count:
+            break
+        k, j, i = np.unravel_index(flat, rho.shape)
+        s = int(rng.choice(sizes))
+        half = s // 2
+        org = np.array([i, j, k]) - half // 2
+        org = np.minimum(np.maximum(org, lo), hi - half)
+        if np.any(org < lo) or np.any(org + half > hi):
+            continue
+        sl = (slice(org[2], org[2] + half), slice(org[1], org[1] + half),
+              slice(org[0], org[0] + half))
+        if taken[sl].any():
+            continue
+        taken[sl] = True
+        out.append((tuple(int(v) for v in org), s))
+    return out
