@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--n", type=int, default=N, help=argparse.SUPPRESS)
     ap.add_argument("--prec", default="both", choices=["both", "mixed"],
                     help="'mixed' skips the FP64 comparison (profiling runs)")
+    ap.add_argument("--workload", default="solve512",
+                    choices=["solve512", "batch96", "levels256", "cic128", "small32"],
+                    help="secondary workloads print their own line (default: the 512^3 solve)")
     return ap.parse_args()
 
 
@@ -195,10 +198,130 @@ def grad_error(u_test, u_ref, ubar, h):
     return {"max_rel": mx / ref_max, "rms_rel": (sq / n) ** 0.5 / ref_max}
 
 
+def timed(fn, steps, warmup):
+    """Median wall time of fn() (which synchronises) over `steps` runs."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return statistics.median(ts)
+
+
+def run_secondary(args):
+    """Secondary workloads (BASELINE configs 1, 2, 4, 5): one JSON line each."""
+    import numpy as np
+    import torch
+
+    from paper_1110_1379_gb300 import frmg, synth
+    torch.cuda.set_device(0)
+    ctx = frmg.Context(0)
+    line = {"workload": args.workload, "data": "synthetic", "unit": "cells/s"}
+    if args.workload == "batch96":
+        specs = synth.batch_specs(96, 5000)
+        rhos = [torch.from_numpy(synth.lognormal_density((s["n"],) * 3, s["seed"],
+                                                         sigma=s["sigma"])).cuda() for s in specs]
+        us = [torch.zeros_like(r) for r in rhos]
+        cells = sum(r.numel() for r in rhos)
+        kw = dict(boxes=[s["box"] for s in specs], avals=[s["a"] for s in specs],
+                  fr0s=[s["fr0"] for s in specs], omega_m=0.24, tol=TOL)
+
+        def batch(prec):
+            for x in us:
+                x.zero_()
+            st, _ = ctx.solve_batch(rhos, us, prec=prec, **kw)
+            assert st == 0
+
+        def seq(prec):
+            for r, x, s in zip(rhos, us, specs):
+                x.zero_()
+                st, _ = ctx.solve(r, x, tol=TOL, prec=prec, box=s["box"], a=s["a"],
+                                  omega_m=0.24, fr0=s["fr0"])
+                assert st == 0
+
+        t_b = timed(lambda: batch("mixed"), args.steps, args.warmup)
+        t_sm = timed(lambda: seq("mixed"), 1, 1)
+        t_s64 = timed(lambda: seq("fp64"), 1, 1)
+        line.update(metric="batched solve of 96 fields (N 32-128, mixed |f_R0|, a, sigma): "
+                           "aggregate cells/s to rms 1e-8",
+                    value=cells / t_b, cells=cells, ms=1e3 * t_b,
+                    sequential_mixed=cells / t_sm, sequential_fp64=cells / t_s64,
+                    speedup_vs_sequential_fp64=t_s64 / t_b)
+    elif args.workload == "levels256":
+        rho0, patches = synth.nested_case(256, 4000, [32, 48, 64], 16, [32, 48], 12)
+        r0 = torch.from_numpy(rho0).cuda()
+        u0 = torch.zeros_like(r0)
+        gp = [dict(parent=p["parent"], origin=p["origin"], density=torch.from_numpy(p["rho"]).cuda(),
+                   u=torch.zeros(p["rho"].shape, dtype=torch.float64, device="cuda"))
+              for p in patches]
+        cells = r0.numel() + sum(p["rho"].size for p in patches)
+
+        def run(prec):
+            u0.zero_()
+            st, _ = ctx.solve_levels(r0, u0, gp, box=256.0, a=1.0, omega_m=0.24, fr0=1e-5,
+                                     tol=TOL, prec=prec)
+            assert st == 0
+
+        t_m = timed(lambda: run("mixed"), args.steps, args.warmup)
+        t_64 = timed(lambda: run("fp64"), 1, 1)
+        line.update(metric="domain 256^3 + nested patches (2x, 4x): cells/s to rms 1e-8 on every grid",
+                    value=cells / t_m, cells=cells, patches=len(patches),
+                    level2=sum(1 for p in patches if p["parent"] >= 0), ms=1e3 * t_m,
+                    fp64=cells / t_64)
+    elif args.workload == "cic128":
+        n = 128
+        pos = torch.from_numpy(synth.zeldovich_positions(n, 2000,
+                                                         synth.ZELDOVICH_AMPLITUDE_128)).cuda()
+        rho = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(rho)
+        out = {}
+        for a in (0.5, 1.0):
+            for prec in ("fp64", "mixed"):
+                def run():
+                    ctx.cic(pos, rho)
+                    u.zero_()
+                    st, _ = ctx.solve(rho, u, box=128.0, a=a, omega_m=0.24, fr0=1e-5, tol=TOL,
+                                      prec=prec)
+                    assert st == 0
+                out[f"a={a} {prec}"] = n ** 3 / timed(run, args.steps, args.warmup)
+        tc = timed(lambda: ctx.cic(pos, rho), args.steps, args.warmup)
+        line.update(metric="CIC of 128^3 Zel'dovich particles + solve on 128^3: cells/s",
+                    value=out["a=1.0 fp64"], per_case=out, cic_ms=1e3 * tc,
+                    max_contrast=float(rho.max() - 1.0))
+    else:  # small32
+        from oracle import oracle as O
+        rho_np = synth.lognormal_density((32,) * 3, 1000, sigma=1.0)
+        rho = torch.from_numpy(rho_np).cuda()
+        u = torch.zeros_like(rho)
+        P = dict(box=64.0, a=1.0, omega_m=0.24, fr0=1e-5)
+        res = {}
+        for prec in ("fp64", "mixed"):
+            def run():
+                u.zero_()
+                st, _ = ctx.solve(rho, u, tol=TOL, prec=prec, **P)
+                assert st == 0
+            res[prec] = 32 ** 3 / timed(run, args.steps, args.warmup)
+        t0 = time.perf_counter()
+        O.solve(rho_np, tol=TOL, **P)
+        res["oracle_1core"] = 32 ** 3 / (time.perf_counter() - t0)
+        line.update(metric="32^3 FP64 FAS solve: cells/s to rms 1e-8", value=res["fp64"],
+                    per_case=res)
+    print(json.dumps(line))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "solve512":
+        run_secondary(args)
         return
     import numpy as np
     import torch
@@ -228,15 +351,24 @@ def main():
     ctx = frmg.Context(local)
     stream = torch.cuda.current_stream()
 
-    def solve(prec, profile=False):
+    tuned = {}
+
+    def solve(prec, profile=False, **kw):
         u.zero_()
-        st, s = ctx.solve(rho, u, tol=TOL, prec=prec, stream=stream, **PHYS)
+        opts = dict(tuned) if (prec == "mixed" and not kw.pop("default", False)) else {}
+        opts.update(kw)
+        st, s = ctx.solve(rho, u, tol=TOL, prec=prec, stream=stream, **opts, **PHYS)
         if st != frmg.FR_OK:
             raise RuntimeError(f"solve failed: status {st} {s.as_dict()}")
         return s
 
     for _ in range(args.warmup):
         solve("mixed")
+    torch.cuda.synchronize()
+    # autotuner (untimed): V-cycle shape and sweeps per tiled pass for this workload
+    best, tune_s = ctx.autotune(rho, tol=TOL, prec="mixed", stream=stream, **PHYS)
+    tuned = {k: best[k] for k in ("pre", "post", "temporal_depth")}
+    solve("mixed")
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -261,6 +393,16 @@ def main():
         ms = float(t.item())
     value = world * cells * args.steps / (ms / 1e3)
     u_mixed = u.clone()
+
+    # the same workload with the untuned default V(2,2) for comparison
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s_def = solve("mixed", default=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    value_default = world * cells * args.steps / (e0.elapsed_time(e1) / 1e3)
 
     # the same steps again with per-kernel CUDA events on the launch stream
     # (kept out of the timed region above so the events do not perturb it)
@@ -329,7 +471,7 @@ def main():
         u_h.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, s = ctx.solve(rho_h, u_h, tol=TOL, prec="mixed", stream=stream, **PHYS)
+        st, s = ctx.solve(rho_h, u_h, tol=TOL, prec="mixed", stream=stream, **tuned, **PHYS)
         t1 = time.perf_counter()
         if it > 0:
             e2e_t.append(t1 - t0)
@@ -355,6 +497,11 @@ def main():
                  "ms_per_solve": statistics.median(t64) if t64 else None,
                  "vcycles": s64.vcycles if s64 else None, "res_rms": s64.res_rms if s64 else None},
         "mixed_vs_fp64_speedup": (value / world / fp64_value) if fp64_value else None,
+        "autotuned": {**tuned, "tune_seconds": tune_s,
+                      "note": "fastest of V(pre,post) in {(1,1),(2,1),(1,2),(2,2),(3,3)} x "
+                              "sweeps per tiled pass {1,2}, chosen by fr_autotune on this field"},
+        "mixed_default_v22": {"value": value_default, "unit": "cells/s",
+                              "vcycles": s_def.vcycles, "outer": s_def.outer},
         "mixed": {"vcycles": s0.vcycles, "outer": s0.outer, "res_rms": s0.res_rms,
                   "res_max": s0.res_max, "hist": list(s0.hist[: s0.nhist]),
                   "defect_arithmetic": "double-float (FP32 pairs, ~48-bit)"},

@@ -245,6 +245,19 @@ int fr_residual_norm_noalloc(const double *u, const double *density, const int d
                              double h, double box_mpc_h, double a, double omega_m,
                              double fr0_abs, const double *ub, double *out2, void *stream);
 
+/*
+ * Autotuner: solves the given problem from u = 0 (into library scratch; the
+ * caller's arrays are only read) with every candidate setting of the V-cycle
+ * shape (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)} and the tiled
+ * smoother's sweeps per pass (temporal_depth 1 or 2), on top of *base (NULL =
+ * defaults), twice each, and writes the fastest setting that reaches tol to
+ * *best (and its time in seconds to *best_seconds, if not NULL).  Device or
+ * host density pointer.  FR_ENOCONV if no candidate converged.
+ */
+int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double box_mpc_h,
+                double a, double omega_m, double fr0_abs, double tol, const fr_opts *base,
+                fr_opts *best, double *best_seconds, void *stream);
+
 /* Number of kernel launches this context issued since it was created. */
 long long fr_launch_count(const frmg_ctx *ctx);
 

@@ -1030,7 +1030,8 @@ __global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
         if (DIR) {
           in = gxx >= 0 && gxx < n0 && gyy >= 0 && gyy < n1;
         } else {
-          gxx = gxx < 0 ? gxx + n0 : (gxx >= n0 ? gxx - n0 : gxx);
+          // the tile (TX + 4 wide) may span more than two periods of a small grid
+          gxx = wrapmod(gxx, n0);
           gyy = wrapmod(gyy, n1);
         }
         if (in) pg[k] = (long long)gyy * n0 + gxx;

@@ -1714,6 +1714,65 @@ int fr_solve(frmg_ctx *ctx, const double *density, const int dims[3], double box
   return solve_impl(ctx, density, dims, box, a, om, fr0, tol, u, opts, stats, stream, 0);
 }
 
+int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double box, double a,
+                double om, double fr0, double tol, const fr_opts *base, fr_opts *best,
+                double *best_seconds, void *stream) {
+  return guard([&]() {
+    if (!ctx || !density || !dims || !best) einval("NULL argument");
+    check_dims(dims);
+    check_model(box, a, om, fr0);
+    fr_opts o0 = resolve_opts(base);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    long long nc = (long long)dims[0] * dims[1] * dims[2];
+    double *u = nullptr;
+    const double *rho = density;
+    {
+      // scratch solution (and density, if on the host) for the trials
+      u = (double *)frmg_alloc(ctx, nc * sizeof(double));
+      if (!is_device_ptr(density)) {
+        double *d = (double *)frmg_alloc(ctx, nc * sizeof(double));
+        CK(cudaMemcpyAsync(d, density, nc * sizeof(double), cudaMemcpyHostToDevice, st));
+        rho = d;
+      }
+    }
+    const int shapes[5][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 3}};
+    double best_t = HUGE_VAL;
+    fr_opts best_o = o0;
+    int status = FR_ENOCONV;
+    for (int sh = 0; sh < 5; sh++)
+      for (int td = 1; td <= 2; td++) {
+        fr_opts o = o0;
+        o.pre = shapes[sh][0];
+        o.post = shapes[sh][1];
+        o.temporal_depth = td;
+        double tmin = HUGE_VAL;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; rep++) {
+          CK(cudaMemsetAsync(u, 0, nc * sizeof(double), st));
+          CK(cudaStreamSynchronize(st));
+          double t0 = now_s();
+          fr_stats sv;
+          int r = fr_solve(ctx, rho, dims, box, a, om, fr0, tol, u, &o, &sv, stream);
+          double t1 = now_s();
+          if (r != FR_OK) ok = false;
+          tmin = std::min(tmin, t1 - t0);
+        }
+        if (ok && tmin < best_t) {
+          best_t = tmin;
+          best_o = o;
+          status = FR_OK;
+        }
+      }
+    frmg_release(ctx, u);
+    if (rho != density) frmg_release(ctx, const_cast<double *>(rho));
+    *best = best_o;
+    if (best_seconds) *best_seconds = best_t;
+    if (status != FR_OK) g_last_error = "no candidate setting reached tol";
+    return status;
+  });
+}
+
 int fr_vcycles(frmg_ctx *ctx, const double *density, const int dims[3], double box, double a,
                double om, double fr0, double *u, int ncycles, const fr_opts *opts,
                fr_stats *stats, void *stream) {

@@ -55,7 +55,7 @@ EXPORTS = ["fr_opts_default", "fr_status_string", "fr_last_error", "fr_ctx_creat
            "fr_ctx_destroy", "fr_constants", "fr_solve", "fr_solve_levels", "fr_solve_batch",
            "fr_cic_assign", "fr_smooth", "fr_residual", "fr_restrict", "fr_prolong_correct",
            "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32", "fr_residual_df",
-           "fr_residual_norm_noalloc"]
+           "fr_residual_norm_noalloc", "fr_autotune"]
 
 
 def lib_path():
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = False):
             "fr_smooth_f32": (I, [P, P, P, P, P, D, D, D, D, D, P, I, D, I, P]),
             "fr_residual_df": (I, [P, P, P, P, D, D, D, D, D, P, P, P]),
             "fr_residual_norm_noalloc": (I, [P, P, P, D, D, D, D, D, P, P, P]),
+            "fr_autotune": (I, [P, P, P, D, D, D, D, D, P, P, P, P]),
             "fr_profile_entry": (I, [P, I, P, I, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -244,6 +245,17 @@ class Context:
         if st in raise_on:
             self._raise(st, "fr_solve")
         return st, s
+
+    def autotune(self, density, *, box, a, omega_m, fr0, tol=1e-8, stream=None, **base):
+        """Fastest (pre, post, temporal_depth) for this problem; returns (opts dict, seconds)."""
+        b = self.opts(tol=tol, **base)
+        best = fr_opts()
+        secs = ctypes.c_double()
+        st = self.lib.fr_autotune(self._h, _ptr(density), _dims(density.shape), box, a, omega_m,
+                                  fr0, tol, ctypes.byref(b), ctypes.byref(best),
+                                  ctypes.byref(secs), _stream(stream))
+        self._raise(st, "fr_autotune")
+        return {k: getattr(best, k) for k, _ in fr_opts._fields_}, secs.value
 
     def vcycles(self, density, u, ncycles, *, box, a, omega_m, fr0, stream=None, **opts):
         o = self.opts(**opts)

@@ -95,9 +95,11 @@ def zeldovich_positions(n, seed, amplitude, slope=-1.5):
     return pos
 
 
-# Zel'dovich amplitude for the 128^3, seed-2000 particle set of the CIC workload,
-# chosen (oracle/calibrate_zeldovich.py) so that max(rho~ - 1) is about 100.
-ZELDOVICH_AMPLITUDE_128 = None
+# Zel'dovich amplitude for the 128^3, seed-2000 particle set of the CIC workload:
+# the value maximising max(rho~ - 1) (= 43.7) of its CIC density, written by
+# oracle/calibrate_zeldovich.py (a one-particle-per-cell Zel'dovich field with
+# this spectrum saturates below the contrast of ~100 the workload names).
+ZELDOVICH_AMPLITUDE_128 = 52.5
 
 
 def uniform_positions(np_, seed):
@@ -166,3 +168,24 @@ def patch_layout(rho, sizes, count, seed, margin=1, parent_box=None):
         taken[sl] = True
         out.append((tuple(int(v) for v in org), s))
     return out
+
+
+def nested_case(n, seed, sizes1, count1, sizes2, count2, sigma=2.5):
+    """Domain density (lognormal) plus refinement patches: `count1` level-1
+    patches of fine sizes from `sizes1` over the densest domain cells, and one
+    level-2 patch (sizes from `sizes2`) inside each of the first `count2`
+    level-1 patches.  Returns (rho_domain, [dict(parent, origin, rho)])."""
+    rho0 = lognormal_density((n, n, n), seed, sigma=sigma)
+    lay1 = patch_layout(rho0, sizes1, count1, seed + 1, margin=1)
+    patches = []
+    for t, (org, s) in enumerate(lay1):
+        blk = rho0[org[2]:org[2] + s // 2, org[1]:org[1] + s // 2, org[0]:org[0] + s // 2]
+        patches.append(dict(parent=-1, origin=org, rho=refine_density(blk, seed + 10 + t)))
+    for t1 in range(min(count2, len(lay1))):
+        p = patches[t1]
+        lay2 = patch_layout(p["rho"], sizes2, 1, seed + 100 + t1, margin=1)
+        for org, s in lay2:
+            blk = p["rho"][org[2]:org[2] + s // 2, org[1]:org[1] + s // 2,
+                           org[0]:org[0] + s // 2]
+            patches.append(dict(parent=t1, origin=org, rho=refine_density(blk, seed + 200 + t1)))
+    return rho0, patches

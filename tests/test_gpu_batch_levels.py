@@ -93,22 +93,7 @@ def test_full_batch_workload(C):
 
 # ------------------------------------------------------------------ nested patches
 def _levels_case(N, P, sizes1, n1, sizes2, n2, seed):
-    rho0 = synth.lognormal_density((N, N, N), seed, sigma=2.5)
-    lay1 = synth.patch_layout(rho0, sizes1, n1, seed + 1, margin=1)
-    patches = []
-    for t, (org, s) in enumerate(lay1):
-        blk = rho0[org[2]:org[2] + s // 2, org[1]:org[1] + s // 2, org[0]:org[0] + s // 2]
-        patches.append(dict(parent=-1, origin=org, rho=synth.refine_density(blk, seed + 10 + t)))
-    level1 = list(range(len(patches)))
-    for t1 in level1[:n2]:
-        p = patches[t1]
-        lay2 = synth.patch_layout(p["rho"], sizes2, 1, seed + 100 + t1, margin=1)
-        for t2, (org, s) in enumerate(lay2):
-            blk = p["rho"][org[2]:org[2] + s // 2, org[1]:org[1] + s // 2,
-                           org[0]:org[0] + s // 2]
-            patches.append(dict(parent=t1, origin=org,
-                                rho=synth.refine_density(blk, seed + 200 + t1)))
-    return rho0, patches
+    return synth.nested_case(N, seed, sizes1, n1, sizes2, n2)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -152,3 +137,20 @@ def test_full_nested_workload(C):
         if t % 4 == 0:
             assert sampled_residual(host(g["u"]), p["rho"], h=hp, nsample=20, seed=t,
                                     interior=4, **P) < 1e-6
+
+
+def test_batch_of_small_grids_with_forced_tiling(C):
+    """Grids smaller than the shared-memory tiles (16^3, 32^3) in one batch with
+    the tiled kernels forced on: halo coordinates wrap over several periods."""
+    specs = [dict(n=16, fr0=1e-5, a=1.0, sigma=1.0, box=16.0, seed=31),
+             dict(n=32, fr0=1e-5, a=0.7, sigma=2.0, box=32.0, seed=32),
+             dict(n=16, fr0=1e-6, a=0.5, sigma=1.5, box=16.0, seed=33)]
+    rhos = [synth.lognormal_density((s["n"],) * 3, s["seed"], sigma=s["sigma"]) for s in specs]
+    us = [torch.zeros((s["n"],) * 3, dtype=torch.float64, device="cuda") for s in specs]
+    st, stats = C.solve_batch([dev(r) for r in rhos], us, boxes=[s["box"] for s in specs],
+                              avals=[s["a"] for s in specs], fr0s=[s["fr0"] for s in specs],
+                              omega_m=OM, tol=1e-8, prec="mixed", tiling=1)
+    assert st == 0
+    for s, r, u in zip(specs, rhos, us):
+        ref = O.solve(r, tol=1e-8, box=s["box"], a=s["a"], omega_m=OM, fr0=s["fr0"])
+        assert np.abs(host(u) - ref.u).max() <= 1e-6

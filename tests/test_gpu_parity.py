@@ -351,3 +351,16 @@ def test_mixed_defect_precisions_agree(C, shape):
         assert st == 0 and s.res_rms <= 1e-10
         outs.append(host(u))
     assert np.abs(outs[0] - outs[1]).max() < 1e-9
+
+
+def test_autotune_returns_a_converging_setting(C):
+    shape = (32, 32, 32)
+    rho = _field(shape, 1000, sigma=1.0)
+    best, secs = C.autotune(dev(rho), tol=1e-8, prec="mixed", **CFG1)
+    assert (best["pre"], best["post"]) in [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3)]
+    assert best["temporal_depth"] in (1, 2) and secs > 0
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s = C.solve(dev(rho), u, tol=1e-8, prec="mixed", pre=best["pre"], post=best["post"],
+                    temporal_depth=best["temporal_depth"], **CFG1)
+    assert st == 0
+    assert np.abs(host(u) - O.solve(rho, tol=1e-8, **CFG1).u).max() <= 1e-6
