@@ -91,12 +91,15 @@ __device__ __forceinline__ df df_exp(df u, float ln2h, float ln2l) {
   r.l *= 0.0625f;
   // Horner: 1 + r (1 + r/2 (1 + r/3 (... (1 + r/7))))
   df t = {1.0f, 0.0f};
+#pragma unroll
   for (int k = 7; k >= 1; k--) {
     t = df_mul(t, r);
-    // t = 1 + t / k
-    float q = t.h / (float)k;
-    float rem = fmaf(-q, (float)k, t.h) + t.l;  // t - q k
-    df tq = {q, rem / (float)k};
+    // t = 1 + t / k: q = t.h (1/k) rounded, then the remainder t - q k (exact
+    // by FMA) divided by k gives the low part (two-step division by a float)
+    const float rk = 1.0f / (float)k;  // a constant after unrolling
+    const float q = t.h * rk;
+    const float rem = fmaf(-q, (float)k, t.h) + t.l;
+    df tq = {q, rem * rk};
     t = df_add_f(tq, 1.0f);
   }
   for (int k = 0; k < 4; k++) t = df_mul(t, t);
@@ -108,6 +111,28 @@ __device__ __forceinline__ df df_exp(df u, float ln2h, float ln2l) {
 
 namespace frmg {
 
+// n / d for 0 <= n < 2^31, 1 <= d < 2^31, by one widening multiply and a
+// shift (division by an invariant integer, Granlund and Montgomery 1994):
+// with l = ceil(log2 d), p = 31 + l and m = ceil(2^p / d) (< 2^32),
+// m = 2^p / d + e with 0 <= e < 1, so n m / 2^p = n / d + n e / 2^p where
+// n e / 2^p < 2^-l <= 1 / d: the floor is that of n / d.
+struct FastDiv {
+  unsigned m;
+  int p;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) l++;
+  const int p = 31 + l;
+  const unsigned long long num = 1ull << p;
+  return {(unsigned)((num + d - 1) / d), p};
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, FastDiv f) {
+  return (unsigned)(((unsigned long long)n * f.m) >> f.p);
+}
+
 // Fine-grid state of the double-float outer loop of one grid.
 struct DFGrid {
   float *uh, *ul;        // u = uh + ul
@@ -117,28 +142,94 @@ struct DFGrid {
   long long foff[6];
   long long ncell;
   int n0, n1, n2;
+  FastDiv fd0, fd1;      // division by n0 and n1 (grids below 2^31 cells)
   float ahh, ahl;        // alpha / 2
   float beh, bel;        // beta
+  float gah, gal;        // gamma
 };
 
-// Splits an FP64 value into a double-float pair.
+// Splits an FP64 value into a double-float pair through the FP64 pipe.
 __device__ __forceinline__ df split_d(double v) {
   float h = (float)v;
   return {h, (float)(v - (double)h)};
 }
 
+// The same split with integer operations (the FP64 pipe is narrow): the
+// 53-bit significand m of v = +-m 2^(e-1075) is rounded to its top 24 bits
+// h (hi = h 2^(e-1046)) and the remainder r = m - h 2^29 (|r| <= 2^28) gives
+// lo = r 2^(e-1075), rounded to 24 bits.  Values outside 2^-70 <= |v| < 2^100
+// (zero, tiny, huge, non-finite) take the FP64 route.
+__device__ __forceinline__ df split_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  if (e < 1023 - 70 || e >= 1023 + 100) return split_d(v);
+  const unsigned sgn = (unsigned)(b >> 63) << 31;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned long long h = (m + (1ull << 28)) >> 29;
+  const int r = (int)((long long)m - (long long)(h << 29));
+  int eh = e - 1023;
+  if (h == (1ull << 24)) {
+    h >>= 1;
+    eh += 1;
+  }
+  const float hi = __uint_as_float(sgn | ((unsigned)(eh + 127) << 23) | ((unsigned)h & 0x7fffffu));
+  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);  // 2^(e-1075), exact
+  const float lo = __uint_as_float(__float_as_uint((float)r * scale) ^ sgn);
+  return {hi, lo};
+}
+
+// hi + lo as an FP64 value with integer operations: the significands are
+// aligned (|lo| <= ulp(hi) / 2, so lo sits at least 24 binary places below
+// hi), added as integers and renormalised; rounding is to nearest at the last
+// step only.  Pairs with hi outside 2^-70 <= |hi| < 2^100 use FP64 arithmetic.
+__device__ __forceinline__ double join_bits(float hi, float lo) {
+  const unsigned hb = __float_as_uint(hi), lb = __float_as_uint(lo);
+  const int eh = (int)((hb >> 23) & 0xffu), el = (int)((lb >> 23) & 0xffu);
+  const bool lzero = (lb << 1) == 0;
+  if (eh < 127 - 70 || eh >= 127 + 100 || (!lzero && (el == 0 || eh - el < 24)))
+    return (double)hi + (double)lo;
+  // significands: hi at bit 52 of a 64-bit integer (scaled 2^29), lo below it
+  long long M = (long long)((hb & 0x7fffffu) | 0x800000u) << 29;
+  const long long ml = (long long)((lb & 0x7fffffu) | 0x800000u);
+  const int d = eh - el;  // >= 24
+  long long L;
+  if (lzero) {
+    L = 0;
+  } else if (d <= 29) {
+    L = ml << (29 - d);
+  } else if (d < 64) {
+    const int sh = d - 29;
+    L = (ml + (1ll << (sh - 1))) >> sh;
+  } else {
+    L = 0;
+  }
+  M = ((hb ^ lb) >> 31) ? M - L : M + L;
+  int E = eh - 127 + 1023;
+  if (M >= (1ll << 53)) {
+    M = (M + 1) >> 1;
+    E += 1;
+  } else if (M < (1ll << 52)) {
+    M <<= 1;
+    E -= 1;
+  }
+  const unsigned long long bits = ((unsigned long long)(hb >> 31) << 63) |
+                                  ((unsigned long long)E << 52) |
+                                  ((unsigned long long)M & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
 // State set-up: u (FP64, or zero), e^u and gamma (rho - 1) as double-float.
-__global__ void k_df_init(DFGrid G, const double *u64, const double *rho, double gamma,
-                          int zero_u, float ln2h, float ln2l) {
+__global__ void k_df_init(DFGrid G, const double *u64, const double *rho, int zero_u,
+                          float ln2h, float ln2l) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= G.ncell) return;
-  df u = zero_u ? df{0.f, 0.f} : split_d(u64[t]);
+  df u = zero_u ? df{0.f, 0.f} : split_bits(u64[t]);
   G.uh[t] = u.h;
   G.ul[t] = u.l;
   df B = zero_u ? df{1.f, 0.f} : df_exp(u, ln2h, ln2l);
   G.Bh[t] = B.h;
   G.Bl[t] = B.l;
-  df r = split_d(gamma * (rho[t] - 1.0));
+  const df r = df_mul(df_add_f(split_bits(rho[t]), -1.0f), df{G.gah, G.gal});
   G.rh[t] = r.h;
   G.rl[t] = r.l;
 }
@@ -160,7 +251,7 @@ __global__ void k_df_update(DFGrid G, const float *delta, float ln2h, float ln2l
 __global__ void k_df_final(DFGrid G, double *u64) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= G.ncell) return;
-  u64[t] = (double)G.uh[t] + (double)G.ul[t];
+  u64[t] = join_bits(G.uh[t], G.ul[t]);
 }
 
 // One face of the double-float operator: (B_i + B_j)(u_j - u_i).
@@ -178,16 +269,25 @@ __device__ __forceinline__ df df_face(df ui, df Bi, df uj, df Bj) {
 // double-float, and the set-up of the FP32 correction problem that follows:
 // r32 = -d, background ub32 = hi(u) with E32 = e^{ub32}, delta = x = 0.
 // Block partials (sum d^2, max |d|) go to partial[2 (base + block)].
+template <bool BIG>
 __global__ void __launch_bounds__(256)
     k_df_defect(DFGrid G, float *r32, float *ub32, float *E32, float *delta, float *x32,
                 double *partial, int base, float ln2h, float ln2l, double *dout = nullptr) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float s2 = 0.0f, mx = 0.0f;
   if (t < G.ncell) {
-    const int i = (int)(t % G.n0);
-    const long long rr = t / G.n0;
-    const int j = (int)(rr % G.n1);
-    const int k = (int)(rr / G.n1);
+    int i, j, k;
+    if (BIG) {
+      i = (int)(t % G.n0);
+      const long long rr = t / G.n0;
+      j = (int)(rr % G.n1);
+      k = (int)(rr / G.n1);
+    } else {
+      const unsigned tu = (unsigned)t, q = fdiv(tu, G.fd0), q2 = fdiv(q, G.fd1);
+      i = (int)(tu - q * (unsigned)G.n0);
+      j = (int)(q - q2 * (unsigned)G.n1);
+      k = (int)q2;
+    }
     const df ui = {G.uh[t], G.ul[t]};
     const df Bi = {G.Bh[t], G.Bl[t]};
     df acc = {0.f, 0.f};
@@ -201,7 +301,7 @@ __global__ void __launch_bounds__(256)
       if (f < 2) o = (long long)k * G.n1 + j;
       else if (f < 4) o = (long long)k * G.n0 + i;
       else o = (long long)j * G.n0 + i;
-      const df ub = split_d(G.bnd[G.foff[f] + o]);
+      const df ub = split_bits(G.bnd[G.foff[f] + o]);
       // u_g = 2 u_b - u_i (mask ratio r = -1), b_g = exp(u_g)
       const df ug = df_sub(df{2.f * ub.h, 2.f * ub.l}, ui);
       acc = df_add(acc, df_face(ui, Bi, ug, df_exp(ug, ln2h, ln2l)));
@@ -222,7 +322,7 @@ __global__ void __launch_bounds__(256)
     E32[t] = expf(ui.h);
     delta[t] = 0.0f;
     x32[t] = 0.0f;
-    if (dout) dout[t] = (double)d.h + (double)d.l;
+    if (dout) dout[t] = join_bits(d.h, d.l);
     s2 = dv * dv;
     mx = fabsf(dv);
   }

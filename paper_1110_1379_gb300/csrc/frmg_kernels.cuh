@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <utility>
 
 namespace frmg {
@@ -238,19 +239,32 @@ __device__ __forceinline__ void finish_op(double xi, double Ei, double acc, doub
   dN = ah * dacc - 0.5 * beta * F / s;
 }
 
+// SFU reciprocal and reciprocal square root (PTX rcp.approx / rsqrt.approx,
+// subnormals flushed: every FP32 quantity here is far from the subnormal range).
+__device__ __forceinline__ float sfu_rcp(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ float sfu_rsqrt(float v) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
 __device__ __forceinline__ void finish_op(float xi, float Ei, float acc, float dacc, float ah,
                                           float beta, bool bg, float &N, float &dN) {
   float B1 = 1.0f + xi;
-  float rs = rsqrtf(B1);  // e^{-d/2}
-  float s = B1 * rs;      // e^{d/2}
-  float y = __fdividef(-xi, B1 + s);
-  float F = bg ? rsqrtf(Ei) : 1.0f;
+  float rs = sfu_rsqrt(B1);  // e^{-d/2}
+  float s = B1 * rs;         // e^{d/2}
+  float y = -xi * sfu_rcp(B1 + s);
+  float F = bg ? sfu_rsqrt(Ei) : 1.0f;
   N = ah * acc + beta * F * y;
   dN = ah * dacc - 0.5f * beta * F * rs;
 }
 
 __device__ __forceinline__ double newton_step(double r, double dN) { return -r / dN; }
-__device__ __forceinline__ float newton_step(float r, float dN) { return __fdividef(-r, dN); }
+__device__ __forceinline__ float newton_step(float r, float dN) { return -r * sfu_rcp(dN); }
 
 // A_i (or N_i) and its derivative at cell (i,j,k) from global memory.
 template <typename T, bool BG>
@@ -841,10 +855,7 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
       const long long gi = (zo + gyw[r]) * n0 + gxw0;
       pd[r] = *reinterpret_cast<const float2 *>(uin + gi);
       px[r] = *reinterpret_cast<const float2 *>(xin + gi);
-      if (fin) {
-        const float2 fv = *reinterpret_cast<const float2 *>(fin + gi);
-        pf[r] = make_float2(fs * (fv.x - fo), fs * (fv.y - fo));
-      }
+      if (fin) pf[r] = *reinterpret_cast<const float2 *>(fin + gi);  // scaled at commit
       if (BG) {
         pu[r] = *reinterpret_cast<const float2 *>(ubin + gi);
         pE[r] = *reinterpret_cast<const float2 *>(Ein + gi);
@@ -860,8 +871,8 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
       sd[o + 1] = pd[r].y;
       sx[o] = px[r].x;
       sx[o + 1] = px[r].y;
-      sf[o] = pf[r].x;
-      sf[o + 1] = pf[r].y;
+      sf[o] = fin ? fs * (pf[r].x - fo) : 0.0f;
+      sf[o + 1] = fin ? fs * (pf[r].y - fo) : 0.0f;
       if (BG) {
         sub[o] = pu[r].x;
         sub[o + 1] = pu[r].y;
@@ -957,6 +968,298 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
 }
 
 // ---------------------------------------------------------------------------
+// Tiled FP32 smoother, one full red-black sweep per pass, rows of the tile
+// distributed over warps.
+//
+// Same schedule as k_smooth_tiled with S = 1: a block owns a 64 x TY tile of
+// one grid and an even number zc of planes and marches along z.  At the step
+// that brings in plane p it updates the red cells of plane p-1 on the tile
+// grown by one cell, then the black cells of plane p-2 on the tile, and
+// writes plane p-2 out; the halo of two cells is loaded from the input buffer
+// and the result goes to the other buffer, so the pass equals one sweep of
+// k_smooth.  What differs is the layout and the work mapping:
+//  * each plane is stored split by colour.  The six neighbours of a cell have
+//    the other colour, so for the colour-c cell of x-pair e they are entries
+//    e and e -+ 1 (x), e -+ PX (y) of the other colour's array, and entry e of
+//    it in planes m -+ 1 (z); u and x = expm1(u) are interleaved, so each
+//    neighbour is one 8-byte shared-memory access, stride-1 across a warp;
+//  * a warp updates whole rows of pairs (lane = pair), so the position of the
+//    colour-c cell inside the pair is the same for the whole warp, and only
+//    the one extra cell per row of the grown red region (at the left or right
+//    end of the row) is handled by two warps as a separate column task;
+//  * the global loads of a plane go through fixed per-thread tables (row
+//    offset, flags) built once, and the next plane's wrapped offset advances
+//    by one plane per step.
+template <int TY>
+struct RBCfg {
+  static constexpr int TX = 64, H = 2;
+  static constexpr int LX = TX + 2 * H, LY = TY + 2 * H, PX = LX / 2, PP = PX * LY;
+  static constexpr int NW = TY / 2, NT = 32 * NW;  // warps, threads
+  static constexpr int NLD = (PP + NT - 1) / NT;   // plane-load rounds per thread
+  static constexpr int NS = 4, NF = 3;             // ring slots of (u, x) [and (ub, E)], of f
+  static constexpr int NE = TY + 2;                // edge cells of the red region
+  static constexpr size_t smem(bool bg) {
+    return (size_t)NS * 2 * PP * sizeof(float2) * (bg ? 2 : 1) +
+           (size_t)NF * 2 * PP * sizeof(float);
+  }
+  // resident blocks per SM that shared memory allows (at most 1024 threads)
+  static constexpr int minb(bool bg) {
+    const int bysm = (int)(228 * 1024 / (smem(bg) + 1024));
+    const int byth = 1024 / NT;
+    return bysm < 1 ? 1 : (bysm < byth ? bysm : byth);
+  }
+  static_assert(TY % 4 == 0 && NW >= 4 && NE <= 64, "tile height");
+};
+
+template <bool BG, bool DIR, int TY>
+__global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
+    k_smooth_rb(const Grid<float> *grids, const int *off, int ngrid, int zc, const int *active,
+                int par) {
+  using C = RBCfg<TY>;
+  constexpr int TX = C::TX, H = C::H, PX = C::PX, PP = C::PP, NW = C::NW, NT = C::NT;
+  constexpr int NLD = C::NLD, NS = C::NS;
+  extern __shared__ float4 smem_rb[];
+  float2 *sux = reinterpret_cast<float2 *>(smem_rb);                         // [NS][2][PP]
+  float2 *sgb = sux + NS * 2 * PP;                                          // [NS][2][PP]
+  float *sfv = reinterpret_cast<float *>(sux + NS * 2 * PP * (BG ? 2 : 1));  // [NF][2][PP]
+  const int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<float> &Gg = grids[g];
+  if (!grid_active(active, Gg.field)) return;
+  const float *__restrict__ uin = par ? Gg.u2 : Gg.u;
+  float *__restrict__ uout = par ? Gg.u : Gg.u2;
+  const float *__restrict__ xin = par ? Gg.x2 : Gg.x;
+  float *__restrict__ xout = par ? Gg.x : Gg.x2;
+  const float *__restrict__ fin = Gg.f;
+  const float *__restrict__ ubin = Gg.ubg;
+  const float *__restrict__ Ein = Gg.Ebg;
+  const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap;
+  const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
+  const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
+  int b = blockIdx.x - off[g];
+  const int X0 = (b % ntx) * TX;
+  b /= ntx;
+  const int Y0 = (b % nty) * TY;
+  b /= nty;
+  const int Z0 = b * zc;  // zc is even, so plane p has the parity of its step
+  const int Z1 = min(Z0 + zc, n2);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long plane = (long long)n0 * n1;
+
+  // plane-load tables: pair q = threadIdx.x + k NT of the (TX + 4) x (TY + 4) tile
+  int roff[NLD];
+  unsigned ldf[NLD];  // bit 0: load, bit 1: write out, bit 2: parity of the row
+#pragma unroll
+  for (int k = 0; k < NLD; k++) {
+    const int q = threadIdx.x + k * NT;
+    roff[k] = 0;
+    ldf[k] = 0;
+    if (q < PP) {
+      const int ly = q / PX, px = q - (q / PX) * PX;
+      const int gx = X0 - H + 2 * px, gy = Y0 - H + ly;
+      bool ok;
+      int gxw, gyw;
+      if (DIR) {
+        ok = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
+        gxw = gx;
+        gyw = gy;
+      } else {
+        ok = true;
+        gxw = wrapmod(gx, n0);
+        gyw = wrapmod(gy, n1);
+      }
+      const bool wr = ok && ly >= H && ly < H + TY && px >= 1 && px < PX - 1 && gx < n0 &&
+                      gy < n1;
+      roff[k] = ok ? gyw * n0 + gxw : 0;
+      ldf[k] = (ok ? 1u : 0u) | (wr ? 2u : 0u) | ((unsigned)(ly & 1) << 2);
+    }
+  }
+  float2 pd[NLD], pq[NLD], pf[NLD], pu[NLD], pE[NLD];
+#pragma unroll
+  for (int k = 0; k < NLD; k++) {
+    pd[k] = make_float2(0.f, 0.f);
+    pq[k] = pd[k];
+    pf[k] = pd[k];
+    pu[k] = pd[k];
+    pE[k] = make_float2(1.f, 1.f);
+  }
+  auto fetch = [&](long long zoff) {
+#pragma unroll
+    for (int k = 0; k < NLD; k++) {
+      if (!(ldf[k] & 1u)) continue;
+      const long long gi = zoff + roff[k];
+      pd[k] = *reinterpret_cast<const float2 *>(uin + gi);
+      pq[k] = *reinterpret_cast<const float2 *>(xin + gi);
+      // raw values: arithmetic on them here would wait for the load
+      if (fin) pf[k] = *reinterpret_cast<const float2 *>(fin + gi);
+      if (BG) {
+        pu[k] = *reinterpret_cast<const float2 *>(ubin + gi);
+        pE[k] = *reinterpret_cast<const float2 *>(Ein + gi);
+      }
+    }
+  };
+  // plane of parity pb into (u, x) slot offset so and f slot offset fo2; the
+  // even-x cell of a pair has colour (y + z) & 1
+  auto commit = [&](int pb, int so, int fo2) {
+#pragma unroll
+    for (int k = 0; k < NLD; k++) {
+      const int q = threadIdx.x + k * NT;
+      if (q >= PP) continue;
+      const int c0 = (int)((ldf[k] >> 2) & 1u) ^ pb;
+      const int i0 = so + c0 * PP + q, i1 = so + (c0 ^ 1) * PP + q;
+      sux[i0] = make_float2(pd[k].x, pq[k].x);
+      sux[i1] = make_float2(pd[k].y, pq[k].y);
+      sfv[fo2 + c0 * PP + q] = fin ? fs * (pf[k].x - fo) : 0.0f;
+      sfv[fo2 + (c0 ^ 1) * PP + q] = fin ? fs * (pf[k].y - fo) : 0.0f;
+      if (BG) {
+        sgb[i0] = make_float2(pu[k].x, pE[k].x);
+        sgb[i1] = make_float2(pu[k].y, pE[k].y);
+      }
+    }
+  };
+  // Newton update of the colour-Q cell of pair (ly, px) of plane m; s is its x
+  // position in the pair; oc, om, op are the (u, x) slot offsets of planes m,
+  // m - 1, m + 1 (colour Q's array at oc + Q PP), ofq the f offset.
+  auto update = [&](auto Qc, int ly, int px, int s, int m, int oc, int om, int op, int ofq) {
+    constexpr int Q = decltype(Qc)::value;
+    const int gx = X0 - H + 2 * px + s, gy = Y0 - H + ly;
+    if (DIR && (gx < 0 || gx >= n0 || gy < 0 || gy >= n1)) return;
+    const int e = ly * PX + px;
+    const int cq = Q * PP, co = (Q ^ 1) * PP;
+    const float2 *V = sux + oc + co;
+    const int ex = s ? e + 1 : e - 1;
+    const float2 own = sux[oc + cq + e];
+    const float2 nin = V[e], nxo = V[ex];
+    const float2 nym = V[e - PX], nyp = V[e + PX];
+    const float2 nzm = sux[om + co + e], nzp = sux[op + co + e];
+    float2 gown = make_float2(0.f, 1.f), gin = gown, gxo = gown, gym = gown, gyp = gown,
+           gzm = gown, gzp = gown;
+    if (BG) {
+      const float2 *GV = sgb + oc + co;
+      gown = sgb[oc + cq + e];
+      gin = GV[e];
+      gxo = GV[ex];
+      gym = GV[e - PX];
+      gyp = GV[e + PX];
+      gzm = sgb[om + co + e];
+      gzp = sgb[op + co + e];
+    }
+    const float2 lft = s ? nin : nxo, rgt = s ? nxo : nin;
+    const float2 glft = s ? gin : gxo, grgt = s ? gxo : gin;
+    const float di = own.x, xi = own.y;
+    const float Ei = BG ? gown.y : 1.0f;
+    const float ubi = BG ? gown.x : 0.0f;
+    const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
+    OpAcc<float, BG> A(di, Ei, xi, Bi, ubi);
+    if (DIR && gx == 0)
+      A.ghost(face_value(Gg, 0, gx, gy, m));
+    else
+      A.reg(lft.x, lft.y, glft.x, glft.y);
+    if (DIR && gx == n0 - 1)
+      A.ghost(face_value(Gg, 1, gx, gy, m));
+    else
+      A.reg(rgt.x, rgt.y, grgt.x, grgt.y);
+    if (DIR && gy == 0)
+      A.ghost(face_value(Gg, 2, gx, gy, m));
+    else
+      A.reg(nym.x, nym.y, gym.x, gym.y);
+    if (DIR && gy == n1 - 1)
+      A.ghost(face_value(Gg, 3, gx, gy, m));
+    else
+      A.reg(nyp.x, nyp.y, gyp.x, gyp.y);
+    if (DIR && m == 0)
+      A.ghost(face_value(Gg, 4, gx, gy, m));
+    else
+      A.reg(nzm.x, nzm.y, gzm.x, gzm.y);
+    if (DIR && m == n2 - 1)
+      A.ghost(face_value(Gg, 5, gx, gy, m));
+    else
+      A.reg(nzp.x, nzp.y, gzp.x, gzp.y);
+    float acc, dacc;
+    A.done(acc, dacc);
+    float N, dN;
+    finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
+    float du = newton_step(N - sfv[ofq + cq + e], dN);
+    du = fminf(fmaxf(du, -cap), cap);
+    const float dn = di + du;
+    sux[oc + cq + e] = make_float2(dn, m_expm1(dn));
+  };
+
+  const int P0 = Z0 - H, PE = Z1 + H;
+  constexpr int SLOT = 2 * PP;
+  // wrapped index of the plane being loaded (periodic grids)
+  int pw = DIR ? P0 : wrapmod(P0, n2);
+  if (!DIR || (P0 >= 0 && P0 < n2)) fetch((long long)pw * plane);
+  commit(P0 & 1, 0, 0);
+  __syncthreads();
+  int cur = 0, fcur = 0;  // ring slots of plane p
+  for (int p = P0; p < PE; p++) {
+    const int pb = p & 1;
+    const bool more = p + 1 < PE;
+    pw = DIR ? p + 1 : (pw + 1 == n2 ? 0 : pw + 1);
+    if (more && (!DIR || (pw >= 0 && pw < n2))) fetch((long long)pw * plane);
+    const int o0 = cur * SLOT, o1 = ((cur + 3) & 3) * SLOT, o2 = ((cur + 2) & 3) * SLOT,
+              o3 = ((cur + 1) & 3) * SLOT;  // planes p, p-1, p-2, p-3
+    const int f1 = (fcur == 0 ? 2 : fcur - 1) * SLOT;  // f of plane p-1
+    const int f2 = (fcur == 2 ? 0 : fcur + 1) * SLOT;  // f of plane p-2 (then p+1)
+    // red cells of plane p-1 on the tile grown by one
+    {
+      const int m = p - 1;
+      if (m >= Z0 - 1 && m < Z1 + 1 && (!DIR || (m >= 0 && m < n2))) {
+        const int s = (w + 1 + pb + 1) & 1;  // rows 1 + w + j NW: parity of (ly + m) = s
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          if (j == 2 && w >= 2) break;
+          update(std::integral_constant<int, 0>{}, 1 + w + j * NW, 1 + lane, s, m, o1, o2, o0,
+                 f1);
+        }
+        if (w == 2 || w == 3) {
+          const int idx = (w - 2) * 32 + lane;
+          if (idx < C::NE) {
+            const int ly = 1 + idx;
+            const int se = (ly + m) & 1;
+            update(std::integral_constant<int, 0>{}, ly, se ? 0 : PX - 1, se, m, o1, o2, o0, f1);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // black cells of plane p-2 on the tile
+    {
+      const int m = p - 2;
+      if (m >= Z0 && m < Z1 && (!DIR || (m >= 0 && m < n2))) {
+        const int s = (w + m + 1) & 1;  // rows 2 + w + j NW: parity of (ly + m + 1) = s
+#pragma unroll
+        for (int j = 0; j < 2; j++)
+          update(std::integral_constant<int, 1>{}, 2 + w + j * NW, 1 + lane, s, m, o2, o3, o1,
+                 f2);
+      }
+    }
+    __syncthreads();
+    // plane p-2 is final: write the tile out
+    {
+      const int wz = p - 2;
+      if (wz >= Z0 && wz < Z1) {
+        const long long woff = (long long)wz * plane;
+#pragma unroll
+        for (int k = 0; k < NLD; k++) {
+          if (!(ldf[k] & 2u)) continue;
+          const int q = threadIdx.x + k * NT;
+          const int c0 = (int)((ldf[k] >> 2) & 1u) ^ (wz & 1);
+          const float2 a = sux[o2 + c0 * PP + q];
+          const float2 bb = sux[o2 + (c0 ^ 1) * PP + q];
+          *reinterpret_cast<float2 *>(uout + woff + roff[k]) = make_float2(a.x, bb.x);
+          *reinterpret_cast<float2 *>(xout + woff + roff[k]) = make_float2(a.y, bb.y);
+        }
+      }
+    }
+    if (more) commit(pb ^ 1, o3, f2);
+    __syncthreads();
+    cur = (cur + 1) & 3;
+    fcur = fcur == 2 ? 0 : fcur + 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Tiled FP32 residual + restriction (same result as k_resid_restrict).
 // A block owns a TX x TY fine tile and an even chunk of zc fine planes, marches
 // along z with a ring of 4 planes (tile plus a halo of 2 cells in x, so that
@@ -1047,12 +1350,7 @@ __global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
         const long long gi = zo + pg[k];
         rd[k] = *reinterpret_cast<const float2 *>(uin + gi);
         rx[k] = *reinterpret_cast<const float2 *>(xin + gi);
-        if (fin) {
-          const float2 fv = *reinterpret_cast<const float2 *>(fin + gi);
-          rf[k] = make_float2(fs * (fv.x - fo), fs * (fv.y - fo));
-        } else {
-          rf[k] = make_float2(0.f, 0.f);
-        }
+        if (fin) rf[k] = *reinterpret_cast<const float2 *>(fin + gi);  // scaled at commit
         if (BG) {
           ru[k] = *reinterpret_cast<const float2 *>(ubin + gi);
           rE[k] = *reinterpret_cast<const float2 *>(Ein + gi);
@@ -1070,8 +1368,8 @@ __global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
         sd[o + 1] = rd[k].y;
         sx[o] = rx[k].x;
         sx[o + 1] = rx[k].y;
-        sf[o] = rf[k].x;
-        sf[o + 1] = rf[k].y;
+        sf[o] = fin ? fs * (rf[k].x - fo) : 0.0f;
+        sf[o + 1] = fin ? fs * (rf[k].y - fo) : 0.0f;
         if (BG) {
           sub[o] = ru[k].x;
           sub[o + 1] = ru[k].y;

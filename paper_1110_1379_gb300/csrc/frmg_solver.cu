@@ -83,6 +83,9 @@ struct frmg_ctx {
   std::vector<std::string> prof_names;
   std::vector<long long> prof_count;
   std::vector<double> prof_ms;
+  // stream of solves issued on the legacy default stream (created on first use)
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_in = nullptr, side_out = nullptr;
 };
 
 static cudaEvent_t ev_get(frmg_ctx *c) {
@@ -327,9 +330,11 @@ __global__ void __launch_bounds__(256) k_prep_zero(const double *rho, double gam
   block_reduce2f<256>(s, m, &partial[2 * (base + blockIdx.x)], &partial[2 * (base + blockIdx.x) + 1]);
 }
 
+// Integer tests on the bit pattern (no FP64 instructions): +-0 has all bits
+// but the sign clear.
 __global__ void k_any_nonzero(const double *u, long long n, int *flag) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n && u[t] != 0.0) atomicExch(flag, 1);
+  if (t < n && ((unsigned long long)__double_as_longlong(u[t]) << 1) != 0) atomicExch(flag, 1);
 }
 
 // u += delta in FP64, x = expm1(u).
@@ -386,6 +391,9 @@ struct Problem {
 
 // tile of the tiled smoother (x by y cells; S = 1 and S = 2 sweeps per pass)
 constexpr int kTX = 64, kTY = 16;
+// tile height of k_smooth_rb: 64 x 16 tiles leave room for three resident
+// blocks per SM (more loads in flight than two blocks of 64 x 32 tiles)
+constexpr int kRbTY = 16;
 
 template <typename T>
 struct LevelSet {
@@ -402,6 +410,11 @@ struct LevelSet {
   std::vector<int> off_tile;
   int *d_off_tile = nullptr;
   int nblk_tile = 0;
+  // one-sweep red-black smoother (64 x kRbTY tiles)
+  int zc_rb = 0;
+  std::vector<int> off_rb;
+  int *d_off_rb = nullptr;
+  int nblk_rb = 0;
   // tiled residual + restriction (fine side of a V-cycle level)
   bool rr_tiled = false;
   int zc_rr = 0;
@@ -471,6 +484,24 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 
     ls.d_off_tile = S.get<int>(ng + 1);
     CK(cudaMemcpyAsync(ls.d_off_tile, ls.off_tile.data(), (ng + 1) * sizeof(int),
                        cudaMemcpyHostToDevice, st));
+    {
+      long long t2 = 0;
+      for (int g = 0; g < ng; g++)
+        t2 += (long long)((ls.h[g].n0 + kTX - 1) / kTX) * ((ls.h[g].n1 + kRbTY - 1) / kRbTY);
+      long long nz2 = std::max<long long>(1, (1216 + t2 - 1) / t2);
+      ls.zc_rb = (int)std::max<long long>(std::min(32, maxn2), (maxn2 + nz2 - 1) / nz2);
+      ls.off_rb.assign(ng + 1, 0);
+      for (int g = 0; g < ng; g++) {
+        const Grid<T> &G = ls.h[g];
+        int nt = ((G.n0 + kTX - 1) / kTX) * ((G.n1 + kRbTY - 1) / kRbTY) *
+                 ((G.n2 + ls.zc_rb - 1) / ls.zc_rb);
+        ls.off_rb[g + 1] = ls.off_rb[g] + nt;
+      }
+      ls.nblk_rb = ls.off_rb[ng];
+      ls.d_off_rb = S.get<int>(ng + 1);
+      CK(cudaMemcpyAsync(ls.d_off_rb, ls.off_rb.data(), (ng + 1) * sizeof(int),
+                         cudaMemcpyHostToDevice, st));
+    }
   }
   if (ls.tiled) {
     // tiled residual + restriction: even z-chunks (coarse planes stay whole)
@@ -681,13 +712,36 @@ static void launch_rr_tiled(frmg_ctx *ctx, LevelSet<float> &F, LevelSet<float> &
     launch_rr_k<BG, false>(ctx, F, C, active, fpar, cpar, partial, st);
 }
 
+template <bool BG, bool DIR>
+static void launch_rb_k(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
+                        cudaStream_t st) {
+  constexpr int TY = kRbTY;
+  using RC = RBCfg<TY>;
+  size_t sm = RC::smem(BG);
+  static bool attr_set = false;
+  if (!attr_set) {
+    CK(cudaFuncSetAttribute(k_smooth_rb<BG, DIR, TY>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_set = true;
+  }
+  k_smooth_rb<BG, DIR, TY><<<s.nblk_rb, RC::NT, sm, st>>>(s.d, s.d_off_rb, s.size(), s.zc_rb,
+                                                           active, par);
+}
+
 template <bool BG, int S>
 static void launch_tiled(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
                          cudaStream_t st) {
-  if (s.dirichlet)
-    launch_tiled_k<BG, true, S>(ctx, s, active, par, st);
-  else
-    launch_tiled_k<BG, false, S>(ctx, s, active, par, st);
+  if constexpr (S == 1) {
+    if (s.dirichlet)
+      launch_rb_k<BG, true>(ctx, s, active, par, st);
+    else
+      launch_rb_k<BG, false>(ctx, s, active, par, st);
+  } else {
+    if (s.dirichlet)
+      launch_tiled_k<BG, true, S>(ctx, s, active, par, st);
+    else
+      launch_tiled_k<BG, false, S>(ctx, s, active, par, st);
+  }
 }
 
 // Passes of the tiled smoother (sweeps per pass) for the pre- and post-smoothing
@@ -827,6 +881,69 @@ static void level_norms(frmg_ctx *ctx, LevelSet<T> &s, T *const *dout, const int
   }
 }
 
+// One V-cycle as a CUDA graph: the first call launches directly (it also sets
+// kernel attributes), the second captures the launches on the stream and
+// instantiates them, later calls replay.  A V-cycle issues the same kernels
+// with the same arguments every time (the pass plan returns every level to
+// its starting buffer; per-field active flags are read from device memory),
+// so the replay is exact.  Not used on the legacy default stream (it cannot be
+// captured) or while per-kernel profiling is on.
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long nlaunch = 0;
+  int calls = 0;
+  bool disabled = false;
+  ~CycleGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+template <typename F>
+static void run_cycle(frmg_ctx *ctx, CycleGraph &g, bool use, cudaStream_t st, F &&launch) {
+  if (!use || ctx->prof || g.disabled || st == nullptr) {
+    launch();
+    return;
+  }
+  if (g.exec) {
+    CK(cudaGraphLaunch(g.exec, st));
+    ctx->launches += g.nlaunch;
+    return;
+  }
+  if (g.calls++ == 0) {
+    launch();
+    return;
+  }
+  long long l0 = ctx->launches;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    g.disabled = true;
+    launch();
+    return;
+  }
+  try {
+    launch();
+  } catch (...) {
+    cudaGraph_t gr;
+    cudaStreamEndCapture(st, &gr);
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    throw;
+  }
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamEndCapture(st, &graph));
+  cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g.exec = nullptr;
+    g.disabled = true;
+    launch();
+    return;
+  }
+  g.nlaunch = ctx->launches - l0;
+  CK(cudaGraphLaunch(g.exec, st));
+}
+
 // Fine-grid residual norms accumulated by the last depth-0 residual+restriction
 // (after pre-smoothing of the last V-cycle); out[p] = rms per problem (NaN for
 // problems without a coarser level).
@@ -861,6 +978,7 @@ struct SolveCfg {
   int tdepth;
   int tiling;
   int defect_fp64;   // mixed: 1 = native FP64 defect/update, 0 = double-float
+  int use_graph;     // V-cycles replayed as CUDA graphs
 };
 
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
@@ -898,12 +1016,13 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
     if (bad(nr[2 * pi])) throw FrError{FR_EDIVERGED, "non-finite initial residual"};
   }
   int maxc = cfg.fixed_cycles > 0 ? cfg.fixed_cycles : cfg.max_vcycles;
+  CycleGraph graph;
   for (int cyc = 0; cyc < maxc; cyc++) {
     int nact = 0;
     for (int v : act) nact += v;
     if (nact == 0) break;
     CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
-    vcycle<double, false>(ctx, H, 0, co, active, st);
+    run_cycle(ctx, graph, cfg.use_graph, st, [&]() { vcycle<double, false>(ctx, H, 0, co, active, st); });
     level_norms<double, false>(ctx, H.all[0], nullptr, nullptr, st, nr);
     for (int pi = 0; pi < np; pi++) {
       if (!act[pi]) continue;
@@ -968,6 +1087,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
     }
   };
   // inner V-cycles with the fused fine-residual norm as the stopping signal
+  CycleGraph gr_bg, gr_plain;
   // Stopping signal: the fine residual after pre-smoothing of each cycle (fused
   // into the residual + restriction kernel).  Successive values are compared
   // (the first cycle always runs); a ratio above 0.75 means FP32 rounding has
@@ -982,9 +1102,11 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
     std::vector<int> iact = act;
     for (int k = 0; k < kmax; k++) {
       if (bg)
-        vcycle<float, true>(ctx, H, 0, co, active, st);
+        run_cycle(ctx, gr_bg, cfg.use_graph, st,
+                  [&]() { vcycle<float, true>(ctx, H, 0, co, active, st); });
       else
-        vcycle<float, false>(ctx, H, 0, co, active, st);
+        run_cycle(ctx, gr_plain, cfg.use_graph, st,
+                  [&]() { vcycle<float, false>(ctx, H, 0, co, active, st); });
       bool go = false;
       for (int pi = 0; pi < np; pi++)
         if (iact[pi]) {
@@ -1125,6 +1247,35 @@ static void split_host(double v, float &h, float &l) {
   l = (float)(v - (double)h);
 }
 
+// Sizes and constants of a double-float fine-grid state (arrays set by the caller).
+static void dfgrid_setup(DFGrid &g, const int n[3], const Consts &k, const double *bnd) {
+  memset(&g, 0, sizeof(g));
+  g.n0 = n[0];
+  g.n1 = n[1];
+  g.n2 = n[2];
+  g.ncell = (long long)g.n0 * g.n1 * g.n2;
+  g.fd0 = make_fastdiv((unsigned)g.n0);
+  g.fd1 = make_fastdiv((unsigned)g.n1);
+  g.bnd = bnd;
+  face_offsets(n, g.foff);
+  split_host(0.5 * k.alpha, g.ahh, g.ahl);
+  split_host(k.beta, g.beh, g.bel);
+  split_host(k.gamma, g.gah, g.gal);
+}
+
+// Defect kernel for one grid: 32-bit index decomposition below 2^31 cells.
+static void launch_df_defect(frmg_ctx *ctx, const DFGrid &g, float *r32, float *ub32, float *E32,
+                             float *delta, float *x32, double *partial, int base, float ln2h,
+                             float ln2l, double *dout, cudaStream_t st) {
+  if (g.ncell < (1ll << 31))
+    k_df_defect<false><<<nblocks(g.ncell), 256, 0, st>>>(g, r32, ub32, E32, delta, x32, partial,
+                                                         base, ln2h, ln2l, dout);
+  else
+    k_df_defect<true><<<nblocks(g.ncell), 256, 0, st>>>(g, r32, ub32, E32, delta, x32, partial,
+                                                        base, ln2h, ln2l, dout);
+  CK_LAUNCH(ctx);
+}
+
 // Mixed precision with the FP64-accurate quantities in double-float (see
 // frmg_df.cuh): the same outer loop as solve_mixed, with the defect, the
 // update and the convergence test evaluated on FP32 pipes at ~48-bit accuracy.
@@ -1141,21 +1292,13 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   std::vector<int> boff(np + 1, 0);
   for (int pi = 0; pi < np; pi++) {
     DFGrid &g = D[pi];
-    memset(&g, 0, sizeof(g));
-    g.n0 = P[pi].n[0];
-    g.n1 = P[pi].n[1];
-    g.n2 = P[pi].n[2];
-    g.ncell = (long long)g.n0 * g.n1 * g.n2;
+    dfgrid_setup(g, P[pi].n, P[pi].k, P[pi].bnd);
     g.uh = S.get<float>(g.ncell);
     g.ul = S.get<float>(g.ncell);
     g.Bh = S.get<float>(g.ncell);
     g.Bl = S.get<float>(g.ncell);
     g.rh = S.get<float>(g.ncell);
     g.rl = S.get<float>(g.ncell);
-    g.bnd = P[pi].bnd;
-    face_offsets(P[pi].n, g.foff);
-    split_host(0.5 * P[pi].k.alpha, g.ahh, g.ahl);
-    split_host(P[pi].k.beta, g.beh, g.bel);
     boff[pi + 1] = boff[pi] + nblocks(g.ncell);
   }
   double *partial = S.get<double>(2 * (size_t)boff[np]);
@@ -1173,8 +1316,8 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   CK(cudaStreamSynchronize(st));
   for (int pi = 0; pi < np; pi++) {
     PROF("df_init");
-    k_df_init<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], P[pi].u, P[pi].rho, P[pi].k.gamma,
-                                                    !nonzero, ln2h, ln2l);
+    k_df_init<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], P[pi].u, P[pi].rho, !nonzero, ln2h,
+                                                    ln2l);
     CK_LAUNCH(ctx);
   }
   auto read_norms = [&](std::vector<double> &out) {
@@ -1214,6 +1357,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
       CK_LAUNCH(ctx);
     }
   };
+  CycleGraph gr_bg, gr_plain;
   // Stopping signal: the fine residual after pre-smoothing of each cycle (fused
   // into the residual + restriction kernel).  Successive values are compared
   // (the first cycle always runs); a ratio above 0.75 means FP32 rounding has
@@ -1228,9 +1372,11 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
     std::vector<int> iact = act;
     for (int k = 0; k < kmax; k++) {
       if (bg)
-        vcycle<float, true>(ctx, H, 0, co, active, st);
+        run_cycle(ctx, gr_bg, cfg.use_graph, st,
+                  [&]() { vcycle<float, true>(ctx, H, 0, co, active, st); });
       else
-        vcycle<float, false>(ctx, H, 0, co, active, st);
+        run_cycle(ctx, gr_plain, cfg.use_graph, st,
+                  [&]() { vcycle<float, false>(ctx, H, 0, co, active, st); });
       bool go = false;
       for (int pi = 0; pi < np; pi++)
         if (iact[pi]) {
@@ -1285,11 +1431,9 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
         if (!act[pi]) continue;
         Grid<float> &G = H.lev[pi][0];
         PROF("df_defect");
-        k_df_defect<<<nblocks(G.ncell), 256, 0, st>>>(D[pi], const_cast<float *>(G.f),
-                                                      H.bg_u[pi], H.bg_E[pi], H.cur_u(pi, 0),
-                                                      H.cur_x(pi, 0), partial, boff[pi], ln2h,
-                                                      ln2l);
-        CK_LAUNCH(ctx);
+        launch_df_defect(ctx, D[pi], const_cast<float *>(G.f), H.bg_u[pi], H.bg_E[pi],
+                         H.cur_u(pi, 0), H.cur_x(pi, 0), partial, boff[pi], ln2h, ln2l, nullptr,
+                         st);
       }
       read_norms(nr);
       int nact = 0;
@@ -1380,11 +1524,14 @@ static void finish(frmg_ctx *ctx, std::vector<Staged> &back, cudaStream_t st) {
 }
 
 // density validation (NaN always rejected; negative unless allowed)
+// (bit tests: exponent all ones = Inf/NaN; sign set on a non-zero = negative)
 __global__ void k_check_density(const double *rho, long long n, int allow_neg, int *bad) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  double v = rho[t];
-  if (!(v == v) || isinf(v) || (!allow_neg && v < 0.0)) atomicExch(bad, 1);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(rho[t]);
+  const bool nonfinite = ((b >> 52) & 0x7ffu) == 0x7ffu;
+  const bool negative = (b >> 63) && (b << 1) != 0;
+  if (nonfinite || (!allow_neg && negative)) atomicExch(bad, 1);
 }
 
 static void validate_density(frmg_ctx *ctx, Scope &S, const double *rho, long long n,
@@ -1406,11 +1553,38 @@ static fr_opts resolve_opts(const fr_opts *o) {
   return r;
 }
 
+// A solve issued on the legacy default stream runs on a stream of the context
+// instead, because the legacy stream cannot be captured into a graph: the side
+// stream waits for the caller's earlier work and the caller's stream waits for
+// the solve, so the ordering seen by the caller is unchanged.
+struct SideStream {
+  frmg_ctx *ctx;
+  cudaStream_t caller, st;
+  SideStream(frmg_ctx *c, cudaStream_t s, bool want) : ctx(c), caller(s), st(s) {
+    if (s != nullptr || !want || c->prof) return;
+    if (!c->side) {
+      CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&c->side_in, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&c->side_out, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(c->side_in, s));
+    CK(cudaStreamWaitEvent(c->side, c->side_in, 0));
+    st = c->side;
+  }
+  ~SideStream() {
+    if (st == caller) return;
+    cudaEventRecord(ctx->side_out, st);
+    cudaStreamWaitEvent(caller, ctx->side_out, 0);
+  }
+};
+
 static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &o, double tol,
-                         std::vector<fr_stats> &stats, cudaStream_t st, int fixed = 0) {
+                         std::vector<fr_stats> &stats, cudaStream_t st_caller, int fixed = 0) {
+  SideStream side(ctx, st_caller, o.use_graph != 0);
+  cudaStream_t st = side.st;
   SolveCfg cfg{tol, o.max_vcycles, o.pre, o.post, o.newton_step_cap, o.inner_cycles,
                o.max_outer, fixed, o.temporal_depth <= 0 ? 1 : o.temporal_depth, o.tiling,
-               o.defect_precision};
+               o.defect_precision, o.use_graph};
   if (o.defect_precision < 0 || o.defect_precision > 1) einval("defect_precision must be 0 or 1");
   if (cfg.tdepth > 2) einval("temporal_depth must be 0, 1 or 2");
   if (o.pre < 0 || o.post < 0 || o.max_vcycles < 0 || !(o.newton_step_cap > 0) ||
@@ -1614,6 +1788,12 @@ void fr_ctx_destroy(frmg_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   prof_harvest(c);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+    cudaEventDestroy(c->side_in);
+    cudaEventDestroy(c->side_out);
+  }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   for (auto &kv : c->sizes) cudaFree(kv.first);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -2076,8 +2256,7 @@ int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, cons
     upload_set(S, ls, st);
     if (tiled && !ls.tiled_ok) einval("tiled smoothing needs at least 16 cells a side");
     ls.tiled = tiled != 0;
-    std::vector<int> plan;
-    for (int n = nsweeps; n > 0; n -= 2) plan.push_back(n >= 2 ? 2 : 1);
+    std::vector<int> plan(nsweeps, 1);  // one sweep per tiled pass, as in the solves
     int par = 0;
     if (bg)
       smooth_set<float, true>(ctx, ls, nsweeps, &plan, nullptr, par, st);
@@ -2135,32 +2314,22 @@ int fr_residual_df(frmg_ctx *ctx, const double *u, const double *density, const 
     const double *dub = stage(S, back, ub, ub ? face_total(dims) : 0, true, false, st);
     double *dd = stage(S, back, d, nc, false, true, st);
     DFGrid g;
-    memset(&g, 0, sizeof(g));
-    g.n0 = dims[0];
-    g.n1 = dims[1];
-    g.n2 = dims[2];
-    g.ncell = nc;
+    dfgrid_setup(g, dims, k, dub);
     g.uh = S.get<float>(nc);
     g.ul = S.get<float>(nc);
     g.Bh = S.get<float>(nc);
     g.Bl = S.get<float>(nc);
     g.rh = S.get<float>(nc);
     g.rl = S.get<float>(nc);
-    g.bnd = dub;
-    face_offsets(dims, g.foff);
-    split_host(0.5 * k.alpha, g.ahh, g.ahl);
-    split_host(k.beta, g.beh, g.bel);
     float ln2h, ln2l;
     split_host(std::log(2.0), ln2h, ln2l);
     (void)p;
-    k_df_init<<<nblocks(nc), 256, 0, st>>>(g, du, dr, k.gamma, 0, ln2h, ln2l);
+    k_df_init<<<nblocks(nc), 256, 0, st>>>(g, du, dr, 0, ln2h, ln2l);
     CK_LAUNCH(ctx);
     float *scratch = S.get<float>(5 * (size_t)nc);
     double *partial = S.get<double>(2 * (size_t)nblocks(nc));
-    k_df_defect<<<nblocks(nc), 256, 0, st>>>(g, scratch, scratch + nc, scratch + 2 * nc,
-                                             scratch + 3 * nc, scratch + 4 * nc, partial, 0,
-                                             ln2h, ln2l, dd);
-    CK_LAUNCH(ctx);
+    launch_df_defect(ctx, g, scratch, scratch + nc, scratch + 2 * nc, scratch + 3 * nc,
+                     scratch + 4 * nc, partial, 0, ln2h, ln2l, dd, st);
     finish(ctx, back, st);
     return FR_OK;
   });
