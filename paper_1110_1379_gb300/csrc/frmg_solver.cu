@@ -410,11 +410,12 @@ struct LevelSet {
   std::vector<int> off_tile;
   int *d_off_tile = nullptr;
   int nblk_tile = 0;
-  // one-sweep red-black smoother (64 x kRbTY tiles)
-  int zc_rb = 0;
-  std::vector<int> off_rb;
-  int *d_off_rb = nullptr;
-  int nblk_rb = 0;
+  // one-sweep red-black smoother (64 x kRbTY tiles); [0] plain, [1] correction
+  // form (their occupancies differ, and with them the best z-chunk)
+  int zc_rb[2] = {0, 0};
+  std::vector<int> off_rb[2];
+  int *d_off_rb[2] = {nullptr, nullptr};
+  int nblk_rb[2] = {0, 0};
   // tiled residual + restriction (fine side of a V-cycle level)
   bool rr_tiled = false;
   int zc_rr = 0;
@@ -427,6 +428,64 @@ struct LevelSet {
   bool empty() const { return h.empty(); }
   int size() const { return (int)h.size(); }
 };
+
+static int sm_count() {
+  static int n = 0;
+  if (n <= 0) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Resident blocks per SM of a kernel launched with `threads` threads and
+// `smem` bytes of dynamic shared memory (raises the kernel's shared-memory
+// limit to `smem` first, as its launch does).
+template <typename K>
+static int resident_blocks(K kernel, int threads, size_t smem) {
+  CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int nb = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem));
+  return std::max(nb, 1);
+}
+
+// z-chunk length of a tiled z-marching kernel.  A block streams its chunk
+// plus `halo` planes; with every block costing the same per plane, a launch
+// takes about (waves of resident blocks) x (chunk + halo) plane-times.  The
+// chunk (even if `even`) minimising that over the set's grids (tiles[g] tiles
+// per plane, n2[g] planes) is returned; ties go to the longer chunk.
+static int pick_chunk(const std::vector<long long> &tiles, const std::vector<int> &n2, long long slots,
+                      int halo, bool even) {
+  int maxn2 = 1;
+  for (int v : n2) maxn2 = std::max(maxn2, v);
+  double best = 1e300;
+  int bz = maxn2, prev = -1;
+  for (int c = 1; c <= maxn2; c++) {
+    int zc = (maxn2 + c - 1) / c;
+    if (even) zc = (zc + 1) & ~1;
+    if (zc == prev) continue;
+    prev = zc;
+    double work = 0.0;  // block-planes of the launch
+    for (size_t g = 0; g < tiles.size(); g++) {
+      const long long nb = tiles[g] * ((n2[g] + zc - 1) / zc);
+      work += (double)nb * (std::min(zc, n2[g]) + halo);
+    }
+    const double per = zc + halo;
+    const double cost = std::ceil(work / ((double)slots * per)) * per;
+    if (cost < best - 1e-9) {
+      best = cost;
+      bz = zc;
+    }
+  }
+  return bz;
+}
+
+template <bool BG, bool DIR>
+static long long rb_slots();
+template <bool DIR>
+static long long rr_slots();
 
 template <typename T>
 static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 0) {
@@ -484,30 +543,39 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 
     ls.d_off_tile = S.get<int>(ng + 1);
     CK(cudaMemcpyAsync(ls.d_off_tile, ls.off_tile.data(), (ng + 1) * sizeof(int),
                        cudaMemcpyHostToDevice, st));
-    {
-      long long t2 = 0;
-      for (int g = 0; g < ng; g++)
-        t2 += (long long)((ls.h[g].n0 + kTX - 1) / kTX) * ((ls.h[g].n1 + kRbTY - 1) / kRbTY);
-      long long nz2 = std::max<long long>(1, (1216 + t2 - 1) / t2);
-      ls.zc_rb = (int)std::max<long long>(std::min(32, maxn2), (maxn2 + nz2 - 1) / nz2);
-      ls.off_rb.assign(ng + 1, 0);
+    if constexpr (sizeof(T) == 4) {
+      std::vector<long long> tl(ng);
+      std::vector<int> n2s(ng);
       for (int g = 0; g < ng; g++) {
-        const Grid<T> &G = ls.h[g];
-        int nt = ((G.n0 + kTX - 1) / kTX) * ((G.n1 + kRbTY - 1) / kRbTY) *
-                 ((G.n2 + ls.zc_rb - 1) / ls.zc_rb);
-        ls.off_rb[g + 1] = ls.off_rb[g] + nt;
+        tl[g] = (long long)((ls.h[g].n0 + kTX - 1) / kTX) * ((ls.h[g].n1 + kRbTY - 1) / kRbTY);
+        n2s[g] = ls.h[g].n2;
       }
-      ls.nblk_rb = ls.off_rb[ng];
-      ls.d_off_rb = S.get<int>(ng + 1);
-      CK(cudaMemcpyAsync(ls.d_off_rb, ls.off_rb.data(), (ng + 1) * sizeof(int),
-                         cudaMemcpyHostToDevice, st));
+      for (int v = 0; v < 2; v++) {
+        const long long slots = ls.dirichlet ? (v ? rb_slots<true, true>() : rb_slots<false, true>())
+                                             : (v ? rb_slots<true, false>() : rb_slots<false, false>());
+        ls.zc_rb[v] = pick_chunk(tl, n2s, slots, 4, false);
+        ls.off_rb[v].assign(ng + 1, 0);
+        for (int g = 0; g < ng; g++)
+          ls.off_rb[v][g + 1] =
+              ls.off_rb[v][g] + (int)(tl[g] * ((n2s[g] + ls.zc_rb[v] - 1) / ls.zc_rb[v]));
+        ls.nblk_rb[v] = ls.off_rb[v][ng];
+        ls.d_off_rb[v] = S.get<int>(ng + 1);
+        CK(cudaMemcpyAsync(ls.d_off_rb[v], ls.off_rb[v].data(), (ng + 1) * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+      }
     }
   }
   if (ls.tiled) {
     // tiled residual + restriction: even z-chunks (coarse planes stay whole)
-    long long nz = std::max<long long>(1, (1216 + txy - 1) / txy);
-    int zc = (int)std::max<long long>(std::min(32, maxn2), (maxn2 + nz - 1) / nz);
-    ls.zc_rr = (zc + 1) & ~1;
+    if constexpr (sizeof(T) == 4) {
+      std::vector<long long> tl(ng);
+      std::vector<int> n2s(ng);
+      for (int g = 0; g < ng; g++) {
+        tl[g] = (long long)((ls.h[g].n0 + kTX - 1) / kTX) * ((ls.h[g].n1 + kTY - 1) / kTY);
+        n2s[g] = ls.h[g].n2;
+      }
+      ls.zc_rr = pick_chunk(tl, n2s, ls.dirichlet ? rr_slots<true>() : rr_slots<false>(), 2, true);
+    }
     ls.off_rr.assign(ng + 1, 0);
     for (int g = 0; g < ng; g++) {
       const Grid<T> &G = ls.h[g];
@@ -724,8 +792,31 @@ static void launch_rb_k(frmg_ctx *ctx, LevelSet<float> &s, const int *active, in
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
-  k_smooth_rb<BG, DIR, TY><<<s.nblk_rb, RC::NT, sm, st>>>(s.d, s.d_off_rb, s.size(), s.zc_rb,
-                                                           active, par);
+  constexpr int v = BG ? 1 : 0;
+  k_smooth_rb<BG, DIR, TY><<<s.nblk_rb[v], RC::NT, sm, st>>>(s.d, s.d_off_rb[v], s.size(),
+                                                              s.zc_rb[v], active, par);
+}
+
+template <bool BG, bool DIR>
+static long long rb_slots() {
+  static long long slots = 0;
+  if (!slots) {
+    using RC = RBCfg<kRbTY>;
+    slots = (long long)sm_count() *
+            resident_blocks(k_smooth_rb<BG, DIR, kRbTY>, RC::NT, RC::smem(BG));
+  }
+  return slots;
+}
+
+template <bool DIR>
+static long long rr_slots() {
+  static long long slots = 0;
+  if (!slots) {
+    using RC = RRCfg<kTX, kTY>;
+    slots = (long long)sm_count() *
+            resident_blocks(k_resid_restrict_tiled<false, DIR, kTX, kTY>, RC::NT, RC::smem(false));
+  }
+  return slots;
 }
 
 template <bool BG, int S>
