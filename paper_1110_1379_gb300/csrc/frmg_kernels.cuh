@@ -80,6 +80,11 @@ __device__ __forceinline__ double m_sqrt(double v) { return sqrt(v); }
 __device__ __forceinline__ float m_rsqrt(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double m_rsqrt(double v) { return rsqrt(v); }
 
+__device__ __forceinline__ int wrapmod(int v, int n) {
+  int r = v % n;
+  return r < 0 ? r + n : r;
+}
+
 __device__ __forceinline__ int find_grid(const int *off, int ngrid, int b) {
   int lo = 0, hi = ngrid;  // off[lo] <= b < off[hi]
   while (hi - lo > 1) {
@@ -588,6 +593,123 @@ __global__ void __launch_bounds__(256) k_prolong(const Grid<T> *fine, const Grid
     }
 }
 
+// Tiled FP32 prolongation and correction (same interpolation as k_prolong,
+// evaluated in the order z, y, x): a block owns a 64 x 16 fine tile (32 x 8
+// coarse cells) and a chunk of kc coarse planes.  The correction
+// e = u^H - R u^h of the coarse tile plus a one-cell halo is staged in shared
+// memory for planes K-1, K, K+1 (ring of three); for each of the fine planes
+// 2K and 2K+1 the z-interpolated coarse plane is formed once in shared memory,
+// and each thread corrects its fine x-pairs (y- then x-interpolation,
+// weights 3/4 and 1/4 per axis) with 8-byte loads and stores, refreshing
+// x = expm1(u).  Patches: coarse cells outside the grid contribute 0.
+constexpr int kPlTX = 64, kPlTY = 16;
+template <bool DIR>
+__global__ void __launch_bounds__(256)
+    k_prolong_tiled(const Grid<float> *fine, const Grid<float> *coarse, const int *off, int ngrid,
+                    int kc, const int *active, int fpar, int cpar) {
+  constexpr int CX = kPlTX / 2 + 2, CY = kPlTY / 2 + 2, CP = CX * CY;
+  constexpr int NQ = (CP + 255) / 256;
+  __shared__ float se[3][CP];
+  __shared__ float sz[CP];
+  const int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<float> &Fg = fine[g];
+  const Grid<float> &Cg = coarse[g];
+  if (!grid_active(active, Fg.field)) return;
+  const int n0 = Fg.n0, n1 = Fg.n1;
+  const int c0 = Cg.n0, c1 = Cg.n1, c2 = Cg.n2;
+  const float *__restrict__ uH = cpar ? Cg.u2 : Cg.u;
+  const float *__restrict__ uR = Cg.uR;
+  float *__restrict__ uf = fpar ? Fg.u2 : Fg.u;
+  float *__restrict__ xf = fpar ? Fg.x2 : Fg.x;
+  const int ntx = (n0 + kPlTX - 1) / kPlTX, nty = (n1 + kPlTY - 1) / kPlTY;
+  int b = blockIdx.x - off[g];
+  const int X0 = (b % ntx) * kPlTX;
+  b /= ntx;
+  const int Y0 = (b % nty) * kPlTY;
+  b /= nty;
+  const int K0 = b * kc, K1 = min(K0 + kc, c2);
+  // coarse staging table: entry q = threadIdx.x + k 256 of the CX x CY tile
+  int qoff[NQ];
+  bool qok[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; k++) {
+    const int q = threadIdx.x + k * 256;
+    qoff[k] = 0;
+    qok[k] = false;
+    if (q < CP) {
+      int I = X0 / 2 - 1 + q % CX, J = Y0 / 2 - 1 + q / CX;
+      if (DIR) {
+        qok[k] = I >= 0 && I < c0 && J >= 0 && J < c1;
+      } else {
+        I = wrapmod(I, c0);
+        J = wrapmod(J, c1);
+        qok[k] = true;
+      }
+      qoff[k] = J * c0 + I;
+    }
+  }
+  const long long cplane = (long long)c0 * c1;
+  // wrapped index of the next coarse plane to stage
+  int kw = DIR ? K0 - 1 : wrapmod(K0 - 1, c2);
+  auto stage = [&](int slot, int K) {
+    const bool vz = !DIR || (K >= 0 && K < c2);
+    const long long zo = (long long)kw * cplane;
+#pragma unroll
+    for (int k = 0; k < NQ; k++) {
+      const int q = threadIdx.x + k * 256;
+      if (q >= CP) continue;
+      float e = 0.0f;
+      if (qok[k] && vz) {
+        const long long i = zo + qoff[k];
+        e = uH[i] - uR[i];
+      }
+      se[slot][q] = e;
+    }
+    kw = DIR ? kw + 1 : (kw + 1 == c2 ? 0 : kw + 1);
+  };
+  const int lane = threadIdx.x & 31, r0 = threadIdx.x >> 5;  // pair, first row
+  const long long fplane = (long long)n0 * n1;
+  const float w3 = 0.75f, w1 = 0.25f;
+  stage(0, K0 - 1);
+  stage(1, K0);
+  int sm = 0, sc = 1, sp = 2;  // ring slots of planes K-1, K, K+1
+  for (int K = K0; K < K1; K++) {
+    stage(sp, K + 1);
+    __syncthreads();
+#pragma unroll
+    for (int cz = 0; cz < 2; cz++) {
+      const int so = cz ? sp : sm;
+      for (int q = threadIdx.x; q < CP; q += 256) sz[q] = w3 * se[sc][q] + w1 * se[so][q];
+      __syncthreads();
+      const int k = 2 * K + cz;
+      const int fx = X0 + 2 * lane;
+#pragma unroll
+      for (int rr = 0; rr < 2; rr++) {
+        const int row = r0 + 8 * rr;
+        const int j = Y0 + row;
+        if (j >= n1 || fx >= n0) continue;
+        const int jy = row / 2 + 1, jy2 = (row & 1) ? jy + 1 : jy - 1;
+        const int ix = lane + 1;
+        const float *za = sz + jy * CX, *zb = sz + jy2 * CX;
+        const float em = w3 * za[ix - 1] + w1 * zb[ix - 1];
+        const float e0 = w3 * za[ix] + w1 * zb[ix];
+        const float ep = w3 * za[ix + 1] + w1 * zb[ix + 1];
+        const long long fi = (long long)k * fplane + (long long)j * n0 + fx;
+        const float2 u = *reinterpret_cast<const float2 *>(uf + fi);
+        const float un0 = u.x + (w3 * e0 + w1 * em);
+        const float un1 = u.y + (w3 * e0 + w1 * ep);
+        *reinterpret_cast<float2 *>(uf + fi) = make_float2(un0, un1);
+        *reinterpret_cast<float2 *>(xf + fi) = make_float2(m_expm1(un0), m_expm1(un1));
+      }
+      __syncthreads();
+    }
+    const int t = sm;
+    sm = sc;
+    sc = sp;
+    sp = t;
+  }
+}
+
 // Block sum of two values (all threads get the result).
 template <int NT>
 __device__ __forceinline__ void block_sum2(double a, double b, double &ra, double &rb) {
@@ -749,11 +871,6 @@ struct TileCfg {
   static constexpr size_t smem(bool bg) { return (size_t)NS * PL * sizeof(float) * (bg ? 5 : 3); }
   static_assert(LY % RPT == 0, "rows must split evenly over threads");
 };
-
-__device__ __forceinline__ int wrapmod(int v, int n) {
-  int r = v % n;
-  return r < 0 ? r + n : r;
-}
 
 // ---------------------------------------------------------------------------
 // Tiled FP32 smoother with temporal blocking: S full red-black sweeps per pass.

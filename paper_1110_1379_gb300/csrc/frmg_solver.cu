@@ -416,6 +416,11 @@ struct LevelSet {
   std::vector<int> off_rb[2];
   int *d_off_rb[2] = {nullptr, nullptr};
   int nblk_rb[2] = {0, 0};
+  // tiled prolongation (fine side of a V-cycle level): chunks of coarse planes
+  int kc_pl = 0;
+  std::vector<int> off_pl;
+  int *d_off_pl = nullptr;
+  int nblk_pl = 0;
   // tiled residual + restriction (fine side of a V-cycle level)
   bool rr_tiled = false;
   int zc_rr = 0;
@@ -484,6 +489,8 @@ static int pick_chunk(const std::vector<long long> &tiles, const std::vector<int
 
 template <bool BG, bool DIR>
 static long long rb_slots();
+template <bool DIR>
+static long long pl_slots();
 template <bool DIR>
 static long long rr_slots();
 
@@ -575,6 +582,23 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 
         n2s[g] = ls.h[g].n2;
       }
       ls.zc_rr = pick_chunk(tl, n2s, ls.dirichlet ? rr_slots<true>() : rr_slots<false>(), 2, true);
+      // prolongation onto this set from its coarser set (every grid even-sized)
+      bool even = true;
+      for (int g = 0; g < ng; g++) {
+        even = even && !(ls.h[g].n2 & 1);
+        tl[g] = (long long)((ls.h[g].n0 + kPlTX - 1) / kPlTX) * ((ls.h[g].n1 + kPlTY - 1) / kPlTY);
+        n2s[g] = ls.h[g].n2 / 2;
+      }
+      if (even) {
+        ls.kc_pl = pick_chunk(tl, n2s, ls.dirichlet ? pl_slots<true>() : pl_slots<false>(), 2, false);
+        ls.off_pl.assign(ng + 1, 0);
+        for (int g = 0; g < ng; g++)
+          ls.off_pl[g + 1] = ls.off_pl[g] + (int)(tl[g] * ((n2s[g] + ls.kc_pl - 1) / ls.kc_pl));
+        ls.nblk_pl = ls.off_pl[ng];
+        ls.d_off_pl = S.get<int>(ng + 1);
+        CK(cudaMemcpyAsync(ls.d_off_pl, ls.off_pl.data(), (ng + 1) * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+      }
     }
     ls.off_rr.assign(ng + 1, 0);
     for (int g = 0; g < ng; g++) {
@@ -809,6 +833,13 @@ static long long rb_slots() {
 }
 
 template <bool DIR>
+static long long pl_slots() {
+  static long long slots = 0;
+  if (!slots) slots = (long long)sm_count() * resident_blocks(k_prolong_tiled<DIR>, 256, 0);
+  return slots;
+}
+
+template <bool DIR>
 static long long rr_slots() {
   static long long slots = 0;
   if (!slots) {
@@ -937,8 +968,21 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
   vcycle<T, BG>(ctx, H, l + 1, o, active, st);
   {
     PROF(pname("prolong", sizeof(T) == 8, l == 0));
-    k_prolong<T><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, F.size(), active,
-                                              H.par[l], H.par[l + 1]);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (F.rr_tiled && F.nblk_pl > 0) {
+        if (F.dirichlet)
+          k_prolong_tiled<true><<<F.nblk_pl, 256, 0, st>>>(F.d, C.d, F.d_off_pl, F.size(),
+                                                           F.kc_pl, active, H.par[l], H.par[l + 1]);
+        else
+          k_prolong_tiled<false><<<F.nblk_pl, 256, 0, st>>>(F.d, C.d, F.d_off_pl, F.size(),
+                                                            F.kc_pl, active, H.par[l], H.par[l + 1]);
+        done = true;
+      }
+    }
+    if (!done)
+      k_prolong<T><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, F.size(), active,
+                                                H.par[l], H.par[l + 1]);
     CK_LAUNCH(ctx);
   }
   smooth_set<T, BG>(ctx, F, o.post, even ? &plan_post : nullptr, active, H.par[l], st, l == 0);
