@@ -135,9 +135,9 @@ __device__ __forceinline__ unsigned fdiv(unsigned n, FastDiv f) {
 
 // Fine-grid state of the double-float outer loop of one grid.
 struct DFGrid {
-  float *uh, *ul;        // u = uh + ul
-  float *Bh, *Bl;        // e^u
-  float *rh, *rl;        // gamma (rho - 1)
+  float2 *u;             // u = (hi, lo)
+  float2 *B;             // e^u
+  float2 *r;             // gamma (rho - 1)
   const double *bnd;     // packed Dirichlet faces (FP64) or null
   long long foff[6];
   long long ncell;
@@ -224,34 +224,31 @@ __global__ void k_df_init(DFGrid G, const double *u64, const double *rho, int ze
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= G.ncell) return;
   df u = zero_u ? df{0.f, 0.f} : split_bits(u64[t]);
-  G.uh[t] = u.h;
-  G.ul[t] = u.l;
+  G.u[t] = make_float2(u.h, u.l);
   df B = zero_u ? df{1.f, 0.f} : df_exp(u, ln2h, ln2l);
-  G.Bh[t] = B.h;
-  G.Bl[t] = B.l;
+  G.B[t] = make_float2(B.h, B.l);
   const df r = df_mul(df_add_f(split_bits(rho[t]), -1.0f), df{G.gah, G.gal});
-  G.rh[t] = r.h;
-  G.rl[t] = r.l;
+  G.r[t] = make_float2(r.h, r.l);
 }
 
 // u += delta, e^u recomputed from u (no drift across outer steps).
 __global__ void k_df_update(DFGrid G, const float *delta, float ln2h, float ln2l) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= G.ncell) return;
-  df s = two_sum(G.uh[t], delta[t]);
-  s.l += G.ul[t];
+  const float2 uo = G.u[t];
+  df s = two_sum(uo.x, delta[t]);
+  s.l += uo.y;
   df u = fast_two_sum(s.h, s.l);
-  G.uh[t] = u.h;
-  G.ul[t] = u.l;
+  G.u[t] = make_float2(u.h, u.l);
   df B = df_exp(u, ln2h, ln2l);
-  G.Bh[t] = B.h;
-  G.Bl[t] = B.l;
+  G.B[t] = make_float2(B.h, B.l);
 }
 
 __global__ void k_df_final(DFGrid G, double *u64) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= G.ncell) return;
-  u64[t] = join_bits(G.uh[t], G.ul[t]);
+  const float2 v = G.u[t];
+  u64[t] = join_bits(v.x, v.y);
 }
 
 // One face of the double-float operator: (B_i + B_j)(u_j - u_i).
@@ -288,13 +285,15 @@ __global__ void __launch_bounds__(256)
       j = (int)(q - q2 * (unsigned)G.n1);
       k = (int)q2;
     }
-    const df ui = {G.uh[t], G.ul[t]};
-    const df Bi = {G.Bh[t], G.Bl[t]};
+    const float2 uv = G.u[t], Bv = G.B[t];
+    const df ui = {uv.x, uv.y};
+    const df Bi = {Bv.x, Bv.y};
     df acc = {0.f, 0.f};
     const bool dir = G.bnd != nullptr;
     const long long sx = 1, sy = G.n0, sz = (long long)G.n0 * G.n1;
     auto reg = [&](long long cj) {
-      acc = df_add(acc, df_face(ui, Bi, df{G.uh[cj], G.ul[cj]}, df{G.Bh[cj], G.Bl[cj]}));
+      const float2 uj = G.u[cj], Bj = G.B[cj];
+      acc = df_add(acc, df_face(ui, Bi, df{uj.x, uj.y}, df{Bj.x, Bj.y}));
     };
     auto ghost = [&](int f) {
       long long o;
@@ -315,7 +314,8 @@ __global__ void __launch_bounds__(256)
     // beta (e^{-u/2} - 1) with e^{-u/2} = 1/sqrt(e^u)
     const df y = df_add_f(df_rsqrt(Bi), -1.0f);
     df d = df_add(df_mul(acc, df{G.ahh, G.ahl}), df_mul(y, df{G.beh, G.bel}));
-    d = df_sub(d, df{G.rh[t], G.rl[t]});
+    const float2 rv = G.r[t];
+    d = df_sub(d, df{rv.x, rv.y});
     const float dv = d.h + d.l;
     r32[t] = -dv;
     ub32[t] = ui.h;

@@ -1377,6 +1377,20 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous global-to-shared copy of 8 bytes (PTX cp.async; both
+// addresses 8-byte aligned); commit_group / wait_group track completion.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Tiled FP32 residual + restriction (same result as k_resid_restrict).
 // A block owns a TX x TY fine tile and an even chunk of zc fine planes, marches
 // along z with a ring of 4 planes (tile plus a halo of 2 cells in x, so that
@@ -1388,7 +1402,13 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
 // fetched into registers while plane m is evaluated.
 template <int TX, int TY>
 struct RRCfg {
-  static constexpr int LX = TX + 4, LY = TY + 2, PL = LX * LY, NS = 4;
+  // planes in flight beyond the three being read; ring of A + 4 slots (the
+  // slot being refilled was last read two iterations earlier)
+#ifndef FR_RR_AHEAD
+#define FR_RR_AHEAD 2
+#endif
+  static constexpr int A = FR_RR_AHEAD;
+  static constexpr int LX = TX + 4, LY = TY + 2, PL = LX * LY, NS = 4 + A;
   static constexpr int PXR = LX / 2, NPAIR = PXR * LY;
   static constexpr int CX = TX / 2, NT = (TX / 2) * (TY / 2);
   static constexpr int K = (NPAIR + NT - 1) / NT;
@@ -1457,61 +1477,54 @@ __global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
         if (in) pg[k] = (long long)gyy * n0 + gxx;
       }
     }
-    float2 rd[K], rx[K], rf[K], ru[K], rE[K];
-    auto fetch = [&](int p) {
-      if (DIR && (p < 0 || p >= n2)) return;
-      const long long zo = (long long)wrapmod(p, n2) * n1 * n0;
+    // copies of plane p into ring slot (p - (Z0 - 1)) mod NS: one commit
+    // group per call (empty when the plane is outside a patch)
+    const bool hasf = fin != nullptr;
+    int pwz = DIR ? Z0 - 1 : wrapmod(Z0 - 1, n2);  // wrapped index of the next plane
+    const long long fplane = (long long)n0 * n1;
+    auto issue = [&](int p, int slot) {
+      if (!DIR || (p >= 0 && p < n2)) {
+        const long long zo = (long long)pwz * fplane;
+        const int base = slot * PL;
 #pragma unroll
-      for (int k = 0; k < K; k++) {
-        if (pg[k] < 0) continue;
-        const long long gi = zo + pg[k];
-        rd[k] = *reinterpret_cast<const float2 *>(uin + gi);
-        rx[k] = *reinterpret_cast<const float2 *>(xin + gi);
-        if (fin) rf[k] = *reinterpret_cast<const float2 *>(fin + gi);  // scaled at commit
-        if (BG) {
-          ru[k] = *reinterpret_cast<const float2 *>(ubin + gi);
-          rE[k] = *reinterpret_cast<const float2 *>(Ein + gi);
+        for (int k = 0; k < K; k++) {
+          if (pg[k] < 0) continue;
+          const long long gi = zo + pg[k];
+          const int o = base + po[k];
+          cp_async8(sd + o, uin + gi);
+          cp_async8(sx + o, xin + gi);
+          if (hasf) cp_async8(sf + o, fin + gi);
+          if (BG) {
+            cp_async8(sub + o, ubin + gi);
+            cp_async8(sE + o, Ein + gi);
+          }
         }
       }
-    };
-    auto commit = [&](int p) {
-      if (DIR && (p < 0 || p >= n2)) return;
-      const int base = wrapmod(p, NS) * PL;
-#pragma unroll
-      for (int k = 0; k < K; k++) {
-        if (pg[k] < 0) continue;
-        const int o = base + po[k];
-        sd[o] = rd[k].x;
-        sd[o + 1] = rd[k].y;
-        sx[o] = rx[k].x;
-        sx[o + 1] = rx[k].y;
-        sf[o] = fin ? fs * (rf[k].x - fo) : 0.0f;
-        sf[o + 1] = fin ? fs * (rf[k].y - fo) : 0.0f;
-        if (BG) {
-          sub[o] = ru[k].x;
-          sub[o + 1] = ru[k].y;
-          sE[o] = rE[k].x;
-          sE[o + 1] = rE[k].y;
-        }
-      }
+      cp_async_commit();
+      pwz = DIR ? pwz + 1 : (pwz + 1 == n2 ? 0 : pwz + 1);
     };
     const int ci = threadIdx.x % CX, cj = threadIdx.x / CX;
     const int lx = 2 + 2 * ci, ly = 1 + 2 * cj;
     const int gx = X0 + 2 * ci, gy = Y0 + 2 * cj;
     const bool valid = gx < n0 && gy < n1;
     float su = 0.f, sdd = 0.f;
-    fetch(Z0 - 1);
-    commit(Z0 - 1);
-    fetch(Z0);
-    commit(Z0);
-    fetch(Z0 + 1);
-    commit(Z0 + 1);
-    __syncthreads();
+    constexpr int A = C::A;
+    // prologue: planes Z0-1 .. Z0+A (slots 0 .. A+1)
+#pragma unroll
+    for (int d = 0; d < A + 2; d++) issue(Z0 - 1 + d, d);
+    int sl = 1;  // ring slot of plane m
     for (int m = Z0; m < Z1; m++) {
-      const bool more = m + 2 <= Z1;
-      if (more) fetch(m + 2);
+      // plane m+1+A into the slot of plane m-3 (last read by iteration m-2,
+      // before the barrier of iteration m-1); planes m-1, m, m+1 must have landed
+      {
+        const int pz = m + 1 + A;
+        if (pz <= Z1) issue(pz, (sl + A + 1) % NS);
+        else cp_async_commit();
+      }
+      cp_async_wait<A>();
+      __syncthreads();
       if (valid) {
-        const int sl = wrapmod(m, NS), slm = wrapmod(m - 1, NS), slp = wrapmod(m + 1, NS);
+        const int slm = sl == 0 ? NS - 1 : sl - 1, slp = sl + 1 == NS ? 0 : sl + 1;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
           const int ax = q & 1, ay = q >> 1;
@@ -1540,7 +1553,7 @@ __global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
           float acc, dacc, N, dN;
           A.done(acc, dacc);
           finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-          const float d = N - sf[o];
+          const float d = N - (hasf ? fs * (sf[o] - fo) : 0.0f);
           sdd += d;
           su += di;
           ss = fmaf(d, d, ss);
@@ -1557,10 +1570,9 @@ __global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
           sdd = 0.f;
         }
       }
-      // plane m+2 goes into the slot of plane m-2, which iteration m does not read
-      if (more) commit(m + 2);
-      __syncthreads();
+      sl = sl + 1 == NS ? 0 : sl + 1;
     }
+    cp_async_wait<0>();
   }
   if (partial) block_reduce2f<NT>(ss, mx, &partial[2 * blockIdx.x], &partial[2 * blockIdx.x + 1]);
 }

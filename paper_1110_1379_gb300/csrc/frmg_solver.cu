@@ -1361,13 +1361,13 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
 
 // Zero-start set-up of the double-float loop: the FP32 right-hand side is the
 // high part of gamma (rho - 1); block partials of its norm as k_prep_zero.
-__global__ void __launch_bounds__(256) k_prep_zero_df(const float *rh, float *r32, float *u32,
+__global__ void __launch_bounds__(256) k_prep_zero_df(const float2 *rv, float *r32, float *u32,
                                                       float *x32, long long n, double *partial,
                                                       int base) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float s = 0.0f, m = 0.0f;
   if (t < n) {
-    float r = rh[t];
+    float r = rv[t].x;
     r32[t] = r;
     u32[t] = 0.0f;
     x32[t] = 0.0f;
@@ -1428,12 +1428,9 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   for (int pi = 0; pi < np; pi++) {
     DFGrid &g = D[pi];
     dfgrid_setup(g, P[pi].n, P[pi].k, P[pi].bnd);
-    g.uh = S.get<float>(g.ncell);
-    g.ul = S.get<float>(g.ncell);
-    g.Bh = S.get<float>(g.ncell);
-    g.Bl = S.get<float>(g.ncell);
-    g.rh = S.get<float>(g.ncell);
-    g.rl = S.get<float>(g.ncell);
+    g.u = S.get<float2>(g.ncell);
+    g.B = S.get<float2>(g.ncell);
+    g.r = S.get<float2>(g.ncell);
     boff[pi + 1] = boff[pi] + nblocks(g.ncell);
   }
   double *partial = S.get<double>(2 * (size_t)boff[np]);
@@ -1545,7 +1542,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
       for (int pi = 0; pi < np; pi++) {
         Grid<float> &G = H.lev[pi][0];
         PROF("prep_inner");
-        k_prep_zero_df<<<nblocks(G.ncell), 256, 0, st>>>(D[pi].rh, const_cast<float *>(G.f),
+        k_prep_zero_df<<<nblocks(G.ncell), 256, 0, st>>>(D[pi].r, const_cast<float *>(G.f),
                                                          H.cur_u(pi, 0), H.cur_x(pi, 0),
                                                          G.ncell, partial, boff[pi]);
         CK_LAUNCH(ctx);
@@ -2450,12 +2447,9 @@ int fr_residual_df(frmg_ctx *ctx, const double *u, const double *density, const 
     double *dd = stage(S, back, d, nc, false, true, st);
     DFGrid g;
     dfgrid_setup(g, dims, k, dub);
-    g.uh = S.get<float>(nc);
-    g.ul = S.get<float>(nc);
-    g.Bh = S.get<float>(nc);
-    g.Bl = S.get<float>(nc);
-    g.rh = S.get<float>(nc);
-    g.rl = S.get<float>(nc);
+    g.u = S.get<float2>(nc);
+    g.B = S.get<float2>(nc);
+    g.r = S.get<float2>(nc);
     float ln2h, ln2l;
     split_host(std::log(2.0), ln2h, ln2l);
     (void)p;
