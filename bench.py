@@ -31,8 +31,13 @@ PHYS = dict(box=256.0, a=1.0, omega_m=0.24, fr0=1e-5)
 SIGMA = 2.0
 SEED = 3000
 TOL = 1e-8
-WORKLOAD = (f"{N}^3 periodic, box 256 Mpc/h, a=1, Om=0.24, |f_R0|=1e-5, lognormal sigma=2.0 "
-            f"P(k)~k^-1.5 seed {SEED}, u0=0, V(2,2) red-black NGS, rms tol 1e-8")
+def workload(n):
+    return (f"{n}^3 periodic, box 256 Mpc/h, a=1, Om=0.24, |f_R0|=1e-5, lognormal sigma=2.0 "
+            f"P(k)~k^-1.5 seed {SEED}, u0=0, red-black NGS V-cycles (shape from fr_autotune), "
+            f"rms tol 1e-8")
+
+
+WORKLOAD = workload(N)
 # CPU oracle sample: same cell size (0.5 Mpc/h), sigma, |f_R0| and a on a 64^3 box
 SAMPLE_N = 64
 SAMPLE_PHYS = dict(box=32.0, a=1.0, omega_m=0.24, fr0=1e-5)
@@ -41,6 +46,7 @@ SAMPLE_PHYS = dict(box=32.0, a=1.0, omega_m=0.24, fr0=1e-5)
 # the operation: each array read or written once).
 ALG_BYTES = {
     "smooth_f32@fine": 12.0,         # one full red-black sweep per launch: read u, f; write u
+    "smooth_bg_f32@fine": 20.0,      # correction form: also reads the background u and e^u
     "smooth_f64@fine": 12.0,         # one colour per launch: (read u, f; write u) / 2, 8 B words
     "resid_restrict_f32@fine": 10.0,  # read u, rhs (8 B) + 4 coarse words / 8 cells
     "resid_restrict_f64@fine": 20.0,
@@ -496,7 +502,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
+        "config": {"workload": workload(n), "global_batch": world, "seq_len": None,
                    "parallelism": f"replicas x{world} (one field per GPU)",
                    "l2": "inputs larger than L2 (1 GiB per FP64 field)"},
         "fp64": {"value": fp64_value, "unit": "cells/s",

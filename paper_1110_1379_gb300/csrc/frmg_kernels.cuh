@@ -445,6 +445,35 @@ __global__ void k_reduce_partials(const double *partial, const int *off, int ngr
   block_reduce2<256>(s, m, &out[2 * g], &out[2 * g + 1]);
 }
 
+// First stage of the per-grid sums for long partial lists: block (c, g)
+// reduces partials [off[g] + c CH, min(off[g] + (c + 1) CH, off[g + 1])) into
+// tmp[2 (g nch + c)] (zeros when the range is empty); k_reduce_partials then
+// sums each grid's nch entries (offsets g nch).
+template <int CH>
+__global__ void k_reduce_partials_chunks(const double *partial, const int *off, int nch,
+                                         double *tmp) {
+  const int g = blockIdx.y, c = blockIdx.x;
+  const int b0 = off[g] + c * CH, b1 = min(b0 + CH, off[g + 1]);
+  double s = 0.0, m = 0.0;
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+    s += partial[2 * b];
+    m = fmax(m, partial[2 * b + 1]);
+  }
+  block_reduce2<256>(s, m, &tmp[2 * (g * nch + c)], &tmp[2 * (g * nch + c) + 1]);
+}
+
+// Second stage: out[2g] = sum, out[2g+1] = max of tmp[g nch .. (g+1) nch).
+__global__ void k_reduce_chunks(const double *tmp, int nch, int ngrid, double *out) {
+  const int g = blockIdx.x;
+  if (g >= ngrid) return;
+  double s = 0.0, m = 0.0;
+  for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+    s += tmp[2 * (g * nch + c)];
+    m = fmax(m, tmp[2 * (g * nch + c) + 1]);
+  }
+  block_reduce2<256>(s, m, &out[2 * g], &out[2 * g + 1]);
+}
+
 // Fused residual + restriction (Sec. V.B.2): for each coarse cell, the 8 fine
 // children give  u^H = uR = mean(u^h),  x^H = expm1(u^H),  f^H <- mean(d^h)
 // (the coarse operator is added by k_fas_rhs).  One thread per coarse cell;
@@ -1136,9 +1165,23 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
   constexpr int TX = C::TX, H = C::H, PX = C::PX, PP = C::PP, NW = C::NW, NT = C::NT;
   constexpr int NLD = C::NLD, NS = C::NS;
   extern __shared__ float4 smem_rb[];
-  float2 *sux = reinterpret_cast<float2 *>(smem_rb);                         // [NS][2][PP]
-  float2 *sgb = sux + NS * 2 * PP;                                          // [NS][2][PP]
+  // plain form: (u, x) per cell; correction form: (u, x, ub, E) per cell, so a
+  // neighbour is one 16-byte access (half the shared-memory instructions)
+  float2 *sux = reinterpret_cast<float2 *>(smem_rb);  // [NS][2][PP] (plain)
+  float4 *s4 = smem_rb;                               // [NS][2][PP] (correction form)
   float *sfv = reinterpret_cast<float *>(sux + NS * 2 * PP * (BG ? 2 : 1));  // [NF][2][PP]
+  // cell e of a slot/colour offset: (u, x, ub, E); ub = 0, E = 1 in the plain form
+  auto cell = [&](int i) -> float4 {
+    if (BG) return s4[i];
+    const float2 v = sux[i];
+    return make_float4(v.x, v.y, 0.f, 1.f);
+  };
+  auto put_ux = [&](int i, float u, float x) {
+    if (BG)
+      *reinterpret_cast<float2 *>(&s4[i]) = make_float2(u, x);
+    else
+      sux[i] = make_float2(u, x);
+  };
   const int g = find_grid(off, ngrid, blockIdx.x);
   const Grid<float> &Gg = grids[g];
   if (!grid_active(active, Gg.field)) return;
@@ -1223,14 +1266,15 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
       if (q >= PP) continue;
       const int c0 = (int)((ldf[k] >> 2) & 1u) ^ pb;
       const int i0 = so + c0 * PP + q, i1 = so + (c0 ^ 1) * PP + q;
-      sux[i0] = make_float2(pd[k].x, pq[k].x);
-      sux[i1] = make_float2(pd[k].y, pq[k].y);
+      if (BG) {
+        s4[i0] = make_float4(pd[k].x, pq[k].x, pu[k].x, pE[k].x);
+        s4[i1] = make_float4(pd[k].y, pq[k].y, pu[k].y, pE[k].y);
+      } else {
+        sux[i0] = make_float2(pd[k].x, pq[k].x);
+        sux[i1] = make_float2(pd[k].y, pq[k].y);
+      }
       sfv[fo2 + c0 * PP + q] = fin ? fs * (pf[k].x - fo) : 0.0f;
       sfv[fo2 + (c0 ^ 1) * PP + q] = fin ? fs * (pf[k].y - fo) : 0.0f;
-      if (BG) {
-        sgb[i0] = make_float2(pu[k].x, pE[k].x);
-        sgb[i1] = make_float2(pu[k].y, pE[k].y);
-      }
     }
   };
   // Newton update of the colour-Q cell of pair (ly, px) of plane m; s is its x
@@ -1242,55 +1286,42 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
     if (DIR && (gx < 0 || gx >= n0 || gy < 0 || gy >= n1)) return;
     const int e = ly * PX + px;
     const int cq = Q * PP, co = (Q ^ 1) * PP;
-    const float2 *V = sux + oc + co;
+    const int V = oc + co;
     const int ex = s ? e + 1 : e - 1;
-    const float2 own = sux[oc + cq + e];
-    const float2 nin = V[e], nxo = V[ex];
-    const float2 nym = V[e - PX], nyp = V[e + PX];
-    const float2 nzm = sux[om + co + e], nzp = sux[op + co + e];
-    float2 gown = make_float2(0.f, 1.f), gin = gown, gxo = gown, gym = gown, gyp = gown,
-           gzm = gown, gzp = gown;
-    if (BG) {
-      const float2 *GV = sgb + oc + co;
-      gown = sgb[oc + cq + e];
-      gin = GV[e];
-      gxo = GV[ex];
-      gym = GV[e - PX];
-      gyp = GV[e + PX];
-      gzm = sgb[om + co + e];
-      gzp = sgb[op + co + e];
-    }
-    const float2 lft = s ? nin : nxo, rgt = s ? nxo : nin;
-    const float2 glft = s ? gin : gxo, grgt = s ? gxo : gin;
+    const float4 own = cell(oc + cq + e);
+    const float4 nin = cell(V + e), nxo = cell(V + ex);
+    const float4 nym = cell(V + e - PX), nyp = cell(V + e + PX);
+    const float4 nzm = cell(om + co + e), nzp = cell(op + co + e);
+    const float4 lft = s ? nin : nxo, rgt = s ? nxo : nin;
     const float di = own.x, xi = own.y;
-    const float Ei = BG ? gown.y : 1.0f;
-    const float ubi = BG ? gown.x : 0.0f;
+    const float Ei = BG ? own.w : 1.0f;
+    const float ubi = BG ? own.z : 0.0f;
     const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
     OpAcc<float, BG> A(di, Ei, xi, Bi, ubi);
     if (DIR && gx == 0)
       A.ghost(face_value(Gg, 0, gx, gy, m));
     else
-      A.reg(lft.x, lft.y, glft.x, glft.y);
+      A.reg(lft.x, lft.y, lft.z, lft.w);
     if (DIR && gx == n0 - 1)
       A.ghost(face_value(Gg, 1, gx, gy, m));
     else
-      A.reg(rgt.x, rgt.y, grgt.x, grgt.y);
+      A.reg(rgt.x, rgt.y, rgt.z, rgt.w);
     if (DIR && gy == 0)
       A.ghost(face_value(Gg, 2, gx, gy, m));
     else
-      A.reg(nym.x, nym.y, gym.x, gym.y);
+      A.reg(nym.x, nym.y, nym.z, nym.w);
     if (DIR && gy == n1 - 1)
       A.ghost(face_value(Gg, 3, gx, gy, m));
     else
-      A.reg(nyp.x, nyp.y, gyp.x, gyp.y);
+      A.reg(nyp.x, nyp.y, nyp.z, nyp.w);
     if (DIR && m == 0)
       A.ghost(face_value(Gg, 4, gx, gy, m));
     else
-      A.reg(nzm.x, nzm.y, gzm.x, gzm.y);
+      A.reg(nzm.x, nzm.y, nzm.z, nzm.w);
     if (DIR && m == n2 - 1)
       A.ghost(face_value(Gg, 5, gx, gy, m));
     else
-      A.reg(nzp.x, nzp.y, gzp.x, gzp.y);
+      A.reg(nzp.x, nzp.y, nzp.z, nzp.w);
     float acc, dacc;
     A.done(acc, dacc);
     float N, dN;
@@ -1298,7 +1329,7 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
     float du = newton_step(N - sfv[ofq + cq + e], dN);
     du = fminf(fmaxf(du, -cap), cap);
     const float dn = di + du;
-    sux[oc + cq + e] = make_float2(dn, m_expm1(dn));
+    put_ux(oc + cq + e, dn, m_expm1(dn));
   };
 
   const int P0 = Z0 - H, PE = Z1 + H;
@@ -1362,8 +1393,8 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
           if (!(ldf[k] & 2u)) continue;
           const int q = threadIdx.x + k * NT;
           const int c0 = (int)((ldf[k] >> 2) & 1u) ^ (wz & 1);
-          const float2 a = sux[o2 + c0 * PP + q];
-          const float2 bb = sux[o2 + (c0 ^ 1) * PP + q];
+          const float4 a = cell(o2 + c0 * PP + q);
+          const float4 bb = cell(o2 + (c0 ^ 1) * PP + q);
           *reinterpret_cast<float2 *>(uout + woff + roff[k]) = make_float2(a.x, bb.x);
           *reinterpret_cast<float2 *>(xout + woff + roff[k]) = make_float2(a.y, bb.y);
         }

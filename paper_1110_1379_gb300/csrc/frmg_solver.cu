@@ -428,11 +428,21 @@ struct LevelSet {
   int *d_off_rr = nullptr;
   int nblk_rr = 0;
   double *partial = nullptr;  // per-block norm partials
+  int red_nch = 0;            // chunks of the two-stage sum over off_full partials
+  double *red_tmp = nullptr;  // its chunk sums
   double *red = nullptr;      // per-grid (sum of squares, max)
   T **d_dout = nullptr;       // per-grid residual output pointers
   bool empty() const { return h.empty(); }
   int size() const { return (int)h.size(); }
 };
+
+// Chunks of the two-stage sum of per-block partials (0: one stage suffices).
+constexpr int kRedChunk = 4096;
+static int red_chunks(const std::vector<int> &off) {
+  int maxc = 0;
+  for (size_t g = 0; g + 1 < off.size(); g++) maxc = std::max(maxc, off[g + 1] - off[g]);
+  return maxc <= 2 * kRedChunk ? 0 : (maxc + kRedChunk - 1) / kRedChunk;
+}
 
 static int sm_count() {
   static int n = 0;
@@ -614,6 +624,8 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 
     ls.rr_tiled = true;
   }
   ls.partial = S.get<double>(2 * (size_t)std::max(ls.nblk_full, ls.nblk_rr));
+  ls.red_nch = red_chunks(ls.off_full);
+  if (ls.red_nch) ls.red_tmp = S.get<double>(2 * (size_t)ls.red_nch * ng);
   ls.red = S.get<double>(2 * (size_t)ng);
   ls.d_dout = S.get<T *>(ng);
   // host vectors must stay alive until the copies finished
@@ -904,7 +916,8 @@ static void smooth_set(frmg_ctx *ctx, LevelSet<T> &s, int sweeps, const std::vec
   if constexpr (sizeof(T) == 4) {
     if (s.tiled && plan) {
       for (int S : *plan) {
-        PROF(pname("smooth", false, fine));
+        // the correction form is reported apart from the plain one (different kernel)
+        PROF(BG ? (fine ? "smooth_bg_f32@fine" : "smooth_bg_f32@coarse") : pname("smooth", false, fine));
         if (S == 2)
           launch_tiled<BG, 2>(ctx, s, active, par, st);
         else
@@ -988,6 +1001,22 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
   smooth_set<T, BG>(ctx, F, o.post, even ? &plan_post : nullptr, active, H.par[l], st, l == 0);
 }
 
+// Per-grid (sum, max) of per-block partials: one block per grid for short
+// lists, two stages (chunks of kRedChunk partials, then the chunk sums) for
+// the long lists of one-thread-per-cell kernels on fine grids.
+static void reduce_partials(frmg_ctx *ctx, const double *partial, const int *d_off, int ng,
+                            int nch, double *tmp, double *out, cudaStream_t st) {
+  if (nch == 0) {
+    k_reduce_partials<<<ng, 256, 0, st>>>(partial, d_off, ng, out);
+    CK_LAUNCH(ctx);
+    return;
+  }
+  k_reduce_partials_chunks<kRedChunk><<<dim3(nch, ng), 256, 0, st>>>(partial, d_off, nch, tmp);
+  CK_LAUNCH(ctx);
+  k_reduce_chunks<<<ng, 256, 0, st>>>(tmp, nch, ng, out);
+  CK_LAUNCH(ctx);
+}
+
 // Residual norms of every grid of a level set: out[2g] = rms, out[2g+1] = max.
 // dout (host array of ng device pointers, entries may be null) receives d.
 template <typename T, bool BG>
@@ -1003,8 +1032,7 @@ static void level_norms(frmg_ctx *ctx, LevelSet<T> &s, T *const *dout, const int
                                                         active, par);
     CK_LAUNCH(ctx);
   }
-  k_reduce_partials<<<ng, 256, 0, st>>>(s.partial, s.d_off_full, ng, s.red);
-  CK_LAUNCH(ctx);
+  reduce_partials(ctx, s.partial, s.d_off_full, ng, s.red_nch, s.red_tmp, s.red, st);
   double *hp = pinned_buf(ctx, 2 * (size_t)ng);
   CK(cudaMemcpyAsync(hp, s.red, 2 * ng * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1286,8 +1314,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
     std::vector<double> r0(np, 0.0);
     {
       LevelSet<double> &A0 = H64.all[0];
-      k_reduce_partials<<<np, 256, 0, st>>>(A0.partial, A0.d_off_full, np, A0.red);
-      CK_LAUNCH(ctx);
+      reduce_partials(ctx, A0.partial, A0.d_off_full, np, A0.red_nch, A0.red_tmp, A0.red, st);
       double *hp = pinned_buf(ctx, 2 * (size_t)np);
       CK(cudaMemcpyAsync(hp, A0.red, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -1452,9 +1479,10 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
                                                     ln2l);
     CK_LAUNCH(ctx);
   }
+  const int bnch = red_chunks(boff);
+  double *btmp = bnch ? S.get<double>(2 * (size_t)bnch * np) : nullptr;
   auto read_norms = [&](std::vector<double> &out) {
-    k_reduce_partials<<<np, 256, 0, st>>>(partial, d_boff, np, red);
-    CK_LAUNCH(ctx);
+    reduce_partials(ctx, partial, d_boff, np, bnch, btmp, red, st);
     double *hp = pinned_buf(ctx, 2 * (size_t)np);
     CK(cudaMemcpyAsync(hp, red, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
