@@ -52,9 +52,22 @@ ALG_BYTES = {
     "resid_restrict_f64@fine": 20.0,
     "prolong_f32@fine": 9.0,         # read/write u (8 B) + 2 coarse words / 8 cells
     "prolong_f64@fine": 18.0,
-    "df_defect": 36.0,               # 6 double-float state words in, 3 FP32 words out
+    "df_defect": 44.0,               # (hi, lo) of u, e^u, gamma(rho-1) in; 5 FP32 words out
+    "df_update": 28.0,               # (hi, lo) of u and delta in; (hi, lo) of u, e^u out
     "residual_f64@fine": 24.0,       # read u, rho, write d (FP64 defect)
     "residual_f32@fine": 12.0,
+}
+
+# DRAM bytes per cell of one launch (dram__bytes_read.sum + dram__bytes_write.sum
+# over the cells of the launch) from the ncu captures summarised under
+# profiles/ (384^3 launches; traffic grows in proportion to the cells, so it is
+# scaled to the workload's grid).  Valid for the kernels as captured there.
+TRAFFIC_PER_CELL = {
+    "smooth_f32@fine": (1118.444e6 / 384 ** 3, "profiles/smooth_rb_f32_384.md"),
+    "smooth_bg_f32@fine": (1652.112e6 / 384 ** 3, "profiles/smooth_rb_bg_f32_384.md"),
+    "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "profiles/resid_restrict_tiled_f32_384.md"),
+    "prolong_f32@fine": (678.570e6 / 384 ** 3, "profiles/prolong_tiled_f32_384.md"),
+    "df_defect": (2466.320e6 / 384 ** 3, "profiles/df_defect_384.md"),
 }
 
 
@@ -480,14 +493,35 @@ def main():
     if dom_name in ALG_BYTES:
         traffic_alg = ALG_BYTES[dom_name] * cells
         achieved = traffic_alg / (avg_ms / 1e3) / 1e9
+        tr = TRAFFIC_PER_CELL.get(dom_name)
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": tr[0] * cells if tr else None,
+                "traffic_source": (f"ncu dram bytes of one 384^3 launch ({tr[1]}), scaled to "
+                                   f"{n}^3 by cells") if tr else None,
                 "alg_bytes_per_launch": traffic_alg, "avg_launch_ms": avg_ms,
                 "launches": dom_cnt, "peak_source": peak_src}
     else:
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "traffic": None, "avg_launch_ms": avg_ms, "launches": dom_cnt,
                 "peak_source": peak_src}
+    # every fine-level kernel family against the same roof (algorithmic bytes /
+    # event-timed launch), and the whole solve's effective bandwidth
+    kernel_roofs = {}
+    alg_total = 0.0
+    for name, (cnt, tms) in prof.items():
+        if name not in ALG_BYTES or cnt == 0:
+            continue
+        per = ALG_BYTES[name] * cells
+        alg_total += per * cnt
+        ach = per / (tms / cnt / 1e3) / 1e9
+        tr = TRAFFIC_PER_CELL.get(name)
+        kernel_roofs[name] = {"launches_per_solve": cnt / args.steps, "avg_launch_ms": tms / cnt,
+                              "achieved_gbs": ach, "frac": ach / hbm,
+                              "traffic_bytes": tr[0] * cells if tr else None}
+    solve_eff = {"alg_bytes_per_solve": alg_total / args.steps,
+                 "effective_gbs": alg_total / args.steps / (ms / args.steps / 1e3) / 1e9,
+                 "note": "fine-level kernel families only; coarse levels add about 1/7"}
 
 
     if rank != 0:
@@ -521,6 +555,8 @@ def main():
                                  "grad_fR_max_rel": gerr["max_rel"],
                                  "grad_fR_rms_rel": gerr["rms_rel"]},
         "roofline": roof,
+        "kernel_rooflines": kernel_roofs,
+        "solve_effective_bandwidth": solve_eff,
         "kernels_ms": {k: {"launches": c, "total_ms": t} for k, (c, t) in sorted(prof.items())},
         "cpu_baseline": cpu,
         "e2e": e2e,
