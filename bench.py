@@ -234,7 +234,7 @@ def timed(fn, steps, warmup):
 
 
 def run_secondary(args):
-    """Secondary workloads (BASELINE configs 1, 2, 4, 5): one JSON line each."""
+    """Secondary workloads (the 32^3, 128^3 CIC, nested-patch and 96-field batch cases): one JSON line each."""
     import numpy as np
     import torch
 
