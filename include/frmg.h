@@ -258,6 +258,42 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
                 double a, double omega_m, double fr0_abs, double tol, const fr_opts *base,
                 fr_opts *best, double *best_seconds, void *stream);
 
+/*
+ * Modified Poisson equation for the potential Phi (Sec. III.B; Eq. discrete_poisson):
+ *   (1/h^2) [sum of the six neighbours - 6 phi_i] = s_i,
+ *   s_i = 2 gamma (rho_i - 1) - (beta/2) (e^{-u_i/2} - 1),
+ * the paper's right-hand side for n = 1 written in u = ln(f_R / fbar_R), the
+ * variable of fr_solve (gamma = Omega_m a, beta = Omega_m a^4 (a^-3 + 4 OL/Om),
+ * as fr_constants returns them).  density, u: [n2][n1][n0] FP64 (u is normally
+ * fr_solve's solution on the same grid); phi_inout: initial guess in, solution
+ * out.  Host or device pointers (host arrays are staged).
+ * phib == NULL: periodic grid.  The equation has a solution only for a source
+ * of zero mean, so the source's mean is removed (returned in *src_mean when
+ * not NULL) and phi is returned with zero mean.
+ * phib != NULL: refinement patch with the packed boundary values phi_b of its
+ * six faces (layout as fr_smooth's ub); a neighbour outside the patch is the
+ * ghost 2 phi_b - phi_i (Eq. phi_b with mask ratio -1, Eq. bc_modified_poisson);
+ * h = the patch's cell size in code units (h <= 0: 1 / dims[0]).
+ * Multigrid in the correction scheme (Sec. V.A.2, Eq. bc_modified_poisson_coarse;
+ * trilinear prolongation of Sec. V.A.3): FP32 V-cycles (opts->pre / opts->post
+ * red-black Gauss-Seidel sweeps) on the correction equation inside a defect
+ * correction whose defect and update are evaluated in double-float (~48-bit)
+ * arithmetic.  Stops when the rms of L(phi) - s is <= tol (FR_OK); FR_ENOCONV
+ * after opts->max_outer outer steps or opts->max_vcycles V-cycles (phi holds
+ * the last iterate).  stats (optional): vcycles, outer, res0_rms, res_rms,
+ * res_max, seconds, hist.  Synchronous on return.
+ */
+int fr_poisson_solve(frmg_ctx *ctx, const double *density, const double *u, const int dims[3],
+                     double box_mpc_h, double a, double omega_m, double fr0_abs,
+                     const double *phib, double h, double tol, double *phi_inout,
+                     const fr_opts *opts, fr_stats *stats, double *src_mean, void *stream);
+
+/* The source s of fr_poisson_solve (before any mean removal), FP64 out
+ * (host or device), evaluated in double-float arithmetic. */
+int fr_poisson_source(frmg_ctx *ctx, const double *density, const double *u, const int dims[3],
+                      double box_mpc_h, double a, double omega_m, double fr0_abs,
+                      double *s_out, void *stream);
+
 /* Number of kernel launches this context issued since it was created. */
 long long fr_launch_count(const frmg_ctx *ctx);
 

@@ -1,137 +1,13 @@
-// frmg_df.cuh -- double-float ("float-float") arithmetic and the FP64-accurate
-// fine-grid defect of the mixed-precision loop.
-//
-// GB300 executes FP64 at 1/64 of its FP32 rate, so the quantities that need
-// FP64 accuracy in the mixed-precision outer loop (the fine-grid defect, the
-// update u += delta and the convergence test) are carried as unevaluated sums
-// of two floats, hi + lo with |lo| <= ulp(hi)/2: about 48 significant bits,
-// evaluated on the FP32 pipes.  The building blocks are the error-free
-// transformations of Knuth (TwoSum), Dekker (FastTwoSum) and the FMA form of
-// Dekker's TwoProduct; every operation below states its error.
+// frmg_df.cuh -- the FP64-accurate fine-grid state, defect and update of the
+// mixed-precision loop of the f(R) solve, in double-float arithmetic
+// (frmg_dfmath.cuh).
 #pragma once
 
 #include <cuda_runtime.h>
 
-namespace frmg {
-
-struct df {
-  float h, l;
-};
-
-// s + e = a + b exactly (Knuth's TwoSum, no ordering requirement).
-__device__ __forceinline__ df two_sum(float a, float b) {
-  float s = a + b;
-  float bb = s - a;
-  float e = (a - (s - bb)) + (b - bb);
-  return {s, e};
-}
-
-// s + e = a + b exactly when |a| >= |b| or a == 0 (Dekker's FastTwoSum).
-__device__ __forceinline__ df fast_two_sum(float a, float b) {
-  float s = a + b;
-  float e = b - (s - a);
-  return {s, e};
-}
-
-// p + e = a * b exactly (FMA form of Dekker's TwoProduct).
-__device__ __forceinline__ df two_prod(float a, float b) {
-  float p = a * b;
-  float e = fmaf(a, b, -p);
-  return {p, e};
-}
-
-// a + b with absolute error about eps^2 (|a| + |b|), eps = 2^-24: enough
-// whenever the result is judged against the size of the terms, as a residual is.
-__device__ __forceinline__ df df_add(df a, df b) {
-  df s = two_sum(a.h, b.h);
-  s.l += a.l + b.l;
-  return fast_two_sum(s.h, s.l);
-}
-
-__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
-
-__device__ __forceinline__ df df_add_f(df a, float b) {
-  df s = two_sum(a.h, b);
-  s.l += a.l;
-  return fast_two_sum(s.h, s.l);
-}
-
-__device__ __forceinline__ df df_mul(df a, df b) {
-  df p = two_prod(a.h, b.h);
-  p.l = fmaf(a.h, b.l, fmaf(a.l, b.h, p.l));
-  return fast_two_sum(p.h, p.l);
-}
-
-__device__ __forceinline__ df df_mul_f(df a, float b) {
-  df p = two_prod(a.h, b);
-  p.l = fmaf(a.l, b, p.l);
-  return fast_two_sum(p.h, p.l);
-}
-
-// 1/sqrt(a) for a > 0: FP32 estimate refined by one Newton step in double-float
-// (the step doubles the number of correct bits).
-__device__ __forceinline__ df df_rsqrt(df a) {
-  float y = rsqrtf(a.h);
-  // y' = y + y (1 - a y^2) / 2
-  df y2 = two_prod(y, y);
-  df ay2 = df_mul(a, y2);
-  df r = df_add_f(df_neg(ay2), 1.0f);
-  return df_add_f({0.5f * y * r.h, 0.0f}, y);
-}
-
-// e^u for u = (h, l) (|u| < 80): u = n ln2 + r, e^r from its Taylor series at
-// r/16 (degree 7, truncation below 1e-17 relative) squared four times, scaled
-// by 2^n.  ln2 enters as the double-float pair (ln2h, ln2l) supplied by the host.
-__device__ __forceinline__ df df_exp(df u, float ln2h, float ln2l) {
-  float n = rintf(u.h * 1.44269504f);  // nearest integer to u / ln2
-  df nl = df_add(two_prod(n, ln2h), two_prod(n, ln2l));
-  df r = df_sub(u, nl);
-  r.h *= 0.0625f;  // exact scaling by 2^-4
-  r.l *= 0.0625f;
-  // Horner: 1 + r (1 + r/2 (1 + r/3 (... (1 + r/7))))
-  df t = {1.0f, 0.0f};
-#pragma unroll
-  for (int k = 7; k >= 1; k--) {
-    t = df_mul(t, r);
-    // t = 1 + t / k: q = t.h (1/k) rounded, then the remainder t - q k (exact
-    // by FMA) divided by k gives the low part (two-step division by a float)
-    const float rk = 1.0f / (float)k;  // a constant after unrolling
-    const float q = t.h * rk;
-    const float rem = fmaf(-q, (float)k, t.h) + t.l;
-    df tq = {q, rem * rk};
-    t = df_add_f(tq, 1.0f);
-  }
-  for (int k = 0; k < 4; k++) t = df_mul(t, t);
-  int ni = (int)n;
-  return {ldexpf(t.h, ni), ldexpf(t.l, ni)};
-}
-
-}  // namespace frmg
+#include "frmg_dfmath.cuh"
 
 namespace frmg {
-
-// n / d for 0 <= n < 2^31, 1 <= d < 2^31, by one widening multiply and a
-// shift (division by an invariant integer, Granlund and Montgomery 1994):
-// with l = ceil(log2 d), p = 31 + l and m = ceil(2^p / d) (< 2^32),
-// m = 2^p / d + e with 0 <= e < 1, so n m / 2^p = n / d + n e / 2^p where
-// n e / 2^p < 2^-l <= 1 / d: the floor is that of n / d.
-struct FastDiv {
-  unsigned m;
-  int p;
-};
-
-inline FastDiv make_fastdiv(unsigned d) {
-  int l = 0;
-  while ((1ull << l) < d) l++;
-  const int p = 31 + l;
-  const unsigned long long num = 1ull << p;
-  return {(unsigned)((num + d - 1) / d), p};
-}
-
-__device__ __forceinline__ unsigned fdiv(unsigned n, FastDiv f) {
-  return (unsigned)(((unsigned long long)n * f.m) >> f.p);
-}
 
 // Fine-grid state of the double-float outer loop of one grid.
 struct DFGrid {
@@ -147,76 +23,6 @@ struct DFGrid {
   float beh, bel;        // beta
   float gah, gal;        // gamma
 };
-
-// Splits an FP64 value into a double-float pair through the FP64 pipe.
-__device__ __forceinline__ df split_d(double v) {
-  float h = (float)v;
-  return {h, (float)(v - (double)h)};
-}
-
-// The same split with integer operations (the FP64 pipe is narrow): the
-// 53-bit significand m of v = +-m 2^(e-1075) is rounded to its top 24 bits
-// h (hi = h 2^(e-1046)) and the remainder r = m - h 2^29 (|r| <= 2^28) gives
-// lo = r 2^(e-1075), rounded to 24 bits.  Values outside 2^-70 <= |v| < 2^100
-// (zero, tiny, huge, non-finite) take the FP64 route.
-__device__ __forceinline__ df split_bits(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)((b >> 52) & 0x7ffu);
-  if (e < 1023 - 70 || e >= 1023 + 100) return split_d(v);
-  const unsigned sgn = (unsigned)(b >> 63) << 31;
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  unsigned long long h = (m + (1ull << 28)) >> 29;
-  const int r = (int)((long long)m - (long long)(h << 29));
-  int eh = e - 1023;
-  if (h == (1ull << 24)) {
-    h >>= 1;
-    eh += 1;
-  }
-  const float hi = __uint_as_float(sgn | ((unsigned)(eh + 127) << 23) | ((unsigned)h & 0x7fffffu));
-  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);  // 2^(e-1075), exact
-  const float lo = __uint_as_float(__float_as_uint((float)r * scale) ^ sgn);
-  return {hi, lo};
-}
-
-// hi + lo as an FP64 value with integer operations: the significands are
-// aligned (|lo| <= ulp(hi) / 2, so lo sits at least 24 binary places below
-// hi), added as integers and renormalised; rounding is to nearest at the last
-// step only.  Pairs with hi outside 2^-70 <= |hi| < 2^100 use FP64 arithmetic.
-__device__ __forceinline__ double join_bits(float hi, float lo) {
-  const unsigned hb = __float_as_uint(hi), lb = __float_as_uint(lo);
-  const int eh = (int)((hb >> 23) & 0xffu), el = (int)((lb >> 23) & 0xffu);
-  const bool lzero = (lb << 1) == 0;
-  if (eh < 127 - 70 || eh >= 127 + 100 || (!lzero && (el == 0 || eh - el < 24)))
-    return (double)hi + (double)lo;
-  // significands: hi at bit 52 of a 64-bit integer (scaled 2^29), lo below it
-  long long M = (long long)((hb & 0x7fffffu) | 0x800000u) << 29;
-  const long long ml = (long long)((lb & 0x7fffffu) | 0x800000u);
-  const int d = eh - el;  // >= 24
-  long long L;
-  if (lzero) {
-    L = 0;
-  } else if (d <= 29) {
-    L = ml << (29 - d);
-  } else if (d < 64) {
-    const int sh = d - 29;
-    L = (ml + (1ll << (sh - 1))) >> sh;
-  } else {
-    L = 0;
-  }
-  M = ((hb ^ lb) >> 31) ? M - L : M + L;
-  int E = eh - 127 + 1023;
-  if (M >= (1ll << 53)) {
-    M = (M + 1) >> 1;
-    E += 1;
-  } else if (M < (1ll << 52)) {
-    M <<= 1;
-    E -= 1;
-  }
-  const unsigned long long bits = ((unsigned long long)(hb >> 31) << 63) |
-                                  ((unsigned long long)E << 52) |
-                                  ((unsigned long long)M & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)bits);
-}
 
 // State set-up: u (FP64, or zero), e^u and gamma (rho - 1) as double-float.
 __global__ void k_df_init(DFGrid G, const double *u64, const double *rho, int zero_u,

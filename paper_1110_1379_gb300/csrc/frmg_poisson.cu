@@ -1,0 +1,742 @@
+// frmg_poisson.cu -- the modified Poisson equation for the potential Phi.
+//
+// Sec. III.B gives the equation in code units and Eq. (discrete_poisson) its
+// 7-point discretisation,
+//   (1/h^2)[sum of the six neighbours - 6 phi_i] = s_i,
+//   s_i = 2 Om a (rho_i - 1) - (1/6) Om a^4 [(n a^2 xi)^(1/(n+1)) e^{-u~_i/(n+1)}
+//                                            - 3 (a^-3 + 4 OL/Om)],
+// which for n = 1, in the f(R) solver's variable u = u~ - ubar (ubar: the
+// homogeneous solution, where the bracket vanishes), reads
+//   s_i = 2 gamma (rho_i - 1) - (beta/2) (e^{-u_i/2} - 1),
+//   gamma = Om a,  beta = Om a^4 (a^-3 + 4 OL/Om).
+// On a refinement patch a missing neighbour is the ghost 2 phi_b - phi_i
+// (Eq. phi_b with mask ratio -1), which is Eq. (bc_modified_poisson).  The
+// operator is linear, so the multigrid is the correction scheme of Sec. V.A.2:
+// on coarser levels L^H e^H = R(s - L phi)^h with e = 0 on patch boundaries
+// (Eq. bc_modified_poisson_coarse: only the left-hand side is modified), and
+// e^h += P e^H with the trilinear 27/9/3/1 weights of Sec. V.A.3 (coarse cells
+// outside a patch contribute 0).
+//
+// Precision follows the f(R) solve: phi, the source, the fine defect and its
+// norm are double-float pairs (hi + lo, ~48-bit significands) on the FP32
+// pipes, and the correction equation L e = -d is solved by FP32 V-cycles;
+// phi += e.  On a periodic grid the equation has a solution only for a source
+// of zero mean, so the source's mean is removed (and reported) and phi is
+// returned with zero mean.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "frmg.h"
+#include "frmg_dfmath.cuh"
+#include "frmg_internal.h"
+
+using namespace frmg;
+
+namespace {
+
+struct PError {
+  int status;
+  std::string msg;
+};
+
+#define PCK(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw PError{FR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};       \
+  } while (0)
+
+#define PLAUNCH(ctx)                                                                    \
+  do {                                                                                  \
+    frmg_launch_counter(ctx)++;                                                         \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess)                                                              \
+      throw PError{FR_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)};  \
+  } while (0)
+
+constexpr int kNT = 256;
+
+long long nblk(long long n) { return (n + kNT - 1) / kNT; }
+
+// ------------------------------------------------------------------ device
+struct PLevel {
+  float *e;        // correction
+  float *f;        // right-hand side of the correction equation
+  int n0, n1, n2;
+  long long ncell;
+  FastDiv fd0, fd1;
+  float h2;        // h^2
+  int patch;       // 1: Dirichlet (ghost = -e on the boundary), 0: periodic
+};
+
+__device__ __forceinline__ void decomp(const PLevel &L, unsigned t, int &i, int &j, int &k) {
+  const unsigned q = fdiv(t, L.fd0), q2 = fdiv(q, L.fd1);
+  i = (int)(t - q * (unsigned)L.n0);
+  j = (int)(q - q2 * (unsigned)L.n1);
+  k = (int)q2;
+}
+
+// sum of the six neighbours of (i,j,k) and the number of missing ones (patch)
+__device__ __forceinline__ float nbsum(const PLevel &L, const float *e, int i, int j, int k,
+                                       long long c, int &nmiss) {
+  const long long sy = L.n0, sz = (long long)L.n0 * L.n1;
+  float s = 0.0f;
+  nmiss = 0;
+  if (L.patch) {
+    if (i > 0) s += e[c - 1]; else nmiss++;
+    if (i < L.n0 - 1) s += e[c + 1]; else nmiss++;
+    if (j > 0) s += e[c - sy]; else nmiss++;
+    if (j < L.n1 - 1) s += e[c + sy]; else nmiss++;
+    if (k > 0) s += e[c - sz]; else nmiss++;
+    if (k < L.n2 - 1) s += e[c + sz]; else nmiss++;
+  } else {
+    s += e[i > 0 ? c - 1 : c + (L.n0 - 1)];
+    s += e[i < L.n0 - 1 ? c + 1 : c - (L.n0 - 1)];
+    s += e[j > 0 ? c - sy : c + (L.n1 - 1) * sy];
+    s += e[j < L.n1 - 1 ? c + sy : c - (L.n1 - 1) * sy];
+    s += e[k > 0 ? c - sz : c + (L.n2 - 1) * sz];
+    s += e[k < L.n2 - 1 ? c + sz : c - (L.n2 - 1) * sz];
+  }
+  return s;
+}
+
+// Red-black Gauss-Seidel on L e = f (one colour per launch): with the ghosts
+// -e_i on patch faces, e_i = (sum of the neighbours in the grid - h^2 f_i) / (6 + missing).
+__global__ void __launch_bounds__(kNT) k_lsmooth(PLevel L, int colour) {
+  const long long half = L.ncell / 2;
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= half) return;
+  // cell 2t or 2t+1 along x, whichever has the colour (n0 even)
+  int i, j, k;
+  decomp(L, (unsigned)(2 * t), i, j, k);
+  i += (i + j + k + colour) & 1;
+  const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
+  int nm;
+  const float s = nbsum(L, L.e, i, j, k, c, nm);
+  L.e[c] = (s - L.h2 * L.f[c]) / (6.0f + (float)nm);
+}
+
+// Residual d = f - L e of the 8 children of each coarse cell, averaged into
+// the coarse right-hand side; coarse e = 0.  Optional per-block (sum d^2, max |d|).
+__global__ void __launch_bounds__(kNT) k_lresid_restrict(PLevel F, PLevel C, double *partial) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  float ss = 0.0f, mx = 0.0f;
+  if (t < C.ncell) {
+    int I, J, K;
+    decomp(C, (unsigned)t, I, J, K);
+    float sd = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
+      const long long c = ((long long)k * F.n1 + j) * F.n0 + i;
+      int nm;
+      const float s = nbsum(F, F.e, i, j, k, c, nm);
+      const float d = F.f[c] - (s - (6.0f + (float)nm) * F.e[c]) / F.h2;
+      sd += d;
+      ss = fmaf(d, d, ss);
+      mx = fmaxf(mx, fabsf(d));
+    }
+    C.f[t] = 0.125f * sd;
+    C.e[t] = 0.0f;
+  }
+  if (partial) {
+    for (int o = 16; o > 0; o >>= 1) {
+      ss += __shfl_down_sync(0xffffffffu, ss, o);
+      mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    __shared__ float a[kNT / 32], b[kNT / 32];
+    if ((threadIdx.x & 31) == 0) {
+      a[threadIdx.x >> 5] = ss;
+      b[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s2 = 0.0;
+      float m2 = 0.0f;
+      for (int w = 0; w < kNT / 32; w++) {
+        s2 += (double)a[w];
+        m2 = fmaxf(m2, b[w]);
+      }
+      partial[2 * blockIdx.x] = s2;
+      partial[2 * blockIdx.x + 1] = (double)m2;
+    }
+  }
+}
+
+// e^h += P e^H: trilinear, per axis 3/4 on the containing coarse cell and 1/4
+// on the neighbour on the child's side (products: 27/9/3/1 over 64).
+__global__ void __launch_bounds__(kNT) k_lprolong(PLevel F, PLevel C) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= F.ncell) return;
+  int i, j, k;
+  decomp(F, (unsigned)t, i, j, k);
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  const int di = (i & 1) ? 1 : -1, dj = (j & 1) ? 1 : -1, dk = (k & 1) ? 1 : -1;
+  float acc = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    int ii = I + ((q & 1) ? di : 0), jj = J + (((q >> 1) & 1) ? dj : 0),
+        kk = K + ((q >> 2) ? dk : 0);
+    const float w = ((q & 1) ? 0.25f : 0.75f) * (((q >> 1) & 1) ? 0.25f : 0.75f) *
+                    ((q >> 2) ? 0.25f : 0.75f);
+    bool in = true;
+    if (C.patch) {
+      in = ii >= 0 && ii < C.n0 && jj >= 0 && jj < C.n1 && kk >= 0 && kk < C.n2;
+    } else {
+      ii = ii < 0 ? ii + C.n0 : (ii >= C.n0 ? ii - C.n0 : ii);
+      jj = jj < 0 ? jj + C.n1 : (jj >= C.n1 ? jj - C.n1 : jj);
+      kk = kk < 0 ? kk + C.n2 : (kk >= C.n2 ? kk - C.n2 : kk);
+    }
+    if (in) acc = fmaf(w, C.e[((long long)kk * C.n1 + jj) * C.n0 + ii], acc);
+  }
+  F.e[t] += acc;
+}
+
+// Coarsest level: one block, red-black sweeps until the rms residual falls by
+// 1e-3 of its value before the first sweep (at most maxit sweeps) or stops falling.
+__global__ void __launch_bounds__(kNT) k_lcoarsest(PLevel L, int maxit) {
+  __shared__ float red[kNT / 32];
+  __shared__ float r0s, rprev;
+  auto rms = [&]() -> float {
+    float ss = 0.0f;
+    for (long long c = threadIdx.x; c < L.ncell; c += kNT) {
+      int i, j, k;
+      decomp(L, (unsigned)c, i, j, k);
+      int nm;
+      const float s = nbsum(L, L.e, i, j, k, c, nm);
+      const float d = L.f[c] - (s - (6.0f + (float)nm) * L.e[c]) / L.h2;
+      ss = fmaf(d, d, ss);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    float tot = 0.0f;
+    for (int w = 0; w < kNT / 32; w++) tot += red[w];
+    __syncthreads();
+    return sqrtf(tot / (float)L.ncell);
+  };
+  const float r0 = rms();
+  if (threadIdx.x == 0) {
+    r0s = r0;
+    rprev = r0;
+  }
+  __syncthreads();
+  for (int it = 0; it < maxit; it++) {
+    for (int colour = 0; colour < 2; colour++) {
+      for (long long t = threadIdx.x; t < L.ncell / 2; t += kNT) {
+        int i, j, k;
+        decomp(L, (unsigned)(2 * t), i, j, k);
+        i += (i + j + k + colour) & 1;
+        const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
+        int nm;
+        const float s = nbsum(L, L.e, i, j, k, c, nm);
+        L.e[c] = (s - L.h2 * L.f[c]) / (6.0f + (float)nm);
+      }
+      __syncthreads();
+    }
+    const float r = rms();
+    const bool stop = r <= 1e-3f * r0s || !(r < rprev);
+    __syncthreads();
+    if (threadIdx.x == 0) rprev = r;
+    __syncthreads();
+    if (stop) break;
+  }
+}
+
+// ---- double-float fine level
+
+struct PFine {
+  float2 *phi;         // phi (hi, lo)
+  float2 *s;           // source (hi, lo)
+  const double *phib;  // patch faces (FP64) or null
+  long long foff[6];
+  int n0, n1, n2;
+  long long ncell;
+  FastDiv fd0, fd1;
+  float ih2h, ih2l;    // 1/h^2 as a double-float pair
+};
+
+__device__ __forceinline__ df ldf(const float2 *p, long long c) {
+  const float2 v = p[c];
+  return {v.x, v.y};
+}
+
+// Sum of two double-float values across a warp; lane 0 holds the total.
+__device__ __forceinline__ df warp_df_sum(df v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    df w = {__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+// Block (sum, max) of a double-float per-thread value: partial[2 b] = sum
+// (as FP64), partial[2 b + 1] = max |value| (the max is taken on the high parts).
+__device__ __forceinline__ void block_df_partial(df v, float amax, double *partial) {
+  __shared__ double ws[kNT / 32];
+  __shared__ float wm[kNT / 32];
+  v = warp_df_sum(v);
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_down_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) {
+    ws[threadIdx.x >> 5] = join_bits(v.h, v.l);
+    wm[threadIdx.x >> 5] = amax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    float m = 0.0f;
+    for (int w = 0; w < kNT / 32; w++) {
+      s += ws[w];
+      m = fmaxf(m, wm[w]);
+    }
+    partial[2 * blockIdx.x] = s;
+    partial[2 * blockIdx.x + 1] = (double)m;
+  }
+}
+
+// s = 2 gamma (rho - 1) - (beta/2)(e^{-u/2} - 1) and phi = phi0, both as
+// pairs; per-block partial sums of s (for its mean).
+__global__ void __launch_bounds__(kNT)
+    k_psource(PFine P, const double *rho, const double *u, const double *phi0, float g2h,
+              float g2l, float bh, float bl, float ln2h, float ln2l, double *partial) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  df v = {0.f, 0.f};
+  float am = 0.0f;
+  if (t < P.ncell) {
+    const df r = split_bits(rho[t]);
+    const df uu = split_bits(u[t]);
+    const df e = df_exp(df{-0.5f * uu.h, -0.5f * uu.l}, ln2h, ln2l);  // exact halving
+    const df s = df_sub(df_mul(df_add_f(r, -1.0f), df{g2h, g2l}),
+                        df_mul(df_add_f(e, -1.0f), df{bh, bl}));
+    P.s[t] = make_float2(s.h, s.l);
+    const df p = phi0 ? split_bits(phi0[t]) : df{0.f, 0.f};
+    P.phi[t] = make_float2(p.h, p.l);
+    v = s;
+    am = fabsf(s.h);
+  }
+  block_df_partial(v, am, partial);
+}
+
+// Fine defect d = L(phi) - (s - smean) in double-float; the FP32 correction
+// problem gets f = -d and e = 0.  Per-block partials of (d^2, max |d|).
+__global__ void __launch_bounds__(kNT)
+    k_pdefect(PFine P, float smh, float sml, float *f32, float *e32, double *partial,
+              double *dout) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  float ss = 0.0f, mx = 0.0f;
+  if (t < P.ncell) {
+    const unsigned tu = (unsigned)t, q = fdiv(tu, P.fd0), q2 = fdiv(q, P.fd1);
+    const int i = (int)(tu - q * (unsigned)P.n0), j = (int)(q - q2 * (unsigned)P.n1),
+              k = (int)q2;
+    const long long sy = P.n0, sz = (long long)P.n0 * P.n1;
+    const df pi = ldf(P.phi, t);
+    df acc = {0.f, 0.f};
+    int nb = 0;  // neighbours inside
+    auto reg = [&](long long cj) {
+      acc = df_add(acc, ldf(P.phi, cj));
+      nb++;
+    };
+    auto ghost = [&](int f, long long o) {
+      // ghost 2 phi_b - phi_i: phi_b enters here, -phi_i with the diagonal
+      const df b = split_bits(P.phib[P.foff[f] + o]);
+      acc = df_add(acc, df{2.0f * b.h, 2.0f * b.l});
+    };
+    const bool pat = P.phib != nullptr;
+    if (i > 0) reg(t - 1); else if (!pat) reg(t + (P.n0 - 1)); else ghost(0, (long long)k * P.n1 + j);
+    if (i < P.n0 - 1) reg(t + 1); else if (!pat) reg(t - (P.n0 - 1)); else ghost(1, (long long)k * P.n1 + j);
+    if (j > 0) reg(t - sy); else if (!pat) reg(t + (P.n1 - 1) * sy); else ghost(2, (long long)k * P.n0 + i);
+    if (j < P.n1 - 1) reg(t + sy); else if (!pat) reg(t - (P.n1 - 1) * sy); else ghost(3, (long long)k * P.n0 + i);
+    if (k > 0) reg(t - sz); else if (!pat) reg(t + (P.n2 - 1) * sz); else ghost(4, (long long)j * P.n0 + i);
+    if (k < P.n2 - 1) reg(t + sz); else if (!pat) reg(t - (P.n2 - 1) * sz); else ghost(5, (long long)j * P.n0 + i);
+    // diagonal: -(6 + missing) phi_i = -(12 - nb) phi_i
+    acc = df_sub(acc, df_mul_f(pi, (float)(12 - nb)));
+    df d = df_mul(acc, df{P.ih2h, P.ih2l});
+    d = df_sub(d, df_sub(ldf(P.s, t), df{smh, sml}));
+    const float dv = d.h + d.l;
+    f32[t] = -dv;
+    e32[t] = 0.0f;
+    if (dout) dout[t] = join_bits(d.h, d.l);
+    ss = dv * dv;
+    mx = fabsf(dv);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_down_sync(0xffffffffu, ss, o);
+    mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  }
+  __shared__ float a[kNT / 32], b[kNT / 32];
+  if ((threadIdx.x & 31) == 0) {
+    a[threadIdx.x >> 5] = ss;
+    b[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    float m2 = 0.0f;
+    for (int w = 0; w < kNT / 32; w++) {
+      s2 += (double)a[w];
+      m2 = fmaxf(m2, b[w]);
+    }
+    partial[2 * blockIdx.x] = s2;
+    partial[2 * blockIdx.x + 1] = (double)m2;
+  }
+}
+
+// phi += e (pair arithmetic)
+__global__ void __launch_bounds__(kNT) k_pupdate(PFine P, const float *e) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= P.ncell) return;
+  const float2 p = P.phi[t];
+  df s = two_sum(p.x, e[t]);
+  s.l += p.y;
+  s = fast_two_sum(s.h, s.l);
+  P.phi[t] = make_float2(s.h, s.l);
+}
+
+// per-block sums of phi (for its mean)
+__global__ void __launch_bounds__(kNT) k_pphisum(PFine P, double *partial) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  df v = {0.f, 0.f};
+  if (t < P.ncell) v = ldf(P.phi, t);
+  block_df_partial(v, fabsf(v.h), partial);
+}
+
+// phi64 = phi - mean
+__global__ void __launch_bounds__(kNT) k_pfinal(PFine P, float mh, float ml, double *out) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= P.ncell) return;
+  const df p = df_sub(ldf(P.phi, t), df{mh, ml});
+  out[t] = join_bits(p.h, p.l);
+}
+
+// ------------------------------------------------------------------ host
+void split_host(double v, float &h, float &l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+bool on_device(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Arena {
+  frmg_ctx *c;
+  std::vector<void *> ptrs;
+  explicit Arena(frmg_ctx *c_) : c(c_) {}
+  template <typename T>
+  T *get(size_t n) {
+    void *p = frmg_alloc(c, n * sizeof(T));
+    ptrs.push_back(p);
+    return (T *)p;
+  }
+  ~Arena() {
+    for (void *p : ptrs) frmg_release(c, p);
+  }
+};
+
+// sum (and max) of per-block partials on the host, FP64
+void host_sum(const double *dpart, long long nb, double *pinned, double &sum, double &mx,
+              cudaStream_t st) {
+  PCK(cudaMemcpyAsync(pinned, dpart, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PCK(cudaStreamSynchronize(st));
+  sum = 0.0;
+  mx = 0.0;
+  for (long long b = 0; b < nb; b++) {
+    sum += pinned[2 * b];
+    mx = std::max(mx, pinned[2 * b + 1]);
+  }
+}
+
+int level_count(const int n[3]) {
+  int L = 1, m[3] = {n[0], n[1], n[2]};
+  while (true) {
+    bool ok = true;
+    for (int d = 0; d < 3; d++) ok = ok && (m[d] % 2 == 0) && (m[d] / 2 >= 4);
+    if (!ok) break;
+    for (int d = 0; d < 3; d++) m[d] /= 2;
+    L++;
+  }
+  return L;
+}
+
+struct PoissonSolver {
+  frmg_ctx *ctx;
+  cudaStream_t st;
+  std::vector<PLevel> lev;
+  int pre = 2, post = 2;
+
+  void smooth(int l, int n) {
+    const PLevel &L = lev[l];
+    for (int it = 0; it < n; it++)
+      for (int c = 0; c < 2; c++) {
+        k_lsmooth<<<nblk(L.ncell / 2), kNT, 0, st>>>(L, c);
+        PLAUNCH(ctx);
+      }
+  }
+  void vcycle(int l, double *partial0) {
+    if (l == (int)lev.size() - 1) {
+      k_lcoarsest<<<1, kNT, 0, st>>>(lev[l], 500);
+      PLAUNCH(ctx);
+      return;
+    }
+    smooth(l, pre);
+    k_lresid_restrict<<<nblk(lev[l + 1].ncell), kNT, 0, st>>>(lev[l], lev[l + 1],
+                                                             l == 0 ? partial0 : nullptr);
+    PLAUNCH(ctx);
+    vcycle(l + 1, nullptr);
+    k_lprolong<<<nblk(lev[l].ncell), kNT, 0, st>>>(lev[l], lev[l + 1]);
+    PLAUNCH(ctx);
+    smooth(l, post);
+  }
+};
+
+}  // namespace
+
+extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const double *u,
+                                const int dims[3], double box_mpc_h, double a, double omega_m,
+                                double fr0_abs, const double *phib, double h, double tol,
+                                double *phi_inout, const fr_opts *opts, fr_stats *stats,
+                                double *src_mean, void *stream) {
+  try {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!ctx || !density || !u || !dims || !phi_inout)
+      throw PError{FR_EINVAL, "NULL argument"};
+    for (int d = 0; d < 3; d++)
+      if (dims[d] < 2 || (dims[d] & 1)) throw PError{FR_EINVAL, "dims must be even and >= 2"};
+    const long long nc = (long long)dims[0] * dims[1] * dims[2];
+    if (nc >= (1ll << 31)) throw PError{FR_EINVAL, "grid too large (at most 2^31 - 1 cells)"};
+    if (!(tol >= 0)) throw PError{FR_EINVAL, "tol must be >= 0"};
+    fr_opts o;
+    fr_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.pre < 0 || o.post < 0 || o.pre + o.post < 1 || o.max_vcycles < 1 || o.max_outer < 1)
+      throw PError{FR_EINVAL, "invalid options"};
+    if (h <= 0) h = 1.0 / dims[0];
+    double k6[6];
+    int stc = fr_constants(box_mpc_h, dims[0], a, omega_m, fr0_abs, k6);
+    if (stc != FR_OK) return stc;
+    const double beta = k6[1], gamma = k6[2];
+    cudaStream_t st = (cudaStream_t)stream;
+    Arena A(ctx);
+    // inputs on the device
+    auto dev_in = [&](const double *p, long long n) -> const double * {
+      if (!p) return nullptr;
+      if (on_device(p)) return p;
+      double *d = A.get<double>(n);
+      PCK(cudaMemcpyAsync(d, p, n * sizeof(double), cudaMemcpyHostToDevice, st));
+      return d;
+    };
+    long long nface = 2ll * dims[1] * dims[2] + 2ll * dims[0] * dims[2] + 2ll * dims[0] * dims[1];
+    const double *drho = dev_in(density, nc);
+    const double *du = dev_in(u, nc);
+    const double *dphib = dev_in(phib, nface);
+    const bool phi_dev = on_device(phi_inout);
+    const double *dphi0 = dev_in(phi_inout, nc);
+    double *dphi_out = phi_dev ? phi_inout : A.get<double>(nc);
+
+    PFine P;
+    memset(&P, 0, sizeof(P));
+    P.n0 = dims[0];
+    P.n1 = dims[1];
+    P.n2 = dims[2];
+    P.ncell = nc;
+    P.fd0 = make_fastdiv((unsigned)P.n0);
+    P.fd1 = make_fastdiv((unsigned)P.n1);
+    P.phi = A.get<float2>(nc);
+    P.s = A.get<float2>(nc);
+    P.phib = dphib;
+    {
+      long long off = 0;
+      const long long fs[6] = {(long long)dims[1] * dims[2], (long long)dims[1] * dims[2],
+                               (long long)dims[0] * dims[2], (long long)dims[0] * dims[2],
+                               (long long)dims[0] * dims[1], (long long)dims[0] * dims[1]};
+      for (int f = 0; f < 6; f++) {
+        P.foff[f] = off;
+        off += fs[f];
+      }
+    }
+    split_host(1.0 / (h * h), P.ih2h, P.ih2l);
+    // multigrid levels of the correction equation
+    PoissonSolver S{ctx, st, {}, o.pre, o.post};
+    {
+      const int nl = level_count(dims);
+      int m[3] = {dims[0], dims[1], dims[2]};
+      double hl = h;
+      for (int l = 0; l < nl; l++) {
+        PLevel L;
+        L.n0 = m[0];
+        L.n1 = m[1];
+        L.n2 = m[2];
+        L.ncell = (long long)m[0] * m[1] * m[2];
+        L.fd0 = make_fastdiv((unsigned)m[0]);
+        L.fd1 = make_fastdiv((unsigned)m[1]);
+        L.h2 = (float)(hl * hl);
+        L.patch = phib != nullptr;
+        L.e = A.get<float>(L.ncell);
+        L.f = A.get<float>(L.ncell);
+        PCK(cudaMemsetAsync(L.e, 0, L.ncell * sizeof(float), st));
+        S.lev.push_back(L);
+        for (int d = 0; d < 3; d++) m[d] /= 2;
+        hl *= 2.0;
+      }
+    }
+    const long long nb = nblk(nc);
+    double *partial = A.get<double>(2 * nb);
+    double *pin = nullptr;
+    PCK(cudaMallocHost(&pin, 2 * nb * sizeof(double)));
+    struct PinFree {
+      double *p;
+      ~PinFree() {
+        if (p) cudaFreeHost(p);
+      }
+    } pinfree{pin};
+    float ln2h, ln2l, g2h, g2l, bh, bl;
+    split_host(std::log(2.0), ln2h, ln2l);
+    split_host(2.0 * gamma, g2h, g2l);
+    split_host(0.5 * beta, bh, bl);
+    k_psource<<<nb, kNT, 0, st>>>(P, drho, du, dphi0, g2h, g2l, bh, bl, ln2h, ln2l, partial);
+    PLAUNCH(ctx);
+    double ssum, smax;
+    host_sum(partial, nb, pin, ssum, smax, st);
+    const double smean = phib ? 0.0 : ssum / (double)nc;
+    if (src_mean) *src_mean = smean;
+    float smh, sml;
+    split_host(smean, smh, sml);
+
+    fr_stats sv;
+    memset(&sv, 0, sizeof(sv));
+    auto push = [&](double v) {
+      if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = v;
+    };
+    double prev = HUGE_VAL;
+    int status = FR_ENOCONV;
+    double *partial0 = A.get<double>(2 * nblk(S.lev.size() > 1 ? S.lev[1].ncell : 1));
+    for (int outer = 0; outer < o.max_outer; outer++) {
+      k_pdefect<<<nb, kNT, 0, st>>>(P, smh, sml, S.lev[0].f, S.lev[0].e, partial, nullptr);
+      PLAUNCH(ctx);
+      double s2, dmax;
+      host_sum(partial, nb, pin, s2, dmax, st);
+      const double r = std::sqrt(s2 / (double)nc);
+      if (outer == 0) sv.res0_rms = r;
+      sv.res_rms = r;
+      sv.res_max = dmax;
+      sv.outer = outer + 1;
+      push(-r);
+      if (!(r == r)) throw PError{FR_EDIVERGED, "non-finite residual"};
+      if (r <= tol) {
+        status = FR_OK;
+        break;
+      }
+      if (outer > 0 && r > prev) throw PError{FR_EDIVERGED, "defect grew"};
+      prev = r;
+      if (sv.vcycles >= o.max_vcycles) break;
+      // FP32 correction solve: stop near the FP32 floor (1e-5 of its start)
+      // or when the cycle contraction stalls
+      double rp = HUGE_VAL;
+      const long long nbc = S.lev.size() > 1 ? nblk(S.lev[1].ncell) : 0;
+      for (int k = 0; k < o.max_vcycles; k++) {
+        if (S.lev.size() == 1) {
+          k_lcoarsest<<<1, kNT, 0, st>>>(S.lev[0], 500);
+          PLAUNCH(ctx);
+          sv.vcycles++;
+          break;
+        }
+        S.vcycle(0, partial0);
+        sv.vcycles++;
+        double a2, am;
+        host_sum(partial0, nbc, pin, a2, am, st);
+        const double rr = std::sqrt(a2 / (double)nc);  // residual after pre-smoothing
+        push(rr);
+        const double pred = rp < HUGE_VAL ? rr * std::sqrt(rr / rp) : rr;
+        if (!(rr < 0.75 * rp) || rr <= 1e-5 * r || pred <= 0.5 * tol ||
+            sv.vcycles >= o.max_vcycles)
+          break;
+        rp = rr;
+      }
+      k_pupdate<<<nb, kNT, 0, st>>>(P, S.lev[0].e);
+      PLAUNCH(ctx);
+    }
+    // gauge (periodic): phi of zero mean
+    double pmean = 0.0;
+    if (!phib) {
+      k_pphisum<<<nb, kNT, 0, st>>>(P, partial);
+      PLAUNCH(ctx);
+      double psum, pm;
+      host_sum(partial, nb, pin, psum, pm, st);
+      pmean = psum / (double)nc;
+    }
+    float mh, ml;
+    split_host(pmean, mh, ml);
+    k_pfinal<<<nb, kNT, 0, st>>>(P, mh, ml, dphi_out);
+    PLAUNCH(ctx);
+    if (!phi_dev)
+      PCK(cudaMemcpyAsync(phi_inout, dphi_out, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    sv.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = sv;
+    if (status != FR_OK) frmg_set_error("no convergence within the V-cycle or outer limits");
+    return status;
+  } catch (PError &e) {
+    frmg_set_error(e.msg);
+    if (stream) cudaStreamSynchronize((cudaStream_t)stream);
+    return e.status;
+  }
+}
+
+extern "C" int fr_poisson_source(frmg_ctx *ctx, const double *density, const double *u,
+                                 const int dims[3], double box_mpc_h, double a,
+                                 double omega_m, double fr0_abs, double *s_out, void *stream) {
+  try {
+    if (!ctx || !density || !u || !dims || !s_out) throw PError{FR_EINVAL, "NULL argument"};
+    for (int d = 0; d < 3; d++)
+      if (dims[d] < 1) throw PError{FR_EINVAL, "bad dims"};
+    const long long nc = (long long)dims[0] * dims[1] * dims[2];
+    double k6[6];
+    int stc = fr_constants(box_mpc_h, dims[0], a, omega_m, fr0_abs, k6);
+    if (stc != FR_OK) return stc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Arena A(ctx);
+    auto dev_in = [&](const double *p) -> const double * {
+      if (on_device(p)) return p;
+      double *d = A.get<double>(nc);
+      PCK(cudaMemcpyAsync(d, p, nc * sizeof(double), cudaMemcpyHostToDevice, st));
+      return d;
+    };
+    const double *drho = dev_in(density), *du = dev_in(u);
+    const bool out_dev = on_device(s_out);
+    double *ds = out_dev ? s_out : A.get<double>(nc);
+    PFine P;
+    memset(&P, 0, sizeof(P));
+    P.ncell = nc;
+    P.phi = A.get<float2>(nc);
+    P.s = A.get<float2>(nc);
+    const long long nb = nblk(nc);
+    double *partial = A.get<double>(2 * nb);
+    float ln2h, ln2l, g2h, g2l, bh, bl;
+    split_host(std::log(2.0), ln2h, ln2l);
+    split_host(2.0 * k6[2], g2h, g2l);
+    split_host(0.5 * k6[1], bh, bl);
+    k_psource<<<nb, kNT, 0, st>>>(P, drho, du, nullptr, g2h, g2l, bh, bl, ln2h, ln2l, partial);
+    PLAUNCH(ctx);
+    PFine Q = P;  // k_pfinal converts its phi array: point it at the source
+    Q.phi = P.s;
+    k_pfinal<<<nb, kNT, 0, st>>>(Q, 0.f, 0.f, ds);
+    PLAUNCH(ctx);
+    if (!out_dev) PCK(cudaMemcpyAsync(s_out, ds, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    return FR_OK;
+  } catch (PError &e) {
+    frmg_set_error(e.msg);
+    return e.status;
+  }
+}

@@ -55,7 +55,7 @@ EXPORTS = ["fr_opts_default", "fr_status_string", "fr_last_error", "fr_ctx_creat
            "fr_ctx_destroy", "fr_constants", "fr_solve", "fr_solve_levels", "fr_solve_batch",
            "fr_cic_assign", "fr_smooth", "fr_residual", "fr_restrict", "fr_prolong_correct",
            "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32", "fr_residual_df",
-           "fr_residual_norm_noalloc", "fr_autotune"]
+           "fr_residual_norm_noalloc", "fr_autotune", "fr_poisson_solve", "fr_poisson_source"]
 
 
 def lib_path():
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = False):
             "fr_residual_df": (I, [P, P, P, P, D, D, D, D, D, P, P, P]),
             "fr_residual_norm_noalloc": (I, [P, P, P, D, D, D, D, D, P, P, P]),
             "fr_autotune": (I, [P, P, P, D, D, D, D, D, P, P, P, P]),
+            "fr_poisson_solve": (I, [P, P, P, P, D, D, D, D, P, D, D, P, P, P, P, P]),
+            "fr_poisson_source": (I, [P, P, P, P, D, D, D, D, P, P]),
             "fr_profile_entry": (I, [P, I, P, I, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -245,6 +247,30 @@ class Context:
         if st in raise_on:
             self._raise(st, "fr_solve")
         return st, s
+
+    def poisson(self, density, u, phi, *, box, a, omega_m, fr0, tol=1e-8, phib=None, h=None,
+                stream=None, raise_on=(FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_ETIMEOUT), **opts):
+        """Modified Poisson solve for Phi given the f(R) solution u; phi in/out.
+        Returns (status, stats, source mean removed)."""
+        _check_f64(density, "density")
+        _check_f64(u, "u")
+        _check_f64(phi, "phi")
+        o = self.opts(tol=tol, **opts)
+        s = fr_stats()
+        mean = ctypes.c_double(0.0)
+        st = self.lib.fr_poisson_solve(self._h, _ptr(density), _ptr(u), _dims(phi.shape), box, a,
+                                       omega_m, fr0, _ptr(phib), 0.0 if h is None else h, tol,
+                                       _ptr(phi), ctypes.byref(o), ctypes.byref(s),
+                                       ctypes.byref(mean), _stream(stream))
+        if st in raise_on:
+            self._raise(st, "fr_poisson_solve")
+        return st, s, mean.value
+
+    def poisson_source(self, density, u, out, *, box, a, omega_m, fr0, stream=None):
+        """The Poisson source s (FP64) of density and u into out."""
+        st = self.lib.fr_poisson_source(self._h, _ptr(density), _ptr(u), _dims(out.shape), box, a,
+                                        omega_m, fr0, _ptr(out), _stream(stream))
+        self._raise(st, "fr_poisson_source")
 
     def autotune(self, density, *, box, a, omega_m, fr0, tol=1e-8, stream=None, **base):
         """Fastest (pre, post, temporal_depth) for this problem; returns (opts dict, seconds)."""
