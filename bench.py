@@ -83,7 +83,7 @@ def parse_args():
     ap.add_argument("--prec", default="both", choices=["both", "mixed"],
                     help="'mixed' skips the FP64 comparison (profiling runs)")
     ap.add_argument("--workload", default="solve512",
-                    choices=["solve512", "batch96", "levels256", "cic128", "small32"],
+                    choices=["solve512", "batch96", "levels256", "cic128", "small32", "poisson512"],
                     help="secondary workloads print their own line (default: the 512^3 solve)")
     return ap.parse_args()
 
@@ -217,6 +217,14 @@ def grad_error(u_test, u_ref, ubar, h):
     return {"max_rel": mx / ref_max, "rms_rel": (sq / n) ** 0.5 / ref_max}
 
 
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 def timed(fn, steps, warmup):
     """Median wall time of fn() (which synchronises) over `steps` runs."""
     import torch
@@ -313,6 +321,47 @@ def run_secondary(args):
         line.update(metric="CIC of 128^3 Zel'dovich particles + solve on 128^3: cells/s",
                     value=out["a=1.0 fp64"], per_case=out, cic_ms=1e3 * tc,
                     max_contrast=float(rho.max() - 1.0))
+    elif args.workload == "poisson512":
+        # modified Poisson solve for Phi on the f(R) workload's field (512^3): the
+        # f(R) solution u is computed first (untimed), then the Poisson solve from
+        # phi = 0 to rms(L phi - s) <= 1e-8 is timed
+        from oracle import poisson as PO
+        n = N
+        rho_np = synth.lognormal_density((n, n, n), SEED, sigma=SIGMA)
+        rho = torch.from_numpy(rho_np).cuda()
+        u = torch.zeros_like(rho)
+        st, _ = ctx.solve(rho, u, tol=TOL, prec="mixed", **PHYS)
+        assert st == 0
+        phi = torch.zeros_like(rho)
+        stats = []
+
+        def run():
+            phi.zero_()
+            st, s, _ = ctx.poisson(rho, u, phi, tol=TOL, **PHYS)
+            assert st == 0
+            stats.append(s)
+        t = timed(run, args.steps, args.warmup)
+        s = stats[-1]
+        # algorithmic bytes per solve: per V(2,2) cycle on the fine level 4 sweeps x
+        # 12 B (read e, f; write e) + residual/restriction 8 B + prolongation 8 B,
+        # x 8/7 for the coarser levels; per outer step the double-float defect
+        # (phi, s pairs in: 16 B; f, e out: 8 B) and update (phi pair, e in, pair out:
+        # 20 B); the source once (rho, u in: 16 B; s, phi pairs out: 16 B)
+        alg = n ** 3 * (s.vcycles * 64.0 * 8 / 7 + s.outer * 44.0 + 32.0)
+        # CPU oracle: exact FFT solve of a bounded 128^3 sample of the same field type
+        ns = 128
+        rs = synth.lognormal_density((ns,) * 3, SEED, sigma=SIGMA)
+        us = np.zeros_like(rs)
+        t0 = time.perf_counter()
+        PO.solve_periodic(PO.source(us, rs, **PHYS), 1.0 / ns)
+        t_or = time.perf_counter() - t0
+        line.update(metric="modified Poisson solve for Phi (Eq. discrete_poisson) on the "
+                           "512^3 f(R) solution: cells/s to rms 1e-8",
+                    value=n ** 3 / t, ms=1e3 * t, vcycles=s.vcycles, outer=s.outer,
+                    res_rms=s.res_rms,
+                    effective_gbs=alg / t / 1e9,
+                    effective_frac_of_hbm=alg / t / 1e9 / _hbm_peak(),
+                    oracle_fft_128_cells_per_s=ns ** 3 / t_or)
     else:  # small32
         from oracle import oracle as O
         rho_np = synth.lognormal_density((32,) * 3, 1000, sigma=1.0)

@@ -66,7 +66,8 @@ long long nblk(long long n) { return (n + kNT - 1) / kNT; }
 
 // ------------------------------------------------------------------ device
 struct PLevel {
-  float *e;        // correction
+  float *e;        // correction (current buffer)
+  float *e_alt;    // second buffer of the tiled smoother (null: not tiled)
   float *f;        // right-hand side of the correction equation
   int n0, n1, n2;
   long long ncell;
@@ -120,6 +121,163 @@ __global__ void __launch_bounds__(kNT) k_lsmooth(PLevel L, int colour) {
   int nm;
   const float s = nbsum(L, L.e, i, j, k, c, nm);
   L.e[c] = (s - L.h2 * L.f[c]) / (6.0f + (float)nm);
+}
+
+// Tiled red-black Gauss-Seidel on L e = f, one full sweep per pass (the
+// schedule of the f(R) solver's tiled smoother): a block owns a 64 x 16 tile
+// and a chunk of zc planes and marches along z with a ring of four planes of e
+// and f in shared memory (the tile plus a halo of two cells).  At the step for
+// plane p it updates the red cells of plane p-1 on the tile grown by one cell,
+// then the black cells of plane p-2 on the tile, and writes plane p-2 to the
+// other buffer (the halos are read from the unmodified input, so the pass
+// equals one sweep of k_lsmooth).  Warps update whole rows of the tile (lane =
+// x-pair); the next plane is prefetched into registers during the updates.
+template <bool PATCH>
+__global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
+  constexpr int TX = 64, TY = 16, H = 2, LX = TX + 2 * H, LY = TY + 2 * H, PX = LX / 2;
+  constexpr int PP = PX * LY, NW = TY / 2, NT = 32 * NW, NLD = (PP + NT - 1) / NT, NS = 4;
+  constexpr int NE = TY + 2, PL = LX * LY;
+  __shared__ __align__(16) float se[NS * PL];
+  __shared__ __align__(16) float sf[NS * PL];
+  const int n0 = L.n0, n1 = L.n1, n2 = L.n2;
+  const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
+  int b = blockIdx.x;
+  const int X0 = (b % ntx) * TX;
+  b /= ntx;
+  const int Y0 = (b % nty) * TY;
+  b /= nty;
+  const int Z0 = b * zc, Z1 = min(Z0 + zc, n2);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long plane = (long long)n0 * n1;
+  const float *__restrict__ ein = L.e;
+  float *__restrict__ eout = L.e_alt;
+  const float *__restrict__ fin = L.f;
+  const float h2 = L.h2;
+  auto wrapm = [](int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+  };
+  int roff[NLD], sidx[NLD];
+  unsigned ldf[NLD];  // bit 0: load, bit 1: write out
+#pragma unroll
+  for (int k = 0; k < NLD; k++) {
+    const int q = threadIdx.x + k * NT;
+    roff[k] = 0;
+    sidx[k] = 0;
+    ldf[k] = 0;
+    if (q < PP) {
+      const int ly = q / PX, px = q - (q / PX) * PX;
+      const int gx = X0 - H + 2 * px, gy = Y0 - H + ly;
+      bool ok = true;
+      int gxw = gx, gyw = gy;
+      if (PATCH) {
+        ok = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
+      } else {
+        gxw = wrapm(gx, n0);
+        gyw = wrapm(gy, n1);
+      }
+      const bool wr = ok && ly >= H && ly < H + TY && px >= 1 && px < PX - 1 && gx < n0 &&
+                      gy < n1;
+      roff[k] = ok ? gyw * n0 + gxw : 0;
+      sidx[k] = ly * LX + 2 * px;
+      ldf[k] = (ok ? 1u : 0u) | (wr ? 2u : 0u);
+    }
+  }
+  float2 pe[NLD], pf[NLD];
+#pragma unroll
+  for (int k = 0; k < NLD; k++) {
+    pe[k] = make_float2(0.f, 0.f);
+    pf[k] = pe[k];
+  }
+  auto fetch = [&](long long zoff) {
+#pragma unroll
+    for (int k = 0; k < NLD; k++) {
+      if (!(ldf[k] & 1u)) continue;
+      pe[k] = *reinterpret_cast<const float2 *>(ein + zoff + roff[k]);
+      pf[k] = *reinterpret_cast<const float2 *>(fin + zoff + roff[k]);
+    }
+  };
+  auto commit = [&](int so) {
+#pragma unroll
+    for (int k = 0; k < NLD; k++) {
+      if (threadIdx.x + k * NT >= PP) continue;
+      *reinterpret_cast<float2 *>(&se[so + sidx[k]]) = pe[k];
+      *reinterpret_cast<float2 *>(&sf[so + sidx[k]]) = pf[k];
+    }
+  };
+  // Gauss-Seidel update of the colour-Q cell of pair (ly, px) of plane m; s is
+  // its x position in the pair; oc, om, op the slot offsets of planes m, m-1, m+1
+  auto update = [&](int ly, int px, int s, int m, int oc, int om, int op) {
+    const int lx = 2 * px + s;
+    const int gx = X0 - H + lx, gy = Y0 - H + ly;
+    if (PATCH && (gx < 0 || gx >= n0 || gy < 0 || gy >= n1)) return;
+    const int i = ly * LX + lx;
+    float sum = 0.0f;
+    int nm = 0;
+    if (!PATCH || gx > 0) sum += se[oc + i - 1]; else nm++;
+    if (!PATCH || gx < n0 - 1) sum += se[oc + i + 1]; else nm++;
+    if (!PATCH || gy > 0) sum += se[oc + i - LX]; else nm++;
+    if (!PATCH || gy < n1 - 1) sum += se[oc + i + LX]; else nm++;
+    if (!PATCH || m > 0) sum += se[om + i]; else nm++;
+    if (!PATCH || m < n2 - 1) sum += se[op + i]; else nm++;
+    se[oc + i] = (sum - h2 * sf[oc + i]) / (6.0f + (float)nm);
+  };
+  const int P0 = Z0 - H, PE = Z1 + H;
+  auto inr = [&](int pz) { return !PATCH || (pz >= 0 && pz < n2); };
+  int pw = PATCH ? P0 : wrapm(P0, n2);
+  if (inr(P0)) fetch((long long)pw * plane);
+  commit(0);
+  __syncthreads();
+  int cur = 0;
+  for (int p = P0; p < PE; p++) {
+    const bool more = p + 1 < PE;
+    pw = PATCH ? p + 1 : (pw + 1 == n2 ? 0 : pw + 1);
+    if (more && inr(p + 1)) fetch((long long)pw * plane);
+    const int o0 = cur * PL, o1 = ((cur + 3) & 3) * PL, o2 = ((cur + 2) & 3) * PL,
+              o3 = ((cur + 1) & 3) * PL;  // planes p, p-1, p-2, p-3
+    {
+      const int m = p - 1;  // red cells, tile grown by one
+      if (m >= Z0 - 1 && m < Z1 + 1 && inr(m)) {
+        const int s = (w + p) & 1;  // rows 1 + w + j NW: (ly + m) & 1
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          if (j == 2 && w >= 2) break;
+          update(1 + w + j * NW, 1 + lane, s, m, o1, o2, o0);
+        }
+        if (w == 2 || w == 3) {
+          const int idx = (w - 2) * 32 + lane;
+          if (idx < NE) {
+            const int ly = 1 + idx, se_ = (ly + m) & 1;
+            update(ly, se_ ? 0 : PX - 1, se_, m, o1, o2, o0);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    {
+      const int m = p - 2;  // black cells, tile
+      if (m >= Z0 && m < Z1 && inr(m)) {
+        const int s = (w + m + 1) & 1;  // rows 2 + w + j NW: (ly + m + 1) & 1
+#pragma unroll
+        for (int j = 0; j < 2; j++) update(2 + w + j * NW, 1 + lane, s, m, o2, o3, o1);
+      }
+    }
+    __syncthreads();
+    {
+      const int wz = p - 2;
+      if (wz >= Z0 && wz < Z1) {
+        const long long woff = (long long)wz * plane;
+#pragma unroll
+        for (int k = 0; k < NLD; k++)
+          if (ldf[k] & 2u)
+            *reinterpret_cast<float2 *>(eout + woff + roff[k]) =
+                *reinterpret_cast<const float2 *>(&se[o2 + sidx[k]]);
+      }
+    }
+    if (more) commit(o3);
+    __syncthreads();
+    cur = (cur + 1) & 3;
+  }
 }
 
 // Residual d = f - L e of the 8 children of each coarse cell, averaged into
@@ -475,13 +633,25 @@ struct PoissonSolver {
   std::vector<PLevel> lev;
   int pre = 2, post = 2;
 
+  std::vector<int> zc, nblk_t;  // tiled smoother: z-chunk and blocks per level (0: not tiled)
+
   void smooth(int l, int n) {
-    const PLevel &L = lev[l];
-    for (int it = 0; it < n; it++)
+    for (int it = 0; it < n; it++) {
+      PLevel &L = lev[l];
+      if (nblk_t[l] > 0) {
+        if (L.patch)
+          k_lsmooth_tiled<true><<<nblk_t[l], 256, 0, st>>>(L, zc[l]);
+        else
+          k_lsmooth_tiled<false><<<nblk_t[l], 256, 0, st>>>(L, zc[l]);
+        PLAUNCH(ctx);
+        std::swap(L.e, L.e_alt);
+        continue;
+      }
       for (int c = 0; c < 2; c++) {
         k_lsmooth<<<nblk(L.ncell / 2), kNT, 0, st>>>(L, c);
         PLAUNCH(ctx);
       }
+    }
   }
   void vcycle(int l, double *partial0) {
     if (l == (int)lev.size() - 1) {
@@ -567,7 +737,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
     }
     split_host(1.0 / (h * h), P.ih2h, P.ih2l);
     // multigrid levels of the correction equation
-    PoissonSolver S{ctx, st, {}, o.pre, o.post};
+    PoissonSolver S{ctx, st, {}, o.pre, o.post, {}, {}};
     {
       const int nl = level_count(dims);
       int m[3] = {dims[0], dims[1], dims[2]};
@@ -584,7 +754,38 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
         L.patch = phib != nullptr;
         L.e = A.get<float>(L.ncell);
         L.f = A.get<float>(L.ncell);
+        L.e_alt = nullptr;
         PCK(cudaMemsetAsync(L.e, 0, L.ncell * sizeof(float), st));
+        // tiled smoother on levels large enough to fill the GPU with 64 x 16
+        // tiles; z-chunks minimise (waves of 4 resident blocks per SM) x
+        // (planes per block, chunk + 4)
+        int zcl = 0, nbt = 0;
+        if (m[0] >= 32 && m[1] >= 16 && m[2] >= 8) {
+          int sms = 0, dev = 0;
+          PCK(cudaGetDevice(&dev));
+          PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+          const long long slots = 4ll * std::max(sms, 1);
+          const long long tiles = (long long)((m[0] + 63) / 64) * ((m[1] + 15) / 16);
+          double best = 1e300;
+          for (int c = 1; c <= m[2]; c++) {
+            const int z = (m[2] + c - 1) / c;
+            const long long blocks = tiles * ((m[2] + z - 1) / z);
+            const double cost = std::ceil((double)blocks / slots) * (z + 4);
+            if (cost < best - 1e-9) {
+              best = cost;
+              zcl = z;
+            }
+          }
+          const long long blocks = tiles * ((m[2] + zcl - 1) / zcl);
+          if (blocks >= sms) {
+            nbt = (int)blocks;
+            L.e_alt = A.get<float>(L.ncell);
+          } else {
+            zcl = 0;
+          }
+        }
+        S.zc.push_back(zcl);
+        S.nblk_t.push_back(nbt);
         S.lev.push_back(L);
         for (int d = 0; d < 3; d++) m[d] /= 2;
         hl *= 2.0;

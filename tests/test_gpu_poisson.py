@@ -161,3 +161,35 @@ def test_full_size_workload_sampled(C):
         src = PO.source(un[k:k + 1, j:j + 1, i:i + 1], rho_np[k:k + 1, j:j + 1, i:i + 1],
                         **PH)[0, 0, 0]
         assert abs(lap - (src - mean)) <= 10 * tol + 1e-12 * abs(src)
+
+
+def test_periodic_solve_tiled_levels_match_fft_oracle(C):
+    """128^3: the fine and 64^3 levels use the tiled smoother."""
+    shape = (128, 128, 128)
+    rho = synth.lognormal_density(shape, 71, sigma=1.5)
+    u = _u_field(shape, 72)
+    h = 1.0 / shape[2]
+    s = PO.source(u, rho, **P)
+    ref, mean = PO.solve_periodic(s, h)
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    tol = 1e-9
+    st, stats, gmean = C.poisson(dev(rho), dev(u), phi, tol=tol, **P)
+    assert st == 0 and stats.res_rms <= tol
+    assert np.abs(host(phi) - ref).max() <= 100 * tol / 39.0
+
+
+def test_patch_solve_tiled_satisfies_oracle_equation(C):
+    """A patch large enough for the tiled smoother; by uniqueness of the
+    Dirichlet problem, a small oracle residual fixes the solution."""
+    shape = (48, 64, 64)
+    rng = np.random.default_rng(13)
+    rho = synth.lognormal_density(shape, 81, sigma=1.0)
+    u = _u_field(shape, 82, amp=0.5)
+    h = 1.0 / 256
+    phib = rng.uniform(-1e-3, 1e-3, sum(O.face_sizes(shape)))
+    s = PO.source(u, rho, **P)
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    tol = 1e-8
+    st, stats, _ = C.poisson(dev(rho), dev(u), phi, tol=tol, phib=dev(phib), h=h, **P)
+    assert st == 0 and stats.res_rms <= tol
+    assert np.sqrt(np.mean(PO.residual(host(phi), s, h, phib) ** 2)) <= 2 * tol
