@@ -259,6 +259,30 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
                 fr_opts *best, double *best_seconds, void *stream);
 
 /*
+ * Triangle-shaped-cloud density assignment (Sec. VI.C, the code's default
+ * scheme): arguments and result as fr_cic_assign; each particle spreads over
+ * the 27 nearest cell centres with weights prod_d W(x_d), W = 3/4 - d^2 for the
+ * nearest centre (d = offset in cells, |d| <= 1/2) and (1/2 -+ d)^2 / 2 for its
+ * two neighbours; periodic.  FR_EINVAL if a position is outside [0, 1).
+ */
+int fr_tsc_assign(frmg_ctx *ctx, const double *pos, long long np, const int dims[3],
+                  double *density_out, void *stream);
+
+#define FR_SCHEME_CIC 0
+#define FR_SCHEME_TSC 1
+/*
+ * Force interpolation (Sec. VI.C): force_out[np][3] = -grad Phi at the
+ * particles pos[np][3] (box units, [0, 1)), the gradient by central
+ * differences on the periodic grid of phi ([n2][n1][n0], box units: h_d = 1/n_d)
+ * and interpolated with the weights of `scheme` (FR_SCHEME_CIC or
+ * FR_SCHEME_TSC: use the scheme of the density assignment, which conserves
+ * momentum).  Host or device pointers; dims >= 3; synchronous on return.
+ * FR_EINVAL for positions outside [0, 1) (their forces are set to 0).
+ */
+int fr_particle_forces(frmg_ctx *ctx, const double *phi, const int dims[3], const double *pos,
+                       long long np, int scheme, double *force_out, void *stream);
+
+/*
  * Modified Poisson equation for the potential Phi (Sec. III.B; Eq. discrete_poisson):
  *   (1/h^2) [sum of the six neighbours - 6 phi_i] = s_i,
  *   s_i = 2 gamma (rho_i - 1) - (beta/2) (e^{-u_i/2} - 1),

@@ -55,7 +55,8 @@ EXPORTS = ["fr_opts_default", "fr_status_string", "fr_last_error", "fr_ctx_creat
            "fr_ctx_destroy", "fr_constants", "fr_solve", "fr_solve_levels", "fr_solve_batch",
            "fr_cic_assign", "fr_smooth", "fr_residual", "fr_restrict", "fr_prolong_correct",
            "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32", "fr_residual_df",
-           "fr_residual_norm_noalloc", "fr_autotune", "fr_poisson_solve", "fr_poisson_source"]
+           "fr_residual_norm_noalloc", "fr_autotune", "fr_poisson_solve", "fr_poisson_source",
+           "fr_tsc_assign", "fr_particle_forces"]
 
 
 def lib_path():
@@ -101,6 +102,8 @@ def load(build_if_missing: bool = False):
             "fr_autotune": (I, [P, P, P, D, D, D, D, D, P, P, P, P]),
             "fr_poisson_solve": (I, [P, P, P, P, D, D, D, D, P, D, D, P, P, P, P, P]),
             "fr_poisson_source": (I, [P, P, P, P, D, D, D, D, P, P]),
+            "fr_tsc_assign": (I, [P, P, L, P, P, P]),
+            "fr_particle_forces": (I, [P, P, P, P, L, I, P, P]),
             "fr_profile_entry": (I, [P, I, P, I, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -330,6 +333,19 @@ class Context:
                                       ctypes.byref(o), stats, _stream(stream))
         self._raise(st, "fr_solve_levels", allow=(FR_ENOCONV, FR_EDIVERGED))
         return st, list(stats)
+
+    def tsc(self, pos, out, stream=None):
+        """TSC density of particles pos [np, 3] into out [n2, n1, n0]."""
+        st = self.lib.fr_tsc_assign(self._h, _ptr(pos), int(pos.shape[0]), _dims(out.shape),
+                                    _ptr(out), _stream(stream))
+        self._raise(st, "fr_tsc_assign")
+
+    def forces(self, phi, pos, out, scheme="tsc", stream=None):
+        """-grad Phi at the particles (same-scheme interpolation) into out [np, 3]."""
+        sc = {"cic": 0, "tsc": 1}[scheme]
+        st = self.lib.fr_particle_forces(self._h, _ptr(phi), _dims(phi.shape), _ptr(pos),
+                                         int(pos.shape[0]), sc, _ptr(out), _stream(stream))
+        self._raise(st, "fr_particle_forces")
 
     def cic(self, pos, out, stream=None):
         st = self.lib.fr_cic_assign(self._h, _ptr(pos), int(pos.shape[0]), _dims(out.shape),
