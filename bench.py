@@ -318,9 +318,24 @@ def run_secondary(args):
                     assert st == 0
                 out[f"a={a} {prec}"] = n ** 3 / timed(run, args.steps, args.warmup)
         tc = timed(lambda: ctx.cic(pos, rho), args.steps, args.warmup)
+        cic_contrast = float(rho.max() - 1.0)
+        tt = timed(lambda: ctx.tsc(pos, rho), args.steps, args.warmup)
+        tsc_contrast = float(rho.max() - 1.0)
+        # forces at the particles from a 128^3 potential (TSC, the assignment's scheme)
+        phi = torch.from_numpy(synth.gaussian_random_field((n, n, n), 7, sigma=1.0)).cuda()
+        force = torch.empty((pos.shape[0], 3), dtype=torch.float64, device="cuda")
+        tf = timed(lambda: ctx.forces(phi, pos, force, scheme="tsc"), args.steps, args.warmup)
+        from oracle import particles as PM
+        sub = pos[: 200000].cpu().numpy()
+        t0 = time.perf_counter()
+        PM.assign(sub, (n, n, n), "tsc")
+        t_or = (time.perf_counter() - t0) * pos.shape[0] / sub.shape[0]
         line.update(metric="CIC of 128^3 Zel'dovich particles + solve on 128^3: cells/s",
                     value=out["a=1.0 fp64"], per_case=out, cic_ms=1e3 * tc,
-                    max_contrast=float(rho.max() - 1.0))
+                    tsc_ms=1e3 * tt, tsc_forces_ms=1e3 * tf,
+                    oracle_tsc_ms_estimate=1e3 * t_or,
+                    particles=int(pos.shape[0]),
+                    max_contrast=cic_contrast, max_contrast_tsc=tsc_contrast)
     elif args.workload == "poisson512":
         # modified Poisson solve for Phi on the f(R) workload's field (512^3): the
         # f(R) solution u is computed first (untimed), then the Poisson solve from
