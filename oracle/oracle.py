@@ -141,6 +141,17 @@ def restrict(fine):
     return out
 
 
+def truncation_error(u, rho, *, box, a, omega_m, fr0, h=None):
+    """Truncation-error estimate of Sec. V.B.2 on the coarser grid of a periodic grid:
+    tau^h = L^H(R u) - R L^h(u), with L^H at cell size 2h and density R rho."""
+    u = _f64(u)
+    rho = _f64(rho)
+    h = 1.0 / u.shape[2] if h is None else h
+    P = dict(box=box, a=a, omega_m=omega_m, fr0=fr0)
+    return (residual(restrict(u), restrict(rho), h=2.0 * h, **P)
+            - restrict(residual(u, rho, h=h, **P)))
+
+
 def prolong_correct(uf, uH, uR, dirichlet=False):
     uf = np.array(uf, dtype=np.float64, copy=True, order="C")
     _check(_load().orc_prolong_correct(_p(uf), _p(_dims(uf.shape)), _p(_f64(uH)),

@@ -406,3 +406,29 @@ def test_cic_brute_force():
                         w *= max(0.0, 1.0 - abs(dx))
                     ref[k, j, i] += w
     assert np.abs(rho - ref).max() < 1e-12
+
+
+# ---------------------------------------------------------------- truncation error (Sec. V.B.2)
+def test_truncation_error_vanishes_on_homogeneous_solution():
+    P = dict(box=64.0, a=1.0, omega_m=0.24, fr0=1e-5)
+    tau = O.truncation_error(np.zeros((8, 8, 8)), np.ones((8, 8, 8)), **P)
+    assert np.abs(tau).max() == 0.0
+
+
+def test_truncation_error_is_second_order():
+    """For smooth fields tau^h = O(h^2): halving h divides its rms by ~4 (the
+    coarse-grid operator at 2h against the restricted fine operator)."""
+    P = dict(box=64.0, a=1.0, omega_m=0.24, fr0=1e-5)
+
+    def fields(n):
+        x = (np.arange(n) + 0.5) / n
+        z, y, xx = np.meshgrid(x, x, x, indexing="ij")
+        u = 0.6 * np.sin(2 * np.pi * xx) * np.cos(2 * np.pi * y) + 0.3 * np.sin(2 * np.pi * z)
+        rho = 1.0 + 0.4 * np.cos(2 * np.pi * (xx + z))
+        return u, rho
+
+    r = []
+    for n in (16, 32, 64):
+        u, rho = fields(n)
+        r.append(np.sqrt(np.mean(O.truncation_error(u, rho, **P) ** 2)))
+    assert 3.5 < r[0] / r[1] < 4.5 and 3.7 < r[1] / r[2] < 4.3
