@@ -76,6 +76,10 @@ typedef struct {
                                and the convergence test: 0 = double-float (pairs of FP32
                                values, ~48-bit significands, on the FP32 pipes),
                                1 = native FP64 */
+    double tau_alpha;       /* > 0: also stop once rms(L(u)) <= tau_alpha * rms(tau), tau the
+                               truncation-error estimate L^H(R u) - R L^h(u) of Sec. V.B.2
+                               on the first coarser grid (the paper asks tau_alpha <= 1/3);
+                               0 = off (default) */
 } fr_opts;
 
 #define FR_HIST 64
@@ -91,6 +95,9 @@ typedef struct {
                              mixed, the fine residual after pre-smoothing of each
                              FP32 cycle, and the FP64-accurate defect (negated)
                              at each outer step */
+    double tau_rms;   /* rms of the truncation-error estimate (tau_alpha > 0: of the
+                         last evaluation; FP64: after the last V-cycle; mixed: after
+                         the FP32 full-variable phase), NaN when not evaluated */
 } fr_stats;
 
 /* Refinement patch (Sec. V.A.1, V.B.1, VI.B): a box of fine cells at twice the

@@ -539,6 +539,42 @@ __global__ void k_fas_rhs(const Grid<T> *grids, const int *off, int ngrid, const
   f[t] = N - f[t];
 }
 
+// Truncation-error estimate of Sec. V.B.2 on the coarse grid of a V-cycle
+// level, tau = A^H(R u) - R A^h(u), after k_resid_restrict has put R u (and
+// its x) into the coarse grid and R d = R(A^h(u) - f^h) into its f: then
+// R A^h(u) = f^H + R f^h.  The density terms of the operator cancel between
+// the two and are not part of A.  One thread per coarse cell; per-block
+// partials (sum tau^2, max |tau|).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_tau(const Grid<T> *fine, const Grid<T> *coarse, const int *off, int ngrid, int fpar,
+          int cpar, double *partial) {
+  int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<T> F = view(fine, g, fpar);
+  const Grid<T> C = view(coarse, g, cpar);
+  float ss = 0.0f, mx = 0.0f;
+  long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
+  if (t < C.ncell) {
+    int I = (int)(t % C.n0);
+    long long r = t / C.n0;
+    int J = (int)(r % C.n1);
+    int K = (int)(r / C.n1);
+    T N, dN;
+    cell_eval<T, false>(C, I, J, K, t, N, dN);
+    T rf = T(0);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
+      rf += rhs_at(F, idx3(F, i, j, k));
+    }
+    const T tau = N - (C.f[t] + rf * T(0.125));
+    const float tf = (float)tau;
+    ss = tf * tf;
+    mx = fabsf(tf);
+  }
+  block_reduce2f<256>(ss, mx, &partial[2 * blockIdx.x], &partial[2 * blockIdx.x + 1]);
+}
+
 // u^h += P (u^H - R u^h), trilinear 27/9/3/1 over 64 (Sec. V.A.3); x^h refreshed.
 // One thread per coarse cell writes its 8 children: the correction
 // e = u^H - R u^h of the 3x3x3 coarse neighbourhood is interpolated separably

@@ -816,6 +816,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
 
     fr_stats sv;
     memset(&sv, 0, sizeof(sv));
+    sv.tau_rms = std::nan("");  // not evaluated by the linear solve
     auto push = [&](double v) {
       if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = v;
     };

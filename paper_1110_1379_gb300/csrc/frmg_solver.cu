@@ -1142,12 +1142,41 @@ struct SolveCfg {
   int tiling;
   int defect_fp64;   // mixed: 1 = native FP64 defect/update, 0 = double-float
   int use_graph;     // V-cycles replayed as CUDA graphs
+  double tau_alpha;  // > 0: truncation-error stopping rule (Sec. V.B.2)
 };
 
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
 
 static void hist_push(fr_stats &s, double v) {
   if (s.nhist < FR_HIST) s.hist[s.nhist++] = v;
+}
+
+// rms of the truncation-error estimate tau = A^H(R u) - R A^h(u) of every
+// problem with a coarser level (NaN for the others), from the current fine
+// u of the hierarchy's plain (full-variable) form.  Overwrites the first
+// coarser level's u, x, uR and f (the next V-cycle restricts them again).
+template <typename T>
+static std::vector<double> tau_norms(frmg_ctx *ctx, Hier<T> &H, int np, cudaStream_t st) {
+  std::vector<double> out(np, std::nan(""));
+  if (H.cont.empty() || H.cont[0].empty()) return out;
+  auto &F = H.cont[0];
+  auto &C = H.next[0];
+  k_resid_restrict<T, false><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, C.size(),
+                                                          nullptr, H.par[0], H.par[1], nullptr);
+  CK_LAUNCH(ctx);
+  k_tau<T><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, C.size(), H.par[0], H.par[1],
+                                        C.partial);
+  CK_LAUNCH(ctx);
+  reduce_partials(ctx, C.partial, C.d_off_full, C.size(), C.red_nch, C.red_tmp, C.red, st);
+  const int ng = C.size();
+  double *hp = pinned_buf(ctx, 2 * (size_t)ng);
+  CK(cudaMemcpyAsync(hp, C.red, 2 * ng * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int g = 0; g < ng; g++) {
+    const Grid<T> &G = C.h[g];
+    out[G.field] = std::sqrt(hp[2 * g] / (double)G.ncell);
+  }
+  return out;
 }
 
 // Plain FP64: V-cycles until every problem has rms <= tol.
@@ -1174,6 +1203,7 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
     stats[pi].res_rms = nr[2 * pi];
     stats[pi].res_max = nr[2 * pi + 1];
     stats[pi].vcycles = 0;
+    stats[pi].tau_rms = std::nan("");
     prev[pi] = nr[2 * pi];
     if (cfg.fixed_cycles <= 0 && nr[2 * pi] <= cfg.tol) act[pi] = 0;
     if (bad(nr[2 * pi])) throw FrError{FR_EDIVERGED, "non-finite initial residual"};
@@ -1187,9 +1217,12 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
     CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
     run_cycle(ctx, graph, cfg.use_graph, st, [&]() { vcycle<double, false>(ctx, H, 0, co, active, st); });
     level_norms<double, false>(ctx, H.all[0], nullptr, nullptr, st, nr);
+    std::vector<double> tau;
+    if (cfg.tau_alpha > 0) tau = tau_norms<double>(ctx, H, np, st);
     for (int pi = 0; pi < np; pi++) {
       if (!act[pi]) continue;
       stats[pi].vcycles++;
+      if (cfg.tau_alpha > 0) stats[pi].tau_rms = tau[pi];
       stats[pi].res_rms = nr[2 * pi];
       stats[pi].res_max = nr[2 * pi + 1];
       hist_push(stats[pi], nr[2 * pi]);
@@ -1197,7 +1230,11 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
       grow[pi] = nr[2 * pi] > prev[pi] ? grow[pi] + 1 : 0;
       if (grow[pi] >= 5) throw FrError{FR_EDIVERGED, "residual grew for 5 cycles"};
       prev[pi] = nr[2 * pi];
-      if (cfg.fixed_cycles <= 0 && nr[2 * pi] <= cfg.tol) act[pi] = 0;
+      // Sec. V.B.2: |d| <~ tau_alpha |tau| also ends the iteration
+      const double lim = cfg.tau_alpha > 0 && tau[pi] == tau[pi]
+                             ? std::max(cfg.tol, cfg.tau_alpha * tau[pi])
+                             : cfg.tol;
+      if (cfg.fixed_cycles <= 0 && nr[2 * pi] <= lim) act[pi] = 0;
     }
   }
 }
@@ -1239,7 +1276,16 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
   for (int pi = 0; pi < np; pi++) {
     stats[pi].vcycles = 0;
     stats[pi].outer = 0;
+    stats[pi].tau_rms = std::nan("");
   }
+  // truncation-error estimate of the full-variable FP32 phase (Sec. V.B.2);
+  // with tau_alpha > 0, rms(d) <= tau_alpha rms(tau) also ends the solve
+  std::vector<double> tau(np, std::nan(""));
+  auto tol_of = [&](int pi) {
+    stats[pi].tau_rms = tau[pi];
+    return cfg.tau_alpha > 0 && tau[pi] == tau[pi] ? std::max(cfg.tol, cfg.tau_alpha * tau[pi])
+                                                  : cfg.tol;
+  };
   auto update = [&]() {
     for (int pi = 0; pi < np; pi++) {
       if (!act[pi]) continue;
@@ -1325,6 +1371,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
     }
     // stop well above the FP32 rounding floor; the correction solves finish
     inner(false, r0, 1e-4, 40);
+    if (cfg.tau_alpha > 0) tau = tau_norms<float>(ctx, H, np, st);
     update();
   } else {
     for (int pi = 0; pi < np; pi++) {
@@ -1350,7 +1397,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
         if (grow[pi] >= 3) throw FrError{FR_EDIVERGED, "FP64 defect grew for 3 outer steps"};
       }
       prev[pi] = nr[2 * pi];
-      if (nr[2 * pi] <= cfg.tol || stats[pi].vcycles >= cfg.max_vcycles)
+      if (nr[2 * pi] <= tol_of(pi) || stats[pi].vcycles >= cfg.max_vcycles)
         act[pi] = 0;
       else
         nact++;
@@ -1508,7 +1555,16 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   for (int pi = 0; pi < np; pi++) {
     stats[pi].vcycles = 0;
     stats[pi].outer = 0;
+    stats[pi].tau_rms = std::nan("");
   }
+  // truncation-error estimate of the full-variable FP32 phase (Sec. V.B.2);
+  // with tau_alpha > 0, rms(d) <= tau_alpha rms(tau) also ends the solve
+  std::vector<double> tau(np, std::nan(""));
+  auto tol_of = [&](int pi) {
+    stats[pi].tau_rms = tau[pi];
+    return cfg.tau_alpha > 0 && tau[pi] == tau[pi] ? std::max(cfg.tol, cfg.tau_alpha * tau[pi])
+                                                  : cfg.tol;
+  };
   auto update = [&]() {
     for (int pi = 0; pi < np; pi++) {
       if (!act[pi]) continue;
@@ -1583,6 +1639,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
       }
       // stop well above the FP32 rounding floor; the correction solves finish
       inner(false, r0, 1e-4, 40);
+      if (cfg.tau_alpha > 0) tau = tau_norms<float>(ctx, H, np, st);
       update();
     }
     for (int outer = 0; outer < cfg.max_outer; outer++) {
@@ -1610,7 +1667,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
           if (grow[pi] >= 3) throw FrError{FR_EDIVERGED, "defect grew for 3 outer steps"};
         }
         prev[pi] = nr[2 * pi];
-        if (nr[2 * pi] <= cfg.tol || stats[pi].vcycles >= cfg.max_vcycles)
+        if (nr[2 * pi] <= tol_of(pi) || stats[pi].vcycles >= cfg.max_vcycles)
           act[pi] = 0;
         else
           nact++;
@@ -1744,12 +1801,13 @@ static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &
   cudaStream_t st = side.st;
   SolveCfg cfg{tol, o.max_vcycles, o.pre, o.post, o.newton_step_cap, o.inner_cycles,
                o.max_outer, fixed, o.temporal_depth <= 0 ? 1 : o.temporal_depth, o.tiling,
-               o.defect_precision, o.use_graph};
+               o.defect_precision, o.use_graph, o.tau_alpha};
   if (o.defect_precision < 0 || o.defect_precision > 1) einval("defect_precision must be 0 or 1");
   if (cfg.tdepth > 2) einval("temporal_depth must be 0, 1 or 2");
   if (o.pre < 0 || o.post < 0 || o.max_vcycles < 0 || !(o.newton_step_cap > 0) ||
       !(tol >= 0) || o.inner_cycles < 1 || o.max_outer < 1)
     einval("invalid options");
+  if (!(o.tau_alpha >= 0)) einval("tau_alpha must be >= 0");
   for (auto &p : P) {
     p.nl = count_levels(p.n);
     p.k = model_consts(p.box, p.h, p.a, p.om, p.fr0);
@@ -1764,9 +1822,16 @@ static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &
     solve_fp64(ctx, P, cfg, stats, st);
 }
 
-static int status_from_stats(const std::vector<fr_stats> &stats, double tol) {
-  for (auto &s : stats)
-    if (!(s.res_rms <= tol)) return FR_ENOCONV;
+// FR_OK when every grid reached tol, or (tau_alpha > 0) tau_alpha times the
+// rms of its truncation-error estimate (Sec. V.B.2).
+static int status_from_stats(const std::vector<fr_stats> &stats, double tol,
+                             double tau_alpha = 0.0) {
+  for (auto &s : stats) {
+    const double lim = tau_alpha > 0 && s.tau_rms == s.tau_rms
+                           ? std::max(tol, tau_alpha * s.tau_rms)
+                           : tol;
+    if (!(s.res_rms <= lim)) return FR_ENOCONV;
+  }
   return FR_OK;
 }
 
@@ -1913,6 +1978,7 @@ void fr_opts_default(fr_opts *o) {
   o->temporal_depth = 0;
   o->tiling = 0;
   o->defect_precision = 0;
+  o->tau_alpha = 0.0;
 }
 
 const char *fr_status_string(int s) {
@@ -2035,7 +2101,7 @@ static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], d
     int status = FR_OK;
     try {
       run_problems(ctx, P, o, tol, sv, st, fixed);
-      status = fixed > 0 ? FR_OK : status_from_stats(sv, tol);
+      status = fixed > 0 ? FR_OK : status_from_stats(sv, tol, o.tau_alpha);
     } catch (FrError &e) {
       if (e.status != FR_EDIVERGED) throw;
       status = e.status;
@@ -2158,7 +2224,7 @@ int fr_solve_batch(frmg_ctx *ctx, int nfields, const double *const *density, con
     int status = FR_OK;
     try {
       run_problems(ctx, P, o, tol, sv, st);
-      status = status_from_stats(sv, tol);
+      status = status_from_stats(sv, tol, o.tau_alpha);
     } catch (FrError &e) {
       if (e.status != FR_EDIVERGED) throw;
       status = e.status;
@@ -2221,7 +2287,7 @@ int fr_solve_levels(frmg_ctx *ctx, const double *density, const int dims[3], dou
     auto run = [&](std::vector<Problem> &P, std::vector<fr_stats> &sv, double tl) {
       try {
         run_problems(ctx, P, o, tl, sv, st);
-        int s2 = status_from_stats(sv, tl);
+        int s2 = status_from_stats(sv, tl, o.tau_alpha);
         if (s2 != FR_OK && status == FR_OK) status = s2;
       } catch (FrError &e) {
         if (e.status != FR_EDIVERGED) throw;

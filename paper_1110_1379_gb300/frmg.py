@@ -28,7 +28,8 @@ class fr_opts(ctypes.Structure):
                 ("newton_step_cap", ctypes.c_double), ("inner_cycles", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("allow_negative_density", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("temporal_depth", ctypes.c_int),
-                ("tiling", ctypes.c_int), ("defect_precision", ctypes.c_int)]
+                ("tiling", ctypes.c_int), ("defect_precision", ctypes.c_int),
+                ("tau_alpha", ctypes.c_double)]
 
 
 FR_HIST = 64
@@ -38,7 +39,8 @@ class fr_stats(ctypes.Structure):
     _fields_ = [("vcycles", ctypes.c_int), ("outer", ctypes.c_int),
                 ("res0_rms", ctypes.c_double), ("res_rms", ctypes.c_double),
                 ("res_max", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("nhist", ctypes.c_int), ("hist", ctypes.c_double * FR_HIST)]
+                ("nhist", ctypes.c_int), ("hist", ctypes.c_double * FR_HIST),
+                ("tau_rms", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}

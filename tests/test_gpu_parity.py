@@ -411,3 +411,36 @@ def test_graph_replay_batch_with_fields_leaving(C):
     for a, b in zip(res[0][0], res[1][0]):
         assert np.array_equal(a, b)
     assert res[0][1] == res[1][1]
+
+
+# ------------------------------------------------------- truncation-error rule (Sec. V.B.2)
+def test_truncation_error_rule_fp64_matches_oracle(C):
+    """FP64 solve with tau_alpha = 1/3: the reported tau is the oracle's
+    L^H(R u) - R L^h(u) at the returned u (same arithmetic class, FP64), and the
+    solve stops once rms(d) <= tau_alpha rms(tau), before a tight tolerance."""
+    shape = (32, 32, 32)
+    rho = _field(shape, 1000, sigma=1.0)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s = C.solve(dev(rho), u, tol=1e-13, prec="fp64", tau_alpha=1.0 / 3.0, **CFG1)
+    assert st == 0
+    tau = O.truncation_error(host(u), rho, **CFG1)
+    tref = float(np.sqrt(np.mean(tau ** 2)))
+    # the GPU sums tau^2 per block in FP32 (256 terms): ~1e-6 relative on the norm
+    assert s.tau_rms == pytest.approx(tref, rel=1e-5)
+    assert s.res_rms <= max(1e-13, s.tau_rms / 3.0)
+    u2 = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st2, s2 = C.solve(dev(rho), u2, tol=1e-13, prec="fp64", **CFG1)
+    assert st2 == 0 and s2.vcycles > s.vcycles and np.isnan(s2.tau_rms)
+
+
+def test_truncation_error_rule_mixed(C):
+    """Mixed solve: tau from the FP32 full-variable phase, close to the oracle's
+    tau at the returned u; the defect ends below tau_alpha rms(tau)."""
+    shape = (32, 32, 32)
+    rho = _field(shape, 1000, sigma=1.0)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s = C.solve(dev(rho), u, tol=1e-13, prec="mixed", tau_alpha=1.0 / 3.0, **CFG1)
+    assert st == 0
+    tref = float(np.sqrt(np.mean(O.truncation_error(host(u), rho, **CFG1) ** 2)))
+    assert s.tau_rms == pytest.approx(tref, rel=2e-2)
+    assert s.res_rms <= s.tau_rms / 3.0
