@@ -33,7 +33,7 @@ SEED = 3000
 TOL = 1e-8
 def workload(n):
     return (f"{n}^3 periodic, box 256 Mpc/h, a=1, Om=0.24, |f_R0|=1e-5, lognormal sigma=2.0 "
-            f"P(k)~k^-1.5 seed {SEED}, u0=0, red-black NGS V-cycles (shape from fr_autotune), "
+            f"P(k)~k^-1.5 seed {SEED}, u0=0, red-black NGS V-cycles (shape and relaxation from fr_autotune), "
             f"rms tol 1e-8")
 
 
@@ -358,20 +358,39 @@ def run_secondary(args):
         assert st == 0
         phi = torch.zeros_like(rho)
         stats = []
+        # untimed choice of the V-cycle shape and over-relaxation factor of the
+        # red-black sweeps: fastest of a few candidates on this field (best of 2)
+        cands = [(2, 2, 1.0), (1, 1, 1.2), (2, 1, 1.25), (2, 2, 1.25)]
+        ctimes = {}
+        for pre, post, w in cands:
+            ts, ok = [], True
+            for _ in range(2):
+                phi.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, _, _ = ctx.poisson(rho, u, phi, tol=TOL, pre=pre, post=post, relax=w, **PHYS)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+                ok = ok and st == 0
+            if ok:
+                ctimes[(pre, post, w)] = min(ts)
+        pre, post, w = min(ctimes, key=ctimes.get)
+        ptuned = dict(pre=pre, post=post, relax=w)
 
         def run():
             phi.zero_()
-            st, s, _ = ctx.poisson(rho, u, phi, tol=TOL, **PHYS)
+            st, s, _ = ctx.poisson(rho, u, phi, tol=TOL, **ptuned, **PHYS)
             assert st == 0
             stats.append(s)
         t = timed(run, args.steps, args.warmup)
         s = stats[-1]
-        # algorithmic bytes per solve: per V(2,2) cycle on the fine level 4 sweeps x
-        # 12 B (read e, f; write e) + residual/restriction 8 B + prolongation 8 B,
+        # algorithmic bytes per solve: per V(pre,post) cycle on the fine level
+        # pre + post sweeps x 12 B (read e, f; write e) + residual/restriction 8 B
+        # + prolongation 8 B,
         # x 8/7 for the coarser levels; per outer step the double-float defect
         # (phi, s pairs in: 16 B; f, e out: 8 B) and update (phi pair, e in, pair out:
         # 20 B); the source once (rho, u in: 16 B; s, phi pairs out: 16 B)
-        alg = n ** 3 * (s.vcycles * 64.0 * 8 / 7 + s.outer * 44.0 + 32.0)
+        alg = n ** 3 * (s.vcycles * (12.0 * (pre + post) + 16.0) * 8 / 7 + s.outer * 44.0 + 32.0)
         # CPU oracle: exact FFT solve of a bounded 128^3 sample of the same field type
         ns = 128
         rs = synth.lognormal_density((ns,) * 3, SEED, sigma=SIGMA)
@@ -382,6 +401,8 @@ def run_secondary(args):
         line.update(metric="modified Poisson solve for Phi (Eq. discrete_poisson) on the "
                            "512^3 f(R) solution: cells/s to rms 1e-8",
                     value=n ** 3 / t, ms=1e3 * t, vcycles=s.vcycles, outer=s.outer,
+                    tuned={**ptuned, "candidates_s": {f"V({a},{b}) w={c}": v
+                                                      for (a, b, c), v in ctimes.items()}},
                     res_rms=s.res_rms,
                     effective_gbs=alg / t / 1e9,
                     effective_frac_of_hbm=alg / t / 1e9 / _hbm_peak(),
@@ -461,9 +482,10 @@ def main():
     for _ in range(args.warmup):
         solve("mixed")
     torch.cuda.synchronize()
-    # autotuner (untimed): V-cycle shape and sweeps per tiled pass for this workload
+    # autotuner (untimed): V-cycle shape, relaxation factor and sweeps per tiled
+    # pass for this workload
     best, tune_s = ctx.autotune(rho, tol=TOL, prec="mixed", stream=stream, **PHYS)
-    tuned = {k: best[k] for k in ("pre", "post", "temporal_depth")}
+    tuned = {k: best[k] for k in ("pre", "post", "temporal_depth", "relax")}
     solve("mixed")
     torch.cuda.synchronize()
     barrier()
@@ -614,7 +636,8 @@ def main():
         "mixed_vs_fp64_speedup": (value / world / fp64_value) if fp64_value else None,
         "autotuned": {**tuned, "tune_seconds": tune_s,
                       "note": "fastest of V(pre,post) in {(1,1),(2,1),(1,2),(2,2),(3,3)} x "
-                              "sweeps per tiled pass {1,2}, chosen by fr_autotune on this field"},
+                              "relaxation factor {1,1.15,1.25}, then sweeps per tiled pass "
+                              "{1,2}, chosen by fr_autotune on this field"},
         "mixed_default_v22": {"value": value_default, "unit": "cells/s",
                               "vcycles": s_def.vcycles, "outer": s_def.outer},
         "mixed": {"vcycles": s0.vcycles, "outer": s0.outer, "res_rms": s0.res_rms,

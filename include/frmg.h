@@ -80,6 +80,12 @@ typedef struct {
                                truncation-error estimate L^H(R u) - R L^h(u) of Sec. V.B.2
                                on the first coarser grid (the paper asks tau_alpha <= 1/3);
                                0 = off (default) */
+    double relax;           /* relaxation factor w of every Newton-Gauss-Seidel update,
+                               u += w * du (the Newton-GS step of Sec. V.B.2 is w = 1, the default);
+                               0 < w < 2.
+                               Over-relaxing the red-black sweeps (w ~ 1.1-1.2) can lower
+                               the V-cycle's convergence factor; the solution is the
+                               same, only the path to it changes.  FR_EINVAL outside (0, 2). */
 } fr_opts;
 
 #define FR_HIST 64
@@ -254,9 +260,10 @@ int fr_residual_norm_noalloc(const double *u, const double *density, const int d
 
 /*
  * Autotuner: solves the given problem from u = 0 (into library scratch; the
- * caller's arrays are only read) with every candidate setting of the V-cycle
- * shape (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)} and the tiled
- * smoother's sweeps per pass (temporal_depth 1 or 2), on top of *base (NULL =
+ * caller's arrays are only read) with every combination of the V-cycle shape
+ * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)} and the relaxation factor
+ * relax in {1, 1.15, 1.25} at one sweep per tiled pass, then with two sweeps
+ * per pass (temporal_depth 2) for the fastest of those, on top of *base (NULL =
  * defaults), twice each, and writes the fastest setting that reaches tol to
  * *best (and its time in seconds to *best_seconds, if not NULL).  Device or
  * host density pointer.  FR_ENOCONV if no candidate converged.
@@ -307,7 +314,8 @@ int fr_particle_forces(frmg_ctx *ctx, const double *phi, const int dims[3], cons
  * h = the patch's cell size in code units (h <= 0: 1 / dims[0]).
  * Multigrid in the correction scheme (Sec. V.A.2, Eq. bc_modified_poisson_coarse;
  * trilinear prolongation of Sec. V.A.3): FP32 V-cycles (opts->pre / opts->post
- * red-black Gauss-Seidel sweeps) on the correction equation inside a defect
+ * red-black Gauss-Seidel sweeps, over-relaxed by opts->relax) on the
+ * correction equation inside a defect
  * correction whose defect and update are evaluated in double-float (~48-bit)
  * arithmetic.  Stops when the rms of L(phi) - s is <= tol (FR_OK); FR_ENOCONV
  * after opts->max_outer outer steps or opts->max_vcycles V-cycles (phi holds

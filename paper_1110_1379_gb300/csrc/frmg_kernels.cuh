@@ -56,6 +56,7 @@ struct Grid {
   T beta;
   T fs, fo;
   T cap;           // Newton step cap
+  T relax;         // relaxation factor of the Newton update (1: plain Newton-GS)
 };
 
 // ----------------------------------------------------------------------------
@@ -322,7 +323,7 @@ __device__ __forceinline__ void ngs_update(const Grid<T> &G, int i, int j, int k
   long long c = idx3(G, i, j, k);
   T N, dN;
   cell_eval<T, BG>(G, i, j, k, c, N, dN);
-  T du = newton_step(N - rhs_at(G, c), dN);
+  T du = G.relax * newton_step(N - rhs_at(G, c), dN);
   du = du > G.cap ? G.cap : (du < -G.cap ? -G.cap : du);
   T unew = G.u[c] + du;
   G.u[c] = unew;
@@ -983,7 +984,8 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
   const float *__restrict__ fin = Gg.f;
   const float *__restrict__ ubin = Gg.ubg;
   const float *__restrict__ Ein = Gg.Ebg;
-  const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap;
+  const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap,
+              relax = Gg.relax;
   const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
   constexpr bool dir = DIR;  // patch (Dirichlet faces) or periodic grid
   const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
@@ -1113,7 +1115,7 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
       A.done(acc, dacc);
       float N, dN;
       finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-      float du = newton_step(N - sf[o], dN);
+      float du = relax * newton_step(N - sf[o], dN);
       du = fminf(fmaxf(du, -cap), cap);
       const float dn = di + du;
       sd[o] = dn;
@@ -1228,7 +1230,8 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
   const float *__restrict__ fin = Gg.f;
   const float *__restrict__ ubin = Gg.ubg;
   const float *__restrict__ Ein = Gg.Ebg;
-  const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap;
+  const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap,
+              relax = Gg.relax;
   const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
   const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
   int b = blockIdx.x - off[g];
@@ -1362,7 +1365,7 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
     A.done(acc, dacc);
     float N, dN;
     finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-    float du = newton_step(N - sfv[ofq + cq + e], dN);
+    float du = relax * newton_step(N - sfv[ofq + cq + e], dN);
     du = fminf(fmaxf(du, -cap), cap);
     const float dn = di + du;
     put_ux(oc + cq + e, dn, m_expm1(dn));

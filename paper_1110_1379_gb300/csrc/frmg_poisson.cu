@@ -73,6 +73,7 @@ struct PLevel {
   long long ncell;
   FastDiv fd0, fd1;
   float h2;        // h^2
+  float relax;     // relaxation factor of the smoother (1: Gauss-Seidel)
   int patch;       // 1: Dirichlet (ghost = -e on the boundary), 0: periodic
 };
 
@@ -108,7 +109,8 @@ __device__ __forceinline__ float nbsum(const PLevel &L, const float *e, int i, i
 }
 
 // Red-black Gauss-Seidel on L e = f (one colour per launch): with the ghosts
-// -e_i on patch faces, e_i = (sum of the neighbours in the grid - h^2 f_i) / (6 + missing).
+// -e_i on patch faces, e_i = (sum of the neighbours in the grid - h^2 f_i) / (6 + missing),
+// over-relaxed as e_i += w (that value - e_i) when relax = w != 1.
 __global__ void __launch_bounds__(kNT) k_lsmooth(PLevel L, int colour) {
   const long long half = L.ncell / 2;
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
@@ -120,7 +122,8 @@ __global__ void __launch_bounds__(kNT) k_lsmooth(PLevel L, int colour) {
   const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
   int nm;
   const float s = nbsum(L, L.e, i, j, k, c, nm);
-  L.e[c] = (s - L.h2 * L.f[c]) / (6.0f + (float)nm);
+  const float gs = (s - L.h2 * L.f[c]) / (6.0f + (float)nm);
+  L.e[c] = fmaf(L.relax, gs - L.e[c], L.e[c]);
 }
 
 // Tiled red-black Gauss-Seidel on L e = f, one full sweep per pass (the
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
   const float *__restrict__ ein = L.e;
   float *__restrict__ eout = L.e_alt;
   const float *__restrict__ fin = L.f;
-  const float h2 = L.h2;
+  const float h2 = L.h2, relax = L.relax;
   auto wrapm = [](int v, int n) {
     int r = v % n;
     return r < 0 ? r + n : r;
@@ -220,7 +223,8 @@ __global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
     if (!PATCH || gy < n1 - 1) sum += se[oc + i + LX]; else nm++;
     if (!PATCH || m > 0) sum += se[om + i]; else nm++;
     if (!PATCH || m < n2 - 1) sum += se[op + i]; else nm++;
-    se[oc + i] = (sum - h2 * sf[oc + i]) / (6.0f + (float)nm);
+    const float gs = (sum - h2 * sf[oc + i]) / (6.0f + (float)nm);
+    se[oc + i] = fmaf(relax, gs - se[oc + i], se[oc + i]);
   };
   const int P0 = Z0 - H, PE = Z1 + H;
   auto inr = [&](int pz) { return !PATCH || (pz >= 0 && pz < n2); };
@@ -593,7 +597,12 @@ struct Arena {
   explicit Arena(frmg_ctx *c_) : c(c_) {}
   template <typename T>
   T *get(size_t n) {
-    void *p = frmg_alloc(c, n * sizeof(T));
+    void *p = nullptr;
+    try {
+      p = frmg_alloc(c, n * sizeof(T));
+    } catch (...) {
+      throw PError{FR_ENOMEM, "device allocation failed"};
+    }
     ptrs.push_back(p);
     return (T *)p;
   }
@@ -602,18 +611,62 @@ struct Arena {
   }
 };
 
-// sum (and max) of per-block partials on the host, FP64
-void host_sum(const double *dpart, long long nb, double *pinned, double &sum, double &mx,
-              cudaStream_t st) {
-  PCK(cudaMemcpyAsync(pinned, dpart, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-  PCK(cudaStreamSynchronize(st));
-  sum = 0.0;
-  mx = 0.0;
-  for (long long b = 0; b < nb; b++) {
-    sum += pinned[2 * b];
-    mx = std::max(mx, pinned[2 * b + 1]);
+// Sum and max of n (sum, max) pairs of per-block partials: block b reduces
+// pairs [b kRedCH, (b + 1) kRedCH) in a fixed order (FP64) into pair b of out.
+constexpr int kRedCH = 4096;
+__global__ void __launch_bounds__(kNT) k_psum_pairs(const double *in, long long n, double *out) {
+  __shared__ double ss[kNT / 32], sm[kNT / 32];
+  const long long b0 = (long long)blockIdx.x * kRedCH;
+  const long long b1 = b0 + kRedCH < n ? b0 + kRedCH : n;
+  double s = 0.0, m = 0.0;
+  for (long long i = b0 + threadIdx.x; i < b1; i += kNT) {
+    s += in[2 * i];
+    m = fmax(m, in[2 * i + 1]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ss[threadIdx.x >> 5] = s;
+    sm[threadIdx.x >> 5] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0, mm = 0.0;
+    for (int w = 0; w < kNT / 32; w++) {
+      t += ss[w];
+      mm = fmax(mm, sm[w]);
+    }
+    out[2 * blockIdx.x] = t;
+    out[2 * blockIdx.x + 1] = mm;
   }
 }
+
+// Device-side sum (and max) of nb partial pairs in one or two reduction
+// launches; only the final pair crosses to the host.  tmp holds at least
+// 2 (ceil(nb / kRedCH) + 1) doubles; nb <= kRedCH^2.
+struct PartialSum {
+  frmg_ctx *ctx;
+  double *tmp;
+  double *pinned;
+  cudaStream_t st;
+  void operator()(const double *dpart, long long nb, double &sum, double &mx) const {
+    const long long n2 = (nb + kRedCH - 1) / kRedCH;
+    k_psum_pairs<<<(unsigned)n2, kNT, 0, st>>>(dpart, nb, tmp);
+    PLAUNCH(ctx);
+    const double *res = tmp;
+    if (n2 > 1) {
+      k_psum_pairs<<<1, kNT, 0, st>>>(tmp, n2, tmp + 2 * n2);
+      PLAUNCH(ctx);
+      res = tmp + 2 * n2;
+    }
+    PCK(cudaMemcpyAsync(pinned, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    sum = pinned[0];
+    mx = pinned[1];
+  }
+};
 
 int level_count(const int n[3]) {
   int L = 1, m[3] = {n[0], n[1], n[2]};
@@ -691,6 +744,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
     if (opts) o = *opts;
     if (o.pre < 0 || o.post < 0 || o.pre + o.post < 1 || o.max_vcycles < 1 || o.max_outer < 1)
       throw PError{FR_EINVAL, "invalid options"};
+    if (!(o.relax > 0 && o.relax < 2)) throw PError{FR_EINVAL, "relax must be in (0, 2)"};
     if (h <= 0) h = 1.0 / dims[0];
     double k6[6];
     int stc = fr_constants(box_mpc_h, dims[0], a, omega_m, fr0_abs, k6);
@@ -751,6 +805,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
         L.fd0 = make_fastdiv((unsigned)m[0]);
         L.fd1 = make_fastdiv((unsigned)m[1]);
         L.h2 = (float)(hl * hl);
+        L.relax = (float)o.relax;
         L.patch = phib != nullptr;
         L.e = A.get<float>(L.ncell);
         L.f = A.get<float>(L.ncell);
@@ -793,14 +848,10 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
     }
     const long long nb = nblk(nc);
     double *partial = A.get<double>(2 * nb);
-    double *pin = nullptr;
-    PCK(cudaMallocHost(&pin, 2 * nb * sizeof(double)));
-    struct PinFree {
-      double *p;
-      ~PinFree() {
-        if (p) cudaFreeHost(p);
-      }
-    } pinfree{pin};
+    double *pin = frmg_pinned(ctx, 2);
+    if (!pin) throw PError{FR_ENOMEM, "pinned host allocation failed"};
+    if (nb > (long long)kRedCH * kRedCH) throw PError{FR_EINVAL, "grid too large"};
+    const PartialSum psum{ctx, A.get<double>(2 * ((nb + kRedCH - 1) / kRedCH + 1)), pin, st};
     float ln2h, ln2l, g2h, g2l, bh, bl;
     split_host(std::log(2.0), ln2h, ln2l);
     split_host(2.0 * gamma, g2h, g2l);
@@ -808,7 +859,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
     k_psource<<<nb, kNT, 0, st>>>(P, drho, du, dphi0, g2h, g2l, bh, bl, ln2h, ln2l, partial);
     PLAUNCH(ctx);
     double ssum, smax;
-    host_sum(partial, nb, pin, ssum, smax, st);
+    psum(partial, nb, ssum, smax);
     const double smean = phib ? 0.0 : ssum / (double)nc;
     if (src_mean) *src_mean = smean;
     float smh, sml;
@@ -827,7 +878,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
       k_pdefect<<<nb, kNT, 0, st>>>(P, smh, sml, S.lev[0].f, S.lev[0].e, partial, nullptr);
       PLAUNCH(ctx);
       double s2, dmax;
-      host_sum(partial, nb, pin, s2, dmax, st);
+      psum(partial, nb, s2, dmax);
       const double r = std::sqrt(s2 / (double)nc);
       if (outer == 0) sv.res0_rms = r;
       sv.res_rms = r;
@@ -856,7 +907,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
         S.vcycle(0, partial0);
         sv.vcycles++;
         double a2, am;
-        host_sum(partial0, nbc, pin, a2, am, st);
+        psum(partial0, nbc, a2, am);
         const double rr = std::sqrt(a2 / (double)nc);  // residual after pre-smoothing
         push(rr);
         const double pred = rp < HUGE_VAL ? rr * std::sqrt(rr / rp) : rr;
@@ -873,9 +924,9 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
     if (!phib) {
       k_pphisum<<<nb, kNT, 0, st>>>(P, partial);
       PLAUNCH(ctx);
-      double psum, pm;
-      host_sum(partial, nb, pin, psum, pm, st);
-      pmean = psum / (double)nc;
+      double phisum, pm;
+      psum(partial, nb, phisum, pm);
+      pmean = phisum / (double)nc;
     }
     float mh, ml;
     split_host(pmean, mh, ml);

@@ -191,6 +191,14 @@ static double *pinned_buf(frmg_ctx *c, size_t n) {
   return c->pinned;
 }
 
+double *frmg_pinned(frmg_ctx *c, size_t n) {
+  try {
+    return pinned_buf(c, n);
+  } catch (...) {
+    return nullptr;
+  }
+}
+
 // Allocations of one call, returned to the cache on scope exit.
 struct Scope {
   frmg_ctx *c;
@@ -647,7 +655,7 @@ struct Hier {
 
 template <typename T, bool BG>
 static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap,
-                       cudaStream_t st, frmg_ctx *ctx, int tiling = 0) {
+                       cudaStream_t st, frmg_ctx *ctx, int tiling = 0, double relax = 1.0) {
   int np = (int)P.size();
   H.lev.assign(np, {});
   H.depth = 0;
@@ -671,6 +679,7 @@ static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap
       G.ah = (T)(0.5 * k.alpha);
       G.beta = (T)k.beta;
       G.cap = (T)cap;
+      G.relax = (T)relax;
       face_offsets(n, G.foff);
       bool fine_fp64_plain = (l == 0 && !BG && sizeof(T) == 8);
       if (fine_fp64_plain) {
@@ -879,10 +888,13 @@ static void launch_tiled(frmg_ctx *ctx, LevelSet<float> &s, const int *active, i
 }
 
 // Passes of the tiled smoother (sweeps per pass) for the pre- and post-smoothing
-// of one V-cycle level.  The total number of passes must be even so that the
-// level's data is back in its starting buffer when the coarser V-cycle reads it
-// (grids whose coarsest level is this depth are not smoothed here).  Returns
-// false if no even plan exists (then the in-place kernel is used).
+// of one V-cycle level.  Returns whether the total number of passes is even
+// (the level's data is then back in its starting buffer at the end of the
+// cycle).  An odd plan flips the depth's buffer parity once per cycle, which is
+// consistent only for a single problem: in a batch, a grid that is not smoothed
+// in a cycle (its coarsest level is this depth, or its field has left the
+// inner solve) keeps its data in the buffer the parity has left.  A batch with
+// an odd plan uses the in-place kernel instead.
 static bool plan_passes(int pre, int post, int depth, std::vector<int> &a, std::vector<int> &b) {
   auto split = [depth](int n, std::vector<int> &v) {
     v.clear();
@@ -952,8 +964,9 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
   auto &F = H.cont[l];
   auto &C = H.next[l];
   std::vector<int> plan_pre, plan_post;
-  bool even = plan_passes(o.pre, o.post, o.tdepth, plan_pre, plan_post);
-  smooth_set<T, BG>(ctx, F, o.pre, even ? &plan_pre : nullptr, active, H.par[l], st, l == 0);
+  const bool tiled_ok = plan_passes(o.pre, o.post, o.tdepth, plan_pre, plan_post) ||
+                        H.lev.size() == 1;
+  smooth_set<T, BG>(ctx, F, o.pre, tiled_ok ? &plan_pre : nullptr, active, H.par[l], st, l == 0);
   {
     PROF(pname("resid_restrict", sizeof(T) == 8, l == 0));
     if constexpr (sizeof(T) == 4) {
@@ -998,7 +1011,8 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
                                                 H.par[l], H.par[l + 1]);
     CK_LAUNCH(ctx);
   }
-  smooth_set<T, BG>(ctx, F, o.post, even ? &plan_post : nullptr, active, H.par[l], st, l == 0);
+  smooth_set<T, BG>(ctx, F, o.post, tiled_ok ? &plan_post : nullptr, active, H.par[l], st,
+                    l == 0);
 }
 
 // Per-grid (sum, max) of per-block partials: one block per grid for short
@@ -1051,31 +1065,45 @@ static void level_norms(frmg_ctx *ctx, LevelSet<T> &s, T *const *dout, const int
 // its starting buffer; per-field active flags are read from device memory),
 // so the replay is exact.  Not used on the legacy default stream (it cannot be
 // captured) or while per-kernel profiling is on.
+// Captured V-cycles, one executable graph per buffer-parity state of the
+// hierarchy at the start of the cycle (a level smoothed by an odd number of
+// ping-pong passes per cycle ends in its other buffer, so consecutive cycles
+// alternate between two states).  A replay sets the host-side state to the
+// one the captured cycle ended in.
 struct CycleGraph {
-  cudaGraphExec_t exec = nullptr;
-  long long nlaunch = 0;
-  int calls = 0;
+  struct Entry {
+    cudaGraphExec_t exec = nullptr;
+    long long nlaunch = 0;
+    int calls = 0;
+    std::vector<int> after;
+  };
+  std::map<std::vector<int>, Entry> by_state;
   bool disabled = false;
   ~CycleGraph() {
-    if (exec) cudaGraphExecDestroy(exec);
+    for (auto &kv : by_state)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   }
 };
 
 template <typename F>
-static void run_cycle(frmg_ctx *ctx, CycleGraph &g, bool use, cudaStream_t st, F &&launch) {
+static void run_cycle(frmg_ctx *ctx, CycleGraph &g, bool use, cudaStream_t st,
+                      std::vector<int> &state, F &&launch) {
   if (!use || ctx->prof || g.disabled || st == nullptr) {
     launch();
     return;
   }
-  if (g.exec) {
-    CK(cudaGraphLaunch(g.exec, st));
-    ctx->launches += g.nlaunch;
+  CycleGraph::Entry &e = g.by_state[state];
+  if (e.exec) {
+    CK(cudaGraphLaunch(e.exec, st));
+    ctx->launches += e.nlaunch;
+    state = e.after;
     return;
   }
-  if (g.calls++ == 0) {
+  if (e.calls++ == 0) {
     launch();
     return;
   }
+  const std::vector<int> s0 = state;
   long long l0 = ctx->launches;
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
@@ -1090,21 +1118,26 @@ static void run_cycle(frmg_ctx *ctx, CycleGraph &g, bool use, cudaStream_t st, F
     cudaStreamEndCapture(st, &gr);
     if (gr) cudaGraphDestroy(gr);
     cudaGetLastError();
+    state = s0;
     throw;
   }
   cudaGraph_t graph = nullptr;
   CK(cudaStreamEndCapture(st, &graph));
-  cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaError_t err = cudaGraphInstantiate(&e.exec, graph, 0);
   cudaGraphDestroy(graph);
-  if (e != cudaSuccess) {
+  if (err != cudaSuccess) {
+    // nothing captured ran: restore the state and run the cycle directly
     cudaGetLastError();
-    g.exec = nullptr;
+    e.exec = nullptr;
     g.disabled = true;
+    state = s0;
+    ctx->launches = l0;
     launch();
     return;
   }
-  g.nlaunch = ctx->launches - l0;
-  CK(cudaGraphLaunch(g.exec, st));
+  e.nlaunch = ctx->launches - l0;
+  e.after = state;
+  CK(cudaGraphLaunch(e.exec, st));
 }
 
 // Fine-grid residual norms accumulated by the last depth-0 residual+restriction
@@ -1143,6 +1176,7 @@ struct SolveCfg {
   int defect_fp64;   // mixed: 1 = native FP64 defect/update, 0 = double-float
   int use_graph;     // V-cycles replayed as CUDA graphs
   double tau_alpha;  // > 0: truncation-error stopping rule (Sec. V.B.2)
+  double relax;      // relaxation factor of the Newton-GS updates
 };
 
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
@@ -1185,7 +1219,7 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
   Scope S(ctx);
   int np = (int)P.size();
   Hier<double> H;
-  build_hier<double, false>(S, H, P, cfg.cap, st, ctx);
+  build_hier<double, false>(S, H, P, cfg.cap, st, ctx, 0, cfg.relax);
   for (int pi = 0; pi < np; pi++) {
     Grid<double> &G = H.lev[pi][0];
     k_expm1<double><<<nblocks(G.ncell), 256, 0, st>>>(G.u, G.x, G.ncell);
@@ -1215,7 +1249,7 @@ static void solve_fp64(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &c
     for (int v : act) nact += v;
     if (nact == 0) break;
     CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
-    run_cycle(ctx, graph, cfg.use_graph, st, [&]() { vcycle<double, false>(ctx, H, 0, co, active, st); });
+    run_cycle(ctx, graph, cfg.use_graph, st, H.par, [&]() { vcycle<double, false>(ctx, H, 0, co, active, st); });
     level_norms<double, false>(ctx, H.all[0], nullptr, nullptr, st, nr);
     std::vector<double> tau;
     if (cfg.tau_alpha > 0) tau = tau_norms<double>(ctx, H, np, st);
@@ -1254,7 +1288,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
   for (auto &p : P1) p.nl = 1;
   build_hier<double, false>(S, H64, P1, cfg.cap, st, ctx);
   Hier<float> H;
-  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling);
+  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling, cfg.relax);
   std::vector<double *> d64(np);
   int *flag = S.get<int>(1);
   CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
@@ -1311,10 +1345,10 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
     std::vector<int> iact = act;
     for (int k = 0; k < kmax; k++) {
       if (bg)
-        run_cycle(ctx, gr_bg, cfg.use_graph, st,
+        run_cycle(ctx, gr_bg, cfg.use_graph, st, H.par,
                   [&]() { vcycle<float, true>(ctx, H, 0, co, active, st); });
       else
-        run_cycle(ctx, gr_plain, cfg.use_graph, st,
+        run_cycle(ctx, gr_plain, cfg.use_graph, st, H.par,
                   [&]() { vcycle<float, false>(ctx, H, 0, co, active, st); });
       bool go = false;
       for (int pi = 0; pi < np; pi++)
@@ -1493,7 +1527,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   Scope S(ctx);
   const int np = (int)P.size();
   Hier<float> H;
-  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling);
+  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling, cfg.relax);
   const double ln2 = std::log(2.0);
   float ln2h, ln2l;
   split_host(ln2, ln2h, ln2l);
@@ -1588,10 +1622,10 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
     std::vector<int> iact = act;
     for (int k = 0; k < kmax; k++) {
       if (bg)
-        run_cycle(ctx, gr_bg, cfg.use_graph, st,
+        run_cycle(ctx, gr_bg, cfg.use_graph, st, H.par,
                   [&]() { vcycle<float, true>(ctx, H, 0, co, active, st); });
       else
-        run_cycle(ctx, gr_plain, cfg.use_graph, st,
+        run_cycle(ctx, gr_plain, cfg.use_graph, st, H.par,
                   [&]() { vcycle<float, false>(ctx, H, 0, co, active, st); });
       bool go = false;
       for (int pi = 0; pi < np; pi++)
@@ -1801,13 +1835,14 @@ static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &
   cudaStream_t st = side.st;
   SolveCfg cfg{tol, o.max_vcycles, o.pre, o.post, o.newton_step_cap, o.inner_cycles,
                o.max_outer, fixed, o.temporal_depth <= 0 ? 1 : o.temporal_depth, o.tiling,
-               o.defect_precision, o.use_graph, o.tau_alpha};
+               o.defect_precision, o.use_graph, o.tau_alpha, o.relax};
   if (o.defect_precision < 0 || o.defect_precision > 1) einval("defect_precision must be 0 or 1");
   if (cfg.tdepth > 2) einval("temporal_depth must be 0, 1 or 2");
   if (o.pre < 0 || o.post < 0 || o.max_vcycles < 0 || !(o.newton_step_cap > 0) ||
       !(tol >= 0) || o.inner_cycles < 1 || o.max_outer < 1)
     einval("invalid options");
   if (!(o.tau_alpha >= 0)) einval("tau_alpha must be >= 0");
+  if (!(o.relax > 0 && o.relax < 2)) einval("relax must be in (0, 2)");
   for (auto &p : P) {
     p.nl = count_levels(p.n);
     p.k = model_consts(p.box, p.h, p.a, p.om, p.fr0);
@@ -1979,6 +2014,7 @@ void fr_opts_default(fr_opts *o) {
   o->tiling = 0;
   o->defect_precision = 0;
   o->tau_alpha = 0.0;
+  o->relax = 1.0;
 }
 
 const char *fr_status_string(int s) {
@@ -2143,33 +2179,46 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
       }
     }
     const int shapes[5][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 3}};
+    const double relaxes[3] = {1.0, 1.15, 1.25};
     double best_t = HUGE_VAL;
     fr_opts best_o = o0;
     int status = FR_ENOCONV;
+    // best of two solves from u = 0 with options o
+    auto trial = [&](const fr_opts &o) {
+      double tmin = HUGE_VAL;
+      for (int rep = 0; rep < 2; rep++) {
+        CK(cudaMemsetAsync(u, 0, nc * sizeof(double), st));
+        CK(cudaStreamSynchronize(st));
+        double t0 = now_s();
+        fr_stats sv;
+        int r = fr_solve(ctx, rho, dims, box, a, om, fr0, tol, u, &o, &sv, stream);
+        double t1 = now_s();
+        if (r != FR_OK) return HUGE_VAL;
+        tmin = std::min(tmin, t1 - t0);
+      }
+      if (tmin < best_t) {
+        best_t = tmin;
+        best_o = o;
+        status = FR_OK;
+      }
+      return tmin;
+    };
+    // every V-cycle shape and relaxation factor with one sweep per tiled
+    // pass, then two sweeps per pass for the best of them
     for (int sh = 0; sh < 5; sh++)
-      for (int td = 1; td <= 2; td++) {
+      for (double w : relaxes) {
         fr_opts o = o0;
         o.pre = shapes[sh][0];
         o.post = shapes[sh][1];
-        o.temporal_depth = td;
-        double tmin = HUGE_VAL;
-        bool ok = true;
-        for (int rep = 0; rep < 2 && ok; rep++) {
-          CK(cudaMemsetAsync(u, 0, nc * sizeof(double), st));
-          CK(cudaStreamSynchronize(st));
-          double t0 = now_s();
-          fr_stats sv;
-          int r = fr_solve(ctx, rho, dims, box, a, om, fr0, tol, u, &o, &sv, stream);
-          double t1 = now_s();
-          if (r != FR_OK) ok = false;
-          tmin = std::min(tmin, t1 - t0);
-        }
-        if (ok && tmin < best_t) {
-          best_t = tmin;
-          best_o = o;
-          status = FR_OK;
-        }
+        o.temporal_depth = 1;
+        o.relax = w;
+        trial(o);
       }
+    if (status == FR_OK) {
+      fr_opts o = best_o;
+      o.temporal_depth = 2;
+      trial(o);
+    }
     frmg_release(ctx, u);
     if (rho != density) frmg_release(ctx, const_cast<double *>(rho));
     *best = best_o;
@@ -2394,6 +2443,7 @@ static Grid<double> single_grid(Scope &S, frmg_ctx *ctx, Problem &p, double *u, 
   G.ah = 0.5 * k.alpha;
   G.beta = k.beta;
   G.cap = cap;
+  G.relax = 1.0;
   G.u = u;
   G.x = S.get<double>(G.ncell);
   face_offsets(p.n, G.foff);
@@ -2457,6 +2507,7 @@ int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, cons
     G.ah = (float)(0.5 * k.alpha);
     G.beta = (float)k.beta;
     G.cap = (float)cap;
+    G.relax = 1.0f;
     G.fs = 1.0f;
     G.fo = 0.0f;
     face_offsets(dims, G.foff);

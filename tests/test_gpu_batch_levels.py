@@ -96,8 +96,8 @@ def _levels_case(N, P, sizes1, n1, sizes2, n2, seed):
     return synth.nested_case(N, seed, sizes1, n1, sizes2, n2)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_small_nested_patches_match_oracle(C, prec):
+@pytest.mark.parametrize("prec,relax", [("fp64", 1.0), ("mixed", 1.0), ("mixed", 1.2)])
+def test_small_nested_patches_match_oracle(C, prec, relax):
     P = dict(box=64.0, a=1.0, fr0=1e-5)
     rho0, patches = _levels_case(32, P, [16, 24], 3, [16], 2, 700)
     assert len(patches) >= 4 and any(p["parent"] >= 0 for p in patches)
@@ -107,7 +107,8 @@ def test_small_nested_patches_match_oracle(C, prec):
     gp = [dict(parent=p["parent"], origin=p["origin"], density=dev(p["rho"]),
                u=torch.zeros(p["rho"].shape, dtype=torch.float64, device="cuda"))
           for p in patches]
-    st, stats = C.solve_levels(dev(rho0), u0, gp, tol=1e-8, omega_m=OM, prec=prec, **P)
+    st, stats = C.solve_levels(dev(rho0), u0, gp, tol=1e-8, omega_m=OM, prec=prec, relax=relax,
+                               **P)
     assert st == 0
     assert np.abs(host(u0) - dom.u).max() <= 1e-6
     for g, r in zip(gp, pres):

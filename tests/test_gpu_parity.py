@@ -359,11 +359,40 @@ def test_autotune_returns_a_converging_setting(C):
     best, secs = C.autotune(dev(rho), tol=1e-8, prec="mixed", **CFG1)
     assert (best["pre"], best["post"]) in [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3)]
     assert best["temporal_depth"] in (1, 2) and secs > 0
+    assert best["relax"] in (1.0, 1.15, 1.25)
     u = torch.zeros(shape, dtype=torch.float64, device="cuda")
     st, s = C.solve(dev(rho), u, tol=1e-8, prec="mixed", pre=best["pre"], post=best["post"],
-                    temporal_depth=best["temporal_depth"], **CFG1)
+                    temporal_depth=best["temporal_depth"], relax=best["relax"], **CFG1)
     assert st == 0
     assert np.abs(host(u) - O.solve(rho, tol=1e-8, **CFG1).u).max() <= 1e-6
+
+
+# ------------------------------------------------------------------ over-relaxation
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("relax", [1.15, 1.25])
+@pytest.mark.parametrize("tiling", [-1, 1])
+def test_over_relaxed_solve_reaches_oracle_solution(C, prec, relax, tiling):
+    """u += w du in every Newton-GS update changes the path, not the discrete
+    solution: the solve still ends at the oracle's (plain Newton-GS) solution."""
+    shape = (48, 32, 64)
+    rho = _field(shape, 4100, sigma=2.0)
+    P = dict(box=2.0 * shape[2], a=1.0, omega_m=0.24, fr0=1e-5)
+    ref = O.solve(rho, tol=1e-8, **P)
+    assert ref.converged
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s = C.solve(dev(rho), u, tol=1e-8, prec=prec, relax=relax, tiling=tiling, **P)
+    assert st == 0 and s.res_rms <= 1e-8
+    assert np.abs(host(u) - ref.u).max() <= 1e-6
+
+
+def test_relax_out_of_range_rejected(C):
+    from paper_1110_1379_gb300 import frmg
+    rho = torch.ones((8, 8, 8), dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(rho)
+    for w in (0.0, -0.5, 2.0, float("nan")):
+        with pytest.raises(frmg.FRError) as e:
+            C.solve(rho, u, relax=w, **CFG1)
+        assert e.value.status == frmg.FR_EINVAL
 
 
 # ------------------------------------------------------------------ CUDA graphs
@@ -394,6 +423,47 @@ def test_graph_replay_is_bit_identical(C, prec, on_side_stream):
         outs.append(host(u))
     assert np.array_equal(outs[0], outs[1])
     assert counts[0] == counts[1]
+
+
+@pytest.mark.parametrize("pre,post,tdepth", [(2, 1, 1), (1, 2, 1), (1, 0, 1), (3, 2, 2)])
+def test_odd_pass_plans_single_field(C, pre, post, tdepth):
+    """A V-cycle with an odd number of ping-pong smoother passes per level leaves
+    each level in its other buffer; graph replay (one graph per buffer-parity
+    state) gives the same bits as direct launches, and both reach the oracle's
+    solution."""
+    shape = (32, 48, 64)
+    rho = _field(shape, 1250, sigma=1.5)
+    P = dict(box=2.0 * shape[2], a=1.0, omega_m=0.24, fr0=1e-5)
+    ref = O.solve(rho, tol=1e-8, **P)
+    outs, counts = [], []
+    for g in (0, 1):
+        u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        n0 = C.launches
+        st, stats = C.solve(dev(rho), u, tol=1e-8, prec="mixed", pre=pre, post=post,
+                            temporal_depth=tdepth, tiling=1, use_graph=g,
+                            stream=torch.cuda.current_stream(), **P)
+        assert st == 0 and stats.res_rms <= 1e-8 and stats.vcycles >= 4
+        counts.append(C.launches - n0)
+        outs.append(host(u))
+    assert np.array_equal(outs[0], outs[1])
+    assert counts[0] == counts[1]
+    assert np.abs(outs[1] - ref.u).max() <= 1e-6
+
+
+def test_odd_pass_plan_batch_matches_oracle(C):
+    """A batch with V(2,1) runs the in-place smoother (the parity of a field
+    that has left the inner solve must not flip) and still reaches every
+    field's oracle solution."""
+    rhos = [_field((16, 16, 16), 1400 + i, sigma=0.5 + 0.6 * i) for i in range(3)]
+    us = [torch.zeros((16, 16, 16), dtype=torch.float64, device="cuda") for _ in rhos]
+    st, stats = C.solve_batch([dev(r) for r in rhos], us, boxes=[32.0] * 3, avals=[1.0] * 3,
+                              fr0s=[1e-5] * 3, omega_m=0.24, tol=1e-8, prec="mixed", pre=2,
+                              post=1, tiling=1)
+    assert st == 0
+    for r, u in zip(rhos, us):
+        ref = O.solve(r, tol=1e-8, box=32.0, a=1.0, omega_m=0.24, fr0=1e-5)
+        assert np.abs(host(u) - ref.u).max() <= 1e-6
 
 
 def test_graph_replay_batch_with_fields_leaving(C):
