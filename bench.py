@@ -241,6 +241,35 @@ def timed(fn, steps, warmup):
     return statistics.median(ts)
 
 
+# V-cycle shapes and over-relaxation factors tried, untimed, before a secondary
+# workload is timed (the headline solve uses fr_autotune instead)
+SHAPE_CANDIDATES = [dict(pre=2, post=2, relax=1.0), dict(pre=2, post=2, relax=1.25),
+                    dict(pre=2, post=1, relax=1.25), dict(pre=1, post=1, relax=1.15)]
+
+
+def pick_options(run, cands=SHAPE_CANDIDATES):
+    """Fastest of cands for run(**opts) (best of 2 untimed runs each; a
+    candidate that raises is skipped).  Returns (opts, {label: seconds})."""
+    import torch
+    times = {}
+    for c in cands:
+        ts = []
+        try:
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                run(**c)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+        except (AssertionError, RuntimeError):
+            continue
+        times[f"V({c['pre']},{c['post']}) w={c['relax']}"] = (min(ts), c)
+    if not times:
+        raise RuntimeError("no candidate setting converged")
+    best = min(times.values(), key=lambda v: v[0])[1]
+    return dict(best), {k: v[0] for k, v in times.items()}
+
+
 def run_secondary(args):
     """Secondary workloads (the 32^3, 128^3 CIC, nested-patch and 96-field batch cases): one JSON line each."""
     import numpy as np
@@ -267,11 +296,13 @@ def run_secondary(args):
         kw = dict(boxes=[s["box"] for s in specs], avals=[s["a"] for s in specs],
                   fr0s=[s["fr0"] for s in specs], omega_m=0.24, tol=TOL)
 
-        def batch(prec):
+        def batch(prec, **opts):
             for x in us:
                 x.zero_()
-            st, _ = ctx.solve_batch(rhos, us, prec=prec, **kw)
+            st, _ = ctx.solve_batch(rhos, us, prec=prec, **kw, **opts)
             assert st == 0
+
+        bopts, btimes = pick_options(lambda **o: batch("mixed", **o))
 
         def seq(prec):
             for r, x, s in zip(rhos, us, specs):
@@ -280,7 +311,8 @@ def run_secondary(args):
                                   omega_m=0.24, fr0=s["fr0"])
                 assert st == 0
 
-        t_b = shard.max_over_ranks(timed(lambda: batch("mixed"), args.steps, args.warmup), "cuda")
+        t_b = shard.max_over_ranks(timed(lambda: batch("mixed", **bopts), args.steps,
+                                         args.warmup), "cuda")
         t_sm = shard.max_over_ranks(timed(lambda: seq("mixed"), 1, 1), "cuda")
         t_s64 = shard.max_over_ranks(timed(lambda: seq("fp64"), 1, 1), "cuda")
         line.update(metric="batched solve of 96 fields (N 32-128, mixed |f_R0|, a, sigma): "
@@ -288,7 +320,8 @@ def run_secondary(args):
                     value=cells / t_b, cells=cells, ms=1e3 * t_b, n_gpus=world,
                     fields_per_rank=len(specs),
                     sequential_mixed=cells / t_sm, sequential_fp64=cells / t_s64,
-                    speedup_vs_sequential_fp64=t_s64 / t_b)
+                    speedup_vs_sequential_fp64=t_s64 / t_b,
+                    tuned={**bopts, "candidates_s": btimes})
     elif args.workload == "levels256":
         rho0, patches = synth.nested_case(256, 4000, [32, 48, 64], 16, [32, 48], 12)
         r0 = torch.from_numpy(rho0).cuda()
@@ -298,18 +331,19 @@ def run_secondary(args):
               for p in patches]
         cells = r0.numel() + sum(p["rho"].size for p in patches)
 
-        def run(prec):
+        def run(prec, **opts):
             u0.zero_()
             st, _ = ctx.solve_levels(r0, u0, gp, box=256.0, a=1.0, omega_m=0.24, fr0=1e-5,
-                                     tol=TOL, prec=prec)
+                                     tol=TOL, prec=prec, **opts)
             assert st == 0
 
-        t_m = timed(lambda: run("mixed"), args.steps, args.warmup)
+        lopts, ltimes = pick_options(lambda **o: run("mixed", **o))
+        t_m = timed(lambda: run("mixed", **lopts), args.steps, args.warmup)
         t_64 = timed(lambda: run("fp64"), 1, 1)
         line.update(metric="domain 256^3 + nested patches (2x, 4x): cells/s to rms 1e-8 on every grid",
                     value=cells / t_m, cells=cells, patches=len(patches),
                     level2=sum(1 for p in patches if p["parent"] >= 0), ms=1e3 * t_m,
-                    fp64=cells / t_64)
+                    fp64=cells / t_64, tuned={**lopts, "candidates_s": ltimes})
     elif args.workload == "cic128":
         n = 128
         pos = torch.from_numpy(synth.zeldovich_positions(n, 2000,
@@ -485,7 +519,7 @@ def main():
     # autotuner (untimed): V-cycle shape, relaxation factor and sweeps per tiled
     # pass for this workload
     best, tune_s = ctx.autotune(rho, tol=TOL, prec="mixed", stream=stream, **PHYS)
-    tuned = {k: best[k] for k in ("pre", "post", "temporal_depth", "relax")}
+    tuned = {k: best[k] for k in ("pre", "post", "temporal_depth", "relax", "fmg")}
     solve("mixed")
     torch.cuda.synchronize()
     barrier()
@@ -637,7 +671,8 @@ def main():
         "autotuned": {**tuned, "tune_seconds": tune_s,
                       "note": "fastest of V(pre,post) in {(1,1),(2,1),(1,2),(2,2),(3,3)} x "
                               "relaxation factor {1,1.15,1.25}, then sweeps per tiled pass "
-                              "{1,2}, chosen by fr_autotune on this field"},
+                              "{1,2} and full-multigrid start {0,1}, chosen by fr_autotune "
+                              "on this field"},
         "mixed_default_v22": {"value": value_default, "unit": "cells/s",
                               "vcycles": s_def.vcycles, "outer": s_def.outer},
         "mixed": {"vcycles": s0.vcycles, "outer": s0.outer, "res_rms": s0.res_rms,

@@ -83,9 +83,17 @@ typedef struct {
     double relax;           /* relaxation factor w of every Newton-Gauss-Seidel update,
                                u += w * du (the Newton-GS step of Sec. V.B.2 is w = 1, the default);
                                0 < w < 2.
-                               Over-relaxing the red-black sweeps (w ~ 1.1-1.2) can lower
+                               Over-relaxing the red-black sweeps (w ~ 1.1-1.25) can lower
                                the V-cycle's convergence factor; the solution is the
-                               same, only the path to it changes.  FR_EINVAL outside (0, 2). */
+                               same, only the path to it changes.  On strongly nonlinear
+                               fields it can also slow convergence down (fr_autotune tries
+                               it per field).  FR_EINVAL outside (0, 2). */
+    int fmg;                /* mixed solves of one field from u = 0: 1 = full-multigrid start
+                               (the density term averaged to every level, the coarsest level
+                               solved, then at each finer level the interpolated coarser
+                               solution and one V-cycle from there; the last one, on the
+                               finest grid, counts as the first V-cycle); 0 = start the
+                               V-cycles from u = 0 (default).  Ignored otherwise. */
 } fr_opts;
 
 #define FR_HIST 64
@@ -262,8 +270,9 @@ int fr_residual_norm_noalloc(const double *u, const double *density, const int d
  * Autotuner: solves the given problem from u = 0 (into library scratch; the
  * caller's arrays are only read) with every combination of the V-cycle shape
  * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)} and the relaxation factor
- * relax in {1, 1.15, 1.25} at one sweep per tiled pass, then with two sweeps
- * per pass (temporal_depth 2) for the fastest of those, on top of *base (NULL =
+ * relax in {1, 1.15, 1.25} at one sweep per tiled pass, then for the fastest
+ * of those with two sweeps per pass (temporal_depth 2) and with the
+ * full-multigrid start (fmg 1), on top of *base (NULL =
  * defaults), twice each, and writes the fastest setting that reaches tol to
  * *best (and its time in seconds to *best_seconds, if not NULL).  Device or
  * host density pointer.  FR_ENOCONV if no candidate converged.

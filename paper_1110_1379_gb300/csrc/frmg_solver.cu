@@ -949,6 +949,31 @@ static void smooth_set(frmg_ctx *ctx, LevelSet<T> &s, int sweeps, const std::vec
     }
 }
 
+// u^h += P (u^H - R u^h) from depth l + 1 onto depth l (tiled where the
+// depth's sets have the tiled schedule).
+template <typename T>
+static void prolong_level(frmg_ctx *ctx, Hier<T> &H, int l, const int *active, cudaStream_t st) {
+  auto &F = H.cont[l];
+  auto &C = H.next[l];
+  PROF(pname("prolong", sizeof(T) == 8, l == 0));
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {
+    if (F.rr_tiled && F.nblk_pl > 0) {
+      if (F.dirichlet)
+        k_prolong_tiled<true><<<F.nblk_pl, 256, 0, st>>>(F.d, C.d, F.d_off_pl, F.size(),
+                                                         F.kc_pl, active, H.par[l], H.par[l + 1]);
+      else
+        k_prolong_tiled<false><<<F.nblk_pl, 256, 0, st>>>(F.d, C.d, F.d_off_pl, F.size(),
+                                                          F.kc_pl, active, H.par[l], H.par[l + 1]);
+      done = true;
+    }
+  }
+  if (!done)
+    k_prolong<T><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, F.size(), active,
+                                              H.par[l], H.par[l + 1]);
+  CK_LAUNCH(ctx);
+}
+
 template <typename T, bool BG>
 static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const int *active,
                    cudaStream_t st) {
@@ -992,27 +1017,39 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
     CK_LAUNCH(ctx);
   }
   vcycle<T, BG>(ctx, H, l + 1, o, active, st);
-  {
-    PROF(pname("prolong", sizeof(T) == 8, l == 0));
-    bool done = false;
-    if constexpr (sizeof(T) == 4) {
-      if (F.rr_tiled && F.nblk_pl > 0) {
-        if (F.dirichlet)
-          k_prolong_tiled<true><<<F.nblk_pl, 256, 0, st>>>(F.d, C.d, F.d_off_pl, F.size(),
-                                                           F.kc_pl, active, H.par[l], H.par[l + 1]);
-        else
-          k_prolong_tiled<false><<<F.nblk_pl, 256, 0, st>>>(F.d, C.d, F.d_off_pl, F.size(),
-                                                            F.kc_pl, active, H.par[l], H.par[l + 1]);
-        done = true;
-      }
-    }
-    if (!done)
-      k_prolong<T><<<C.nblk_full, 256, 0, st>>>(F.d, C.d, C.d_off_full, F.size(), active,
-                                                H.par[l], H.par[l + 1]);
-    CK_LAUNCH(ctx);
-  }
+  prolong_level<T>(ctx, H, l, active, st);
   smooth_set<T, BG>(ctx, F, o.post, tiled_ok ? &plan_post : nullptr, active, H.par[l], st,
                     l == 0);
+}
+
+// Full-multigrid start of the FP32 full-variable phase for a single field from
+// u = 0 (the density term already in the finest right-hand side): the
+// right-hand side is averaged down to every level, the coarsest level is
+// solved, and at each finer level the coarser solution is interpolated (the
+// V-cycle's trilinear prolongation applied to u^H with R u^h = 0 and u^h = 0)
+// and one V-cycle is run from that level.  Ends with the V-cycle on the finest
+// level.
+static void fmg_start(frmg_ctx *ctx, Hier<float> &H, const CycleOpts &co, const int *active,
+                      cudaStream_t st) {
+  std::vector<Grid<float>> &lev = H.lev[0];
+  const int L = (int)lev.size();
+  for (int l = 1; l < L; l++) {
+    Grid<float> &F = lev[l - 1];
+    Grid<float> &C = lev[l];
+    k_restrict_avg<float><<<nblocks(C.ncell), 256, 0, st>>>(F.f, F.n0, F.n1, F.n2,
+                                                            const_cast<float *>(C.f));
+    CK_LAUNCH(ctx);
+    CK(cudaMemsetAsync(H.cur_u(0, l), 0, C.ncell * sizeof(float), st));
+    CK(cudaMemsetAsync(H.cur_x(0, l), 0, C.ncell * sizeof(float), st));
+  }
+  vcycle<float, false>(ctx, H, L - 1, co, active, st);
+  for (int l = L - 2; l >= 0; l--) {
+    CK(cudaMemsetAsync(lev[l + 1].uR, 0, lev[l + 1].ncell * sizeof(float), st));
+    CK(cudaMemsetAsync(H.cur_u(0, l), 0, lev[l].ncell * sizeof(float), st));
+    CK(cudaMemsetAsync(H.cur_x(0, l), 0, lev[l].ncell * sizeof(float), st));
+    prolong_level<float>(ctx, H, l, active, st);
+    vcycle<float, false>(ctx, H, l, co, active, st);
+  }
 }
 
 // Per-grid (sum, max) of per-block partials: one block per grid for short
@@ -1177,6 +1214,7 @@ struct SolveCfg {
   int use_graph;     // V-cycles replayed as CUDA graphs
   double tau_alpha;  // > 0: truncation-error stopping rule (Sec. V.B.2)
   double relax;      // relaxation factor of the Newton-GS updates
+  int fmg;           // full-multigrid start (mixed, single field, u0 = 0)
 };
 
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
@@ -1334,11 +1372,16 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
   // Stopping signal: the fine residual after pre-smoothing of each cycle (fused
   // into the residual + restriction kernel).  Successive values are compared
   // (the first cycle always runs); a ratio above 0.75 means FP32 rounding has
-  // taken over.  A correction solve stops once the residual at the end of the
-  // cycle, predicted as mid * sqrt(mid / previous mid) (the rest of the cycle
-  // does about half of a cycle's contraction), is below 0.7 tol.
+  // taken over, or that the full-variable iteration is making little headway
+  // in a strongly nonlinear field (continuing it there has run into overflow;
+  // the correction form takes over instead).  The full-variable phase also
+  // stops once the ratio exceeds three times the best ratio of the solve (the
+  // FP32 floor is near: further cycles gain little).  A correction solve stops once
+  // the residual at the end of the cycle, predicted as mid * sqrt(mid /
+  // previous mid) (the rest of the cycle does about half of a cycle's
+  // contraction), is below 0.7 tol.
   auto inner = [&](bool bg, const std::vector<double> &r0, double floor_rel, int kmax) {
-    std::vector<double> rp(np, HUGE_VAL);
+    std::vector<double> rp(np, HUGE_VAL), rbest(np, HUGE_VAL);
     // fields leave the inner solve one by one (their active flag drops until
     // the next outer step), so a batch does not run every field as long as
     // its slowest one
@@ -1366,7 +1409,10 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
         if (!(r == r)) { go = true; continue; }  // single-level grid: one coarsest solve per cycle
         hist_push(stats[pi], r);
         const double pred = rp[pi] < HUGE_VAL ? r * std::sqrt(r / rp[pi]) : r;
-        if (r < 0.75 * rp[pi] && r > floor_rel * r0[pi] && pred > (bg ? 0.7 : 0.3) * cfg.tol)
+        const double ratio = rp[pi] < HUGE_VAL ? r / rp[pi] : 0.0;
+        if (rp[pi] < HUGE_VAL) rbest[pi] = std::min(rbest[pi], ratio);
+        if (ratio < 0.75 && (bg || ratio <= 3.0 * rbest[pi]) && r > floor_rel * r0[pi] &&
+            pred > (bg ? 0.7 : 0.3) * cfg.tol)
           go = true;
         else
           iact[pi] = 0;
@@ -1403,8 +1449,13 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
         stats[pi].res0_rms = r0[pi];
       }
     }
-    // stop well above the FP32 rounding floor; the correction solves finish
-    inner(false, r0, 1e-4, 40);
+    if (cfg.fmg && np == 1) {
+      fmg_start(ctx, H, co, active, st);
+      stats[0].vcycles++;
+    }
+    // run to the FP32 rounding floor (1e-6 of the starting residual, or the
+    // contraction stalls); the correction solves finish
+    inner(false, r0, 1e-6, 40);
     if (cfg.tau_alpha > 0) tau = tau_norms<float>(ctx, H, np, st);
     update();
   } else {
@@ -1611,11 +1662,16 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   // Stopping signal: the fine residual after pre-smoothing of each cycle (fused
   // into the residual + restriction kernel).  Successive values are compared
   // (the first cycle always runs); a ratio above 0.75 means FP32 rounding has
-  // taken over.  A correction solve stops once the residual at the end of the
-  // cycle, predicted as mid * sqrt(mid / previous mid) (the rest of the cycle
-  // does about half of a cycle's contraction), is below 0.7 tol.
+  // taken over, or that the full-variable iteration is making little headway
+  // in a strongly nonlinear field (continuing it there has run into overflow;
+  // the correction form takes over instead).  The full-variable phase also
+  // stops once the ratio exceeds three times the best ratio of the solve (the
+  // FP32 floor is near: further cycles gain little).  A correction solve stops once
+  // the residual at the end of the cycle, predicted as mid * sqrt(mid /
+  // previous mid) (the rest of the cycle does about half of a cycle's
+  // contraction), is below 0.7 tol.
   auto inner = [&](bool bg, const std::vector<double> &r0, double floor_rel, int kmax) {
-    std::vector<double> rp(np, HUGE_VAL);
+    std::vector<double> rp(np, HUGE_VAL), rbest(np, HUGE_VAL);
     // fields leave the inner solve one by one (their active flag drops until
     // the next outer step), so a batch does not run every field as long as
     // its slowest one
@@ -1643,7 +1699,10 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
         if (!(r == r)) { go = true; continue; }
         hist_push(stats[pi], r);
         const double pred = rp[pi] < HUGE_VAL ? r * std::sqrt(r / rp[pi]) : r;
-        if (r < 0.75 * rp[pi] && r > floor_rel * r0[pi] && pred > (bg ? 0.7 : 0.3) * cfg.tol)
+        const double ratio = rp[pi] < HUGE_VAL ? r / rp[pi] : 0.0;
+        if (rp[pi] < HUGE_VAL) rbest[pi] = std::min(rbest[pi], ratio);
+        if (ratio < 0.75 && (bg || ratio <= 3.0 * rbest[pi]) && r > floor_rel * r0[pi] &&
+            pred > (bg ? 0.7 : 0.3) * cfg.tol)
           go = true;
         else
           iact[pi] = 0;
@@ -1671,8 +1730,13 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
         r0[pi] = nr[2 * pi];
         stats[pi].res0_rms = nr[2 * pi];
       }
-      // stop well above the FP32 rounding floor; the correction solves finish
-      inner(false, r0, 1e-4, 40);
+      if (cfg.fmg && np == 1) {
+        fmg_start(ctx, H, co, active, st);
+        stats[0].vcycles++;
+      }
+      // run to the FP32 rounding floor (1e-6 of the starting residual, or the
+      // contraction stalls); the correction solves finish
+      inner(false, r0, 1e-6, 40);
       if (cfg.tau_alpha > 0) tau = tau_norms<float>(ctx, H, np, st);
       update();
     }
@@ -1835,7 +1899,7 @@ static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &
   cudaStream_t st = side.st;
   SolveCfg cfg{tol, o.max_vcycles, o.pre, o.post, o.newton_step_cap, o.inner_cycles,
                o.max_outer, fixed, o.temporal_depth <= 0 ? 1 : o.temporal_depth, o.tiling,
-               o.defect_precision, o.use_graph, o.tau_alpha, o.relax};
+               o.defect_precision, o.use_graph, o.tau_alpha, o.relax, o.fmg};
   if (o.defect_precision < 0 || o.defect_precision > 1) einval("defect_precision must be 0 or 1");
   if (cfg.tdepth > 2) einval("temporal_depth must be 0, 1 or 2");
   if (o.pre < 0 || o.post < 0 || o.max_vcycles < 0 || !(o.newton_step_cap > 0) ||
@@ -1843,6 +1907,7 @@ static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &
     einval("invalid options");
   if (!(o.tau_alpha >= 0)) einval("tau_alpha must be >= 0");
   if (!(o.relax > 0 && o.relax < 2)) einval("relax must be in (0, 2)");
+  if (o.fmg < 0 || o.fmg > 1) einval("fmg must be 0 or 1");
   for (auto &p : P) {
     p.nl = count_levels(p.n);
     p.k = model_consts(p.box, p.h, p.a, p.om, p.fr0);
@@ -2015,6 +2080,7 @@ void fr_opts_default(fr_opts *o) {
   o->defect_precision = 0;
   o->tau_alpha = 0.0;
   o->relax = 1.0;
+  o->fmg = 0;
 }
 
 const char *fr_status_string(int s) {
@@ -2204,7 +2270,8 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
       return tmin;
     };
     // every V-cycle shape and relaxation factor with one sweep per tiled
-    // pass, then two sweeps per pass for the best of them
+    // pass, then for the best of them two sweeps per pass and the
+    // full-multigrid start
     for (int sh = 0; sh < 5; sh++)
       for (double w : relaxes) {
         fr_opts o = o0;
@@ -2215,8 +2282,12 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
         trial(o);
       }
     if (status == FR_OK) {
-      fr_opts o = best_o;
+      const fr_opts b = best_o;
+      fr_opts o = b;
       o.temporal_depth = 2;
+      trial(o);
+      o = b;
+      o.fmg = 1;
       trial(o);
     }
     frmg_release(ctx, u);

@@ -29,7 +29,8 @@ class fr_opts(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("allow_negative_density", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("temporal_depth", ctypes.c_int),
                 ("tiling", ctypes.c_int), ("defect_precision", ctypes.c_int),
-                ("tau_alpha", ctypes.c_double), ("relax", ctypes.c_double)]
+                ("tau_alpha", ctypes.c_double), ("relax", ctypes.c_double),
+                ("fmg", ctypes.c_int)]
 
 
 FR_HIST = 64

@@ -385,6 +385,22 @@ def test_over_relaxed_solve_reaches_oracle_solution(C, prec, relax, tiling):
     assert np.abs(host(u) - ref.u).max() <= 1e-6
 
 
+@pytest.mark.parametrize("shape,relax", [((48, 32, 64), 1.0), ((48, 32, 64), 1.15),
+                                         ((32, 32, 32), 1.25), ((12, 20, 36), 1.0)])
+def test_fmg_start_reaches_oracle_solution(C, shape, relax):
+    """The full-multigrid start changes the first iterate, not the solution."""
+    rho = _field(shape, 4200, sigma=2.0)
+    P = dict(box=2.0 * shape[2], a=1.0, omega_m=0.24, fr0=1e-5)
+    ref = O.solve(rho, tol=1e-8, **P)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s = C.solve(dev(rho), u, tol=1e-8, prec="mixed", relax=relax, fmg=1, **P)
+    assert st == 0 and s.res_rms <= 1e-8
+    assert np.abs(host(u) - ref.u).max() <= 1e-6
+    # the first entry of the residual history (first V-cycle after the start)
+    # lies well below the residual of u = 0
+    assert s.hist[0] < 0.5 * s.res0_rms
+
+
 def test_relax_out_of_range_rejected(C):
     from paper_1110_1379_gb300 import frmg
     rho = torch.ones((8, 8, 8), dtype=torch.float64, device="cuda")
