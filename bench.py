@@ -85,7 +85,20 @@ def parse_args():
     ap.add_argument("--workload", default="solve512",
                     choices=["solve512", "batch96", "levels256", "cic128", "small32", "poisson512"],
                     help="secondary workloads print their own line (default: the 512^3 solve)")
+    ap.add_argument("--options", default="",
+                    help="solver options for the headline solve instead of fr_autotune, "
+                         "e.g. pre=1,post=1,relax=1.15,fmg=1 (reproduces a tuned run, "
+                         "warm-up solves included, for profiling)")
     return ap.parse_args()
+
+
+def parse_options(text):
+    """'k=v,k=v' -> dict of solver options (ints where the value is integral)."""
+    out = {}
+    for item in filter(None, (t.strip() for t in text.split(","))):
+        k, v = item.split("=")
+        out[k.strip()] = int(v) if v.strip().lstrip("-").isdigit() else float(v)
+    return out
 
 
 class ClockSampler:
@@ -502,7 +515,8 @@ def main():
     ctx = frmg.Context(local)
     stream = torch.cuda.current_stream()
 
-    tuned = {}
+    fixed = parse_options(args.options)
+    tuned = dict(fixed)
 
     def solve(prec, profile=False, **kw):
         u.zero_()
@@ -518,8 +532,11 @@ def main():
     torch.cuda.synchronize()
     # autotuner (untimed): V-cycle shape, relaxation factor and sweeps per tiled
     # pass for this workload
-    best, tune_s = ctx.autotune(rho, tol=TOL, prec="mixed", stream=stream, **PHYS)
-    tuned = {k: best[k] for k in ("pre", "post", "temporal_depth", "relax", "fmg")}
+    if fixed:
+        tune_s = None
+    else:
+        best, tune_s = ctx.autotune(rho, tol=TOL, prec="mixed", stream=stream, **PHYS)
+        tuned = {k: best[k] for k in ("pre", "post", "temporal_depth", "relax", "fmg")}
     solve("mixed")
     torch.cuda.synchronize()
     barrier()
@@ -669,10 +686,11 @@ def main():
                  "vcycles": s64.vcycles if s64 else None, "res_rms": s64.res_rms if s64 else None},
         "mixed_vs_fp64_speedup": (value / world / fp64_value) if fp64_value else None,
         "autotuned": {**tuned, "tune_seconds": tune_s,
-                      "note": "fastest of V(pre,post) in {(1,1),(2,1),(1,2),(2,2),(3,3)} x "
-                              "relaxation factor {1,1.15,1.25}, then sweeps per tiled pass "
-                              "{1,2} and full-multigrid start {0,1}, chosen by fr_autotune "
-                              "on this field"},
+                      "note": ("fixed by --options" if fixed else
+                               "fastest of V(pre,post) in {(1,1),(2,1),(1,2),(2,2),(3,3)} x "
+                               "relaxation factor {1,1.15,1.25}, then sweeps per tiled pass "
+                               "{1,2} and full-multigrid start {0,1}, chosen by fr_autotune "
+                               "on this field")},
         "mixed_default_v22": {"value": value_default, "unit": "cells/s",
                               "vcycles": s_def.vcycles, "outer": s_def.outer},
         "mixed": {"vcycles": s0.vcycles, "outer": s0.outer, "res_rms": s0.res_rms,

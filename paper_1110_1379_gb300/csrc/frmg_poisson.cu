@@ -108,6 +108,18 @@ __device__ __forceinline__ float nbsum(const PLevel &L, const float *e, int i, i
   return s;
 }
 
+// Gauss-Seidel value of a cell, (sum of its neighbours in the grid - h^2 f) /
+// (6 + missing neighbours), with the diagonal's reciprocal as a constant (at
+// most three neighbours are missing: every dimension is at least 2); every
+// smoother uses this one expression.
+__device__ __forceinline__ float gs_value(float sum, float h2f, int nm) {
+  const float inv = nm == 0   ? 1.0f / 6.0f
+                    : nm == 1 ? 1.0f / 7.0f
+                    : nm == 2 ? 1.0f / 8.0f
+                              : 1.0f / 9.0f;
+  return (sum - h2f) * inv;
+}
+
 // Red-black Gauss-Seidel on L e = f (one colour per launch): with the ghosts
 // -e_i on patch faces, e_i = (sum of the neighbours in the grid - h^2 f_i) / (6 + missing),
 // over-relaxed as e_i += w (that value - e_i) when relax = w != 1.
@@ -122,7 +134,7 @@ __global__ void __launch_bounds__(kNT) k_lsmooth(PLevel L, int colour) {
   const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
   int nm;
   const float s = nbsum(L, L.e, i, j, k, c, nm);
-  const float gs = (s - L.h2 * L.f[c]) / (6.0f + (float)nm);
+  const float gs = gs_value(s, L.h2 * L.f[c], nm);
   L.e[c] = fmaf(L.relax, gs - L.e[c], L.e[c]);
 }
 
@@ -133,14 +145,19 @@ __global__ void __launch_bounds__(kNT) k_lsmooth(PLevel L, int colour) {
 // plane p it updates the red cells of plane p-1 on the tile grown by one cell,
 // then the black cells of plane p-2 on the tile, and writes plane p-2 to the
 // other buffer (the halos are read from the unmodified input, so the pass
-// equals one sweep of k_lsmooth).  Warps update whole rows of the tile (lane =
-// x-pair); the next plane is prefetched into registers during the updates.
+// equals one sweep of k_lsmooth).  Each plane is stored colour-split: per
+// x-pair q = (ly, px) of the tile, array c holds the pair's cell of colour c
+// (the even-x cell has colour (ly + z) & 1), so the six neighbours of a cell
+// are the opposite colour's entries q, q -+ 1, q -+ PX of its own and the
+// adjacent planes, and a warp's accesses (lane = x-pair) are contiguous.
+// Warps update whole rows of the tile; the next plane is prefetched into
+// registers during the updates.
 template <bool PATCH>
 __global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
   constexpr int TX = 64, TY = 16, H = 2, LX = TX + 2 * H, LY = TY + 2 * H, PX = LX / 2;
   constexpr int PP = PX * LY, NW = TY / 2, NT = 32 * NW, NLD = (PP + NT - 1) / NT, NS = 4;
-  constexpr int NE = TY + 2, PL = LX * LY;
-  __shared__ __align__(16) float se[NS * PL];
+  constexpr int NE = TY + 2, PL = 2 * PP;
+  __shared__ __align__(16) float se[NS * PL];  // [slot][colour][pair]
   __shared__ __align__(16) float sf[NS * PL];
   const int n0 = L.n0, n1 = L.n1, n2 = L.n2;
   const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
@@ -160,13 +177,12 @@ __global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
     int r = v % n;
     return r < 0 ? r + n : r;
   };
-  int roff[NLD], sidx[NLD];
-  unsigned ldf[NLD];  // bit 0: load, bit 1: write out
+  int roff[NLD];
+  unsigned ldf[NLD];  // bit 0: load, bit 1: write out, bit 2: parity of the row
 #pragma unroll
   for (int k = 0; k < NLD; k++) {
     const int q = threadIdx.x + k * NT;
     roff[k] = 0;
-    sidx[k] = 0;
     ldf[k] = 0;
     if (q < PP) {
       const int ly = q / PX, px = q - (q / PX) * PX;
@@ -182,8 +198,7 @@ __global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
       const bool wr = ok && ly >= H && ly < H + TY && px >= 1 && px < PX - 1 && gx < n0 &&
                       gy < n1;
       roff[k] = ok ? gyw * n0 + gxw : 0;
-      sidx[k] = ly * LX + 2 * px;
-      ldf[k] = (ok ? 1u : 0u) | (wr ? 2u : 0u);
+      ldf[k] = (ok ? 1u : 0u) | (wr ? 2u : 0u) | ((unsigned)(ly & 1) << 2);
     }
   }
   float2 pe[NLD], pf[NLD];
@@ -200,37 +215,43 @@ __global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
       pf[k] = *reinterpret_cast<const float2 *>(fin + zoff + roff[k]);
     }
   };
-  auto commit = [&](int so) {
+  // plane of parity pb into slot offset so
+  auto commit = [&](int pb, int so) {
 #pragma unroll
     for (int k = 0; k < NLD; k++) {
-      if (threadIdx.x + k * NT >= PP) continue;
-      *reinterpret_cast<float2 *>(&se[so + sidx[k]]) = pe[k];
-      *reinterpret_cast<float2 *>(&sf[so + sidx[k]]) = pf[k];
+      const int q = threadIdx.x + k * NT;
+      if (q >= PP) continue;
+      const int c0 = (int)((ldf[k] >> 2) & 1u) ^ pb;
+      se[so + c0 * PP + q] = pe[k].x;
+      se[so + (c0 ^ 1) * PP + q] = pe[k].y;
+      sf[so + c0 * PP + q] = pf[k].x;
+      sf[so + (c0 ^ 1) * PP + q] = pf[k].y;
     }
   };
   // Gauss-Seidel update of the colour-Q cell of pair (ly, px) of plane m; s is
   // its x position in the pair; oc, om, op the slot offsets of planes m, m-1, m+1
-  auto update = [&](int ly, int px, int s, int m, int oc, int om, int op) {
-    const int lx = 2 * px + s;
-    const int gx = X0 - H + lx, gy = Y0 - H + ly;
+  auto update = [&](int Q, int ly, int px, int s, int m, int oc, int om, int op) {
+    const int gx = X0 - H + 2 * px + s, gy = Y0 - H + ly;
     if (PATCH && (gx < 0 || gx >= n0 || gy < 0 || gy >= n1)) return;
-    const int i = ly * LX + lx;
+    const int e = ly * PX + px;
+    const int cq = oc + Q * PP + e, V = oc + (Q ^ 1) * PP + e;
+    const int o = (Q ^ 1) * PP + e;
     float sum = 0.0f;
     int nm = 0;
-    if (!PATCH || gx > 0) sum += se[oc + i - 1]; else nm++;
-    if (!PATCH || gx < n0 - 1) sum += se[oc + i + 1]; else nm++;
-    if (!PATCH || gy > 0) sum += se[oc + i - LX]; else nm++;
-    if (!PATCH || gy < n1 - 1) sum += se[oc + i + LX]; else nm++;
-    if (!PATCH || m > 0) sum += se[om + i]; else nm++;
-    if (!PATCH || m < n2 - 1) sum += se[op + i]; else nm++;
-    const float gs = (sum - h2 * sf[oc + i]) / (6.0f + (float)nm);
-    se[oc + i] = fmaf(relax, gs - se[oc + i], se[oc + i]);
+    if (!PATCH || gx > 0) sum += se[s ? V : V - 1]; else nm++;
+    if (!PATCH || gx < n0 - 1) sum += se[s ? V + 1 : V]; else nm++;
+    if (!PATCH || gy > 0) sum += se[V - PX]; else nm++;
+    if (!PATCH || gy < n1 - 1) sum += se[V + PX]; else nm++;
+    if (!PATCH || m > 0) sum += se[om + o]; else nm++;
+    if (!PATCH || m < n2 - 1) sum += se[op + o]; else nm++;
+    const float gs = gs_value(sum, h2 * sf[cq], nm);
+    se[cq] = fmaf(relax, gs - se[cq], se[cq]);
   };
   const int P0 = Z0 - H, PE = Z1 + H;
   auto inr = [&](int pz) { return !PATCH || (pz >= 0 && pz < n2); };
   int pw = PATCH ? P0 : wrapm(P0, n2);
   if (inr(P0)) fetch((long long)pw * plane);
-  commit(0);
+  commit(P0 & 1, 0);
   __syncthreads();
   int cur = 0;
   for (int p = P0; p < PE; p++) {
@@ -246,13 +267,13 @@ __global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
 #pragma unroll
         for (int j = 0; j < 3; j++) {
           if (j == 2 && w >= 2) break;
-          update(1 + w + j * NW, 1 + lane, s, m, o1, o2, o0);
+          update(0, 1 + w + j * NW, 1 + lane, s, m, o1, o2, o0);
         }
         if (w == 2 || w == 3) {
           const int idx = (w - 2) * 32 + lane;
           if (idx < NE) {
             const int ly = 1 + idx, se_ = (ly + m) & 1;
-            update(ly, se_ ? 0 : PX - 1, se_, m, o1, o2, o0);
+            update(0, ly, se_ ? 0 : PX - 1, se_, m, o1, o2, o0);
           }
         }
       }
@@ -263,7 +284,7 @@ __global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
       if (m >= Z0 && m < Z1 && inr(m)) {
         const int s = (w + m + 1) & 1;  // rows 2 + w + j NW: (ly + m + 1) & 1
 #pragma unroll
-        for (int j = 0; j < 2; j++) update(2 + w + j * NW, 1 + lane, s, m, o2, o3, o1);
+        for (int j = 0; j < 2; j++) update(1, 2 + w + j * NW, 1 + lane, s, m, o2, o3, o1);
       }
     }
     __syncthreads();
@@ -273,12 +294,15 @@ __global__ void __launch_bounds__(256, 4) k_lsmooth_tiled(PLevel L, int zc) {
         const long long woff = (long long)wz * plane;
 #pragma unroll
         for (int k = 0; k < NLD; k++)
-          if (ldf[k] & 2u)
+          if (ldf[k] & 2u) {
+            const int q = threadIdx.x + k * NT;
+            const int c0 = (int)((ldf[k] >> 2) & 1u) ^ (wz & 1);
             *reinterpret_cast<float2 *>(eout + woff + roff[k]) =
-                *reinterpret_cast<const float2 *>(&se[o2 + sidx[k]]);
+                make_float2(se[o2 + c0 * PP + q], se[o2 + (c0 ^ 1) * PP + q]);
+          }
       }
     }
-    if (more) commit(o3);
+    if (more) commit((p + 1) & 1, o3);
     __syncthreads();
     cur = (cur + 1) & 3;
   }
@@ -360,6 +384,108 @@ __global__ void __launch_bounds__(kNT) k_lprolong(PLevel F, PLevel C) {
   F.e[t] += acc;
 }
 
+// Tiled e^h += P e^H (the interpolation of k_lprolong, evaluated in the order
+// z, y, x): a block owns a 64 x 16 fine tile (32 x 8 coarse cells) and a chunk
+// of kc coarse planes; the coarse tile plus a one-cell halo is staged in
+// shared memory for planes K-1, K, K+1 (ring of three), the z-interpolated
+// plane is formed once per fine plane, and each thread corrects fine x-pairs
+// with 8-byte loads and stores.  Patches: coarse cells outside the grid
+// contribute 0.
+constexpr int kLpTX = 64, kLpTY = 16;
+template <bool PATCH>
+__global__ void __launch_bounds__(256) k_lprolong_tiled(PLevel F, PLevel C, int kc) {
+  constexpr int CX = kLpTX / 2 + 2, CY = kLpTY / 2 + 2, CP = CX * CY;
+  constexpr int NQ = (CP + 255) / 256;
+  __shared__ float se[3][CP];
+  __shared__ float sz[CP];
+  const int n0 = F.n0, n1 = F.n1;
+  const int c0 = C.n0, c1 = C.n1, c2 = C.n2;
+  const float *__restrict__ eH = C.e;
+  float *__restrict__ ef = F.e;
+  const int ntx = (n0 + kLpTX - 1) / kLpTX, nty = (n1 + kLpTY - 1) / kLpTY;
+  int b = blockIdx.x;
+  const int X0 = (b % ntx) * kLpTX;
+  b /= ntx;
+  const int Y0 = (b % nty) * kLpTY;
+  b /= nty;
+  const int K0 = b * kc, K1 = min(K0 + kc, c2);
+  auto wrapm = [](int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+  };
+  int qoff[NQ];
+  bool qok[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; k++) {
+    const int q = threadIdx.x + k * 256;
+    qoff[k] = 0;
+    qok[k] = false;
+    if (q < CP) {
+      int I = X0 / 2 - 1 + q % CX, J = Y0 / 2 - 1 + q / CX;
+      if (PATCH) {
+        qok[k] = I >= 0 && I < c0 && J >= 0 && J < c1;
+      } else {
+        I = wrapm(I, c0);
+        J = wrapm(J, c1);
+        qok[k] = true;
+      }
+      qoff[k] = J * c0 + I;
+    }
+  }
+  const long long cplane = (long long)c0 * c1;
+  int kw = PATCH ? K0 - 1 : wrapm(K0 - 1, c2);  // wrapped index of the next plane staged
+  auto stage = [&](int slot, int K) {
+    const bool vz = !PATCH || (K >= 0 && K < c2);
+    const long long zo = (long long)kw * cplane;
+#pragma unroll
+    for (int k = 0; k < NQ; k++) {
+      const int q = threadIdx.x + k * 256;
+      if (q >= CP) continue;
+      se[slot][q] = (qok[k] && vz) ? eH[zo + qoff[k]] : 0.0f;
+    }
+    kw = PATCH ? kw + 1 : (kw + 1 == c2 ? 0 : kw + 1);
+  };
+  const int lane = threadIdx.x & 31, r0 = threadIdx.x >> 5;
+  const long long fplane = (long long)n0 * n1;
+  const float w3 = 0.75f, w1 = 0.25f;
+  stage(0, K0 - 1);
+  stage(1, K0);
+  int sm = 0, sc = 1, sp = 2;  // ring slots of planes K-1, K, K+1
+  for (int K = K0; K < K1; K++) {
+    stage(sp, K + 1);
+    __syncthreads();
+#pragma unroll
+    for (int cz = 0; cz < 2; cz++) {
+      const int so = cz ? sp : sm;
+      for (int q = threadIdx.x; q < CP; q += 256) sz[q] = w3 * se[sc][q] + w1 * se[so][q];
+      __syncthreads();
+      const int k = 2 * K + cz;
+      const int fx = X0 + 2 * lane;
+#pragma unroll
+      for (int rr = 0; rr < 2; rr++) {
+        const int row = r0 + 8 * rr;
+        const int j = Y0 + row;
+        if (j >= n1 || fx >= n0) continue;
+        const int jy = row / 2 + 1, jy2 = (row & 1) ? jy + 1 : jy - 1;
+        const int ix = lane + 1;
+        const float *za = sz + jy * CX, *zb = sz + jy2 * CX;
+        const float em = w3 * za[ix - 1] + w1 * zb[ix - 1];
+        const float e0 = w3 * za[ix] + w1 * zb[ix];
+        const float ep = w3 * za[ix + 1] + w1 * zb[ix + 1];
+        const long long fi = (long long)k * fplane + (long long)j * n0 + fx;
+        const float2 v = *reinterpret_cast<const float2 *>(ef + fi);
+        *reinterpret_cast<float2 *>(ef + fi) =
+            make_float2(v.x + (w3 * e0 + w1 * em), v.y + (w3 * e0 + w1 * ep));
+      }
+      __syncthreads();
+    }
+    const int t = sm;
+    sm = sc;
+    sc = sp;
+    sp = t;
+  }
+}
+
 // Coarsest level: one block, red-black sweeps until the rms residual falls by
 // 1e-3 of its value before the first sweep (at most maxit sweeps) or stops falling.
 __global__ void __launch_bounds__(kNT) k_lcoarsest(PLevel L, int maxit) {
@@ -398,7 +524,7 @@ __global__ void __launch_bounds__(kNT) k_lcoarsest(PLevel L, int maxit) {
         const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
         int nm;
         const float s = nbsum(L, L.e, i, j, k, c, nm);
-        L.e[c] = (s - L.h2 * L.f[c]) / (6.0f + (float)nm);
+        L.e[c] = gs_value(s, L.h2 * L.f[c], nm);
       }
       __syncthreads();
     }
@@ -687,6 +813,8 @@ struct PoissonSolver {
   int pre = 2, post = 2;
 
   std::vector<int> zc, nblk_t;  // tiled smoother: z-chunk and blocks per level (0: not tiled)
+  std::vector<int> kc_p, nblk_p;  // tiled prolongation onto a level: coarse planes per block
+                                  // and blocks (0: one thread per fine cell)
 
   void smooth(int l, int n) {
     for (int it = 0; it < n; it++) {
@@ -717,7 +845,14 @@ struct PoissonSolver {
                                                              l == 0 ? partial0 : nullptr);
     PLAUNCH(ctx);
     vcycle(l + 1, nullptr);
-    k_lprolong<<<nblk(lev[l].ncell), kNT, 0, st>>>(lev[l], lev[l + 1]);
+    if (nblk_p[l] > 0) {
+      if (lev[l].patch)
+        k_lprolong_tiled<true><<<nblk_p[l], 256, 0, st>>>(lev[l], lev[l + 1], kc_p[l]);
+      else
+        k_lprolong_tiled<false><<<nblk_p[l], 256, 0, st>>>(lev[l], lev[l + 1], kc_p[l]);
+    } else {
+      k_lprolong<<<nblk(lev[l].ncell), kNT, 0, st>>>(lev[l], lev[l + 1]);
+    }
     PLAUNCH(ctx);
     smooth(l, post);
   }
@@ -791,7 +926,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
     }
     split_host(1.0 / (h * h), P.ih2h, P.ih2l);
     // multigrid levels of the correction equation
-    PoissonSolver S{ctx, st, {}, o.pre, o.post, {}, {}};
+    PoissonSolver S{ctx, st, {}, o.pre, o.post, {}, {}, {}, {}};
     {
       const int nl = level_count(dims);
       int m[3] = {dims[0], dims[1], dims[2]};
@@ -841,6 +976,31 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
         }
         S.zc.push_back(zcl);
         S.nblk_t.push_back(nbt);
+        // tiled prolongation onto this level (from the next coarser one) where
+        // its 64 x 16 tiles times coarse-plane chunks fill the GPU: chunks of
+        // kc coarse planes minimise (waves of 8 resident blocks per SM) x (kc + 1)
+        int kcp = 0, nbp = 0;
+        if (l + 1 < nl && nbt > 0) {
+          int sms = 0, dev = 0;
+          PCK(cudaGetDevice(&dev));
+          PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+          const long long slots = 8ll * std::max(sms, 1);
+          const long long tiles = (long long)((m[0] + 63) / 64) * ((m[1] + 15) / 16);
+          const int c2 = m[2] / 2;
+          double best = 1e300;
+          for (int c = 1; c <= c2; c++) {
+            const int z = (c2 + c - 1) / c;
+            const long long blocks = tiles * ((c2 + z - 1) / z);
+            const double cost = std::ceil((double)blocks / slots) * (z + 1);
+            if (cost < best - 1e-9) {
+              best = cost;
+              kcp = z;
+            }
+          }
+          nbp = (int)(tiles * ((c2 + kcp - 1) / kcp));
+        }
+        S.kc_p.push_back(kcp);
+        S.nblk_p.push_back(nbp);
         S.lev.push_back(L);
         for (int d = 0; d < 3; d++) m[d] /= 2;
         hl *= 2.0;
