@@ -536,7 +536,8 @@ def main():
         tune_s = None
     else:
         best, tune_s = ctx.autotune(rho, tol=TOL, prec="mixed", stream=stream, **PHYS)
-        tuned = {k: best[k] for k in ("pre", "post", "temporal_depth", "relax", "fmg")}
+        tuned = {k: best[k] for k in ("pre", "post", "temporal_depth", "relax", "fmg",
+                                          "tiling")}
     solve("mixed")
     torch.cuda.synchronize()
     barrier()
@@ -688,9 +689,9 @@ def main():
         "autotuned": {**tuned, "tune_seconds": tune_s,
                       "note": ("fixed by --options" if fixed else
                                "fastest of V(pre,post) in {(1,1),(2,1),(1,2),(2,2),(3,3)} x "
-                               "relaxation factor {1,1.15,1.25}, then sweeps per tiled pass "
-                               "{1,2} and full-multigrid start {0,1}, chosen by fr_autotune "
-                               "on this field")},
+                               "relaxation factor {1,1.15,1.25}, then one at a time sweeps "
+                               "per tiled pass {1,2}, full-multigrid start {0,1} and tiling "
+                               "{0,1}, chosen by fr_autotune on this field")},
         "mixed_default_v22": {"value": value_default, "unit": "cells/s",
                               "vcycles": s_def.vcycles, "outer": s_def.outer},
         "mixed": {"vcycles": s0.vcycles, "outer": s0.outer, "res_rms": s0.res_rms,

@@ -270,9 +270,9 @@ int fr_residual_norm_noalloc(const double *u, const double *density, const int d
  * Autotuner: solves the given problem from u = 0 (into library scratch; the
  * caller's arrays are only read) with every combination of the V-cycle shape
  * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)} and the relaxation factor
- * relax in {1, 1.15, 1.25} at one sweep per tiled pass, then for the fastest
- * of those with two sweeps per pass (temporal_depth 2) and with the
- * full-multigrid start (fmg 1), on top of *base (NULL =
+ * relax in {1, 1.15, 1.25} at one sweep per tiled pass, then, one at a time on
+ * top of the fastest setting so far, two sweeps per pass (temporal_depth 2),
+ * the full-multigrid start (fmg 1) and tiling 1, on top of *base (NULL =
  * defaults), twice each, and writes the fastest setting that reaches tol to
  * *best (and its time in seconds to *best_seconds, if not NULL).  Device or
  * host density pointer.  FR_ENOCONV if no candidate converged.

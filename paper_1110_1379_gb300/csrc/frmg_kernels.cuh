@@ -35,6 +35,8 @@
 #include <type_traits>
 #include <utility>
 
+#include "frmg_dfmath.cuh"
+
 namespace frmg {
 
 template <typename T>
@@ -57,7 +59,25 @@ struct Grid {
   T fs, fo;
   T cap;           // Newton step cap
   T relax;         // relaxation factor of the Newton update (1: plain Newton-GS)
+  FastDiv fd0, fd1;  // division by n0 and n1 (cell index -> (i, j, k))
 };
+
+// (i, j, k) of the linear cell index c < ncell: 32-bit multiply-shift division
+// below 2^31 cells, 64-bit division above.
+template <typename T>
+__device__ __forceinline__ void cell_ijk(const Grid<T> &G, long long c, int &i, int &j, int &k) {
+  if (G.ncell < (1ll << 31)) {
+    const unsigned cu = (unsigned)c, q = fdiv(cu, G.fd0), q2 = fdiv(q, G.fd1);
+    i = (int)(cu - q * (unsigned)G.n0);
+    j = (int)(q - q2 * (unsigned)G.n1);
+    k = (int)q2;
+  } else {
+    i = (int)(c % G.n0);
+    const long long r = c / G.n0;
+    j = (int)(r % G.n1);
+    k = (int)(r / G.n1);
+  }
+}
 
 // ----------------------------------------------------------------------------
 // math wrappers (library functions; no re-derived constants)
@@ -340,13 +360,10 @@ __global__ void k_smooth(const Grid<T> *grids, const int *off, int ngrid, int co
   const Grid<T> G = view(grids, g, par);
   if (!grid_active(active, G.field)) return;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
-  int hx = G.n0 >> 1;
-  if (t >= (long long)hx * G.n1 * G.n2) return;
-  int ih = (int)(t % hx);
-  long long r = t / hx;
-  int j = (int)(r % G.n1);
-  int k = (int)(r / G.n1);
-  int i = 2 * ih + ((j + k + colour) & 1);
+  if (2 * t >= G.ncell) return;
+  int i, j, k;
+  cell_ijk(G, 2 * t, i, j, k);  // even cell of the pair
+  i += (j + k + colour) & 1;
   ngs_update<T, BG>(G, i, j, k);
 }
 
@@ -419,10 +436,8 @@ __global__ void __launch_bounds__(NT) k_residual(const Grid<T> *grids, const int
   float s = 0.0f, m = 0.0f;
   long long t = (long long)(blockIdx.x - off[g]) * NT + threadIdx.x;
   if (grid_active(active, G.field) && t < G.ncell) {
-    int i = (int)(t % G.n0);
-    long long r = t / G.n0;
-    int j = (int)(r % G.n1);
-    int k = (int)(r / G.n1);
+    int i, j, k;
+    cell_ijk(G, t, i, j, k);
     T N, dN;
     cell_eval<T, BG>(G, i, j, k, t, N, dN);
     T d = N - rhs_at(G, t);
@@ -489,10 +504,8 @@ __global__ void __launch_bounds__(256)
   float ss = 0.0f, mx = 0.0f;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
   if (grid_active(active, F.field) && t < C.ncell) {
-    int I = (int)(t % C.n0);
-    long long r = t / C.n0;
-    int J = (int)(r % C.n1);
-    int K = (int)(r / C.n1);
+    int I, J, K;
+    cell_ijk(C, t, I, J, K);
     T su = T(0), sd = T(0);
 #pragma unroll
     for (int cz = 0; cz < 2; cz++)
@@ -530,10 +543,8 @@ __global__ void k_fas_rhs(const Grid<T> *grids, const int *off, int ngrid, const
   if (!grid_active(active, G.field)) return;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
   if (t >= G.ncell) return;
-  int i = (int)(t % G.n0);
-  long long r = t / G.n0;
-  int j = (int)(r % G.n1);
-  int k = (int)(r / G.n1);
+  int i, j, k;
+  cell_ijk(G, t, i, j, k);
   T N, dN;
   cell_eval<T, BG>(G, i, j, k, t, N, dN);
   T *f = const_cast<T *>(G.f);
@@ -556,10 +567,8 @@ __global__ void __launch_bounds__(256)
   float ss = 0.0f, mx = 0.0f;
   long long t = (long long)(blockIdx.x - off[g]) * blockDim.x + threadIdx.x;
   if (t < C.ncell) {
-    int I = (int)(t % C.n0);
-    long long r = t / C.n0;
-    int J = (int)(r % C.n1);
-    int K = (int)(r / C.n1);
+    int I, J, K;
+    cell_ijk(C, t, I, J, K);
     T N, dN;
     cell_eval<T, false>(C, I, J, K, t, N, dN);
     T rf = T(0);
@@ -598,10 +607,8 @@ __global__ void __launch_bounds__(256) k_prolong(const Grid<T> *fine, const Grid
   T *__restrict__ uf = fpar ? Fg.u2 : Fg.u;
   T *__restrict__ xf = fpar ? Fg.x2 : Fg.x;
   const bool dir = Fg.bnd != nullptr;
-  const int I = (int)(t % c0);
-  long long r = t / c0;
-  const int J = (int)(r % c1);
-  const int K = (int)(r / c1);
+  int I, J, K;
+  cell_ijk(Cg, t, I, J, K);
   // e over the 3x3x3 neighbourhood, index [dz][dy][dx] with d = -1, 0, 1
   T e[3][3][3];
 #pragma unroll
@@ -828,21 +835,17 @@ __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid
     if (it >= 0) {
       for (int colour = 0; colour < 2; colour++) {
         for (long long t = threadIdx.x; t < nh; t += NT) {
-          int ih = (int)(t % hx);
-          long long r = t / hx;
-          int j = (int)(r % G.n1);
-          int k = (int)(r / G.n1);
-          ngs_update<T, BG>(G, 2 * ih + ((j + k + colour) & 1), j, k);
+          int i, j, k;
+          cell_ijk(G, 2 * t, i, j, k);
+          ngs_update<T, BG>(G, i + ((j + k + colour) & 1), j, k);
         }
         __syncthreads();
       }
       if (shift) {
         double S = 0.0, D = 0.0;
         for (long long t = threadIdx.x; t < n; t += NT) {
-          int i = (int)(t % G.n0);
-          long long r = t / G.n0;
-          int j = (int)(r % G.n1);
-          int k = (int)(r / G.n1);
+          int i, j, k;
+          cell_ijk(G, t, i, j, k);
           T N, dN;
           cell_eval<T, BG>(G, i, j, k, t, N, dN);
           S += (double)(N - rhs_at(G, t));
@@ -866,10 +869,8 @@ __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid
     }
     double s = 0.0;
     for (long long t = threadIdx.x; t < n; t += NT) {
-      int i = (int)(t % G.n0);
-      long long r = t / G.n0;
-      int j = (int)(r % G.n1);
-      int k = (int)(r / G.n1);
+      int i, j, k;
+      cell_ijk(G, t, i, j, k);
       T N, dN;
       cell_eval<T, BG>(G, i, j, k, t, N, dN);
       double d = (double)(N - rhs_at(G, t));

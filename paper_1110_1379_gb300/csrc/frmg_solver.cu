@@ -525,6 +525,11 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 
   }
   ls.nblk_half = ls.off_half[ng];
   ls.nblk_full = ls.off_full[ng];
+  // every grid reaches the device through here: its index dividers too
+  for (auto &g : ls.h) {
+    g.fd0 = make_fastdiv((unsigned)g.n0);
+    g.fd1 = make_fastdiv((unsigned)g.n1);
+  }
   ls.d = S.get<Grid<T>>(ng);
   ls.d_off_half = S.get<int>(ng + 1);
   ls.d_off_full = S.get<int>(ng + 1);
@@ -2270,8 +2275,8 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
       return tmin;
     };
     // every V-cycle shape and relaxation factor with one sweep per tiled
-    // pass, then for the best of them two sweeps per pass and the
-    // full-multigrid start
+    // pass; then, one at a time on top of the best setting so far, two sweeps
+    // per tiled pass, the full-multigrid start and tiling wherever possible
     for (int sh = 0; sh < 5; sh++)
       for (double w : relaxes) {
         fr_opts o = o0;
@@ -2282,12 +2287,14 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
         trial(o);
       }
     if (status == FR_OK) {
-      const fr_opts b = best_o;
-      fr_opts o = b;
+      fr_opts o = best_o;
       o.temporal_depth = 2;
       trial(o);
-      o = b;
+      o = best_o;
       o.fmg = 1;
+      trial(o);
+      o = best_o;
+      o.tiling = 1;
       trial(o);
     }
     frmg_release(ctx, u);
