@@ -1181,16 +1181,20 @@ struct RBCfg {
   static constexpr int LX = TX + 2 * H, LY = TY + 2 * H, PX = LX / 2, PP = PX * LY;
   static constexpr int NW = TY / 2, NT = 32 * NW;  // warps, threads
   static constexpr int NLD = (PP + NT - 1) / NT;   // plane-load rounds per thread
-  static constexpr int NS = 4, NF = 3;             // ring slots of (u, x) [and (ub, E)], of f
+  // ring slots of (u, x) [and (ub, E)]; the right-hand side is kept per
+  // colour: a red half-plane is read one step after it is loaded, a black one
+  // two steps after, so two red and three black half-slots suffice
+  static constexpr int NS = 4, NFR = 2, NFB = 3;
   static constexpr int NE = TY + 2;                // edge cells of the red region
   static constexpr size_t smem(bool bg) {
     return (size_t)NS * 2 * PP * sizeof(float2) * (bg ? 2 : 1) +
-           (size_t)NF * 2 * PP * sizeof(float);
+           (size_t)(NFR + NFB) * PP * sizeof(float);
   }
-  // resident blocks per SM that shared memory allows (at most 1024 threads)
+  // resident blocks per SM that shared memory allows, at most 3 (a fourth
+  // block of 256 threads caps the registers at 64 per thread: measured slower)
   static constexpr int minb(bool bg) {
     const int bysm = (int)(228 * 1024 / (smem(bg) + 1024));
-    const int byth = 1024 / NT;
+    const int byth = 1024 / NT < 3 ? 1024 / NT : 3;
     return bysm < 1 ? 1 : (bysm < byth ? bysm : byth);
   }
   static_assert(TY % 4 == 0 && NW >= 4 && NE <= 64, "tile height");
@@ -1202,13 +1206,14 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
                 int par) {
   using C = RBCfg<TY>;
   constexpr int TX = C::TX, H = C::H, PX = C::PX, PP = C::PP, NW = C::NW, NT = C::NT;
-  constexpr int NLD = C::NLD, NS = C::NS;
+  constexpr int NLD = C::NLD, NS = C::NS, NFR = C::NFR, NFB = C::NFB;
   extern __shared__ float4 smem_rb[];
   // plain form: (u, x) per cell; correction form: (u, x, ub, E) per cell, so a
   // neighbour is one 16-byte access (half the shared-memory instructions)
   float2 *sux = reinterpret_cast<float2 *>(smem_rb);  // [NS][2][PP] (plain)
   float4 *s4 = smem_rb;                               // [NS][2][PP] (correction form)
-  float *sfv = reinterpret_cast<float *>(sux + NS * 2 * PP * (BG ? 2 : 1));  // [NF][2][PP]
+  // right-hand side: red half-slots [NFR][PP], then black half-slots [NFB][PP]
+  float *sfv = reinterpret_cast<float *>(sux + NS * 2 * PP * (BG ? 2 : 1));
   // cell e of a slot/colour offset: (u, x, ub, E); ub = 0, E = 1 in the plain form
   auto cell = [&](int i) -> float4 {
     if (BG) return s4[i];
@@ -1297,9 +1302,9 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
       }
     }
   };
-  // plane of parity pb into (u, x) slot offset so and f slot offset fo2; the
-  // even-x cell of a pair has colour (y + z) & 1
-  auto commit = [&](int pb, int so, int fo2) {
+  // plane of parity pb into (u, x) slot offset so and the f half-slot offsets
+  // fr (red) and fb (black); the even-x cell of a pair has colour (y + z) & 1
+  auto commit = [&](int pb, int so, int fr, int fb) {
 #pragma unroll
     for (int k = 0; k < NLD; k++) {
       const int q = threadIdx.x + k * NT;
@@ -1313,8 +1318,8 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
         sux[i0] = make_float2(pd[k].x, pq[k].x);
         sux[i1] = make_float2(pd[k].y, pq[k].y);
       }
-      sfv[fo2 + c0 * PP + q] = fin ? fs * (pf[k].x - fo) : 0.0f;
-      sfv[fo2 + (c0 ^ 1) * PP + q] = fin ? fs * (pf[k].y - fo) : 0.0f;
+      sfv[(c0 ? fb : fr) + q] = fin ? fs * (pf[k].x - fo) : 0.0f;
+      sfv[(c0 ? fr : fb) + q] = fin ? fs * (pf[k].y - fo) : 0.0f;
     }
   };
   // Newton update of the colour-Q cell of pair (ly, px) of plane m; s is its x
@@ -1366,7 +1371,7 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
     A.done(acc, dacc);
     float N, dN;
     finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-    float du = relax * newton_step(N - sfv[ofq + cq + e], dN);
+    float du = relax * newton_step(N - sfv[ofq + e], dN);
     du = fminf(fmaxf(du, -cap), cap);
     const float dn = di + du;
     put_ux(oc + cq + e, dn, m_expm1(dn));
@@ -1377,9 +1382,11 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
   // wrapped index of the plane being loaded (periodic grids)
   int pw = DIR ? P0 : wrapmod(P0, n2);
   if (!DIR || (P0 >= 0 && P0 < n2)) fetch((long long)pw * plane);
-  commit(P0 & 1, 0, 0);
+  // f half-slots: red of plane m at (m & 1) PP, black at (NFR + b) PP with b
+  // advancing by one per plane (mod NFB)
+  commit(P0 & 1, 0, (P0 & 1) * PP, NFR * PP);
   __syncthreads();
-  int cur = 0, fcur = 0;  // ring slots of plane p
+  int cur = 0, bcur = 0;  // ring slot of plane p, black f half-slot of plane p
   for (int p = P0; p < PE; p++) {
     const int pb = p & 1;
     const bool more = p + 1 < PE;
@@ -1387,8 +1394,9 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
     if (more && (!DIR || (pw >= 0 && pw < n2))) fetch((long long)pw * plane);
     const int o0 = cur * SLOT, o1 = ((cur + 3) & 3) * SLOT, o2 = ((cur + 2) & 3) * SLOT,
               o3 = ((cur + 1) & 3) * SLOT;  // planes p, p-1, p-2, p-3
-    const int f1 = (fcur == 0 ? 2 : fcur - 1) * SLOT;  // f of plane p-1
-    const int f2 = (fcur == 2 ? 0 : fcur + 1) * SLOT;  // f of plane p-2 (then p+1)
+    const int bnx = bcur == NFB - 1 ? 0 : bcur + 1;  // black f of plane p-2, then p+1
+    const int f1 = ((p - 1) & 1) * PP;  // red f of plane p-1 (then of p+1)
+    const int f2 = (NFR + bnx) * PP;
     // red cells of plane p-1 on the tile grown by one
     {
       const int m = p - 1;
@@ -1440,10 +1448,10 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
         }
       }
     }
-    if (more) commit(pb ^ 1, o3, f2);
+    if (more) commit(pb ^ 1, o3, f1, f2);
     __syncthreads();
     cur = (cur + 1) & 3;
-    fcur = fcur == 2 ? 0 : fcur + 1;
+    bcur = bnx;
   }
 }
 
