@@ -63,8 +63,8 @@ ALG_BYTES = {
 # profiles/ (384^3 launches; traffic grows in proportion to the cells, so it is
 # scaled to the workload's grid).  Valid for the kernels as captured there.
 TRAFFIC_PER_CELL = {
-    "smooth_f32@fine": (1118.444e6 / 384 ** 3, "profiles/smooth_rb_f32_384.md"),
-    "smooth_bg_f32@fine": (1652.112e6 / 384 ** 3, "profiles/smooth_rb_bg_f32_384.md"),
+    "smooth_f32@fine": (1117.662e6 / 384 ** 3, "profiles/smooth_rb_f32_384.md"),
+    "smooth_bg_f32@fine": (1639.797e6 / 384 ** 3, "profiles/smooth_rb_bg_f32_384.md"),
     "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "profiles/resid_restrict_tiled_f32_384.md"),
     "prolong_f32@fine": (678.570e6 / 384 ** 3, "profiles/prolong_tiled_f32_384.md"),
     "df_defect": (2466.320e6 / 384 ** 3, "profiles/df_defect_384.md"),
