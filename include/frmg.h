@@ -94,6 +94,10 @@ typedef struct {
                                solution and one V-cycle from there; the last one, on the
                                finest grid, counts as the first V-cycle); 0 = start the
                                V-cycles from u = 0 (default).  Ignored otherwise. */
+    int initial_guess;      /* fr_solve, fr_solve_batch, fr_solve_levels (domain grid):
+                               1 = u holds the initial guess (default); 0 = start from
+                               u = 0: the contents of u are not read (a host u is not
+                               copied to the device), u is output only. */
 } fr_opts;
 
 #define FR_HIST 64

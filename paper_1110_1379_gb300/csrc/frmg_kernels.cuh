@@ -1455,6 +1455,151 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
   }
 }
 
+// Tiled FAS right-hand side of a coarse level, f <- A(u) - f (the same
+// operator evaluation, face order and arithmetic as k_fas_rhs): a block owns a
+// 64 x 16 tile and a chunk of zc planes and marches along z with a ring of
+// three planes of (u, x) [and (ub, E)] in shared memory (tile plus a halo of
+// one cell); at the step that has loaded plane p it evaluates plane p-1, each
+// thread four cells (two rows, x = lane and lane + 32), with f read and written
+// in place.  The next plane is prefetched into registers during the evaluation.
+constexpr int kFrTX = 64, kFrTY = 16;
+// dynamic shared memory of k_fas_rhs_tiled: three planes of the tile plus halo,
+// (u, x, ub, E) per cell in the correction form, (u, x) in the plain one
+constexpr size_t fas_rhs_tiled_smem(bool bg) {
+  return (size_t)3 * (kFrTX + 2) * (kFrTY + 2) * (bg ? sizeof(float4) : sizeof(float2));
+}
+template <bool BG, bool DIR>
+__global__ void __launch_bounds__(256)
+    k_fas_rhs_tiled(const Grid<float> *grids, const int *off, int ngrid, int zc,
+                    const int *active, int par) {
+  constexpr int LX = kFrTX + 2, LY = kFrTY + 2, PC = LX * LY, NT = 256;
+  constexpr int NLD = (PC + NT - 1) / NT;
+  extern __shared__ float4 sfr[];
+  float2 *s2 = reinterpret_cast<float2 *>(sfr);
+  auto cellv = [&](int i) -> float4 {
+    if (BG) return sfr[i];
+    const float2 v = s2[i];
+    return make_float4(v.x, v.y, 0.f, 1.f);
+  };
+  const int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<float> &Gg = grids[g];
+  if (!grid_active(active, Gg.field)) return;
+  const float *__restrict__ uin = par ? Gg.u2 : Gg.u;
+  const float *__restrict__ xin = par ? Gg.x2 : Gg.x;
+  const float *__restrict__ ubin = Gg.ubg;
+  const float *__restrict__ Ein = Gg.Ebg;
+  float *__restrict__ f = const_cast<float *>(Gg.f);
+  const float ah = Gg.ah, beta = Gg.beta;
+  const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
+  const int ntx = (n0 + kFrTX - 1) / kFrTX, nty = (n1 + kFrTY - 1) / kFrTY;
+  int b = blockIdx.x - off[g];
+  const int X0 = (b % ntx) * kFrTX;
+  b /= ntx;
+  const int Y0 = (b % nty) * kFrTY;
+  b /= nty;
+  const int Z0 = b * zc, Z1 = min(Z0 + zc, n2);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long plane = (long long)n0 * n1;
+  // plane-load table: cell q = threadIdx.x + k NT of the (TX + 2) x (TY + 2) tile
+  int roff[NLD];
+  bool lok[NLD];
+#pragma unroll
+  for (int k = 0; k < NLD; k++) {
+    const int q = threadIdx.x + k * NT;
+    roff[k] = 0;
+    lok[k] = false;
+    if (q < PC) {
+      const int gx = X0 - 1 + q % LX, gy = Y0 - 1 + q / LX;
+      if (DIR) {
+        lok[k] = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
+        roff[k] = lok[k] ? gy * n0 + gx : 0;
+      } else {
+        lok[k] = true;
+        roff[k] = wrapmod(gy, n1) * n0 + wrapmod(gx, n0);
+      }
+    }
+  }
+  float4 pv[NLD];
+  // plane at offset zoff (vz false: outside a patch, never read)
+  auto fetch = [&](long long zoff, bool vz) {
+#pragma unroll
+    for (int k = 0; k < NLD; k++) {
+      pv[k] = make_float4(0.f, 0.f, 0.f, 1.f);
+      if (!vz || !lok[k]) continue;
+      const long long gi = zoff + roff[k];
+      pv[k].x = uin[gi];
+      pv[k].y = xin[gi];
+      if (BG) {
+        pv[k].z = ubin[gi];
+        pv[k].w = Ein[gi];
+      }
+    }
+  };
+  auto commit = [&](int so) {
+#pragma unroll
+    for (int k = 0; k < NLD; k++) {
+      const int q = threadIdx.x + k * NT;
+      if (q >= PC) continue;
+      if (BG)
+        sfr[so + q] = pv[k];
+      else
+        s2[so + q] = make_float2(pv[k].x, pv[k].y);
+    }
+  };
+  // f <- A(u) - f at tile cell (lx, ly) of plane m; om, oc, op: slots of m-1, m, m+1
+  auto eval = [&](int lx, int ly, int m, int om, int oc, int op) {
+    const int gx = X0 - 1 + lx, gy = Y0 - 1 + ly;
+    if (gx >= n0 || gy >= n1) return;
+    const int i = ly * LX + lx;
+    const float4 own = cellv(oc + i);
+    const float di = own.x, xi = own.y;
+    const float Ei = BG ? own.w : 1.0f;
+    const float ubi = BG ? own.z : 0.0f;
+    const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
+    OpAcc<float, BG> A(di, Ei, xi, Bi, ubi);
+    auto nb = [&](int j) {
+      const float4 v = cellv(j);
+      A.reg(v.x, v.y, v.z, v.w);
+    };
+    if (DIR && gx == 0) A.ghost(face_value(Gg, 0, gx, gy, m)); else nb(oc + i - 1);
+    if (DIR && gx == n0 - 1) A.ghost(face_value(Gg, 1, gx, gy, m)); else nb(oc + i + 1);
+    if (DIR && gy == 0) A.ghost(face_value(Gg, 2, gx, gy, m)); else nb(oc + i - LX);
+    if (DIR && gy == n1 - 1) A.ghost(face_value(Gg, 3, gx, gy, m)); else nb(oc + i + LX);
+    if (DIR && m == 0) A.ghost(face_value(Gg, 4, gx, gy, m)); else nb(om + i);
+    if (DIR && m == n2 - 1) A.ghost(face_value(Gg, 5, gx, gy, m)); else nb(op + i);
+    float acc, dacc, N, dN;
+    A.done(acc, dacc);
+    finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
+    const long long c = (long long)m * plane + (long long)gy * n0 + gx;
+    f[c] = N - f[c];
+  };
+  const int P0 = Z0 - 1, PE = Z1 + 1;
+  auto inr = [&](int pz) { return !DIR || (pz >= 0 && pz < n2); };
+  int pw = DIR ? P0 : wrapmod(P0, n2);
+  fetch((long long)pw * plane, inr(P0));
+  commit(0);
+  __syncthreads();
+  int cur = 0;  // ring slot of plane p
+  for (int p = P0; p < PE; p++) {
+    const bool more = p + 1 < PE;
+    pw = DIR ? p + 1 : (pw + 1 == n2 ? 0 : pw + 1);
+    if (more) fetch((long long)pw * plane, inr(p + 1));
+    const int o0 = cur * PC, o1 = (cur == 0 ? 2 : cur - 1) * PC,
+              o2 = (cur == 2 ? 0 : cur + 1) * PC;  // planes p, p-1, p-2
+    const int m = p - 1;
+    if (m >= Z0 && m < Z1) {
+#pragma unroll
+      for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int h = 0; h < 2; h++) eval(1 + lane + 32 * h, 1 + w + 8 * r, m, o2, o1, o0);
+    }
+    __syncthreads();
+    if (more) commit(o2);
+    __syncthreads();
+    cur = cur == 2 ? 0 : cur + 1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Asynchronous global-to-shared copy of 8 bytes (PTX cp.async; both
 // addresses 8-byte aligned); commit_group / wait_group track completion.

@@ -424,6 +424,12 @@ struct LevelSet {
   std::vector<int> off_rb[2];
   int *d_off_rb[2] = {nullptr, nullptr};
   int nblk_rb[2] = {0, 0};
+  // tiled FAS right-hand side (coarse side of a V-cycle level); [0] plain,
+  // [1] correction form
+  int zc_fr[2] = {0, 0};
+  std::vector<int> off_fr[2];
+  int *d_off_fr[2] = {nullptr, nullptr};
+  int nblk_fr[2] = {0, 0};
   // tiled prolongation (fine side of a V-cycle level): chunks of coarse planes
   int kc_pl = 0;
   std::vector<int> off_pl;
@@ -507,6 +513,8 @@ static int pick_chunk(const std::vector<long long> &tiles, const std::vector<int
 
 template <bool BG, bool DIR>
 static long long rb_slots();
+template <bool BG, bool DIR>
+static long long fr_slots();
 template <bool DIR>
 static long long pl_slots();
 template <bool DIR>
@@ -591,6 +599,21 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 
         ls.nblk_rb[v] = ls.off_rb[v][ng];
         ls.d_off_rb[v] = S.get<int>(ng + 1);
         CK(cudaMemcpyAsync(ls.d_off_rb[v], ls.off_rb[v].data(), (ng + 1) * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+      }
+      for (int g = 0; g < ng; g++)
+        tl[g] = (long long)((ls.h[g].n0 + kFrTX - 1) / kFrTX) * ((ls.h[g].n1 + kFrTY - 1) / kFrTY);
+      for (int v = 0; v < 2; v++) {
+        const long long slots = ls.dirichlet ? (v ? fr_slots<true, true>() : fr_slots<false, true>())
+                                             : (v ? fr_slots<true, false>() : fr_slots<false, false>());
+        ls.zc_fr[v] = pick_chunk(tl, n2s, slots, 2, false);
+        ls.off_fr[v].assign(ng + 1, 0);
+        for (int g = 0; g < ng; g++)
+          ls.off_fr[v][g + 1] =
+              ls.off_fr[v][g] + (int)(tl[g] * ((n2s[g] + ls.zc_fr[v] - 1) / ls.zc_fr[v]));
+        ls.nblk_fr[v] = ls.off_fr[v][ng];
+        ls.d_off_fr[v] = S.get<int>(ng + 1);
+        CK(cudaMemcpyAsync(ls.d_off_fr[v], ls.off_fr[v].data(), (ng + 1) * sizeof(int),
                            cudaMemcpyHostToDevice, st));
       }
     }
@@ -848,6 +871,21 @@ static void launch_rb_k(frmg_ctx *ctx, LevelSet<float> &s, const int *active, in
 }
 
 template <bool BG, bool DIR>
+static void launch_fas_rhs_tiled(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
+                                 cudaStream_t st) {
+  const size_t sm = fas_rhs_tiled_smem(BG);
+  static bool attr_set = false;
+  if (!attr_set) {
+    CK(cudaFuncSetAttribute(k_fas_rhs_tiled<BG, DIR>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_set = true;
+  }
+  constexpr int v = BG ? 1 : 0;
+  k_fas_rhs_tiled<BG, DIR><<<s.nblk_fr[v], 256, sm, st>>>(s.d, s.d_off_fr[v], s.size(),
+                                                         s.zc_fr[v], active, par);
+}
+
+template <bool BG, bool DIR>
 static long long rb_slots() {
   static long long slots = 0;
   if (!slots) {
@@ -855,6 +893,15 @@ static long long rb_slots() {
     slots = (long long)sm_count() *
             resident_blocks(k_smooth_rb<BG, DIR, kRbTY>, RC::NT, RC::smem(BG));
   }
+  return slots;
+}
+
+template <bool BG, bool DIR>
+static long long fr_slots() {
+  static long long slots = 0;
+  if (!slots)
+    slots = (long long)sm_count() *
+            resident_blocks(k_fas_rhs_tiled<BG, DIR>, 256, fas_rhs_tiled_smem(BG));
   return slots;
 }
 
@@ -1017,8 +1064,19 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
   }
   {
     PROF(pname("fas_rhs", sizeof(T) == 8, false));
-    k_fas_rhs<T, BG><<<C.nblk_full, 256, 0, st>>>(C.d, C.d_off_full, C.size(), active,
-                                                  H.par[l + 1]);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (C.tiled && C.nblk_fr[BG ? 1 : 0] > 0) {
+        if (C.dirichlet)
+          launch_fas_rhs_tiled<BG, true>(ctx, C, active, H.par[l + 1], st);
+        else
+          launch_fas_rhs_tiled<BG, false>(ctx, C, active, H.par[l + 1], st);
+        done = true;
+      }
+    }
+    if (!done)
+      k_fas_rhs<T, BG><<<C.nblk_full, 256, 0, st>>>(C.d, C.d_off_full, C.size(), active,
+                                                    H.par[l + 1]);
     CK_LAUNCH(ctx);
   }
   vcycle<T, BG>(ctx, H, l + 1, o, active, st);
@@ -1873,6 +1931,15 @@ static fr_opts resolve_opts(const fr_opts *o) {
   return r;
 }
 
+// u of a solve: staged (host pointers) and, unless opts->initial_guess is set,
+// zeroed on the device instead of read (nothing is copied in for a host u)
+static double *stage_u(Scope &S, std::vector<Staged> &back, double *u, size_t n,
+                       const fr_opts &o, cudaStream_t st) {
+  double *d = stage(S, back, u, n, o.initial_guess != 0, true, st);
+  if (!o.initial_guess) CK(cudaMemsetAsync(d, 0, n * sizeof(double), st));
+  return d;
+}
+
 // A solve issued on the legacy default stream runs on a stream of the context
 // instead, because the legacy stream cannot be captured into a graph: the side
 // stream waits for the caller's earlier work and the caller's stream waits for
@@ -1913,6 +1980,7 @@ static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &
   if (!(o.tau_alpha >= 0)) einval("tau_alpha must be >= 0");
   if (!(o.relax > 0 && o.relax < 2)) einval("relax must be in (0, 2)");
   if (o.fmg < 0 || o.fmg > 1) einval("fmg must be 0 or 1");
+  if (o.initial_guess < 0 || o.initial_guess > 1) einval("initial_guess must be 0 or 1");
   for (auto &p : P) {
     p.nl = count_levels(p.n);
     p.k = model_consts(p.box, p.h, p.a, p.om, p.fr0);
@@ -2086,6 +2154,7 @@ void fr_opts_default(fr_opts *o) {
   o->tau_alpha = 0.0;
   o->relax = 1.0;
   o->fmg = 0;
+  o->initial_guess = 1;
 }
 
 const char *fr_status_string(int s) {
@@ -2190,7 +2259,7 @@ static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], d
     std::vector<Staged> back;
     long long nc = (long long)dims[0] * dims[1] * dims[2];
     const double *drho = stage(S, back, density, nc, true, false, st);
-    double *du = stage(S, back, u, nc, true, true, st);
+    double *du = stage_u(S, back, u, nc, o, st);
     validate_density(ctx, S, drho, nc, o.allow_negative_density, st);
     Problem p;
     memset(&p, 0, sizeof(p));
@@ -2343,7 +2412,7 @@ int fr_solve_batch(frmg_ctx *ctx, int nfields, const double *const *density, con
       p.om = om;
       p.fr0 = fr0[i];
       p.rho = stage(S, back, density[i], nc, true, false, st);
-      p.u = stage(S, back, u[i], nc, true, true, st);
+      p.u = stage_u(S, back, u[i], nc, o, st);
       validate_density(ctx, S, p.rho, nc, o.allow_negative_density, st);
     }
     std::vector<fr_stats> sv(nfields);
@@ -2406,7 +2475,7 @@ int fr_solve_levels(frmg_ctx *ctx, const double *density, const int dims[3], dou
     }
     long long nc = (long long)dims[0] * dims[1] * dims[2];
     const double *drho = stage(S, back, density, nc, true, false, st);
-    double *du = stage(S, back, u, nc, true, true, st);
+    double *du = stage_u(S, back, u, nc, o, st);
     validate_density(ctx, S, drho, nc, o.allow_negative_density, st);
     std::vector<fr_stats> all(1 + npatch);
     memset(all.data(), 0, all.size() * sizeof(fr_stats));

@@ -116,6 +116,29 @@ def test_small_nested_patches_match_oracle(C, prec, relax):
         assert np.abs(host(g["u"]) - r.u).max() <= 1e-6
 
 
+@pytest.mark.parametrize("tiling", [-1, 1])
+def test_tiled_patch_levels_match_oracle(C, tiling):
+    """Patches of 32^3 (coarse patch levels of 16^3, tiled with tiling=1: the
+    tiled smoother, residual+restriction, prolongation and FAS right-hand side
+    on Dirichlet grids) against the one-thread-per-cell kernels and the oracle."""
+    P = dict(box=64.0, a=1.0, fr0=1e-5)
+    rho0, patches = _levels_case(32, P, [32], 2, [], 0, 720)
+    assert len(patches) >= 1 and all(p["rho"].shape == (32, 32, 32) for p in patches)
+    dom, pres = O.solve_levels(rho0, [dict(parent=p["parent"], origin=p["origin"], rho=p["rho"])
+                                      for p in patches], tol=1e-8, omega_m=OM, **P)
+    u0 = torch.zeros(rho0.shape, dtype=torch.float64, device="cuda")
+    gp = [dict(parent=p["parent"], origin=p["origin"], density=dev(p["rho"]),
+               u=torch.zeros(p["rho"].shape, dtype=torch.float64, device="cuda"))
+          for p in patches]
+    st, stats = C.solve_levels(dev(rho0), u0, gp, tol=1e-8, omega_m=OM, prec="mixed",
+                               tiling=tiling, **P)
+    assert st == 0
+    assert np.abs(host(u0) - dom.u).max() <= 1e-6
+    for g, r in zip(gp, pres):
+        assert r.converged
+        assert np.abs(host(g["u"]) - r.u).max() <= 1e-6
+
+
 def test_full_nested_workload(C):
     """256^3 domain, 8-32 level-1 patches of 32^3-64^3 and level-2 patches inside
     them (lognormal sigma 2.5, |f_R0| = 1e-5), mixed precision."""

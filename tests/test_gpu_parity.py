@@ -401,6 +401,26 @@ def test_fmg_start_reaches_oracle_solution(C, shape, relax):
     assert s.hist[0] < 0.5 * s.res0_rms
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_initial_guess_zero_does_not_read_u(C, prec):
+    """initial_guess=0: u is output only (host NaNs are neither copied in nor
+    read); the result equals the solve from a zeroed u, bit for bit."""
+    shape = (32, 32, 32)
+    rho = _field(shape, 1000, sigma=1.0)
+    u0 = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, s0 = C.solve(dev(rho), u0, tol=1e-8, prec=prec, **CFG1)
+    assert st == 0
+    for host_u in (False, True):
+        u1 = torch.full(shape, float("nan"), dtype=torch.float64,
+                        device="cpu" if host_u else "cuda")
+        st, s1 = C.solve(dev(rho), u1, tol=1e-8, prec=prec, initial_guess=0, **CFG1)
+        assert st == 0 and s1.vcycles == s0.vcycles
+        assert np.array_equal(host(u1), host(u0))
+    from paper_1110_1379_gb300 import frmg
+    with pytest.raises(frmg.FRError):
+        C.solve(dev(rho), u0, initial_guess=2, **CFG1)
+
+
 def test_relax_out_of_range_rejected(C):
     from paper_1110_1379_gb300 import frmg
     rho = torch.ones((8, 8, 8), dtype=torch.float64, device="cuda")
