@@ -355,6 +355,156 @@ __global__ void __launch_bounds__(kNT) k_lresid_restrict(PLevel F, PLevel C, dou
   }
 }
 
+// Tiled residual + restriction (the arithmetic of k_lresid_restrict): a block
+// owns a 64 x 16 fine tile (32 x 8 coarse cells, one per thread) and a chunk
+// of kc coarse planes, and keeps a ring of four fine planes of e (tile plus a
+// one-cell halo) in shared memory: coarse plane K needs fine planes 2K-1 ..
+// 2K+2, and each step loads the next two (prefetched into registers while the
+// residuals of the current pair of fine planes are formed).  f is read by
+// each thread for its own 2 x 2 x 2 children.  Optional per-block norm
+// partials (sum d^2, max |d|).
+constexpr int kLrTX = 64, kLrTY = 16;
+template <bool PATCH>
+__global__ void __launch_bounds__(256) k_lresid_restrict_tiled(PLevel F, PLevel C, int kc,
+                                                               double *partial) {
+  constexpr int LX = kLrTX + 2, LY = kLrTY + 2, PC = LX * LY, NT = 256;
+  constexpr int NLD = (PC + NT - 1) / NT;
+  __shared__ float se[4 * PC];
+  const int n0 = F.n0, n1 = F.n1, n2 = F.n2;
+  const int ntx = (n0 + kLrTX - 1) / kLrTX, nty = (n1 + kLrTY - 1) / kLrTY;
+  int b = blockIdx.x;
+  const int X0 = (b % ntx) * kLrTX;
+  b /= ntx;
+  const int Y0 = (b % nty) * kLrTY;
+  b /= nty;
+  const int K0 = b * kc, K1 = min(K0 + kc, C.n2);
+  const long long plane = (long long)n0 * n1;
+  auto wrapm = [](int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+  };
+  int roff[NLD];
+  bool lok[NLD];
+#pragma unroll
+  for (int k = 0; k < NLD; k++) {
+    const int q = threadIdx.x + k * NT;
+    roff[k] = 0;
+    lok[k] = false;
+    if (q < PC) {
+      const int gx = X0 - 1 + q % LX, gy = Y0 - 1 + q / LX;
+      if (PATCH) {
+        lok[k] = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
+        roff[k] = lok[k] ? gy * n0 + gx : 0;
+      } else {
+        lok[k] = true;
+        roff[k] = wrapm(gy, n1) * n0 + wrapm(gx, n0);
+      }
+    }
+  }
+  float pv[2][NLD];
+  // fine plane z (may lie outside a patch: never read then) into registers
+  auto fetch = [&](int r, int z) {
+    const bool vz = !PATCH || (z >= 0 && z < n2);
+    const long long zo = (long long)(PATCH ? z : wrapm(z, n2)) * plane;
+#pragma unroll
+    for (int k = 0; k < NLD; k++) pv[r][k] = (vz && lok[k]) ? F.e[zo + roff[k]] : 0.0f;
+  };
+  auto commit = [&](int r, int slot) {
+#pragma unroll
+    for (int k = 0; k < NLD; k++) {
+      const int q = threadIdx.x + k * NT;
+      if (q < PC) se[slot * PC + q] = pv[r][k];
+    }
+  };
+  // this thread's coarse cell of the tile
+  const int cx = threadIdx.x & 31, cy = threadIdx.x >> 5;
+  const int I = X0 / 2 + cx, J = Y0 / 2 + cy;
+  const bool own = 2 * I < n0 && 2 * J < n1;
+  float ss = 0.0f, mx = 0.0f;
+  // planes 2K0-1 .. 2K0+2 into slots 0..3 (slot of fine plane z: (z - 2K0 + 1) & 3)
+  fetch(0, 2 * K0 - 1);
+  fetch(1, 2 * K0);
+  commit(0, 0);
+  commit(1, 1);
+  fetch(0, 2 * K0 + 1);
+  fetch(1, 2 * K0 + 2);
+  commit(0, 2);
+  commit(1, 3);
+  __syncthreads();
+  for (int K = K0; K < K1; K++) {
+    const bool more = K + 1 < K1;
+    if (more) {
+      fetch(0, 2 * K + 3);
+      fetch(1, 2 * K + 4);
+    }
+    if (own) {
+      float sd = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
+        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+        const int lx = 1 + 2 * cx + dx, ly = 1 + 2 * cy + dy;
+        const int sm = ((k - 1 - 2 * K0 + 1) & 3) * PC, sc = ((k - 2 * K0 + 1) & 3) * PC,
+                  sp = ((k + 1 - 2 * K0 + 1) & 3) * PC;
+        const int o = ly * LX + lx;
+        float s = 0.0f;
+        int nm = 0;
+        if (PATCH) {
+          if (i > 0) s += se[sc + o - 1]; else nm++;
+          if (i < n0 - 1) s += se[sc + o + 1]; else nm++;
+          if (j > 0) s += se[sc + o - LX]; else nm++;
+          if (j < n1 - 1) s += se[sc + o + LX]; else nm++;
+          if (k > 0) s += se[sm + o]; else nm++;
+          if (k < n2 - 1) s += se[sp + o]; else nm++;
+        } else {
+          s += se[sc + o - 1];
+          s += se[sc + o + 1];
+          s += se[sc + o - LX];
+          s += se[sc + o + LX];
+          s += se[sm + o];
+          s += se[sp + o];
+        }
+        const long long c = (long long)k * plane + (long long)j * n0 + i;
+        const float d = F.f[c] - (s - (6.0f + (float)nm) * se[sc + o]) / F.h2;
+        sd += d;
+        ss = fmaf(d, d, ss);
+        mx = fmaxf(mx, fabsf(d));
+      }
+      const long long t = ((long long)K * C.n1 + J) * C.n0 + I;
+      C.f[t] = 0.125f * sd;
+      C.e[t] = 0.0f;
+    }
+    __syncthreads();
+    if (more) {
+      commit(0, (2 * K + 3 - 2 * K0 + 1) & 3);
+      commit(1, (2 * K + 4 - 2 * K0 + 1) & 3);
+    }
+    __syncthreads();
+  }
+  if (partial) {
+    for (int o = 16; o > 0; o >>= 1) {
+      ss += __shfl_down_sync(0xffffffffu, ss, o);
+      mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    __shared__ float a[NT / 32], bm[NT / 32];
+    if ((threadIdx.x & 31) == 0) {
+      a[threadIdx.x >> 5] = ss;
+      bm[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s2 = 0.0;
+      float m2 = 0.0f;
+      for (int w = 0; w < NT / 32; w++) {
+        s2 += (double)a[w];
+        m2 = fmaxf(m2, bm[w]);
+      }
+      partial[2 * blockIdx.x] = s2;
+      partial[2 * blockIdx.x + 1] = (double)m2;
+    }
+  }
+}
+
 // e^h += P e^H: trilinear, per axis 3/4 on the containing coarse cell and 1/4
 // on the neighbour on the child's side (products: 27/9/3/1 over 64).
 __global__ void __launch_bounds__(kNT) k_lprolong(PLevel F, PLevel C) {
@@ -815,6 +965,7 @@ struct PoissonSolver {
   std::vector<int> zc, nblk_t;  // tiled smoother: z-chunk and blocks per level (0: not tiled)
   std::vector<int> kc_p, nblk_p;  // tiled prolongation onto a level: coarse planes per block
                                   // and blocks (0: one thread per fine cell)
+  std::vector<int> kc_r, nblk_r;  // tiled residual + restriction from a level (same layout)
 
   void smooth(int l, int n) {
     for (int it = 0; it < n; it++) {
@@ -841,8 +992,16 @@ struct PoissonSolver {
       return;
     }
     smooth(l, pre);
-    k_lresid_restrict<<<nblk(lev[l + 1].ncell), kNT, 0, st>>>(lev[l], lev[l + 1],
-                                                             l == 0 ? partial0 : nullptr);
+    double *part = l == 0 ? partial0 : nullptr;
+    if (nblk_r[l] > 0) {
+      if (lev[l].patch)
+        k_lresid_restrict_tiled<true><<<nblk_r[l], 256, 0, st>>>(lev[l], lev[l + 1], kc_r[l], part);
+      else
+        k_lresid_restrict_tiled<false><<<nblk_r[l], 256, 0, st>>>(lev[l], lev[l + 1], kc_r[l],
+                                                                  part);
+    } else {
+      k_lresid_restrict<<<nblk(lev[l + 1].ncell), kNT, 0, st>>>(lev[l], lev[l + 1], part);
+    }
     PLAUNCH(ctx);
     vcycle(l + 1, nullptr);
     if (nblk_p[l] > 0) {
@@ -926,7 +1085,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
     }
     split_host(1.0 / (h * h), P.ih2h, P.ih2l);
     // multigrid levels of the correction equation
-    PoissonSolver S{ctx, st, {}, o.pre, o.post, {}, {}, {}, {}};
+    PoissonSolver S{ctx, st, {}, o.pre, o.post, {}, {}, {}, {}, {}, {}};
     {
       const int nl = level_count(dims);
       int m[3] = {dims[0], dims[1], dims[2]};
@@ -1001,6 +1160,10 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
         }
         S.kc_p.push_back(kcp);
         S.nblk_p.push_back(nbp);
+        // the residual + restriction from this level uses the same tiles and
+        // coarse-plane chunks (blocks of 256 threads, one per coarse cell)
+        S.kc_r.push_back(kcp);
+        S.nblk_r.push_back(nbp);
         S.lev.push_back(L);
         for (int d = 0; d < 3; d++) m[d] /= 2;
         hl *= 2.0;
@@ -1033,7 +1196,11 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
     };
     double prev = HUGE_VAL;
     int status = FR_ENOCONV;
-    double *partial0 = A.get<double>(2 * nblk(S.lev.size() > 1 ? S.lev[1].ncell : 1));
+    // fine-level norm partials of the residual + restriction (one per block)
+    const long long nbc = S.lev.size() > 1
+                              ? (S.nblk_r[0] > 0 ? (long long)S.nblk_r[0] : nblk(S.lev[1].ncell))
+                              : 0;
+    double *partial0 = A.get<double>(2 * std::max<long long>(nbc, 1));
     for (int outer = 0; outer < o.max_outer; outer++) {
       k_pdefect<<<nb, kNT, 0, st>>>(P, smh, sml, S.lev[0].f, S.lev[0].e, partial, nullptr);
       PLAUNCH(ctx);
@@ -1056,7 +1223,6 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
       // FP32 correction solve: stop near the FP32 floor (1e-5 of its start)
       // or when the cycle contraction stalls
       double rp = HUGE_VAL;
-      const long long nbc = S.lev.size() > 1 ? nblk(S.lev[1].ncell) : 0;
       for (int k = 0; k < o.max_vcycles; k++) {
         if (S.lev.size() == 1) {
           k_lcoarsest<<<1, kNT, 0, st>>>(S.lev[0], 500);
