@@ -64,3 +64,31 @@ def test_constants_without_gpu(lib):
     assert ct == pytest.approx(PF.ctilde(256.0), rel=1e-14)
     with pytest.raises(frmg.FRError):
         frmg.constants(-1.0, 32, 1.0, 0.24, 1e-5)
+
+
+def test_options_struct_matches_the_header(lib):
+    """fr_opts_default through the binding's struct: every documented default
+    lands in its field (a layout mismatch would scramble them), and the struct
+    fields follow the header's member order."""
+    from paper_1110_1379_gb300 import frmg
+    o = frmg.Context.opts()
+    assert (o.tol, o.max_vcycles, o.pre, o.post, o.prec) == (1e-8, 100, 2, 2, frmg.FR_FP64)
+    assert (o.newton_step_cap, o.inner_cycles, o.max_outer) == (1.0, 2, 40)
+    assert (o.allow_negative_density, o.use_graph, o.temporal_depth, o.tiling) == (0, 1, 0, 0)
+    assert (o.defect_precision, o.tau_alpha, o.relax, o.fmg, o.initial_guess) == (0, 0.0, 1.0, 0, 1)
+    src = open(os.path.join(ROOT, "include", "frmg.h")).read()
+    body = src[src.index("typedef struct {\n    double tol;"):src.index("} fr_opts;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    members = re.findall(r"\b(?:double|int|fr_precision)\s+([a-z_0-9, ]+);", body)
+    names = [m.strip() for grp in members for m in grp.split(",")]
+    assert names == [f for f, _ in frmg.fr_opts._fields_]
+
+
+def test_stats_struct_matches_the_header():
+    from paper_1110_1379_gb300 import frmg
+    src = open(os.path.join(ROOT, "include", "frmg.h")).read()
+    body = src[src.index("typedef struct {\n    int vcycles;"):src.index("} fr_stats;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b(?:double|int)\s+([a-z_0-9]+)(?:\[[A-Z_]+\])?;", body)
+    assert names == [f for f, _ in frmg.fr_stats._fields_]
+    assert frmg.FR_HIST == int(re.search(r"#define FR_HIST (\d+)", src).group(1))
