@@ -116,11 +116,13 @@ def test_small_nested_patches_match_oracle(C, prec, relax):
         assert np.abs(host(g["u"]) - r.u).max() <= 1e-6
 
 
-@pytest.mark.parametrize("tiling", [-1, 1])
-def test_tiled_patch_levels_match_oracle(C, tiling):
+@pytest.mark.parametrize("tiling,fmg", [(-1, 0), (1, 0), (1, 1)])
+def test_tiled_patch_levels_match_oracle(C, tiling, fmg):
     """Patches of 32^3 (coarse patch levels of 16^3, tiled with tiling=1: the
     tiled smoother, residual+restriction, prolongation and FAS right-hand side
-    on Dirichlet grids) against the one-thread-per-cell kernels and the oracle."""
+    on Dirichlet grids) against the one-thread-per-cell kernels and the oracle;
+    fmg=1 starts the domain solve by full multigrid (the patch starts from the
+    interpolated parent solution, so it keeps its V-cycles)."""
     P = dict(box=64.0, a=1.0, fr0=1e-5)
     rho0, patches = _levels_case(32, P, [32], 2, [], 0, 720)
     assert len(patches) >= 1 and all(p["rho"].shape == (32, 32, 32) for p in patches)
@@ -131,7 +133,7 @@ def test_tiled_patch_levels_match_oracle(C, tiling):
                u=torch.zeros(p["rho"].shape, dtype=torch.float64, device="cuda"))
           for p in patches]
     st, stats = C.solve_levels(dev(rho0), u0, gp, tol=1e-8, omega_m=OM, prec="mixed",
-                               tiling=tiling, **P)
+                               tiling=tiling, fmg=fmg, **P)
     assert st == 0
     assert np.abs(host(u0) - dom.u).max() <= 1e-6
     for g, r in zip(gp, pres):
