@@ -1,0 +1,154 @@
+"""Pins of the masked-region oracle (general mask scheme, Sec. V, V.A.1, V.B.1,
+V.B.2, V.A.3) to things other than itself: the independently written patch and
+periodic operators of the C oracle in the two special cases the paper names,
+a finite-difference derivative, the homogeneous solution, brute-force Newton
+on a small irregular region, and second-order convergence to the closed-form
+spherical Gaussian (Sec. VI.B.1's field) on a spherical region."""
+import numpy as np
+import pytest
+
+import paper_fields as PF
+from oracle import masked as M
+from oracle import oracle as O
+
+P = dict(box=128.0, a=0.9, omega_m=0.24, fr0=1e-5)
+
+
+def _box_mask(shape):
+    m = -np.ones(shape)
+    m[1:-1, 1:-1, 1:-1] = 1.0
+    return m
+
+
+def _faces(u):
+    """Packed u_b = (ghost + first interior)/2 of the interior block of u."""
+    mid = lambda a, b: 0.5 * (a + b)
+    I = (slice(1, -1),) * 3
+    fx0 = mid(u[1:-1, 1:-1, 0], u[1:-1, 1:-1, 1])
+    fx1 = mid(u[1:-1, 1:-1, -1], u[1:-1, 1:-1, -2])
+    fy0 = mid(u[1:-1, 0, 1:-1], u[1:-1, 1, 1:-1])
+    fy1 = mid(u[1:-1, -1, 1:-1], u[1:-1, -2, 1:-1])
+    fz0 = mid(u[0, 1:-1, 1:-1], u[1, 1:-1, 1:-1])
+    fz1 = mid(u[-1, 1:-1, 1:-1], u[-2, 1:-1, 1:-1])
+    assert u[I].shape[0] == fx0.shape[0]
+    return np.concatenate([f.ravel() for f in (fx0, fx1, fy0, fy1, fz0, fz1)])
+
+
+def _irregular_mask(shape, seed, frac=0.6):
+    rng = np.random.default_rng(seed)
+    m = rng.uniform(-1.0, 1.0, shape)
+    m = np.where(rng.uniform(size=shape) < frac, np.abs(m) + 0.05, -np.abs(m))
+    m = np.clip(m, -1.0, 1.0)
+    m[0], m[-1], m[:, 0], m[:, -1], m[:, :, 0], m[:, :, -1] = -1, -1, -1, -1, -1, -1
+    return m
+
+
+def test_box_mask_is_the_patch_operator():
+    """Masks +1 inside, -1 on the outer layer: r = -1 on every ghost face and
+    u_b = (u_g + u_i)/2, which is the refinement-patch operator (Eq.
+    bc_modified_fR_op with r = -1) of the C oracle."""
+    shape = (10, 12, 14)
+    rng = np.random.default_rng(1)
+    u = rng.uniform(-1.0, 0.5, shape)
+    rho = np.exp(rng.normal(0, 0.7, shape))
+    h = 1.0 / 64
+    Lm, dLm = M.operator(u, _box_mask(shape), rho, h=h, **P)
+    I = (slice(1, -1),) * 3
+    ref = O.residual(u[I], rho[I], h=h, ub=_faces(u), **P)
+    assert np.abs(Lm[I] - ref).max() <= 1e-10 * np.abs(ref).max()
+    # derivative against the C oracle's cell by cell
+    for (k, j, i) in [(0, 0, 0), (3, 4, 5), (7, 9, 11), (0, 5, 11)]:
+        _, dref = O.cell_op(u[I], rho[I], i, j, k, h=h, ub=_faces(u), **P)
+        assert dLm[1 + k, 1 + j, 1 + i] == pytest.approx(dref, rel=1e-12)
+
+
+def test_zero_ghost_mask_is_the_unmodified_operator():
+    """Ghost masks 0: r = 0 and u_b = u_g, so the equation reduces to the
+    regular grid's (the paper's remark after Eq. bc_modified_fR_dop): the C
+    oracle's periodic operator on the whole box agrees at every active cell."""
+    shape = (8, 10, 12)
+    rng = np.random.default_rng(2)
+    u = rng.uniform(-1.0, 0.5, shape)
+    rho = np.exp(rng.normal(0, 0.7, shape))
+    m = np.zeros(shape)
+    m[1:-1, 1:-1, 1:-1] = rng.uniform(0.1, 1.0, (6, 8, 10))
+    h = 1.0 / 32
+    Lm, _ = M.operator(u, m, rho, h=h, **P)
+    ref = O.residual(u, rho, h=h, **P)
+    I = (slice(1, -1),) * 3
+    assert np.abs(Lm[I] - ref[I]).max() <= 1e-10 * np.abs(ref[I]).max()
+
+
+def test_derivative_matches_finite_differences_for_any_ratio():
+    """Eq. bc_modified_fR_dop with general r = m_g/m_i: central differences of
+    L_i in u_i (u_b fixed by the initial values)."""
+    shape = (8, 8, 8)
+    rng = np.random.default_rng(3)
+    m = _irregular_mask(shape, 4)
+    u0 = rng.uniform(-1.0, 0.5, shape)
+    rho = np.exp(rng.normal(0, 0.7, shape))
+    h = 1.0 / 32
+    _, dL = M.operator(u0, m, rho, h=h, **P)
+    act = np.argwhere(m > 0)
+    assert len(act) > 20
+    eps = 1e-6
+    for k, j, i in act[:: max(1, len(act) // 25)]:
+        up, um = u0.copy(), u0.copy()
+        up[k, j, i] += eps
+        um[k, j, i] -= eps
+        Lp, _ = M.operator(up, m, rho, h=h, u_init=u0, **P)
+        Lmn, _ = M.operator(um, m, rho, h=h, u_init=u0, **P)
+        fd = (Lp[k, j, i] - Lmn[k, j, i]) / (2 * eps)
+        assert dL[k, j, i] == pytest.approx(fd, rel=1e-6, abs=1e-6 * abs(fd) + 1e-3)
+
+
+def test_homogeneous_state_is_exact_for_any_mask():
+    shape = (10, 10, 10)
+    m = _irregular_mask(shape, 5)
+    u = np.zeros(shape)
+    rho = np.ones(shape)
+    Lm, _ = M.operator(u, m, rho, h=1.0 / 40, **P)
+    _, beta, gamma = PF.coefficients(P["box"], 40, P["a"], P["omega_m"], P["fr0"])
+    assert np.abs(Lm).max() <= 1e-12 * (beta + gamma)
+
+
+def test_multigrid_equals_brute_force_newton():
+    """FAS V-cycles with masked levels reach the solution of dense Newton on the
+    active cells of an irregular region (mask values in (-1, 1), several
+    ghost ratios)."""
+    shape = (16, 16, 16)
+    rng = np.random.default_rng(6)
+    k, j, i = np.indices(shape)
+    r2 = ((i - 7.5) ** 2 + (j - 7.5) ** 2 + (k - 7.5) ** 2) / 25.0
+    blob = np.exp(-r2) + 0.3 * rng.uniform(-1, 1, shape)
+    m = np.clip(2.0 * blob - 0.4, -1.0, 1.0)
+    m[[0, -1]], m[:, [0, -1]], m[:, :, [0, -1]] = -1.0, -1.0, -1.0
+    assert (m > 0).sum() > 100 and M.num_levels(m) >= 2
+    u0 = 0.2 * np.sin(0.4 * i) * np.cos(0.3 * j) + 0.1 * np.cos(0.5 * k)
+    rho = np.exp(rng.normal(0, 0.5, shape))
+    h = 1.0 / 64
+    res = M.solve(u0, m, rho, h=h, tol=1e-11, **P)
+    assert res.converged and res.cycles >= 2
+    ref = M.dense_newton(u0, m, rho, h=h, **P)
+    act = m > 0
+    assert np.abs(res.u[act] - ref[act]).max() < 1e-9
+    assert np.abs(res.u[~act] - u0[~act]).max() < 1e-14  # ghost values are never changed
+
+
+def test_spherical_region_converges_at_second_order():
+    """Sec. VI.B.1's spherical Gaussian (3D analogue of Eq. gaussian_dens) on a
+    spherical active region whose ghosts hold the closed form: the error at the
+    active cells falls about fourfold when h halves."""
+    G = dict(amp=0.9, width=0.08, centre=(0.5, 0.5, 0.5))
+    errs = []
+    for N, nb in ((64, 24), (128, 48)):
+        lo = N // 2 - nb // 2
+        rho, ue = PF.spherical_gaussian_patch(lo, nb, N, **P, **G)
+        x = (np.arange(lo, lo + nb) + 0.5) / N
+        z, y, xx = np.meshgrid(x, x, x, indexing="ij")
+        rr = np.sqrt((xx - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
+        m = np.where(rr < 0.15, 1.0, -1.0)
+        res = M.solve(ue, m, rho, h=1.0 / N, tol=1e-10, **P)
+        assert res.converged
+        errs.append(np.abs(res.u - ue)[m > 0].max())
+    assert errs[0] / errs[1] > 3.0
