@@ -346,6 +346,40 @@ int fr_poisson_source(frmg_ctx *ctx, const double *density, const double *u, con
                       double box_mpc_h, double a, double omega_m, double fr0_abs,
                       double *s_out, void *stream);
 
+/*
+ * General mask scheme (Sec. V; Eqs. u_i-1jk, bc_modified_fR_op and
+ * bc_modified_fR_dop of Sec. V.B.1; the masked multigrid of Sec. V.B.2,
+ * V.A.2 and V.A.3): FAS solve of the f(R) equation on a refinement region of
+ * any shape.  The region is a box of dims = (n0, n1, n2) cells of size h (code
+ * units, box side 1) with a mask value per cell in [-1, 1]: cells with
+ * mask > 0 are active and relaxed, the others are ghosts whose values stay
+ * fixed; every cell of the box's outer layer must be a ghost (FR_EINVAL
+ * otherwise).  density: rho~ on every cell; mask: [n2][n1][n0]; u_inout: in,
+ * the initial values of the active cells and the ghost values (interpolated
+ * from the parent level in an AMR code), out, the solution on the active
+ * cells (ghost values unchanged).  Host or device pointers.
+ * Across a face from an active cell i to a ghost g the ghost enters as
+ * u_g = u_b - r u_b + r u_i with r = m_g / m_i and b_g = exp(u_g); u_b is
+ * fixed from the initial values, u_b = (m_i u_g - m_g u_i) / (m_i - m_g).
+ * Coarser levels: masks, densities and initial values restricted as the mean
+ * of the 8 children, active where the coarse mask is > 0; R d^h sums the
+ * active children only; the correction reaches active fine cells only and a
+ * masked coarse cell contributes nothing to it.  Levels halve while the sizes
+ * stay even and >= 4, the coarser level's outer layer stays masked and it
+ * keeps an active cell.  The paper's masks are +1 (active) and -1 on the
+ * finest level; a small positive mask puts the boundary close to the cell
+ * centre and makes |r| large (the ghost then amplifies changes of u_i by |r|).
+ * FP64 arithmetic (opts->prec is not used); V(pre,post)
+ * red-black Newton-Gauss-Seidel (opts->pre, post, newton_step_cap, relax),
+ * until the rms of L(u) over the active cells is <= tol (FR_OK) or
+ * opts->max_vcycles V-cycles (FR_ENOCONV).  stats: vcycles, res0_rms,
+ * res_rms, res_max, seconds, hist.  Synchronous on return.
+ */
+int fr_solve_masked(frmg_ctx *ctx, const double *density, const double *mask, const int dims[3],
+                    double h, double box_mpc_h, double a, double omega_m, double fr0_abs,
+                    double tol, double *u_inout, const fr_opts *opts, fr_stats *stats,
+                    void *stream);
+
 /* Number of kernel launches this context issued since it was created. */
 long long fr_launch_count(const frmg_ctx *ctx);
 

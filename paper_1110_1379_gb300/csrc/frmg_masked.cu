@@ -1,0 +1,548 @@
+// frmg_masked.cu -- the general mask scheme: FAS solve of the f(R) equation on
+// a refinement region of any shape.
+//
+// Sec. V (the mask scheme), Sec. V.B.1 (Eqs. u_i-1jk, bc_modified_fR_op,
+// bc_modified_fR_dop), Sec. V.B.2 (FAS with masked restriction, coarse masks
+// and boundary values), Sec. V.A.2 (masked restriction of the residual) and
+// Sec. V.A.3 (masked prolongation).  A region is a box of cells with a mask m
+// in [-1, 1] per cell: m > 0 marks an active cell (relaxed), the others are
+// ghosts whose values stay fixed; the box's outer layer must be ghosts.
+//
+// * Across the face from an active cell i to a ghost g, with r = m_g / m_i,
+//   the ghost enters as u_g = u_b - r u_b + r u_i, b_g = exp(u_g), where the
+//   boundary value u_b = (m_i u_g0 - m_g u_i0) / (m_i - m_g) is computed from
+//   the initial values once and kept (six per cell, NaN where no ghost face).
+// * L_i = (alpha/2) sum_faces (e^{u_i} + e^{u_j})(u_j - u_i)
+//         + beta (e^{-u_i/2} - 1) - gamma (rho_i - 1),
+//   in the solver's variable u = u~ - ubar (alpha = c~^2 |fbar~_R| / h^2);
+//   with the ghost faces above this is Eq. bc_modified_fR_op, and its
+//   derivative in u_i is Eq. bc_modified_fR_dop.
+// * Levels: masks, densities and initial values restrict as the mean of the
+//   8 children, a coarse cell is active when its mask is > 0, and its ghost
+//   boundary values follow from the restricted initial values as on the
+//   finest level.  R u^h is the mean of all 8 children (for active coarse
+//   cells only), R d^h the sum over the active children / 8; the correction
+//   u^H - R u^h is prolonged (trilinear 27/9/3/1) onto active fine cells, a
+//   masked coarse cell contributing 0.  Levels halve while the sizes stay even
+//   and >= 4, the next level's outer layer stays masked and it keeps an
+//   active cell.
+//
+// FP64 throughout (one thread per cell), red-black Newton-Gauss-Seidel with
+// the step clamped to |du| <= cap and optionally over-relaxed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "frmg.h"
+#include "frmg_dfmath.cuh"
+#include "frmg_internal.h"
+
+using namespace frmg;
+
+namespace {
+
+struct MError {
+  int status;
+  std::string msg;
+};
+
+#define MCK(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw MError{FR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};       \
+  } while (0)
+
+#define MLAUNCH(ctx)                                                                    \
+  do {                                                                                  \
+    frmg_launch_counter(ctx)++;                                                         \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess)                                                              \
+      throw MError{FR_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)};  \
+  } while (0)
+
+constexpr int kNT = 256;
+
+long long nblk(long long n) { return (n + kNT - 1) / kNT; }
+
+// One level of a masked region.
+struct MLevel {
+  double *u;        // iterate in active cells, fixed ghost values elsewhere
+  const double *m;  // mask
+  const double *rho;
+  double *f;        // FAS right-hand side (0 on the finest level)
+  double *uR;       // R u^h of the active cells (coarse levels)
+  double *d;        // residual (fine side) or R d^h (coarse side)
+  double *ub;       // [6][ncell] boundary values of the ghost faces (NaN elsewhere)
+  int n0, n1, n2;
+  long long ncell;
+  FastDiv fd0, fd1;
+  double ah;        // alpha / 2 at this level's h
+  double beta, gamma;
+};
+
+__device__ __forceinline__ void ijk(const MLevel &L, long long c, int &i, int &j, int &k) {
+  const unsigned cu = (unsigned)c, q = fdiv(cu, L.fd0), q2 = fdiv(q, L.fd1);
+  i = (int)(cu - q * (unsigned)L.n0);
+  j = (int)(q - q2 * (unsigned)L.n1);
+  k = (int)q2;
+}
+
+// neighbour offset of face f (-x, +x, -y, +y, -z, +z)
+__device__ __forceinline__ long long face_step(const MLevel &L, int f) {
+  const long long s = f < 2 ? 1 : (f < 4 ? (long long)L.n0 : (long long)L.n0 * L.n1);
+  return (f & 1) ? s : -s;
+}
+
+// L_i and dL_i/du_i at active cell c (Eqs. bc_modified_fR_op / _dop)
+__device__ __forceinline__ void m_cell(const MLevel &L, long long c, double &N, double &dN) {
+  const double ui = L.u[c], mi = L.m[c];
+  const double bi = exp(ui);
+  double acc = 0.0, dacc = 0.0;
+#pragma unroll
+  for (int f = 0; f < 6; f++) {
+    const long long cj = c + face_step(L, f);
+    const double mj = L.m[cj];
+    if (mj > 0.0) {
+      const double uj = L.u[cj], bj = exp(uj);
+      acc += (bi + bj) * (uj - ui);
+      dacc += bi * (uj - ui) - (bi + bj);
+    } else {
+      const double r = mj / mi, ub = L.ub[f * L.ncell + c];
+      const double ug = ub - r * ub + r * ui, bg = exp(ug);
+      acc += (bi + bg) * (ug - ui);
+      dacc += (bi + r * bg) * (ug - ui) + (bi + bg) * (r - 1.0);
+    }
+  }
+  const double s = exp(-0.5 * ui);
+  N = L.ah * acc + L.beta * (s - 1.0) - L.gamma * (L.rho[c] - 1.0);
+  dN = L.ah * dacc - 0.5 * L.beta * s;
+}
+
+}  // namespace
+
+namespace {
+
+// Boundary values of the ghost faces from the current (initial) values.
+__global__ void __launch_bounds__(kNT) k_mub(MLevel L) {
+  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (c >= L.ncell) return;
+  const double mi = L.m[c], ui = L.u[c];
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+  for (int f = 0; f < 6; f++) {
+    double v = nan;
+    if (mi > 0.0) {
+      const long long cj = c + face_step(L, f);
+      const double mg = L.m[cj];
+      if (mg <= 0.0) v = (mi * L.u[cj] - mg * ui) / (mi - mg);
+    }
+    L.ub[f * L.ncell + c] = v;
+  }
+}
+
+// One colour of a red-black Newton-Gauss-Seidel sweep over the active cells
+// (one thread per cell pair along x; the colour's cell of the pair).
+__global__ void __launch_bounds__(kNT) k_msmooth(MLevel L, int colour, double cap, double relax) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (2 * t >= L.ncell) return;
+  int i, j, k;
+  ijk(L, 2 * t, i, j, k);
+  i += (i + j + k + colour) & 1;
+  const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
+  if (!(L.m[c] > 0.0)) return;
+  double N, dN;
+  m_cell(L, c, N, dN);
+  double du = -relax * (N - L.f[c]) / dN;
+  du = du > cap ? cap : (du < -cap ? -cap : du);
+  L.u[c] += du;
+}
+
+// d = L(u) - f on active cells (0 on ghosts); per-block partials
+// (sum d^2, max |d|).
+__global__ void __launch_bounds__(kNT) k_mresid(MLevel L, double *partial) {
+  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  double s = 0.0, mx = 0.0;
+  if (c < L.ncell) {
+    double d = 0.0;
+    if (L.m[c] > 0.0) {
+      double N, dN;
+      m_cell(L, c, N, dN);
+      d = N - L.f[c];
+    }
+    L.d[c] = d;
+    s = d * d;
+    mx = fabs(d);
+  }
+  __shared__ double ss[kNT / 32], sm[kNT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ss[threadIdx.x >> 5] = s;
+    sm[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kNT / 32; w++) {
+      a += ss[w];
+      b = fmax(b, sm[w]);
+    }
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// Setup of a coarser level: mean of the 8 children of the mask, the density
+// and the (initial) values.
+__global__ void __launch_bounds__(kNT) k_minit(MLevel F, MLevel C) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= C.ncell) return;
+  int I, J, K;
+  ijk(C, t, I, J, K);
+  double sm = 0.0, sr = 0.0, su = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const long long c = ((long long)(2 * K + (q >> 2)) * F.n1 + 2 * J + ((q >> 1) & 1)) * F.n0 +
+                        2 * I + (q & 1);
+    sm += F.m[c];
+    sr += F.rho[c];
+    su += F.u[c];
+  }
+  const_cast<double *>(C.m)[t] = 0.125 * sm;
+  const_cast<double *>(C.rho)[t] = 0.125 * sr;
+  C.u[t] = 0.125 * su;
+}
+
+// FAS restriction onto the active coarse cells: u^H = R u^h (all children),
+// R d^h = sum over the active children / 8; ghosts keep their values.
+__global__ void __launch_bounds__(kNT) k_mrestrict(MLevel F, MLevel C) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= C.ncell) return;
+  if (!(C.m[t] > 0.0)) return;
+  int I, J, K;
+  ijk(C, t, I, J, K);
+  double su = 0.0, sd = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const long long c = ((long long)(2 * K + (q >> 2)) * F.n1 + 2 * J + ((q >> 1) & 1)) * F.n0 +
+                        2 * I + (q & 1);
+    su += F.u[c];
+    if (F.m[c] > 0.0) sd += F.d[c];
+  }
+  C.uR[t] = 0.125 * su;
+  C.u[t] = 0.125 * su;
+  C.d[t] = 0.125 * sd;
+}
+
+// f^H = L^H(R u^h) - R d^h on the active coarse cells (after k_mrestrict).
+__global__ void __launch_bounds__(kNT) k_mfas(MLevel C) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= C.ncell) return;
+  if (!(C.m[t] > 0.0)) {
+    C.f[t] = 0.0;
+    return;
+  }
+  double N, dN;
+  m_cell(C, t, N, dN);
+  C.f[t] = N - C.d[t];
+}
+
+// u^h += P e^H on the active fine cells, e^H = u^H - R u^h on active coarse
+// cells and 0 on masked ones and outside the box (trilinear 27/9/3/1).
+__global__ void __launch_bounds__(kNT) k_mprolong(MLevel F, MLevel C) {
+  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (c >= F.ncell) return;
+  if (!(F.m[c] > 0.0)) return;
+  int i, j, k;
+  ijk(F, c, i, j, k);
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  const int di = (i & 1) ? 1 : -1, dj = (j & 1) ? 1 : -1, dk = (k & 1) ? 1 : -1;
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int ii = I + ((q & 1) ? di : 0), jj = J + (((q >> 1) & 1) ? dj : 0),
+              kk = K + ((q >> 2) ? dk : 0);
+    if (ii < 0 || ii >= C.n0 || jj < 0 || jj >= C.n1 || kk < 0 || kk >= C.n2) continue;
+    const long long cc = ((long long)kk * C.n1 + jj) * C.n0 + ii;
+    if (!(C.m[cc] > 0.0)) continue;
+    const double w = ((q & 1) ? 0.25 : 0.75) * (((q >> 1) & 1) ? 0.25 : 0.75) *
+                     ((q >> 2) ? 0.25 : 0.75);
+    acc += w * (C.u[cc] - C.uR[cc]);
+  }
+  F.u[c] += acc;
+}
+
+// Flags of a level's mask: [0] an outer-layer cell is active, [1] number of
+// active cells.
+__global__ void __launch_bounds__(kNT) k_mflags(MLevel L, unsigned long long *flags) {
+  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (c >= L.ncell) return;
+  if (!(L.m[c] > 0.0)) return;
+  int i, j, k;
+  ijk(L, c, i, j, k);
+  if (i == 0 || j == 0 || k == 0 || i == L.n0 - 1 || j == L.n1 - 1 || k == L.n2 - 1)
+    atomicOr(&flags[0], 1ull);
+  atomicAdd(&flags[1], 1ull);
+}
+
+// Flags of the inputs: [0] a mask outside [-1, 1] or NaN, [1] a non-finite
+// value or density (or a negative density unless allowed).
+__global__ void __launch_bounds__(kNT) k_mcheck(const double *m, const double *rho,
+                                                const double *u, long long n, int allow_neg,
+                                                int *bad) {
+  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (c >= n) return;
+  const double mv = m[c], r = rho[c], uv = u[c];
+  if (!(mv >= -1.0 && mv <= 1.0)) atomicOr(&bad[0], 1);
+  if (!isfinite(r) || !isfinite(uv) || (!allow_neg && r < 0.0)) atomicOr(&bad[1], 1);
+}
+
+}  // namespace
+
+namespace {
+
+bool m_on_device(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct MArena {
+  frmg_ctx *c;
+  std::vector<void *> ptrs;
+  explicit MArena(frmg_ctx *c_) : c(c_) {}
+  template <typename T>
+  T *get(size_t n) {
+    void *p = nullptr;
+    try {
+      p = frmg_alloc(c, n * sizeof(T));
+    } catch (...) {
+      throw MError{FR_ENOMEM, "device allocation failed"};
+    }
+    ptrs.push_back(p);
+    return (T *)p;
+  }
+  ~MArena() {
+    for (void *p : ptrs) frmg_release(c, p);
+  }
+};
+
+struct MSolver {
+  frmg_ctx *ctx;
+  cudaStream_t st;
+  std::vector<MLevel> lev;
+  int pre, post;
+  double cap, relax, tol;
+  double *partial;  // per-block (sum d^2, max |d|) of the finest level
+  double *host;     // pinned staging of the partials
+  long long nact0;  // active cells of the finest level
+
+  void smooth(MLevel &L, int n) {
+    for (int s = 0; s < n; s++)
+      for (int colour = 0; colour < 2; colour++) {
+        k_msmooth<<<(unsigned)nblk((L.ncell + 1) / 2), kNT, 0, st>>>(L, colour, cap, relax);
+        MLAUNCH(ctx);
+      }
+  }
+  // rms over the active cells of level L (and its max |d|); host sync
+  double rms(MLevel &L, long long nact, double *dmax) {
+    const long long nb = nblk(L.ncell);
+    k_mresid<<<(unsigned)nb, kNT, 0, st>>>(L, partial);
+    MLAUNCH(ctx);
+    MCK(cudaMemcpyAsync(host, partial, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    double s = 0.0, mx = 0.0;
+    for (long long b = 0; b < nb; b++) {
+      s += host[2 * b];
+      mx = std::max(mx, host[2 * b + 1]);
+    }
+    if (dmax) *dmax = mx;
+    return std::sqrt(s / (double)std::max(nact, 1ll));
+  }
+  void coarsest(MLevel &L, long long nact) {
+    const double r0 = rms(L, nact, nullptr);
+    const double thr = std::max(1e-3 * r0, 0.1 * tol);
+    for (int it = 0; it < 500; it++) {
+      smooth(L, 1);
+      if (rms(L, nact, nullptr) <= thr) break;
+    }
+  }
+  std::vector<long long> nact;
+  void vcycle(int l) {
+    MLevel &L = lev[l];
+    if (l == (int)lev.size() - 1) {
+      coarsest(L, nact[l]);
+      return;
+    }
+    MLevel &C = lev[l + 1];
+    smooth(L, pre);
+    k_mresid<<<(unsigned)nblk(L.ncell), kNT, 0, st>>>(L, partial);
+    MLAUNCH(ctx);
+    k_mrestrict<<<(unsigned)nblk(C.ncell), kNT, 0, st>>>(L, C);
+    MLAUNCH(ctx);
+    k_mfas<<<(unsigned)nblk(C.ncell), kNT, 0, st>>>(C);
+    MLAUNCH(ctx);
+    vcycle(l + 1);
+    k_mprolong<<<(unsigned)nblk(L.ncell), kNT, 0, st>>>(L, C);
+    MLAUNCH(ctx);
+    smooth(L, post);
+  }
+};
+
+}  // namespace
+
+extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const double *mask,
+                               const int dims[3], double h, double box_mpc_h, double a,
+                               double omega_m, double fr0_abs, double tol, double *u_inout,
+                               const fr_opts *opts, fr_stats *stats, void *stream) {
+  MArena A(ctx);
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!ctx || !density || !mask || !dims || !u_inout) throw MError{FR_EINVAL, "NULL argument"};
+    for (int d = 0; d < 3; d++)
+      if (dims[d] < 3) throw MError{FR_EINVAL, "dims must be >= 3 (outer ghost layer)"};
+    const long long nc = (long long)dims[0] * dims[1] * dims[2];
+    if (nc >= (1ll << 31)) throw MError{FR_EINVAL, "region too large (at most 2^31 - 1 cells)"};
+    if (!(h > 0) || !(tol >= 0)) throw MError{FR_EINVAL, "h must be > 0 and tol >= 0"};
+    fr_opts o;
+    fr_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.pre < 0 || o.post < 0 || o.pre + o.post < 1 || o.max_vcycles < 0 ||
+        !(o.newton_step_cap > 0) || !(o.relax > 0 && o.relax < 2))
+      throw MError{FR_EINVAL, "invalid options"};
+    double k6[6];
+    if (fr_constants(box_mpc_h, 1, a, omega_m, fr0_abs, k6) != FR_OK)
+      throw MError{FR_EINVAL, "box, a and |f_R0| must be > 0 and 0 < Omega_m < 1"};
+    const double alpha = k6[0] / (h * h);  // alpha(h = 1) / h^2
+    // inputs on the device
+    auto stage_in = [&](const double *p) -> double * {
+      double *d = A.get<double>(nc);
+      MCK(cudaMemcpyAsync(d, p, nc * sizeof(double), m_on_device(p) ? cudaMemcpyDeviceToDevice
+                                                                  : cudaMemcpyHostToDevice,
+                          st));
+      return d;
+    };
+    const bool u_dev = m_on_device(u_inout);
+    double *du = stage_in(u_inout);
+    const double *drho = m_on_device(density) ? density : stage_in(density);
+    const double *dm = m_on_device(mask) ? mask : stage_in(mask);
+    int *bad = A.get<int>(2);
+    unsigned long long *flags = A.get<unsigned long long>(2);
+    int hb[2];
+    unsigned long long hf[2];
+    MCK(cudaMemsetAsync(bad, 0, 2 * sizeof(int), st));
+    k_mcheck<<<(unsigned)nblk(nc), kNT, 0, st>>>(dm, drho, du, nc, o.allow_negative_density, bad);
+    MLAUNCH(ctx);
+    MCK(cudaMemcpyAsync(hb, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    if (hb[0]) throw MError{FR_EINVAL, "mask values must lie in [-1, 1]"};
+    if (hb[1]) throw MError{FR_EINVAL, "non-finite (or negative) density, or non-finite u"};
+    // levels
+    MSolver S{ctx, st, {}, o.pre, o.post, o.newton_step_cap, o.relax, tol, nullptr, nullptr, 0, {}};
+    auto make = [&](int n0, int n1, int n2, double hl, double *u, const double *m,
+                    const double *rho) {
+      MLevel L;
+      L.n0 = n0;
+      L.n1 = n1;
+      L.n2 = n2;
+      L.ncell = (long long)n0 * n1 * n2;
+      L.fd0 = make_fastdiv((unsigned)n0);
+      L.fd1 = make_fastdiv((unsigned)n1);
+      L.u = u;
+      L.m = m;
+      L.rho = rho;
+      L.f = A.get<double>(L.ncell);
+      L.uR = A.get<double>(L.ncell);
+      L.d = A.get<double>(L.ncell);
+      L.ub = A.get<double>(6 * L.ncell);
+      L.ah = 0.5 * alpha * (h * h) / (hl * hl);
+      L.beta = k6[1];
+      L.gamma = k6[2];
+      MCK(cudaMemsetAsync(L.f, 0, L.ncell * sizeof(double), st));
+      return L;
+    };
+    auto level_flags = [&](MLevel &L) {
+      MCK(cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned long long), st));
+      k_mflags<<<(unsigned)nblk(L.ncell), kNT, 0, st>>>(L, flags);
+      MLAUNCH(ctx);
+      MCK(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
+      MCK(cudaStreamSynchronize(st));
+    };
+    S.lev.push_back(make(dims[0], dims[1], dims[2], h, du, dm, drho));
+    level_flags(S.lev[0]);
+    if (hf[0]) throw MError{FR_EINVAL, "the outer layer of a masked region must be masked"};
+    S.nact.push_back((long long)hf[1]);
+    S.nact0 = (long long)hf[1];
+    for (;;) {
+      const MLevel &F = S.lev.back();
+      if (F.n0 % 2 || F.n1 % 2 || F.n2 % 2 || F.n0 < 8 || F.n1 < 8 || F.n2 < 8) break;
+      const int c0 = F.n0 / 2, c1 = F.n1 / 2, c2 = F.n2 / 2;
+      const long long ncc = (long long)c0 * c1 * c2;
+      MLevel C = make(c0, c1, c2, h * (double)(1 << S.lev.size()), A.get<double>(ncc),
+                      A.get<double>(ncc), A.get<double>(ncc));
+      k_minit<<<(unsigned)nblk(ncc), kNT, 0, st>>>(F, C);
+      MLAUNCH(ctx);
+      level_flags(C);
+      if (hf[0] || hf[1] == 0) break;  // the level would not be a valid masked region
+      S.lev.push_back(C);
+      S.nact.push_back((long long)hf[1]);
+    }
+    for (auto &L : S.lev) {
+      k_mub<<<(unsigned)nblk(L.ncell), kNT, 0, st>>>(L);
+      MLAUNCH(ctx);
+    }
+    S.partial = A.get<double>(2 * nblk(nc));
+    double *pin = frmg_pinned(ctx, 2 * nblk(nc));
+    if (!pin) throw MError{FR_ENOMEM, "pinned host allocation failed"};
+    S.host = pin;
+    fr_stats sv;
+    memset(&sv, 0, sizeof(sv));
+    sv.tau_rms = std::nan("");
+    double dmax = 0.0;
+    double r = S.rms(S.lev[0], S.nact0, &dmax);
+    sv.res0_rms = r;
+    if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = r;
+    int status = FR_OK;
+    while (r > tol) {
+      if (sv.vcycles >= o.max_vcycles) {
+        status = FR_ENOCONV;
+        break;
+      }
+      S.vcycle(0);
+      sv.vcycles++;
+      r = S.rms(S.lev[0], S.nact0, &dmax);
+      if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = r;
+      if (!(r == r)) {
+        status = FR_EDIVERGED;
+        break;
+      }
+    }
+    sv.res_rms = r;
+    sv.res_max = dmax;
+    MCK(cudaMemcpyAsync(u_inout, du, nc * sizeof(double),
+                        u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    sv.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = sv;
+    if (status == FR_ENOCONV) frmg_set_error("no convergence within opts->max_vcycles");
+    if (status == FR_EDIVERGED) frmg_set_error("non-finite residual");
+    return status;
+  } catch (MError &e) {
+    frmg_set_error(e.msg);
+    if (st) cudaStreamSynchronize(st);
+    else cudaDeviceSynchronize();
+    return e.status;
+  }
+}

@@ -59,7 +59,7 @@ EXPORTS = ["fr_opts_default", "fr_status_string", "fr_last_error", "fr_ctx_creat
            "fr_cic_assign", "fr_smooth", "fr_residual", "fr_restrict", "fr_prolong_correct",
            "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32", "fr_residual_df",
            "fr_residual_norm_noalloc", "fr_autotune", "fr_poisson_solve", "fr_poisson_source",
-           "fr_tsc_assign", "fr_particle_forces"]
+           "fr_tsc_assign", "fr_particle_forces", "fr_solve_masked"]
 
 
 def lib_path():
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = False):
             "fr_poisson_source": (I, [P, P, P, P, D, D, D, D, P, P]),
             "fr_tsc_assign": (I, [P, P, L, P, P, P]),
             "fr_particle_forces": (I, [P, P, P, P, L, I, P, P]),
+            "fr_solve_masked": (I, [P, P, P, P, D, D, D, D, D, D, P, P, P, P]),
             "fr_profile_entry": (I, [P, I, P, I, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -252,6 +253,22 @@ class Context:
                                _stream(stream))
         if st in raise_on:
             self._raise(st, "fr_solve")
+        return st, s
+
+    def solve_masked(self, density, mask, u, *, h, box, a, omega_m, fr0, tol=1e-8, stream=None,
+                     raise_on=(FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_ETIMEOUT), **opts):
+        """General mask scheme on one region (box of cells with a mask per cell;
+        u: initial/ghost values in, solution out).  Returns (status, stats)."""
+        _check_f64(density, "density")
+        _check_f64(mask, "mask")
+        _check_f64(u, "u")
+        o = self.opts(tol=tol, **opts)
+        s = fr_stats()
+        st = self.lib.fr_solve_masked(self._h, _ptr(density), _ptr(mask), _dims(u.shape), h, box,
+                                      a, omega_m, fr0, tol, _ptr(u), ctypes.byref(o),
+                                      ctypes.byref(s), _stream(stream))
+        if st in raise_on:
+            self._raise(st, "fr_solve_masked")
         return st, s
 
     def poisson(self, density, u, phi, *, box, a, omega_m, fr0, tol=1e-8, phib=None, h=None,
