@@ -83,7 +83,8 @@ def parse_args():
     ap.add_argument("--prec", default="both", choices=["both", "mixed"],
                     help="'mixed' skips the FP64 comparison (profiling runs)")
     ap.add_argument("--workload", default="solve512",
-                    choices=["solve512", "batch96", "levels256", "cic128", "small32", "poisson512"],
+                    choices=["solve512", "batch96", "levels256", "cic128", "small32", "poisson512",
+                             "masked256"],
                     help="secondary workloads print their own line (default: the 512^3 solve)")
     ap.add_argument("--options", default="",
                     help="solver options for the headline solve instead of fr_autotune, "
@@ -392,6 +393,44 @@ def run_secondary(args):
                     oracle_tsc_ms_estimate=1e3 * t_or,
                     particles=int(pos.shape[0]),
                     max_contrast=cic_contrast, max_contrast_tsc=tsc_contrast)
+    elif args.workload == "masked256":
+        # general mask scheme: a 256^3 box (a refinement of cell size 1/512) whose
+        # active region is the union of spheres (radius 16-40 cells) around the
+        # 32 densest cells of a lognormal field at least 24 cells inside the box
+        # (a masked margin for the coarse levels), masks +1 / -1, ghosts at u = 0
+        from oracle import masked as OM
+        n = 256
+        rho_np = synth.lognormal_density((n, n, n), 6000, sigma=1.5)
+        m_np = synth.sphere_union_mask(rho_np, 32, (16, 40), 6001, margin=24)
+        u_np = np.zeros_like(rho_np)
+        PM = dict(box=128.0, a=1.0, omega_m=0.24, fr0=1e-5)
+        h = 1.0 / (2 * n)
+        rho, m = torch.from_numpy(rho_np).cuda(), torch.from_numpy(m_np).cuda()
+        u = torch.zeros_like(rho)
+        active = int((m_np > 0).sum())
+        stats = []
+
+        def run(**o):
+            u.zero_()
+            st, s = ctx.solve_masked(rho, m, u, h=h, tol=TOL, **o, **PM)
+            assert st == 0
+            stats.append(s)
+        mopts, mtimes = pick_options(run, SHAPE_CANDIDATES + [dict(pre=3, post=3, relax=1.25)])
+        t = timed(lambda: run(**mopts), args.steps, args.warmup)
+        s = stats[-1]
+        # CPU oracle: the same recipe on a 48^3 box (bounded sample)
+        ns = 48
+        rs = synth.lognormal_density((ns,) * 3, 6000, sigma=1.5)
+        ms = synth.sphere_union_mask(rs, 3, (3, 8), 6001)
+        t0 = time.perf_counter()
+        ro = OM.solve(np.zeros_like(rs), ms, rs, h=1.0 / (2 * ns), tol=TOL, **PM)
+        t_or = time.perf_counter() - t0
+        line.update(metric="general mask scheme: FP64 FAS solve of an irregular refinement region "
+                           "(union of spheres in a 256^3 box): active cells/s to rms 1e-8",
+                    value=active / t, ms=1e3 * t, active_cells=active, box_cells=n ** 3,
+                    vcycles=s.vcycles, res_rms=s.res_rms,
+                    oracle_48_active_cells_per_s=int((ms > 0).sum()) / t_or,
+                    oracle_48_vcycles=ro.cycles, tuned={**mopts, "candidates_s": mtimes})
     elif args.workload == "poisson512":
         # modified Poisson solve for Phi on the f(R) workload's field (512^3): the
         # f(R) solution u is computed first (untimed), then the Poisson solve from

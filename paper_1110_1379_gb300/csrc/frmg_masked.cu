@@ -280,6 +280,56 @@ __global__ void __launch_bounds__(kNT) k_mprolong(MLevel F, MLevel C) {
   F.u[c] += acc;
 }
 
+// Coarsest level, one block: red-black sweeps until the rms over the active
+// cells falls to max(1e-3 of its value before the first sweep, 0.1 tol), at
+// most 500 sweeps.
+constexpr int kCoNT = 1024;
+__global__ void __launch_bounds__(kCoNT) k_mcoarsest(MLevel L, long long nact, double tol,
+                                                     double cap, double relax) {
+  __shared__ double red[kCoNT / 32];
+  __shared__ double tot;
+  auto rms = [&]() -> double {
+    double s = 0.0;
+    for (long long c = threadIdx.x; c < L.ncell; c += kCoNT) {
+      if (!(L.m[c] > 0.0)) continue;
+      double N, dN;
+      m_cell(L, c, N, dN);
+      const double d = N - L.f[c];
+      s += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kCoNT / 32; w++) t += red[w];
+      tot = sqrt(t / (double)(nact > 0 ? nact : 1));
+    }
+    __syncthreads();
+    const double r = tot;
+    __syncthreads();
+    return r;
+  };
+  const double thr = fmax(1e-3 * rms(), 0.1 * tol);
+  for (int it = 0; it < 500; it++) {
+    for (int colour = 0; colour < 2; colour++) {
+      for (long long c = threadIdx.x; c < L.ncell; c += kCoNT) {
+        if (!(L.m[c] > 0.0)) continue;
+        int i, j, k;
+        ijk(L, c, i, j, k);
+        if (((i + j + k) & 1) != colour) continue;
+        double N, dN;
+        m_cell(L, c, N, dN);
+        double du = -relax * (N - L.f[c]) / dN;
+        du = du > cap ? cap : (du < -cap ? -cap : du);
+        L.u[c] += du;
+      }
+      __syncthreads();
+    }
+    if (rms() <= thr) break;
+  }
+}
+
 // Flags of a level's mask: [0] an outer-layer cell is active, [1] number of
 // active cells.
 __global__ void __launch_bounds__(kNT) k_mflags(MLevel L, unsigned long long *flags) {
@@ -371,12 +421,8 @@ struct MSolver {
     return std::sqrt(s / (double)std::max(nact, 1ll));
   }
   void coarsest(MLevel &L, long long nact) {
-    const double r0 = rms(L, nact, nullptr);
-    const double thr = std::max(1e-3 * r0, 0.1 * tol);
-    for (int it = 0; it < 500; it++) {
-      smooth(L, 1);
-      if (rms(L, nact, nullptr) <= thr) break;
-    }
+    k_mcoarsest<<<1, kCoNT, 0, st>>>(L, nact, tol, cap, relax);
+    MLAUNCH(ctx);
   }
   std::vector<long long> nact;
   void vcycle(int l) {

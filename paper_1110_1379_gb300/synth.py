@@ -189,3 +189,40 @@ def nested_case(n, seed, sizes1, count1, sizes2, count2, sigma=2.5):
                            org[0]:org[0] + s // 2]
             patches.append(dict(parent=t1, origin=org, rho=refine_density(blk, seed + 200 + t1)))
     return rho0, patches
+
+
+def sphere_union_mask(rho, count, radii, seed, margin=2):
+    """Mask of an irregular refinement region: +1 inside the union of `count`
+    spheres centred on the densest cells of rho (at least one minimum radius
+    apart, at least the maximum radius + margin cells from the box edge), with
+    radii drawn uniformly from radii = (rmin, rmax) cells; -1 elsewhere (so the
+    box's outer layer is masked).  A wider masked margin lets the multigrid
+    hierarchy coarsen further (each coarser level must keep its outer layer
+    masked)."""
+    rng = np.random.default_rng(seed)
+    n2, n1, n0 = rho.shape
+    rmin, rmax = radii
+    edge = int(np.ceil(rmax)) + margin
+    inner = np.full(rho.shape, -np.inf)
+    inner[edge:n2 - edge, edge:n1 - edge, edge:n0 - edge] = \
+        rho[edge:n2 - edge, edge:n1 - edge, edge:n0 - edge]
+    order = np.argsort(inner, axis=None)[::-1]
+    centres = []
+    for c in order:
+        if len(centres) == count or not np.isfinite(inner.flat[c]):
+            break
+        p = np.array(np.unravel_index(c, rho.shape))
+        if all(np.sum((p - q) ** 2) >= rmin ** 2 for q in centres):
+            centres.append(p)
+    m = -np.ones(rho.shape)
+    for p in centres:
+        r = rng.uniform(rmin, rmax)
+        R = int(np.ceil(r))
+        lo = [max(0, int(p[d]) - R) for d in range(3)]
+        hi = [min(rho.shape[d], int(p[d]) + R + 1) for d in range(3)]
+        k, j, i = np.meshgrid(np.arange(lo[0], hi[0]), np.arange(lo[1], hi[1]),
+                              np.arange(lo[2], hi[2]), indexing="ij")
+        inside = (k - p[0]) ** 2 + (j - p[1]) ** 2 + (i - p[2]) ** 2 < r * r
+        sub = m[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+        sub[inside] = 1.0
+    return m
