@@ -395,6 +395,7 @@ struct Problem {
   const double *bnd;  // device packed faces (patches) or null
   Consts k;
   int nl;
+  int zero_u;         // 1: start from u = 0 without reading u (initial_guess = 0)
 };
 
 // tile of the tiled smoother (x by y cells; S = 1 and S = 2 sweeps per pass)
@@ -1599,6 +1600,29 @@ __global__ void __launch_bounds__(256) k_prep_zero_df(const float2 *rv, float *r
   block_reduce2f<256>(s, m, &partial[2 * (base + blockIdx.x)], &partial[2 * (base + blockIdx.x) + 1]);
 }
 
+// Zero start of the double-float state and of the FP32 full-variable phase in
+// one pass: u = 0, e^u = 1, r = gamma (rho - 1) as a pair; the FP32 right-hand
+// side r32 = hi(r), u32 = x32 = 0; per-block partials of r32 (its norm is the
+// residual of u = 0).  Equals k_df_init with zero_u followed by k_prep_zero_df.
+__global__ void __launch_bounds__(256) k_df_init_zero(DFGrid G, const double *rho, float *r32,
+                                                      float *u32, float *x32, double *partial,
+                                                      int base) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float s = 0.0f, m = 0.0f;
+  if (t < G.ncell) {
+    G.u[t] = make_float2(0.f, 0.f);
+    G.B[t] = make_float2(1.f, 0.f);
+    const df r = df_mul(df_add_f(split_bits(rho[t]), -1.0f), df{G.gah, G.gal});
+    G.r[t] = make_float2(r.h, r.l);
+    r32[t] = r.h;
+    u32[t] = 0.0f;
+    x32[t] = 0.0f;
+    s = r.h * r.h;
+    m = fabsf(r.h);
+  }
+  block_reduce2f<256>(s, m, &partial[2 * (base + blockIdx.x)], &partial[2 * (base + blockIdx.x) + 1]);
+}
+
 static void split_host(double v, float &h, float &l) {
   h = (float)v;
   l = (float)(v - (double)h);
@@ -1659,20 +1683,27 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   double *red = S.get<double>(2 * (size_t)np);
   int *d_boff = S.get<int>(np + 1);
   CK(cudaMemcpyAsync(d_boff, boff.data(), (np + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-  int *flag = S.get<int>(1);
-  CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  for (int pi = 0; pi < np; pi++) {
-    k_any_nonzero<<<nblocks(D[pi].ncell), 256, 0, st>>>(P[pi].u, D[pi].ncell, flag);
-    CK_LAUNCH(ctx);
-  }
+  // a zero start that the caller declared (initial_guess = 0) reads no u and
+  // sets the state up in one fused pass below; otherwise u is scanned for a
+  // non-zero value
+  bool zero_start = true;
+  for (auto &p : P) zero_start = zero_start && p.zero_u;
   int nonzero = 0;
-  CK(cudaMemcpyAsync(&nonzero, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  for (int pi = 0; pi < np; pi++) {
-    PROF("df_init");
-    k_df_init<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], P[pi].u, P[pi].rho, !nonzero, ln2h,
-                                                    ln2l);
-    CK_LAUNCH(ctx);
+  if (!zero_start) {
+    int *flag = S.get<int>(1);
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    for (int pi = 0; pi < np; pi++) {
+      k_any_nonzero<<<nblocks(D[pi].ncell), 256, 0, st>>>(P[pi].u, D[pi].ncell, flag);
+      CK_LAUNCH(ctx);
+    }
+    CK(cudaMemcpyAsync(&nonzero, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int pi = 0; pi < np; pi++) {
+      PROF("df_init");
+      k_df_init<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], P[pi].u, P[pi].rho, !nonzero, ln2h,
+                                                      ln2l);
+      CK_LAUNCH(ctx);
+    }
   }
   const int bnch = red_chunks(boff);
   double *btmp = bnch ? S.get<double>(2 * (size_t)bnch * np) : nullptr;
@@ -1782,9 +1813,15 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
       for (int pi = 0; pi < np; pi++) {
         Grid<float> &G = H.lev[pi][0];
         PROF("prep_inner");
-        k_prep_zero_df<<<nblocks(G.ncell), 256, 0, st>>>(D[pi].r, const_cast<float *>(G.f),
-                                                         H.cur_u(pi, 0), H.cur_x(pi, 0),
-                                                         G.ncell, partial, boff[pi]);
+        if (zero_start)
+          k_df_init_zero<<<nblocks(G.ncell), 256, 0, st>>>(D[pi], P[pi].rho,
+                                                           const_cast<float *>(G.f),
+                                                           H.cur_u(pi, 0), H.cur_x(pi, 0),
+                                                           partial, boff[pi]);
+        else
+          k_prep_zero_df<<<nblocks(G.ncell), 256, 0, st>>>(D[pi].r, const_cast<float *>(G.f),
+                                                           H.cur_u(pi, 0), H.cur_x(pi, 0),
+                                                           G.ncell, partial, boff[pi]);
         CK_LAUNCH(ctx);
       }
       read_norms(nr);
@@ -1936,7 +1973,10 @@ static fr_opts resolve_opts(const fr_opts *o) {
 static double *stage_u(Scope &S, std::vector<Staged> &back, double *u, size_t n,
                        const fr_opts &o, cudaStream_t st) {
   double *d = stage(S, back, u, n, o.initial_guess != 0, true, st);
-  if (!o.initial_guess) CK(cudaMemsetAsync(d, 0, n * sizeof(double), st));
+  // the double-float mixed solve of a zero start never reads u (its result
+  // overwrites all of u); the other solves iterate on u itself
+  const bool unread = o.prec == FR_MIXED && o.defect_precision == 0;
+  if (!o.initial_guess && !unread) CK(cudaMemsetAsync(d, 0, n * sizeof(double), st));
   return d;
 }
 
@@ -2271,6 +2311,7 @@ static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], d
     p.fr0 = fr0;
     p.rho = drho;
     p.u = du;
+    p.zero_u = !o.initial_guess;
     std::vector<Problem> P{p};
     std::vector<fr_stats> sv(1);
     memset(sv.data(), 0, sizeof(fr_stats));
@@ -2413,6 +2454,7 @@ int fr_solve_batch(frmg_ctx *ctx, int nfields, const double *const *density, con
       p.fr0 = fr0[i];
       p.rho = stage(S, back, density[i], nc, true, false, st);
       p.u = stage_u(S, back, u[i], nc, o, st);
+      p.zero_u = !o.initial_guess;
       validate_density(ctx, S, p.rho, nc, o.allow_negative_density, st);
     }
     std::vector<fr_stats> sv(nfields);
@@ -2502,6 +2544,7 @@ int fr_solve_levels(frmg_ctx *ctx, const double *density, const int dims[3], dou
       p.fr0 = fr0;
       p.rho = drho;
       p.u = du;
+      p.zero_u = !o.initial_guess;
       std::vector<Problem> P{p};
       std::vector<fr_stats> sv(1);
       memset(sv.data(), 0, sizeof(fr_stats));
