@@ -396,6 +396,7 @@ struct Problem {
   Consts k;
   int nl;
   int zero_u;         // 1: start from u = 0 without reading u (initial_guess = 0)
+  int check_rho;      // the solve validates rho itself: 0 no, 1 yes, 2 yes, negatives allowed
 };
 
 // tile of the tiled smoother (x by y cells; S = 1 and S = 2 sweeps per pass)
@@ -1604,12 +1605,20 @@ __global__ void __launch_bounds__(256) k_prep_zero_df(const float2 *rv, float *r
 // one pass: u = 0, e^u = 1, r = gamma (rho - 1) as a pair; the FP32 right-hand
 // side r32 = hi(r), u32 = x32 = 0; per-block partials of r32 (its norm is the
 // residual of u = 0).  Equals k_df_init with zero_u followed by k_prep_zero_df.
+// check_rho > 0: also the density validation of k_check_density (negative
+// values allowed if 2), flagged in *bad.
 __global__ void __launch_bounds__(256) k_df_init_zero(DFGrid G, const double *rho, float *r32,
                                                       float *u32, float *x32, double *partial,
-                                                      int base) {
+                                                      int base, int check_rho, int *bad) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float s = 0.0f, m = 0.0f;
   if (t < G.ncell) {
+    if (check_rho > 0) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(rho[t]);
+      const bool nonfinite = ((b >> 52) & 0x7ffu) == 0x7ffu;
+      const bool negative = (b >> 63) && (b << 1) != 0;
+      if (nonfinite || (check_rho == 1 && negative)) atomicExch(bad, 1);
+    }
     G.u[t] = make_float2(0.f, 0.f);
     G.B[t] = make_float2(1.f, 0.f);
     const df r = df_mul(df_add_f(split_bits(rho[t]), -1.0f), df{G.gah, G.gal});
@@ -1688,6 +1697,8 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   // non-zero value
   bool zero_start = true;
   for (auto &p : P) zero_start = zero_start && p.zero_u;
+  int *rho_bad = S.get<int>(1);
+  CK(cudaMemsetAsync(rho_bad, 0, sizeof(int), st));
   int nonzero = 0;
   if (!zero_start) {
     int *flag = S.get<int>(1);
@@ -1817,7 +1828,8 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
           k_df_init_zero<<<nblocks(G.ncell), 256, 0, st>>>(D[pi], P[pi].rho,
                                                            const_cast<float *>(G.f),
                                                            H.cur_u(pi, 0), H.cur_x(pi, 0),
-                                                           partial, boff[pi]);
+                                                           partial, boff[pi], P[pi].check_rho,
+                                                           rho_bad);
         else
           k_prep_zero_df<<<nblocks(G.ncell), 256, 0, st>>>(D[pi].r, const_cast<float *>(G.f),
                                                            H.cur_u(pi, 0), H.cur_x(pi, 0),
@@ -1825,6 +1837,12 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
         CK_LAUNCH(ctx);
       }
       read_norms(nr);
+      if (zero_start) {
+        int hb = 0;
+        CK(cudaMemcpyAsync(&hb, rho_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (hb) throw FrError{FR_EINVAL, "density has NaN/Inf or negative values"};
+      }
       std::vector<double> r0(np);
       for (int pi = 0; pi < np; pi++) {
         r0[pi] = nr[2 * pi];
@@ -2300,7 +2318,11 @@ static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], d
     long long nc = (long long)dims[0] * dims[1] * dims[2];
     const double *drho = stage(S, back, density, nc, true, false, st);
     double *du = stage_u(S, back, u, nc, o, st);
-    validate_density(ctx, S, drho, nc, o.allow_negative_density, st);
+    // the mixed double-float solve of a zero start validates rho in its first
+    // pass; every other solve validates it here
+    const bool defer = !o.initial_guess && o.prec == FR_MIXED && o.defect_precision == 0 &&
+                       fixed <= 0;
+    if (!defer) validate_density(ctx, S, drho, nc, o.allow_negative_density, st);
     Problem p;
     memset(&p, 0, sizeof(p));
     for (int d = 0; d < 3; d++) p.n[d] = dims[d];
@@ -2312,6 +2334,7 @@ static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], d
     p.rho = drho;
     p.u = du;
     p.zero_u = !o.initial_guess;
+    p.check_rho = defer ? (o.allow_negative_density ? 2 : 1) : 0;
     std::vector<Problem> P{p};
     std::vector<fr_stats> sv(1);
     memset(sv.data(), 0, sizeof(fr_stats));

@@ -421,6 +421,28 @@ def test_initial_guess_zero_does_not_read_u(C, prec):
         C.solve(dev(rho), u0, initial_guess=2, **CFG1)
 
 
+def test_zero_start_validates_density(C):
+    """The mixed zero start validates rho in its fused first pass: NaN and
+    (unless allowed) negative values are rejected as on every other path."""
+    from paper_1110_1379_gb300 import frmg
+    shape = (16, 16, 16)
+    rho = _field(shape, 1500, sigma=0.5)
+    for bad, allow, ok in ((np.nan, 0, False), (np.inf, 0, False), (-0.2, 0, False),
+                           (-0.2, 1, True), (-0.0, 0, True)):
+        r = rho.copy()
+        r[3, 4, 5] = bad
+        u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        if ok:
+            st, s = C.solve(dev(r), u, tol=1e-8, prec="mixed", initial_guess=0,
+                            allow_negative_density=allow, **CFG1)
+            assert st == 0
+        else:
+            with pytest.raises(frmg.FRError) as e:
+                C.solve(dev(r), u, tol=1e-8, prec="mixed", initial_guess=0,
+                        allow_negative_density=allow, **CFG1)
+            assert e.value.status == frmg.FR_EINVAL
+
+
 def test_relax_out_of_range_rejected(C):
     from paper_1110_1379_gb300 import frmg
     rho = torch.ones((8, 8, 8), dtype=torch.float64, device="cuda")
