@@ -37,16 +37,37 @@ __global__ void k_df_init(DFGrid G, const double *u64, const double *rho, int ze
   G.r[t] = make_float2(r.h, r.l);
 }
 
-// u += delta, e^u recomputed from u (no drift across outer steps).
+// u += delta and e^u.  For |delta| < 2^-5 (the correction steps) e^u is the
+// old e^u times e^delta, e^delta by its Taylor series to degree 7 in
+// double-float (truncation below 2^-40 delta^8 / 8!, far under the pair's
+// rounding); larger steps (the first update after the full-variable phase)
+// recompute e^u from u.
 __global__ void k_df_update(DFGrid G, const float *delta, float ln2h, float ln2l) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= G.ncell) return;
   const float2 uo = G.u[t];
-  df s = two_sum(uo.x, delta[t]);
+  const float dl = delta[t];
+  df s = two_sum(uo.x, dl);
   s.l += uo.y;
   df u = fast_two_sum(s.h, s.l);
   G.u[t] = make_float2(u.h, u.l);
-  df B = df_exp(u, ln2h, ln2l);
+  df B;
+  if (fabsf(dl) < 0.03125f) {
+    // Horner: e^d = 1 + d (1 + d/2 (1 + d/3 (... (1 + d/7))))
+    df q = {1.0f, 0.0f};
+#pragma unroll
+    for (int k = 7; k >= 1; k--) {
+      q = df_mul_f(q, dl);
+      const float rk = 1.0f / (float)k;  // a constant after unrolling
+      const float qh = q.h * rk;
+      const float rem = fmaf(-qh, (float)k, q.h) + q.l;
+      q = df_add_f(df{qh, rem * rk}, 1.0f);
+    }
+    const float2 Bo = G.B[t];
+    B = df_mul(df{Bo.x, Bo.y}, q);
+  } else {
+    B = df_exp(u, ln2h, ln2l);
+  }
   G.B[t] = make_float2(B.h, B.l);
 }
 
