@@ -176,6 +176,11 @@ static int assign_impl(frmg_ctx *ctx, const double *pos, long long np, const int
       frmg_set_error("dims must be positive");
       return FR_EINVAL;
     }
+  if (cudaSetDevice(frmg_device(ctx)) != cudaSuccess) {
+    cudaGetLastError();
+    frmg_set_error("cudaSetDevice failed");
+    return FR_ECUDA;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   long long nc = (long long)dims[0] * dims[1] * dims[2];
   const double *dpos = pos;
@@ -263,6 +268,11 @@ extern "C" int fr_particle_forces(frmg_ctx *ctx, const double *phi, const int di
       frmg_set_error("dims must be at least 3");
       return FR_EINVAL;
     }
+  if (cudaSetDevice(frmg_device(ctx)) != cudaSuccess) {
+    cudaGetLastError();
+    frmg_set_error("cudaSetDevice failed");
+    return FR_ECUDA;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const long long nc = (long long)dims[0] * dims[1] * dims[2];
   std::vector<void *> tmp;

@@ -14,3 +14,5 @@ double *frmg_pinned(frmg_ctx *c, size_t n);
 void frmg_release(frmg_ctx *c, void *p);
 void frmg_set_error(const std::string &s);
 long long &frmg_launch_counter(frmg_ctx *c);
+// the device a context was created on
+int frmg_device(frmg_ctx *c);

@@ -457,6 +457,7 @@ extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const doubl
   try {
     const auto t0 = std::chrono::steady_clock::now();
     if (!ctx || !density || !mask || !dims || !u_inout) throw MError{FR_EINVAL, "NULL argument"};
+    MCK(cudaSetDevice(frmg_device(ctx)));
     for (int d = 0; d < 3; d++)
       if (dims[d] < 3) throw MError{FR_EINVAL, "dims must be >= 3 (outer ghost layer)"};
     const long long nc = (long long)dims[0] * dims[1] * dims[2];

@@ -1028,6 +1028,7 @@ extern "C" int fr_poisson_solve(frmg_ctx *ctx, const double *density, const doub
     const auto t0 = std::chrono::steady_clock::now();
     if (!ctx || !density || !u || !dims || !phi_inout)
       throw PError{FR_EINVAL, "NULL argument"};
+    PCK(cudaSetDevice(frmg_device(ctx)));
     for (int d = 0; d < 3; d++)
       if (dims[d] < 2 || (dims[d] & 1)) throw PError{FR_EINVAL, "dims must be even and >= 2"};
     const long long nc = (long long)dims[0] * dims[1] * dims[2];
@@ -1277,6 +1278,7 @@ extern "C" int fr_poisson_source(frmg_ctx *ctx, const double *density, const dou
                                  double omega_m, double fr0_abs, double *s_out, void *stream) {
   try {
     if (!ctx || !density || !u || !dims || !s_out) throw PError{FR_EINVAL, "NULL argument"};
+    PCK(cudaSetDevice(frmg_device(ctx)));
     for (int d = 0; d < 3; d++)
       if (dims[d] < 1) throw PError{FR_EINVAL, "bad dims"};
     const long long nc = (long long)dims[0] * dims[1] * dims[2];

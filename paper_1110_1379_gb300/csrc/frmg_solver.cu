@@ -141,6 +141,7 @@ struct ProfScope {
 #define PROF(name) ProfScope prof_scope_(ctx, st, name)
 
 long long &frmg_launch_counter(frmg_ctx *c) { return c->launches; }
+int frmg_device(frmg_ctx *c) { return c->device; }
 
 static size_t round_bytes(size_t b) { return (b + 4095) & ~(size_t)4095; }
 
