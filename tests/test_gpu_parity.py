@@ -194,6 +194,27 @@ def test_host_pointers_same_as_device(C):
     assert np.abs(host(u) - u_host).max() < 1e-14
 
 
+@pytest.mark.parametrize("pinned", [False, True])
+@pytest.mark.parametrize("initial_guess", [0, 1])
+def test_mixed_host_output_equals_device(C, pinned, initial_guess):
+    """A host u (page-locked: copied out early, while the last defect is
+    checked; pageable: copied at the end) receives exactly the device result,
+    also when the solve needs more than one outer step."""
+    shape = (48, 32, 64)
+    rho = _field(shape, 4300, sigma=2.0)
+    P = dict(box=2.0 * shape[2], a=1.0, omega_m=0.24, fr0=1e-5)
+    ud = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st, sd = C.solve(dev(rho), ud, tol=1e-9, prec="mixed", initial_guess=initial_guess, **P)
+    assert st == 0 and sd.outer >= 2
+    uh = torch.zeros(shape, dtype=torch.float64, pin_memory=pinned)
+    rh = torch.from_numpy(rho)
+    if pinned:
+        rh = rh.pin_memory()
+    st, sh = C.solve(rh, uh, tol=1e-9, prec="mixed", initial_guess=initial_guess, **P)
+    assert st == 0 and sh.vcycles == sd.vcycles and sh.outer == sd.outer
+    assert np.array_equal(uh.numpy(), host(ud))
+
+
 # ------------------------------------------------------------------ edge cases
 def test_invalid_arguments(C):
     from paper_1110_1379_gb300 import frmg
