@@ -1324,57 +1324,109 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
   };
   // Newton update of the colour-Q cell of pair (ly, px) of plane m; s is its x
   // position in the pair; oc, om, op are the (u, x) slot offsets of planes m,
-  // m - 1, m + 1 (colour Q's array at oc + Q PP), ofq the f offset.
-  auto update = [&](auto Qc, int ly, int px, int s, int m, int oc, int om, int op, int ofq) {
+  // m - 1, m + 1 (colour Q's array at oc + Q PP), ofq the f offset.  Split in
+  // three: gather (the shared-memory reads), compute (registers and, on patch
+  // faces, the boundary values) and store, so that two independent updates
+  // can read all their operands before either writes (the compiler cannot
+  // tell that a write of one colour never feeds a read of the other).
+  struct CellIn {
+    float4 own, lft, rgt, nym, nyp, nzm, nzp;
+    float f;
+    int e, gx, gy;
+  };
+  auto gather = [&](auto Qc, int ly, int px, int s, int oc, int om, int op, int ofq) {
     constexpr int Q = decltype(Qc)::value;
-    const int gx = X0 - H + 2 * px + s, gy = Y0 - H + ly;
-    if (DIR && (gx < 0 || gx >= n0 || gy < 0 || gy >= n1)) return;
+    CellIn c;
+    c.gx = X0 - H + 2 * px + s;
+    c.gy = Y0 - H + ly;
     const int e = ly * PX + px;
+    c.e = e;
     const int cq = Q * PP, co = (Q ^ 1) * PP;
     const int V = oc + co;
     const int ex = s ? e + 1 : e - 1;
-    const float4 own = cell(oc + cq + e);
+    c.own = cell(oc + cq + e);
     const float4 nin = cell(V + e), nxo = cell(V + ex);
-    const float4 nym = cell(V + e - PX), nyp = cell(V + e + PX);
-    const float4 nzm = cell(om + co + e), nzp = cell(op + co + e);
-    const float4 lft = s ? nin : nxo, rgt = s ? nxo : nin;
-    const float di = own.x, xi = own.y;
-    const float Ei = BG ? own.w : 1.0f;
-    const float ubi = BG ? own.z : 0.0f;
+    c.lft = s ? nin : nxo;
+    c.rgt = s ? nxo : nin;
+    c.nym = cell(V + e - PX);
+    c.nyp = cell(V + e + PX);
+    c.nzm = cell(om + co + e);
+    c.nzp = cell(op + co + e);
+    c.f = sfv[ofq + e];
+    return c;
+  };
+  auto inside = [&](const CellIn &c) {
+    return !DIR || (c.gx >= 0 && c.gx < n0 && c.gy >= 0 && c.gy < n1);
+  };
+  // new (u, x) of the cell
+  auto compute = [&](const CellIn &c, int m) -> float2 {
+    const int gx = c.gx, gy = c.gy;
+    const float di = c.own.x, xi = c.own.y;
+    const float Ei = BG ? c.own.w : 1.0f;
+    const float ubi = BG ? c.own.z : 0.0f;
     const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
     OpAcc<float, BG> A(di, Ei, xi, Bi, ubi);
     if (DIR && gx == 0)
       A.ghost(face_value(Gg, 0, gx, gy, m));
     else
-      A.reg(lft.x, lft.y, lft.z, lft.w);
+      A.reg(c.lft.x, c.lft.y, c.lft.z, c.lft.w);
     if (DIR && gx == n0 - 1)
       A.ghost(face_value(Gg, 1, gx, gy, m));
     else
-      A.reg(rgt.x, rgt.y, rgt.z, rgt.w);
+      A.reg(c.rgt.x, c.rgt.y, c.rgt.z, c.rgt.w);
     if (DIR && gy == 0)
       A.ghost(face_value(Gg, 2, gx, gy, m));
     else
-      A.reg(nym.x, nym.y, nym.z, nym.w);
+      A.reg(c.nym.x, c.nym.y, c.nym.z, c.nym.w);
     if (DIR && gy == n1 - 1)
       A.ghost(face_value(Gg, 3, gx, gy, m));
     else
-      A.reg(nyp.x, nyp.y, nyp.z, nyp.w);
+      A.reg(c.nyp.x, c.nyp.y, c.nyp.z, c.nyp.w);
     if (DIR && m == 0)
       A.ghost(face_value(Gg, 4, gx, gy, m));
     else
-      A.reg(nzm.x, nzm.y, nzm.z, nzm.w);
+      A.reg(c.nzm.x, c.nzm.y, c.nzm.z, c.nzm.w);
     if (DIR && m == n2 - 1)
       A.ghost(face_value(Gg, 5, gx, gy, m));
     else
-      A.reg(nzp.x, nzp.y, nzp.z, nzp.w);
+      A.reg(c.nzp.x, c.nzp.y, c.nzp.z, c.nzp.w);
     float acc, dacc;
     A.done(acc, dacc);
     float N, dN;
     finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-    float du = relax * newton_step(N - sfv[ofq + e], dN);
+    float du = relax * newton_step(N - c.f, dN);
     du = fminf(fmaxf(du, -cap), cap);
     const float dn = di + du;
-    put_ux(oc + cq + e, dn, m_expm1(dn));
+    return make_float2(dn, m_expm1(dn));
+  };
+  auto update = [&](auto Qc, int ly, int px, int s, int m, int oc, int om, int op, int ofq) {
+    constexpr int Q = decltype(Qc)::value;
+    const CellIn c = gather(Qc, ly, px, s, oc, om, op, ofq);
+    if (!inside(c)) return;
+    const float2 r = compute(c, m);
+    put_ux(oc + Q * PP + c.e, r.x, r.y);
+  };
+  // two updates of the same colour and plane (rows lya and lyb): both gather
+  // before either stores, and their arithmetic interleaves
+  auto update2 = [&](auto Qc, int lya, int lyb, int px, int s, int m, int oc, int om, int op,
+                     int ofq) {
+    constexpr int Q = decltype(Qc)::value;
+    const CellIn a = gather(Qc, lya, px, s, oc, om, op, ofq);
+    const CellIn b = gather(Qc, lyb, px, s, oc, om, op, ofq);
+    if (DIR) {
+      if (inside(a)) {
+        const float2 r = compute(a, m);
+        put_ux(oc + Q * PP + a.e, r.x, r.y);
+      }
+      if (inside(b)) {
+        const float2 r = compute(b, m);
+        put_ux(oc + Q * PP + b.e, r.x, r.y);
+      }
+    } else {
+      const float2 ra = compute(a, m), rb = compute(b, m);
+      put_ux(oc + Q * PP + a.e, ra.x, ra.y);
+      put_ux(oc + Q * PP + b.e, rb.x, rb.y);
+    }
   };
 
   const int P0 = Z0 - H, PE = Z1 + H;
@@ -1402,12 +1454,11 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
       const int m = p - 1;
       if (m >= Z0 - 1 && m < Z1 + 1 && (!DIR || (m >= 0 && m < n2))) {
         const int s = (w + 1 + pb + 1) & 1;  // rows 1 + w + j NW: parity of (ly + m) = s
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-          if (j == 2 && w >= 2) break;
-          update(std::integral_constant<int, 0>{}, 1 + w + j * NW, 1 + lane, s, m, o1, o2, o0,
+        update2(std::integral_constant<int, 0>{}, 1 + w, 1 + w + NW, 1 + lane, s, m, o1, o2, o0,
+                f1);
+        if (w < 2)
+          update(std::integral_constant<int, 0>{}, 1 + w + 2 * NW, 1 + lane, s, m, o1, o2, o0,
                  f1);
-        }
         if (w == 2 || w == 3) {
           const int idx = (w - 2) * 32 + lane;
           if (idx < C::NE) {
@@ -1424,10 +1475,8 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
       const int m = p - 2;
       if (m >= Z0 && m < Z1 && (!DIR || (m >= 0 && m < n2))) {
         const int s = (w + m + 1) & 1;  // rows 2 + w + j NW: parity of (ly + m + 1) = s
-#pragma unroll
-        for (int j = 0; j < 2; j++)
-          update(std::integral_constant<int, 1>{}, 2 + w + j * NW, 1 + lane, s, m, o2, o3, o1,
-                 f2);
+        update2(std::integral_constant<int, 1>{}, 2 + w, 2 + w + NW, 1 + lane, s, m, o2, o3, o1,
+                f2);
       }
     }
     __syncthreads();
