@@ -28,7 +28,10 @@
 //   active cell.
 //
 // FP64 throughout (one thread per cell), red-black Newton-Gauss-Seidel with
-// the step clamped to |du| <= cap and optionally over-relaxed.
+// the step clamped to |du| <= cap and optionally over-relaxed.  Every level
+// keeps b = exp(u) beside u, written by each kernel that writes u, so an
+// operator evaluation takes one exponential (e^{-u_i/2}) plus one per ghost
+// face instead of eight: FP64 exponentials are the cost of these kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -73,12 +76,15 @@ long long nblk(long long n) { return (n + kNT - 1) / kNT; }
 // One level of a masked region.
 struct MLevel {
   double *u;        // iterate in active cells, fixed ghost values elsewhere
+  double *b;        // exp(u) of every cell, rewritten wherever u changes
   const double *m;  // mask
   const double *rho;
   double *f;        // FAS right-hand side (0 on the finest level)
   double *uR;       // R u^h of the active cells (coarse levels)
   double *d;        // residual (fine side) or R d^h (coarse side)
   double *ub;       // [6][ncell] boundary values of the ghost faces (NaN elsewhere)
+  const int *act;   // active cells in index order, colour 0 ((i+j+k) even) first
+  long long na0, na;  // active cells of colour 0, of both colours
   int n0, n1, n2;
   long long ncell;
   FastDiv fd0, fd1;
@@ -99,17 +105,18 @@ __device__ __forceinline__ long long face_step(const MLevel &L, int f) {
   return (f & 1) ? s : -s;
 }
 
-// L_i and dL_i/du_i at active cell c (Eqs. bc_modified_fR_op / _dop)
+// L_i and dL_i/du_i at active cell c (Eqs. bc_modified_fR_op / _dop); the
+// exponentials of the cell and of its active neighbours come from the cache b
 __device__ __forceinline__ void m_cell(const MLevel &L, long long c, double &N, double &dN) {
   const double ui = L.u[c], mi = L.m[c];
-  const double bi = exp(ui);
+  const double bi = L.b[c];
   double acc = 0.0, dacc = 0.0;
 #pragma unroll
   for (int f = 0; f < 6; f++) {
     const long long cj = c + face_step(L, f);
     const double mj = L.m[cj];
     if (mj > 0.0) {
-      const double uj = L.u[cj], bj = exp(uj);
+      const double uj = L.u[cj], bj = L.b[cj];
       acc += (bi + bj) * (uj - ui);
       dacc += bi * (uj - ui) - (bi + bj);
     } else {
@@ -128,11 +135,13 @@ __device__ __forceinline__ void m_cell(const MLevel &L, long long c, double &N, 
 
 namespace {
 
-// Boundary values of the ghost faces from the current (initial) values.
+// Boundary values of the ghost faces from the current (initial) values, and
+// the exponential cache of every cell.
 __global__ void __launch_bounds__(kNT) k_mub(MLevel L) {
   const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
   if (c >= L.ncell) return;
   const double mi = L.m[c], ui = L.u[c];
+  L.b[c] = exp(ui);
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
 #pragma unroll
   for (int f = 0; f < 6; f++) {
@@ -146,35 +155,78 @@ __global__ void __launch_bounds__(kNT) k_mub(MLevel L) {
   }
 }
 
+// Active-cell lists: per block of kNT cells, the active cells of each colour
+// (k_mcount), then each cell's place in its colour's list from the scanned
+// block bases (k_mlist).  A colour's cells are independent of one another, so
+// a sweep over the list equals the sweep over the box; the lists keep warps
+// full where the region covers a small part of the box.
+__global__ void __launch_bounds__(kNT) k_mcount(MLevel L, int *cnt) {
+  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  bool a0 = false, a1 = false;
+  if (c < L.ncell && L.m[c] > 0.0) {
+    int i, j, k;
+    ijk(L, c, i, j, k);
+    a0 = ((i + j + k) & 1) == 0;
+    a1 = !a0;
+  }
+  const int n0 = __syncthreads_count(a0), n1 = __syncthreads_count(a1);
+  if (threadIdx.x == 0) {
+    cnt[2 * blockIdx.x] = n0;
+    cnt[2 * blockIdx.x + 1] = n1;
+  }
+}
+
+__global__ void __launch_bounds__(kNT) k_mlist(MLevel L, const int *base, int *act) {
+  constexpr int NWp = kNT / 32;
+  __shared__ int wo[2][NWp];
+  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  bool a[2] = {false, false};
+  if (c < L.ncell && L.m[c] > 0.0) {
+    int i, j, k;
+    ijk(L, c, i, j, k);
+    a[(i + j + k) & 1] = true;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned bal[2];
+  for (int q = 0; q < 2; q++) {
+    bal[q] = __ballot_sync(0xffffffffu, a[q]);
+    if (lane == 0) wo[q][w] = __popc(bal[q]);
+  }
+  __syncthreads();
+  for (int q = 0; q < 2; q++) {
+    if (!a[q]) continue;
+    int o = base[2 * blockIdx.x + q];
+    for (int v = 0; v < w; v++) o += wo[q][v];
+    act[o + __popc(bal[q] & ((1u << lane) - 1u))] = (int)c;
+  }
+}
+
 // One colour of a red-black Newton-Gauss-Seidel sweep over the active cells
-// (one thread per cell pair along x; the colour's cell of the pair).
+// (one thread per active cell of the colour).
 __global__ void __launch_bounds__(kNT) k_msmooth(MLevel L, int colour, double cap, double relax) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
-  if (2 * t >= L.ncell) return;
-  int i, j, k;
-  ijk(L, 2 * t, i, j, k);
-  i += (i + j + k + colour) & 1;
-  const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
-  if (!(L.m[c] > 0.0)) return;
+  const long long n = colour ? L.na - L.na0 : L.na0;
+  if (t >= n) return;
+  const long long c = L.act[(colour ? L.na0 : 0) + t];
   double N, dN;
   m_cell(L, c, N, dN);
   double du = -relax * (N - L.f[c]) / dN;
   du = du > cap ? cap : (du < -cap ? -cap : du);
-  L.u[c] += du;
+  const double un = L.u[c] + du;
+  L.u[c] = un;
+  L.b[c] = exp(un);
 }
 
-// d = L(u) - f on active cells (0 on ghosts); per-block partials
-// (sum d^2, max |d|).
+// d = L(u) - f on the active cells (one thread per active cell; ghosts' d is
+// never read); per-block partials (sum d^2, max |d|).
 __global__ void __launch_bounds__(kNT) k_mresid(MLevel L, double *partial) {
-  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   double s = 0.0, mx = 0.0;
-  if (c < L.ncell) {
-    double d = 0.0;
-    if (L.m[c] > 0.0) {
-      double N, dN;
-      m_cell(L, c, N, dN);
-      d = N - L.f[c];
-    }
+  if (t < L.na) {
+    const long long c = L.act[t];
+    double N, dN;
+    m_cell(L, c, N, dN);
+    const double d = N - L.f[c];
     L.d[c] = d;
     s = d * d;
     mx = fabs(d);
@@ -239,6 +291,7 @@ __global__ void __launch_bounds__(kNT) k_mrestrict(MLevel F, MLevel C) {
   }
   C.uR[t] = 0.125 * su;
   C.u[t] = 0.125 * su;
+  C.b[t] = exp(0.125 * su);
   C.d[t] = 0.125 * sd;
 }
 
@@ -255,12 +308,13 @@ __global__ void __launch_bounds__(kNT) k_mfas(MLevel C) {
   C.f[t] = N - C.d[t];
 }
 
-// u^h += P e^H on the active fine cells, e^H = u^H - R u^h on active coarse
-// cells and 0 on masked ones and outside the box (trilinear 27/9/3/1).
+// u^h += P e^H on the active fine cells (one thread per active cell), e^H =
+// u^H - R u^h on active coarse cells and 0 on masked ones and outside the box
+// (trilinear 27/9/3/1).
 __global__ void __launch_bounds__(kNT) k_mprolong(MLevel F, MLevel C) {
-  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
-  if (c >= F.ncell) return;
-  if (!(F.m[c] > 0.0)) return;
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= F.na) return;
+  const long long c = F.act[t];
   int i, j, k;
   ijk(F, c, i, j, k);
   const int I = i >> 1, J = j >> 1, K = k >> 1;
@@ -277,7 +331,9 @@ __global__ void __launch_bounds__(kNT) k_mprolong(MLevel F, MLevel C) {
                      ((q >> 2) ? 0.25 : 0.75);
     acc += w * (C.u[cc] - C.uR[cc]);
   }
-  F.u[c] += acc;
+  const double un = F.u[c] + acc;
+  F.u[c] = un;
+  F.b[c] = exp(un);
 }
 
 // Coarsest level, one block: red-black sweeps until the rms over the active
@@ -322,7 +378,9 @@ __global__ void __launch_bounds__(kCoNT) k_mcoarsest(MLevel L, long long nact, d
         m_cell(L, c, N, dN);
         double du = -relax * (N - L.f[c]) / dN;
         du = du > cap ? cap : (du < -cap ? -cap : du);
-        L.u[c] += du;
+        const double un = L.u[c] + du;
+        L.u[c] = un;
+        L.b[c] = exp(un);
       }
       __syncthreads();
     }
@@ -401,13 +459,14 @@ struct MSolver {
   void smooth(MLevel &L, int n) {
     for (int s = 0; s < n; s++)
       for (int colour = 0; colour < 2; colour++) {
-        k_msmooth<<<(unsigned)nblk((L.ncell + 1) / 2), kNT, 0, st>>>(L, colour, cap, relax);
+        k_msmooth<<<(unsigned)nblk(std::max(colour ? L.na - L.na0 : L.na0, 1ll)), kNT, 0, st>>>(
+            L, colour, cap, relax);
         MLAUNCH(ctx);
       }
   }
   // rms over the active cells of level L (and its max |d|); host sync
   double rms(MLevel &L, long long nact, double *dmax) {
-    const long long nb = nblk(L.ncell);
+    const long long nb = nblk(std::max(L.na, 1ll));
     k_mresid<<<(unsigned)nb, kNT, 0, st>>>(L, partial);
     MLAUNCH(ctx);
     MCK(cudaMemcpyAsync(host, partial, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -433,14 +492,14 @@ struct MSolver {
     }
     MLevel &C = lev[l + 1];
     smooth(L, pre);
-    k_mresid<<<(unsigned)nblk(L.ncell), kNT, 0, st>>>(L, partial);
+    k_mresid<<<(unsigned)nblk(std::max(L.na, 1ll)), kNT, 0, st>>>(L, partial);
     MLAUNCH(ctx);
     k_mrestrict<<<(unsigned)nblk(C.ncell), kNT, 0, st>>>(L, C);
     MLAUNCH(ctx);
     k_mfas<<<(unsigned)nblk(C.ncell), kNT, 0, st>>>(C);
     MLAUNCH(ctx);
     vcycle(l + 1);
-    k_mprolong<<<(unsigned)nblk(L.ncell), kNT, 0, st>>>(L, C);
+    k_mprolong<<<(unsigned)nblk(std::max(L.na, 1ll)), kNT, 0, st>>>(L, C);
     MLAUNCH(ctx);
     smooth(L, post);
   }
@@ -508,12 +567,15 @@ extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const doubl
       L.fd0 = make_fastdiv((unsigned)n0);
       L.fd1 = make_fastdiv((unsigned)n1);
       L.u = u;
+      L.b = A.get<double>(L.ncell);
       L.m = m;
       L.rho = rho;
       L.f = A.get<double>(L.ncell);
       L.uR = A.get<double>(L.ncell);
       L.d = A.get<double>(L.ncell);
       L.ub = A.get<double>(6 * L.ncell);
+      L.act = nullptr;  // set once the level set is final
+      L.na0 = L.na = 0;
       L.ah = 0.5 * alpha * (h * h) / (hl * hl);
       L.beta = k6[1];
       L.gamma = k6[2];
@@ -549,6 +611,36 @@ extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const doubl
     for (auto &L : S.lev) {
       k_mub<<<(unsigned)nblk(L.ncell), kNT, 0, st>>>(L);
       MLAUNCH(ctx);
+    }
+    // active-cell lists of every level
+    for (size_t l = 0; l < S.lev.size(); l++) {
+      MLevel &L = S.lev[l];
+      const long long nb = nblk(L.ncell);
+      int *cnt = A.get<int>(2 * nb), *base = A.get<int>(2 * nb);
+      int *act = A.get<int>(std::max(S.nact[l], 1ll));
+      k_mcount<<<(unsigned)nb, kNT, 0, st>>>(L, cnt);
+      MLAUNCH(ctx);
+      std::vector<int> hc(2 * nb), hbase(2 * nb);
+      MCK(cudaMemcpyAsync(hc.data(), cnt, 2 * nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+      MCK(cudaStreamSynchronize(st));
+      long long n0 = 0, n1 = 0;  // colour 0 first, then colour 1
+      for (long long b = 0; b < nb; b++) n0 += hc[2 * b];
+      long long o0 = 0, o1 = n0;
+      for (long long b = 0; b < nb; b++) {
+        hbase[2 * b] = (int)o0;
+        hbase[2 * b + 1] = (int)o1;
+        o0 += hc[2 * b];
+        o1 += hc[2 * b + 1];
+        n1 += hc[2 * b + 1];
+      }
+      if (n0 + n1 != S.nact[l]) throw MError{FR_ECUDA, "active-cell count mismatch"};
+      MCK(cudaMemcpyAsync(base, hbase.data(), 2 * nb * sizeof(int), cudaMemcpyHostToDevice, st));
+      k_mlist<<<(unsigned)nb, kNT, 0, st>>>(L, base, act);
+      MLAUNCH(ctx);
+      MCK(cudaStreamSynchronize(st));
+      L.act = act;
+      L.na0 = n0;
+      L.na = n0 + n1;
     }
     S.partial = A.get<double>(2 * nblk(nc));
     double *pin = frmg_pinned(ctx, 2 * nblk(nc));
