@@ -369,11 +369,19 @@ int fr_poisson_source(frmg_ctx *ctx, const double *density, const double *u, con
  * keeps an active cell.  The paper's masks are +1 (active) and -1 on the
  * finest level; a small positive mask puts the boundary close to the cell
  * centre and makes |r| large (the ghost then amplifies changes of u_i by |r|).
- * FP64 arithmetic (opts->prec is not used); V(pre,post)
- * red-black Newton-Gauss-Seidel (opts->pre, post, newton_step_cap, relax),
- * until the rms of L(u) over the active cells is <= tol (FR_OK) or
- * opts->max_vcycles V-cycles (FR_ENOCONV).  stats: vcycles, res0_rms,
- * res_rms, res_max, seconds, hist.  Synchronous on return.
+ * V(pre,post) red-black Newton-Gauss-Seidel (opts->pre, post,
+ * newton_step_cap, relax), until the rms of L(u) over the active cells is
+ * <= tol (FR_OK) or opts->max_vcycles V-cycles (FR_ENOCONV).
+ * opts->prec = FR_FP64: every step in FP64.  FR_MIXED: the same V-cycles in
+ * FP32 first (mask, density and ghost boundary values read from the FP64
+ * copies), until their residual stalls (ratio >= 0.75 per cycle), grows past
+ * three times its best, or falls to 1e-6 of its start or to tol; then FP64
+ * V-cycles from that iterate until tol (a non-finite FP32 residual discards
+ * the FP32 phase).  The convergence test is always the FP64 residual.
+ * stats: vcycles (both phases), res0_rms, res_rms, res_max, seconds, hist (the
+ * rms after each V-cycle; mixed: FP32 values, then the FP64 values negated),
+ * outer (mixed: FP64 residual evaluations after the FP32 phase).
+ * Synchronous on return.
  */
 int fr_solve_masked(frmg_ctx *ctx, const double *density, const double *mask, const int dims[3],
                     double h, double box_mpc_h, double a, double omega_m, double fr0_abs,

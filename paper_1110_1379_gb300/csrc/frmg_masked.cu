@@ -73,26 +73,34 @@ constexpr int kNT = 256;
 
 long long nblk(long long n) { return (n + kNT - 1) / kNT; }
 
-// One level of a masked region.
-struct MLevel {
-  double *u;        // iterate in active cells, fixed ghost values elsewhere
-  double *b;        // exp(u) of every cell, rewritten wherever u changes
+// One level of a masked region, iterate and work arrays in T (FP64, or FP32
+// for the first phase of a mixed-precision solve); the mask, density and
+// ghost boundary values are always the FP64 level's.
+template <typename T>
+struct MLevelT {
+  T *u;             // iterate in active cells, fixed ghost values elsewhere
+  T *b;             // exp(u) of every cell, rewritten wherever u changes
   const double *m;  // mask
   const double *rho;
-  double *f;        // FAS right-hand side (0 on the finest level)
-  double *uR;       // R u^h of the active cells (coarse levels)
-  double *d;        // residual (fine side) or R d^h (coarse side)
+  T *f;             // FAS right-hand side (0 on the finest level)
+  T *uR;            // R u^h of the active cells (coarse levels)
+  T *d;             // residual (fine side) or R d^h (coarse side)
   double *ub;       // [6][ncell] boundary values of the ghost faces (NaN elsewhere)
   const int *act;   // active cells in index order, colour 0 ((i+j+k) even) first
   long long na0, na;  // active cells of colour 0, of both colours
   int n0, n1, n2;
   long long ncell;
   FastDiv fd0, fd1;
-  double ah;        // alpha / 2 at this level's h
-  double beta, gamma;
+  T ah;             // alpha / 2 at this level's h
+  T beta, gamma;
 };
+using MLevel = MLevelT<double>;
 
-__device__ __forceinline__ void ijk(const MLevel &L, long long c, int &i, int &j, int &k) {
+__device__ __forceinline__ double m_exp(double v) { return exp(v); }
+__device__ __forceinline__ float m_exp(float v) { return expf(v); }
+
+template <typename T>
+__device__ __forceinline__ void ijk(const MLevelT<T> &L, long long c, int &i, int &j, int &k) {
   const unsigned cu = (unsigned)c, q = fdiv(cu, L.fd0), q2 = fdiv(q, L.fd1);
   i = (int)(cu - q * (unsigned)L.n0);
   j = (int)(q - q2 * (unsigned)L.n1);
@@ -100,35 +108,46 @@ __device__ __forceinline__ void ijk(const MLevel &L, long long c, int &i, int &j
 }
 
 // neighbour offset of face f (-x, +x, -y, +y, -z, +z)
-__device__ __forceinline__ long long face_step(const MLevel &L, int f) {
+template <typename T>
+__device__ __forceinline__ long long face_step(const MLevelT<T> &L, int f) {
   const long long s = f < 2 ? 1 : (f < 4 ? (long long)L.n0 : (long long)L.n0 * L.n1);
   return (f & 1) ? s : -s;
 }
 
 // L_i and dL_i/du_i at active cell c (Eqs. bc_modified_fR_op / _dop); the
-// exponentials of the cell and of its active neighbours come from the cache b
-__device__ __forceinline__ void m_cell(const MLevel &L, long long c, double &N, double &dN) {
-  const double ui = L.u[c], mi = L.m[c];
-  const double bi = L.b[c];
-  double acc = 0.0, dacc = 0.0;
+// exponentials of the cell and of its active neighbours come from the cache b.
+// In FP32 the mass term's e^{-u/2} - 1 is formed by expm1f (no cancellation
+// near u = 0).
+template <typename T>
+__device__ __forceinline__ void m_cell(const MLevelT<T> &L, long long c, T &N, T &dN) {
+  const T ui = L.u[c], mi = (T)L.m[c];
+  const T bi = L.b[c];
+  T acc = T(0), dacc = T(0);
 #pragma unroll
   for (int f = 0; f < 6; f++) {
     const long long cj = c + face_step(L, f);
-    const double mj = L.m[cj];
-    if (mj > 0.0) {
-      const double uj = L.u[cj], bj = L.b[cj];
+    const double mjd = L.m[cj];
+    if (mjd > 0.0) {
+      const T uj = L.u[cj], bj = L.b[cj];
       acc += (bi + bj) * (uj - ui);
       dacc += bi * (uj - ui) - (bi + bj);
     } else {
-      const double r = mj / mi, ub = L.ub[f * L.ncell + c];
-      const double ug = ub - r * ub + r * ui, bg = exp(ug);
+      const T r = (T)mjd / mi, ub = (T)L.ub[f * L.ncell + c];
+      const T ug = ub - r * ub + r * ui, bg = m_exp(ug);
       acc += (bi + bg) * (ug - ui);
-      dacc += (bi + r * bg) * (ug - ui) + (bi + bg) * (r - 1.0);
+      dacc += (bi + r * bg) * (ug - ui) + (bi + bg) * (r - T(1));
     }
   }
-  const double s = exp(-0.5 * ui);
-  N = L.ah * acc + L.beta * (s - 1.0) - L.gamma * (L.rho[c] - 1.0);
-  dN = L.ah * dacc - 0.5 * L.beta * s;
+  T s, sm1;
+  if constexpr (sizeof(T) == 8) {
+    s = exp(-0.5 * ui);
+    sm1 = s - 1.0;
+  } else {
+    sm1 = expm1f(-0.5f * ui);
+    s = sm1 + 1.0f;
+  }
+  N = L.ah * acc + L.beta * sm1 - L.gamma * ((T)L.rho[c] - T(1));
+  dN = L.ah * dacc - T(0.5) * L.beta * s;
 }
 
 }  // namespace
@@ -203,33 +222,35 @@ __global__ void __launch_bounds__(kNT) k_mlist(MLevel L, const int *base, int *a
 
 // One colour of a red-black Newton-Gauss-Seidel sweep over the active cells
 // (one thread per active cell of the colour).
-__global__ void __launch_bounds__(kNT) k_msmooth(MLevel L, int colour, double cap, double relax) {
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_msmooth(MLevelT<T> L, int colour, T cap, T relax) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   const long long n = colour ? L.na - L.na0 : L.na0;
   if (t >= n) return;
   const long long c = L.act[(colour ? L.na0 : 0) + t];
-  double N, dN;
+  T N, dN;
   m_cell(L, c, N, dN);
-  double du = -relax * (N - L.f[c]) / dN;
+  T du = -relax * (N - L.f[c]) / dN;
   du = du > cap ? cap : (du < -cap ? -cap : du);
-  const double un = L.u[c] + du;
+  const T un = L.u[c] + du;
   L.u[c] = un;
-  L.b[c] = exp(un);
+  L.b[c] = m_exp(un);
 }
 
 // d = L(u) - f on the active cells (one thread per active cell; ghosts' d is
 // never read); per-block partials (sum d^2, max |d|).
-__global__ void __launch_bounds__(kNT) k_mresid(MLevel L, double *partial) {
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_mresid(MLevelT<T> L, double *partial) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   double s = 0.0, mx = 0.0;
   if (t < L.na) {
     const long long c = L.act[t];
-    double N, dN;
+    T N, dN;
     m_cell(L, c, N, dN);
-    const double d = N - L.f[c];
+    const T d = N - L.f[c];
     L.d[c] = d;
-    s = d * d;
-    mx = fabs(d);
+    s = (double)d * (double)d;
+    mx = fabs((double)d);
   }
   __shared__ double ss[kNT / 32], sm[kNT / 32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -275,13 +296,14 @@ __global__ void __launch_bounds__(kNT) k_minit(MLevel F, MLevel C) {
 
 // FAS restriction onto the active coarse cells: u^H = R u^h (all children),
 // R d^h = sum over the active children / 8; ghosts keep their values.
-__global__ void __launch_bounds__(kNT) k_mrestrict(MLevel F, MLevel C) {
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_mrestrict(MLevelT<T> F, MLevelT<T> C) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   if (t >= C.ncell) return;
   if (!(C.m[t] > 0.0)) return;
   int I, J, K;
   ijk(C, t, I, J, K);
-  double su = 0.0, sd = 0.0;
+  T su = T(0), sd = T(0);
 #pragma unroll
   for (int q = 0; q < 8; q++) {
     const long long c = ((long long)(2 * K + (q >> 2)) * F.n1 + 2 * J + ((q >> 1) & 1)) * F.n0 +
@@ -289,21 +311,22 @@ __global__ void __launch_bounds__(kNT) k_mrestrict(MLevel F, MLevel C) {
     su += F.u[c];
     if (F.m[c] > 0.0) sd += F.d[c];
   }
-  C.uR[t] = 0.125 * su;
-  C.u[t] = 0.125 * su;
-  C.b[t] = exp(0.125 * su);
-  C.d[t] = 0.125 * sd;
+  C.uR[t] = T(0.125) * su;
+  C.u[t] = T(0.125) * su;
+  C.b[t] = m_exp(T(0.125) * su);
+  C.d[t] = T(0.125) * sd;
 }
 
 // f^H = L^H(R u^h) - R d^h on the active coarse cells (after k_mrestrict).
-__global__ void __launch_bounds__(kNT) k_mfas(MLevel C) {
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_mfas(MLevelT<T> C) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   if (t >= C.ncell) return;
   if (!(C.m[t] > 0.0)) {
-    C.f[t] = 0.0;
+    C.f[t] = T(0);
     return;
   }
-  double N, dN;
+  T N, dN;
   m_cell(C, t, N, dN);
   C.f[t] = N - C.d[t];
 }
@@ -311,7 +334,8 @@ __global__ void __launch_bounds__(kNT) k_mfas(MLevel C) {
 // u^h += P e^H on the active fine cells (one thread per active cell), e^H =
 // u^H - R u^h on active coarse cells and 0 on masked ones and outside the box
 // (trilinear 27/9/3/1).
-__global__ void __launch_bounds__(kNT) k_mprolong(MLevel F, MLevel C) {
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_mprolong(MLevelT<T> F, MLevelT<T> C) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   if (t >= F.na) return;
   const long long c = F.act[t];
@@ -319,7 +343,7 @@ __global__ void __launch_bounds__(kNT) k_mprolong(MLevel F, MLevel C) {
   ijk(F, c, i, j, k);
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   const int di = (i & 1) ? 1 : -1, dj = (j & 1) ? 1 : -1, dk = (k & 1) ? 1 : -1;
-  double acc = 0.0;
+  T acc = T(0);
 #pragma unroll
   for (int q = 0; q < 8; q++) {
     const int ii = I + ((q & 1) ? di : 0), jj = J + (((q >> 1) & 1) ? dj : 0),
@@ -327,30 +351,31 @@ __global__ void __launch_bounds__(kNT) k_mprolong(MLevel F, MLevel C) {
     if (ii < 0 || ii >= C.n0 || jj < 0 || jj >= C.n1 || kk < 0 || kk >= C.n2) continue;
     const long long cc = ((long long)kk * C.n1 + jj) * C.n0 + ii;
     if (!(C.m[cc] > 0.0)) continue;
-    const double w = ((q & 1) ? 0.25 : 0.75) * (((q >> 1) & 1) ? 0.25 : 0.75) *
-                     ((q >> 2) ? 0.25 : 0.75);
+    const T w = T(((q & 1) ? 0.25 : 0.75) * (((q >> 1) & 1) ? 0.25 : 0.75) *
+                  ((q >> 2) ? 0.25 : 0.75));
     acc += w * (C.u[cc] - C.uR[cc]);
   }
-  const double un = F.u[c] + acc;
+  const T un = F.u[c] + acc;
   F.u[c] = un;
-  F.b[c] = exp(un);
+  F.b[c] = m_exp(un);
 }
 
 // Coarsest level, one block: red-black sweeps until the rms over the active
 // cells falls to max(1e-3 of its value before the first sweep, 0.1 tol), at
 // most 500 sweeps.
 constexpr int kCoNT = 1024;
-__global__ void __launch_bounds__(kCoNT) k_mcoarsest(MLevel L, long long nact, double tol,
-                                                     double cap, double relax) {
+template <typename T>
+__global__ void __launch_bounds__(kCoNT) k_mcoarsest(MLevelT<T> L, long long nact, double tol,
+                                                     T cap, T relax) {
   __shared__ double red[kCoNT / 32];
   __shared__ double tot;
   auto rms = [&]() -> double {
     double s = 0.0;
     for (long long c = threadIdx.x; c < L.ncell; c += kCoNT) {
       if (!(L.m[c] > 0.0)) continue;
-      double N, dN;
+      T N, dN;
       m_cell(L, c, N, dN);
-      const double d = N - L.f[c];
+      const double d = (double)(N - L.f[c]);
       s += d * d;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -374,13 +399,13 @@ __global__ void __launch_bounds__(kCoNT) k_mcoarsest(MLevel L, long long nact, d
         int i, j, k;
         ijk(L, c, i, j, k);
         if (((i + j + k) & 1) != colour) continue;
-        double N, dN;
+        T N, dN;
         m_cell(L, c, N, dN);
-        double du = -relax * (N - L.f[c]) / dN;
+        T du = -relax * (N - L.f[c]) / dN;
         du = du > cap ? cap : (du < -cap ? -cap : du);
-        const double un = L.u[c] + du;
+        const T un = L.u[c] + du;
         L.u[c] = un;
-        L.b[c] = exp(un);
+        L.b[c] = m_exp(un);
       }
       __syncthreads();
     }
@@ -399,6 +424,27 @@ __global__ void __launch_bounds__(kNT) k_mflags(MLevel L, unsigned long long *fl
   if (i == 0 || j == 0 || k == 0 || i == L.n0 - 1 || j == L.n1 - 1 || k == L.n2 - 1)
     atomicOr(&flags[0], 1ull);
   atomicAdd(&flags[1], 1ull);
+}
+
+// First phase of a mixed-precision solve: an FP32 copy of a level (iterate,
+// exponential cache, zero right-hand side) ...
+__global__ void __launch_bounds__(kNT) k_mto32(MLevel D, MLevelT<float> S) {
+  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (c >= D.ncell) return;
+  const float v = (float)D.u[c];
+  S.u[c] = v;
+  S.b[c] = expf(v);
+  S.f[c] = 0.0f;
+}
+
+// ... and its result back on the active cells of the FP64 finest level.
+__global__ void __launch_bounds__(kNT) k_mto64(MLevelT<float> S, MLevel D) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= D.na) return;
+  const long long c = D.act[t];
+  const double v = (double)S.u[c];
+  D.u[c] = v;
+  D.b[c] = exp(v);
 }
 
 // Flags of the inputs: [0] a mask outside [-1, 1] or NaN, [1] a non-finite
@@ -446,17 +492,19 @@ struct MArena {
   }
 };
 
+template <typename T>
 struct MSolver {
   frmg_ctx *ctx;
   cudaStream_t st;
-  std::vector<MLevel> lev;
+  std::vector<MLevelT<T>> lev;
   int pre, post;
-  double cap, relax, tol;
+  T cap, relax;
+  double tol;
   double *partial;  // per-block (sum d^2, max |d|) of the finest level
   double *host;     // pinned staging of the partials
   long long nact0;  // active cells of the finest level
 
-  void smooth(MLevel &L, int n) {
+  void smooth(MLevelT<T> &L, int n) {
     for (int s = 0; s < n; s++)
       for (int colour = 0; colour < 2; colour++) {
         k_msmooth<<<(unsigned)nblk(std::max(colour ? L.na - L.na0 : L.na0, 1ll)), kNT, 0, st>>>(
@@ -465,7 +513,7 @@ struct MSolver {
       }
   }
   // rms over the active cells of level L (and its max |d|); host sync
-  double rms(MLevel &L, long long nact, double *dmax) {
+  double rms(MLevelT<T> &L, long long nact, double *dmax) {
     const long long nb = nblk(std::max(L.na, 1ll));
     k_mresid<<<(unsigned)nb, kNT, 0, st>>>(L, partial);
     MLAUNCH(ctx);
@@ -479,18 +527,18 @@ struct MSolver {
     if (dmax) *dmax = mx;
     return std::sqrt(s / (double)std::max(nact, 1ll));
   }
-  void coarsest(MLevel &L, long long nact) {
+  void coarsest(MLevelT<T> &L, long long nact) {
     k_mcoarsest<<<1, kCoNT, 0, st>>>(L, nact, tol, cap, relax);
     MLAUNCH(ctx);
   }
   std::vector<long long> nact;
   void vcycle(int l) {
-    MLevel &L = lev[l];
+    MLevelT<T> &L = lev[l];
     if (l == (int)lev.size() - 1) {
       coarsest(L, nact[l]);
       return;
     }
-    MLevel &C = lev[l + 1];
+    MLevelT<T> &C = lev[l + 1];
     smooth(L, pre);
     k_mresid<<<(unsigned)nblk(std::max(L.na, 1ll)), kNT, 0, st>>>(L, partial);
     MLAUNCH(ctx);
@@ -556,7 +604,8 @@ extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const doubl
     if (hb[0]) throw MError{FR_EINVAL, "mask values must lie in [-1, 1]"};
     if (hb[1]) throw MError{FR_EINVAL, "non-finite (or negative) density, or non-finite u"};
     // levels
-    MSolver S{ctx, st, {}, o.pre, o.post, o.newton_step_cap, o.relax, tol, nullptr, nullptr, 0, {}};
+    MSolver<double> S{ctx,    st,      {}, o.pre, o.post, o.newton_step_cap, o.relax, tol,
+                      nullptr, nullptr, 0,  {}};
     auto make = [&](int n0, int n1, int n2, double hl, double *u, const double *m,
                     const double *rho) {
       MLevel L;
@@ -654,6 +703,66 @@ extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const doubl
     sv.res0_rms = r;
     if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = r;
     int status = FR_OK;
+    const bool mixed = o.prec == FR_MIXED;
+    if (mixed && r > tol) {
+      // first phase: FP32 V-cycles of the same scheme from the same start,
+      // until their residual stalls (ratio >= 0.75), grows past 3x its best,
+      // or falls to 1e-6 of the start or to tol
+      MSolver<float> S32{ctx, st, {}, o.pre, o.post, (float)o.newton_step_cap, (float)o.relax,
+                         tol, S.partial, S.host, S.nact0, S.nact};
+      for (const MLevel &D : S.lev) {
+        MLevelT<float> F;
+        F.u = A.get<float>(D.ncell);
+        F.b = A.get<float>(D.ncell);
+        F.f = A.get<float>(D.ncell);
+        F.uR = A.get<float>(D.ncell);
+        F.d = A.get<float>(D.ncell);
+        F.m = D.m;
+        F.rho = D.rho;
+        F.ub = D.ub;
+        F.act = D.act;
+        F.na0 = D.na0;
+        F.na = D.na;
+        F.n0 = D.n0;
+        F.n1 = D.n1;
+        F.n2 = D.n2;
+        F.ncell = D.ncell;
+        F.fd0 = D.fd0;
+        F.fd1 = D.fd1;
+        F.ah = (float)D.ah;
+        F.beta = (float)D.beta;
+        F.gamma = (float)D.gamma;
+        k_mto32<<<(unsigned)nblk(D.ncell), kNT, 0, st>>>(D, F);
+        MLAUNCH(ctx);
+        S32.lev.push_back(F);
+      }
+      const double r0 = r;
+      double rp = r, best = r;
+      bool ok = false;
+      while (sv.vcycles < o.max_vcycles) {
+        S32.vcycle(0);
+        sv.vcycles++;
+        double m32 = 0.0;
+        const double rn = S32.rms(S32.lev[0], S.nact0, &m32);
+        if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = rn;
+        if (!(rn == rn)) {  // keep the FP64 start
+          ok = false;
+          break;
+        }
+        ok = true;
+        const bool stop = rn <= tol || rn <= 1e-6 * r0 || rn >= 0.75 * rp || rn > 3.0 * best;
+        rp = rn;
+        best = std::min(best, rn);
+        if (stop) break;
+      }
+      if (ok) {
+        k_mto64<<<(unsigned)nblk(std::max(S.lev[0].na, 1ll)), kNT, 0, st>>>(S32.lev[0], S.lev[0]);
+        MLAUNCH(ctx);
+        r = S.rms(S.lev[0], S.nact0, &dmax);
+        if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = -r;
+        sv.outer++;
+      }
+    }
     while (r > tol) {
       if (sv.vcycles >= o.max_vcycles) {
         status = FR_ENOCONV;
@@ -662,7 +771,8 @@ extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const doubl
       S.vcycle(0);
       sv.vcycles++;
       r = S.rms(S.lev[0], S.nact0, &dmax);
-      if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = r;
+      if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = mixed ? -r : r;
+      if (mixed) sv.outer++;
       if (!(r == r)) {
         status = FR_EDIVERGED;
         break;

@@ -146,3 +146,43 @@ def test_invalid_regions_rejected(C):
         C.solve_masked(dev(r), dev(m), dev(u0), h=1.0 / 64, **P)
     with pytest.raises(frmg.FRError):
         C.solve_masked(dev(rho), dev(m), dev(u0), h=-1.0, **P)
+
+
+@pytest.mark.parametrize("n,seed", [(32, 7), (24, 8)])
+def test_mixed_precision_reaches_the_oracle_solution(C, n, seed):
+    """prec='mixed': FP32 V-cycles of the same scheme, then FP64 ones; the
+    FP64 residual meets tol and the solution is the oracle's (the unique
+    discrete solution), with the ghosts untouched."""
+    m, u0, rho = _blob_region(n, seed)
+    h = 1.0 / (4 * n)
+    ref = M.solve(u0, m, rho, h=h, tol=1e-11, **P)
+    assert ref.converged
+    u = dev(u0)
+    st, s = C.solve_masked(dev(rho), dev(m), u, h=h, tol=1e-10, prec="mixed", **P)
+    assert st == 0 and s.res_rms <= 1e-10 and s.outer >= 1
+    hist = list(s.hist[: s.nhist])
+    # first entry the FP64 start, then FP32 cycles (positive), then FP64
+    # evaluations (negated)
+    k = next(i for i, v in enumerate(hist) if v < 0)
+    assert k >= 2 and all(v > 0 for v in hist[:k]) and all(v < 0 for v in hist[k:])
+    assert -hist[-1] == pytest.approx(s.res_rms, rel=1e-12)
+    got = host(u)
+    act = m > 0
+    assert np.abs(got[act] - ref.u[act]).max() < 1e-9
+    assert np.array_equal(got[~act], u0[~act])
+
+
+def test_mixed_precision_equals_fp64_solve_on_sphere_union(C):
+    """A union of spheres in a 64^3 box (the masked bench recipe, smaller):
+    the mixed and the FP64 solves reach the same solution."""
+    from paper_1110_1379_gb300 import synth
+    n = 64
+    rho = synth.lognormal_density((n, n, n), 77, sigma=1.5)
+    m = synth.sphere_union_mask(rho, 6, (4, 10), 78, margin=6)
+    h = 1.0 / (2 * n)
+    u64, umx = dev(np.zeros_like(rho)), dev(np.zeros_like(rho))
+    st, s = C.solve_masked(dev(rho), dev(m), u64, h=h, tol=1e-9, **P)
+    st2, s2 = C.solve_masked(dev(rho), dev(m), umx, h=h, tol=1e-9, prec="mixed", **P)
+    assert st == 0 and st2 == 0 and s2.res_rms <= 1e-9
+    act = m > 0
+    assert np.abs(host(u64)[act] - host(umx)[act]).max() < 1e-8
