@@ -63,8 +63,8 @@ ALG_BYTES = {
 # profiles/ (384^3 launches; traffic grows in proportion to the cells, so it is
 # scaled to the workload's grid).  Valid for the kernels as captured there.
 TRAFFIC_PER_CELL = {
-    "smooth_f32@fine": (1117.662e6 / 384 ** 3, "profiles/smooth_rb_f32_384.md"),
-    "smooth_bg_f32@fine": (1639.797e6 / 384 ** 3, "profiles/smooth_rb_bg_f32_384.md"),
+    "smooth_f32@fine": (1120.145e6 / 384 ** 3, "profiles/smooth_rb_f32_384.md"),
+    "smooth_bg_f32@fine": (1640.735e6 / 384 ** 3, "profiles/smooth_rb_bg_f32_384.md"),
     "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "profiles/resid_restrict_tiled_f32_384.md"),
     "prolong_f32@fine": (678.570e6 / 384 ** 3, "profiles/prolong_tiled_f32_384.md"),
     "df_defect": (2466.320e6 / 384 ** 3, "profiles/df_defect_384.md"),
@@ -94,11 +94,15 @@ def parse_args():
 
 
 def parse_options(text):
-    """'k=v,k=v' -> dict of solver options (ints where the value is integral)."""
+    """'k=v,k=v' -> dict of solver options (ints where the value is integral,
+    prec as its name)."""
     out = {}
     for item in filter(None, (t.strip() for t in text.split(","))):
-        k, v = item.split("=")
-        out[k.strip()] = int(v) if v.strip().lstrip("-").isdigit() else float(v)
+        k, v = (t.strip() for t in item.split("="))
+        if k == "prec":
+            out[k] = v
+        else:
+            out[k] = int(v) if v.lstrip("-").isdigit() else float(v)
     return out
 
 
@@ -422,7 +426,10 @@ def run_secondary(args):
         # throughout, or FP32 V-cycles finished in FP64)
         mcands = [dict(c, prec=p) for p in ("fp64", "mixed")
                   for c in SHAPE_CANDIDATES + [dict(pre=3, post=3, relax=1.25)]]
-        mopts, mtimes = pick_options(run, mcands)
+        if args.options:  # a fixed setting instead (profiling runs)
+            mopts, mtimes = parse_options(args.options), {}
+        else:
+            mopts, mtimes = pick_options(run, mcands)
         t = timed(lambda: run(**mopts), args.steps, args.warmup)
         s = stats[-1]
         # CPU oracle: the same recipe on a 48^3 box (bounded sample)
@@ -432,13 +439,14 @@ def run_secondary(args):
         t0 = time.perf_counter()
         ro = OM.solve(np.zeros_like(rs), ms, rs, h=1.0 / (2 * ns), tol=TOL, **PM)
         t_or = time.perf_counter() - t0
-        fp64_best = min(v for k, v in mtimes.items() if k.endswith("fp64"))
+        fp64_times = [v for k, v in mtimes.items() if k.endswith("fp64")]
+        fp64_best = min(fp64_times) if fp64_times else None
         line.update(metric="general mask scheme: FAS solve of an irregular refinement region "
                            "(union of spheres in a 256^3 box), FP64-accurate residual: "
                            "active cells/s to rms 1e-8",
                     value=active / t, ms=1e3 * t, active_cells=active, box_cells=n ** 3,
                     vcycles=s.vcycles, outer=s.outer, res_rms=s.res_rms,
-                    fp64_only_ms=1e3 * fp64_best,
+                    fp64_only_ms=None if fp64_best is None else 1e3 * fp64_best,
                     dtype="f32+f64 (mixed)" if mopts.get("prec") == "mixed" else "f64",
                     oracle_48_active_cells_per_s=int((ms > 0).sum()) / t_or,
                     oracle_48_vcycles=ro.cycles, tuned={**mopts, "candidates_s": mtimes})
