@@ -375,12 +375,16 @@ int fr_poisson_source(frmg_ctx *ctx, const double *density, const double *u, con
  * opts->prec = FR_FP64: every step in FP64.  FR_MIXED: the same V-cycles in
  * FP32 first (mask, density and ghost boundary values read from the FP64
  * copies), until their residual stalls (ratio >= 0.75 per cycle), grows past
- * three times its best, or falls to 1e-6 of its start or to tol; then FP64
- * V-cycles from that iterate until tol (a non-finite FP32 residual discards
- * the FP32 phase).  The convergence test is always the FP64 residual.
+ * three times its best, or falls to 1e-6 of its start or to tol (a
+ * non-finite FP32 residual discards this phase); then outer steps: the FP64
+ * residual d, opts->inner_cycles FP32 V-cycles of the correction form
+ * L(g + v) - L(g) = -d (g the FP64 iterate rounded to FP32), u += v; a step
+ * that does not halve the FP64 residual hands over to FP64 V-cycles.  The
+ * convergence test is always the FP64 residual.
  * stats: vcycles (both phases), res0_rms, res_rms, res_max, seconds, hist (the
- * rms after each V-cycle; mixed: FP32 values, then the FP64 values negated),
- * outer (mixed: FP64 residual evaluations after the FP32 phase).
+ * rms after each V-cycle; mixed: the FP32 phase's values, then the FP64
+ * residual (negated) after each outer step and FP64 V-cycle), outer (mixed:
+ * FP64 residual evaluations after the FP32 phase).
  * Synchronous on return.
  */
 int fr_solve_masked(frmg_ctx *ctx, const double *density, const double *mask, const int dims[3],

@@ -27,8 +27,10 @@
 //   and >= 4, the next level's outer layer stays masked and it keeps an
 //   active cell.
 //
-// FP64 throughout (one thread per cell), red-black Newton-Gauss-Seidel with
-// the step clamped to |du| <= cap and optionally over-relaxed.  Every level
+// FP64, or mixed (FP32 V-cycles of the full variable, then outer steps of
+// FP32 V-cycles of the correction form against the FP64 residual); red-black
+// Newton-Gauss-Seidel with the step clamped to |du| <= cap and optionally
+// over-relaxed.  Every level
 // keeps b = exp(u) beside u, written by each kernel that writes u, so an
 // operator evaluation takes one exponential (e^{-u_i/2}) plus one per ghost
 // face instead of eight: FP64 exponentials are the cost of these kernels.
@@ -74,12 +76,16 @@ constexpr int kNT = 256;
 long long nblk(long long n) { return (n + kNT - 1) / kNT; }
 
 // One level of a masked region, iterate and work arrays in T (FP64, or FP32
-// for the first phase of a mixed-precision solve); the mask, density and
-// ghost boundary values are always the FP64 level's.
-template <typename T>
+// in a mixed-precision solve); the mask, density and ghost boundary values are
+// always the FP64 level's.  BG: the correction form of the outer steps of a
+// mixed solve, whose unknown is the correction v to a background (the FP64
+// iterate rounded to FP32) and whose operator is L(background + v) -
+// L(background), evaluated without forming either term.
+template <typename T, bool BG = false>
 struct MLevelT {
-  T *u;             // iterate in active cells, fixed ghost values elsewhere
-  T *b;             // exp(u) of every cell, rewritten wherever u changes
+  T *u;             // iterate (BG: correction v) in active cells; fixed ghost values
+                    // (BG: 0) elsewhere
+  T *b;             // exp(u) (BG: expm1(v)) of every cell, rewritten wherever u changes
   const double *m;  // mask
   const double *rho;
   T *f;             // FAS right-hand side (0 on the finest level)
@@ -93,14 +99,24 @@ struct MLevelT {
   FastDiv fd0, fd1;
   T ah;             // alpha / 2 at this level's h
   T beta, gamma;
+  T *bgu, *bgE;     // BG: background value and its exponential per cell
 };
 using MLevel = MLevelT<double>;
 
 __device__ __forceinline__ double m_exp(double v) { return exp(v); }
 __device__ __forceinline__ float m_exp(float v) { return expf(v); }
+// the per-cell cache of a new value
+template <typename T, bool BG>
+__device__ __forceinline__ T m_cache(T v) {
+  if constexpr (BG)
+    return expm1f(v);
+  else
+    return m_exp(v);
+}
 
-template <typename T>
-__device__ __forceinline__ void ijk(const MLevelT<T> &L, long long c, int &i, int &j, int &k) {
+template <typename T, bool BG>
+__device__ __forceinline__ void ijk(const MLevelT<T, BG> &L, long long c, int &i, int &j,
+                                    int &k) {
   const unsigned cu = (unsigned)c, q = fdiv(cu, L.fd0), q2 = fdiv(q, L.fd1);
   i = (int)(cu - q * (unsigned)L.n0);
   j = (int)(q - q2 * (unsigned)L.n1);
@@ -108,8 +124,8 @@ __device__ __forceinline__ void ijk(const MLevelT<T> &L, long long c, int &i, in
 }
 
 // neighbour offset of face f (-x, +x, -y, +y, -z, +z)
-template <typename T>
-__device__ __forceinline__ long long face_step(const MLevelT<T> &L, int f) {
+template <typename T, bool BG>
+__device__ __forceinline__ long long face_step(const MLevelT<T, BG> &L, int f) {
   const long long s = f < 2 ? 1 : (f < 4 ? (long long)L.n0 : (long long)L.n0 * L.n1);
   return (f & 1) ? s : -s;
 }
@@ -118,8 +134,43 @@ __device__ __forceinline__ long long face_step(const MLevelT<T> &L, int f) {
 // exponentials of the cell and of its active neighbours come from the cache b.
 // In FP32 the mass term's e^{-u/2} - 1 is formed by expm1f (no cancellation
 // near u = 0).
-template <typename T>
-__device__ __forceinline__ void m_cell(const MLevelT<T> &L, long long c, T &N, T &dN) {
+template <typename T, bool BG>
+__device__ __forceinline__ void m_cell(const MLevelT<T, BG> &L, long long c, T &N, T &dN) {
+  if constexpr (BG) {
+    // correction form: with B = E (1 + x) = e^{background + v}, a regular face
+    // adds (E_i x_i + E_j x_j) g + (B_i + B_j) e (g, e the background and
+    // correction differences); a ghost face has background value
+    // u_b - r u_b + r ubg_i and correction r v_i; the mass term is
+    // beta e^{-ubg_i/2} (e^{-v_i/2} - 1); the density term cancels
+    const T vi = L.u[c], xi = L.b[c], mi = (T)L.m[c];
+    const T gi = L.bgu[c], Ei = L.bgE[c];
+    const T Bi = Ei + Ei * xi;
+    T acc = T(0), dacc = T(0);
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+      const long long cj = c + face_step(L, f);
+      const double mjd = L.m[cj];
+      if (mjd > 0.0) {
+        const T vj = L.u[cj], xj = L.b[cj], Ej = L.bgE[cj];
+        const T Bj = Ej + Ej * xj;
+        const T g = L.bgu[cj] - gi, e = vj - vi;
+        acc += (Ei * xi + Ej * xj) * g + (Bi + Bj) * e;
+        dacc += Bi * (g + e) - (Bi + Bj);
+      } else {
+        const T r = (T)mjd / mi, ub = (T)L.ub[f * L.ncell + c];
+        const T gg = ub - r * ub + r * gi, Eg = m_exp(gg);
+        const T vg = r * vi, xg = expm1f(vg);
+        const T Bg = Eg + Eg * xg;
+        const T g = gg - gi, e = vg - vi;
+        acc += (Ei * xi + Eg * xg) * g + (Bi + Bg) * e;
+        dacc += (Bi + r * Bg) * (g + e) + (Bi + Bg) * (r - T(1));
+      }
+    }
+    const T F = rsqrtf(Ei), em = expm1f(-0.5f * vi);
+    N = L.ah * acc + L.beta * F * em;
+    dN = L.ah * dacc - T(0.5) * L.beta * F * (em + T(1));
+    return;
+  }
   const T ui = L.u[c], mi = (T)L.m[c];
   const T bi = L.b[c];
   T acc = T(0), dacc = T(0);
@@ -222,8 +273,8 @@ __global__ void __launch_bounds__(kNT) k_mlist(MLevel L, const int *base, int *a
 
 // One colour of a red-black Newton-Gauss-Seidel sweep over the active cells
 // (one thread per active cell of the colour).
-template <typename T>
-__global__ void __launch_bounds__(kNT) k_msmooth(MLevelT<T> L, int colour, T cap, T relax) {
+template <typename T, bool BG>
+__global__ void __launch_bounds__(kNT) k_msmooth(MLevelT<T, BG> L, int colour, T cap, T relax) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   const long long n = colour ? L.na - L.na0 : L.na0;
   if (t >= n) return;
@@ -234,13 +285,13 @@ __global__ void __launch_bounds__(kNT) k_msmooth(MLevelT<T> L, int colour, T cap
   du = du > cap ? cap : (du < -cap ? -cap : du);
   const T un = L.u[c] + du;
   L.u[c] = un;
-  L.b[c] = m_exp(un);
+  L.b[c] = m_cache<T, BG>(un);
 }
 
 // d = L(u) - f on the active cells (one thread per active cell; ghosts' d is
 // never read); per-block partials (sum d^2, max |d|).
-template <typename T>
-__global__ void __launch_bounds__(kNT) k_mresid(MLevelT<T> L, double *partial) {
+template <typename T, bool BG>
+__global__ void __launch_bounds__(kNT) k_mresid(MLevelT<T, BG> L, double *partial) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   double s = 0.0, mx = 0.0;
   if (t < L.na) {
@@ -296,8 +347,8 @@ __global__ void __launch_bounds__(kNT) k_minit(MLevel F, MLevel C) {
 
 // FAS restriction onto the active coarse cells: u^H = R u^h (all children),
 // R d^h = sum over the active children / 8; ghosts keep their values.
-template <typename T>
-__global__ void __launch_bounds__(kNT) k_mrestrict(MLevelT<T> F, MLevelT<T> C) {
+template <typename T, bool BG>
+__global__ void __launch_bounds__(kNT) k_mrestrict(MLevelT<T, BG> F, MLevelT<T, BG> C) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   if (t >= C.ncell) return;
   if (!(C.m[t] > 0.0)) return;
@@ -313,13 +364,13 @@ __global__ void __launch_bounds__(kNT) k_mrestrict(MLevelT<T> F, MLevelT<T> C) {
   }
   C.uR[t] = T(0.125) * su;
   C.u[t] = T(0.125) * su;
-  C.b[t] = m_exp(T(0.125) * su);
+  C.b[t] = m_cache<T, BG>(T(0.125) * su);
   C.d[t] = T(0.125) * sd;
 }
 
 // f^H = L^H(R u^h) - R d^h on the active coarse cells (after k_mrestrict).
-template <typename T>
-__global__ void __launch_bounds__(kNT) k_mfas(MLevelT<T> C) {
+template <typename T, bool BG>
+__global__ void __launch_bounds__(kNT) k_mfas(MLevelT<T, BG> C) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   if (t >= C.ncell) return;
   if (!(C.m[t] > 0.0)) {
@@ -334,8 +385,8 @@ __global__ void __launch_bounds__(kNT) k_mfas(MLevelT<T> C) {
 // u^h += P e^H on the active fine cells (one thread per active cell), e^H =
 // u^H - R u^h on active coarse cells and 0 on masked ones and outside the box
 // (trilinear 27/9/3/1).
-template <typename T>
-__global__ void __launch_bounds__(kNT) k_mprolong(MLevelT<T> F, MLevelT<T> C) {
+template <typename T, bool BG>
+__global__ void __launch_bounds__(kNT) k_mprolong(MLevelT<T, BG> F, MLevelT<T, BG> C) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
   if (t >= F.na) return;
   const long long c = F.act[t];
@@ -357,15 +408,15 @@ __global__ void __launch_bounds__(kNT) k_mprolong(MLevelT<T> F, MLevelT<T> C) {
   }
   const T un = F.u[c] + acc;
   F.u[c] = un;
-  F.b[c] = m_exp(un);
+  F.b[c] = m_cache<T, BG>(un);
 }
 
 // Coarsest level, one block: red-black sweeps until the rms over the active
 // cells falls to max(1e-3 of its value before the first sweep, 0.1 tol), at
 // most 500 sweeps.
 constexpr int kCoNT = 1024;
-template <typename T>
-__global__ void __launch_bounds__(kCoNT) k_mcoarsest(MLevelT<T> L, long long nact, double tol,
+template <typename T, bool BG>
+__global__ void __launch_bounds__(kCoNT) k_mcoarsest(MLevelT<T, BG> L, long long nact, double tol,
                                                      T cap, T relax) {
   __shared__ double red[kCoNT / 32];
   __shared__ double tot;
@@ -405,7 +456,7 @@ __global__ void __launch_bounds__(kCoNT) k_mcoarsest(MLevelT<T> L, long long nac
         du = du > cap ? cap : (du < -cap ? -cap : du);
         const T un = L.u[c] + du;
         L.u[c] = un;
-        L.b[c] = m_exp(un);
+        L.b[c] = m_cache<T, BG>(un);
       }
       __syncthreads();
     }
@@ -443,6 +494,51 @@ __global__ void __launch_bounds__(kNT) k_mto64(MLevelT<float> S, MLevel D) {
   if (t >= D.na) return;
   const long long c = D.act[t];
   const double v = (double)S.u[c];
+  D.u[c] = v;
+  D.b[c] = exp(v);
+}
+
+// Outer step of a mixed solve, finest level: background = the FP64 iterate
+// rounded to FP32 (every cell), its exponential, correction 0, right-hand side
+// -d (d the FP64 residual, active cells).
+__global__ void __launch_bounds__(kNT) k_mbg_fine(MLevel D, MLevelT<float, true> S) {
+  const long long c = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (c >= D.ncell) return;
+  const float g = (float)D.u[c];
+  S.bgu[c] = g;
+  S.bgE[c] = expf(g);
+  S.u[c] = 0.0f;
+  S.b[c] = 0.0f;
+  S.f[c] = D.m[c] > 0.0 ? -(float)D.d[c] : 0.0f;
+}
+
+// ... coarser levels: background the mean of the 8 children's, correction 0.
+__global__ void __launch_bounds__(kNT) k_mbg_coarse(MLevelT<float, true> F,
+                                                    MLevelT<float, true> C) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= C.ncell) return;
+  int I, J, K;
+  ijk(C, t, I, J, K);
+  float sg = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const long long c = ((long long)(2 * K + (q >> 2)) * F.n1 + 2 * J + ((q >> 1) & 1)) * F.n0 +
+                        2 * I + (q & 1);
+    sg += F.bgu[c];
+  }
+  const float g = 0.125f * sg;
+  C.bgu[t] = g;
+  C.bgE[t] = expf(g);
+  C.u[t] = 0.0f;
+  C.b[t] = 0.0f;
+}
+
+// u += v on the active cells of the FP64 finest level, and its exponential.
+__global__ void __launch_bounds__(kNT) k_madd64(MLevelT<float, true> S, MLevel D) {
+  const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (t >= D.na) return;
+  const long long c = D.act[t];
+  const double v = D.u[c] + (double)S.u[c];
   D.u[c] = v;
   D.b[c] = exp(v);
 }
@@ -492,11 +588,11 @@ struct MArena {
   }
 };
 
-template <typename T>
+template <typename T, bool BG = false>
 struct MSolver {
   frmg_ctx *ctx;
   cudaStream_t st;
-  std::vector<MLevelT<T>> lev;
+  std::vector<MLevelT<T, BG>> lev;
   int pre, post;
   T cap, relax;
   double tol;
@@ -504,7 +600,7 @@ struct MSolver {
   double *host;     // pinned staging of the partials
   long long nact0;  // active cells of the finest level
 
-  void smooth(MLevelT<T> &L, int n) {
+  void smooth(MLevelT<T, BG> &L, int n) {
     for (int s = 0; s < n; s++)
       for (int colour = 0; colour < 2; colour++) {
         k_msmooth<<<(unsigned)nblk(std::max(colour ? L.na - L.na0 : L.na0, 1ll)), kNT, 0, st>>>(
@@ -513,7 +609,7 @@ struct MSolver {
       }
   }
   // rms over the active cells of level L (and its max |d|); host sync
-  double rms(MLevelT<T> &L, long long nact, double *dmax) {
+  double rms(MLevelT<T, BG> &L, long long nact, double *dmax) {
     const long long nb = nblk(std::max(L.na, 1ll));
     k_mresid<<<(unsigned)nb, kNT, 0, st>>>(L, partial);
     MLAUNCH(ctx);
@@ -527,18 +623,18 @@ struct MSolver {
     if (dmax) *dmax = mx;
     return std::sqrt(s / (double)std::max(nact, 1ll));
   }
-  void coarsest(MLevelT<T> &L, long long nact) {
+  void coarsest(MLevelT<T, BG> &L, long long nact) {
     k_mcoarsest<<<1, kCoNT, 0, st>>>(L, nact, tol, cap, relax);
     MLAUNCH(ctx);
   }
   std::vector<long long> nact;
   void vcycle(int l) {
-    MLevelT<T> &L = lev[l];
+    MLevelT<T, BG> &L = lev[l];
     if (l == (int)lev.size() - 1) {
       coarsest(L, nact[l]);
       return;
     }
-    MLevelT<T> &C = lev[l + 1];
+    MLevelT<T, BG> &C = lev[l + 1];
     smooth(L, pre);
     k_mresid<<<(unsigned)nblk(std::max(L.na, 1ll)), kNT, 0, st>>>(L, partial);
     MLAUNCH(ctx);
@@ -625,6 +721,7 @@ extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const doubl
       L.ub = A.get<double>(6 * L.ncell);
       L.act = nullptr;  // set once the level set is final
       L.na0 = L.na = 0;
+      L.bgu = L.bgE = nullptr;
       L.ah = 0.5 * alpha * (h * h) / (hl * hl);
       L.beta = k6[1];
       L.gamma = k6[2];
@@ -732,6 +829,7 @@ extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const doubl
         F.ah = (float)D.ah;
         F.beta = (float)D.beta;
         F.gamma = (float)D.gamma;
+        F.bgu = F.bgE = nullptr;
         k_mto32<<<(unsigned)nblk(D.ncell), kNT, 0, st>>>(D, F);
         MLAUNCH(ctx);
         S32.lev.push_back(F);
@@ -761,6 +859,64 @@ extern "C" int fr_solve_masked(frmg_ctx *ctx, const double *density, const doubl
         r = S.rms(S.lev[0], S.nact0, &dmax);
         if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = -r;
         sv.outer++;
+        // outer steps: opts->inner_cycles FP32 V-cycles of the correction form
+        // against the FP64 residual, then u += v and the FP64 residual; a
+        // step that does not halve it (or a non-finite correction) hands over
+        // to FP64 V-cycles
+        MSolver<float, true> SB{ctx,     st,     {}, o.pre, o.post, (float)o.newton_step_cap,
+                                (float)o.relax, tol, S.partial, S.host, S.nact0, S.nact};
+        for (const MLevelT<float> &F : S32.lev) {
+          MLevelT<float, true> B;
+          B.u = F.u;
+          B.b = F.b;
+          B.m = F.m;
+          B.rho = F.rho;
+          B.f = F.f;
+          B.uR = F.uR;
+          B.d = F.d;
+          B.ub = F.ub;
+          B.act = F.act;
+          B.na0 = F.na0;
+          B.na = F.na;
+          B.n0 = F.n0;
+          B.n1 = F.n1;
+          B.n2 = F.n2;
+          B.ncell = F.ncell;
+          B.fd0 = F.fd0;
+          B.fd1 = F.fd1;
+          B.ah = F.ah;
+          B.beta = F.beta;
+          B.gamma = F.gamma;
+          B.bgu = A.get<float>(F.ncell);
+          B.bgE = A.get<float>(F.ncell);
+          SB.lev.push_back(B);
+        }
+        const int inner = std::max(1, o.inner_cycles);
+        double rp = r;
+        while (r > tol && sv.vcycles < o.max_vcycles) {
+          k_mbg_fine<<<(unsigned)nblk(S.lev[0].ncell), kNT, 0, st>>>(S.lev[0], SB.lev[0]);
+          MLAUNCH(ctx);
+          for (size_t l = 1; l < SB.lev.size(); l++) {
+            k_mbg_coarse<<<(unsigned)nblk(SB.lev[l].ncell), kNT, 0, st>>>(SB.lev[l - 1],
+                                                                           SB.lev[l]);
+            MLAUNCH(ctx);
+          }
+          for (int k = 0; k < inner && sv.vcycles < o.max_vcycles; k++) {
+            SB.vcycle(0);
+            sv.vcycles++;
+          }
+          double mc = 0.0;
+          const double rc = SB.rms(SB.lev[0], S.nact0, &mc);
+          if (!(rc == rc)) break;
+          k_madd64<<<(unsigned)nblk(std::max(S.lev[0].na, 1ll)), kNT, 0, st>>>(SB.lev[0],
+                                                                                 S.lev[0]);
+          MLAUNCH(ctx);
+          r = S.rms(S.lev[0], S.nact0, &dmax);
+          if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = -r;
+          sv.outer++;
+          if (!(r == r) || r > 0.5 * rp) break;
+          rp = r;
+        }
       }
     }
     while (r > tol) {
