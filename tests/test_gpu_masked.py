@@ -186,3 +186,12 @@ def test_mixed_precision_equals_fp64_solve_on_sphere_union(C):
     assert st == 0 and st2 == 0 and s2.res_rms <= 1e-9
     act = m > 0
     assert np.abs(host(u64)[act] - host(umx)[act]).max() < 1e-8
+
+
+def test_mixed_precision_respects_the_cycle_limit(C):
+    """The V-cycle limit counts the FP32 and the FP64 cycles together."""
+    from paper_1110_1379_gb300 import frmg
+    m, u0, rho = _blob_region(16, 14)
+    st, s = C.solve_masked(dev(rho), dev(m), dev(u0), h=1.0 / 64, tol=1e-14, max_vcycles=3,
+                           prec="mixed", **P)
+    assert st == frmg.FR_ENOCONV and s.vcycles == 3
