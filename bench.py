@@ -87,9 +87,10 @@ def parse_args():
                              "masked256"],
                     help="secondary workloads print their own line (default: the 512^3 solve)")
     ap.add_argument("--options", default="",
-                    help="solver options for the headline solve instead of fr_autotune, "
-                         "e.g. pre=1,post=1,relax=1.15,fmg=1 (reproduces a tuned run, "
-                         "warm-up solves included, for profiling)")
+                    help="solver options for the headline solve instead of fr_autotune "
+                         "(and for the levels256 and masked256 workloads instead of their "
+                         "untimed search), e.g. pre=1,post=1,relax=1.15,fmg=1 (reproduces a "
+                         "tuned run, warm-up solves included, for profiling)")
     return ap.parse_args()
 
 
@@ -284,6 +285,8 @@ def pick_options(run, cands=SHAPE_CANDIDATES):
         label = f"V({c['pre']},{c['post']}) w={c['relax']}"
         if "prec" in c:
             label += f" {c['prec']}"
+        if "tiling" in c:
+            label += f" tiling={c['tiling']}"
         times[label] = (min(ts), c)
     if not times:
         raise RuntimeError("no candidate setting converged")
@@ -317,19 +320,19 @@ def run_secondary(args):
         kw = dict(boxes=[s["box"] for s in specs], avals=[s["a"] for s in specs],
                   fr0s=[s["fr0"] for s in specs], omega_m=0.24, tol=TOL)
 
+        # every solve starts from u = 0 (initial_guess = 0: u is output only)
         def batch(prec, **opts):
-            for x in us:
-                x.zero_()
-            st, _ = ctx.solve_batch(rhos, us, prec=prec, **kw, **opts)
+            st, _ = ctx.solve_batch(rhos, us, prec=prec, initial_guess=0, **kw, **opts)
             assert st == 0
 
-        bopts, btimes = pick_options(lambda **o: batch("mixed", **o))
+        bopts, btimes = pick_options(lambda **o: batch("mixed", **o),
+                                     [dict(c, tiling=t) for t in (0, 1)
+                                      for c in SHAPE_CANDIDATES])
 
         def seq(prec):
             for r, x, s in zip(rhos, us, specs):
-                x.zero_()
                 st, _ = ctx.solve(r, x, tol=TOL, prec=prec, box=s["box"], a=s["a"],
-                                  omega_m=0.24, fr0=s["fr0"])
+                                  omega_m=0.24, fr0=s["fr0"], initial_guess=0)
                 assert st == 0
 
         t_b = shard.max_over_ranks(timed(lambda: batch("mixed", **bopts), args.steps,
@@ -352,19 +355,29 @@ def run_secondary(args):
               for p in patches]
         cells = r0.numel() + sum(p["rho"].size for p in patches)
 
+        # the domain starts from u = 0 (initial_guess = 0), every patch from
+        # its parent's interpolated solution
         def run(prec, **opts):
-            u0.zero_()
             st, _ = ctx.solve_levels(r0, u0, gp, box=256.0, a=1.0, omega_m=0.24, fr0=1e-5,
-                                     tol=TOL, prec=prec, **opts)
+                                     tol=TOL, prec=prec, initial_guess=0, **opts)
             assert st == 0
 
-        lopts, ltimes = pick_options(lambda **o: run("mixed", **o))
+        if args.options:  # a fixed setting instead (profiling runs)
+            lopts, ltimes = parse_options(args.options), {}
+        else:
+            # untimed choice of V-cycle shape, relaxation and tiling (the
+            # shared-memory kernels on the patch levels too, or only where the
+            # grids fill the GPU)
+            lopts, ltimes = pick_options(lambda **o: run("mixed", **o),
+                                         [dict(c, tiling=t) for t in (0, 1)
+                                          for c in SHAPE_CANDIDATES])
         t_m = timed(lambda: run("mixed", **lopts), args.steps, args.warmup)
-        t_64 = timed(lambda: run("fp64"), 1, 1)
+        t_64 = None if args.options else timed(lambda: run("fp64"), 1, 1)
         line.update(metric="domain 256^3 + nested patches (2x, 4x): cells/s to rms 1e-8 on every grid",
                     value=cells / t_m, cells=cells, patches=len(patches),
                     level2=sum(1 for p in patches if p["parent"] >= 0), ms=1e3 * t_m,
-                    fp64=cells / t_64, tuned={**lopts, "candidates_s": ltimes})
+                    fp64=None if t_64 is None else cells / t_64,
+                    tuned={**lopts, "candidates_s": ltimes})
     elif args.workload == "cic128":
         n = 128
         pos = torch.from_numpy(synth.zeldovich_positions(n, 2000,

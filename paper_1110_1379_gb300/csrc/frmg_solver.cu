@@ -340,10 +340,13 @@ __global__ void __launch_bounds__(256) k_prep_zero(const double *rho, double gam
 }
 
 // Integer tests on the bit pattern (no FP64 instructions): +-0 has all bits
-// but the sign clear.
+// but the sign clear.  One plain store per warp that saw a non-zero value
+// (every writer stores 1; an atomic per cell serialises on the flag when u is
+// non-zero everywhere).  Launched with a multiple of 32 threads per block.
 __global__ void k_any_nonzero(const double *u, long long n, int *flag) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n && ((unsigned long long)__double_as_longlong(u[t]) << 1) != 0) atomicExch(flag, 1);
+  const bool nz = t < n && ((unsigned long long)__double_as_longlong(u[t]) << 1) != 0;
+  if (__any_sync(0xffffffffu, nz) && (threadIdx.x & 31) == 0) *flag = 1;
 }
 
 // u += delta in FP64, x = expm1(u).
