@@ -30,10 +30,12 @@
 // FP64, or mixed (FP32 V-cycles of the full variable, then outer steps of
 // FP32 V-cycles of the correction form against the FP64 residual); red-black
 // Newton-Gauss-Seidel with the step clamped to |du| <= cap and optionally
-// over-relaxed.  Every level
-// keeps b = exp(u) beside u, written by each kernel that writes u, so an
-// operator evaluation takes one exponential (e^{-u_i/2}) plus one per ghost
-// face instead of eight: FP64 exponentials are the cost of these kernels.
+// over-relaxed.  Every level keeps b = exp(u) (correction form: expm1 of the
+// correction) beside u, written by each kernel that writes u, so an operator
+// evaluation takes one exponential (e^{-u_i/2}) plus one per ghost face
+// instead of eight.  The fine-level sweeps, residual and prolongation run
+// over per-colour lists of the active cells, so that regions covering a small
+// part of their box keep every warp busy.
 #include <cuda_runtime.h>
 
 #include <algorithm>
