@@ -86,6 +86,9 @@ struct frmg_ctx {
   // stream of solves issued on the legacy default stream (created on first use)
   cudaStream_t side = nullptr;
   cudaEvent_t side_in = nullptr, side_out = nullptr;
+  // stream of the early device-to-host copy of a mixed solve's result
+  cudaStream_t copy = nullptr;
+  cudaEvent_t copy_in = nullptr, copy_out = nullptr;
 };
 
 static cudaEvent_t ev_get(frmg_ctx *c) {
@@ -349,6 +352,13 @@ __global__ void k_any_nonzero(const double *u, long long n, int *flag) {
   if (__any_sync(0xffffffffu, nz) && (threadIdx.x & 31) == 0) *flag = 1;
 }
 
+// n doubles from device memory to page-locked host memory written by the
+// kernel itself (a zero-copy read-back that does not wait behind copies
+// queued on the copy engines).
+__global__ void k_copy_to_host(const double *src, double *dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
 // u += delta in FP64, x = expm1(u).
 __global__ void k_update64(double *u64, double *x64, const float *delta, long long n) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -401,6 +411,9 @@ struct Problem {
   int nl;
   int zero_u;         // 1: start from u = 0 without reading u (initial_guess = 0)
   int check_rho;      // the solve validates rho itself: 0 no, 1 yes, 2 yes, negatives allowed
+  double *host_u;     // page-locked host destination of u (single-field solves with
+                      // a page-locked host u), else null
+  int early_copied;   // set by the mixed solve: u already copied to host_u
 };
 
 // tile of the tiled smoother (x by y cells; S = 1 and S = 2 sweeps per pass)
@@ -1722,10 +1735,20 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   }
   const int bnch = red_chunks(boff);
   double *btmp = bnch ? S.get<double>(2 * (size_t)bnch * np) : nullptr;
+  // the norms reach the host through a kernel that writes them into the
+  // page-locked buffer (its device mapping), so that an early copy of the
+  // result (below) does not hold them up
   auto read_norms = [&](std::vector<double> &out) {
     reduce_partials(ctx, partial, d_boff, np, bnch, btmp, red, st);
     double *hp = pinned_buf(ctx, 2 * (size_t)np);
-    CK(cudaMemcpyAsync(hp, red, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    double *hpd = nullptr;
+    if (cudaHostGetDevicePointer((void **)&hpd, hp, 0) == cudaSuccess && hpd) {
+      k_copy_to_host<<<1, 256, 0, st>>>(red, hpd, 2 * np);
+      CK_LAUNCH(ctx);
+    } else {
+      cudaGetLastError();
+      CK(cudaMemcpyAsync(hp, red, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     CK(cudaStreamSynchronize(st));
     prof_harvest(ctx);
     out.assign(2 * np, 0.0);
@@ -1779,8 +1802,12 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   // the residual at the end of the cycle, predicted as mid * sqrt(mid /
   // previous mid) (the rest of the cycle does about half of a cycle's
   // contraction), is below 0.7 tol.
+  // returns whether every field that took part stopped because its predicted
+  // end-of-cycle residual fell below the tolerance (the outer step is then
+  // likely the last)
   auto inner = [&](bool bg, const std::vector<double> &r0, double floor_rel, int kmax) {
     std::vector<double> rp(np, HUGE_VAL), rbest(np, HUGE_VAL);
+    std::vector<int> by_pred(np, 0);
     // fields leave the inner solve one by one (their active flag drops until
     // the next outer step), so a batch does not run every field as long as
     // its slowest one
@@ -1810,17 +1837,47 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
         const double pred = rp[pi] < HUGE_VAL ? r * std::sqrt(r / rp[pi]) : r;
         const double ratio = rp[pi] < HUGE_VAL ? r / rp[pi] : 0.0;
         if (rp[pi] < HUGE_VAL) rbest[pi] = std::min(rbest[pi], ratio);
-        if (ratio < 0.75 && (bg || ratio <= 3.0 * rbest[pi]) && r > floor_rel * r0[pi] &&
-            pred > (bg ? 0.7 : 0.3) * cfg.tol)
+        const bool moving = ratio < 0.75 && (bg || ratio <= 3.0 * rbest[pi]) &&
+                            r > floor_rel * r0[pi];
+        if (moving && pred > (bg ? 0.7 : 0.3) * cfg.tol) {
           go = true;
-        else
+        } else {
           iact[pi] = 0;
+          by_pred[pi] = moving;
+        }
         rp[pi] = r;
       }
       if (!go) break;
       CK(cudaMemcpyAsync(active, iact.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    bool all = true;
+    for (int pi = 0; pi < np; pi++)
+      if (act[pi] && !by_pred[pi]) all = false;
+    return all;
+  };
+  // Early result copy (one field whose u is page-locked host memory): when an
+  // outer step's correction solve predicts convergence, the result is formed
+  // and its device-to-host copy started on the context's copy stream before
+  // the FP64-accurate defect confirms it, so the copy overlaps that check; a
+  // later update makes the copy stale and the result is formed and copied
+  // again at the end.
+  bool early = false, stale = false;
+  auto early_copy = [&]() {
+    if (!ctx->copy) {
+      CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ctx->copy_in, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->copy_out, cudaEventDisableTiming));
+    }
+    if (early) CK(cudaStreamWaitEvent(st, ctx->copy_out, 0));  // the last copy has read u
+    finalize();
+    CK(cudaEventRecord(ctx->copy_in, st));
+    CK(cudaStreamWaitEvent(ctx->copy, ctx->copy_in, 0));
+    CK(cudaMemcpyAsync(P[0].host_u, P[0].u, (size_t)D[0].ncell * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->copy));
+    CK(cudaEventRecord(ctx->copy_out, ctx->copy));
+    early = true;
+    stale = false;
   };
   try {
     CK(cudaMemcpyAsync(active, act.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1908,15 +1965,22 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
           CK_LAUNCH(ctx);
         }
       }
-      inner(true, r0, 1e-6, std::max(cfg.inner_cycles, 12));
+      const bool likely_last = inner(true, r0, 1e-6, std::max(cfg.inner_cycles, 12));
       update();
+      stale = true;
+      if (likely_last && np == 1 && P[0].host_u) early_copy();
     }
   } catch (...) {
+    if (early) cudaStreamWaitEvent(st, ctx->copy_out, 0);
     finalize();
     cudaStreamSynchronize(st);
     throw;
   }
-  finalize();
+  if (early) CK(cudaStreamWaitEvent(st, ctx->copy_out, 0));
+  if (early && !stale)
+    P[0].early_copied = 1;  // u was formed after the last update and is on the host
+  else
+    finalize();
 }
 
 // ---------------------------------------------------------------------------
@@ -1929,6 +1993,18 @@ static bool is_device_ptr(const void *p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// page-locked (or registered) host memory: a device-to-host copy into it runs
+// asynchronously
+static bool is_pinned_host(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
 }
 
 struct Staged {
@@ -2258,6 +2334,12 @@ void fr_ctx_destroy(frmg_ctx *c) {
     cudaEventDestroy(c->side_in);
     cudaEventDestroy(c->side_out);
   }
+  if (c->copy) {
+    cudaStreamSynchronize(c->copy);
+    cudaStreamDestroy(c->copy);
+    cudaEventDestroy(c->copy_in);
+    cudaEventDestroy(c->copy_out);
+  }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   for (auto &kv : c->sizes) cudaFree(kv.first);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -2339,6 +2421,7 @@ static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], d
     p.u = du;
     p.zero_u = !o.initial_guess;
     p.check_rho = defer ? (o.allow_negative_density ? 2 : 1) : 0;
+    p.host_u = du != u && is_pinned_host(u) ? u : nullptr;
     std::vector<Problem> P{p};
     std::vector<fr_stats> sv(1);
     memset(sv.data(), 0, sizeof(fr_stats));
@@ -2351,6 +2434,11 @@ static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], d
       status = e.status;
       g_last_error = e.msg;
     }
+    // the mixed solve may have copied its final u to the host already
+    if (P[0].early_copied)
+      back.erase(std::remove_if(back.begin(), back.end(),
+                                [&](const Staged &b) { return b.host_dst == (void *)u; }),
+                 back.end());
     finish(ctx, back, st);
     sv[0].seconds = now_s() - t0;
     if (stats) *stats = sv[0];
