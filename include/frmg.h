@@ -49,7 +49,9 @@ typedef enum {
     FR_ECUDA = 3,      /* a CUDA call failed */
     FR_ENOCONV = 4,    /* max_vcycles reached before tol */
     FR_EDIVERGED = 5,  /* NaN/Inf or a residual growing for several cycles */
-    FR_ETIMEOUT = 6    /* a bounded device-side wait ran out */
+    FR_ETIMEOUT = 6    /* reserved for a bounded device-side wait that ran out; no
+                          kernel of this library waits on another, so no entry
+                          point returns it */
 } fr_status;
 
 typedef enum {
@@ -134,7 +136,11 @@ void fr_opts_default(fr_opts *opts);
 const char *fr_status_string(int status);
 const char *fr_last_error(void);
 
-/* Library-owned context: device, workspace, streams, captured graphs. */
+/* Library-owned context: device, workspace, streams, captured graphs.
+ * The environment variable FRMG_WORKSPACE_LIMIT (bytes), read when the
+ * context is created, caps the device workspace the context holds (in use and
+ * cached); a call that would need more fails with FR_ENOMEM, as it does when
+ * cudaMalloc fails. */
 int fr_ctx_create(frmg_ctx **out, int device);
 void fr_ctx_destroy(frmg_ctx *ctx);
 
@@ -250,13 +256,16 @@ int fr_vcycles(frmg_ctx *ctx, const double *density, const int dims[3], double b
 /*
  * Residual norm of one grid without allocating anything (no cudaMalloc,
  * cudaFree or allocating library call), for callers that cannot allocate
- * device memory at that point: code recording a CUDA stream capture, code
- * whose device memory is owned by another allocator, loops that cannot afford
- * the synchronisation of an allocation.  The paper has no counterpart; this is
- * a service entry point of the library.
+ * device memory at that point: code whose device memory is owned by another
+ * allocator (a caching pool that leaves nothing for cudaMalloc, or that must
+ * account for every allocation), and loops that cannot afford the device
+ * synchronisation an allocation or a free may bring.  The paper has no
+ * counterpart; this is a service entry point of the library.
  * out2 (device) receives {rms of L(u) over the cells, max |L(u)|}; u, density,
- * ub (optional patch faces, as fr_smooth) and out2 must be device pointers;
- * no context is needed.  Grids are limited to 33,554,432 cells (FR_EINVAL
+ * ub (optional patch faces, as fr_smooth) and out2 must be device memory of
+ * the current device (or managed memory): the kernels run on the current
+ * device, and a pointer to another GPU's memory is refused with FR_EINVAL.
+ * No context is needed.  Grids are limited to 33,554,432 cells (FR_EINVAL
  * beyond, with a message in fr_last_error()).  The call is asynchronous on
  * `stream`: out2 is valid once the stream reaches it.
  * Scratch: a fixed 16 KB array of this library's module on each GPU that
@@ -264,7 +273,11 @@ int fr_vcycles(frmg_ctx *ctx, const double *density, const int dims[3], double b
  * that GPU; each call overwrites all of it before reading it, but calls that
  * overlap on the GPU (different streams, no ordering) race on it.  The first
  * call on each device looks up the array's device address (with that device
- * current); make that first call before any stream capture begins.
+ * current) and keeps it; make that first call before any stream capture
+ * begins.  The kept address belongs to the device's primary context: after
+ * cudaDeviceReset (or anything else that destroys that context) the module is
+ * loaded again, possibly at another address, and the kept one is stale, so
+ * do not call this entry point on that device again in the same process.
  */
 int fr_residual_norm_noalloc(const double *u, const double *density, const int dims[3],
                              double h, double box_mpc_h, double a, double omega_m,

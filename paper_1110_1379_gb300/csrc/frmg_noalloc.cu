@@ -1,11 +1,11 @@
 // frmg_noalloc.cu -- residual norm of one grid without any device allocation.
 //
 // Some callers cannot allocate device memory at the moment they want to know
-// how far a field is from solving the equation: code that is recording a CUDA
-// stream capture (a cudaMalloc there invalidates the capture), code whose
-// device memory is entirely owned by another allocator (a framework's caching
-// pool that leaves nothing for cudaMalloc), and latency-critical loops that
-// cannot afford the implicit device synchronisation of cudaMalloc/cudaFree.
+// how far a field is from solving the equation: code whose device memory is
+// entirely owned by another allocator (a framework's caching pool that leaves
+// nothing for cudaMalloc, or that must see every allocation), and
+// latency-critical loops that cannot afford the implicit device
+// synchronisation of cudaMalloc/cudaFree.
 // fr_residual_norm_noalloc serves them: the caller passes device inputs and a
 // device output, and the only scratch (the per-block partial sums of the
 // reduction) lives in a fixed array of this library's module that every GPU
@@ -133,13 +133,17 @@ __global__ void k_na_final(const double *partials, long long ncell, double *out2
   }
 }
 
-bool on_device(const void *p) {
+// p is device memory of the current device `dev` (the kernels run there), or
+// managed memory; device memory of another GPU is refused, since without peer
+// access the kernels could not read it.
+bool on_device(const void *p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 int fail(int status, const std::string &msg) {
@@ -162,8 +166,16 @@ extern "C" int fr_residual_norm_noalloc(const double *u, const double *density,
     return fail(FR_EINVAL, "grid of " + std::to_string(ncell) +
                                " cells exceeds the 33554432-cell limit of the allocation-free "
                                "residual norm");
-  if (!on_device(u) || !on_device(density) || !on_device(out2) || (ub && !on_device(ub)))
-    return fail(FR_EINVAL, "the allocation-free path takes device pointers only");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FR_ECUDA, "cudaGetDevice failed");
+  }
+  if (dev < 0 || dev >= kNAMaxDevices) return fail(FR_EINVAL, "device index out of range");
+  if (!on_device(u, dev) || !on_device(density, dev) || !on_device(out2, dev) ||
+      (ub && !on_device(ub, dev)))
+    return fail(FR_EINVAL,
+                "the allocation-free path takes device pointers of the current device only");
   // constants at cell size h: alpha scales as 1/h^2 from its value at h = 1
   double k6[6];
   int st = fr_constants(box_mpc_h, 1, a, omega_m, fr0_abs, k6);
@@ -188,13 +200,8 @@ extern "C" int fr_residual_norm_noalloc(const double *u, const double *density,
   G.beta = k6[1];
   G.gamma = k6[2];
   // one-time set-up per device (with that device current): device address of
-  // the module's scratch array
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(FR_ECUDA, "cudaGetDevice failed");
-  }
-  if (dev < 0 || dev >= kNAMaxDevices) return fail(FR_EINVAL, "device index out of range");
+  // the module's scratch array, valid for the life of the device's primary
+  // context (cudaDeviceReset ends it; the header says so)
   double *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_na_mu);
