@@ -27,6 +27,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 N = 512
+# the same metric string on both arms (the precision is in "dtype")
+METRIC = "f(R) MG solve: cells/s to converge (rms <= 1e-8)"
 PHYS = dict(box=256.0, a=1.0, omega_m=0.24, fr0=1e-5)
 SIGMA = 2.0
 SEED = 3000
@@ -59,15 +61,16 @@ ALG_BYTES = {
 }
 
 # DRAM bytes per cell of one launch (dram__bytes_read.sum + dram__bytes_write.sum
-# over the cells of the launch) from the ncu captures summarised under
-# profiles/ (384^3 launches; traffic grows in proportion to the cells, so it is
-# scaled to the workload's grid).  Valid for the kernels as captured there.
+# over the cells of the launch) from one ncu capture of each kernel on a 384^3
+# fine grid of the same workload recipe (traffic grows in proportion to the
+# cells, so it is scaled to the workload's grid).  Valid for the kernels as
+# captured; the second entry names the captured launch.
 TRAFFIC_PER_CELL = {
-    "smooth_f32@fine": (1120.145e6 / 384 ** 3, "profiles/smooth_rb_f32_384.md"),
-    "smooth_bg_f32@fine": (1640.735e6 / 384 ** 3, "profiles/smooth_rb_bg_f32_384.md"),
-    "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "profiles/resid_restrict_tiled_f32_384.md"),
-    "prolong_f32@fine": (678.570e6 / 384 ** 3, "profiles/prolong_tiled_f32_384.md"),
-    "df_defect": (2466.320e6 / 384 ** 3, "profiles/df_defect_384.md"),
+    "smooth_f32@fine": (1120.145e6 / 384 ** 3, "k_smooth_rb plain form, one 384^3 launch"),
+    "smooth_bg_f32@fine": (1640.735e6 / 384 ** 3, "k_smooth_rb correction form, one 384^3 launch"),
+    "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "k_resid_restrict_tiled, one 384^3 launch"),
+    "prolong_f32@fine": (678.570e6 / 384 ** 3, "k_prolong_tiled, one 384^3 launch"),
+    "df_defect": (2466.320e6 / 384 ** 3, "k_df_defect, one 384^3 launch"),
 }
 
 
@@ -182,6 +185,36 @@ def cpu_baseline(budget_s=12.0):
                       f"seed {SEED}; {dt:.1f} s on 1 core"}
 
 
+def oracle_proxy(ctx, opts, stream):
+    """The headline cell size (0.5 Mpc/h), sigma, seed, a and |f_R0| on a 128^3
+    box: the GPU mixed solve with the headline's setting against the FP64 CPU
+    oracle's solution, element by element (u and grad f_R)."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_1110_1379_gb300 import frmg, synth
+    n = 128
+    ph = dict(PHYS, box=64.0)
+    rho_np = synth.lognormal_density((n,) * 3, SEED, sigma=SIGMA)
+    t0 = time.perf_counter()
+    ref = O.solve(rho_np, tol=TOL, **ph)
+    t_or = time.perf_counter() - t0
+    r = torch.from_numpy(rho_np).cuda()
+    x = torch.empty_like(r)
+    st, s = ctx.solve(r, x, tol=TOL, prec="mixed", initial_guess=0, stream=stream, **opts, **ph)
+    assert st == frmg.FR_OK and ref.converged
+    uref = torch.from_numpy(ref.u).cuda()
+    ubar = frmg.constants(ph["box"], n, ph["a"], ph["omega_m"], ph["fr0"])[5]
+    g = grad_error(x, uref, ubar, 1.0 / n)
+    return {"grid": "128^3, box 64 Mpc/h (0.5 Mpc/h cells), sigma 2, seed 3000, a=1, |f_R0|=1e-5",
+            "max_abs_du_vs_oracle": float((x - uref).abs().max()),
+            "rms_du_vs_oracle": float(((x - uref) ** 2).mean().sqrt()),
+            "grad_fR_max_rel_vs_oracle": g["max_rel"], "grad_fR_rms_rel_vs_oracle": g["rms_rel"],
+            "gpu_vcycles": s.vcycles, "oracle_vcycles": ref.cycles,
+            "oracle_seconds": t_or}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -200,7 +233,7 @@ def run_reference(args):
     tot = sum(times)
     value = args.steps * SAMPLE_N ** 3 / tot
     line = {
-        "impl": "reference", "metric": "f(R) MG solve: cells/s to converge (rms <= 1e-8)",
+        "impl": "reference", "metric": METRIC,
         "value": value, "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -589,19 +622,33 @@ def main():
     fixed = parse_options(args.options)
     tuned = dict(fixed)
 
-    def solve(prec, profile=False, **kw):
+    def solve(prec, profile=False, out=None, phys=None, **kw):
         # the workload starts from u = 0: the mixed solve is told so
         # (initial_guess = 0, u is then output only); the FP64 solve iterates on u
+        out = u if out is None else out
         opts = dict(tuned) if (prec == "mixed" and not kw.pop("default", False)) else {}
         if prec == "mixed":
             opts["initial_guess"] = 0
         else:
-            u.zero_()
+            out.zero_()
         opts.update(kw)
-        st, s = ctx.solve(rho, u, tol=TOL, prec=prec, stream=stream, **opts, **PHYS)
+        st, s = ctx.solve(rho, out, tol=TOL, prec=prec, stream=stream, **opts,
+                          **(phys or PHYS))
         if st != frmg.FR_OK:
             raise RuntimeError(f"solve failed: status {st} {s.as_dict()}")
         return s
+
+    def event_timed(fn, steps):
+        """Device time per call of fn() over `steps` calls (CUDA events on the
+        solve stream), and fn's last return value."""
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(steps):
+            r = fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / steps, r
 
     for _ in range(args.warmup):
         solve("mixed")
@@ -699,6 +746,50 @@ def main():
     else:
         fp64_value, du, du_rms, gerr = None, None, None, {"max_rel": None, "rms_rel": None}
 
+    # the same tuned solve with the native FP64 defect, update and convergence
+    # test (defect_precision = 1) instead of double-float, against the FP64 solve
+    u_dp1 = torch.empty_like(u)
+    solve("mixed", out=u_dp1, defect_precision=1)
+    ms_dp1, s_dp1 = event_timed(lambda: solve("mixed", out=u_dp1, defect_precision=1),
+                                args.steps)
+    fp64_defect = {"value": cells / (ms_dp1 / 1e3), "unit": "cells/s", "ms_per_solve": ms_dp1,
+                   "vcycles": s_dp1.vcycles, "outer": s_dp1.outer, "res_rms": s_dp1.res_rms,
+                   "defect_arithmetic": "native FP64"}
+    if t64:
+        fp64_defect["max_abs_du_vs_fp64_gpu"] = float((u_dp1 - u).abs().max())
+        g1 = grad_error(u_dp1, u, ubar, 1.0 / n)
+        fp64_defect["grad_fR_max_rel_vs_fp64_gpu"] = g1["max_rel"]
+    del u_dp1
+
+    # the other two |f_R0| of the 512^3 configuration (the stiffest, 1e-4, and
+    # 1e-6), with the setting tuned on the 1e-5 field and the library defaults;
+    # accuracy against the plain FP64 GPU solve of the same field
+    fr0_scan = {}
+    if args.prec == "both":
+        u_ref = torch.empty_like(u)
+        for f0 in (1e-4, 1e-6):
+            ph = dict(PHYS, fr0=f0)
+            solve("mixed", phys=ph)
+            ms_t, s_t = event_timed(lambda: solve("mixed", phys=ph), args.steps)
+            u_t = u.clone()
+            ms_d, s_d = event_timed(lambda: solve("mixed", phys=ph, default=True), 2)
+            ms_f, s_f = event_timed(lambda: solve("fp64", out=u_ref, phys=ph), 1)
+            ub_f = frmg.constants(PHYS["box"], n, PHYS["a"], PHYS["omega_m"], f0)[5]
+            gf = grad_error(u_t, u_ref, ub_f, 1.0 / n)
+            fr0_scan[f"{f0:g}"] = {
+                "mixed_tuned": {"value": cells / (ms_t / 1e3), "ms_per_solve": ms_t,
+                                "vcycles": s_t.vcycles, "outer": s_t.outer,
+                                "res_rms": s_t.res_rms},
+                "mixed_default_v22": {"value": cells / (ms_d / 1e3), "ms_per_solve": ms_d,
+                                      "vcycles": s_d.vcycles, "outer": s_d.outer},
+                "fp64": {"value": cells / (ms_f / 1e3), "ms_per_solve": ms_f,
+                         "vcycles": s_f.vcycles},
+                "max_abs_du_vs_fp64_gpu": float((u_t - u_ref).abs().max()),
+                "grad_fR_max_rel_vs_fp64_gpu": gf["max_rel"],
+                "grad_fR_rms_rel_vs_fp64_gpu": gf["rms_rel"]}
+            del u_t
+        del u_ref
+
     # roofline of the dominant kernel family during the timed mixed steps
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dom_name, (dom_cnt, dom_ms) = dom
@@ -719,8 +810,8 @@ def main():
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": tr[0] * cells if tr else None,
-                "traffic_source": (f"ncu dram bytes of one 384^3 launch ({tr[1]}), scaled to "
-                                   f"{n}^3 by cells") if tr else None,
+                "traffic_source": (f"ncu dram bytes ({tr[1]}), scaled to {n}^3 by cells")
+                if tr else None,
                 "alg_bytes_per_launch": traffic_alg, "avg_launch_ms": avg_ms,
                 "launches": dom_cnt, "peak_source": peak_src}
     else:
@@ -749,11 +840,13 @@ def main():
     if rank != 0:
         return
     cpu = None
+    proxy = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline()
+        proxy = oracle_proxy(ctx, tuned, stream)
     s0 = stats[-1]
     line = {
-        "metric": "f(R) MG solve: cells/s to converge (rms <= 1e-8), mixed FP32/FP64",
+        "metric": METRIC,
         "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
@@ -779,6 +872,9 @@ def main():
         "accuracy_vs_fp64_gpu": {"max_abs_du": du, "rms_du": du_rms,
                                  "grad_fR_max_rel": gerr["max_rel"],
                                  "grad_fR_rms_rel": gerr["rms_rel"]},
+        "accuracy_vs_oracle_128_proxy": proxy,
+        "mixed_fp64_defect": fp64_defect,
+        "fr0_scan": fr0_scan,
         "roofline": roof,
         "kernel_rooflines": kernel_roofs,
         "solve_effective_bandwidth": solve_eff,

@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -74,6 +75,10 @@ struct frmg_ctx {
   long long launches = 0;
   std::multimap<size_t, void *> free_blocks;
   std::map<void *, size_t> sizes;
+  // device workspace held by the allocator (in use or cached) and its cap
+  // (0 = none; FRMG_WORKSPACE_LIMIT at creation): an allocation that would
+  // pass the cap fails with FR_ENOMEM as a failed cudaMalloc does
+  size_t held = 0, limit = 0;
   double *pinned = nullptr;
   size_t pinned_n = 0;
   // optional per-kernel timing with CUDA events on the launch stream
@@ -156,21 +161,31 @@ void *frmg_alloc(frmg_ctx *c, size_t bytes) {
     c->free_blocks.erase(it);
     return p;
   }
+  auto device_malloc = [&](void **q) {
+    if (c->limit && c->held + bytes > c->limit) return false;
+    if (cudaMalloc(q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
   void *p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
-    cudaGetLastError();
+  if (!device_malloc(&p)) {
     // drop the cache and retry once
     for (auto &kv : c->free_blocks) {
       cudaFree(kv.second);
+      c->held -= c->sizes[kv.second];
       c->sizes.erase(kv.second);
     }
     c->free_blocks.clear();
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      throw FrError{FR_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
-    }
+    if (!device_malloc(&p))
+      throw FrError{FR_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed" +
+                                   (c->limit ? " (workspace limit " + std::to_string(c->limit) +
+                                                   " bytes)"
+                                             : std::string())};
   }
   c->sizes[p] = bytes;
+  c->held += bytes;
   return p;
 }
 
@@ -2303,7 +2318,7 @@ const char *fr_status_string(int s) {
     case FR_ECUDA: return "FR_ECUDA: CUDA error";
     case FR_ENOCONV: return "FR_ENOCONV: tolerance not reached";
     case FR_EDIVERGED: return "FR_EDIVERGED: iteration diverged";
-    case FR_ETIMEOUT: return "FR_ETIMEOUT: device wait timed out";
+    case FR_ETIMEOUT: return "FR_ETIMEOUT: device wait timed out (reserved; not returned)";
     default: return "unknown status";
   }
 }
@@ -2319,6 +2334,7 @@ int fr_ctx_create(frmg_ctx **out, int device) {
     CK(cudaSetDevice(device));
     frmg_ctx *c = new frmg_ctx();
     c->device = device;
+    if (const char *lim = getenv("FRMG_WORKSPACE_LIMIT")) c->limit = strtoull(lim, nullptr, 10);
     *out = c;
     return FR_OK;
   });
