@@ -1,0 +1,183 @@
+"""The headline configuration against the FP64 oracle.
+
+The throughput workload is a 512^3 periodic grid with 0.5 Mpc/h cells
+(box 256 Mpc/h), a = 1, Omega_m = 0.24, a lognormal density of sigma = 2
+(seed 3000) and |f_R0| in {1e-4, 1e-5, 1e-6} (alpha = 3595, 359.5, 35.95 per
+unit grid spacing: the larger |f_R0|, the stiffer the flux term), solved from
+u = 0 to rms(L(u)) <= 1e-8 (Sec. VI.E).
+
+* 128^3 proxy, element by element: the same cell size (box 64 Mpc/h), sigma,
+  seed and a, at all three |f_R0|, solved by the oracle and by the GPU with
+  the library defaults, with the setting the autotuner picks for the 512^3
+  field, with that setting and the native FP64 defect, with this field's own
+  autotuned setting, and in plain FP64.  max|u - u_oracle| <= 1e-6 (a relative
+  error of f_R, since u is a logarithm), and the error of grad f_R (central
+  differences of f~_R = -e^{u + ubar}) relative to the oracle's largest
+  gradient <= 1e-6.
+* 512^3, the workload itself, mixed precision with the default and tuned
+  settings at all three |f_R0|: the FP64 residual of the returned u (the
+  library's FP64 kernel) has rms <= 1e-8, the oracle's pointwise L_i(u) at
+  sampled cells equals that FP64 residual there, and the flux terms
+  telescope (sum_i L_i = sum_i [beta (e^{-u/2} - 1) - gamma (rho - 1)]).
+"""
+import multiprocessing as mp
+from concurrent.futures import ProcessPoolExecutor
+
+import numpy as np
+import pytest
+
+import paper_fields as PF
+from gpu_common import ctx, dev, host, local_block, torch  # noqa: F401
+from oracle import oracle as O
+from paper_1110_1379_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+OM = 0.24
+SEED = 3000
+SIGMA = 2.0
+FR0S = (1e-4, 1e-5, 1e-6)
+# the setting fr_autotune picks for the 512^3 |f_R0| = 1e-5 field
+TUNED = dict(pre=1, post=1, relax=1.15, fmg=1, tiling=1)
+
+
+def _oracle_solve(args):
+    n, box, fr0 = args
+    rho = synth.lognormal_density((n,) * 3, SEED, sigma=SIGMA)
+    r = O.solve(rho, tol=1e-8, box=box, a=1.0, omega_m=OM, fr0=fr0)
+    return r.u, r.converged, r.cycles
+
+
+@pytest.fixture(scope="module")
+def proxy():
+    """Oracle solutions of the 128^3 proxy at the three |f_R0| (solved in
+    parallel in spawned processes)."""
+    n, box = 128, 64.0
+    with ProcessPoolExecutor(3, mp_context=mp.get_context("spawn")) as ex:
+        sols = list(ex.map(_oracle_solve, [(n, box, f) for f in FR0S]))
+    rho = synth.lognormal_density((n,) * 3, SEED, sigma=SIGMA)
+    out = {}
+    for f, (u, conv, cyc) in zip(FR0S, sols):
+        assert conv, f
+        out[f] = u
+    return n, box, rho, out
+
+
+@pytest.fixture(scope="module")
+def C():
+    return ctx()
+
+
+def grad_fr_error(u, uref, ubar, h):
+    """(max, rms) of the grad f~_R error relative to max |grad f~_R| of uref."""
+    mx = sq = gmax = 0.0
+    n = 0
+    for ax in range(3):
+        def g(v):
+            f = -np.exp(v + ubar)
+            return (np.roll(f, -1, ax) - np.roll(f, 1, ax)) / (2 * h)
+        gr = g(uref)
+        dg = g(u) - gr
+        mx = max(mx, float(np.abs(dg).max()))
+        sq += float((dg * dg).sum())
+        gmax = max(gmax, float(np.abs(gr).max()))
+        n += dg.size
+    return mx / gmax, (sq / n) ** 0.5 / gmax
+
+
+SETTINGS = {
+    "default": dict(prec="mixed"),
+    "tuned": dict(prec="mixed", **TUNED),
+    "tuned_fp64_defect": dict(prec="mixed", defect_precision=1, **TUNED),
+    "autotuned": None,
+    "fp64": dict(prec="fp64"),
+}
+
+
+@pytest.mark.parametrize("fr0", FR0S)
+@pytest.mark.parametrize("setting", list(SETTINGS))
+def test_proxy_128_matches_oracle(C, proxy, fr0, setting):
+    n, box, rho, sols = proxy
+    uref = sols[fr0]
+    P = dict(box=box, a=1.0, omega_m=OM, fr0=fr0)
+    r = dev(rho)
+    opts = SETTINGS[setting]
+    if opts is None:
+        best, _ = C.autotune(r, tol=1e-8, prec="mixed", **P)
+        opts = {k: best[k] for k in ("prec", "pre", "post", "temporal_depth", "relax", "fmg",
+                                     "tiling")}
+    u = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
+    st, s = C.solve(r, u, tol=1e-8, **opts, **P)
+    assert st == 0 and s.res_rms <= 1e-8, (setting, fr0, s.as_dict())
+    # the returned u, checked by the FP64 residual kernel
+    d = torch.empty_like(u)
+    C.residual(u, r, d, **P)
+    assert float(torch.sqrt((d * d).mean())) <= 1e-8
+    uh = host(u)
+    du = float(np.abs(uh - uref).max())
+    # u~ = ln(-a^2 f_R) = u + ln |fbar~_R(a)|
+    ubar = float(np.log(PF.fbar_tilde_abs(1.0, OM, fr0)))
+    gmax, grms = grad_fr_error(uh, uref, ubar, 1.0 / n)
+    print(f"128^3 |f_R0|={fr0:g} {setting}: vcycles={s.vcycles} outer={s.outer} "
+          f"max|du|={du:.2e} grad_fR max_rel={gmax:.2e} rms_rel={grms:.2e}")
+    assert du <= 1e-6
+    assert gmax <= 1e-6 and grms <= 1e-7
+
+
+def sampled_vs_fp64(uh, rhoh, dh, *, box, fr0, h, nsample=200, seed=0):
+    """max over sampled cells of |L_i(oracle) - d_i(GPU FP64)| relative to the
+    size of the cell's terms, and the largest oracle |L_i| seen."""
+    rng = np.random.default_rng(seed)
+    n2, n1, n0 = uh.shape
+    worst_rel = worst_abs = 0.0
+    alpha, beta, gamma = PF.coefficients(box, n0, 1.0, OM, fr0)
+    for _ in range(nsample):
+        k, j, i = (int(rng.integers(0, m)) for m in (n2, n1, n0))
+        ub = local_block(uh, k, j, i)
+        rb = local_block(rhoh, k, j, i)
+        L, _ = O.cell_op(ub, rb, 3, 3, 3, box=box, a=1.0, omega_m=OM, fr0=fr0, h=h)
+        # scale of the largest term of L_i: flux, mass and density terms
+        nb = ub[3, 3, 3]
+        flux = 0.5 * alpha * sum(abs((np.exp(nb) + np.exp(ub[3 + dk, 3 + dj, 3 + di])) *
+                                     (ub[3 + dk, 3 + dj, 3 + di] - nb))
+                                 for dk, dj, di in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                                                    (0, 0, 1), (0, 0, -1)))
+        scale = flux + beta * abs(np.expm1(-nb / 2)) + gamma * abs(rb[3, 3, 3] - 1) + 1e-300
+        worst_rel = max(worst_rel, abs(L - dh[k, j, i]) / scale)
+        worst_abs = max(worst_abs, abs(L))
+    return worst_rel, worst_abs
+
+
+@pytest.fixture(scope="module")
+def field512():
+    n = 512
+    return n, synth.lognormal_density((n,) * 3, SEED, sigma=SIGMA)
+
+
+@pytest.mark.parametrize("fr0", FR0S)
+@pytest.mark.parametrize("setting", ["default", "tuned"])
+def test_headline_512_converges_in_fp64(C, field512, fr0, setting):
+    n, rho_np = field512
+    box = 256.0
+    P = dict(box=box, a=1.0, omega_m=OM, fr0=fr0)
+    r = dev(rho_np)
+    u = torch.empty_like(r)
+    opts = dict(prec="mixed", initial_guess=0)
+    if setting == "tuned":
+        opts.update(TUNED)
+    st, s = C.solve(r, u, tol=1e-8, **opts, **P)
+    assert st == 0 and s.res_rms <= 1e-8, (setting, fr0, s.as_dict())
+    d = torch.empty_like(u)
+    C.residual(u, r, d, **P)
+    rms64 = float(torch.sqrt((d * d).mean()))
+    uh, dh = host(u), host(d)
+    del d
+    rel, worst = sampled_vs_fp64(uh, rho_np, dh, box=box, fr0=fr0, h=1.0 / n, seed=int(fr0 * 1e7))
+    _, beta, gamma = PF.coefficients(box, n, 1.0, OM, fr0)
+    tel = float(np.sum(beta * np.expm1(-uh / 2) - gamma * (rho_np - 1.0)))
+    print(f"512^3 |f_R0|={fr0:g} {setting}: vcycles={s.vcycles} outer={s.outer} "
+          f"df rms={s.res_rms:.3e} FP64 rms={rms64:.3e} sampled max|L|={worst:.2e} "
+          f"oracle-vs-FP64 rel={rel:.1e} telescoping={tel:.2e}")
+    assert rms64 <= 1e-8
+    assert rel <= 1e-10
+    assert abs(tel) <= 10 * uh.size * 1e-8
