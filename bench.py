@@ -66,7 +66,8 @@ ALG_BYTES = {
 # cells, so it is scaled to the workload's grid).  Valid for the kernels as
 # captured; the second entry names the captured launch.
 TRAFFIC_PER_CELL = {
-    "smooth_f32@fine": (1120.145e6 / 384 ** 3, "k_smooth_rb plain form, one 384^3 launch"),
+    "smooth_f32@fine": ((470.301e6 + 408.505e6) / 384 ** 3,
+                        "k_smooth_rc plain form, 64x16 tiles, one 384^3 launch"),
     "smooth_bg_f32@fine": (1640.735e6 / 384 ** 3, "k_smooth_rb correction form, one 384^3 launch"),
     "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "k_resid_restrict_tiled, one 384^3 launch"),
     "prolong_f32@fine": (678.570e6 / 384 ** 3, "k_prolong_tiled, one 384^3 launch"),
@@ -660,7 +661,7 @@ def main():
     else:
         best, tune_s = ctx.autotune(rho, tol=TOL, prec="mixed", stream=stream, **PHYS)
         tuned = {k: best[k] for k in ("pre", "post", "temporal_depth", "relax", "fmg",
-                                          "tiling")}
+                                          "tiling", "smooth_tile")}
     solve("mixed")
     torch.cuda.synchronize()
     barrier()
@@ -862,8 +863,11 @@ def main():
                       "note": ("fixed by --options" if fixed else
                                "fastest of V(pre,post) in {(1,1),(2,1),(1,2),(2,2),(3,3)} x "
                                "relaxation factor {1,1.15,1.25}, then one at a time sweeps "
-                               "per tiled pass {1,2}, full-multigrid start {0,1} and tiling "
-                               "{0,1}, chosen by fr_autotune on this field")},
+                               "per tiled pass {1,2}, full-multigrid start {0,1}, tiling "
+                               "{0,1} and the smoother's tile (smooth_tile: 16 and 8 = "
+                               "register-column kernel on 64x16 / 64x8 tiles, -1 = "
+                               "shared-memory plane ring on 64x16), chosen by fr_autotune "
+                               "on this field")},
         "mixed_default_v22": {"value": value_default, "unit": "cells/s",
                               "vcycles": s_def.vcycles, "outer": s_def.outer},
         "mixed": {"vcycles": s0.vcycles, "outer": s0.outer, "res_rms": s0.res_rms,

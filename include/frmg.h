@@ -100,6 +100,13 @@ typedef struct {
                                1 = u holds the initial guess (default); 0 = start from
                                u = 0: the contents of u are not read (a host u is not
                                copied to the device), u is output only. */
+    int smooth_tile;        /* mixed: kernel and tile of the one-sweep FP32 smoother of
+                               the plain (full-variable) form on tiled levels: 8 or 16 =
+                               register-column kernel on 64 x 8 or 64 x 16 tiles (each
+                               thread keeps its x-pairs' last four planes in registers),
+                               -1 = shared-memory plane-ring kernel on 64 x 16 tiles,
+                               0 = library default.  Every choice performs the same
+                               sweep (identical results); only the speed differs. */
 } fr_opts;
 
 #define FR_HIST 64
@@ -214,7 +221,9 @@ int fr_smooth(frmg_ctx *ctx, double *u, const double *density, const double *f,
  * unknown.  bg non-NULL: u is a correction delta on the FP32 background bg and
  * the equation is A(bg + delta) - A(bg) = f.  tiled != 0 selects the
  * shared-memory temporally blocked kernel (grids of at least 16 cells a side),
- * 0 the one-colour-per-launch kernel; both give the same sweeps. */
+ * 8 or 16 the register-column kernel on 64 x 8 or 64 x 16 tiles (plain form,
+ * bg NULL; the correction form keeps the shared-memory kernel), 0 the
+ * one-colour-per-launch kernel; all give the same sweeps. */
 int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, const int dims[3],
                   double h, double box_mpc_h, double a, double omega_m, double fr0_abs,
                   const float *ub, int nsweeps, double step_cap, int tiled, void *stream);
@@ -289,10 +298,12 @@ int fr_residual_norm_noalloc(const double *u, const double *density, const int d
  * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)} and the relaxation factor
  * relax in {1, 1.15, 1.25} at one sweep per tiled pass, then, one at a time on
  * top of the fastest setting so far, two sweeps per pass (temporal_depth 2),
- * the full-multigrid start (fmg 1) and tiling 1, on top of *base (NULL =
+ * the full-multigrid start (fmg 1) and tiling 1, then the smoother's kernel
+ * and tile shape (smooth_tile 16, 8 and -1), on top of *base (NULL =
  * defaults), twice each, and writes the fastest setting that reaches tol to
- * *best (and its time in seconds to *best_seconds, if not NULL).  Device or
- * host density pointer.  FR_ENOCONV if no candidate converged.
+ * *best (and its time in seconds to *best_seconds, if not NULL; best->smooth_tile
+ * names the chosen tile, never 0).  Device or host density pointer.
+ * FR_ENOCONV if no candidate converged.
  */
 int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double box_mpc_h,
                 double a, double omega_m, double fr0_abs, double tol, const fr_opts *base,

@@ -1504,6 +1504,295 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
   }
 }
 
+// ---------------------------------------------------------------------------
+// One red-black sweep per launch with register-resident z-columns (plain FP32
+// form; the same sweep, cell for cell and bit for bit, as k_smooth_rb).
+//
+// A block owns a 64 x TY tile and a chunk of zc planes and marches along z over
+// the planes Z0-2 .. Z1+1.  Every x-pair of the tile plus a halo of two cells
+// (34 x (TY + 4) pairs) has one owner thread for the whole march, which keeps
+// the pair's red and black cell (u, x = expm1(u)) and right-hand sides for the
+// last four planes in registers: the z neighbours of an update are the owner's
+// own registers, and only the xy exchange goes through shared memory.  At the
+// step that loads plane p:
+//   1. the pair's u and f of plane p (loaded a step earlier) are split into its
+//      red and black cell, x is computed from u (the x cache is not read), and
+//      the black cell, still old, is published to the black half-plane of p;
+//   2. the red cells of plane p-1 on the tile grown by one cell are updated:
+//      x and y neighbours are black cells of plane p-1 (the other cell of the
+//      pair from registers, the rest from the black half-plane published a
+//      step earlier), z neighbours are the owner's old black cells of planes
+//      p-2 and p; the new values are published to the red half-plane of p-1;
+//   3. the black cells of plane p-2 on the tile are updated from the new red
+//      cells (red half-plane of p-2, published a step earlier, and the owner's
+//      red cells of planes p-3 and p-1), and plane p-2 (u and its x cache) is
+//      written out.
+// Half-planes are double-buffered by step parity, so a step reads only what
+// the previous step wrote and one barrier per step suffices.  The ring of
+// register planes is indexed by the step modulo 4, which the loop unrolls into
+// compile-time indices; which cell of a pair is red is a per-slot bit flipped
+// every plane, applied with selects, so an update is straight-line code and
+// the updates of a thread's slots interleave.
+// Thread layout (256 threads, 8 warps): warp w owns the interior pairs
+// px = 1 + lane of rows 2 + w + 8 j (j < TY / 8), and thread t < NHALO also
+// one halo pair: the four halo rows for t < 128, the two halo columns above.
+template <int TY>
+struct RCCfg {
+  static constexpr int TX = 64, H = 2, PX = TX / 2 + 2, LY = TY + 2 * H, PP = PX * LY;
+  static constexpr int NT = 256, NW = NT / 32;
+  static constexpr int NI = TY / NW;                  // interior rows per thread
+  static constexpr int NSL = NI + 1;                  // pair slots per thread
+  static constexpr int NHR = 4 * (TX / 2);            // halo-row pairs
+  static constexpr int NHALO = NHR + 2 * LY;          // all halo pairs
+  static constexpr int MINB = TY <= 8 ? 3 : 2;        // resident blocks per SM
+  static constexpr size_t smem() { return (size_t)4 * PP * sizeof(float2); }
+  static_assert(TY % NW == 0 && NHALO <= NT, "tile height");
+};
+
+template <bool DIR, int TY>
+__global__ void __launch_bounds__(RCCfg<TY>::NT, RCCfg<TY>::MINB)
+    k_smooth_rc(const Grid<float> *grids, const int *off, int ngrid, int zc, const int *active,
+                int par) {
+  using C = RCCfg<TY>;
+  constexpr int TX = C::TX, PX = C::PX, PP = C::PP, NI = C::NI, NSL = C::NSL;
+  constexpr int NHR = C::NHR, NHALO = C::NHALO, LY = C::LY;
+  extern __shared__ float2 smem_rc[];
+  // black half-planes [2][PP] (old values), red half-planes [2][PP] (new values)
+  float2 *const sbk = smem_rc;
+  float2 *const srd = smem_rc + 2 * PP;
+  const int g = find_grid(off, ngrid, blockIdx.x);
+  const Grid<float> &Gg = grids[g];
+  if (!grid_active(active, Gg.field)) return;
+  const float *__restrict__ uin = par ? Gg.u2 : Gg.u;
+  float *__restrict__ uout = par ? Gg.u : Gg.u2;
+  float *__restrict__ xout = par ? Gg.x : Gg.x2;
+  const float *__restrict__ fin = Gg.f;
+  const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap,
+              relax = Gg.relax;
+  const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
+  const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
+  int b = blockIdx.x - off[g];
+  const int X0 = (b % ntx) * TX;
+  b /= ntx;
+  const int Y0 = (b % nty) * TY;
+  b /= nty;
+  const int Z0 = b * zc;
+  const int Z1 = min(Z0 + zc, n2);
+  const int P0 = Z0 - 2, nstep = Z1 - Z0 + 4;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long plane = (long long)n0 * n1;
+
+  // slots: NI interior pairs, then (threads < NHALO) one halo pair.
+  // fl: bit 0 load, bit 1 write out, bit 2 / 3 red update of the even / odd
+  // cell; ro: 1 if the red cell of plane P0 is the odd one
+  int q[NSL], roff[NSL], gyv[NSL], gxe[NSL];
+  unsigned fl[NSL], ro[NSL];
+#pragma unroll
+  for (int s = 0; s < NSL; s++) {
+    int px = -1, ly = -1;
+    const bool interior = s < NI;
+    if (interior) {
+      px = 1 + lane;
+      ly = 2 + w + C::NW * s;
+    } else if ((int)threadIdx.x < NHALO) {
+      const int t = threadIdx.x;
+      if (t < NHR) {
+        const int r = t >> 5;
+        px = 1 + lane;
+        ly = r < 2 ? r : TY + r;  // rows 0, 1, TY + 2, TY + 3
+      } else {
+        const int k = t - NHR;
+        px = k < LY ? 0 : PX - 1;
+        ly = k < LY ? k : k - LY;
+      }
+    }
+    q[s] = 0;
+    roff[s] = 0;
+    gyv[s] = 0;
+    gxe[s] = 0;
+    fl[s] = 0;
+    ro[s] = 0;
+    if (px < 0) continue;
+    const int gx = X0 - 2 + 2 * px, gy = Y0 - 2 + ly;
+    q[s] = ly * PX + px;
+    gyv[s] = gy;
+    gxe[s] = gx;
+    ro[s] = (unsigned)((gy + P0) & 1);  // gx even: colour of the even cell = (y + z) & 1
+    bool ok;
+    int gxw, gyw;
+    if (DIR) {
+      ok = gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
+      gxw = gx;
+      gyw = gy;
+    } else {
+      ok = true;
+      gxw = wrapmod(gx, n0);
+      gyw = wrapmod(gy, n1);
+    }
+    if (!ok) continue;
+    roff[s] = gyw * n0 + gxw;
+    unsigned f = 1u;
+    // red update on the tile grown by one cell: x in [X0-1, X0+TX], y in [Y0-1, Y0+TY]
+    const bool yin = gy >= Y0 - 1 && gy <= Y0 + TY;
+    if (yin && gx >= X0 - 1 && gx <= X0 + TX) f |= 4u;
+    if (yin && gx + 1 >= X0 - 1 && gx + 1 <= X0 + TX) f |= 8u;
+    if (interior && gx < n0 && gy < n1) f |= 2u;
+    fl[s] = f;
+  }
+
+  // register ring: plane P0 + k in slot k & 3; red and black cell (u, x), f
+  float2 R[NSL][4], B[NSL][4];
+  float FR[NSL][4], FB[NSL][4];
+  float2 pu[NSL], pf[NSL];  // prefetched plane (u, f of the even and odd cell)
+#pragma unroll
+  for (int s = 0; s < NSL; s++) {
+    pu[s] = make_float2(0.f, 0.f);
+    pf[s] = pu[s];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      R[s][r] = pu[s];
+      B[s][r] = pu[s];
+      FR[s][r] = 0.f;
+      FB[s][r] = 0.f;
+    }
+  }
+  int pw = DIR ? P0 : wrapmod(P0, n2);  // wrapped index of the next plane to load
+  auto fetch = [&]() {
+    if (!DIR || (pw >= 0 && pw < n2)) {
+      const long long zo = (long long)pw * plane;
+#pragma unroll
+      for (int s = 0; s < NSL; s++) {
+        if (!(fl[s] & 1u)) continue;
+        pu[s] = *reinterpret_cast<const float2 *>(uin + zo + roff[s]);
+        if (fin) pf[s] = *reinterpret_cast<const float2 *>(fin + zo + roff[s]);
+      }
+    }
+    pw = DIR ? pw + 1 : (pw + 1 == n2 ? 0 : pw + 1);
+  };
+  fetch();
+
+  // Newton update of one cell: own (u, x, f), neighbours -x, +x, -y, +y, -z, +z
+  // as (u, x); the same face order and arithmetic as k_smooth_rb
+  auto newton = [&](float2 own, float fi, float2 lf, float2 rt, float2 ym, float2 yp, float2 zm,
+                    float2 zp, int gx, int gy, int m) -> float {
+    const float di = own.x, xi = own.y;
+    const float Bi = 1.0f + xi;
+    OpAcc<float, false> A(di, 1.0f, xi, Bi, 0.0f);
+    if (DIR && gx == 0)
+      A.ghost(face_value(Gg, 0, gx, gy, m));
+    else
+      A.reg(lf.x, lf.y, 0.0f, 1.0f);
+    if (DIR && gx == n0 - 1)
+      A.ghost(face_value(Gg, 1, gx, gy, m));
+    else
+      A.reg(rt.x, rt.y, 0.0f, 1.0f);
+    if (DIR && gy == 0)
+      A.ghost(face_value(Gg, 2, gx, gy, m));
+    else
+      A.reg(ym.x, ym.y, 0.0f, 1.0f);
+    if (DIR && gy == n1 - 1)
+      A.ghost(face_value(Gg, 3, gx, gy, m));
+    else
+      A.reg(yp.x, yp.y, 0.0f, 1.0f);
+    if (DIR && m == 0)
+      A.ghost(face_value(Gg, 4, gx, gy, m));
+    else
+      A.reg(zm.x, zm.y, 0.0f, 1.0f);
+    if (DIR && m == n2 - 1)
+      A.ghost(face_value(Gg, 5, gx, gy, m));
+    else
+      A.reg(zp.x, zp.y, 0.0f, 1.0f);
+    float acc, dacc, N, dN;
+    A.done(acc, dacc);
+    finish_op(xi, 1.0f, acc, dacc, ah, beta, false, N, dN);
+    float du = relax * newton_step(N - fi, dN);
+    du = fminf(fmaxf(du, -cap), cap);
+    return di + du;
+  };
+  auto sel = [](bool c, float2 a, float2 b) { return c ? a : b; };
+
+  auto step = [&](auto Kc, int k) {
+    constexpr int K = decltype(Kc)::value;  // ring slot of plane p
+    constexpr int K1 = (K + 3) & 3, K2 = (K + 2) & 3, K3 = (K + 1) & 3;
+    constexpr unsigned PK = K & 1, PK1 = K1 & 1, PK2 = K2 & 1;  // plane parities (rel. P0)
+    const int p = P0 + k;
+    // 1. plane p from the prefetch registers; publish its black cells
+    {
+      const bool inz = !DIR || (p >= 0 && p < n2);
+#pragma unroll
+      for (int s = 0; s < NSL; s++) {
+        if (!(fl[s] & 1u)) continue;
+        const bool odd = (ro[s] ^ PK) != 0;  // red cell is the odd one
+        const float ur = odd ? pu[s].y : pu[s].x, ub = odd ? pu[s].x : pu[s].y;
+        // the red cell's x is needed only if this pair's red cell is updated
+        const bool needr = s < NI || (fl[s] & (odd ? 8u : 4u));
+        R[s][K] = make_float2(ur, needr ? m_expm1(ur) : 0.0f);
+        B[s][K] = make_float2(ub, m_expm1(ub));
+        if (fin) {
+          const float fr = odd ? pf[s].y : pf[s].x, fb = odd ? pf[s].x : pf[s].y;
+          FR[s][K] = fs * (fr - fo);
+          FB[s][K] = fs * (fb - fo);
+        } else {
+          FR[s][K] = 0.0f;
+          FB[s][K] = 0.0f;
+        }
+        if (inz) sbk[PK * PP + q[s]] = B[s][K];
+      }
+    }
+    if (k + 1 < nstep) fetch();
+    // 2. red cells of plane m = p - 1 on the grown tile
+    {
+      const int m = p - 1;
+      if (m >= Z0 - 1 && m <= Z1 && (!DIR || (m >= 0 && m < n2))) {
+#pragma unroll
+        for (int s = 0; s < NSL; s++) {
+          const bool odd = (ro[s] ^ PK1) != 0;
+          if (!((s < NI && !DIR) || (fl[s] & (odd ? 8u : 4u)))) continue;
+          const float2 *bk = sbk + PK1 * PP + q[s];
+          const float2 ym = bk[-PX], yp = bk[PX];
+          const float2 nx = bk[odd ? 1 : -1];
+          const float un = newton(R[s][K1], FR[s][K1], sel(odd, B[s][K1], nx),
+                                  sel(odd, nx, B[s][K1]), ym, yp, B[s][K2], B[s][K],
+                                  gxe[s] + (odd ? 1 : 0), gyv[s], m);
+          R[s][K1] = make_float2(un, m_expm1(un));
+          srd[PK1 * PP + q[s]] = R[s][K1];
+        }
+      }
+    }
+    // 3. black cells of plane m = p - 2 on the tile, then plane m is final
+    {
+      const int m = p - 2;
+      if (m >= Z0 && m < Z1 && (!DIR || (m >= 0 && m < n2))) {
+#pragma unroll
+        for (int s = 0; s < NI; s++) {
+          if (DIR && !(fl[s] & 1u)) continue;
+          const bool odd = (ro[s] ^ PK2) == 0;  // black cell is the odd one
+          const float2 *rd = srd + PK2 * PP + q[s];
+          const float2 ym = rd[-PX], yp = rd[PX];
+          const float2 nx = rd[odd ? 1 : -1];
+          const float un = newton(B[s][K2], FB[s][K2], sel(odd, R[s][K2], nx),
+                                  sel(odd, nx, R[s][K2]), ym, yp, R[s][K3], R[s][K1],
+                                  gxe[s] + (odd ? 1 : 0), gyv[s], m);
+          B[s][K2] = make_float2(un, m_expm1(un));
+          if (fl[s] & 2u) {
+            const float2 e = sel(odd, R[s][K2], B[s][K2]), o = sel(odd, B[s][K2], R[s][K2]);
+            const long long oo = (long long)m * plane + roff[s];
+            *reinterpret_cast<float2 *>(uout + oo) = make_float2(e.x, o.x);
+            *reinterpret_cast<float2 *>(xout + oo) = make_float2(e.y, o.y);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  };
+  for (int k = 0; k < nstep; k += 4) {
+    step(std::integral_constant<int, 0>{}, k);
+    if (k + 1 < nstep) step(std::integral_constant<int, 1>{}, k + 1);
+    if (k + 2 < nstep) step(std::integral_constant<int, 2>{}, k + 2);
+    if (k + 3 < nstep) step(std::integral_constant<int, 3>{}, k + 3);
+  }
+}
+
 // Tiled FAS right-hand side of a coarse level, f <- A(u) - f (the same
 // operator evaluation, face order and arithmetic as k_fas_rhs): a block owns a
 // 64 x 16 tile and a chunk of zc planes and marches along z with a ring of

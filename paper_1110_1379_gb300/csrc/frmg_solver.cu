@@ -436,6 +436,9 @@ constexpr int kTX = 64, kTY = 16;
 // tile height of k_smooth_rb: 64 x 16 tiles leave room for three resident
 // blocks per SM (more loads in flight than two blocks of 64 x 32 tiles)
 constexpr int kRbTY = 16;
+// plain-form one-sweep smoother of the solves when fr_opts.smooth_tile = 0:
+// the register-column kernel on 64 x kDefaultSmoothTile tiles (-1 = k_smooth_rb)
+constexpr int kDefaultSmoothTile = 16;
 
 template <typename T>
 struct LevelSet {
@@ -458,6 +461,13 @@ struct LevelSet {
   std::vector<int> off_rb[2];
   int *d_off_rb[2] = {nullptr, nullptr};
   int nblk_rb[2] = {0, 0};
+  // register-column one-sweep smoother of the plain form (64 x rc_ty tiles;
+  // 0: the plain form uses k_smooth_rb too)
+  int rc_ty = 0;
+  int zc_rc = 0;
+  std::vector<int> off_rc;
+  int *d_off_rc = nullptr;
+  int nblk_rc = 0;
   // tiled FAS right-hand side (coarse side of a V-cycle level); [0] plain,
   // [1] correction form
   int zc_fr[2] = {0, 0};
@@ -547,6 +557,8 @@ static int pick_chunk(const std::vector<long long> &tiles, const std::vector<int
 
 template <bool BG, bool DIR>
 static long long rb_slots();
+template <bool DIR, int TY>
+static long long rc_slots();
 template <bool BG, bool DIR>
 static long long fr_slots();
 template <bool DIR>
@@ -555,7 +567,8 @@ template <bool DIR>
 static long long rr_slots();
 
 template <typename T>
-static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 0) {
+static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 0,
+                       int stile = 0) {
   if (ls.empty()) return;
   int ng = ls.size();
   ls.off_half.assign(ng + 1, 0);
@@ -633,6 +646,22 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 
         ls.nblk_rb[v] = ls.off_rb[v][ng];
         ls.d_off_rb[v] = S.get<int>(ng + 1);
         CK(cudaMemcpyAsync(ls.d_off_rb[v], ls.off_rb[v].data(), (ng + 1) * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+      }
+      if (stile == 8 || stile == 16) {
+        ls.rc_ty = stile;
+        for (int g = 0; g < ng; g++)
+          tl[g] = (long long)((ls.h[g].n0 + kTX - 1) / kTX) * ((ls.h[g].n1 + stile - 1) / stile);
+        const long long slots =
+            stile == 8 ? (ls.dirichlet ? rc_slots<true, 8>() : rc_slots<false, 8>())
+                       : (ls.dirichlet ? rc_slots<true, 16>() : rc_slots<false, 16>());
+        ls.zc_rc = pick_chunk(tl, n2s, slots, 4, false);
+        ls.off_rc.assign(ng + 1, 0);
+        for (int g = 0; g < ng; g++)
+          ls.off_rc[g + 1] = ls.off_rc[g] + (int)(tl[g] * ((n2s[g] + ls.zc_rc - 1) / ls.zc_rc));
+        ls.nblk_rc = ls.off_rc[ng];
+        ls.d_off_rc = S.get<int>(ng + 1);
+        CK(cudaMemcpyAsync(ls.d_off_rc, ls.off_rc.data(), (ng + 1) * sizeof(int),
                            cudaMemcpyHostToDevice, st));
       }
       for (int g = 0; g < ng; g++)
@@ -717,7 +746,8 @@ struct Hier {
 
 template <typename T, bool BG>
 static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap,
-                       cudaStream_t st, frmg_ctx *ctx, int tiling = 0, double relax = 1.0) {
+                       cudaStream_t st, frmg_ctx *ctx, int tiling = 0, double relax = 1.0,
+                       int stile = 0) {
   int np = (int)P.size();
   H.lev.assign(np, {});
   H.depth = 0;
@@ -813,10 +843,10 @@ static void build_hier(Scope &S, Hier<T> &H, std::vector<Problem> &P, double cap
     }
   }
   for (int l = 0; l < H.depth; l++) {
-    upload_set(S, H.cont[l], st, tiling);
-    upload_set(S, H.next[l], st, tiling);
-    upload_set(S, H.coarsest[l], st, tiling);
-    upload_set(S, H.all[l], st, tiling);
+    upload_set(S, H.cont[l], st, tiling, stile);
+    upload_set(S, H.next[l], st, tiling, stile);
+    upload_set(S, H.coarsest[l], st, tiling, stile);
+    upload_set(S, H.all[l], st, tiling, stile);
   }
 }
 
@@ -887,9 +917,25 @@ static void launch_rr_tiled(frmg_ctx *ctx, LevelSet<float> &F, LevelSet<float> &
     launch_rr_k<BG, false>(ctx, F, C, active, fpar, cpar, partial, st);
 }
 
+template <bool DIR, int TY>
+static void launch_rc_k(LevelSet<float> &s, const int *active, int par, cudaStream_t st) {
+  using RC = RCCfg<TY>;
+  const size_t sm = RC::smem();
+  static bool attr_set = false;
+  if (!attr_set) {
+    CK(cudaFuncSetAttribute(k_smooth_rc<DIR, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)sm));
+    attr_set = true;
+  }
+  k_smooth_rc<DIR, TY><<<s.nblk_rc, RC::NT, sm, st>>>(s.d, s.d_off_rc, s.size(), s.zc_rc, active,
+                                                       par);
+}
+
 template <bool BG, bool DIR>
 static void launch_rb_k(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
                         cudaStream_t st) {
+  if (!BG && s.rc_ty == 16) return launch_rc_k<DIR, 16>(s, active, par, st);
+  if (!BG && s.rc_ty == 8) return launch_rc_k<DIR, 8>(s, active, par, st);
   constexpr int TY = kRbTY;
   using RC = RBCfg<TY>;
   size_t sm = RC::smem(BG);
@@ -927,6 +973,15 @@ static long long rb_slots() {
     slots = (long long)sm_count() *
             resident_blocks(k_smooth_rb<BG, DIR, kRbTY>, RC::NT, RC::smem(BG));
   }
+  return slots;
+}
+
+template <bool DIR, int TY>
+static long long rc_slots() {
+  static long long slots = 0;
+  if (!slots)
+    slots = (long long)sm_count() *
+            resident_blocks(k_smooth_rc<DIR, TY>, RCCfg<TY>::NT, RCCfg<TY>::smem());
   return slots;
 }
 
@@ -1312,6 +1367,7 @@ struct SolveCfg {
   double tau_alpha;  // > 0: truncation-error stopping rule (Sec. V.B.2)
   double relax;      // relaxation factor of the Newton-GS updates
   int fmg;           // full-multigrid start (mixed, single field, u0 = 0)
+  int stile;         // plain FP32 one-sweep smoother: 8/16 register-column tiles, -1 ring
 };
 
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
@@ -1423,7 +1479,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
   for (auto &p : P1) p.nl = 1;
   build_hier<double, false>(S, H64, P1, cfg.cap, st, ctx);
   Hier<float> H;
-  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling, cfg.relax);
+  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling, cfg.relax, cfg.stile);
   std::vector<double *> d64(np);
   int *flag = S.get<int>(1);
   CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
@@ -1706,7 +1762,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   Scope S(ctx);
   const int np = (int)P.size();
   Hier<float> H;
-  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling, cfg.relax);
+  build_hier<float, true>(S, H, P, cfg.cap, st, ctx, cfg.tiling, cfg.relax, cfg.stile);
   const double ln2 = std::log(2.0);
   float ln2h, ln2l;
   split_host(ln2, ln2h, ln2l);
@@ -2124,8 +2180,11 @@ static void run_problems(frmg_ctx *ctx, std::vector<Problem> &P, const fr_opts &
   cudaStream_t st = side.st;
   SolveCfg cfg{tol, o.max_vcycles, o.pre, o.post, o.newton_step_cap, o.inner_cycles,
                o.max_outer, fixed, o.temporal_depth <= 0 ? 1 : o.temporal_depth, o.tiling,
-               o.defect_precision, o.use_graph, o.tau_alpha, o.relax, o.fmg};
+               o.defect_precision, o.use_graph, o.tau_alpha, o.relax, o.fmg,
+               o.smooth_tile == 0 ? kDefaultSmoothTile : o.smooth_tile};
   if (o.defect_precision < 0 || o.defect_precision > 1) einval("defect_precision must be 0 or 1");
+  if (!(o.smooth_tile == 0 || o.smooth_tile == -1 || o.smooth_tile == 8 || o.smooth_tile == 16))
+    einval("smooth_tile must be 0, -1, 8 or 16");
   if (cfg.tdepth > 2) einval("temporal_depth must be 0, 1 or 2");
   if (o.pre < 0 || o.post < 0 || o.max_vcycles < 0 || !(o.newton_step_cap > 0) ||
       !(tol >= 0) || o.inner_cycles < 1 || o.max_outer < 1)
@@ -2308,6 +2367,7 @@ void fr_opts_default(fr_opts *o) {
   o->relax = 1.0;
   o->fmg = 0;
   o->initial_guess = 1;
+  o->smooth_tile = 0;
 }
 
 const char *fr_status_string(int s) {
@@ -2537,6 +2597,15 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
       o = best_o;
       o.tiling = 1;
       trial(o);
+      // kernel and tile of the plain one-sweep smoother: register columns on
+      // 64 x 16 (the default) or 64 x 8 tiles, or the shared-memory plane ring
+      if (best_o.smooth_tile == 0) best_o.smooth_tile = kDefaultSmoothTile;
+      for (int t : {16, 8, -1}) {
+        if (t == best_o.smooth_tile) continue;
+        o = best_o;
+        o.smooth_tile = t;
+        trial(o);
+      }
     }
     frmg_release(ctx, u);
     if (rho != density) frmg_release(ctx, const_cast<double *>(rho));
@@ -2849,9 +2918,11 @@ int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, cons
       CK_LAUNCH(ctx);
       G.Ebg = E;
     }
+    if (!(tiled == 0 || tiled == 1 || tiled == 8 || tiled == 16))
+      einval("tiled must be 0, 1, 8 or 16");
     LevelSet<float> ls;
     ls.h.push_back(G);
-    upload_set(S, ls, st);
+    upload_set(S, ls, st, 0, tiled > 1 ? tiled : 0);
     if (tiled && !ls.tiled_ok) einval("tiled smoothing needs at least 16 cells a side");
     ls.tiled = tiled != 0;
     std::vector<int> plan(nsweeps, 1);  // one sweep per tiled pass, as in the solves

@@ -30,7 +30,8 @@ class fr_opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("temporal_depth", ctypes.c_int),
                 ("tiling", ctypes.c_int), ("defect_precision", ctypes.c_int),
                 ("tau_alpha", ctypes.c_double), ("relax", ctypes.c_double),
-                ("fmg", ctypes.c_int), ("initial_guess", ctypes.c_int)]
+                ("fmg", ctypes.c_int), ("initial_guess", ctypes.c_int),
+                ("smooth_tile", ctypes.c_int)]
 
 
 FR_HIST = 64

@@ -76,6 +76,7 @@ def test_options_struct_matches_the_header(lib):
     assert (o.newton_step_cap, o.inner_cycles, o.max_outer) == (1.0, 2, 40)
     assert (o.allow_negative_density, o.use_graph, o.temporal_depth, o.tiling) == (0, 1, 0, 0)
     assert (o.defect_precision, o.tau_alpha, o.relax, o.fmg, o.initial_guess) == (0, 0.0, 1.0, 0, 1)
+    assert o.smooth_tile == 0
     src = open(os.path.join(ROOT, "include", "frmg.h")).read()
     body = src[src.index("typedef struct {\n    double tol;"):src.index("} fr_opts;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)

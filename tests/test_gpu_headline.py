@@ -89,6 +89,9 @@ SETTINGS = {
     "default": dict(prec="mixed"),
     "tuned": dict(prec="mixed", **TUNED),
     "tuned_fp64_defect": dict(prec="mixed", defect_precision=1, **TUNED),
+    "tuned_ring_smoother": dict(prec="mixed", smooth_tile=-1, **TUNED),
+    "tuned_rc8_smoother": dict(prec="mixed", smooth_tile=8, **TUNED),
+    "tuned_rc16_smoother": dict(prec="mixed", smooth_tile=16, **TUNED),
     "autotuned": None,
     "fp64": dict(prec="fp64"),
 }
@@ -105,7 +108,8 @@ def test_proxy_128_matches_oracle(C, proxy, fr0, setting):
     if opts is None:
         best, _ = C.autotune(r, tol=1e-8, prec="mixed", **P)
         opts = {k: best[k] for k in ("prec", "pre", "post", "temporal_depth", "relax", "fmg",
-                                     "tiling")}
+                                     "tiling", "smooth_tile")}
+        assert opts["smooth_tile"] in (16, 8, -1)
     u = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
     st, s = C.solve(r, u, tol=1e-8, **opts, **P)
     assert st == 0 and s.res_rms <= 1e-8, (setting, fr0, s.as_dict())
@@ -122,6 +126,17 @@ def test_proxy_128_matches_oracle(C, proxy, fr0, setting):
           f"max|du|={du:.2e} grad_fR max_rel={gmax:.2e} rms_rel={grms:.2e}")
     assert du <= 1e-6
     assert gmax <= 1e-6 and grms <= 1e-7
+    _solutions[(fr0, setting)] = (uh, s.vcycles, s.outer)
+    # every kernel choice of the plain FP32 smoother performs the same sweeps,
+    # so the solves are identical
+    group = [k for k in ("tuned_ring_smoother", "tuned_rc8_smoother", "tuned_rc16_smoother")
+             if (fr0, k) in _solutions]
+    if setting in group and len(group) > 1:
+        a, b = _solutions[(fr0, group[0])], _solutions[(fr0, setting)]
+        assert a[1:] == b[1:] and np.array_equal(a[0], b[0])
+
+
+_solutions = {}
 
 
 def sampled_vs_fp64(uh, rhoh, dh, *, box, fr0, h, nsample=200, seed=0):

@@ -288,6 +288,29 @@ def test_f32_tiled_smoother_equals_simple(C, shape, bg, faces, nsweeps):
     assert np.abs(outs[0] - outs[1]).max() < 2e-6
 
 
+@pytest.mark.parametrize("shape", F32_SHAPES + [(64, 48, 256), (40, 130, 66)])
+@pytest.mark.parametrize("faces", [False, True])
+@pytest.mark.parametrize("nsweeps", [1, 2, 3])
+def test_register_column_smoother_is_the_ring_smoother(C, shape, faces, nsweeps):
+    """The register-column one-sweep kernel (64 x 8 and 64 x 16 tiles) performs
+    the same sweeps as the shared-memory plane-ring kernel, bit for bit: same
+    cells, same face order, same arithmetic (x = expm1(u) recomputed from u
+    equals the cached x)."""
+    rng = np.random.default_rng(31)
+    u0 = rng.uniform(-1.5, 0.3, shape)
+    f = rng.standard_normal(shape) * 0.3
+    ub = rng.uniform(-1.5, 0.3, sum(O.face_sizes(shape))) if faces else None
+    P = dict(box=128.0, a=0.9, omega_m=0.24, fr0=1e-5, h=1.0 / 48)
+    outs = {}
+    for tiled in (1, 8, 16):
+        u = _f32(u0)
+        C.smooth_f32(u, nsweeps, f=_f32(f), ub=None if ub is None else _f32(ub), tiled=tiled,
+                     **P)
+        outs[tiled] = host(u)
+    assert np.array_equal(outs[1], outs[8])
+    assert np.array_equal(outs[1], outs[16])
+
+
 @pytest.mark.parametrize("bg", [False, True])
 @pytest.mark.parametrize("faces", [False, True])
 def test_f32_smoother_matches_oracle(C, bg, faces):
@@ -381,9 +404,11 @@ def test_autotune_returns_a_converging_setting(C):
     assert (best["pre"], best["post"]) in [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3)]
     assert best["temporal_depth"] in (1, 2) and secs > 0
     assert best["relax"] in (1.0, 1.15, 1.25)
+    assert best["smooth_tile"] in (16, 8, -1)
     u = torch.zeros(shape, dtype=torch.float64, device="cuda")
     st, s = C.solve(dev(rho), u, tol=1e-8, prec="mixed", pre=best["pre"], post=best["post"],
-                    temporal_depth=best["temporal_depth"], relax=best["relax"], **CFG1)
+                    temporal_depth=best["temporal_depth"], relax=best["relax"],
+                    smooth_tile=best["smooth_tile"], **CFG1)
     assert st == 0
     assert np.abs(host(u) - O.solve(rho, tol=1e-8, **CFG1).u).max() <= 1e-6
 
