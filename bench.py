@@ -88,7 +88,7 @@ def parse_args():
                     help="'mixed' skips the FP64 comparison (profiling runs)")
     ap.add_argument("--workload", default="solve512",
                     choices=["solve512", "batch96", "levels256", "cic128", "small32", "poisson512",
-                             "masked256"],
+                             "masked256", "symmetron512"],
                     help="secondary workloads print their own line (default: the 512^3 solve)")
     ap.add_argument("--options", default="",
                     help="solver options for the headline solve instead of fr_autotune "
@@ -559,6 +559,53 @@ def run_secondary(args):
                     effective_gbs=alg / t / 1e9,
                     effective_frac_of_hbm=alg / t / 1e9 / _hbm_peak(),
                     oracle_fft_128_cells_per_s=ns ** 3 / t_or)
+    elif args.workload == "symmetron512":
+        # the symmetron field (second scalar-field model) on the headline's
+        # 512^3 grid and density: 0.5 Mpc/h cells, lognormal sigma 2, seed
+        # 3000, a = 1, a_SSB = 0.5, lambda_0 = 1 Mpc/h, from the homogeneous
+        # positive solution to rms(L) <= 1e-8
+        from oracle import symmetron as OS
+        n = N
+        SP = dict(box=256.0, a=1.0, a_ssb=0.5, lambda0=1.0)
+        rho = torch.from_numpy(synth.lognormal_density((n,) * 3, SEED, sigma=SIGMA)).cuda()
+        chi = torch.empty_like(rho)
+        stats = []
+
+        def run(prec, **o):
+            st, s = ctx.symmetron(rho, chi, tol=TOL, prec=prec, initial_guess=0, **o, **SP)
+            assert st == 0
+            stats.append(s)
+        scands = [dict(pre=2, post=2, relax=1.0), dict(pre=1, post=1, relax=1.0),
+                  dict(pre=2, post=1, relax=1.0), dict(pre=2, post=2, relax=1.15)]
+        sopts, stimes = pick_options(lambda **o: run("mixed", **o), scands)
+        t = timed(lambda: run("mixed", **sopts), args.steps, args.warmup)
+        s = stats[-1]
+        chi_m = chi.clone()
+        t64 = timed(lambda: run("fp64"), 1, 1)
+        s64 = stats[-1]
+        du = float((chi_m - chi).abs().max())
+        # algorithmic bytes: per fine V(pre,post) cycle, (pre + post) sweeps of
+        # 20 B (delta, g, rho, f read; delta written), residual + restriction
+        # 16 B + 1.5 B of coarse writes, prolongation 8 B + 1 B, x 8/7 for the
+        # coarse levels; per outer step the FP64 defect (chi, rho: 16 B), the
+        # set-up (chi, d in; g, f, delta out: 28 B) and the update (20 B)
+        alg = n ** 3 * (s.vcycles * (20.0 * (sopts["pre"] + sopts["post"]) + 26.5) * 8 / 7 +
+                        (s.outer + 1) * 16.0 + s.outer * 48.0)
+        # CPU oracle (numpy, FP64) on a bounded 64^3 sample of the same recipe
+        ns = 64
+        rs = synth.lognormal_density((ns,) * 3, SEED, sigma=SIGMA)
+        t0 = time.perf_counter()
+        ro = OS.solve(rs, box=0.5 * ns, a=1.0, a_ssb=0.5, lambda0=1.0, tol=TOL)
+        t_or = time.perf_counter() - t0
+        line.update(metric="symmetron field solve (second scalar-field model) on the 512^3 "
+                           "headline grid and density: cells/s to rms 1e-8",
+                    value=n ** 3 / t, ms=1e3 * t, vcycles=s.vcycles, outer=s.outer,
+                    res_rms=s.res_rms, fp64=n ** 3 / t64, fp64_vcycles=s64.vcycles,
+                    max_abs_dchi_mixed_vs_fp64=du,
+                    effective_gbs=alg / t / 1e9, effective_frac_of_hbm=alg / t / 1e9 / _hbm_peak(),
+                    dtype="f32+f64 (mixed)",
+                    tuned={**sopts, "candidates_s": stimes},
+                    oracle_64_cells_per_s=ns ** 3 / t_or, oracle_64_vcycles=ro.cycles)
     else:  # small32
         from oracle import oracle as O
         rho_np = synth.lognormal_density((32,) * 3, 1000, sigma=1.0)

@@ -416,6 +416,39 @@ int fr_solve_masked(frmg_ctx *ctx, const double *density, const double *mask, co
                     double tol, double *u_inout, const fr_opts *opts, fr_stats *stats,
                     void *stream);
 
+/*
+ * Symmetron field equation (a second scalar-field model on the same FAS
+ * machinery; the paper's Sec. I and VII name the symmetron of Hinterbichler &
+ * Khoury 2010 among the models its solver carries over to).  In
+ * chi = phi / phi_0 (phi_0 the vacuum value), with the vacuum range lambda0
+ * (Mpc/h) and the expansion factor a_ssb at which the mean matter density
+ * falls to the symmetry-breaking density, the quasi-static comoving equation
+ *   laplacian chi = (a^2 / (2 lambda0^2)) [ ((a_ssb / a)^3 rho - 1) chi + chi^3 ]
+ * is discretised with the 7-point Laplacian (Sec. IV) on a periodic grid of
+ * cells of box / dims[0] Mpc/h and solved as
+ *   L_i = A sum_{6 faces} (chi_j - chi_i) - [ (s rho_i - 1) chi_i + chi_i^3 ] = 0,
+ *   A = 2 lambda0^2 / (a^2 (box / dims[0])^2),  s = (a_ssb / a)^3,
+ * by FAS V-cycles of red-black Newton-Gauss-Seidel (Sec. V.B.2: 8-child
+ * average restriction, trilinear prolongation, A / 4 per coarser level) until
+ * rms(L) <= tol.  The field is symmetric under chi -> -chi; the solution
+ * sought is the positive branch, reached from a positive initial guess.
+ * density: rho (mean 1, finite and >= 0), [n2][n1][n0]; chi_inout: initial
+ * guess in (opts->initial_guess = 0: start from the homogeneous positive
+ * solution sqrt(1 - s), or 1 before symmetry breaking), solution out.  Host
+ * or device pointers.  opts: pre, post, newton_step_cap, relax, max_vcycles,
+ * max_outer, initial_guess, prec: FR_FP64 = every step in FP64; FR_MIXED =
+ * FP64 residual, update and convergence test around FP32 FAS V-cycles of
+ * the correction equation L(g + delta) - L(g) = -L(chi), g = fp32(chi), run
+ * until their fine residual is predicted below max(0.1 tol, 1e-6 rms L(chi))
+ * (at most max_vcycles per outer step).  stats: vcycles, outer, res0_rms,
+ * res_rms, res_max, seconds, hist.  FR_EINVAL for bad arguments or density,
+ * FR_ENOCONV if tol is not reached (chi holds the last iterate),
+ * FR_EDIVERGED for a non-finite or growing residual.  Synchronous on return.
+ */
+int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const int dims[3],
+                       double box_mpc_h, double a, double a_ssb, double lambda0, double tol,
+                       double *chi_inout, const fr_opts *opts, fr_stats *stats, void *stream);
+
 /* Number of kernel launches this context issued since it was created. */
 long long fr_launch_count(const frmg_ctx *ctx);
 

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfrmg.so")
 SOURCES = ["frmg_solver.cu", "frmg_cic.cu", "frmg_noalloc.cu", "frmg_poisson.cu",
-           "frmg_masked.cu"]
+           "frmg_masked.cu", "frmg_symmetron.cu"]
 HEADERS = ["frmg_kernels.cuh", "frmg_df.cuh", "frmg_dfmath.cuh", "frmg_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

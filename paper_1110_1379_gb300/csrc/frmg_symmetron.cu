@@ -1,0 +1,720 @@
+// frmg_symmetron.cu -- FAS multigrid solve of the symmetron field equation on
+// a periodic grid (sm_103a), the second scalar-field model on the machinery
+// of the f(R) solver.
+//
+// The paper (Sec. I, Sec. VII) lists the symmetron (Hinterbichler & Khoury
+// 2010) among the screened models whose equations its multigrid solver
+// carries over to.  In chi = phi / phi_0 (phi_0 the vacuum value), with the
+// vacuum range lambda_0 and the expansion factor a_SSB at which the mean
+// matter density falls to the symmetry-breaking density, the quasi-static
+// comoving equation is
+//   laplacian chi = (a^2 / (2 lambda_0^2)) [ ((a_SSB / a)^3 rho - 1) chi + chi^3 ],
+// rho the density in units of its mean.  Discretised with the 7-point
+// Laplacian (Sec. IV) and divided by the bracket's coefficient, on a grid of
+// cells of B h Mpc/h:
+//   L_i(chi) = A sum_{6 faces} (chi_j - chi_i) - [ (s rho_i - 1) chi_i + chi_i^3 ],
+//   A = 2 lambda_0^2 / (a^2 (B h)^2),  s = (a_SSB / a)^3,
+// dL_i/dchi_i = -6 A - [ (s rho_i - 1) + 3 chi_i^2 ].
+// The solve is the paper's (Sec. V.B.2): red-black Newton-Gauss-Seidel
+// sweeps, FAS V-cycles (8-child average restriction of chi, of the residual
+// and of the density; trilinear 27/9/3/1 prolongation of Sec. V.A.3), the
+// coarse operator the same L with A / 4 per level.
+//
+// Precision: FR_FP64 runs every step in FP64.  FR_MIXED is a defect
+// correction: the FP64 residual d = L(chi) and test rms(d) <= tol, and FP32
+// FAS V-cycles on the correction equation
+//   N(delta) = L(g + delta) - L(g) = -d,   g = fp32(chi) per level (restricted),
+//   N_i = A sum (delta_j - delta_i) - delta_i [ (s rho_i - 1 + 3 g_i^2) + delta_i (3 g_i + delta_i) ],
+// every term carrying a factor of delta (FP32 rounding relative to the
+// correction), then chi += delta in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "frmg.h"
+#include "frmg_internal.h"
+
+namespace {
+
+struct SError {
+  int status;
+  std::string msg;
+};
+
+#define SCK(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      cudaGetLastError();                                                           \
+      throw SError{FR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};   \
+    }                                                                               \
+  } while (0)
+#define SLAUNCH(ctx)                                                                      \
+  do {                                                                                    \
+    frmg_launch_counter(ctx)++;                                                           \
+    cudaError_t e_ = cudaGetLastError();                                                  \
+    if (e_ != cudaSuccess)                                                                \
+      throw SError{FR_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)};    \
+  } while (0)
+
+constexpr int kNT = 256;
+
+struct SArena {
+  frmg_ctx *c;
+  std::vector<void *> ptrs;
+  explicit SArena(frmg_ctx *c_) : c(c_) {}
+  template <typename T>
+  T *get(size_t n) {
+    void *p = nullptr;
+    try {
+      p = frmg_alloc(c, std::max<size_t>(n, 1) * sizeof(T));
+    } catch (...) {
+      throw SError{FR_ENOMEM, "device allocation failed"};
+    }
+    ptrs.push_back(p);
+    return (T *)p;
+  }
+  ~SArena() {
+    for (void *p : ptrs) frmg_release(c, p);
+  }
+};
+
+// One level of the hierarchy.  Full form (FP64 solve): u = chi.  Correction
+// form (FP32 inner solve): u = delta, g = background fp32(chi) restricted.
+template <typename T>
+struct SLevel {
+  T *u;            // unknown
+  T *uR;           // restricted fine unknown (coarse levels)
+  T *f;            // right-hand side (FAS); null = 0
+  const T *rho;    // density (mean 1), restricted on coarse levels
+  const float *g;  // background (correction form), null otherwise
+  int n0, n1, n2;
+  long long nc;
+  T A, s, cap, relax;
+};
+
+template <typename T>
+__device__ __forceinline__ void sy_ijk(const SLevel<T> &L, long long c, int &i, int &j, int &k) {
+  i = (int)(c % L.n0);
+  const long long r = c / L.n0;
+  j = (int)(r % L.n1);
+  k = (int)(r / L.n1);
+}
+
+// N_i and dN_i/du_i at cell (i, j, k); CORR selects the correction form.
+template <typename T, bool CORR>
+__device__ __forceinline__ void sy_op(const SLevel<T> &L, int i, int j, int k, T &N, T &dN) {
+  const long long sx = 1, sy = L.n0, sz = (long long)L.n0 * L.n1;
+  const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
+  const T ui = L.u[c];
+  const long long xm = i > 0 ? c - sx : c + (L.n0 - 1) * sx;
+  const long long xp = i < L.n0 - 1 ? c + sx : c - (L.n0 - 1) * sx;
+  const long long ym = j > 0 ? c - sy : c + (L.n1 - 1) * sy;
+  const long long yp = j < L.n1 - 1 ? c + sy : c - (L.n1 - 1) * sy;
+  const long long zm = k > 0 ? c - sz : c + (L.n2 - 1) * sz;
+  const long long zp = k < L.n2 - 1 ? c + sz : c - (L.n2 - 1) * sz;
+  const T lap = (L.u[xm] - ui) + (L.u[xp] - ui) + (L.u[ym] - ui) + (L.u[yp] - ui) +
+                (L.u[zm] - ui) + (L.u[zp] - ui);
+  const T m = L.s * L.rho[c] - T(1);
+  if (CORR) {
+    const T gi = (T)L.g[c];
+    const T lin = m + T(3) * gi * gi;
+    N = L.A * lap - ui * (lin + ui * (T(3) * gi + ui));
+    const T w = gi + ui;
+    dN = T(-6) * L.A - (m + T(3) * w * w);
+  } else {
+    N = L.A * lap - (m * ui + ui * ui * ui);
+    dN = T(-6) * L.A - (m + T(3) * ui * ui);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T sy_rhs(const SLevel<T> &L, long long c) {
+  return L.f ? L.f[c] : T(0);
+}
+
+// One colour of a red-black Newton-Gauss-Seidel sweep (red = (i + j + k) even).
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(kNT) k_sy_smooth(SLevel<T> L, int colour) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * t >= L.nc) return;
+  int i, j, k;
+  sy_ijk(L, 2 * t, i, j, k);
+  i += (j + k + colour) & 1;
+  T N, dN;
+  sy_op<T, CORR>(L, i, j, k, N, dN);
+  const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
+  T du = -L.relax * (N - sy_rhs(L, c)) / dN;
+  du = du > L.cap ? L.cap : (du < -L.cap ? -L.cap : du);
+  L.u[c] += du;
+}
+
+// Block partials (sum of squares, max |v|) into part[2 blockIdx.x ..].
+template <typename T>
+__device__ __forceinline__ void sy_block_norms(T v2, T vmax, double *part) {
+  __shared__ double ss[kNT / 32], sm[kNT / 32];
+  double s = (double)v2, m = (double)vmax;
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    ss[w] = s;
+    sm[w] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ts = 0.0, tm = 0.0;
+    for (int q = 0; q < kNT / 32; q++) {
+      ts += ss[q];
+      tm = fmax(tm, sm[q]);
+    }
+    part[2 * blockIdx.x] = ts;
+    part[2 * blockIdx.x + 1] = tm;
+  }
+}
+
+// Residual d = N(u) - f of the 8 children of each coarse cell, restricted:
+// coarse uR = u^H = mean of the children's u, coarse f = mean of d (the FAS
+// right-hand side is completed by k_sy_fas_rhs); optional norm partials of d.
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(kNT) k_sy_resid_restrict(SLevel<T> F, SLevel<T> Cs,
+                                                           double *part) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  T s2 = T(0), mx = T(0);
+  if (t < Cs.nc) {
+    int I, J, K;
+    sy_ijk(Cs, t, I, J, K);
+    T su = T(0), sd = T(0);
+    for (int q = 0; q < 8; q++) {
+      const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
+      const long long c = ((long long)k * F.n1 + j) * F.n0 + i;
+      T N, dN;
+      sy_op<T, CORR>(F, i, j, k, N, dN);
+      const T d = N - sy_rhs(F, c);
+      su += F.u[c];
+      sd += d;
+      s2 += d * d;
+      mx = fmax(mx, fabs(d));
+    }
+    const T uh = su * T(0.125);
+    Cs.uR[t] = uh;
+    Cs.u[t] = uh;
+    Cs.f[t] = sd * T(0.125);
+  }
+  if (part) sy_block_norms<T>(s2, mx, part);
+}
+
+// FAS right-hand side of a coarse level: f <- N^H(u^H) - f (f holding R d^h).
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(kNT) k_sy_fas_rhs(SLevel<T> Cs) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Cs.nc) return;
+  int i, j, k;
+  sy_ijk(Cs, t, i, j, k);
+  T N, dN;
+  sy_op<T, CORR>(Cs, i, j, k, N, dN);
+  Cs.f[t] = N - Cs.f[t];
+}
+
+// u^h += P (u^H - R u^h): trilinear 27/9/3/1 interpolation, periodic.
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_sy_prolong(SLevel<T> F, SLevel<T> Cs) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= F.nc) return;
+  int i, j, k;
+  sy_ijk(F, t, i, j, k);
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  const int I2 = (i & 1) ? (I + 1 == Cs.n0 ? 0 : I + 1) : (I == 0 ? Cs.n0 - 1 : I - 1);
+  const int J2 = (j & 1) ? (J + 1 == Cs.n1 ? 0 : J + 1) : (J == 0 ? Cs.n1 - 1 : J - 1);
+  const int K2 = (k & 1) ? (K + 1 == Cs.n2 ? 0 : K + 1) : (K == 0 ? Cs.n2 - 1 : K - 1);
+  auto e = [&](int a, int b, int c) {
+    const long long q = ((long long)c * Cs.n1 + b) * Cs.n0 + a;
+    return Cs.u[q] - Cs.uR[q];
+  };
+  const T v = T(27) * e(I, J, K) + T(9) * (e(I2, J, K) + e(I, J2, K) + e(I, J, K2)) +
+              T(3) * (e(I2, J2, K) + e(I2, J, K2) + e(I, J2, K2)) + e(I2, J2, K2);
+  F.u[t] += v * T(1.0 / 64.0);
+}
+
+// Coarsest level: one block relaxes the whole grid until its rms residual has
+// fallen by `rel` (or below `abs_`), at most maxit sweeps, or (stall != 0,
+// the FP32 solve at its rounding floor) four sweeps in a row have not brought
+// it below 0.9 of its best value (a single sweep may raise the rms of a
+// red-black sweep's residual without the solve having stalled).
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(kNT) k_sy_coarsest(SLevel<T> L, double rel, double abs_,
+                                                     int maxit, int stall) {
+  __shared__ double red[kNT / 32];
+  __shared__ double lim_s, best_s;
+  __shared__ int stop_s, flat_s;
+  auto rms = [&]() -> double {
+    double s = 0.0;
+    for (long long c = threadIdx.x; c < L.nc; c += blockDim.x) {
+      int i, j, k;
+      sy_ijk(L, c, i, j, k);
+      T N, dN;
+      sy_op<T, CORR>(L, i, j, k, N, dN);
+      const double d = (double)(N - sy_rhs(L, c));
+      s += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double tot = 0.0;
+    for (int q = 0; q < kNT / 32; q++) tot += red[q];
+    return sqrt(tot / (double)L.nc);
+  };
+  const double r0 = rms();
+  if (threadIdx.x == 0) {
+    lim_s = fmax(rel * r0, abs_);
+    best_s = r0;
+    flat_s = 0;
+    stop_s = 0;  // at least one sweep
+  }
+  __syncthreads();
+  for (int it = 0; it < maxit && !stop_s; it++) {
+    for (int colour = 0; colour < 2; colour++) {
+      for (long long t = threadIdx.x; 2 * t < L.nc; t += blockDim.x) {
+        int i, j, k;
+        sy_ijk(L, 2 * t, i, j, k);
+        i += (j + k + colour) & 1;
+        T N, dN;
+        sy_op<T, CORR>(L, i, j, k, N, dN);
+        const long long c = ((long long)k * L.n1 + j) * L.n0 + i;
+        T du = -L.relax * (N - sy_rhs(L, c)) / dN;
+        du = du > L.cap ? L.cap : (du < -L.cap ? -L.cap : du);
+        L.u[c] += du;
+      }
+      __syncthreads();
+    }
+    const double r = rms();
+    if (threadIdx.x == 0) {
+      if (r < 0.9 * best_s) {
+        best_s = r;
+        flat_s = 0;
+      } else {
+        flat_s++;
+      }
+      stop_s = r <= lim_s || !(r == r) || (stall && flat_s >= 4);
+    }
+    __syncthreads();
+  }
+}
+
+// 8-child average of an array (coarse dims c0 x c1 x c2).
+template <typename S, typename D>
+__global__ void __launch_bounds__(kNT) k_sy_restrict(const S *fine, D *coarse, int c0, int c1,
+                                                     int c2) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nc = (long long)c0 * c1 * c2;
+  if (t >= nc) return;
+  const int I = (int)(t % c0);
+  const long long r = t / c0;
+  const int J = (int)(r % c1), K = (int)(r / c1);
+  const int f0 = 2 * c0, f1 = 2 * c1;
+  double s = 0.0;
+  for (int q = 0; q < 8; q++) {
+    const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
+    s += (double)fine[((long long)k * f1 + j) * f0 + i];
+  }
+  coarse[t] = (D)(s * 0.125);
+}
+
+// FP64 residual of the full equation, d = L(chi), with norm partials.
+__global__ void __launch_bounds__(kNT) k_sy_defect64(SLevel<double> L, double *d, double *part) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (t < L.nc) {
+    int i, j, k;
+    sy_ijk(L, t, i, j, k);
+    double N, dN;
+    sy_op<double, false>(L, i, j, k, N, dN);
+    v = N;
+    if (d) d[t] = v;
+  }
+  sy_block_norms<double>(v * v, fabs(v), part);
+}
+
+// Set-up of an outer step: fine right-hand side -d (FP32), background
+// g = fp32(chi), correction delta = 0, density in FP32.
+__global__ void __launch_bounds__(kNT) k_sy_prep(const double *chi, const double *d, float *g,
+                                                 float *f, float *delta, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  g[t] = (float)chi[t];
+  f[t] = (float)(-d[t]);
+  delta[t] = 0.0f;
+}
+
+__global__ void __launch_bounds__(kNT) k_sy_update(double *chi, const float *delta, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) chi[t] += (double)delta[t];
+}
+
+__global__ void __launch_bounds__(kNT) k_sy_fill(double *v, double x, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) v[t] = x;
+}
+
+template <typename S, typename D>
+__global__ void __launch_bounds__(kNT) k_sy_convert(const S *in, D *out, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (D)in[t];
+}
+
+// density check: finite and, the model's density being a mass density, >= 0
+__global__ void __launch_bounds__(kNT) k_sy_check_rho(const double *rho, long long n, int *bad) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    const double r = rho[t];
+    if (!(r >= 0.0) || isinf(r)) atomicOr(bad, 1);
+  }
+}
+
+// sum and max of per-block partial pairs, one block, fixed order
+__global__ void __launch_bounds__(kNT) k_sy_reduce(const double *part, long long nb,
+                                                   double *out) {
+  __shared__ double ss[kNT], sm[kNT];
+  double s = 0.0, m = 0.0;
+  for (long long b = threadIdx.x; b < nb; b += kNT) {
+    s += part[2 * b];
+    m = fmax(m, part[2 * b + 1]);
+  }
+  ss[threadIdx.x] = s;
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ts = 0.0, tm = 0.0;
+    for (int q = 0; q < kNT; q++) {
+      ts += ss[q];
+      tm = fmax(tm, sm[q]);
+    }
+    out[0] = ts;
+    out[1] = tm;
+  }
+}
+
+long long nblk(long long n) { return (n + kNT - 1) / kNT; }
+
+bool on_device(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int sy_levels(const int n[3]) {
+  int m[3] = {n[0], n[1], n[2]};
+  int nl = 1;
+  while (m[0] % 2 == 0 && m[1] % 2 == 0 && m[2] % 2 == 0 && m[0] / 2 >= 4 && m[1] / 2 >= 4 &&
+         m[2] / 2 >= 4) {
+    for (int d = 0; d < 3; d++) m[d] /= 2;
+    nl++;
+  }
+  return nl;
+}
+
+// The hierarchy of one precision and form, and the V-cycle on it.
+template <typename T, bool CORR>
+struct SHier {
+  std::vector<SLevel<T>> lev;
+  frmg_ctx *ctx;
+  cudaStream_t st;
+  int pre, post;
+  double *part0;  // fine norm partials of the residual + restriction (or null)
+  double crs_abs;  // absolute floor of the coarsest solve (FP64: 0.1 tol)
+
+  void smooth(int l, int sweeps) {
+    const SLevel<T> &L = lev[l];
+    const long long half = (L.nc + 1) / 2;
+    for (int it = 0; it < sweeps; it++)
+      for (int colour = 0; colour < 2; colour++) {
+        k_sy_smooth<T, CORR><<<(unsigned)nblk(half), kNT, 0, st>>>(L, colour);
+        SLAUNCH(ctx);
+      }
+  }
+  void vcycle(int l) {
+    const int nl = (int)lev.size();
+    if (l == nl - 1) {
+      k_sy_coarsest<T, CORR><<<1, kNT, 0, st>>>(lev[l], 1e-3, crs_abs, 500, CORR ? 1 : 0);
+      SLAUNCH(ctx);
+      return;
+    }
+    smooth(l, pre);
+    k_sy_resid_restrict<T, CORR><<<(unsigned)nblk(lev[l + 1].nc), kNT, 0, st>>>(
+        lev[l], lev[l + 1], l == 0 ? part0 : nullptr);
+    SLAUNCH(ctx);
+    k_sy_fas_rhs<T, CORR><<<(unsigned)nblk(lev[l + 1].nc), kNT, 0, st>>>(lev[l + 1]);
+    SLAUNCH(ctx);
+    vcycle(l + 1);
+    k_sy_prolong<T><<<(unsigned)nblk(lev[l].nc), kNT, 0, st>>>(lev[l], lev[l + 1]);
+    SLAUNCH(ctx);
+    smooth(l, post);
+  }
+};
+
+}  // namespace
+
+extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const int dims[3],
+                                  double box, double a, double a_ssb, double lambda0, double tol,
+                                  double *chi_inout, const fr_opts *opts, fr_stats *stats,
+                                  void *stream) {
+  const auto t_start = std::chrono::steady_clock::now();
+  try {
+    if (!ctx || !density || !dims || !chi_inout) throw SError{FR_EINVAL, "NULL argument"};
+    for (int d = 0; d < 3; d++)
+      if (dims[d] < 2 || (dims[d] & 1)) throw SError{FR_EINVAL, "dims must be even and >= 2"};
+    if (!(box > 0) || !(a > 0) || !(a_ssb > 0) || !(lambda0 > 0) || !(tol >= 0))
+      throw SError{FR_EINVAL, "box, a, a_ssb and lambda0 must be > 0, tol >= 0"};
+    fr_opts o;
+    fr_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.pre < 0 || o.post < 0 || o.pre + o.post < 1 || !(o.newton_step_cap > 0) ||
+        !(o.relax > 0 && o.relax < 2) || o.max_vcycles < 1 || o.max_outer < 1 ||
+        (o.prec != FR_FP64 && o.prec != FR_MIXED))
+      throw SError{FR_EINVAL, "invalid options"};
+    SCK(cudaSetDevice(frmg_device(ctx)));
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nc = (long long)dims[0] * dims[1] * dims[2];
+    if (nblk(nc) >= (1ll << 31)) throw SError{FR_EINVAL, "grid too large"};
+    SArena A(ctx);
+    // host arrays are staged through device buffers
+    const bool rho_dev = on_device(density), chi_dev = on_device(chi_inout);
+    const double *rho = density;
+    if (!rho_dev) {
+      double *r = A.get<double>(nc);
+      SCK(cudaMemcpyAsync(r, density, nc * sizeof(double), cudaMemcpyHostToDevice, st));
+      rho = r;
+    }
+    double *chi = chi_inout;
+    if (!chi_dev) chi = A.get<double>(nc);
+    const double s = std::pow(a_ssb / a, 3.0);
+    if (o.initial_guess) {
+      if (!chi_dev)
+        SCK(cudaMemcpyAsync(chi, chi_inout, nc * sizeof(double), cudaMemcpyHostToDevice, st));
+    } else {
+      // the homogeneous solution on the positive branch (1 before symmetry
+      // breaking, from where the field relaxes to its symmetric value 0)
+      const double chib = s < 1.0 ? std::sqrt(1.0 - s) : 1.0;
+      k_sy_fill<<<(unsigned)nblk(nc), kNT, 0, st>>>(chi, chib, nc);
+      SLAUNCH(ctx);
+    }
+    {
+      int *bad = A.get<int>(1);
+      SCK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+      k_sy_check_rho<<<(unsigned)nblk(nc), kNT, 0, st>>>(rho, nc, bad);
+      SLAUNCH(ctx);
+      int hb = 0;
+      SCK(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SCK(cudaStreamSynchronize(st));
+      if (hb) throw SError{FR_EINVAL, "density must be finite and >= 0"};
+    }
+    // levels: sizes and coefficients (A quarters per level)
+    const int nl = sy_levels(dims);
+    std::vector<std::array<int, 3>> ns(nl);
+    std::vector<double> Al(nl);
+    for (int l = 0; l < nl; l++) {
+      for (int d = 0; d < 3; d++) ns[l][d] = dims[d] >> l;
+      const double hl = box * std::ldexp(1.0, l) / dims[0];  // cell size, Mpc/h
+      Al[l] = 2.0 * lambda0 * lambda0 / (a * a * hl * hl);
+    }
+    auto ncell = [&](int l) { return (long long)ns[l][0] * ns[l][1] * ns[l][2]; };
+    double *part = A.get<double>(2 * nblk(nc));
+    double *red = A.get<double>(2);
+    double *pin = frmg_pinned(ctx, 2);
+    if (!pin) throw SError{FR_ENOMEM, "pinned host allocation failed"};
+    auto norms = [&](double *pp, long long nb, long long n, double &rms, double &mx) {
+      k_sy_reduce<<<1, kNT, 0, st>>>(pp, nb, red);
+      SLAUNCH(ctx);
+      SCK(cudaMemcpyAsync(pin, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SCK(cudaStreamSynchronize(st));
+      rms = std::sqrt(pin[0] / (double)n);
+      mx = pin[1];
+    };
+    fr_stats sv;
+    memset(&sv, 0, sizeof(sv));
+    sv.tau_rms = std::nan("");
+    auto push = [&](double v) {
+      if (sv.nhist < FR_HIST) sv.hist[sv.nhist++] = v;
+    };
+    auto bad_v = [](double v) { return !(v == v) || std::isinf(v); };
+    int status = FR_ENOCONV;
+    SLevel<double> fine64;
+    memset(&fine64, 0, sizeof(fine64));
+    fine64.u = chi;
+    fine64.rho = rho;
+    fine64.n0 = dims[0];
+    fine64.n1 = dims[1];
+    fine64.n2 = dims[2];
+    fine64.nc = nc;
+    fine64.A = Al[0];
+    fine64.s = s;
+    fine64.cap = o.newton_step_cap;
+    fine64.relax = o.relax;
+    double *d64 = nullptr;
+    auto defect = [&](double &rms, double &mx) {
+      k_sy_defect64<<<(unsigned)nblk(nc), kNT, 0, st>>>(fine64, d64, part);
+      SLAUNCH(ctx);
+      norms(part, nblk(nc), nc, rms, mx);
+    };
+
+    if (o.prec == FR_FP64) {
+      SHier<double, false> H;
+      H.ctx = ctx;
+      H.st = st;
+      H.pre = o.pre;
+      H.post = o.post;
+      H.part0 = nullptr;
+      H.crs_abs = 0.1 * tol;
+      H.lev.push_back(fine64);
+      for (int l = 1; l < nl; l++) {
+        SLevel<double> L = fine64;
+        L.n0 = ns[l][0];
+        L.n1 = ns[l][1];
+        L.n2 = ns[l][2];
+        L.nc = ncell(l);
+        L.A = Al[l];
+        L.u = A.get<double>(L.nc);
+        L.uR = A.get<double>(L.nc);
+        L.f = A.get<double>(L.nc);
+        double *r = A.get<double>(L.nc);
+        k_sy_restrict<double, double><<<(unsigned)nblk(L.nc), kNT, 0, st>>>(
+            H.lev[l - 1].rho, r, L.n0, L.n1, L.n2);
+        SLAUNCH(ctx);
+        L.rho = r;
+        H.lev.push_back(L);
+      }
+      double rms, mx;
+      defect(rms, mx);
+      sv.res0_rms = rms;
+      push(rms);
+      if (bad_v(rms)) throw SError{FR_EDIVERGED, "non-finite residual"};
+      double prev = rms;
+      int grow = 0;
+      while (rms > tol && sv.vcycles < o.max_vcycles) {
+        H.vcycle(0);
+        sv.vcycles++;
+        defect(rms, mx);
+        push(rms);
+        if (bad_v(rms)) throw SError{FR_EDIVERGED, "non-finite residual"};
+        grow = rms > prev ? grow + 1 : 0;
+        if (grow >= 5) throw SError{FR_EDIVERGED, "residual grew for 5 cycles"};
+        prev = rms;
+      }
+      sv.res_rms = rms;
+      sv.res_max = mx;
+      status = rms <= tol ? FR_OK : FR_ENOCONV;
+    } else {
+      d64 = A.get<double>(nc);
+      SHier<float, true> H;
+      H.ctx = ctx;
+      H.st = st;
+      H.pre = o.pre;
+      H.post = o.post;
+      H.crs_abs = 0.0;
+      std::vector<float *> gl(nl);
+      for (int l = 0; l < nl; l++) {
+        SLevel<float> L;
+        memset(&L, 0, sizeof(L));
+        L.n0 = ns[l][0];
+        L.n1 = ns[l][1];
+        L.n2 = ns[l][2];
+        L.nc = ncell(l);
+        L.A = (float)Al[l];
+        L.s = (float)s;
+        L.cap = (float)o.newton_step_cap;
+        L.relax = (float)o.relax;
+        L.u = A.get<float>(L.nc);
+        L.f = A.get<float>(L.nc);
+        if (l > 0) L.uR = A.get<float>(L.nc);
+        float *r = A.get<float>(L.nc);
+        if (l == 0) {
+          k_sy_convert<double, float><<<(unsigned)nblk(L.nc), kNT, 0, st>>>(rho, r, L.nc);
+        } else {
+          k_sy_restrict<float, float><<<(unsigned)nblk(L.nc), kNT, 0, st>>>(
+              H.lev[l - 1].rho, r, L.n0, L.n1, L.n2);
+        }
+        SLAUNCH(ctx);
+        L.rho = r;
+        gl[l] = A.get<float>(L.nc);
+        L.g = gl[l];
+        H.lev.push_back(L);
+      }
+      const long long nb1 = nl > 1 ? nblk(ncell(1)) : 0;
+      double *part_in = nl > 1 ? A.get<double>(2 * nb1) : nullptr;
+      H.part0 = part_in;
+      double rms, mx;
+      defect(rms, mx);
+      sv.res0_rms = rms;
+      push(rms);
+      if (bad_v(rms)) throw SError{FR_EDIVERGED, "non-finite residual"};
+      double prev = rms;
+      int grow = 0;
+      while (rms > tol && sv.outer < o.max_outer && sv.vcycles < o.max_vcycles * o.max_outer) {
+        sv.outer++;
+        // correction problem of this outer step: N(delta) = -d on g = fp32(chi)
+        k_sy_prep<<<(unsigned)nblk(nc), kNT, 0, st>>>(chi, d64, gl[0], H.lev[0].f, H.lev[0].u,
+                                                      nc);
+        SLAUNCH(ctx);
+        for (int l = 1; l < nl; l++) {
+          k_sy_restrict<float, float><<<(unsigned)nblk(ncell(l)), kNT, 0, st>>>(
+              gl[l - 1], gl[l], ns[l][0], ns[l][1], ns[l][2]);
+          SLAUNCH(ctx);
+        }
+        // inner V-cycles until the fine correction residual (after
+        // pre-smoothing, times the last contraction) is predicted below
+        // max(0.1 tol, 1e-6 rms(d)), or the contraction stalls near the FP32
+        // floor, or max_vcycles cycles
+        const double target = std::max(0.1 * tol, 1e-6 * rms);
+        double rp = HUGE_VAL, q = 0.3;
+        for (int c = 0; c < o.max_vcycles; c++) {
+          H.vcycle(0);
+          sv.vcycles++;
+          if (nl == 1) break;
+          double r, m;
+          norms(part_in, nb1, nc, r, m);
+          if (bad_v(r)) throw SError{FR_EDIVERGED, "non-finite inner residual"};
+          if (c > 0) q = r / rp;
+          rp = r;
+          if (r * q <= target || q > 0.8) break;
+        }
+        k_sy_update<<<(unsigned)nblk(nc), kNT, 0, st>>>(chi, H.lev[0].u, nc);
+        SLAUNCH(ctx);
+        defect(rms, mx);
+        push(-rms);
+        if (bad_v(rms)) throw SError{FR_EDIVERGED, "non-finite residual"};
+        grow = rms > prev ? grow + 1 : 0;
+        if (grow >= 3) throw SError{FR_EDIVERGED, "defect grew for 3 outer steps"};
+        prev = rms;
+      }
+      sv.res_rms = rms;
+      sv.res_max = mx;
+      status = rms <= tol ? FR_OK : FR_ENOCONV;
+    }
+    if (!chi_dev)
+      SCK(cudaMemcpyAsync(chi_inout, chi, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    sv.seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = sv;
+    if (status != FR_OK) frmg_set_error("tol not reached");
+    return status;
+  } catch (SError &e) {
+    frmg_set_error(e.msg);
+    return e.status;
+  } catch (std::exception &e) {
+    frmg_set_error(e.what());
+    return FR_ENOMEM;
+  }
+}

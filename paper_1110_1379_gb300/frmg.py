@@ -60,7 +60,7 @@ EXPORTS = ["fr_opts_default", "fr_status_string", "fr_last_error", "fr_ctx_creat
            "fr_cic_assign", "fr_smooth", "fr_residual", "fr_restrict", "fr_prolong_correct",
            "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32", "fr_residual_df",
            "fr_residual_norm_noalloc", "fr_autotune", "fr_poisson_solve", "fr_poisson_source",
-           "fr_tsc_assign", "fr_particle_forces", "fr_solve_masked"]
+           "fr_tsc_assign", "fr_particle_forces", "fr_solve_masked", "fr_symmetron_solve"]
 
 
 def lib_path():
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = False):
             "fr_particle_forces": (I, [P, P, P, P, L, I, P, P]),
             "fr_solve_masked": (I, [P, P, P, P, D, D, D, D, D, D, P, P, P, P]),
             "fr_profile_entry": (I, [P, I, P, I, P, P]),
+            "fr_symmetron_solve": (I, [P, P, P, D, D, D, D, D, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -270,6 +271,21 @@ class Context:
                                       ctypes.byref(s), _stream(stream))
         if st in raise_on:
             self._raise(st, "fr_solve_masked")
+        return st, s
+
+    def symmetron(self, density, chi, *, box, a, a_ssb, lambda0, tol=1e-8, stream=None,
+                  raise_on=(FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_ETIMEOUT), **opts):
+        """Symmetron field chi = phi/phi_0 (in: initial guess unless
+        initial_guess=0; out: solution).  Returns (status, stats)."""
+        _check_f64(density, "density")
+        _check_f64(chi, "chi")
+        o = self.opts(tol=tol, **opts)
+        s = fr_stats()
+        st = self.lib.fr_symmetron_solve(self._h, _ptr(density), _dims(density.shape), box, a,
+                                         a_ssb, lambda0, tol, _ptr(chi), ctypes.byref(o),
+                                         ctypes.byref(s), _stream(stream))
+        if st in raise_on:
+            self._raise(st, "fr_symmetron_solve")
         return st, s
 
     def poisson(self, density, u, phi, *, box, a, omega_m, fr0, tol=1e-8, phib=None, h=None,
