@@ -587,10 +587,11 @@ def run_secondary(args):
         # algorithmic bytes: per fine V(pre,post) cycle, (pre + post) sweeps of
         # 20 B (delta, g, rho, f read; delta written), residual + restriction
         # 16 B + 1.5 B of coarse writes, prolongation 8 B + 1 B, x 8/7 for the
-        # coarse levels; per outer step the FP64 defect (chi, rho: 16 B), the
-        # set-up (chi, d in; g, f, delta out: 28 B) and the update (20 B)
+        # coarse levels; per defect the double-float pass (chi, rho pairs in:
+        # 16 B; g, f, delta out: 12 B), per outer step the update (chi pair and
+        # delta in, chi pair out: 20 B); once the pair splits (32 B) and the join (16 B)
         alg = n ** 3 * (s.vcycles * (20.0 * (sopts["pre"] + sopts["post"]) + 26.5) * 8 / 7 +
-                        (s.outer + 1) * 16.0 + s.outer * 48.0)
+                        (s.outer + 1) * 28.0 + s.outer * 20.0 + 48.0)
         # CPU oracle (numpy, FP64) on a bounded 64^3 sample of the same recipe
         ns = 64
         rs = synth.lognormal_density((ns,) * 3, SEED, sigma=SIGMA)

@@ -436,8 +436,13 @@ int fr_solve_masked(frmg_ctx *ctx, const double *density, const double *mask, co
  * guess in (opts->initial_guess = 0: start from the homogeneous positive
  * solution sqrt(1 - s), or 1 before symmetry breaking), solution out.  Host
  * or device pointers.  opts: pre, post, newton_step_cap, relax, max_vcycles,
- * max_outer, initial_guess, prec: FR_FP64 = every step in FP64; FR_MIXED =
- * FP64 residual, update and convergence test around FP32 FAS V-cycles of
+ * max_outer, initial_guess, tiling (FR_MIXED: the FP32 sweeps of a level run
+ * as one register-column kernel per sweep on 64 x 8 tiles where the level
+ * fills the GPU with tiles (0), wherever it is at least 16 cells a side (1),
+ * or never (-1: one launch per colour)), prec: FR_FP64 = every step in FP64; FR_MIXED =
+ * the residual, the update of chi and the convergence test in double-float
+ * (chi and rho as pairs of FP32 values, ~48-bit significands, on the FP32
+ * pipes) around FP32 FAS V-cycles of
  * the correction equation L(g + delta) - L(g) = -L(chi), g = fp32(chi), run
  * until their fine residual is predicted below max(0.1 tol, 1e-6 rms L(chi))
  * (at most max_vcycles per outer step).  stats: vcycles, outer, res0_rms,

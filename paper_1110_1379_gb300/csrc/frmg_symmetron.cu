@@ -35,9 +35,11 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "frmg.h"
+#include "frmg_dfmath.cuh"
 #include "frmg_internal.h"
 
 namespace {
@@ -89,7 +91,9 @@ struct SArena {
 // form (FP32 inner solve): u = delta, g = background fp32(chi) restricted.
 template <typename T>
 struct SLevel {
-  T *u;            // unknown
+  T *u;            // unknown (the current buffer)
+  T *u2;           // second buffer of the register-column smoother (null: not used)
+  int zc;          // its z-chunk
   T *uR;           // restricted fine unknown (coarse levels)
   T *f;            // right-hand side (FAS); null = 0
   const T *rho;    // density (mean 1), restricted on coarse levels
@@ -97,10 +101,19 @@ struct SLevel {
   int n0, n1, n2;
   long long nc;
   T A, s, cap, relax;
+  frmg::FastDiv fd0, fd1;  // division by n0 and n1 (grids below 2^31 cells)
 };
 
+// (i, j, k) of cell c: 32-bit multiply-shift division below 2^31 cells
 template <typename T>
 __device__ __forceinline__ void sy_ijk(const SLevel<T> &L, long long c, int &i, int &j, int &k) {
+  if (L.nc < (1ll << 31)) {
+    const unsigned cu = (unsigned)c, q = frmg::fdiv(cu, L.fd0), q2 = frmg::fdiv(q, L.fd1);
+    i = (int)(cu - q * (unsigned)L.n0);
+    j = (int)(q - q2 * (unsigned)L.n1);
+    k = (int)q2;
+    return;
+  }
   i = (int)(c % L.n0);
   const long long r = c / L.n0;
   j = (int)(r % L.n1);
@@ -310,6 +323,184 @@ __global__ void __launch_bounds__(kNT) k_sy_coarsest(SLevel<T> L, double rel, do
   }
 }
 
+__device__ __forceinline__ int wrapmod_sy(int v, int n) {
+  int r = v % n;
+  return r < 0 ? r + n : r;
+}
+
+// One red-black sweep of the FP32 correction form with register-resident
+// z-columns (periodic grids of at least 16 cells a side): the layout and
+// march of the f(R) solver's register-column smoother on 64 x 8 tiles with a
+// halo of two cells.  Every x-pair of the tile plus halo has one owner
+// thread that keeps, for the last four planes, the pair's red and black cell
+// (delta and the cell's coefficients c1 = s rho - 1 + 3 g^2, c2 = 3 g and
+// right-hand side f) in registers; only delta crosses between threads,
+// through double-buffered half-planes in shared memory.  At the step that
+// loads plane p: the black cells of p are published (old values), the red
+// cells of p-1 on the tile grown by one cell are updated from black
+// neighbours and published, and the black cells of p-2 on the tile are
+// updated from the new red cells and written out (delta only; the
+// coefficients are recomputed from rho and g at every load).  Reads buffer
+// uin, writes uout (halos come from the unmodified input), so the sweep is
+// the same as two launches of k_sy_smooth up to FP32 rounding order.
+constexpr int kSyTX = 64, kSyTY = 8, kSyPX = kSyTX / 2 + 2, kSyLY = kSyTY + 4;
+constexpr int kSyPP = kSyPX * kSyLY, kSyNHR = 4 * (kSyTX / 2), kSyNHALO = kSyNHR + 2 * kSyLY;
+static_assert(kSyNHALO <= kNT, "halo pairs per thread");
+
+__global__ void __launch_bounds__(kNT, 3)
+    k_sy_smooth_rc(SLevel<float> L, const float *__restrict__ uin, float *__restrict__ uout,
+                   int zc) {
+  constexpr int NSL = 2;  // one interior pair, one halo pair
+  __shared__ float sbk[2][kSyPP], srd[2][kSyPP];
+  const int n0 = L.n0, n1 = L.n1, n2 = L.n2;
+  const int ntx = (n0 + kSyTX - 1) / kSyTX, nty = (n1 + kSyTY - 1) / kSyTY;
+  int b = blockIdx.x;
+  const int X0 = (b % ntx) * kSyTX;
+  b /= ntx;
+  const int Y0 = (b % nty) * kSyTY;
+  b /= nty;
+  const int Z0 = b * zc;
+  const int Z1 = min(Z0 + zc, n2);
+  const int P0 = Z0 - 2, nstep = Z1 - Z0 + 4;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long plane = (long long)n0 * n1;
+  const float A = L.A, s = L.s, cap = L.cap, relax = L.relax;
+  const float *__restrict__ rho = L.rho;
+  const float *__restrict__ gin = L.g;
+  const float *__restrict__ fin = L.f;
+  int q[NSL], roff[NSL];
+  unsigned fl[NSL], ro[NSL];  // fl: bit 0 load, 1 write, 2 / 3 red update of even / odd cell
+#pragma unroll
+  for (int sl = 0; sl < NSL; sl++) {
+    int px = -1, ly = -1;
+    const bool interior = sl == 0;
+    if (interior) {
+      px = 1 + lane;
+      ly = 2 + w;
+    } else if ((int)threadIdx.x < kSyNHALO) {
+      const int t = threadIdx.x;
+      if (t < kSyNHR) {
+        const int r = t >> 5;
+        px = 1 + lane;
+        ly = r < 2 ? r : kSyTY + r;
+      } else {
+        const int k = t - kSyNHR;
+        px = k < kSyLY ? 0 : kSyPX - 1;
+        ly = k < kSyLY ? k : k - kSyLY;
+      }
+    }
+    q[sl] = 0;
+    roff[sl] = 0;
+    fl[sl] = 0;
+    ro[sl] = 0;
+    if (px < 0) continue;
+    const int gx = X0 - 2 + 2 * px, gy = Y0 - 2 + ly;
+    q[sl] = ly * kSyPX + px;
+    ro[sl] = (unsigned)((gy + P0) & 1);
+    roff[sl] = wrapmod_sy(gy, n1) * n0 + wrapmod_sy(gx, n0);
+    unsigned f = 1u;
+    const bool yin = gy >= Y0 - 1 && gy <= Y0 + kSyTY;
+    if (yin && gx >= X0 - 1 && gx <= X0 + kSyTX) f |= 4u;
+    if (yin && gx + 1 >= X0 - 1 && gx + 1 <= X0 + kSyTX) f |= 8u;
+    if (interior && gx < n0 && gy < n1) f |= 2u;
+    fl[sl] = f;
+  }
+  // per slot and ring plane: red and black cell (delta, c1, c2, f)
+  float4 R[NSL][4], B[NSL][4];
+  float2 pu[NSL], pr[NSL], pg[NSL], pf[NSL];
+#pragma unroll
+  for (int sl = 0; sl < NSL; sl++) {
+    pu[sl] = pr[sl] = pg[sl] = pf[sl] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < 4; r++) R[sl][r] = B[sl][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  int pw = wrapmod_sy(P0, n2);
+  auto fetch = [&]() {
+    const long long zo = (long long)pw * plane;
+#pragma unroll
+    for (int sl = 0; sl < NSL; sl++) {
+      if (!(fl[sl] & 1u)) continue;
+      const long long o = zo + roff[sl];
+      pu[sl] = *reinterpret_cast<const float2 *>(uin + o);
+      pr[sl] = *reinterpret_cast<const float2 *>(rho + o);
+      pg[sl] = *reinterpret_cast<const float2 *>(gin + o);
+      pf[sl] = fin ? *reinterpret_cast<const float2 *>(fin + o) : make_float2(0.f, 0.f);
+    }
+    pw = pw + 1 == n2 ? 0 : pw + 1;
+  };
+  fetch();
+  auto cell = [&](float d, float r, float g, float f) {
+    return make_float4(d, s * r - 1.0f + 3.0f * g * g, 3.0f * g, f);
+  };
+  // Newton update: own (delta, c1, c2, f), six neighbour deltas
+  auto newton = [&](float4 c, float lf, float rt, float ym, float yp, float zm, float zp) {
+    const float d = c.x;
+    const float lap = (lf - d) + (rt - d) + (ym - d) + (yp - d) + (zm - d) + (zp - d);
+    const float N = A * lap - d * (c.y + d * (c.z + d));
+    const float dN = -6.0f * A - (c.y + d * (2.0f * c.z + 3.0f * d));
+    float du = -relax * (N - c.w) / dN;
+    du = fminf(fmaxf(du, -cap), cap);
+    return d + du;
+  };
+  auto step = [&](auto Kc, int k) {
+    constexpr int K = decltype(Kc)::value;
+    constexpr int K1 = (K + 3) & 3, K2 = (K + 2) & 3, K3 = (K + 1) & 3;
+    constexpr unsigned PK = K & 1, PK1 = K1 & 1, PK2 = K2 & 1;
+    const int p = P0 + k;
+#pragma unroll
+    for (int sl = 0; sl < NSL; sl++) {
+      if (!(fl[sl] & 1u)) continue;
+      const bool odd = (ro[sl] ^ PK) != 0;  // red cell is the odd one
+      const float4 e = cell(pu[sl].x, pr[sl].x, pg[sl].x, pf[sl].x);
+      const float4 o = cell(pu[sl].y, pr[sl].y, pg[sl].y, pf[sl].y);
+      R[sl][K] = odd ? o : e;
+      B[sl][K] = odd ? e : o;
+      sbk[PK][q[sl]] = B[sl][K].x;
+    }
+    if (k + 1 < nstep) fetch();
+    {
+      const int m = p - 1;
+      if (m >= Z0 - 1 && m <= Z1) {
+#pragma unroll
+        for (int sl = 0; sl < NSL; sl++) {
+          const bool odd = (ro[sl] ^ PK1) != 0;
+          if (!((sl == 0) || (fl[sl] & (odd ? 8u : 4u)))) continue;
+          const float *bk = &sbk[PK1][q[sl]];
+          const float nx = bk[odd ? 1 : -1];
+          const float in = B[sl][K1].x;
+          const float dn = newton(R[sl][K1], odd ? in : nx, odd ? nx : in, bk[-kSyPX], bk[kSyPX],
+                                  B[sl][K2].x, B[sl][K].x);
+          R[sl][K1].x = dn;
+          srd[PK1][q[sl]] = dn;
+        }
+      }
+    }
+    {
+      const int m = p - 2;
+      if (m >= Z0 && m < Z1) {
+        const bool odd = (ro[0] ^ PK2) == 0;  // black cell is the odd one
+        const float *rd = &srd[PK2][q[0]];
+        const float nx = rd[odd ? 1 : -1];
+        const float in = R[0][K2].x;
+        const float dn = newton(B[0][K2], odd ? in : nx, odd ? nx : in, rd[-kSyPX], rd[kSyPX],
+                                R[0][K3].x, R[0][K1].x);
+        B[0][K2].x = dn;
+        if (fl[0] & 2u) {
+          const float de = odd ? R[0][K2].x : dn, dd = odd ? dn : R[0][K2].x;
+          *reinterpret_cast<float2 *>(uout + (long long)m * plane + roff[0]) = make_float2(de, dd);
+        }
+      }
+    }
+    __syncthreads();
+  };
+  for (int k = 0; k < nstep; k += 4) {
+    step(std::integral_constant<int, 0>{}, k);
+    if (k + 1 < nstep) step(std::integral_constant<int, 1>{}, k + 1);
+    if (k + 2 < nstep) step(std::integral_constant<int, 2>{}, k + 2);
+    if (k + 3 < nstep) step(std::integral_constant<int, 3>{}, k + 3);
+  }
+}
+
 // 8-child average of an array (coarse dims c0 x c1 x c2).
 template <typename S, typename D>
 __global__ void __launch_bounds__(kNT) k_sy_restrict(const S *fine, D *coarse, int c0, int c1,
@@ -344,22 +535,6 @@ __global__ void __launch_bounds__(kNT) k_sy_defect64(SLevel<double> L, double *d
   sy_block_norms<double>(v * v, fabs(v), part);
 }
 
-// Set-up of an outer step: fine right-hand side -d (FP32), background
-// g = fp32(chi), correction delta = 0, density in FP32.
-__global__ void __launch_bounds__(kNT) k_sy_prep(const double *chi, const double *d, float *g,
-                                                 float *f, float *delta, long long n) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  g[t] = (float)chi[t];
-  f[t] = (float)(-d[t]);
-  delta[t] = 0.0f;
-}
-
-__global__ void __launch_bounds__(kNT) k_sy_update(double *chi, const float *delta, long long n) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) chi[t] += (double)delta[t];
-}
-
 __global__ void __launch_bounds__(kNT) k_sy_fill(double *v, double x, long long n) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) v[t] = x;
@@ -369,6 +544,92 @@ template <typename S, typename D>
 __global__ void __launch_bounds__(kNT) k_sy_convert(const S *in, D *out, long long n) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) out[t] = (D)in[t];
+}
+
+// ---- double-float outer loop of the mixed solve (FP64 accuracy on the FP32
+// pipes, see frmg_dfmath.cuh): chi and rho are held as (hi, lo) pairs.
+__global__ void __launch_bounds__(kNT) k_sy_split(const double *v, float2 *p, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double x = v[t];
+  const float h = (float)x;
+  p[t] = make_float2(h, (float)(x - (double)h));
+}
+
+__global__ void __launch_bounds__(kNT) k_sy_join(const float2 *p, double *v, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) v[t] = (double)p[t].x + (double)p[t].y;
+}
+
+// Defect d = L(chi) in double-float from the pairs of chi and rho, and the
+// set-up of the outer step's FP32 correction problem in the same pass:
+// background g = hi(chi), right-hand side f = -hi(d), delta = 0; norm
+// partials of d.  Ah + Al = A and sh + sl = s as pairs (host-split).
+__global__ void __launch_bounds__(kNT) k_sy_defect_df(SLevel<float> L, const float2 *chi,
+                                                      const float2 *rho, float Ah, float Al,
+                                                      float sh, float sl, float *g, float *f,
+                                                      float *delta, double *part) {
+  using frmg::df;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (t < L.nc) {
+    int i, j, k;
+    sy_ijk(L, t, i, j, k);
+    const long long sx = 1, sy = L.n0, sz = (long long)L.n0 * L.n1;
+    const long long xm = i > 0 ? t - sx : t + (L.n0 - 1) * sx;
+    const long long xp = i < L.n0 - 1 ? t + sx : t - (L.n0 - 1) * sx;
+    const long long ym = j > 0 ? t - sy : t + (L.n1 - 1) * sy;
+    const long long yp = j < L.n1 - 1 ? t + sy : t - (L.n1 - 1) * sy;
+    const long long zm = k > 0 ? t - sz : t + (L.n2 - 1) * sz;
+    const long long zp = k < L.n2 - 1 ? t + sz : t - (L.n2 - 1) * sz;
+    const float2 c2 = chi[t];
+    const df ci = {c2.x, c2.y};
+    auto diff = [&](long long q) {
+      const float2 n = chi[q];
+      return frmg::df_sub({n.x, n.y}, ci);
+    };
+    // sum of the six face differences, in the face order of the other kernels
+    df lap = diff(xm);
+    lap = frmg::df_add(lap, diff(xp));
+    lap = frmg::df_add(lap, diff(ym));
+    lap = frmg::df_add(lap, diff(yp));
+    lap = frmg::df_add(lap, diff(zm));
+    lap = frmg::df_add(lap, diff(zp));
+    const float2 r2 = rho[t];
+    const df m = frmg::df_add_f(frmg::df_mul({r2.x, r2.y}, {sh, sl}), -1.0f);  // s rho - 1
+    const df loc = frmg::df_mul(ci, frmg::df_add(m, frmg::df_mul(ci, ci)));  // chi (m + chi^2)
+    const df d = frmg::df_sub(frmg::df_mul(lap, {Ah, Al}), loc);
+    v = (double)d.h + (double)d.l;
+    g[t] = c2.x;
+    f[t] = -d.h;
+    delta[t] = 0.0f;
+  }
+  sy_block_norms<double>(v * v, fabs(v), part);
+}
+
+// chi += delta in double-float
+__global__ void __launch_bounds__(kNT) k_sy_update_df(float2 *chi, const float *delta,
+                                                      long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float2 c = chi[t];
+  const frmg::df r = frmg::df_add_f({c.x, c.y}, delta[t]);
+  chi[t] = make_float2(r.h, r.l);
+}
+
+// First stage of a long partial-pair sum: block b reduces pairs
+// [b 4096, (b + 1) 4096) in a fixed order.
+constexpr int kSyRedCH = 4096;
+__global__ void __launch_bounds__(kNT) k_sy_reduce_chunks(const double *in, long long n,
+                                                          double *out) {
+  const long long b0 = (long long)blockIdx.x * kSyRedCH;
+  const long long b1 = b0 + kSyRedCH < n ? b0 + kSyRedCH : n;
+  double s = 0.0, m = 0.0;
+  for (long long i = b0 + threadIdx.x; i < b1; i += kNT) {
+    s += in[2 * i];
+    m = fmax(m, in[2 * i + 1]);
+  }
+  sy_block_norms<double>(s, m, out);
 }
 
 // density check: finite and, the model's density being a mass density, >= 0
@@ -405,6 +666,16 @@ __global__ void __launch_bounds__(kNT) k_sy_reduce(const double *part, long long
 
 long long nblk(long long n) { return (n + kNT - 1) / kNT; }
 
+int sm_count_sy() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return std::max(n, 1);
+}
+
 bool on_device(const void *p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -436,7 +707,19 @@ struct SHier {
   double crs_abs;  // absolute floor of the coarsest solve (FP64: 0.1 tol)
 
   void smooth(int l, int sweeps) {
-    const SLevel<T> &L = lev[l];
+    SLevel<T> &L = lev[l];
+    if constexpr (CORR && sizeof(T) == 4) {
+      if (L.u2) {
+        const int ntx = (L.n0 + kSyTX - 1) / kSyTX, nty = (L.n1 + kSyTY - 1) / kSyTY;
+        const unsigned nb = (unsigned)(ntx * nty * ((L.n2 + L.zc - 1) / L.zc));
+        for (int it = 0; it < sweeps; it++) {
+          k_sy_smooth_rc<<<nb, kNT, 0, st>>>(L, L.u, L.u2, L.zc);
+          SLAUNCH(ctx);
+          std::swap(L.u, L.u2);
+        }
+        return;
+      }
+    }
     const long long half = (L.nc + 1) / 2;
     for (int it = 0; it < sweeps; it++)
       for (int colour = 0; colour < 2; colour++) {
@@ -532,9 +815,20 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
     auto ncell = [&](int l) { return (long long)ns[l][0] * ns[l][1] * ns[l][2]; };
     double *part = A.get<double>(2 * nblk(nc));
     double *red = A.get<double>(2);
+    const long long nch_max = (nblk(nc) + kSyRedCH - 1) / kSyRedCH;
+    double *red_tmp = A.get<double>(2 * nch_max);
     double *pin = frmg_pinned(ctx, 2);
     if (!pin) throw SError{FR_ENOMEM, "pinned host allocation failed"};
+    // sum of squares and max over nb per-block partials (two fixed-order
+    // stages for long lists), rms over n cells
     auto norms = [&](double *pp, long long nb, long long n, double &rms, double &mx) {
+      if (nb > 2 * kSyRedCH) {
+        const long long nch = (nb + kSyRedCH - 1) / kSyRedCH;
+        k_sy_reduce_chunks<<<(unsigned)nch, kNT, 0, st>>>(pp, nb, red_tmp);
+        SLAUNCH(ctx);
+        pp = red_tmp;
+        nb = nch;
+      }
       k_sy_reduce<<<1, kNT, 0, st>>>(pp, nb, red);
       SLAUNCH(ctx);
       SCK(cudaMemcpyAsync(pin, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -562,6 +856,8 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
     fine64.s = s;
     fine64.cap = o.newton_step_cap;
     fine64.relax = o.relax;
+    fine64.fd0 = frmg::make_fastdiv((unsigned)dims[0]);
+    fine64.fd1 = frmg::make_fastdiv((unsigned)dims[1]);
     double *d64 = nullptr;
     auto defect = [&](double &rms, double &mx) {
       k_sy_defect64<<<(unsigned)nblk(nc), kNT, 0, st>>>(fine64, d64, part);
@@ -583,6 +879,8 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
         L.n0 = ns[l][0];
         L.n1 = ns[l][1];
         L.n2 = ns[l][2];
+        L.fd0 = frmg::make_fastdiv((unsigned)L.n0);
+        L.fd1 = frmg::make_fastdiv((unsigned)L.n1);
         L.nc = ncell(l);
         L.A = Al[l];
         L.u = A.get<double>(L.nc);
@@ -616,7 +914,6 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
       sv.res_max = mx;
       status = rms <= tol ? FR_OK : FR_ENOCONV;
     } else {
-      d64 = A.get<double>(nc);
       SHier<float, true> H;
       H.ctx = ctx;
       H.st = st;
@@ -630,6 +927,8 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
         L.n0 = ns[l][0];
         L.n1 = ns[l][1];
         L.n2 = ns[l][2];
+        L.fd0 = frmg::make_fastdiv((unsigned)L.n0);
+        L.fd1 = frmg::make_fastdiv((unsigned)L.n1);
         L.nc = ncell(l);
         L.A = (float)Al[l];
         L.s = (float)s;
@@ -638,6 +937,26 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
         L.u = A.get<float>(L.nc);
         L.f = A.get<float>(L.nc);
         if (l > 0) L.uR = A.get<float>(L.nc);
+        // the register-column smoother on levels of at least 16 cells a side
+        // with enough tiles to fill the GPU (else one colour per launch)
+        if (o.tiling >= 0 && L.n0 >= 16 && L.n1 >= 16 && L.n2 >= 16) {
+          const long long tiles = (long long)((L.n0 + kSyTX - 1) / kSyTX) *
+                                  ((L.n1 + kSyTY - 1) / kSyTY);
+          const long long slots = 3ll * sm_count_sy();
+          if (o.tiling == 1 || tiles * ((L.n2 + 31) / 32) >= slots) {
+            double best = 1e300;
+            for (int c = 1; c <= L.n2; c++) {
+              const int z = (L.n2 + c - 1) / c;
+              const long long nbk = tiles * ((L.n2 + z - 1) / z);
+              const double cost = std::ceil((double)nbk / slots) * (z + 4);
+              if (cost < best - 1e-9) {
+                best = cost;
+                L.zc = z;
+              }
+            }
+            L.u2 = A.get<float>(L.nc);
+          }
+        }
         float *r = A.get<float>(L.nc);
         if (l == 0) {
           k_sy_convert<double, float><<<(unsigned)nblk(L.nc), kNT, 0, st>>>(rho, r, L.nc);
@@ -654,19 +973,36 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
       const long long nb1 = nl > 1 ? nblk(ncell(1)) : 0;
       double *part_in = nl > 1 ? A.get<double>(2 * nb1) : nullptr;
       H.part0 = part_in;
+      // chi and rho as double-float pairs for the outer loop
+      float2 *chi2 = A.get<float2>(nc), *rho2 = A.get<float2>(nc);
+      k_sy_split<<<(unsigned)nblk(nc), kNT, 0, st>>>(chi, chi2, nc);
+      SLAUNCH(ctx);
+      k_sy_split<<<(unsigned)nblk(nc), kNT, 0, st>>>(rho, rho2, nc);
+      SLAUNCH(ctx);
+      const float Ah = (float)Al[0], Alo = (float)(Al[0] - (double)Ah);
+      const float sh = (float)s, slo = (float)(s - (double)sh);
+      // defect of chi in double-float, with the set-up of the FP32 correction
+      // problem of the next outer step (g = hi(chi), f = -hi(d), delta = 0)
+      auto defect_df = [&](double &rms_, double &mx_) {
+        k_sy_defect_df<<<(unsigned)nblk(nc), kNT, 0, st>>>(H.lev[0], chi2, rho2, Ah, Alo, sh,
+                                                           slo, gl[0], H.lev[0].f, H.lev[0].u,
+                                                           part);
+        SLAUNCH(ctx);
+        norms(part, nblk(nc), nc, rms_, mx_);
+      };
       double rms, mx;
-      defect(rms, mx);
+      defect_df(rms, mx);
       sv.res0_rms = rms;
       push(rms);
-      if (bad_v(rms)) throw SError{FR_EDIVERGED, "non-finite residual"};
+      std::string diverged;
+      if (bad_v(rms)) diverged = "non-finite residual";
       double prev = rms;
       int grow = 0;
-      while (rms > tol && sv.outer < o.max_outer && sv.vcycles < o.max_vcycles * o.max_outer) {
+      while (diverged.empty() && rms > tol && sv.outer < o.max_outer &&
+             sv.vcycles < o.max_vcycles * o.max_outer) {
         sv.outer++;
         // correction problem of this outer step: N(delta) = -d on g = fp32(chi)
-        k_sy_prep<<<(unsigned)nblk(nc), kNT, 0, st>>>(chi, d64, gl[0], H.lev[0].f, H.lev[0].u,
-                                                      nc);
-        SLAUNCH(ctx);
+        // (fine level set up by the defect pass)
         for (int l = 1; l < nl; l++) {
           k_sy_restrict<float, float><<<(unsigned)nblk(ncell(l)), kNT, 0, st>>>(
               gl[l - 1], gl[l], ns[l][0], ns[l][1], ns[l][2]);
@@ -684,23 +1020,26 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
           if (nl == 1) break;
           double r, m;
           norms(part_in, nb1, nc, r, m);
-          if (bad_v(r)) throw SError{FR_EDIVERGED, "non-finite inner residual"};
+          if (bad_v(r)) break;  // the defect after the update reports it
           if (c > 0) q = r / rp;
           rp = r;
           if (r * q <= target || q > 0.8) break;
         }
-        k_sy_update<<<(unsigned)nblk(nc), kNT, 0, st>>>(chi, H.lev[0].u, nc);
+        k_sy_update_df<<<(unsigned)nblk(nc), kNT, 0, st>>>(chi2, H.lev[0].u, nc);
         SLAUNCH(ctx);
-        defect(rms, mx);
+        defect_df(rms, mx);
         push(-rms);
-        if (bad_v(rms)) throw SError{FR_EDIVERGED, "non-finite residual"};
+        if (bad_v(rms)) diverged = "non-finite residual";
         grow = rms > prev ? grow + 1 : 0;
-        if (grow >= 3) throw SError{FR_EDIVERGED, "defect grew for 3 outer steps"};
+        if (grow >= 3) diverged = "defect grew for 3 outer steps";
         prev = rms;
       }
       sv.res_rms = rms;
       sv.res_max = mx;
-      status = rms <= tol ? FR_OK : FR_ENOCONV;
+      status = !diverged.empty() ? FR_EDIVERGED : (rms <= tol ? FR_OK : FR_ENOCONV);
+      if (!diverged.empty()) frmg_set_error(diverged);
+      k_sy_join<<<(unsigned)nblk(nc), kNT, 0, st>>>(chi2, chi, nc);
+      SLAUNCH(ctx);
     }
     if (!chi_dev)
       SCK(cudaMemcpyAsync(chi_inout, chi, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -708,7 +1047,7 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
     sv.seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = sv;
-    if (status != FR_OK) frmg_set_error("tol not reached");
+    if (status == FR_ENOCONV) frmg_set_error("tol not reached");
     return status;
   } catch (SError &e) {
     frmg_set_error(e.msg);

@@ -44,6 +44,23 @@ def test_symmetron_matches_oracle(C, shape, sigma, seed, prec):
         assert s.hist[0] == pytest.approx(ref.hist[0], rel=1e-9)
 
 
+@pytest.mark.parametrize("tiling", [1, -1])
+@pytest.mark.parametrize("shape,sigma,seed", [((32, 32, 32), 2.0, 81), ((48, 34, 66), 1.5, 82),
+                                              ((16, 130, 20), 1.0, 83)])
+def test_register_column_sweeps_match_oracle(C, shape, sigma, seed, tiling):
+    """The mixed solve with its FP32 sweeps in the register-column kernel
+    (64 x 8 tiles, ragged and narrow grids that wrap a tile) and with one
+    launch per colour reaches the oracle's solution."""
+    rho = synth.lognormal_density(shape, seed, sigma=sigma)
+    box = 0.5 * shape[2]
+    ref = S.solve(rho, box=box, tol=1e-10, **P)
+    chi = torch.empty(shape, dtype=torch.float64, device="cuda")
+    st, s = C.symmetron(dev(rho), chi, box=box, tol=1e-10, prec="mixed", initial_guess=0,
+                        tiling=tiling, **P)
+    assert st == 0 and s.res_rms <= 1e-10, s.as_dict()
+    assert np.abs(host(chi) - ref.chi).max() <= 1e-7
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("a,expect", [(1.0, np.sqrt(1 - 0.125)), (0.4, 0.0)])
 def test_homogeneous_closed_form(C, prec, a, expect):
@@ -62,7 +79,7 @@ def test_linear_limit_matches_fft(C):
     rho = 1.0 + eps * g
     lin = S.linear_response(g, eps, box=16.0, **P)
     chi = torch.empty((n,) * 3, dtype=torch.float64, device="cuda")
-    st, s = C.symmetron(dev(rho), chi, box=16.0, tol=1e-14, prec="mixed", initial_guess=0, **P)
+    st, s = C.symmetron(dev(rho), chi, box=16.0, tol=1e-12, prec="mixed", initial_guess=0, **P)
     assert st == 0
     dev_ = np.abs(lin - S.background(1.0, 0.5)).max()
     assert np.abs(host(chi) - lin).max() <= 1e-3 * dev_
@@ -109,3 +126,22 @@ def test_256_sampled_against_oracle_residual(C):
     loc = float(np.sum((sv * rho - 1.0) * x + x ** 3))
     assert abs(loc) <= n ** 3 * 1e-8
     assert (x > 0).all() and x.max() < 1.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_overflowing_start_reports_divergence(C, prec):
+    """A start with one cell at 1e120 overflows the cubic term: the solve
+    reports FR_EDIVERGED (made on the host side, nothing faults) and the
+    context keeps working."""
+    from paper_1110_1379_gb300 import frmg
+    shape = (16, 16, 16)
+    rho = dev(synth.lognormal_density(shape, 76, sigma=1.0))
+    chi0 = np.full(shape, 0.9)
+    chi0[3, 4, 5] = 1e120
+    chi = dev(chi0)
+    st, s = C.symmetron(rho, chi, box=8.0, prec=prec, **P)
+    assert st == frmg.FR_EDIVERGED
+    assert b"non-finite" in frmg.load().fr_last_error()
+    chi.fill_(0.9)
+    st, s = C.symmetron(rho, chi, box=8.0, prec=prec, **P)
+    assert st == 0
