@@ -310,6 +310,22 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
                 fr_opts *best, double *best_seconds, void *stream);
 
 /*
+ * Autotuner of a batch (the arguments of fr_solve_batch): solves the batch
+ * from u = 0 (into library scratch; the caller's arrays are only read) with
+ * every combination of the V-cycle shape (pre, post) in {(1,1), (2,1), (1,2),
+ * (2,2), (3,3)}, the relaxation factor in {1, 1.15, 1.25} and tiling in
+ * {0, 1} at one sweep per tiled pass, then the smoother's kernel and tile
+ * (smooth_tile 16, 8, -1) on the fastest, on top of *base (NULL = defaults),
+ * twice each, and writes the fastest setting that reaches tol for every field
+ * to *best (its time in seconds to *best_seconds if not NULL).  Device or host
+ * densities.  FR_ENOCONV if no candidate converged.
+ */
+int fr_autotune_batch(frmg_ctx *ctx, int nfields, const double *const *density,
+                      const int (*dims)[3], const double *box_mpc_h, const double *a,
+                      const double *fr0_abs, double omega_m, double tol, const fr_opts *base,
+                      fr_opts *best, double *best_seconds, void *stream);
+
+/*
  * Triangle-shaped-cloud density assignment (Sec. VI.C, the code's default
  * scheme): arguments and result as fr_cic_assign; each particle spreads over
  * the 27 nearest cell centres with weights prod_d W(x_d), W = 3/4 - d^2 for the

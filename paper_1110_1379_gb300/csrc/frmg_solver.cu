@@ -2616,6 +2616,97 @@ int fr_autotune(frmg_ctx *ctx, const double *density, const int dims[3], double 
   });
 }
 
+int fr_autotune_batch(frmg_ctx *ctx, int nfields, const double *const *density,
+                      const int (*dims)[3], const double *box, const double *a,
+                      const double *fr0, double om, double tol, const fr_opts *base,
+                      fr_opts *best, double *best_seconds, void *stream) {
+  return guard([&]() {
+    if (!ctx || nfields <= 0 || !density || !dims || !box || !a || !fr0 || !best)
+      einval("NULL argument or nfields <= 0");
+    fr_opts o0 = resolve_opts(base);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    // scratch solutions (every trial starts from u = 0 and never reads them)
+    // and device copies of host densities
+    std::vector<void *> held;
+    std::vector<double *> us(nfields);
+    std::vector<const double *> rhos(nfields);
+    struct Release {
+      frmg_ctx *c;
+      std::vector<void *> &v;
+      ~Release() {
+        for (void *p : v) frmg_release(c, p);
+      }
+    } rel{ctx, held};
+    for (int i = 0; i < nfields; i++) {
+      if (!density[i]) einval("NULL field pointer");
+      check_dims(dims[i]);
+      check_model(box[i], a[i], om, fr0[i]);
+      const long long nc = (long long)dims[i][0] * dims[i][1] * dims[i][2];
+      us[i] = (double *)frmg_alloc(ctx, nc * sizeof(double));
+      held.push_back(us[i]);
+      rhos[i] = density[i];
+      if (!is_device_ptr(density[i])) {
+        double *d = (double *)frmg_alloc(ctx, nc * sizeof(double));
+        held.push_back(d);
+        CK(cudaMemcpyAsync(d, density[i], nc * sizeof(double), cudaMemcpyHostToDevice, st));
+        rhos[i] = d;
+      }
+    }
+    CK(cudaStreamSynchronize(st));
+    const int shapes[5][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 3}};
+    const double relaxes[3] = {1.0, 1.15, 1.25};
+    double best_t = HUGE_VAL;
+    fr_opts best_o = o0;
+    int status = FR_ENOCONV;
+    auto trial = [&](fr_opts o) {
+      o.initial_guess = 0;
+      double tmin = HUGE_VAL;
+      for (int rep = 0; rep < 2; rep++) {
+        const double t0 = now_s();
+        const int r = fr_solve_batch(ctx, nfields, rhos.data(), dims, box, a, fr0, om, tol,
+                                     us.data(), &o, nullptr, stream);
+        const double t1 = now_s();
+        if (r != FR_OK) return;
+        tmin = std::min(tmin, t1 - t0);
+      }
+      if (tmin < best_t) {
+        best_t = tmin;
+        best_o = o;
+        best_o.initial_guess = o0.initial_guess;
+        status = FR_OK;
+      }
+    };
+    // V-cycle shape x relaxation x tiling (the shared-memory kernels where the
+    // level sets fill the GPU, or wherever possible), then the smoother's tile
+    for (int tiling : {0, 1})
+      for (int sh = 0; sh < 5; sh++)
+        for (double w : relaxes) {
+          fr_opts o = o0;
+          o.pre = shapes[sh][0];
+          o.post = shapes[sh][1];
+          o.temporal_depth = 1;
+          o.relax = w;
+          o.tiling = tiling;
+          trial(o);
+        }
+    if (status == FR_OK) {
+      if (best_o.smooth_tile == 0) best_o.smooth_tile = kDefaultSmoothTile;
+      const fr_opts b0 = best_o;
+      for (int t : {16, 8, -1}) {
+        if (t == b0.smooth_tile) continue;
+        fr_opts o = b0;
+        o.smooth_tile = t;
+        trial(o);
+      }
+    }
+    *best = best_o;
+    if (best_seconds) *best_seconds = best_t;
+    if (status != FR_OK) g_last_error = "no candidate setting reached tol";
+    return status;
+  });
+}
+
 int fr_vcycles(frmg_ctx *ctx, const double *density, const int dims[3], double box, double a,
                double om, double fr0, double *u, int ncycles, const fr_opts *opts,
                fr_stats *stats, void *stream) {

@@ -60,7 +60,8 @@ EXPORTS = ["fr_opts_default", "fr_status_string", "fr_last_error", "fr_ctx_creat
            "fr_cic_assign", "fr_smooth", "fr_residual", "fr_restrict", "fr_prolong_correct",
            "fr_patch_bc", "fr_vcycles", "fr_launch_count", "fr_profile", "fr_profile_entry", "fr_smooth_f32", "fr_residual_df",
            "fr_residual_norm_noalloc", "fr_autotune", "fr_poisson_solve", "fr_poisson_source",
-           "fr_tsc_assign", "fr_particle_forces", "fr_solve_masked", "fr_symmetron_solve"]
+           "fr_tsc_assign", "fr_particle_forces", "fr_solve_masked", "fr_symmetron_solve",
+           "fr_autotune_batch"]
 
 
 def lib_path():
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = False):
             "fr_solve_masked": (I, [P, P, P, P, D, D, D, D, D, D, P, P, P, P]),
             "fr_profile_entry": (I, [P, I, P, I, P, P]),
             "fr_symmetron_solve": (I, [P, P, P, D, D, D, D, D, P, P, P, P]),
+            "fr_autotune_batch": (I, [P, I, P, P, P, P, P, D, D, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -347,6 +349,25 @@ class Context:
                                      ctypes.byref(o), stats, _stream(stream))
         self._raise(st, "fr_solve_batch", allow=(FR_ENOCONV, FR_EDIVERGED))
         return st, list(stats)
+
+    def autotune_batch(self, densities, *, boxes, avals, fr0s, omega_m, tol=1e-8, stream=None,
+                       **base):
+        """Fastest batch setting (V-cycle shape, relaxation, tiling, smoother
+        tile) for these fields; returns (opts dict, seconds)."""
+        n = len(densities)
+        dens = (ctypes.c_void_p * n)(*[_ptr(d).value for d in densities])
+        dims = ((ctypes.c_int * 3) * n)(*[_dims(d.shape) for d in densities])
+        bx = (ctypes.c_double * n)(*boxes)
+        av = (ctypes.c_double * n)(*avals)
+        fv = (ctypes.c_double * n)(*fr0s)
+        b = self.opts(tol=tol, **base)
+        best = fr_opts()
+        secs = ctypes.c_double()
+        st = self.lib.fr_autotune_batch(self._h, n, dens, dims, bx, av, fv, omega_m, tol,
+                                        ctypes.byref(b), ctypes.byref(best), ctypes.byref(secs),
+                                        _stream(stream))
+        self._raise(st, "fr_autotune_batch")
+        return {k: getattr(best, k) for k, _ in fr_opts._fields_}, secs.value
 
     def solve_levels(self, density, u, patches, *, box, a, omega_m, fr0, tol=1e-8,
                      tol_patch=None, stream=None, **opts):

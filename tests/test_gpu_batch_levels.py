@@ -65,6 +65,26 @@ def test_small_batch_matches_oracle(C, prec):
             assert stt.vcycles == ref.cycles
 
 
+def test_batch_autotune_returns_a_converging_setting(C):
+    specs = [dict(n=16, fr0=1e-4, a=0.5, sigma=1.0, box=16.0, seed=21),
+             dict(n=32, fr0=1e-5, a=1.0, sigma=2.0, box=32.0, seed=22),
+             dict(n=24, fr0=1e-6, a=0.8, sigma=1.5, box=24.0, seed=23)]
+    rhos = [synth.lognormal_density((s["n"],) * 3, s["seed"], sigma=s["sigma"]) for s in specs]
+    kw = dict(boxes=[s["box"] for s in specs], avals=[s["a"] for s in specs],
+              fr0s=[s["fr0"] for s in specs], omega_m=OM, tol=1e-8)
+    best, secs = C.autotune_batch([dev(r) for r in rhos], prec="mixed", **kw)
+    assert secs > 0 and (best["pre"], best["post"]) in [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3)]
+    assert best["relax"] in (1.0, 1.15, 1.25) and best["tiling"] in (0, 1)
+    assert best["smooth_tile"] in (16, 8, -1)
+    us = [torch.zeros((s["n"],) * 3, dtype=torch.float64, device="cuda") for s in specs]
+    opts = {k: best[k] for k in ("pre", "post", "relax", "tiling", "smooth_tile")}
+    st, stats = C.solve_batch([dev(r) for r in rhos], us, prec="mixed", **kw, **opts)
+    assert st == 0
+    for s, r, u in zip(specs, rhos, us):
+        ref = O.solve(r, tol=1e-8, box=s["box"], a=s["a"], omega_m=OM, fr0=s["fr0"])
+        assert np.abs(host(u) - ref.u).max() <= 1e-6
+
+
 def test_full_batch_workload(C):
     """96 fields, N in {32..128}, mixed precision, one batched solve."""
     specs = synth.batch_specs(96, 5000)
