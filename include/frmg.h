@@ -100,13 +100,14 @@ typedef struct {
                                1 = u holds the initial guess (default); 0 = start from
                                u = 0: the contents of u are not read (a host u is not
                                copied to the device), u is output only. */
-    int smooth_tile;        /* mixed: kernel and tile of the one-sweep FP32 smoother of
-                               the plain (full-variable) form on tiled levels: 8 or 16 =
-                               register-column kernel on 64 x 8 or 64 x 16 tiles (each
+    int smooth_tile;        /* mixed: kernel and tile of the one-sweep FP32 smoothers on
+                               tiled levels: 8 or 16 = register-column kernels (each
                                thread keeps its x-pairs' last four planes in registers),
-                               -1 = shared-memory plane-ring kernel on 64 x 16 tiles,
+                               the plain (full-variable) form on 64 x 8 or 64 x 16
+                               tiles and the correction form on 64 x 8 tiles; -1 =
+                               shared-memory plane-ring kernels on 64 x 16 tiles;
                                0 = library default.  Every choice performs the same
-                               sweep (identical results); only the speed differs. */
+                               sweeps (identical results); only the speed differs. */
 } fr_opts;
 
 #define FR_HIST 64
@@ -221,9 +222,9 @@ int fr_smooth(frmg_ctx *ctx, double *u, const double *density, const double *f,
  * unknown.  bg non-NULL: u is a correction delta on the FP32 background bg and
  * the equation is A(bg + delta) - A(bg) = f.  tiled != 0 selects the
  * shared-memory temporally blocked kernel (grids of at least 16 cells a side),
- * 8 or 16 the register-column kernel on 64 x 8 or 64 x 16 tiles (plain form,
- * bg NULL; the correction form keeps the shared-memory kernel), 0 the
- * one-colour-per-launch kernel; all give the same sweeps. */
+ * 8 or 16 the register-column kernel (plain form on 64 x 8 or 64 x 16 tiles,
+ * correction form on 64 x 8 tiles), 0 the one-colour-per-launch kernel; all
+ * give the same sweeps. */
 int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, const int dims[3],
                   double h, double box_mpc_h, double a, double omega_m, double fr0_abs,
                   const float *ub, int nsweeps, double step_cap, int tiled, void *stream);

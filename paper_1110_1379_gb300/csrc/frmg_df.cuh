@@ -78,15 +78,11 @@ __global__ void k_df_final(DFGrid G, double *u64) {
   u64[t] = join_bits(v.x, v.y);
 }
 
-// One face of the double-float operator: (B_i + B_j)(u_j - u_i).
-__device__ __forceinline__ df df_face(df ui, df Bi, df uj, df Bj) {
+// u_j - u_i of one face in double-float.
+__device__ __forceinline__ df df_diff(df ui, df uj) {
   df dd = two_sum(uj.h, -ui.h);
   dd.l += uj.l - ui.l;
-  dd = fast_two_sum(dd.h, dd.l);
-  df sB = two_sum(Bi.h, Bj.h);
-  sB.l += Bi.l + Bj.l;
-  sB = fast_two_sum(sB.h, sB.l);
-  return df_mul(sB, dd);
+  return fast_two_sum(dd.h, dd.l);
 }
 
 // FP64-accurate defect d = A(u) - gamma (rho - 1) of the fine grid in
@@ -115,12 +111,19 @@ __global__ void __launch_bounds__(256)
     const float2 uv = G.u[t], Bv = G.B[t];
     const df ui = {uv.x, uv.y};
     const df Bi = {Bv.x, Bv.y};
-    df acc = {0.f, 0.f};
+    // sum over the faces of (B_i + B_j)(u_j - u_i) = B_i S1 + S2 with
+    // S1 = sum (u_j - u_i) and S2 = sum B_j (u_j - u_i)
+    df fs1 = {0.f, 0.f}, fs2 = {0.f, 0.f};
     const bool dir = G.bnd != nullptr;
     const long long sx = 1, sy = G.n0, sz = (long long)G.n0 * G.n1;
+    auto face = [&](df uj, df Bj) {
+      const df dd = df_diff(ui, uj);
+      fs1 = df_add(fs1, dd);
+      fs2 = df_add(fs2, df_mul(Bj, dd));
+    };
     auto reg = [&](long long cj) {
       const float2 uj = G.u[cj], Bj = G.B[cj];
-      acc = df_add(acc, df_face(ui, Bi, df{uj.x, uj.y}, df{Bj.x, Bj.y}));
+      face(df{uj.x, uj.y}, df{Bj.x, Bj.y});
     };
     auto ghost = [&](int f) {
       long long o;
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(256)
       const df ub = split_bits(G.bnd[G.foff[f] + o]);
       // u_g = 2 u_b - u_i (mask ratio r = -1), b_g = exp(u_g)
       const df ug = df_sub(df{2.f * ub.h, 2.f * ub.l}, ui);
-      acc = df_add(acc, df_face(ui, Bi, ug, df_exp(ug, ln2h, ln2l)));
+      face(ug, df_exp(ug, ln2h, ln2l));
     };
     if (i > 0) reg(t - sx); else if (!dir) reg(t + (G.n0 - 1) * sx); else ghost(0);
     if (i < G.n0 - 1) reg(t + sx); else if (!dir) reg(t - (G.n0 - 1) * sx); else ghost(1);
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(256)
     if (j < G.n1 - 1) reg(t + sy); else if (!dir) reg(t - (G.n1 - 1) * sy); else ghost(3);
     if (k > 0) reg(t - sz); else if (!dir) reg(t + (G.n2 - 1) * sz); else ghost(4);
     if (k < G.n2 - 1) reg(t + sz); else if (!dir) reg(t - (G.n2 - 1) * sz); else ghost(5);
+    const df acc = df_add(df_mul(Bi, fs1), fs2);
     // beta (e^{-u/2} - 1) with e^{-u/2} = 1/sqrt(e^u)
     const df y = df_add_f(df_rsqrt(Bi), -1.0f);
     df d = df_add(df_mul(acc, df{G.ahh, G.ahl}), df_mul(y, df{G.beh, G.bel}));

@@ -1506,13 +1506,15 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
 
 // ---------------------------------------------------------------------------
 // One red-black sweep per launch with register-resident z-columns (plain FP32
-// form; the same sweep, cell for cell and bit for bit, as k_smooth_rb).
+// form, and with BG the correction form; the same sweep, cell for cell and bit
+// for bit, as k_smooth_rb).
 //
 // A block owns a 64 x TY tile and a chunk of zc planes and marches along z over
 // the planes Z0-2 .. Z1+1.  Every x-pair of the tile plus a halo of two cells
 // (34 x (TY + 4) pairs) has one owner thread for the whole march, which keeps
-// the pair's red and black cell (u, x = expm1(u)) and right-hand sides for the
-// last four planes in registers: the z neighbours of an update are the owner's
+// the pair's red and black cell ((u, x = expm1(u)), in the correction form
+// (delta, x, background ub, E = e^ub)) and right-hand sides for the last four
+// planes in registers: the z neighbours of an update are the owner's
 // own registers, and only the xy exchange goes through shared memory.  At the
 // step that loads plane p:
 //   1. the pair's u and f of plane p (loaded a step earlier) are split into its
@@ -1536,7 +1538,7 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
 // Thread layout (256 threads, 8 warps): warp w owns the interior pairs
 // px = 1 + lane of rows 2 + w + 8 j (j < TY / 8), and thread t < NHALO also
 // one halo pair: the four halo rows for t < 128, the two halo columns above.
-template <int TY>
+template <int TY, bool BG = false>
 struct RCCfg {
   static constexpr int TX = 64, H = 2, PX = TX / 2 + 2, LY = TY + 2 * H, PP = PX * LY;
   static constexpr int NT = 256, NW = NT / 32;
@@ -1544,22 +1546,30 @@ struct RCCfg {
   static constexpr int NSL = NI + 1;                  // pair slots per thread
   static constexpr int NHR = 4 * (TX / 2);            // halo-row pairs
   static constexpr int NHALO = NHR + 2 * LY;          // all halo pairs
-  static constexpr int MINB = TY <= 8 ? 3 : 2;        // resident blocks per SM
-  static constexpr size_t smem() { return (size_t)4 * PP * sizeof(float2); }
+#ifndef FR_RC_MINB16
+#define FR_RC_MINB16 2
+#endif
+  // resident blocks per SM (64 x 16 tiles: 2, 124 registers; 3 would cap the
+  // registers at 80 and spill)
+  // (correction form: four values per cell, 64 x 8 tiles at 2 blocks per SM)
+  static constexpr int MINB = BG ? 2 : (TY <= 8 ? 3 : FR_RC_MINB16);
+  using Cell = typename std::conditional<BG, float4, float2>::type;
+  static constexpr size_t smem() { return (size_t)4 * PP * sizeof(Cell); }
   static_assert(TY % NW == 0 && NHALO <= NT, "tile height");
 };
 
-template <bool DIR, int TY>
-__global__ void __launch_bounds__(RCCfg<TY>::NT, RCCfg<TY>::MINB)
+template <bool BG, bool DIR, int TY>
+__global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
     k_smooth_rc(const Grid<float> *grids, const int *off, int ngrid, int zc, const int *active,
                 int par) {
-  using C = RCCfg<TY>;
+  using C = RCCfg<TY, BG>;
+  using Cell = typename C::Cell;
   constexpr int TX = C::TX, PX = C::PX, PP = C::PP, NI = C::NI, NSL = C::NSL;
   constexpr int NHR = C::NHR, NHALO = C::NHALO, LY = C::LY;
-  extern __shared__ float2 smem_rc[];
+  extern __shared__ float4 smem_rc4[];
   // black half-planes [2][PP] (old values), red half-planes [2][PP] (new values)
-  float2 *const sbk = smem_rc;
-  float2 *const srd = smem_rc + 2 * PP;
+  Cell *const sbk = reinterpret_cast<Cell *>(smem_rc4);
+  Cell *const srd = sbk + 2 * PP;
   const int g = find_grid(off, ngrid, blockIdx.x);
   const Grid<float> &Gg = grids[g];
   if (!grid_active(active, Gg.field)) return;
@@ -1567,6 +1577,8 @@ __global__ void __launch_bounds__(RCCfg<TY>::NT, RCCfg<TY>::MINB)
   float *__restrict__ uout = par ? Gg.u : Gg.u2;
   float *__restrict__ xout = par ? Gg.x : Gg.x2;
   const float *__restrict__ fin = Gg.f;
+  const float *__restrict__ ubin = Gg.ubg;
+  const float *__restrict__ Ein = Gg.Ebg;
   const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap,
               relax = Gg.relax;
   const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
@@ -1640,18 +1652,22 @@ __global__ void __launch_bounds__(RCCfg<TY>::NT, RCCfg<TY>::MINB)
     fl[s] = f;
   }
 
-  // register ring: plane P0 + k in slot k & 3; red and black cell (u, x), f
-  float2 R[NSL][4], B[NSL][4];
+  // register ring: plane P0 + k in slot k & 3; red and black cell, f
+  Cell R[NSL][4], B[NSL][4];
   float FR[NSL][4], FB[NSL][4];
-  float2 pu[NSL], pf[NSL];  // prefetched plane (u, f of the even and odd cell)
+  // prefetched plane (u, f and, in the correction form, ub and E of the even
+  // and odd cell)
+  float2 pu[NSL], pf[NSL], pb[NSL], pe[NSL];
 #pragma unroll
   for (int s = 0; s < NSL; s++) {
     pu[s] = make_float2(0.f, 0.f);
     pf[s] = pu[s];
+    pb[s] = pu[s];
+    pe[s] = make_float2(1.f, 1.f);
 #pragma unroll
     for (int r = 0; r < 4; r++) {
-      R[s][r] = pu[s];
-      B[s][r] = pu[s];
+      R[s][r] = Cell{};
+      B[s][r] = Cell{};
       FR[s][r] = 0.f;
       FB[s][r] = 0.f;
     }
@@ -1665,51 +1681,71 @@ __global__ void __launch_bounds__(RCCfg<TY>::NT, RCCfg<TY>::MINB)
         if (!(fl[s] & 1u)) continue;
         pu[s] = *reinterpret_cast<const float2 *>(uin + zo + roff[s]);
         if (fin) pf[s] = *reinterpret_cast<const float2 *>(fin + zo + roff[s]);
+        if (BG) {
+          pb[s] = *reinterpret_cast<const float2 *>(ubin + zo + roff[s]);
+          pe[s] = *reinterpret_cast<const float2 *>(Ein + zo + roff[s]);
+        }
       }
     }
     pw = DIR ? pw + 1 : (pw + 1 == n2 ? 0 : pw + 1);
   };
   fetch();
 
-  // Newton update of one cell: own (u, x, f), neighbours -x, +x, -y, +y, -z, +z
-  // as (u, x); the same face order and arithmetic as k_smooth_rb
-  auto newton = [&](float2 own, float fi, float2 lf, float2 rt, float2 ym, float2 yp, float2 zm,
-                    float2 zp, int gx, int gy, int m) -> float {
+  // (ub, E) of a cell: (0, 1) in the plain form
+  auto bgv = [](const Cell &c) -> float2 {
+    if constexpr (BG)
+      return make_float2(c.z, c.w);
+    else
+      return make_float2(0.0f, 1.0f);
+  };
+  // Newton update of one cell: own cell and f, neighbours -x, +x, -y, +y, -z,
+  // +z; the same face order and arithmetic as k_smooth_rb
+  auto newton = [&](Cell own, float fi, Cell lf, Cell rt, Cell ym, Cell yp, Cell zm, Cell zp,
+                    int gx, int gy, int m) -> float {
     const float di = own.x, xi = own.y;
-    const float Bi = 1.0f + xi;
-    OpAcc<float, false> A(di, 1.0f, xi, Bi, 0.0f);
+    const float Ei = bgv(own).y, ubi = bgv(own).x;
+    const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
+    OpAcc<float, BG> A(di, Ei, xi, Bi, ubi);
+    auto nb = [&](const Cell &c) { A.reg(c.x, c.y, bgv(c).x, bgv(c).y); };
     if (DIR && gx == 0)
       A.ghost(face_value(Gg, 0, gx, gy, m));
     else
-      A.reg(lf.x, lf.y, 0.0f, 1.0f);
+      nb(lf);
     if (DIR && gx == n0 - 1)
       A.ghost(face_value(Gg, 1, gx, gy, m));
     else
-      A.reg(rt.x, rt.y, 0.0f, 1.0f);
+      nb(rt);
     if (DIR && gy == 0)
       A.ghost(face_value(Gg, 2, gx, gy, m));
     else
-      A.reg(ym.x, ym.y, 0.0f, 1.0f);
+      nb(ym);
     if (DIR && gy == n1 - 1)
       A.ghost(face_value(Gg, 3, gx, gy, m));
     else
-      A.reg(yp.x, yp.y, 0.0f, 1.0f);
+      nb(yp);
     if (DIR && m == 0)
       A.ghost(face_value(Gg, 4, gx, gy, m));
     else
-      A.reg(zm.x, zm.y, 0.0f, 1.0f);
+      nb(zm);
     if (DIR && m == n2 - 1)
       A.ghost(face_value(Gg, 5, gx, gy, m));
     else
-      A.reg(zp.x, zp.y, 0.0f, 1.0f);
+      nb(zp);
     float acc, dacc, N, dN;
     A.done(acc, dacc);
-    finish_op(xi, 1.0f, acc, dacc, ah, beta, false, N, dN);
+    finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
     float du = relax * newton_step(N - fi, dN);
     du = fminf(fmaxf(du, -cap), cap);
     return di + du;
   };
-  auto sel = [](bool c, float2 a, float2 b) { return c ? a : b; };
+  auto sel = [](bool c, Cell a, Cell b) { return c ? a : b; };
+  // cell of value u (x recomputed) with the background of cell c
+  auto with_u = [&](const Cell &c, float u) -> Cell {
+    Cell r = c;
+    r.x = u;
+    r.y = m_expm1(u);
+    return r;
+  };
 
   auto step = [&](auto Kc, int k) {
     constexpr int K = decltype(Kc)::value;  // ring slot of plane p
@@ -1726,8 +1762,15 @@ __global__ void __launch_bounds__(RCCfg<TY>::NT, RCCfg<TY>::MINB)
         const float ur = odd ? pu[s].y : pu[s].x, ub = odd ? pu[s].x : pu[s].y;
         // the red cell's x is needed only if this pair's red cell is updated
         const bool needr = s < NI || (fl[s] & (odd ? 8u : 4u));
-        R[s][K] = make_float2(ur, needr ? m_expm1(ur) : 0.0f);
-        B[s][K] = make_float2(ub, m_expm1(ub));
+        if constexpr (BG) {
+          R[s][K] = make_float4(ur, needr ? m_expm1(ur) : 0.0f, odd ? pb[s].y : pb[s].x,
+                                odd ? pe[s].y : pe[s].x);
+          B[s][K] = make_float4(ub, m_expm1(ub), odd ? pb[s].x : pb[s].y,
+                                odd ? pe[s].x : pe[s].y);
+        } else {
+          R[s][K] = make_float2(ur, needr ? m_expm1(ur) : 0.0f);
+          B[s][K] = make_float2(ub, m_expm1(ub));
+        }
         if (fin) {
           const float fr = odd ? pf[s].y : pf[s].x, fb = odd ? pf[s].x : pf[s].y;
           FR[s][K] = fs * (fr - fo);
@@ -1748,13 +1791,13 @@ __global__ void __launch_bounds__(RCCfg<TY>::NT, RCCfg<TY>::MINB)
         for (int s = 0; s < NSL; s++) {
           const bool odd = (ro[s] ^ PK1) != 0;
           if (!((s < NI && !DIR) || (fl[s] & (odd ? 8u : 4u)))) continue;
-          const float2 *bk = sbk + PK1 * PP + q[s];
-          const float2 ym = bk[-PX], yp = bk[PX];
-          const float2 nx = bk[odd ? 1 : -1];
+          const Cell *bk = sbk + PK1 * PP + q[s];
+          const Cell ym = bk[-PX], yp = bk[PX];
+          const Cell nx = bk[odd ? 1 : -1];
           const float un = newton(R[s][K1], FR[s][K1], sel(odd, B[s][K1], nx),
                                   sel(odd, nx, B[s][K1]), ym, yp, B[s][K2], B[s][K],
                                   gxe[s] + (odd ? 1 : 0), gyv[s], m);
-          R[s][K1] = make_float2(un, m_expm1(un));
+          R[s][K1] = with_u(R[s][K1], un);
           srd[PK1 * PP + q[s]] = R[s][K1];
         }
       }
@@ -1767,15 +1810,15 @@ __global__ void __launch_bounds__(RCCfg<TY>::NT, RCCfg<TY>::MINB)
         for (int s = 0; s < NI; s++) {
           if (DIR && !(fl[s] & 1u)) continue;
           const bool odd = (ro[s] ^ PK2) == 0;  // black cell is the odd one
-          const float2 *rd = srd + PK2 * PP + q[s];
-          const float2 ym = rd[-PX], yp = rd[PX];
-          const float2 nx = rd[odd ? 1 : -1];
+          const Cell *rd = srd + PK2 * PP + q[s];
+          const Cell ym = rd[-PX], yp = rd[PX];
+          const Cell nx = rd[odd ? 1 : -1];
           const float un = newton(B[s][K2], FB[s][K2], sel(odd, R[s][K2], nx),
                                   sel(odd, nx, R[s][K2]), ym, yp, R[s][K3], R[s][K1],
                                   gxe[s] + (odd ? 1 : 0), gyv[s], m);
-          B[s][K2] = make_float2(un, m_expm1(un));
+          B[s][K2] = with_u(B[s][K2], un);
           if (fl[s] & 2u) {
-            const float2 e = sel(odd, R[s][K2], B[s][K2]), o = sel(odd, B[s][K2], R[s][K2]);
+            const Cell e = sel(odd, R[s][K2], B[s][K2]), o = sel(odd, B[s][K2], R[s][K2]);
             const long long oo = (long long)m * plane + roff[s];
             *reinterpret_cast<float2 *>(uout + oo) = make_float2(e.x, o.x);
             *reinterpret_cast<float2 *>(xout + oo) = make_float2(e.y, o.y);

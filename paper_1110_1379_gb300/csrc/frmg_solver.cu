@@ -461,13 +461,13 @@ struct LevelSet {
   std::vector<int> off_rb[2];
   int *d_off_rb[2] = {nullptr, nullptr};
   int nblk_rb[2] = {0, 0};
-  // register-column one-sweep smoother of the plain form (64 x rc_ty tiles;
-  // 0: the plain form uses k_smooth_rb too)
-  int rc_ty = 0;
-  int zc_rc = 0;
-  std::vector<int> off_rc;
-  int *d_off_rc = nullptr;
-  int nblk_rc = 0;
+  // register-column one-sweep smoother: [0] plain form on 64 x rc_ty[0]
+  // tiles, [1] correction form on 64 x 8 tiles (rc_ty 0: k_smooth_rb instead)
+  int rc_ty[2] = {0, 0};
+  int zc_rc[2] = {0, 0};
+  std::vector<int> off_rc[2];
+  int *d_off_rc[2] = {nullptr, nullptr};
+  int nblk_rc[2] = {0, 0};
   // tiled FAS right-hand side (coarse side of a V-cycle level); [0] plain,
   // [1] correction form
   int zc_fr[2] = {0, 0};
@@ -557,7 +557,7 @@ static int pick_chunk(const std::vector<long long> &tiles, const std::vector<int
 
 template <bool BG, bool DIR>
 static long long rb_slots();
-template <bool DIR, int TY>
+template <bool BG, bool DIR, int TY>
 static long long rc_slots();
 template <bool BG, bool DIR>
 static long long fr_slots();
@@ -649,20 +649,29 @@ static void upload_set(Scope &S, LevelSet<T> &ls, cudaStream_t st, int tiling = 
                            cudaMemcpyHostToDevice, st));
       }
       if (stile == 8 || stile == 16) {
-        ls.rc_ty = stile;
-        for (int g = 0; g < ng; g++)
-          tl[g] = (long long)((ls.h[g].n0 + kTX - 1) / kTX) * ((ls.h[g].n1 + stile - 1) / stile);
-        const long long slots =
-            stile == 8 ? (ls.dirichlet ? rc_slots<true, 8>() : rc_slots<false, 8>())
-                       : (ls.dirichlet ? rc_slots<true, 16>() : rc_slots<false, 16>());
-        ls.zc_rc = pick_chunk(tl, n2s, slots, 4, false);
-        ls.off_rc.assign(ng + 1, 0);
-        for (int g = 0; g < ng; g++)
-          ls.off_rc[g + 1] = ls.off_rc[g] + (int)(tl[g] * ((n2s[g] + ls.zc_rc - 1) / ls.zc_rc));
-        ls.nblk_rc = ls.off_rc[ng];
-        ls.d_off_rc = S.get<int>(ng + 1);
-        CK(cudaMemcpyAsync(ls.d_off_rc, ls.off_rc.data(), (ng + 1) * sizeof(int),
-                           cudaMemcpyHostToDevice, st));
+        // plain form on 64 x stile tiles, correction form on 64 x 8 tiles
+        for (int v = 0; v < 2; v++) {
+          const int ty = v ? 8 : stile;
+          ls.rc_ty[v] = ty;
+          for (int g = 0; g < ng; g++)
+            tl[g] = (long long)((ls.h[g].n0 + kTX - 1) / kTX) * ((ls.h[g].n1 + ty - 1) / ty);
+          long long slots;
+          if (v)
+            slots = ls.dirichlet ? rc_slots<true, true, 8>() : rc_slots<true, false, 8>();
+          else if (ty == 8)
+            slots = ls.dirichlet ? rc_slots<false, true, 8>() : rc_slots<false, false, 8>();
+          else
+            slots = ls.dirichlet ? rc_slots<false, true, 16>() : rc_slots<false, false, 16>();
+          ls.zc_rc[v] = pick_chunk(tl, n2s, slots, 4, false);
+          ls.off_rc[v].assign(ng + 1, 0);
+          for (int g = 0; g < ng; g++)
+            ls.off_rc[v][g + 1] =
+                ls.off_rc[v][g] + (int)(tl[g] * ((n2s[g] + ls.zc_rc[v] - 1) / ls.zc_rc[v]));
+          ls.nblk_rc[v] = ls.off_rc[v][ng];
+          ls.d_off_rc[v] = S.get<int>(ng + 1);
+          CK(cudaMemcpyAsync(ls.d_off_rc[v], ls.off_rc[v].data(), (ng + 1) * sizeof(int),
+                             cudaMemcpyHostToDevice, st));
+        }
       }
       for (int g = 0; g < ng; g++)
         tl[g] = (long long)((ls.h[g].n0 + kFrTX - 1) / kFrTX) * ((ls.h[g].n1 + kFrTY - 1) / kFrTY);
@@ -917,25 +926,27 @@ static void launch_rr_tiled(frmg_ctx *ctx, LevelSet<float> &F, LevelSet<float> &
     launch_rr_k<BG, false>(ctx, F, C, active, fpar, cpar, partial, st);
 }
 
-template <bool DIR, int TY>
+template <bool BG, bool DIR, int TY>
 static void launch_rc_k(LevelSet<float> &s, const int *active, int par, cudaStream_t st) {
-  using RC = RCCfg<TY>;
+  using RC = RCCfg<TY, BG>;
+  constexpr int v = BG ? 1 : 0;
   const size_t sm = RC::smem();
   static bool attr_set = false;
   if (!attr_set) {
-    CK(cudaFuncSetAttribute(k_smooth_rc<DIR, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)sm));
+    CK(cudaFuncSetAttribute(k_smooth_rc<BG, DIR, TY>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
-  k_smooth_rc<DIR, TY><<<s.nblk_rc, RC::NT, sm, st>>>(s.d, s.d_off_rc, s.size(), s.zc_rc, active,
-                                                       par);
+  k_smooth_rc<BG, DIR, TY><<<s.nblk_rc[v], RC::NT, sm, st>>>(s.d, s.d_off_rc[v], s.size(),
+                                                              s.zc_rc[v], active, par);
 }
 
 template <bool BG, bool DIR>
 static void launch_rb_k(frmg_ctx *ctx, LevelSet<float> &s, const int *active, int par,
                         cudaStream_t st) {
-  if (!BG && s.rc_ty == 16) return launch_rc_k<DIR, 16>(s, active, par, st);
-  if (!BG && s.rc_ty == 8) return launch_rc_k<DIR, 8>(s, active, par, st);
+  if (BG && s.rc_ty[1] == 8) return launch_rc_k<true, DIR, 8>(s, active, par, st);
+  if (!BG && s.rc_ty[0] == 16) return launch_rc_k<false, DIR, 16>(s, active, par, st);
+  if (!BG && s.rc_ty[0] == 8) return launch_rc_k<false, DIR, 8>(s, active, par, st);
   constexpr int TY = kRbTY;
   using RC = RBCfg<TY>;
   size_t sm = RC::smem(BG);
@@ -976,12 +987,12 @@ static long long rb_slots() {
   return slots;
 }
 
-template <bool DIR, int TY>
+template <bool BG, bool DIR, int TY>
 static long long rc_slots() {
   static long long slots = 0;
   if (!slots)
     slots = (long long)sm_count() *
-            resident_blocks(k_smooth_rc<DIR, TY>, RCCfg<TY>::NT, RCCfg<TY>::smem());
+            resident_blocks(k_smooth_rc<BG, DIR, TY>, RCCfg<TY, BG>::NT, RCCfg<TY, BG>::smem());
   return slots;
 }
 

@@ -289,24 +289,33 @@ def test_f32_tiled_smoother_equals_simple(C, shape, bg, faces, nsweeps):
 
 
 @pytest.mark.parametrize("shape", F32_SHAPES + [(64, 48, 256), (40, 130, 66)])
+@pytest.mark.parametrize("bg", [False, True])
 @pytest.mark.parametrize("faces", [False, True])
 @pytest.mark.parametrize("nsweeps", [1, 2, 3])
-def test_register_column_smoother_is_the_ring_smoother(C, shape, faces, nsweeps):
-    """The register-column one-sweep kernel (64 x 8 and 64 x 16 tiles) performs
-    the same sweeps as the shared-memory plane-ring kernel, bit for bit: same
-    cells, same face order, same arithmetic (x = expm1(u) recomputed from u
-    equals the cached x)."""
+def test_register_column_smoother_is_the_ring_smoother(C, shape, bg, faces, nsweeps):
+    """The register-column one-sweep kernels (plain form on 64 x 8 and 64 x 16
+    tiles, correction form on 64 x 8) perform the same sweeps as the
+    shared-memory plane-ring kernels, bit for bit: same cells, same face order,
+    same arithmetic (x = expm1(u) recomputed from u equals the cached x).  The
+    patch faces of the correction form are the exception: there the compiler
+    contracts the ghost terms into fused multiply-adds differently in the two
+    kernels, so they agree to FP32 rounding."""
     rng = np.random.default_rng(31)
-    u0 = rng.uniform(-1.5, 0.3, shape)
+    u0 = rng.uniform(-0.3, 0.3, shape) if bg else rng.uniform(-1.5, 0.3, shape)
     f = rng.standard_normal(shape) * 0.3
+    b = rng.uniform(-1.5, 0.3, shape) if bg else None
     ub = rng.uniform(-1.5, 0.3, sum(O.face_sizes(shape))) if faces else None
     P = dict(box=128.0, a=0.9, omega_m=0.24, fr0=1e-5, h=1.0 / 48)
     outs = {}
     for tiled in (1, 8, 16):
         u = _f32(u0)
-        C.smooth_f32(u, nsweeps, f=_f32(f), ub=None if ub is None else _f32(ub), tiled=tiled,
-                     **P)
+        C.smooth_f32(u, nsweeps, bg=None if b is None else _f32(b), f=_f32(f),
+                     ub=None if ub is None else _f32(ub), tiled=tiled, **P)
         outs[tiled] = host(u)
+    if bg and faces:
+        for t in (8, 16):
+            assert np.abs(outs[1].astype(np.float64) - outs[t]).max() < 2e-6
+        return
     assert np.array_equal(outs[1], outs[8])
     assert np.array_equal(outs[1], outs[16])
 
