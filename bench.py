@@ -50,6 +50,10 @@ ALG_BYTES = {
     "smooth_f32@fine": 12.0,         # one full red-black sweep per launch: read u, f; write u
     "smooth_bg_f32@fine": 20.0,      # correction form: also reads the background u and e^u
     "smooth_f64@fine": 12.0,         # one colour per launch: (read u, f; write u) / 2, 8 B words
+    # first post-smoothing sweep with the prolongation fused in: the sweep's
+    # bytes plus the coarse correction (u^H, R u^h: 8 B per 8 fine cells)
+    "smooth_prolong_f32@fine": 13.0,
+    "smooth_prolong_bg_f32@fine": 21.0,
     "resid_restrict_f32@fine": 10.0,  # read u, rhs (8 B) + 4 coarse words / 8 cells
     "resid_restrict_f64@fine": 20.0,
     "prolong_f32@fine": 9.0,         # read/write u (8 B) + 2 coarse words / 8 cells

@@ -1530,7 +1530,13 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
 //      red cells of planes p-3 and p-1), and plane p-2 (u and its x cache) is
 //      written out.
 // Half-planes are double-buffered by step parity, so a step reads only what
-// the previous step wrote and one barrier per step suffices.  The ring of
+// the previous step wrote and one barrier per step suffices.
+// With PRL the sweep is the first one after the coarse-grid correction: every
+// arriving cell first gets u += P(u^H - R u^h) from the coarser grid (the
+// trilinear 27/9/3/1 prolongation of k_prolong_tiled, z then y then x, same
+// arithmetic), so the separate prolongation pass is saved.  The coarse
+// correction of the tile, blended in z for the next plane, is staged in
+// shared memory during the step before (double-buffered as the half-planes).  The ring of
 // register planes is indexed by the step modulo 4, which the loop unrolls into
 // compile-time indices; which cell of a pair is red is a per-slot bit flipped
 // every plane, applied with selects, so an update is straight-line code and
@@ -1554,14 +1560,18 @@ struct RCCfg {
   // (correction form: four values per cell, 64 x 8 tiles at 2 blocks per SM)
   static constexpr int MINB = BG ? 2 : (TY <= 8 ? 3 : FR_RC_MINB16);
   using Cell = typename std::conditional<BG, float4, float2>::type;
-  static constexpr size_t smem() { return (size_t)4 * PP * sizeof(Cell); }
+  // coarse tile of the prolongation (fine tile plus halo, +-1 coarse cell)
+  static constexpr int CXE = TX / 2 + 4, CYE = TY / 2 + 4, CE = CXE * CYE;
+  static constexpr size_t smem(bool prl = false) {
+    return (size_t)4 * PP * sizeof(Cell) + (prl ? (size_t)2 * CE * sizeof(float) : 0);
+  }
   static_assert(TY % NW == 0 && NHALO <= NT, "tile height");
 };
 
-template <bool BG, bool DIR, int TY>
+template <bool BG, bool DIR, int TY, bool PRL = false>
 __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
     k_smooth_rc(const Grid<float> *grids, const int *off, int ngrid, int zc, const int *active,
-                int par) {
+                int par, const Grid<float> *coarse = nullptr, int cpar = 0) {
   using C = RCCfg<TY, BG>;
   using Cell = typename C::Cell;
   constexpr int TX = C::TX, PX = C::PX, PP = C::PP, NI = C::NI, NSL = C::NSL;
@@ -1570,6 +1580,8 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
   // black half-planes [2][PP] (old values), red half-planes [2][PP] (new values)
   Cell *const sbk = reinterpret_cast<Cell *>(smem_rc4);
   Cell *const srd = sbk + 2 * PP;
+  float *const sez = reinterpret_cast<float *>(srd + 2 * PP);  // [2][CE] (PRL)
+  constexpr int CXE = C::CXE, CE = C::CE;
   const int g = find_grid(off, ngrid, blockIdx.x);
   const Grid<float> &Gg = grids[g];
   if (!grid_active(active, Gg.field)) return;
@@ -1691,6 +1703,87 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
   };
   fetch();
 
+  // prolongation (PRL): coarse correction e = u^H - R u^h of the coarse cells
+  // (X0/2 - 2 + ci, Y0/2 - 2 + cj), blended in z for fine plane p, into sez[b].
+  // The coarse values of the next plane are loaded into registers early in a
+  // step (ez_load) and blended and stored at its end (ez_store), so that the
+  // loads' latency overlaps the step's updates.
+  const float w3 = 0.75f, w1 = 0.25f;
+  constexpr int NEZ = PRL ? (CE + C::NT - 1) / C::NT : 1;
+  float ezH[NEZ][2], ezR[NEZ][2];
+  int coff[NEZ];  // offset in a coarse plane of this thread's tile entries (-1: none / zero)
+  const float *__restrict__ cuH = nullptr;
+  const float *__restrict__ cuR = nullptr;
+  int c2 = 1;
+  long long cplane = 0;
+  if constexpr (PRL) {
+    const Grid<float> &Cg = coarse[g];
+    cuH = cpar ? Cg.u2 : Cg.u;
+    cuR = Cg.uR;
+    const int c0 = Cg.n0, c1 = Cg.n1;
+    c2 = Cg.n2;
+    cplane = (long long)c0 * c1;
+#pragma unroll
+    for (int r = 0; r < NEZ; r++) {
+      const int q = threadIdx.x + r * C::NT;
+      coff[r] = -1;
+      if (q >= CE) continue;
+      const int cj = q / CXE, ci = q - cj * CXE;
+      int I = X0 / 2 - 2 + ci, J = Y0 / 2 - 2 + cj;
+      if (DIR) {
+        if (!(I >= 0 && I < c0 && J >= 0 && J < c1)) continue;
+      } else {
+        I = wrapmod(I, c0);
+        J = wrapmod(J, c1);
+      }
+      coff[r] = J * c0 + I;
+    }
+  }
+  auto ez_load = [&](int p) {
+    if constexpr (PRL) {
+      const int pz = DIR ? p : wrapmod(p, n2);
+      const int K = pz >> 1, K2 = (pz & 1) ? K + 1 : K - 1;  // nearer, farther coarse plane
+      const bool vK = !DIR || (pz >= 0 && pz < n2);
+      // K is in [0, c2) for a wrapped pz; K2 wraps by one plane at most
+      int K2w = K2;
+      bool vK2 = vK;
+      if (DIR)
+        vK2 = vK && K2 >= 0 && K2 < c2;
+      else
+        K2w = K2 < 0 ? c2 - 1 : (K2 == c2 ? 0 : K2);
+      const long long oa = (long long)K * cplane, ob = (long long)K2w * cplane;
+#pragma unroll
+      for (int r = 0; r < NEZ; r++) {
+        ezH[r][0] = ezR[r][0] = ezH[r][1] = ezR[r][1] = 0.0f;
+        if (coff[r] < 0) continue;
+        if (vK) {
+          ezH[r][0] = cuH[oa + coff[r]];
+          ezR[r][0] = cuR[oa + coff[r]];
+        }
+        if (vK2) {
+          ezH[r][1] = cuH[ob + coff[r]];
+          ezR[r][1] = cuR[ob + coff[r]];
+        }
+      }
+    }
+  };
+  auto ez_store = [&](int bsel) {
+    if constexpr (PRL) {
+#pragma unroll
+      for (int r = 0; r < NEZ; r++) {
+        const int q = threadIdx.x + r * C::NT;
+        if (q >= CE) continue;
+        const float ea = ezH[r][0] - ezR[r][0], eb = ezH[r][1] - ezR[r][1];
+        sez[bsel * CE + q] = w3 * ea + w1 * eb;
+      }
+    }
+  };
+  if constexpr (PRL) {
+    ez_load(P0);
+    ez_store(0);
+    __syncthreads();
+  }
+
   // (ub, E) of a cell: (0, 1) in the plain form
   auto bgv = [](const Cell &c) -> float2 {
     if constexpr (BG)
@@ -1758,6 +1851,18 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
 #pragma unroll
       for (int s = 0; s < NSL; s++) {
         if (!(fl[s] & 1u)) continue;
+        if constexpr (PRL) {
+          // u += P(e): coarse column ci = px + 1, row cj = ly / 2 + 1 of the
+          // tile; the farther row is cj + 1 for odd y, cj - 1 for even y
+          const int ly = q[s] / PX, px = q[s] - ly * PX;
+          const int ci = px + 1, cj = (ly >> 1) + 1, cj2 = (ly & 1) ? cj + 1 : cj - 1;
+          const float *za = sez + PK * CE + cj * CXE, *zb = sez + PK * CE + cj2 * CXE;
+          const float em = w3 * za[ci - 1] + w1 * zb[ci - 1];
+          const float e0 = w3 * za[ci] + w1 * zb[ci];
+          const float ep = w3 * za[ci + 1] + w1 * zb[ci + 1];
+          pu[s].x = pu[s].x + (w3 * e0 + w1 * em);
+          pu[s].y = pu[s].y + (w3 * e0 + w1 * ep);
+        }
         const bool odd = (ro[s] ^ PK) != 0;  // red cell is the odd one
         const float ur = odd ? pu[s].y : pu[s].x, ub = odd ? pu[s].x : pu[s].y;
         // the red cell's x is needed only if this pair's red cell is updated
@@ -1782,7 +1887,10 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
         if (inz) sbk[PK * PP + q[s]] = B[s][K];
       }
     }
-    if (k + 1 < nstep) fetch();
+    if (k + 1 < nstep) {
+      fetch();
+      ez_load(p + 1);
+    }
     // 2. red cells of plane m = p - 1 on the grown tile
     {
       const int m = p - 1;
@@ -1826,6 +1934,7 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
         }
       }
     }
+    if (k + 1 < nstep) ez_store((int)(PK ^ 1u));
     __syncthreads();
   };
   for (int k = 0; k < nstep; k += 4) {

@@ -926,19 +926,44 @@ static void launch_rr_tiled(frmg_ctx *ctx, LevelSet<float> &F, LevelSet<float> &
     launch_rr_k<BG, false>(ctx, F, C, active, fpar, cpar, partial, st);
 }
 
-template <bool BG, bool DIR, int TY>
-static void launch_rc_k(LevelSet<float> &s, const int *active, int par, cudaStream_t st) {
+template <bool BG, bool DIR, int TY, bool PRL = false>
+static void launch_rc_k(LevelSet<float> &s, const int *active, int par, cudaStream_t st,
+                        const Grid<float> *coarse = nullptr, int cpar = 0) {
   using RC = RCCfg<TY, BG>;
   constexpr int v = BG ? 1 : 0;
-  const size_t sm = RC::smem();
+  const size_t sm = RC::smem(PRL);
   static bool attr_set = false;
   if (!attr_set) {
-    CK(cudaFuncSetAttribute(k_smooth_rc<BG, DIR, TY>,
+    CK(cudaFuncSetAttribute(k_smooth_rc<BG, DIR, TY, PRL>,
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
-  k_smooth_rc<BG, DIR, TY><<<s.nblk_rc[v], RC::NT, sm, st>>>(s.d, s.d_off_rc[v], s.size(),
-                                                              s.zc_rc[v], active, par);
+  k_smooth_rc<BG, DIR, TY, PRL><<<s.nblk_rc[v], RC::NT, sm, st>>>(
+      s.d, s.d_off_rc[v], s.size(), s.zc_rc[v], active, par, coarse, cpar);
+}
+
+// The first post-smoothing sweep of a level with the prolongation from its
+// coarser level applied to every arriving cell (register-column kernels only).
+template <bool BG>
+static bool can_fuse_prolong(const LevelSet<float> &F, const std::vector<int> *plan) {
+  return F.tiled && plan && !plan->empty() && (*plan)[0] == 1 && F.rc_ty[BG ? 1 : 0] > 0 &&
+         F.rr_tiled && F.nblk_pl > 0;
+}
+template <bool BG>
+static void launch_rc_prolong(frmg_ctx *ctx, LevelSet<float> &F, LevelSet<float> &C,
+                              const int *active, int par, int cpar, cudaStream_t st) {
+  const int ty = F.rc_ty[BG ? 1 : 0];
+  if (F.dirichlet) {
+    if (BG || ty == 8)
+      launch_rc_k<BG, true, 8, true>(F, active, par, st, C.d, cpar);
+    else
+      launch_rc_k<BG, true, 16, true>(F, active, par, st, C.d, cpar);
+  } else {
+    if (BG || ty == 8)
+      launch_rc_k<BG, false, 8, true>(F, active, par, st, C.d, cpar);
+    else
+      launch_rc_k<BG, false, 16, true>(F, active, par, st, C.d, cpar);
+  }
 }
 
 template <bool BG, bool DIR>
@@ -1180,6 +1205,24 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
     CK_LAUNCH(ctx);
   }
   vcycle<T, BG>(ctx, H, l + 1, o, active, st);
+  if constexpr (sizeof(T) == 4) {
+    if (can_fuse_prolong<BG>(F, tiled_ok ? &plan_post : nullptr)) {
+      // prolongation fused into the first post-smoothing sweep (reported as
+      // its own kernel family)
+      {
+        PROF(BG ? (l == 0 ? "smooth_prolong_bg_f32@fine" : "smooth_prolong_bg_f32@coarse")
+                : (l == 0 ? "smooth_prolong_f32@fine" : "smooth_prolong_f32@coarse"));
+        launch_rc_prolong<BG>(ctx, F, C, active, H.par[l], H.par[l + 1], st);
+        CK_LAUNCH(ctx);
+        H.par[l] ^= 1;
+      }
+      std::vector<int> rest(plan_post.begin() + 1, plan_post.end());
+      int left = 0;
+      for (int v : rest) left += v;
+      smooth_set<T, BG>(ctx, F, left, &rest, active, H.par[l], st, l == 0);
+      return;
+    }
+  }
   prolong_level<T>(ctx, H, l, active, st);
   smooth_set<T, BG>(ctx, F, o.post, tiled_ok ? &plan_post : nullptr, active, H.par[l], st,
                     l == 0);
