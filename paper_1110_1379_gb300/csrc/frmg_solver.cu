@@ -867,6 +867,11 @@ struct CycleOpts {
   double crs_rel, crs_abs;
   int crs_maxit, crs_stall;
   int crs_meanfix;  // constant-mode Newton step in periodic coarsest solves
+  // 1: the solve records the finest-level buffer parity of every field that
+  // leaves an inner solve early, so batches may also run odd numbers of
+  // ping-pong passes per cycle (the parity of the grids still iterating then
+  // flips each cycle while a field that left keeps its data where it was)
+  int odd_ok = 0;
 };
 
 // Profiling names: kernel family, precision, fine (depth 0) or coarse level.
@@ -1167,7 +1172,7 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
   auto &C = H.next[l];
   std::vector<int> plan_pre, plan_post;
   const bool tiled_ok = plan_passes(o.pre, o.post, o.tdepth, plan_pre, plan_post) ||
-                        H.lev.size() == 1;
+                        H.lev.size() == 1 || o.odd_ok;
   smooth_set<T, BG>(ctx, F, o.pre, tiled_ok ? &plan_pre : nullptr, active, H.par[l], st, l == 0);
   {
     PROF(pname("resid_restrict", sizeof(T) == 8, l == 0));
@@ -1549,6 +1554,11 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
   int *active = S.get<int>(np);
   std::vector<int> act(np, 1);
   CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.0, 500, 1, 1};
+  // finest-level buffer parity of each field's FP32 data after an inner solve
+  // (a field that left the solve early keeps the parity it left with)
+  std::vector<int> fpar(np, 0);
+  co.odd_ok = cfg.tau_alpha > 0 ? 0 : 1;  // tau reads every field at the shared parity
+  auto fine_u = [&](int pi) { return fpar[pi] ? H.lev[pi][0].u2 : H.lev[pi][0].u; };
   std::vector<double> nr, inr;
   std::vector<double> prev(np, 0.0);
   std::vector<int> grow(np, 0);
@@ -1570,7 +1580,7 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
       if (!act[pi]) continue;
       Grid<double> &G64 = H64.lev[pi][0];
       PROF("update64");
-      k_update64<<<nblocks(G64.ncell), 256, 0, st>>>(G64.u, G64.x, H.cur_u(pi, 0), G64.ncell);
+      k_update64<<<nblocks(G64.ncell), 256, 0, st>>>(G64.u, G64.x, fine_u(pi), G64.ncell);
       CK_LAUNCH(ctx);
     }
   };
@@ -1600,6 +1610,8 @@ static void solve_mixed(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCfg &
       else
         run_cycle(ctx, gr_plain, cfg.use_graph, st, H.par,
                   [&]() { vcycle<float, false>(ctx, H, 0, co, active, st); });
+      for (int pi = 0; pi < np; pi++)
+        if (iact[pi]) fpar[pi] = H.par[0];  // this cycle moved the field's data
       bool go = false;
       for (int pi = 0; pi < np; pi++)
         if (iact[pi]) {
@@ -1891,6 +1903,11 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
   int *active = S.get<int>(np);
   std::vector<int> act(np, 1);
   CycleOpts co{cfg.pre, cfg.post, cfg.tdepth, 1e-3, 0.0, 500, 1, 1};
+  // finest-level buffer parity of each field's FP32 data after an inner solve
+  // (a field that left the solve early keeps the parity it left with)
+  std::vector<int> fpar(np, 0);
+  co.odd_ok = cfg.tau_alpha > 0 ? 0 : 1;  // tau reads every field at the shared parity
+  auto fine_u = [&](int pi) { return fpar[pi] ? H.lev[pi][0].u2 : H.lev[pi][0].u; };
   std::vector<double> nr, inr;
   std::vector<double> prev(np, 0.0);
   std::vector<int> grow(np, 0);
@@ -1911,7 +1928,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
     for (int pi = 0; pi < np; pi++) {
       if (!act[pi]) continue;
       PROF("df_update");
-      k_df_update<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], H.cur_u(pi, 0), ln2h, ln2l);
+      k_df_update<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], fine_u(pi), ln2h, ln2l);
       CK_LAUNCH(ctx);
     }
   };
@@ -1944,6 +1961,8 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
       else
         run_cycle(ctx, gr_plain, cfg.use_graph, st, H.par,
                   [&]() { vcycle<float, false>(ctx, H, 0, co, active, st); });
+      for (int pi = 0; pi < np; pi++)
+        if (iact[pi]) fpar[pi] = H.par[0];  // this cycle moved the field's data
       bool go = false;
       for (int pi = 0; pi < np; pi++)
         if (iact[pi]) {

@@ -65,6 +65,33 @@ def test_small_batch_matches_oracle(C, prec):
             assert stt.vcycles == ref.cycles
 
 
+@pytest.mark.parametrize("pre,post", [(2, 1), (1, 2), (1, 1)])
+@pytest.mark.parametrize("defect_precision", [0, 1])
+def test_batch_with_odd_pass_plans_matches_oracle(C, pre, post, defect_precision):
+    """Odd numbers of ping-pong passes per cycle in a batch whose fields leave
+    the inner solves at different cycles (each keeps its data in the buffer it
+    left with): every field still reaches the oracle's solution."""
+    specs = [dict(n=16, fr0=1e-4, a=0.5, sigma=1.0, box=16.0, seed=31),
+             dict(n=32, fr0=1e-6, a=1.0, sigma=2.5, box=32.0, seed=32),
+             dict(n=24, fr0=1e-5, a=0.8, sigma=1.5, box=24.0, seed=33),
+             dict(n=32, fr0=1e-4, a=0.35, sigma=0.5, box=16.0, seed=34)]
+    rhos = [synth.lognormal_density((s["n"],) * 3, s["seed"], sigma=s["sigma"]) for s in specs]
+    us = [torch.zeros((s["n"],) * 3, dtype=torch.float64, device="cuda") for s in specs]
+    st, stats = C.solve_batch([dev(r) for r in rhos], us, boxes=[s["box"] for s in specs],
+                              avals=[s["a"] for s in specs], fr0s=[s["fr0"] for s in specs],
+                              omega_m=OM, tol=1e-8, prec="mixed", pre=pre, post=post, tiling=1,
+                              defect_precision=defect_precision)
+    assert st == 0
+    cyc = set()
+    for s, r, u, stt in zip(specs, rhos, us, stats):
+        ref = O.solve(r, tol=1e-8, box=s["box"], a=s["a"], omega_m=OM, fr0=s["fr0"])
+        assert stt.res_rms <= 1e-8
+        assert np.abs(host(u) - ref.u).max() <= 1e-6
+        cyc.add(stt.vcycles)
+    if (pre + post) % 2:
+        assert len(cyc) > 1  # the fields did leave at different cycles
+
+
 def test_batch_autotune_returns_a_converging_setting(C):
     specs = [dict(n=16, fr0=1e-4, a=0.5, sigma=1.0, box=16.0, seed=21),
              dict(n=32, fr0=1e-5, a=1.0, sigma=2.0, box=32.0, seed=22),
