@@ -70,9 +70,13 @@ ALG_BYTES = {
 # cells, so it is scaled to the workload's grid).  Valid for the kernels as
 # captured; the second entry names the captured launch.
 TRAFFIC_PER_CELL = {
-    "smooth_f32@fine": ((470.301e6 + 408.505e6) / 384 ** 3,
+    "smooth_f32@fine": ((470.290e6 + 408.163e6) / 384 ** 3,
                         "k_smooth_rc plain form, 64x16 tiles, one 384^3 launch"),
-    "smooth_bg_f32@fine": (1640.735e6 / 384 ** 3, "k_smooth_rb correction form, one 384^3 launch"),
+    "smooth_prolong_f32@fine": ((539.077e6 + 411.576e6) / 384 ** 3,
+                                "k_smooth_rc plain form with the prolongation fused, 64x16 "
+                                "tiles, one 384^3 launch"),
+    "smooth_bg_f32@fine": ((935.178e6 + 426.044e6) / 384 ** 3,
+                           "k_smooth_rc correction form, 64x8 tiles, one 384^3 launch"),
     "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "k_resid_restrict_tiled, one 384^3 launch"),
     "prolong_f32@fine": (678.570e6 / 384 ** 3, "k_prolong_tiled, one 384^3 launch"),
     "df_defect": (2466.320e6 / 384 ** 3, "k_df_defect, one 384^3 launch"),
