@@ -79,7 +79,6 @@ TRAFFIC_PER_CELL = {
                            "k_smooth_rc correction form, 64x8 tiles, one 384^3 launch"),
     "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "k_resid_restrict_tiled, one 384^3 launch"),
     "prolong_f32@fine": (678.570e6 / 384 ** 3, "k_prolong_tiled, one 384^3 launch"),
-    "df_defect": (2466.320e6 / 384 ** 3, "k_df_defect, one 384^3 launch"),
 }
 
 

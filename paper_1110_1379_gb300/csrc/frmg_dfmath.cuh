@@ -107,6 +107,109 @@ __device__ __forceinline__ df df_exp(df u, float ln2h, float ln2l) {
   return {ldexpf(t.h, ni), ldexpf(t.l, ni)};
 }
 
+// ---- the same arithmetic on two independent values at once ----
+// Blackwell's packed FP32 instructions (PTX add/sub/fma .rn.f32x2) round each
+// lane to nearest exactly as the scalar instruction does, so the error-free
+// transformations above hold lane by lane.  A float2 here holds one
+// quantity of two cells (lane x: the first cell, lane y: the second).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "add.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+// Products stay per lane (mul.rn.f32): with the packed multiply, a product
+// followed by packed sums did not reproduce the scalar error-free
+// transformations lane by lane (measured: two_prod's error term and the sums
+// built on it came out different, and less accurate, in kernels; alone, the
+// same sequence agreed), while per-lane products under the packed sums agree
+// bit for bit with the scalar sequence.
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pc, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "mov.b64 pc, {%6, %7};\n\tfma.rn.f32x2 pr, pa, pb, pc;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+
+// a double-float value of two cells: hi and lo lanes
+struct df2 {
+  float2 h, l;
+};
+
+__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+__device__ __forceinline__ df2 fast_two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b);
+  return {s, sub2(b, sub2(s, a))};
+}
+// p + e = a b: the error term as fma(a, b, -p), -p formed as 0 - p
+__device__ __forceinline__ df2 two_prod2(float2 a, float2 b) {
+  const float2 p = mul2(a, b);
+  return {p, fma2(a, b, sub2(splat2(0.0f), p))};
+}
+__device__ __forceinline__ df2 df_add2(df2 a, df2 b) {
+  df2 s = two_sum2(a.h, b.h);
+  s.l = add2(s.l, add2(a.l, b.l));
+  return fast_two_sum2(s.h, s.l);
+}
+__device__ __forceinline__ df2 df_sub2(df2 a, df2 b) {
+  // a + (-b): the two sums of df_add with b's lanes negated, as subtractions
+  const float2 s = sub2(a.h, b.h);
+  const float2 bb = sub2(s, a.h);
+  float2 e = sub2(sub2(a.h, sub2(s, bb)), add2(b.h, bb));
+  e = add2(e, sub2(a.l, b.l));
+  return fast_two_sum2(s, e);
+}
+__device__ __forceinline__ df2 df_add_f2(df2 a, float b) {
+  df2 s = two_sum2(a.h, splat2(b));
+  s.l = add2(s.l, a.l);
+  return fast_two_sum2(s.h, s.l);
+}
+__device__ __forceinline__ df2 df_mul2(df2 a, df2 b) {
+  df2 p = two_prod2(a.h, b.h);
+  p.l = fma2(a.h, b.l, fma2(a.l, b.h, p.l));
+  return fast_two_sum2(p.h, p.l);
+}
+// u_j - u_i of two cells' faces (df_diff lane by lane)
+__device__ __forceinline__ df2 df_diff2(df2 ui, df2 uj) {
+  const float2 s = sub2(uj.h, ui.h);
+  const float2 bb = sub2(s, uj.h);
+  float2 e = sub2(sub2(uj.h, sub2(s, bb)), add2(ui.h, bb));
+  e = add2(e, sub2(uj.l, ui.l));
+  return fast_two_sum2(s, e);
+}
+// df_rsqrt lane by lane: the FP32 estimate per lane, the Newton step packed
+__device__ __forceinline__ df2 df_rsqrt2(df2 a) {
+  const float2 y = make_float2(rsqrtf(a.h.x), rsqrtf(a.h.y));
+  const df2 y2 = two_prod2(y, y);
+  const df2 ay2 = df_mul2(a, y2);
+  // r = 1 - a y^2
+  df2 r = two_sum2(splat2(1.0f), sub2(splat2(0.0f), ay2.h));
+  r.l = sub2(r.l, ay2.l);
+  r = fast_two_sum2(r.h, r.l);
+  // y + (y / 2) r
+  const float2 c = mul2(mul2(splat2(0.5f), y), r.h);
+  const df2 t = two_sum2(c, y);
+  return fast_two_sum2(t.h, t.l);
+}
+
 // n / d for 0 <= n < 2^31, 1 <= d < 2^31, by one widening multiply and a
 // shift (division by an invariant integer, Granlund and Montgomery 1994):
 // with l = ceil(log2 d), p = 31 + l and m = ceil(2^p / d) (< 2^32),

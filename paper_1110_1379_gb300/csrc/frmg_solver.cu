@@ -1798,7 +1798,7 @@ static void dfgrid_setup(DFGrid &g, const int n[3], const Consts &k, const doubl
   g.n1 = n[1];
   g.n2 = n[2];
   g.ncell = (long long)g.n0 * g.n1 * g.n2;
-  g.fd0 = make_fastdiv((unsigned)g.n0);
+  g.fdh = make_fastdiv((unsigned)std::max(1, g.n0 / 2));
   g.fd1 = make_fastdiv((unsigned)g.n1);
   g.bnd = bnd;
   face_offsets(n, g.foff);
@@ -1807,15 +1807,16 @@ static void dfgrid_setup(DFGrid &g, const int n[3], const Consts &k, const doubl
   split_host(k.gamma, g.gah, g.gal);
 }
 
-// Defect kernel for one grid: 32-bit index decomposition below 2^31 cells.
+// Defect kernel for one grid (two cells per thread): 32-bit index
+// decomposition below 2^31 cells.  Its blocks cover 256 cells each.
 static void launch_df_defect(frmg_ctx *ctx, const DFGrid &g, float *r32, float *ub32, float *E32,
                              float *delta, float *x32, double *partial, int base, float ln2h,
                              float ln2l, double *dout, cudaStream_t st) {
   if (g.ncell < (1ll << 31))
-    k_df_defect<false><<<nblocks(g.ncell), 256, 0, st>>>(g, r32, ub32, E32, delta, x32, partial,
+    k_df_defect<false><<<nblocks(g.ncell), 128, 0, st>>>(g, r32, ub32, E32, delta, x32, partial,
                                                          base, ln2h, ln2l, dout);
   else
-    k_df_defect<true><<<nblocks(g.ncell), 256, 0, st>>>(g, r32, ub32, E32, delta, x32, partial,
+    k_df_defect<true><<<nblocks(g.ncell), 128, 0, st>>>(g, r32, ub32, E32, delta, x32, partial,
                                                         base, ln2h, ln2l, dout);
   CK_LAUNCH(ctx);
 }
