@@ -1929,7 +1929,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
     for (int pi = 0; pi < np; pi++) {
       if (!act[pi]) continue;
       PROF("df_update");
-      k_df_update<<<nblocks(D[pi].ncell), 256, 0, st>>>(D[pi], fine_u(pi), ln2h, ln2l);
+      k_df_update<<<nblocks(D[pi].ncell), 128, 0, st>>>(D[pi], fine_u(pi), ln2h, ln2l);
       CK_LAUNCH(ctx);
     }
   };
