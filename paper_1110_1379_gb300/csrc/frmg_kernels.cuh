@@ -784,9 +784,9 @@ __global__ void __launch_bounds__(256)
 }
 
 // Block sum of two values (all threads get the result).
-template <int NT>
-__device__ __forceinline__ void block_sum2(double a, double b, double &ra, double &rb) {
-  __shared__ double sa[NT / 32], sb[NT / 32];
+template <int NT, typename A>
+__device__ __forceinline__ void block_sum2(A a, A b, A &ra, A &rb) {
+  __shared__ A sa[NT / 32], sb[NT / 32];
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
     b += __shfl_down_sync(0xffffffffu, b, o);
@@ -798,13 +798,28 @@ __device__ __forceinline__ void block_sum2(double a, double b, double &ra, doubl
     sb[w] = b;
   }
   __syncthreads();
-  double ta = 0.0, tb = 0.0;
+  A ta = A(0), tb = A(0);
   for (int q = 0; q < NT / 32; q++) {
     ta += sa[q];
     tb += sb[q];
   }
   ra = ta;
   rb = tb;
+}
+
+// Block sum of one value per thread into *out (shared), written by thread 0.
+template <int NT, typename A>
+__device__ __forceinline__ void block_sum1(A a, A *out) {
+  __shared__ A sa[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sa[w] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    A t = A(0);
+    for (int q = 0; q < NT / 32; q++) t += sa[q];
+    *out = t;
+  }
 }
 
 // Coarsest level: one block per grid, Newton-Gauss-Seidel sweeps until
@@ -822,15 +837,34 @@ __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid
                                                  const int *active, int par, int meanfix) {
   int g = blockIdx.x;
   if (g >= ngrid) return;
-  const Grid<T> G = view(grids, g, par);
+  Grid<T> G = view(grids, g, par);
   if (!grid_active(active, G.field)) return;
-  __shared__ double red_s, red_m;
+  // sums in the precision of the grid: FP64 arithmetic runs at 1/64 of the
+  // FP32 rate here, and the FP32 levels' stopping test needs no more
+  using A = typename std::conditional<sizeof(T) == 4, float, double>::type;
+  __shared__ A red_s;
   __shared__ int stop;
   const long long n = G.ncell;
+  // a grid of up to 16 KB per array is relaxed in shared memory (u and its
+  // x cache copied in and back; the same updates in the same order)
+  constexpr int CAPN = 16384 / (int)sizeof(T);
+  __shared__ T cs_u[CAPN], cs_x[CAPN];
+  T *const gu = G.u;
+  T *const gx = G.x;
+  const bool local = n <= CAPN;
+  if (local) {
+    for (long long t = threadIdx.x; t < n; t += NT) {
+      cs_u[t] = gu[t];
+      cs_x[t] = gx[t];
+    }
+    __syncthreads();
+    G.u = cs_u;
+    G.x = cs_x;
+  }
   const int hx = G.n0 >> 1;
   const long long nh = (long long)hx * G.n1 * G.n2;
   const bool shift = meanfix && G.bnd == nullptr;
-  double thr = 0.0, prev = 0.0;
+  A thr = A(0), prev = A(0);
   for (int it = -1; it < maxit; it++) {
     if (it >= 0) {
       for (int colour = 0; colour < 2; colour++) {
@@ -842,21 +876,21 @@ __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid
         __syncthreads();
       }
       if (shift) {
-        double S = 0.0, D = 0.0;
+        A S = A(0), D = A(0);
         for (long long t = threadIdx.x; t < n; t += NT) {
           int i, j, k;
           cell_ijk(G, t, i, j, k);
           T N, dN;
           cell_eval<T, BG>(G, i, j, k, t, N, dN);
-          S += (double)(N - rhs_at(G, t));
+          S += (A)(N - rhs_at(G, t));
           const T Ei = BG ? (T)G.Ebg[t] : T(1);
           const T F = BG ? m_rsqrt(Ei) : T(1);
-          D += 0.5 * (double)G.beta * (double)(F * m_rsqrt(T(1) + G.x[t]));
+          D += A(0.5) * (A)G.beta * (A)(F * m_rsqrt(T(1) + G.x[t]));
         }
-        double St, Dt;
-        block_sum2<NT>(S, D, St, Dt);
-        double c = Dt > 0.0 ? St / Dt : 0.0;
-        const double cap = (double)G.cap;
+        A St, Dt;
+        block_sum2<NT, A>(S, D, St, Dt);
+        A c = Dt > A(0) ? St / Dt : A(0);
+        const A cap = (A)G.cap;
         c = c > cap ? cap : (c < -cap ? -cap : c);
         __syncthreads();
         for (long long t = threadIdx.x; t < n; t += NT) {
@@ -867,22 +901,22 @@ __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid
         __syncthreads();
       }
     }
-    double s = 0.0;
+    A s = A(0);
     for (long long t = threadIdx.x; t < n; t += NT) {
       int i, j, k;
       cell_ijk(G, t, i, j, k);
       T N, dN;
       cell_eval<T, BG>(G, i, j, k, t, N, dN);
-      double d = (double)(N - rhs_at(G, t));
+      const A d = (A)(N - rhs_at(G, t));
       s += d * d;
     }
-    block_reduce2<NT>(s, 0.0, &red_s, &red_m);
+    block_sum1<NT, A>(s, &red_s);
     __syncthreads();
     if (threadIdx.x == 0) {
-      double rms = sqrt(red_s / (double)n);
+      const A rms = sqrt(red_s / (A)n);
       int st = 0;
       if (it < 0) {
-        thr = fmax(rel * rms, abs_floor);
+        thr = fmax((A)rel * rms, (A)abs_floor);
         if (rms <= thr) st = 1;
       } else {
         if (rms <= thr) st = 1;
@@ -893,6 +927,13 @@ __global__ void __launch_bounds__(NT) k_coarsest(const Grid<T> *grids, int ngrid
     }
     __syncthreads();
     if (stop) break;
+  }
+  if (local) {
+    __syncthreads();
+    for (long long t = threadIdx.x; t < n; t += NT) {
+      gu[t] = cs_u[t];
+      gx[t] = cs_x[t];
+    }
   }
 }
 
