@@ -2152,6 +2152,19 @@ static bool is_pinned_host(const void *p) {
   return at.type == cudaMemoryTypeHost;
 }
 
+// Device address of page-locked host memory, read by a kernel across the
+// host link (null if p is not page-locked host memory).
+static const double *mapped_host(const double *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  return static_cast<const double *>(at.devicePointer);
+}
+
 struct Staged {
   void *dev = nullptr;
   const void *host_src = nullptr;
@@ -2552,12 +2565,15 @@ static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], d
     Scope S(ctx);
     std::vector<Staged> back;
     long long nc = (long long)dims[0] * dims[1] * dims[2];
-    const double *drho = stage(S, back, density, nc, true, false, st);
-    double *du = stage_u(S, back, u, nc, o, st);
     // the mixed double-float solve of a zero start validates rho in its first
     // pass; every other solve validates it here
     const bool defer = !o.initial_guess && o.prec == FR_MIXED && o.defect_precision == 0 &&
                        fixed <= 0;
+    // that first pass is the only reader of rho: page-locked host density is
+    // read there across the host link instead of being copied in first
+    const double *drho = defer ? mapped_host(density) : nullptr;
+    if (!drho) drho = stage(S, back, density, nc, true, false, st);
+    double *du = stage_u(S, back, u, nc, o, st);
     if (!defer) validate_density(ctx, S, drho, nc, o.allow_negative_density, st);
     Problem p;
     memset(&p, 0, sizeof(p));
