@@ -89,11 +89,21 @@ __device__ __forceinline__ double m_exp(double v) { return exp(v); }
 // the correctly rounded-to-1-ulp exponential minus one otherwise (strongly
 // screened cells reach |u| ~ 10, where the SFU approximation's error of a few
 // ulp per unit of |u| would set the FP32 residual floor).
+// Every FP32 operation of the shared operator code is written out as an
+// explicit rounding (fmaf, __fadd_rn, __fmul_rn, ...), so that no kernel's
+// compiler contraction can change it: the scalar and the packed (two cells per
+// instruction, below) evaluations are then the same bit for bit.
+__device__ __forceinline__ float m_expm1_taylor(float d) {
+  float p = fmaf(d, 1.0f / 720.0f, 1.0f / 120.0f);
+  p = fmaf(d, p, 1.0f / 24.0f);
+  p = fmaf(d, p, 1.0f / 6.0f);
+  p = fmaf(d, p, 0.5f);
+  p = fmaf(d, p, 1.0f);
+  return __fmul_rn(d, p);
+}
 __device__ __forceinline__ float m_expm1(float d) {
-  if (fabsf(d) < 0.0625f)
-    return d * (1.0f + d * (0.5f + d * (1.0f / 6.0f + d * (1.0f / 24.0f +
-                                       d * (1.0f / 120.0f + d * (1.0f / 720.0f))))));
-  return expf(d) - 1.0f;
+  if (fabsf(d) < 0.0625f) return m_expm1_taylor(d);
+  return __fsub_rn(expf(d), 1.0f);
 }
 __device__ __forceinline__ double m_expm1(double v) { return expm1(v); }
 __device__ __forceinline__ float m_sqrt(float v) { return sqrtf(v); }
@@ -233,10 +243,10 @@ struct OpAcc<float, false> {
   __device__ __forceinline__ OpAcc(float d, float E, float x, float B, float ub)
       : di(d), Ei(E), xi(x), Bi(B), ubi(ub) {}
   __device__ __forceinline__ void reg(float dj, float xj, float, float) {
-    const float dd = dj - di;
-    S1 += dd;
+    const float dd = __fsub_rn(dj, di);
+    S1 = __fadd_rn(S1, dd);
     S2 = fmaf(xj, dd, S2);
-    S3 += xj;
+    S3 = __fadd_rn(S3, xj);
     n++;
   }
   __device__ __forceinline__ void ghost(float ubf) {
@@ -244,8 +254,9 @@ struct OpAcc<float, false> {
   }
   __device__ __forceinline__ void done(float &a, float &da) const {
     const float nf = (float)n;
-    a = fmaf(Bi + 1.0f, S1, S2) + ga;
-    da = fmaf(Bi, S1, -nf * (Bi + 1.0f)) - S3 + gd;
+    const float b1 = __fadd_rn(Bi, 1.0f);
+    a = __fadd_rn(fmaf(b1, S1, S2), ga);
+    da = __fadd_rn(__fsub_rn(fmaf(Bi, S1, __fmul_rn(-nf, b1)), S3), gd);
   }
 };
 
@@ -280,17 +291,79 @@ __device__ __forceinline__ float sfu_rsqrt(float v) {
 
 __device__ __forceinline__ void finish_op(float xi, float Ei, float acc, float dacc, float ah,
                                           float beta, bool bg, float &N, float &dN) {
-  float B1 = 1.0f + xi;
-  float rs = sfu_rsqrt(B1);  // e^{-d/2}
-  float s = B1 * rs;         // e^{d/2}
-  float y = -xi * sfu_rcp(B1 + s);
-  float F = bg ? sfu_rsqrt(Ei) : 1.0f;
-  N = ah * acc + beta * F * y;
-  dN = ah * dacc - 0.5f * beta * F * rs;
+  const float B1 = __fadd_rn(1.0f, xi);
+  const float rs = sfu_rsqrt(B1);  // e^{-d/2}
+  const float s = __fmul_rn(B1, rs);  // e^{d/2}
+  const float y = __fmul_rn(-xi, sfu_rcp(__fadd_rn(B1, s)));
+  const float bF = bg ? __fmul_rn(beta, sfu_rsqrt(Ei)) : beta;  // beta F
+  N = fmaf(ah, acc, __fmul_rn(bF, y));
+  dN = fmaf(ah, dacc, -__fmul_rn(__fmul_rn(0.5f, bF), rs));
 }
 
 __device__ __forceinline__ double newton_step(double r, double dN) { return -r / dN; }
-__device__ __forceinline__ float newton_step(float r, float dN) { return -r * sfu_rcp(dN); }
+__device__ __forceinline__ float newton_step(float r, float dN) {
+  return __fmul_rn(-r, sfu_rcp(dN));
+}
+// relaxed Newton step w (N - f) / -dN of a cell
+__device__ __forceinline__ double newton_du(double N, double f, double dN, double w) {
+  return w * newton_step(N - f, dN);
+}
+__device__ __forceinline__ float newton_du(float N, float f, float dN, float w) {
+  return __fmul_rn(w, newton_step(__fsub_rn(N, f), dN));
+}
+
+// ---- packed FP32 pairs (add2, sub2, fma2, mul2, splat2 of frmg_dfmath.cuh)
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// m_expm1 of two values: the Taylor branch packed, the exponential branch per lane
+__device__ __forceinline__ float2 m_expm1_2(float2 d) {
+  float2 p = fma2(d, splat2(1.0f / 720.0f), splat2(1.0f / 120.0f));
+  p = fma2(d, p, splat2(1.0f / 24.0f));
+  p = fma2(d, p, splat2(1.0f / 6.0f));
+  p = fma2(d, p, splat2(0.5f));
+  p = fma2(d, p, splat2(1.0f));
+  float2 r = mul2(d, p);
+  if (!(fabsf(d.x) < 0.0625f)) r.x = __fsub_rn(expf(d.x), 1.0f);
+  if (!(fabsf(d.y) < 0.0625f)) r.y = __fsub_rn(expf(d.y), 1.0f);
+  return r;
+}
+
+// The plain-form Newton update of two cells at once, operation for operation
+// the scalar OpAcc<float, false> (six regular faces), finish_op and newton_du:
+// own (u, x), right-hand side f, neighbour u and x in the face order -x, +x,
+// -y, +y, -z, +z; returns the two new u.
+__device__ __forceinline__ float2 newton2_plain(float2 di, float2 xi, float2 fi, const float2 *nu,
+                                                const float2 *nx, float ah, float beta, float cap,
+                                                float relax) {
+  const float2 Bi = add2(splat2(1.0f), xi);
+  float2 S1 = sub2(nu[0], di), S2, S3 = nx[0];
+  S2 = mul2(nx[0], S1);  // fmaf(x, dd, 0) rounds as the product
+#pragma unroll
+  for (int f = 1; f < 6; f++) {
+    const float2 dd = sub2(nu[f], di);
+    S1 = add2(S1, dd);
+    S2 = fma2(nx[f], dd, S2);
+    S3 = add2(S3, nx[f]);
+  }
+  const float2 b1 = add2(Bi, splat2(1.0f));
+  const float2 acc = fma2(b1, S1, S2);
+  const float2 dacc = sub2(fma2(Bi, S1, mul2(splat2(-6.0f), b1)), S3);
+  // finish_op
+  const float2 B1 = add2(splat2(1.0f), xi);
+  const float2 rs = make_float2(sfu_rsqrt(B1.x), sfu_rsqrt(B1.y));
+  const float2 sv = mul2(B1, rs);
+  const float2 den = add2(B1, sv);
+  const float2 y = mul2(neg2(xi), make_float2(sfu_rcp(den.x), sfu_rcp(den.y)));
+  const float2 N = fma2(splat2(ah), acc, mul2(splat2(beta), y));
+  const float2 dN = fma2(splat2(ah), dacc, neg2(mul2(splat2(0.5f * beta), rs)));
+  // newton_du, clamp, update
+  const float2 r = sub2(N, fi);
+  const float2 q = make_float2(sfu_rcp(dN.x), sfu_rcp(dN.y));
+  float2 du = mul2(splat2(relax), mul2(neg2(r), q));
+  du.x = fminf(fmaxf(du.x, -cap), cap);
+  du.y = fminf(fmaxf(du.y, -cap), cap);
+  return add2(di, du);
+}
 
 // A_i (or N_i) and its derivative at cell (i,j,k) from global memory.
 template <typename T, bool BG>
@@ -343,7 +416,7 @@ __device__ __forceinline__ void ngs_update(const Grid<T> &G, int i, int j, int k
   long long c = idx3(G, i, j, k);
   T N, dN;
   cell_eval<T, BG>(G, i, j, k, c, N, dN);
-  T du = G.relax * newton_step(N - rhs_at(G, c), dN);
+  T du = newton_du(N, rhs_at(G, c), dN, G.relax);
   du = du > G.cap ? G.cap : (du < -G.cap ? -G.cap : du);
   T unew = G.u[c] + du;
   G.u[c] = unew;
@@ -1157,7 +1230,7 @@ __global__ void __launch_bounds__(TileCfg<S, TX, TY>::NT)
       A.done(acc, dacc);
       float N, dN;
       finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-      float du = relax * newton_step(N - sf[o], dN);
+      float du = newton_du(N, sf[o], dN, relax);
       du = fminf(fmaxf(du, -cap), cap);
       const float dn = di + du;
       sd[o] = dn;
@@ -1435,7 +1508,7 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
     A.done(acc, dacc);
     float N, dN;
     finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-    float du = relax * newton_step(N - c.f, dN);
+    float du = newton_du(N, c.f, dN, relax);
     du = fminf(fmaxf(du, -cap), cap);
     const float dn = di + du;
     return make_float2(dn, m_expm1(dn));
@@ -1868,11 +1941,19 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
     float acc, dacc, N, dN;
     A.done(acc, dacc);
     finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-    float du = relax * newton_step(N - fi, dN);
+    float du = newton_du(N, fi, dN, relax);
     du = fminf(fmaxf(du, -cap), cap);
     return di + du;
   };
   auto sel = [](bool c, Cell a, Cell b) { return c ? a : b; };
+  // the plain form's two interior slots are updated as packed pairs
+  constexpr bool PACK = !DIR && !BG && NI == 2;
+  auto with_u2 = [](const Cell &c, float u, float x) -> Cell {
+    Cell r = c;
+    r.x = u;
+    r.y = x;
+    return r;
+  };
   // cell of value u (x recomputed) with the background of cell c
   auto with_u = [&](const Cell &c, float u) -> Cell {
     Cell r = c;
@@ -1936,8 +2017,35 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
     {
       const int m = p - 1;
       if (m >= Z0 - 1 && m <= Z1 && (!DIR || (m >= 0 && m < n2))) {
+        if constexpr (PACK) {
+          // the two interior slots (same row parity) in packed pairs
+          const bool odd = (ro[0] ^ PK1) != 0;
+          float2 nu[6], nxv[6];
+          float2 di, xi, fi;
 #pragma unroll
-        for (int s = 0; s < NSL; s++) {
+          for (int s = 0; s < 2; s++) {
+            const Cell *bk = sbk + PK1 * PP + q[s];
+            const Cell nx = bk[odd ? 1 : -1];
+            const Cell in = B[s][K1];
+            const Cell c6[6] = {odd ? in : nx, odd ? nx : in, bk[-PX], bk[PX], B[s][K2], B[s][K]};
+#pragma unroll
+            for (int f = 0; f < 6; f++) {
+              (s ? nu[f].y : nu[f].x) = c6[f].x;
+              (s ? nxv[f].y : nxv[f].x) = c6[f].y;
+            }
+            (s ? di.y : di.x) = R[s][K1].x;
+            (s ? xi.y : xi.x) = R[s][K1].y;
+            (s ? fi.y : fi.x) = FR[s][K1];
+          }
+          const float2 un = newton2_plain(di, xi, fi, nu, nxv, ah, beta, cap, relax);
+          const float2 xn = m_expm1_2(un);
+          R[0][K1] = with_u2(R[0][K1], un.x, xn.x);
+          R[1][K1] = with_u2(R[1][K1], un.y, xn.y);
+          srd[PK1 * PP + q[0]] = R[0][K1];
+          srd[PK1 * PP + q[1]] = R[1][K1];
+        }
+#pragma unroll
+        for (int s = PACK ? 2 : 0; s < NSL; s++) {
           const bool odd = (ro[s] ^ PK1) != 0;
           if (!((s < NI && !DIR) || (fl[s] & (odd ? 8u : 4u)))) continue;
           const Cell *bk = sbk + PK1 * PP + q[s];
@@ -1955,16 +2063,42 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
     {
       const int m = p - 2;
       if (m >= Z0 && m < Z1 && (!DIR || (m >= 0 && m < n2))) {
+        float2 unp = make_float2(0.f, 0.f);
+        if constexpr (PACK) {
+          const bool odd = (ro[0] ^ PK2) == 0;  // black cell is the odd one
+          float2 nu[6], nxv[6];
+          float2 di, xi, fi;
+#pragma unroll
+          for (int s = 0; s < 2; s++) {
+            const Cell *rd = srd + PK2 * PP + q[s];
+            const Cell nx = rd[odd ? 1 : -1];
+            const Cell in = R[s][K2];
+            const Cell c6[6] = {odd ? in : nx, odd ? nx : in, rd[-PX], rd[PX], R[s][K3], R[s][K1]};
+#pragma unroll
+            for (int f = 0; f < 6; f++) {
+              (s ? nu[f].y : nu[f].x) = c6[f].x;
+              (s ? nxv[f].y : nxv[f].x) = c6[f].y;
+            }
+            (s ? di.y : di.x) = B[s][K2].x;
+            (s ? xi.y : xi.x) = B[s][K2].y;
+            (s ? fi.y : fi.x) = FB[s][K2];
+          }
+          unp = newton2_plain(di, xi, fi, nu, nxv, ah, beta, cap, relax);
+        }
 #pragma unroll
         for (int s = 0; s < NI; s++) {
           if (DIR && !(fl[s] & 1u)) continue;
           const bool odd = (ro[s] ^ PK2) == 0;  // black cell is the odd one
-          const Cell *rd = srd + PK2 * PP + q[s];
-          const Cell ym = rd[-PX], yp = rd[PX];
-          const Cell nx = rd[odd ? 1 : -1];
-          const float un = newton(B[s][K2], FB[s][K2], sel(odd, R[s][K2], nx),
-                                  sel(odd, nx, R[s][K2]), ym, yp, R[s][K3], R[s][K1],
-                                  gxe[s] + (odd ? 1 : 0), gyv[s], m);
+          float un;
+          if constexpr (PACK) {
+            un = s ? unp.y : unp.x;
+          } else {
+            const Cell *rd = srd + PK2 * PP + q[s];
+            const Cell ym = rd[-PX], yp = rd[PX];
+            const Cell nx = rd[odd ? 1 : -1];
+            un = newton(B[s][K2], FB[s][K2], sel(odd, R[s][K2], nx), sel(odd, nx, R[s][K2]), ym,
+                        yp, R[s][K3], R[s][K1], gxe[s] + (odd ? 1 : 0), gyv[s], m);
+          }
           B[s][K2] = with_u(B[s][K2], un);
           if (fl[s] & 2u) {
             const Cell e = sel(odd, R[s][K2], B[s][K2]), o = sel(odd, B[s][K2], R[s][K2]);
