@@ -465,8 +465,8 @@ def run_secondary(args):
                     tuned={**lopts, "candidates_s": ltimes})
     elif args.workload == "cic128":
         n = 128
-        pos = torch.from_numpy(synth.zeldovich_positions(n, 2000,
-                                                         synth.ZELDOVICH_AMPLITUDE_128)).cuda()
+        pos = torch.from_numpy(synth.zeldovich_positions(
+            n, 2000, synth.ZELDOVICH_AMPLITUDE_128, slope=synth.ZELDOVICH_SLOPE_128)).cuda()
         rho = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
         u = torch.zeros_like(rho)
         out = {}

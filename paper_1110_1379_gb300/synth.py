@@ -95,11 +95,13 @@ def zeldovich_positions(n, seed, amplitude, slope=-1.5):
     return pos
 
 
-# Zel'dovich amplitude for the 128^3, seed-2000 particle set of the CIC workload:
-# the value maximising max(rho~ - 1) (= 43.7) of its CIC density, written by
-# oracle/calibrate_zeldovich.py (a one-particle-per-cell Zel'dovich field with
-# this spectrum saturates below the contrast of ~100 the workload names).
-ZELDOVICH_AMPLITUDE_128 = 52.5
+# Zel'dovich spectrum slope and amplitude for the 128^3, seed-2000 particle set
+# of the CIC workload, written by oracle/calibrate_zeldovich.py: the first
+# slope of -1.5, -2, -2.5, -3 whose best amplitude reaches the contrast of ~100
+# the workload names (max(rho~ - 1) = 101.0 of the CIC density; with slope
+# -1.5 a one-particle-per-cell field saturates at 43.7).
+ZELDOVICH_SLOPE_128 = -2.5
+ZELDOVICH_AMPLITUDE_128 = 60.0
 
 
 def uniform_positions(np_, seed):

@@ -36,9 +36,11 @@ def test_assignment_matches_oracle(C, scheme, shape):
 
 
 def test_tsc_full_zeldovich_lattice(C):
-    """The 128^3 CIC workload's particles (Zel'dovich, amplitude 52.5) with TSC."""
+    """The 128^3 CIC workload's particles (Zel'dovich, slope -2.5, amplitude
+    60: max(rho~ - 1) of about 100) with TSC."""
     n = 128
-    pos = synth.zeldovich_positions(n, 2000, amplitude=synth.ZELDOVICH_AMPLITUDE_128)
+    pos = synth.zeldovich_positions(n, 2000, amplitude=synth.ZELDOVICH_AMPLITUDE_128,
+                                    slope=synth.ZELDOVICH_SLOPE_128)
     out = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
     C.tsc(dev(pos), out)
     ref = PM.assign(pos, (n, n, n), "tsc")
