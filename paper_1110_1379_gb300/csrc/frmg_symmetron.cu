@@ -171,8 +171,11 @@ __global__ void __launch_bounds__(kNT) k_sy_smooth(SLevel<T> L, int colour) {
 // Block partials (sum of squares, max |v|) into part[2 blockIdx.x ..].
 template <typename T>
 __device__ __forceinline__ void sy_block_norms(T v2, T vmax, double *part) {
-  __shared__ double ss[kNT / 32], sm[kNT / 32];
-  double s = (double)v2, m = (double)vmax;
+  // reduced in the values' own precision (FP64 arithmetic runs at 1/64 of the
+  // FP32 rate here; FP32 sums are ample for a stopping test), one FP64 pair
+  // written per block
+  __shared__ T ss[kNT / 32], sm[kNT / 32];
+  T s = v2, m = vmax;
   for (int o = 16; o > 0; o >>= 1) {
     s += __shfl_down_sync(0xffffffffu, s, o);
     m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -184,13 +187,13 @@ __device__ __forceinline__ void sy_block_norms(T v2, T vmax, double *part) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double ts = 0.0, tm = 0.0;
+    T ts = T(0), tm = T(0);
     for (int q = 0; q < kNT / 32; q++) {
       ts += ss[q];
       tm = fmax(tm, sm[q]);
     }
-    part[2 * blockIdx.x] = ts;
-    part[2 * blockIdx.x + 1] = tm;
+    part[2 * blockIdx.x] = (double)ts;
+    part[2 * blockIdx.x + 1] = (double)tm;
   }
 }
 
@@ -571,7 +574,7 @@ __global__ void __launch_bounds__(kNT) k_sy_defect_df(SLevel<float> L, const flo
                                                       float *delta, double *part) {
   using frmg::df;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double v = 0.0;
+  float v = 0.0f;
   if (t < L.nc) {
     int i, j, k;
     sy_ijk(L, t, i, j, k);
@@ -599,12 +602,12 @@ __global__ void __launch_bounds__(kNT) k_sy_defect_df(SLevel<float> L, const flo
     const df m = frmg::df_add_f(frmg::df_mul({r2.x, r2.y}, {sh, sl}), -1.0f);  // s rho - 1
     const df loc = frmg::df_mul(ci, frmg::df_add(m, frmg::df_mul(ci, ci)));  // chi (m + chi^2)
     const df d = frmg::df_sub(frmg::df_mul(lap, {Ah, Al}), loc);
-    v = (double)d.h + (double)d.l;
+    v = d.h + d.l;
     g[t] = c2.x;
     f[t] = -d.h;
     delta[t] = 0.0f;
   }
-  sy_block_norms<double>(v * v, fabs(v), part);
+  sy_block_norms<float>(v * v, fabsf(v), part);
 }
 
 // chi += delta in double-float
