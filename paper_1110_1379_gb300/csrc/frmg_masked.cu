@@ -295,17 +295,19 @@ __global__ void __launch_bounds__(kNT) k_msmooth(MLevelT<T, BG> L, int colour, T
 template <typename T, bool BG>
 __global__ void __launch_bounds__(kNT) k_mresid(MLevelT<T, BG> L, double *partial) {
   const long long t = (long long)blockIdx.x * kNT + threadIdx.x;
-  double s = 0.0, mx = 0.0;
+  // block sums in the level's precision (FP64 arithmetic runs at 1/64 of the
+  // FP32 rate here), one FP64 pair written per block
+  T s = T(0), mx = T(0);
   if (t < L.na) {
     const long long c = L.act[t];
     T N, dN;
     m_cell(L, c, N, dN);
     const T d = N - L.f[c];
     L.d[c] = d;
-    s = (double)d * (double)d;
-    mx = fabs((double)d);
+    s = d * d;
+    mx = fabs(d);
   }
-  __shared__ double ss[kNT / 32], sm[kNT / 32];
+  __shared__ T ss[kNT / 32], sm[kNT / 32];
   for (int o = 16; o > 0; o >>= 1) {
     s += __shfl_down_sync(0xffffffffu, s, o);
     mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
@@ -316,13 +318,13 @@ __global__ void __launch_bounds__(kNT) k_mresid(MLevelT<T, BG> L, double *partia
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
+    T a = T(0), b = T(0);
     for (int w = 0; w < kNT / 32; w++) {
       a += ss[w];
       b = fmax(b, sm[w]);
     }
-    partial[2 * blockIdx.x] = a;
-    partial[2 * blockIdx.x + 1] = b;
+    partial[2 * blockIdx.x] = (double)a;
+    partial[2 * blockIdx.x + 1] = (double)b;
   }
 }
 
@@ -420,31 +422,32 @@ constexpr int kCoNT = 1024;
 template <typename T, bool BG>
 __global__ void __launch_bounds__(kCoNT) k_mcoarsest(MLevelT<T, BG> L, long long nact, double tol,
                                                      T cap, T relax) {
-  __shared__ double red[kCoNT / 32];
-  __shared__ double tot;
-  auto rms = [&]() -> double {
-    double s = 0.0;
+  // the rms in the level's precision (FP64 arithmetic runs at 1/64 rate)
+  __shared__ T red[kCoNT / 32];
+  __shared__ T tot;
+  auto rms = [&]() -> T {
+    T s = T(0);
     for (long long c = threadIdx.x; c < L.ncell; c += kCoNT) {
       if (!(L.m[c] > 0.0)) continue;
       T N, dN;
       m_cell(L, c, N, dN);
-      const double d = (double)(N - L.f[c]);
+      const T d = N - L.f[c];
       s += d * d;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0.0;
+      T t = T(0);
       for (int w = 0; w < kCoNT / 32; w++) t += red[w];
-      tot = sqrt(t / (double)(nact > 0 ? nact : 1));
+      tot = sqrt(t / (T)(nact > 0 ? nact : 1));
     }
     __syncthreads();
-    const double r = tot;
+    const T r = tot;
     __syncthreads();
     return r;
   };
-  const double thr = fmax(1e-3 * rms(), 0.1 * tol);
+  const T thr = fmax(T(1e-3) * rms(), (T)(0.1 * tol));
   for (int it = 0; it < 500; it++) {
     for (int colour = 0; colour < 2; colour++) {
       for (long long c = threadIdx.x; c < L.ncell; c += kCoNT) {
