@@ -260,6 +260,43 @@ struct OpAcc<float, false> {
   }
 };
 
+// The FP32 correction form regroups its face sum the same way: with
+// P = E x (so B = E + P) and g_j = ub_j - ub_i,
+//   acc  = sum (P_i + P_j) g_j + (B_i + B_j)(d_j - d_i)
+//        = P_i G1 + G2 + B_i S1 + S2,
+//   dacc = sum B_i (g_j + d_j - d_i) - (B_i + B_j) = B_i (G1 + S1) - n B_i - S3,
+//   G1 = sum g_j, G2 = sum P_j g_j, S1 = sum (d_j - d_i), S2 = sum B_j (d_j - d_i),
+//   S3 = sum B_j,
+// nine operations per face instead of about twelve, every rounding explicit.
+template <>
+struct OpAcc<float, true> {
+  float di, Ei, xi, Bi, ubi;
+  float G1 = 0.f, G2 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f, ga = 0.f, gd = 0.f;
+  int n = 0;
+  __device__ __forceinline__ OpAcc(float d, float E, float x, float B, float ub)
+      : di(d), Ei(E), xi(x), Bi(B), ubi(ub) {}
+  __device__ __forceinline__ void reg(float dj, float xj, float ubj, float Ej) {
+    const float Pj = __fmul_rn(Ej, xj);
+    const float Bj = __fadd_rn(Ej, Pj);
+    const float dd = __fsub_rn(dj, di), g = __fsub_rn(ubj, ubi);
+    G1 = __fadd_rn(G1, g);
+    G2 = fmaf(Pj, g, G2);
+    S1 = __fadd_rn(S1, dd);
+    S2 = fmaf(Bj, dd, S2);
+    S3 = __fadd_rn(S3, Bj);
+    n++;
+  }
+  __device__ __forceinline__ void ghost(float ubf) {
+    face_ghost<float, true>(ubf, di, Ei, xi, Bi, ubi, ga, gd);
+  }
+  __device__ __forceinline__ void done(float &a, float &da) const {
+    const float nf = (float)n;
+    const float Pi = __fmul_rn(Ei, xi);
+    a = __fadd_rn(__fadd_rn(fmaf(Pi, G1, G2), fmaf(Bi, S1, S2)), ga);
+    da = __fadd_rn(__fsub_rn(fmaf(Bi, __fadd_rn(G1, S1), __fmul_rn(-nf, Bi)), S3), gd);
+  }
+};
+
 // Mass term and final assembly:  N = (alpha/2) acc + beta F (e^{-d/2} - 1),
 // dN = (alpha/2) dacc - (beta/2) F e^{-d/2},  F = e^{-ub/2}.
 // FP64 uses IEEE sqrt and division; FP32 uses the SFU reciprocal square root
