@@ -564,50 +564,54 @@ __global__ void __launch_bounds__(kNT) k_sy_join(const float2 *p, double *v, lon
   if (t < n) v[t] = (double)p[t].x + (double)p[t].y;
 }
 
-// Defect d = L(chi) in double-float from the pairs of chi and rho, and the
-// set-up of the outer step's FP32 correction problem in the same pass:
-// background g = hi(chi), right-hand side f = -hi(d), delta = 0; norm
-// partials of d.  Ah + Al = A and sh + sl = s as pairs (host-split).
+// Defect of chi in double-float, two cells (an x-pair; every grid has an even
+// n0) per thread on packed FP32 pairs (frmg_dfmath.cuh: add/sub/fma .f32x2,
+// products per lane), and the set-up of the FP32 correction problem of the
+// next outer step: g = hi(chi), f = -hi(d), delta = 0.  The six face
+// differences are summed in the face order -x, +x, -y, +y, -z, +z, then
+// d = A lap - chi (s rho - 1 + chi^2).  Block norms (FP32) of 2 kNT cells.
 __global__ void __launch_bounds__(kNT) k_sy_defect_df(SLevel<float> L, const float2 *chi,
                                                       const float2 *rho, float Ah, float Al,
                                                       float sh, float sl, float *g, float *f,
                                                       float *delta, double *part) {
-  using frmg::df;
+  using frmg::df2;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  float v = 0.0f;
-  if (t < L.nc) {
+  float s2 = 0.0f, mx = 0.0f;
+  if (t < (L.nc >> 1)) {
+    const long long c = 2 * t;
     int i, j, k;
-    sy_ijk(L, t, i, j, k);
-    const long long sx = 1, sy = L.n0, sz = (long long)L.n0 * L.n1;
-    const long long xm = i > 0 ? t - sx : t + (L.n0 - 1) * sx;
-    const long long xp = i < L.n0 - 1 ? t + sx : t - (L.n0 - 1) * sx;
-    const long long ym = j > 0 ? t - sy : t + (L.n1 - 1) * sy;
-    const long long yp = j < L.n1 - 1 ? t + sy : t - (L.n1 - 1) * sy;
-    const long long zm = k > 0 ? t - sz : t + (L.n2 - 1) * sz;
-    const long long zp = k < L.n2 - 1 ? t + sz : t - (L.n2 - 1) * sz;
-    const float2 c2 = chi[t];
-    const df ci = {c2.x, c2.y};
-    auto diff = [&](long long q) {
-      const float2 n = chi[q];
-      return frmg::df_sub({n.x, n.y}, ci);
+    sy_ijk(L, c, i, j, k);
+    const long long sy = L.n0, sz = (long long)L.n0 * L.n1;
+    const float4 *C4 = reinterpret_cast<const float4 *>(chi);
+    const float4 cv = C4[t];
+    const df2 ci = {make_float2(cv.x, cv.z), make_float2(cv.y, cv.w)};
+    auto pair = [&](long long cj) {  // the neighbouring pair starting at cell cj (even)
+      const float4 v = C4[cj >> 1];
+      return df2{make_float2(v.x, v.z), make_float2(v.y, v.w)};
     };
-    // sum of the six face differences, in the face order of the other kernels
-    df lap = diff(xm);
-    lap = frmg::df_add(lap, diff(xp));
-    lap = frmg::df_add(lap, diff(ym));
-    lap = frmg::df_add(lap, diff(yp));
-    lap = frmg::df_add(lap, diff(zm));
-    lap = frmg::df_add(lap, diff(zp));
-    const float2 r2 = rho[t];
-    const df m = frmg::df_add_f(frmg::df_mul({r2.x, r2.y}, {sh, sl}), -1.0f);  // s rho - 1
-    const df loc = frmg::df_mul(ci, frmg::df_add(m, frmg::df_mul(ci, ci)));  // chi (m + chi^2)
-    const df d = frmg::df_sub(frmg::df_mul(lap, {Ah, Al}), loc);
-    v = d.h + d.l;
-    g[t] = c2.x;
-    f[t] = -d.h;
-    delta[t] = 0.0f;
+    // -x: cells (2p - 1, 2p); +x: cells (2p + 1, 2p + 2), wrapping in the row
+    const float2 l = chi[i > 0 ? c - 1 : c + L.n0 - 1];
+    const float2 r = chi[i + 2 < L.n0 ? c + 2 : c + 2 - L.n0];
+    df2 lap = frmg::df_sub2(df2{make_float2(l.x, cv.x), make_float2(l.y, cv.y)}, ci);
+    lap = frmg::df_add2(lap, frmg::df_sub2(df2{make_float2(cv.z, r.x), make_float2(cv.w, r.y)}, ci));
+    lap = frmg::df_add2(lap, frmg::df_sub2(pair(j > 0 ? c - sy : c + (L.n1 - 1) * sy), ci));
+    lap = frmg::df_add2(lap, frmg::df_sub2(pair(j < L.n1 - 1 ? c + sy : c - (L.n1 - 1) * sy), ci));
+    lap = frmg::df_add2(lap, frmg::df_sub2(pair(k > 0 ? c - sz : c + (L.n2 - 1) * sz), ci));
+    lap = frmg::df_add2(lap, frmg::df_sub2(pair(k < L.n2 - 1 ? c + sz : c - (L.n2 - 1) * sz), ci));
+    const float4 rv = reinterpret_cast<const float4 *>(rho)[t];
+    const df2 rp = {make_float2(rv.x, rv.z), make_float2(rv.y, rv.w)};
+    const df2 m = frmg::df_add_f2(frmg::df_mul2(rp, df2{frmg::splat2(sh), frmg::splat2(sl)}),
+                                  -1.0f);  // s rho - 1
+    const df2 loc = frmg::df_mul2(ci, frmg::df_add2(m, frmg::df_mul2(ci, ci)));  // chi (m + chi^2)
+    const df2 d = frmg::df_sub2(frmg::df_mul2(lap, df2{frmg::splat2(Ah), frmg::splat2(Al)}), loc);
+    const float2 v = frmg::add2(d.h, d.l);
+    reinterpret_cast<float2 *>(g)[t] = ci.h;
+    reinterpret_cast<float2 *>(f)[t] = make_float2(-d.h.x, -d.h.y);
+    reinterpret_cast<float2 *>(delta)[t] = make_float2(0.0f, 0.0f);
+    s2 = fmaf(v.y, v.y, v.x * v.x);
+    mx = fmaxf(fabsf(v.x), fabsf(v.y));
   }
-  sy_block_norms<float>(v * v, fabsf(v), part);
+  sy_block_norms<float>(s2, mx, part);
 }
 
 // chi += delta in double-float
@@ -987,11 +991,11 @@ extern "C" int fr_symmetron_solve(frmg_ctx *ctx, const double *density, const in
       // defect of chi in double-float, with the set-up of the FP32 correction
       // problem of the next outer step (g = hi(chi), f = -hi(d), delta = 0)
       auto defect_df = [&](double &rms_, double &mx_) {
-        k_sy_defect_df<<<(unsigned)nblk(nc), kNT, 0, st>>>(H.lev[0], chi2, rho2, Ah, Alo, sh,
-                                                           slo, gl[0], H.lev[0].f, H.lev[0].u,
-                                                           part);
+        k_sy_defect_df<<<(unsigned)nblk(nc / 2), kNT, 0, st>>>(H.lev[0], chi2, rho2, Ah, Alo,
+                                                               sh, slo, gl[0], H.lev[0].f,
+                                                               H.lev[0].u, part);
         SLAUNCH(ctx);
-        norms(part, nblk(nc), nc, rms_, mx_);
+        norms(part, nblk(nc / 2), nc, rms_, mx_);
       };
       double rms, mx;
       defect_df(rms, mx);
