@@ -70,15 +70,17 @@ ALG_BYTES = {
 # cells, so it is scaled to the workload's grid).  Valid for the kernels as
 # captured; the second entry names the captured launch.
 TRAFFIC_PER_CELL = {
-    "smooth_f32@fine": ((470.290e6 + 408.163e6) / 384 ** 3,
+    "smooth_f32@fine": ((466.440e6 + 408.520e6) / 384 ** 3,
                         "k_smooth_rc plain form, 64x16 tiles, one 384^3 launch"),
-    "smooth_prolong_f32@fine": ((539.077e6 + 411.576e6) / 384 ** 3,
+    "smooth_prolong_f32@fine": ((537.745e6 + 412.522e6) / 384 ** 3,
                                 "k_smooth_rc plain form with the prolongation fused, 64x16 "
                                 "tiles, one 384^3 launch"),
-    "smooth_bg_f32@fine": ((935.178e6 + 426.044e6) / 384 ** 3,
+    "smooth_bg_f32@fine": ((930.505e6 + 426.363e6) / 384 ** 3,
                            "k_smooth_rc correction form, 64x8 tiles, one 384^3 launch"),
     "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "k_resid_restrict_tiled, one 384^3 launch"),
     "prolong_f32@fine": (678.570e6 / 384 ** 3, "k_prolong_tiled, one 384^3 launch"),
+    "df_defect": ((1363.777e6 + 1101.749e6) / 384 ** 3,
+                  "k_df_defect, two cells per thread, one 384^3 launch"),
 }
 
 
