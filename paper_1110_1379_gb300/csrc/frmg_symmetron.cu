@@ -240,24 +240,52 @@ __global__ void __launch_bounds__(kNT) k_sy_fas_rhs(SLevel<T> Cs) {
   Cs.f[t] = N - Cs.f[t];
 }
 
-// u^h += P (u^H - R u^h): trilinear 27/9/3/1 interpolation, periodic.
+// u^h += P(u^H - R u^h): the trilinear 27/9/3/1 prolongation (Sec. V.A.3) of
+// the coarse correction onto every fine cell, periodic.  One thread per
+// coarse cell: the correction e = u^H - uR of its 3 x 3 x 3 coarse
+// neighbourhood is read once and blended into its 8 children (the nearer
+// coarse cell of a child is its parent, the farther one is the neighbour on
+// the child's side), each child's x-pair row updated with one paired access.
 template <typename T>
 __global__ void __launch_bounds__(kNT) k_sy_prolong(SLevel<T> F, SLevel<T> Cs) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= F.nc) return;
-  int i, j, k;
-  sy_ijk(F, t, i, j, k);
-  const int I = i >> 1, J = j >> 1, K = k >> 1;
-  const int I2 = (i & 1) ? (I + 1 == Cs.n0 ? 0 : I + 1) : (I == 0 ? Cs.n0 - 1 : I - 1);
-  const int J2 = (j & 1) ? (J + 1 == Cs.n1 ? 0 : J + 1) : (J == 0 ? Cs.n1 - 1 : J - 1);
-  const int K2 = (k & 1) ? (K + 1 == Cs.n2 ? 0 : K + 1) : (K == 0 ? Cs.n2 - 1 : K - 1);
-  auto e = [&](int a, int b, int c) {
-    const long long q = ((long long)c * Cs.n1 + b) * Cs.n0 + a;
-    return Cs.u[q] - Cs.uR[q];
-  };
-  const T v = T(27) * e(I, J, K) + T(9) * (e(I2, J, K) + e(I, J2, K) + e(I, J, K2)) +
-              T(3) * (e(I2, J2, K) + e(I2, J, K2) + e(I, J2, K2)) + e(I2, J2, K2);
-  F.u[t] += v * T(1.0 / 64.0);
+  if (t >= Cs.nc) return;
+  int I, J, K;
+  sy_ijk(Cs, t, I, J, K);
+  const int Im = I == 0 ? Cs.n0 - 1 : I - 1, Ip = I + 1 == Cs.n0 ? 0 : I + 1;
+  const int Jm = J == 0 ? Cs.n1 - 1 : J - 1, Jp = J + 1 == Cs.n1 ? 0 : J + 1;
+  const int Km = K == 0 ? Cs.n2 - 1 : K - 1, Kp = K + 1 == Cs.n2 ? 0 : K + 1;
+  const int xs[3] = {Im, I, Ip}, ys[3] = {Jm, J, Jp}, zs[3] = {Km, K, Kp};
+  T e[3][3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const long long q = ((long long)zs[c] * Cs.n1 + ys[b]) * Cs.n0 + xs[a];
+        e[c][b][a] = Cs.u[q] - Cs.uR[q];
+      }
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+#pragma unroll
+  for (int cz = 0; cz < 2; cz++)
+#pragma unroll
+    for (int cy = 0; cy < 2; cy++) {
+      const int k2 = cz ? 2 : 0, j2 = cy ? 2 : 0;  // farther z and y neighbours
+      T v[2];
+#pragma unroll
+      for (int cx = 0; cx < 2; cx++) {
+        const int i2 = cx ? 2 : 0;
+        v[cx] = T(27) * e[1][1][1] + T(9) * (e[1][1][i2] + e[1][j2][1] + e[k2][1][1]) +
+                T(3) * (e[1][j2][i2] + e[k2][1][i2] + e[k2][j2][1]) + e[k2][j2][i2];
+      }
+      const long long f = ((long long)(2 * K + cz) * F.n1 + (2 * J + cy)) * F.n0 + 2 * I;
+      T2 *fu = reinterpret_cast<T2 *>(F.u + f);
+      T2 uu = *fu;
+      uu.x += v[0] * T(1.0 / 64.0);
+      uu.y += v[1] * T(1.0 / 64.0);
+      *fu = uu;
+    }
 }
 
 // Coarsest level: one block relaxes the whole grid until its rms residual has
@@ -268,30 +296,31 @@ __global__ void __launch_bounds__(kNT) k_sy_prolong(SLevel<T> F, SLevel<T> Cs) {
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(kNT) k_sy_coarsest(SLevel<T> L, double rel, double abs_,
                                                      int maxit, int stall) {
-  __shared__ double red[kNT / 32];
-  __shared__ double lim_s, best_s;
+  // the rms in the level's precision (FP64 arithmetic runs at 1/64 rate)
+  __shared__ T red[kNT / 32];
+  __shared__ T lim_s, best_s;
   __shared__ int stop_s, flat_s;
-  auto rms = [&]() -> double {
-    double s = 0.0;
+  auto rms = [&]() -> T {
+    T s = T(0);
     for (long long c = threadIdx.x; c < L.nc; c += blockDim.x) {
       int i, j, k;
       sy_ijk(L, c, i, j, k);
       T N, dN;
       sy_op<T, CORR>(L, i, j, k, N, dN);
-      const double d = (double)(N - sy_rhs(L, c));
+      const T d = N - sy_rhs(L, c);
       s += d * d;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
-    double tot = 0.0;
+    T tot = T(0);
     for (int q = 0; q < kNT / 32; q++) tot += red[q];
-    return sqrt(tot / (double)L.nc);
+    return sqrt(tot / (T)L.nc);
   };
-  const double r0 = rms();
+  const T r0 = rms();
   if (threadIdx.x == 0) {
-    lim_s = fmax(rel * r0, abs_);
+    lim_s = fmax((T)rel * r0, (T)abs_);
     best_s = r0;
     flat_s = 0;
     stop_s = 0;  // at least one sweep
@@ -312,9 +341,9 @@ __global__ void __launch_bounds__(kNT) k_sy_coarsest(SLevel<T> L, double rel, do
       }
       __syncthreads();
     }
-    const double r = rms();
+    const T r = rms();
     if (threadIdx.x == 0) {
-      if (r < 0.9 * best_s) {
+      if (r < T(0.9) * best_s) {
         best_s = r;
         flat_s = 0;
       } else {
@@ -748,7 +777,7 @@ struct SHier {
     k_sy_fas_rhs<T, CORR><<<(unsigned)nblk(lev[l + 1].nc), kNT, 0, st>>>(lev[l + 1]);
     SLAUNCH(ctx);
     vcycle(l + 1);
-    k_sy_prolong<T><<<(unsigned)nblk(lev[l].nc), kNT, 0, st>>>(lev[l], lev[l + 1]);
+    k_sy_prolong<T><<<(unsigned)nblk(lev[l + 1].nc), kNT, 0, st>>>(lev[l], lev[l + 1]);
     SLAUNCH(ctx);
     smooth(l, post);
   }
