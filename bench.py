@@ -77,8 +77,8 @@ TRAFFIC_PER_CELL = {
                                 "tiles, one 384^3 launch"),
     "smooth_bg_f32@fine": ((930.505e6 + 426.363e6) / 384 ** 3,
                            "k_smooth_rc correction form, 64x8 tiles, one 384^3 launch"),
-    "resid_restrict_f32@fine": (816.198e6 / 384 ** 3, "k_resid_restrict_tiled, one 384^3 launch"),
-    "prolong_f32@fine": (678.570e6 / 384 ** 3, "k_prolong_tiled, one 384^3 launch"),
+    "resid_restrict_f32@fine": ((712.663e6 + 102.480e6) / 384 ** 3,
+                                "k_resid_restrict_tiled plain form, one 384^3 launch"),
     "df_defect": ((1363.777e6 + 1101.749e6) / 384 ** 3,
                   "k_df_defect, two cells per thread, one 384^3 launch"),
 }
