@@ -126,6 +126,11 @@ typedef struct {
     double tau_rms;   /* rms of the truncation-error estimate (tau_alpha > 0: of the
                          last evaluation; FP64: after the last V-cycle; mixed: after
                          the FP32 full-variable phase), NaN when not evaluated */
+    int host_copies;  /* fr_solve with a host u: copies of the result to the host.  A
+                         mixed solve with a page-locked u starts one when an outer step
+                         predicts convergence, overlapping the last defect check; a
+                         later update makes it stale and the result is copied again
+                         (2 or more).  0 for a device u. */
 } fr_stats;
 
 /* Refinement patch (Sec. V.A.1, V.B.1, VI.B): a box of fine cells at twice the

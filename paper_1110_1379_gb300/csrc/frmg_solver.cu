@@ -2021,6 +2021,7 @@ static void solve_mixed_df(frmg_ctx *ctx, std::vector<Problem> &P, const SolveCf
     CK(cudaMemcpyAsync(P[0].host_u, P[0].u, (size_t)D[0].ncell * sizeof(double),
                        cudaMemcpyDeviceToHost, ctx->copy));
     CK(cudaEventRecord(ctx->copy_out, ctx->copy));
+    stats[0].host_copies++;
     early = true;
     stale = false;
   };
@@ -2605,6 +2606,8 @@ static int solve_impl(frmg_ctx *ctx, const double *density, const int dims[3], d
       back.erase(std::remove_if(back.begin(), back.end(),
                                 [&](const Staged &b) { return b.host_dst == (void *)u; }),
                  back.end());
+    for (const Staged &b : back)
+      if (b.host_dst == (void *)u) sv[0].host_copies++;
     finish(ctx, back, st);
     sv[0].seconds = now_s() - t0;
     if (stats) *stats = sv[0];

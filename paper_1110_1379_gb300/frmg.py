@@ -42,7 +42,7 @@ class fr_stats(ctypes.Structure):
                 ("res0_rms", ctypes.c_double), ("res_rms", ctypes.c_double),
                 ("res_max", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("nhist", ctypes.c_int), ("hist", ctypes.c_double * FR_HIST),
-                ("tau_rms", ctypes.c_double)]
+                ("tau_rms", ctypes.c_double), ("host_copies", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}

@@ -213,21 +213,9 @@ def test_mixed_host_output_equals_device(C, pinned, initial_guess):
     st, sh = C.solve(rh, uh, tol=1e-9, prec="mixed", initial_guess=initial_guess, **P)
     assert st == 0 and sh.vcycles == sd.vcycles and sh.outer == sd.outer
     assert np.array_equal(uh.numpy(), host(ud))
-
-
-def test_pinned_host_density_is_validated(C):
-    """A zero-start mixed solve reads a page-locked host density in its first
-    pass, across the host link, without copying it in; a NaN or a negative
-    value there is rejected as from device memory."""
-    from paper_1110_1379_gb300 import frmg
-    shape = (8, 8, 8)
-    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
-    for bad in (float("nan"), -0.5):
-        rh = torch.ones(shape, dtype=torch.float64).pin_memory()
-        rh[1, 2, 3] = bad
-        with pytest.raises(frmg.FRError) as e:
-            C.solve(rh, u, prec="mixed", initial_guess=0, **CFG1)
-        assert e.value.status == frmg.FR_EINVAL
+    assert sd.host_copies == 0 and sh.host_copies >= 1
+    if not pinned:
+        assert sh.host_copies == 1  # pageable memory: copied once, at the end
 
 
 # ------------------------------------------------------------------ edge cases
