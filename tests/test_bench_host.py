@@ -1,5 +1,5 @@
-"""Host-side helpers of bench.py (no GPU): the --options parser and the
-untimed option search."""
+"""Host-side helpers of bench.py (no GPU): the --options parser, the
+untimed option search and the clock sampler."""
 import bench
 
 
@@ -27,3 +27,31 @@ def test_pick_options_takes_the_fastest_converging_candidate(monkeypatch):
     best, times = bench.pick_options(run, cands)
     assert best == dict(pre=2, post=2, relax=1.0, prec="mixed")
     assert times == {"V(2,2) w=1.0 fp64": 3.0, "V(2,2) w=1.0 mixed": 1.0}
+
+
+def test_clock_sampler_reads_clocks_and_reasons(tmp_path, monkeypatch):
+    """ClockSampler against a stand-in nvidia-smi on PATH that prints four
+    sample lines: the first (taken before the timed region) is dropped, the
+    median SM clock and the active throttle reasons of the rest are reported."""
+    fake = tmp_path / "nvidia-smi"
+    lines = ["0, 1500, 2070, 600.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2040, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    fake.write_text("#!/bin/sh\n" + "".join(f"echo '{l}'\n" for l in lines) + "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{bench.os.environ.get('PATH', '')}")
+    s = bench.ClockSampler(0)
+    s.start()
+    bench.time.sleep(0.2)
+    out = s.stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
