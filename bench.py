@@ -79,6 +79,8 @@ TRAFFIC_PER_CELL = {
                            "k_smooth_rc correction form, 64x8 tiles, one 384^3 launch"),
     "resid_restrict_f32@fine": ((712.663e6 + 102.480e6) / 384 ** 3,
                                 "k_resid_restrict_tiled plain form, one 384^3 launch"),
+    "prolong_f32@fine": ((286.715e6 + 392.129e6) / 384 ** 3,
+                         "k_prolong_tiled, one 384^3 launch (the fine level)"),
     "df_defect": ((1363.777e6 + 1101.749e6) / 384 ** 3,
                   "k_df_defect, two cells per thread, one 384^3 launch"),
 }
