@@ -70,13 +70,9 @@ ALG_BYTES = {
 # cells, so it is scaled to the workload's grid).  Valid for the kernels as
 # captured; the second entry names the captured launch.
 TRAFFIC_PER_CELL = {
-    "smooth_f32@fine": ((466.440e6 + 408.520e6) / 384 ** 3,
-                        "k_smooth_rc plain form, 64x16 tiles, one 384^3 launch"),
     "smooth_prolong_f32@fine": ((537.745e6 + 412.522e6) / 384 ** 3,
                                 "k_smooth_rc plain form with the prolongation fused, 64x16 "
                                 "tiles, one 384^3 launch"),
-    "smooth_bg_f32@fine": ((930.505e6 + 426.363e6) / 384 ** 3,
-                           "k_smooth_rc correction form, 64x8 tiles, one 384^3 launch"),
     "resid_restrict_f32@fine": ((712.663e6 + 102.480e6) / 384 ** 3,
                                 "k_resid_restrict_tiled plain form, one 384^3 launch"),
     "prolong_f32@fine": ((286.715e6 + 392.129e6) / 384 ** 3,

@@ -1737,6 +1737,7 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
   const Grid<float> &Gg = grids[g];
   if (!grid_active(active, Gg.field)) return;
   const float *__restrict__ uin = par ? Gg.u2 : Gg.u;
+  const float *__restrict__ xin = par ? Gg.x2 : Gg.x;  // x = expm1(u) of uin
   float *__restrict__ uout = par ? Gg.u : Gg.u2;
   float *__restrict__ xout = par ? Gg.x : Gg.x2;
   const float *__restrict__ fin = Gg.f;
@@ -1820,10 +1821,13 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
   float FR[NSL][4], FB[NSL][4];
   // prefetched plane (u, f and, in the correction form, ub and E of the even
   // and odd cell)
-  float2 pu[NSL], pf[NSL], pb[NSL], pe[NSL];
+  // (without the prolongation, x of the arriving u is read from the x cache
+  // its writer left beside it; with it, u changes on arrival and x is computed)
+  float2 pu[NSL], px[NSL], pf[NSL], pb[NSL], pe[NSL];
 #pragma unroll
   for (int s = 0; s < NSL; s++) {
     pu[s] = make_float2(0.f, 0.f);
+    px[s] = pu[s];
     pf[s] = pu[s];
     pb[s] = pu[s];
     pe[s] = make_float2(1.f, 1.f);
@@ -1843,6 +1847,7 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
       for (int s = 0; s < NSL; s++) {
         if (!(fl[s] & 1u)) continue;
         pu[s] = *reinterpret_cast<const float2 *>(uin + zo + roff[s]);
+        if (!PRL) px[s] = *reinterpret_cast<const float2 *>(xin + zo + roff[s]);
         if (fin) pf[s] = *reinterpret_cast<const float2 *>(fin + zo + roff[s]);
         if (BG) {
           pb[s] = *reinterpret_cast<const float2 *>(ubin + zo + roff[s]);
@@ -2024,16 +2029,17 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
         }
         const bool odd = (ro[s] ^ PK) != 0;  // red cell is the odd one
         const float ur = odd ? pu[s].y : pu[s].x, ub = odd ? pu[s].x : pu[s].y;
+        const float xr = odd ? px[s].y : px[s].x, xb = odd ? px[s].x : px[s].y;
         // the red cell's x is needed only if this pair's red cell is updated
         const bool needr = s < NI || (fl[s] & (odd ? 8u : 4u));
         if constexpr (BG) {
-          R[s][K] = make_float4(ur, needr ? m_expm1(ur) : 0.0f, odd ? pb[s].y : pb[s].x,
-                                odd ? pe[s].y : pe[s].x);
-          B[s][K] = make_float4(ub, m_expm1(ub), odd ? pb[s].x : pb[s].y,
+          R[s][K] = make_float4(ur, needr ? (PRL ? m_expm1(ur) : xr) : 0.0f,
+                                odd ? pb[s].y : pb[s].x, odd ? pe[s].y : pe[s].x);
+          B[s][K] = make_float4(ub, PRL ? m_expm1(ub) : xb, odd ? pb[s].x : pb[s].y,
                                 odd ? pe[s].x : pe[s].y);
         } else {
-          R[s][K] = make_float2(ur, needr ? m_expm1(ur) : 0.0f);
-          B[s][K] = make_float2(ub, m_expm1(ub));
+          R[s][K] = make_float2(ur, needr ? (PRL ? m_expm1(ur) : xr) : 0.0f);
+          B[s][K] = make_float2(ub, PRL ? m_expm1(ub) : xb);
         }
         if (fin) {
           const float fr = odd ? pf[s].y : pf[s].x, fb = odd ? pf[s].x : pf[s].y;
