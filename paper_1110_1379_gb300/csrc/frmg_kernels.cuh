@@ -46,6 +46,7 @@ struct Grid {
   T *x2;           // buffer 1 of the x cache (ping-pongs with u)
   T *x;            // cache: expm1(u)
   const T *f;      // right-hand side storage; f_i = fs * (f[i] - fo); null = 0
+                   // (FP32 grids store f_i itself: fs = 1, fo = 0)
   T *uR;           // R u^h saved for the FAS correction (coarse levels)
   const float *ubg;  // background (BG mode), null otherwise
   const float *Ebg;  // exp(background)
@@ -1743,7 +1744,7 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
   const float *__restrict__ fin = Gg.f;
   const float *__restrict__ ubin = Gg.ubg;
   const float *__restrict__ Ein = Gg.Ebg;
-  const float fs = Gg.fs, fo = Gg.fo, ah = Gg.ah, beta = Gg.beta, cap = Gg.cap,
+  const float ah = Gg.ah, beta = Gg.beta, cap = Gg.cap,
               relax = Gg.relax;
   const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
   const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
@@ -2043,8 +2044,8 @@ __global__ void __launch_bounds__(RCCfg<TY, BG>::NT, RCCfg<TY, BG>::MINB)
         }
         if (fin) {
           const float fr = odd ? pf[s].y : pf[s].x, fb = odd ? pf[s].x : pf[s].y;
-          FR[s][K] = fs * (fr - fo);
-          FB[s][K] = fs * (fb - fo);
+          FR[s][K] = fr;  // FP32 grids: fs = 1, fo = 0, fs (f - fo) = f exactly
+          FB[s][K] = fb;
         } else {
           FR[s][K] = 0.0f;
           FB[s][K] = 0.0f;
@@ -2371,7 +2372,7 @@ __global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
     const float *__restrict__ fin = Fg.f;
     const float *__restrict__ ubin = Fg.ubg;
     const float *__restrict__ Ein = Fg.Ebg;
-    const float fs = Fg.fs, fo = Fg.fo, ah = Fg.ah, beta = Fg.beta;
+    const float ah = Fg.ah, beta = Fg.beta;
     const int n0 = Fg.n0, n1 = Fg.n1, n2 = Fg.n2;
     const int c0 = Cg.n0, c1 = Cg.n1;
     float *__restrict__ cu = cpar ? Cg.u2 : Cg.u;
@@ -2485,7 +2486,7 @@ __global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
           float acc, dacc, N, dN;
           A.done(acc, dacc);
           finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-          const float d = N - (hasf ? fs * (sf[o] - fo) : 0.0f);
+          const float d = N - (hasf ? sf[o] : 0.0f);  // FP32 grids: fs (f - fo) = f
           sdd += d;
           su += di;
           ss = fmaf(d, d, ss);
