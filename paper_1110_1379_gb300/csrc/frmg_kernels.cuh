@@ -2458,35 +2458,79 @@ __global__ void __launch_bounds__(RRCfg<TX, TY>::NT)
       __syncthreads();
       if (valid) {
         const int slm = sl == 0 ? NS - 1 : sl - 1, slp = sl + 1 == NS ? 0 : sl + 1;
+        // the 2 x 2 cells of this thread (rows ly, ly + 1; columns lx, lx + 1)
+        // and their neighbours as aligned pairs: left, own and right pair of
+        // each row, the pairs of rows ly - 1 and ly + 2, and the own pairs of
+        // planes m - 1 and m + 1 (same values and face order as cell by cell)
+        const int r0 = sl * PL + ly * LX + lx, r1 = r0 + LX;
+        const int zm0 = slm * PL + ly * LX + lx, zp0 = slp * PL + ly * LX + lx;
+        auto pr = [&](const float *a, int o) { return *reinterpret_cast<const float2 *>(a + o); };
+        struct Nb {
+          float2 L[2], C[2], R[2], D, U, M[2], P[2];
+        };
+        auto gather = [&](const float *a) {
+          Nb n;
+          n.L[0] = pr(a, r0 - 2);
+          n.C[0] = pr(a, r0);
+          n.R[0] = pr(a, r0 + 2);
+          n.L[1] = pr(a, r1 - 2);
+          n.C[1] = pr(a, r1);
+          n.R[1] = pr(a, r1 + 2);
+          n.D = pr(a, r0 - LX);
+          n.U = pr(a, r1 + LX);
+          n.M[0] = pr(a, zm0);
+          n.M[1] = pr(a, zm0 + LX);
+          n.P[0] = pr(a, zp0);
+          n.P[1] = pr(a, zp0 + LX);
+          return n;
+        };
+        const Nb nu = gather(sd), nx = gather(sx);
+        Nb nb, ne;
+        if (BG) {
+          nb = gather(sub);
+          ne = gather(sE);
+        }
+        const float2 f0 = hasf ? pr(sf, r0) : make_float2(0.f, 0.f);
+        const float2 f1 = hasf ? pr(sf, r1) : make_float2(0.f, 0.f);
+        auto lane = [](const float2 &v, int a) { return a ? v.y : v.x; };
 #pragma unroll
         for (int q = 0; q < 4; q++) {
           const int ax = q & 1, ay = q >> 1;
-          const int li = (ly + ay) * LX + lx + ax;
-          const int o = sl * PL + li;
           const int gxq = gx + ax, gyq = gy + ay;
-          const float di = sd[o], xi = sx[o];
-          const float Ei = BG ? sE[o] : 1.0f;
-          const float ubi = BG ? sub[o] : 0.0f;
+          // value of array n at neighbour k of the cell: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z
+          auto at = [&](const Nb &n, int k) -> float {
+            switch (k) {
+              case 0: return ax ? n.C[ay].x : n.L[ay].y;
+              case 1: return ax ? n.R[ay].x : n.C[ay].y;
+              case 2: return ay ? lane(n.C[0], ax) : lane(n.D, ax);
+              case 3: return ay ? lane(n.U, ax) : lane(n.C[1], ax);
+              case 4: return lane(n.M[ay], ax);
+              default: return lane(n.P[ay], ax);
+            }
+          };
+          const float di = lane(nu.C[ay], ax), xi = lane(nx.C[ay], ax);
+          const float Ei = BG ? lane(ne.C[ay], ax) : 1.0f;
+          const float ubi = BG ? lane(nb.C[ay], ax) : 0.0f;
           const float Bi = BG ? Ei + Ei * xi : 1.0f + xi;
           OpAcc<float, BG> A(di, Ei, xi, Bi, ubi);
-#define FR_NB(OFF) A.reg(sd[OFF], sx[OFF], BG ? sub[OFF] : 0.0f, BG ? sE[OFF] : 1.0f)
+#define FR_NB(K) A.reg(at(nu, K), at(nx, K), BG ? at(nb, K) : 0.0f, BG ? at(ne, K) : 1.0f)
           if (DIR && gxq == 0) A.ghost(face_value(Fg, 0, gxq, gyq, m));
-          else FR_NB(o - 1);
+          else FR_NB(0);
           if (DIR && gxq == n0 - 1) A.ghost(face_value(Fg, 1, gxq, gyq, m));
-          else FR_NB(o + 1);
+          else FR_NB(1);
           if (DIR && gyq == 0) A.ghost(face_value(Fg, 2, gxq, gyq, m));
-          else FR_NB(o - LX);
+          else FR_NB(2);
           if (DIR && gyq == n1 - 1) A.ghost(face_value(Fg, 3, gxq, gyq, m));
-          else FR_NB(o + LX);
+          else FR_NB(3);
           if (DIR && m == 0) A.ghost(face_value(Fg, 4, gxq, gyq, m));
-          else FR_NB(slm * PL + li);
+          else FR_NB(4);
           if (DIR && m == n2 - 1) A.ghost(face_value(Fg, 5, gxq, gyq, m));
-          else FR_NB(slp * PL + li);
+          else FR_NB(5);
 #undef FR_NB
           float acc, dacc, N, dN;
           A.done(acc, dacc);
           finish_op(xi, Ei, acc, dacc, ah, beta, BG, N, dN);
-          const float d = N - (hasf ? sf[o] : 0.0f);  // FP32 grids: fs (f - fo) = f
+          const float d = N - lane(ay ? f1 : f0, ax);  // FP32 grids: fs (f - fo) = f
           sdd += d;
           su += di;
           ss = fmaf(d, d, ss);
