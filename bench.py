@@ -70,10 +70,14 @@ ALG_BYTES = {
 # cells, so it is scaled to the workload's grid).  Valid for the kernels as
 # captured; the second entry names the captured launch.
 TRAFFIC_PER_CELL = {
-    "smooth_prolong_f32@fine": ((537.745e6 + 412.522e6) / 384 ** 3,
+    "smooth_f32@fine": ((702.4e6 + 418.0e6) / 384 ** 3,
+                        "k_smooth_rc plain form, 64x16 tiles, one 384^3 launch"),
+    "smooth_prolong_f32@fine": ((536.8e6 + 412.4e6) / 384 ** 3,
                                 "k_smooth_rc plain form with the prolongation fused, 64x16 "
                                 "tiles, one 384^3 launch"),
-    "resid_restrict_f32@fine": ((712.663e6 + 102.480e6) / 384 ** 3,
+    "smooth_bg_f32@fine": ((1176.2e6 + 430.6e6) / 384 ** 3,
+                           "k_smooth_rc correction form, 64x8 tiles, one 384^3 launch"),
+    "resid_restrict_f32@fine": ((715.0e6 + 102.6e6) / 384 ** 3,
                                 "k_resid_restrict_tiled plain form, one 384^3 launch"),
     "prolong_f32@fine": ((286.715e6 + 392.129e6) / 384 ** 3,
                          "k_prolong_tiled, one 384^3 launch (the fine level)"),
