@@ -1669,9 +1669,10 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
 // planes in registers: the z neighbours of an update are the owner's
 // own registers, and only the xy exchange goes through shared memory.  At the
 // step that loads plane p:
-//   1. the pair's u and f of plane p (loaded a step earlier) are split into its
-//      red and black cell, x is computed from u (the x cache is not read), and
-//      the black cell, still old, is published to the black half-plane of p;
+//   1. the pair's u, x and f of plane p (loaded a step earlier; x from the x
+//      cache that the writer of u left beside it) are split into its red and
+//      black cell, and the black cell, still old, is published to the black
+//      half-plane of p;
 //   2. the red cells of plane p-1 on the tile grown by one cell are updated:
 //      x and y neighbours are black cells of plane p-1 (the other cell of the
 //      pair from registers, the rest from the black half-plane published a
@@ -1686,7 +1687,8 @@ __global__ void __launch_bounds__(RBCfg<TY>::NT, RBCfg<TY>::minb(BG))
 // With PRL the sweep is the first one after the coarse-grid correction: every
 // arriving cell first gets u += P(u^H - R u^h) from the coarser grid (the
 // trilinear 27/9/3/1 prolongation of k_prolong_tiled, z then y then x, same
-// arithmetic), so the separate prolongation pass is saved.  The coarse
+// arithmetic) and its x is computed from the corrected u, so the separate
+// prolongation pass is saved.  The coarse
 // correction of the tile, blended in z for the next plane, is staged in
 // shared memory during the step before (double-buffered as the half-planes).  The ring of
 // register planes is indexed by the step modulo 4, which the loop unrolls into
