@@ -40,38 +40,28 @@ __global__ void k_df_init(DFGrid G, const double *u64, const double *rho, int ze
 // u += delta and e^u, two cells (an x-pair) per thread.  For |delta| < 2^-5
 // (the correction steps) e^u is the old e^u times e^delta, e^delta by its
 // Taylor series to degree 7 in double-float (truncation below 2^-40 delta^8 /
-// 8!, far under the pair's rounding), on packed FP32 pairs when both cells
-// take it; larger steps (the first update after the full-variable phase)
-// recompute e^u from u, cell by cell.
-__device__ __forceinline__ df df_update_exp_small(df Bo, float dl) {
-  // Horner: e^d = 1 + d (1 + d/2 (1 + d/3 (... (1 + d/7))))
-  df q = {1.0f, 0.0f};
-#pragma unroll
-  for (int k = 7; k >= 1; k--) {
-    q = df_mul_f(q, dl);
-    const float rk = 1.0f / (float)k;  // a constant after unrolling
-    const float qh = q.h * rk;
-    const float rem = fmaf(-qh, (float)k, q.h) + q.l;
-    q = df_add_f(df{qh, rem * rk}, 1.0f);
-  }
-  return df_mul(Bo, q);
-}
+// 8!, far under the pair's rounding), on packed FP32 pairs, when every cell
+// of the warp takes it; otherwise (the first update after the full-variable
+// phase) e^u is recomputed from u.
 __global__ void __launch_bounds__(128) k_df_update(DFGrid G, const float *delta, float ln2h,
                                                    float ln2l) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (G.ncell >> 1)) return;
+  const bool in = t < (G.ncell >> 1);
   float4 *U4 = reinterpret_cast<float4 *>(G.u);
   float4 *B4 = reinterpret_cast<float4 *>(G.B);
+  const float2 dl = in ? reinterpret_cast<const float2 *>(delta)[t] : make_float2(0.f, 0.f);
+  // the path is chosen per warp: every lane recomputes e^u from u when one
+  // cell of the warp has a large step (one path executed, not both)
+  const bool smallw = __all_sync(0xffffffffu, fabsf(dl.x) < 0.03125f && fabsf(dl.y) < 0.03125f);
+  if (!in) return;
   const float4 uo = U4[t];
-  const float2 dl = reinterpret_cast<const float2 *>(delta)[t];
   // u + delta: TwoSum of the hi parts, the lo part added, renormalised
   df2 s = two_sum2(make_float2(uo.x, uo.z), dl);
   s.l = add2(s.l, make_float2(uo.y, uo.w));
   const df2 u = fast_two_sum2(s.h, s.l);
   U4[t] = make_float4(u.h.x, u.l.x, u.h.y, u.l.y);
-  const bool small0 = fabsf(dl.x) < 0.03125f, small1 = fabsf(dl.y) < 0.03125f;
   float4 Bn;
-  if (small0 && small1) {
+  if (smallw) {
     const float4 Bo = B4[t];
     df2 q = {splat2(1.0f), splat2(0.0f)};
 #pragma unroll
@@ -89,19 +79,8 @@ __global__ void __launch_bounds__(128) k_df_update(DFGrid G, const float *delta,
     const df2 B = df_mul2(df2{make_float2(Bo.x, Bo.z), make_float2(Bo.y, Bo.w)}, q);
     Bn = make_float4(B.h.x, B.l.x, B.h.y, B.l.y);
   } else {
-    df b0, b1;
-    if (small0) {
-      const float2 bo = G.B[2 * t];
-      b0 = df_update_exp_small(df{bo.x, bo.y}, dl.x);
-    } else {
-      b0 = df_exp(df{u.h.x, u.l.x}, ln2h, ln2l);
-    }
-    if (small1) {
-      const float2 bo = G.B[2 * t + 1];
-      b1 = df_update_exp_small(df{bo.x, bo.y}, dl.y);
-    } else {
-      b1 = df_exp(df{u.h.y, u.l.y}, ln2h, ln2l);
-    }
+    const df b0 = df_exp(df{u.h.x, u.l.x}, ln2h, ln2l);
+    const df b1 = df_exp(df{u.h.y, u.l.y}, ln2h, ln2l);
     Bn = make_float4(b0.h, b0.l, b1.h, b1.l);
   }
   B4[t] = Bn;

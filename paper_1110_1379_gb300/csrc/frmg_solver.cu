@@ -948,10 +948,13 @@ static void launch_rc_k(LevelSet<float> &s, const int *active, int par, cudaStre
 }
 
 // The first post-smoothing sweep of a level with the prolongation from its
-// coarser level applied to every arriving cell (register-column kernels only).
+// coarser level applied to every arriving cell (plain-form register-column
+// kernels only: the fused sweep computes x = expm1(u) of the arriving cells,
+// which the plain sweep reads from the cache, and for the correction form that
+// made the fused sweep slower than the prolongation and the sweep apart).
 template <bool BG>
 static bool can_fuse_prolong(const LevelSet<float> &F, const std::vector<int> *plan) {
-  return F.tiled && plan && !plan->empty() && (*plan)[0] == 1 && F.rc_ty[BG ? 1 : 0] > 0 &&
+  return !BG && F.tiled && plan && !plan->empty() && (*plan)[0] == 1 && F.rc_ty[0] > 0 &&
          F.rr_tiled && F.nblk_pl > 0;
 }
 template <bool BG>
