@@ -957,20 +957,19 @@ static bool can_fuse_prolong(const LevelSet<float> &F, const std::vector<int> *p
   return !BG && F.tiled && plan && !plan->empty() && (*plan)[0] == 1 && F.rc_ty[0] > 0 &&
          F.rr_tiled && F.nblk_pl > 0;
 }
-template <bool BG>
 static void launch_rc_prolong(frmg_ctx *ctx, LevelSet<float> &F, LevelSet<float> &C,
                               const int *active, int par, int cpar, cudaStream_t st) {
-  const int ty = F.rc_ty[BG ? 1 : 0];
+  const int ty = F.rc_ty[0];
   if (F.dirichlet) {
-    if (BG || ty == 8)
-      launch_rc_k<BG, true, 8, true>(F, active, par, st, C.d, cpar);
+    if (ty == 8)
+      launch_rc_k<false, true, 8, true>(F, active, par, st, C.d, cpar);
     else
-      launch_rc_k<BG, true, 16, true>(F, active, par, st, C.d, cpar);
+      launch_rc_k<false, true, 16, true>(F, active, par, st, C.d, cpar);
   } else {
-    if (BG || ty == 8)
-      launch_rc_k<BG, false, 8, true>(F, active, par, st, C.d, cpar);
+    if (ty == 8)
+      launch_rc_k<false, false, 8, true>(F, active, par, st, C.d, cpar);
     else
-      launch_rc_k<BG, false, 16, true>(F, active, par, st, C.d, cpar);
+      launch_rc_k<false, false, 16, true>(F, active, par, st, C.d, cpar);
   }
 }
 
@@ -1213,14 +1212,13 @@ static void vcycle(frmg_ctx *ctx, Hier<T> &H, int l, const CycleOpts &o, const i
     CK_LAUNCH(ctx);
   }
   vcycle<T, BG>(ctx, H, l + 1, o, active, st);
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4 && !BG) {
     if (can_fuse_prolong<BG>(F, tiled_ok ? &plan_post : nullptr)) {
       // prolongation fused into the first post-smoothing sweep (reported as
       // its own kernel family)
       {
-        PROF(BG ? (l == 0 ? "smooth_prolong_bg_f32@fine" : "smooth_prolong_bg_f32@coarse")
-                : (l == 0 ? "smooth_prolong_f32@fine" : "smooth_prolong_f32@coarse"));
-        launch_rc_prolong<BG>(ctx, F, C, active, H.par[l], H.par[l + 1], st);
+        PROF(l == 0 ? "smooth_prolong_f32@fine" : "smooth_prolong_f32@coarse");
+        launch_rc_prolong(ctx, F, C, active, H.par[l], H.par[l + 1], st);
         CK_LAUNCH(ctx);
         H.par[l] ^= 1;
       }
