@@ -608,6 +608,16 @@ int orc_restrict(const double *fine, const int nf[3], double *coarse)
     return ORC_OK;
 }
 
+/* Coarse boundary-face values of a patch from its fine ones (restrict_faces),
+ * packed as the faces of nf and of nf / 2. */
+int orc_restrict_faces(const double *ubf, const int nf[3], double *ubc)
+{
+    if (check_dims(nf) != ORC_OK)
+        return ORC_EINVAL;
+    restrict_faces(ubf, nf, ubc);
+    return ORC_OK;
+}
+
 /* uf += P (uH - uR) on a fine grid of size nf. */
 int orc_prolong_correct(double *uf, const int nf[3], const double *uH, const double *uR,
                         int dirichlet)

@@ -59,13 +59,15 @@ def _load():
             lib.orc_cell_op.argtypes = [P, P, P, D, D, D, D, D, P, I, I, I, P]
             lib.orc_smooth.argtypes = [P, P, P, P, D, D, D, D, D, P, I, D]
             lib.orc_restrict.argtypes = [P, P, P]
+            lib.orc_restrict_faces.argtypes = [P, P, P]
             lib.orc_prolong_correct.argtypes = [P, P, P, P, I]
             lib.orc_num_levels.argtypes = [P]
             lib.orc_solve_grid.argtypes = [P, P, D, D, D, D, D, P, D, I, I, I, D, I, P, P, P, P]
             lib.orc_patch_bc.argtypes = [P, P, I, P, P, P, P]
             lib.orc_cic.argtypes = [P, ctypes.c_long, P, P]
             for name in ("orc_model", "orc_residual", "orc_cell_op", "orc_smooth",
-                         "orc_restrict", "orc_prolong_correct", "orc_num_levels",
+                         "orc_restrict", "orc_restrict_faces", "orc_prolong_correct",
+                         "orc_num_levels",
                          "orc_solve_grid", "orc_patch_bc", "orc_cic"):
                 getattr(lib, name).restype = I
             _lib = lib
@@ -138,6 +140,18 @@ def restrict(fine):
     fine = _f64(fine)
     out = np.empty((fine.shape[0] // 2, fine.shape[1] // 2, fine.shape[2] // 2))
     _check(_load().orc_restrict(_p(fine), _p(_dims(fine.shape)), _p(out)), "restrict")
+    return out
+
+
+def restrict_faces(ub, shape):
+    """Boundary-face values of the grid of half the size of `shape` (n2, n1, n0)
+    from the packed faces ub of `shape`: each coarse face value is the mean of
+    the 4 fine face values covering it (the reading of Sec. V.B.2 used for the
+    coarse levels of a patch)."""
+    ub = _f64(ub)
+    cs = (shape[0] // 2, shape[1] // 2, shape[2] // 2)
+    out = np.empty(sum(face_sizes(cs)))
+    _check(_load().orc_restrict_faces(_p(ub), _p(_dims(shape)), _p(out)), "restrict_faces")
     return out
 
 

@@ -255,6 +255,35 @@ def test_prolongation_exact_for_linear_fields():
     assert np.abs(const - 3.0).max() < 1e-15
 
 
+def test_face_restriction_exact_for_linear_faces():
+    """Coarse patch boundary values (Sec. V.B.2 reading: the mean of the 4 fine
+    face values covering a coarse face cell) reproduce a field linear along
+    each face: the mean of a linear function over the 2 x 2 fine face cells is
+    its value at the coarse face cell's centre.  Distinct slopes along the two
+    in-face axes and unequal sizes make a swapped axis or a shifted block fail."""
+    shape = (6, 10, 14)                       # (n2, n1, n0)
+    n = [shape[2], shape[1], shape[0]]        # n0, n1, n2
+    axes = {0: (1, 2), 1: (0, 2), 2: (0, 1)}  # in-face axes p < q of the face normal to ax
+
+    def faces(nn, coef):
+        out = []
+        for f in range(6):
+            p, q = axes[f // 2]
+            a0, b, c = coef[f]
+            P = (np.arange(nn[p]) + 0.5) / nn[p]
+            Q = (np.arange(nn[q]) + 0.5) / nn[q]
+            out.append((a0 + b * P[None, :] + c * Q[:, None]).ravel())  # index Q n_p + P
+        return np.concatenate(out)
+
+    rng = np.random.default_rng(11)
+    coef = [tuple(rng.uniform(-2.0, 2.0, 3)) for _ in range(6)]
+    fine = faces(n, coef)
+    assert fine.size == sum(O.face_sizes(shape))
+    coarse = O.restrict_faces(fine, shape)
+    expect = faces([v // 2 for v in n], coef)
+    assert np.abs(coarse - expect).max() < 1e-14
+
+
 def test_level_count_rule():
     assert O.num_levels((32, 32, 32)) == 4  # 32 16 8 4
     assert O.num_levels((512, 512, 512)) == 8
