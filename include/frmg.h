@@ -288,11 +288,11 @@ int fr_vcycles(frmg_ctx *ctx, const double *density, const int dims[3], double b
  * that GPU; each call overwrites all of it before reading it, but calls that
  * overlap on the GPU (different streams, no ordering) race on it.  The first
  * call on each device looks up the array's device address (with that device
- * current) and keeps it; make that first call before any stream capture
- * begins.  The kept address belongs to the device's primary context: after
- * cudaDeviceReset (or anything else that destroys that context) the module is
- * loaded again, possibly at another address, and the kept one is stale, so
- * do not call this entry point on that device again in the same process.
+ * current) and keeps it.  The kept address belongs to the device's primary
+ * context: after cudaDeviceReset (or anything else that destroys that
+ * context) the module is loaded again, possibly at another address, and the
+ * kept one is stale, so do not call this entry point on that device again in
+ * the same process.
  */
 int fr_residual_norm_noalloc(const double *u, const double *density, const int dims[3],
                              double h, double box_mpc_h, double a, double omega_m,
