@@ -152,3 +152,82 @@ def test_spherical_region_converges_at_second_order():
         assert res.converged
         errs.append(np.abs(res.u - ue)[m > 0].max())
     assert errs[0] / errs[1] > 3.0
+
+
+def test_masked_transfers_by_brute_force():
+    """Masked transfers (Sec. V.A.2, V.A.3) against loops written from their
+    definitions: R d = (sum of the active children's d) / 8; the prolonged
+    correction at an active fine cell is the 27/9/3/1 / 64 combination of its
+    parent and the parent's neighbours on the child's side (a masked coarse
+    cell, carrying e = 0, and a cell outside the box contribute 0), and 0 at a
+    masked fine cell.  A coarse correction linear in position is reproduced
+    exactly at fine cells whose 8 interpolation parents lie in the box."""
+    rng = np.random.default_rng(5)
+    cs = (3, 4, 5)
+    fs = tuple(2 * c for c in cs)
+    d = rng.normal(size=fs)
+    act = rng.uniform(size=fs) < 0.6
+    R = M.restrict_active(d, act)
+    for K in range(cs[0]):
+        for J in range(cs[1]):
+            for I in range(cs[2]):
+                s = sum(d[2 * K + z, 2 * J + y, 2 * I + x]
+                        for z in (0, 1) for y in (0, 1) for x in (0, 1)
+                        if act[2 * K + z, 2 * J + y, 2 * I + x])
+                assert R[K, J, I] == pytest.approx(s / 8.0, abs=1e-15)
+
+    e = rng.normal(size=cs)
+    e[rng.uniform(size=cs) < 0.3] = 0.0                 # masked coarse cells
+    out = M.prolong_masked(e, act)
+
+    def ec(K, J, I):
+        inside = 0 <= K < cs[0] and 0 <= J < cs[1] and 0 <= I < cs[2]
+        return e[K, J, I] if inside else 0.0
+
+    for k in range(fs[0]):
+        for j in range(fs[1]):
+            for i in range(fs[2]):
+                if not act[k, j, i]:
+                    assert out[k, j, i] == 0.0
+                    continue
+                K, J, I = k // 2, j // 2, i // 2
+                sk, sj, si = (1 if k % 2 else -1), (1 if j % 2 else -1), (1 if i % 2 else -1)
+                v = 0.0
+                for oz, wz in ((0, 3), (sk, 1)):
+                    for oy, wy in ((0, 3), (sj, 1)):
+                        for ox, wx in ((0, 3), (si, 1)):
+                            v += wz * wy * wx * ec(K + oz, J + oy, I + ox)
+                assert out[k, j, i] == pytest.approx(v / 64.0, abs=1e-14)
+
+    # exact for a linear correction (coordinates in fine cell widths, cell centres)
+    Kc, Jc, Ic = np.indices(cs).astype(float)
+    lin = lambda z, y, x: 0.3 - 0.7 * z + 1.1 * y + 0.45 * x
+    eL = lin(2 * Kc + 1, 2 * Jc + 1, 2 * Ic + 1)
+    outL = M.prolong_masked(eL, np.ones(fs, dtype=bool))
+    kf, jf, if_ = np.indices(fs).astype(float)
+    want = lin(kf + 0.5, jf + 0.5, if_ + 0.5)
+    inner = (slice(1, -1),) * 3
+    assert np.abs(outL[inner] - want[inner]).max() < 1e-13
+
+
+def test_ghost_relation_returns_the_ghost_value():
+    """u_b from Eq. u_i-1jk solved for it: put back into u_g = u_b - r u_b +
+    r u_i (r = m_g / m_i) it returns the initial ghost value on every ghost face
+    of an active cell, for any mask ratio."""
+    shape = (6, 7, 8)
+    m = _irregular_mask(shape, 9)
+    rng = np.random.default_rng(4)
+    ut = rng.normal(size=shape)
+    ub = M.boundary_values(ut, m)
+    act = m > 0
+    n = 0
+    for f, (ax, st) in enumerate(M.FACES):
+        ug = np.roll(ut, -st, axis=ax)
+        mg = np.roll(m, -st, axis=ax)
+        ghost = act & (mg <= 0)
+        assert np.array_equal(np.isfinite(ub[f]), ghost)
+        r = mg[ghost] / m[ghost]
+        back = ub[f][ghost] - r * ub[f][ghost] + r * ut[ghost]
+        assert np.abs(back - ug[ghost]).max() < 1e-12
+        n += int(ghost.sum())
+    assert n > 0
