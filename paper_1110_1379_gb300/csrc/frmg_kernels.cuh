@@ -181,13 +181,6 @@ __device__ __forceinline__ void face_vals(T dj, T xj, T ubj, T Ej, T di, T Ei, T
 }
 
 template <typename T, bool BG>
-__device__ __forceinline__ void face_regular(const Grid<T> &G, long long cj, T di, T Ei, T xi,
-                                             T Bi, T ubi, T &acc, T &dacc) {
-  face_vals<T, BG>(G.u[cj], G.x[cj], BG ? (T)G.ubg[cj] : T(0), BG ? (T)G.Ebg[cj] : T(1), di, Ei,
-                   xi, Bi, ubi, acc, dacc);
-}
-
-template <typename T, bool BG>
 __device__ __forceinline__ void face_ghost(T ubf, T di, T Ei, T xi, T Bi, T ubi, T &acc,
                                            T &dacc) {
   T w, Bg;

@@ -301,12 +301,6 @@ static void face_offsets(const int n[3], long long off[6]) {
 // ---------------------------------------------------------------------------
 // small kernels used only by the host driver
 template <typename T>
-__global__ void k_fill(T *p, long long n, T v) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) p[t] = v;
-}
-
-template <typename T>
 __global__ void k_expm1(const T *u, T *x, long long n) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) x[t] = m_expm1(u[t]);
