@@ -3062,7 +3062,7 @@ int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, cons
     if (!ctx || !u || !dims || nsweeps < 0 || !(cap > 0)) einval("bad argument");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    Problem p = one_level(dims, h, box, a, om, fr0);
+    one_level(dims, h, box, a, om, fr0);  // argument checks
     Scope S(ctx);
     std::vector<Staged> back;
     long long nc = (long long)dims[0] * dims[1] * dims[2];
