@@ -41,7 +41,7 @@ __device__ __forceinline__ df two_prod(float a, float b) {
 }
 
 // a + b with absolute error about eps^2 (|a| + |b|), eps = 2^-24: enough
-// whenever the result is judged against the size of the terms, as a residual is.
+// whenever the result is measured against the size of the terms, as a residual is.
 __device__ __forceinline__ df df_add(df a, df b) {
   df s = two_sum(a.h, b.h);
   s.l += a.l + b.l;
