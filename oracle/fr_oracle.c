@@ -238,8 +238,8 @@ static void restrict_avg(const double *fine, const int nf[3], double *coarse)
             }
 }
 
-/* Reading of Sec. V.B.2 ("u_B taken as those in the corresponding AMR cells"):
- * a coarse face value is the mean of the 4 fine face values that cover it. */
+/* Reading of Sec. V.B.2 (coarse u_B from the matching cells of the coarser
+ * level): a coarse face value is the mean of the 4 fine face values that cover it. */
 static void restrict_faces(const double *ubf, const int nf[3], double *ubc)
 {
     int nc[3] = {nf[0] / 2, nf[1] / 2, nf[2] / 2};

@@ -378,8 +378,8 @@ __global__ void k_update64(double *u64, double *x64, const float *delta, long lo
 }
 
 // Restriction of packed boundary faces: a coarse face value is the mean of the
-// 4 fine face values covering it (reading of Sec. V.B.2, "u_B taken as those
-// in the corresponding AMR cells").
+// 4 fine face values covering it (reading of Sec. V.B.2, where the coarse u_B
+// come from the matching cells of the coarser level).
 template <typename T>
 __global__ void k_restrict_faces(const T *fine, int nf0, int nf1, int nf2, T *coarse) {
   int nf[3] = {nf0, nf1, nf2};
