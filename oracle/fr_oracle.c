@@ -265,8 +265,8 @@ static void restrict_faces(const double *ubf, const int nf[3], double *ubc)
  * Sec. V.A.3: the coarse cell containing the fine cell weighs 27/64, the three
  * sharing a face 9/64, the three sharing an edge 3/64, the one sharing a vertex
  * 1/64.  On a periodic grid the coarse neighbours wrap; on a patch a coarse
- * neighbour outside the patch is not a valid multigrid cell and contributes 0
- * (no renormalisation).
+ * neighbour outside the patch belongs to no multigrid level of the patch, so
+ * its weight is dropped (the others are not renormalised).
  */
 static void prolong_add(double *uf, const int nf[3], const double *e, int dirichlet)
 {
