@@ -93,3 +93,16 @@ def test_stats_struct_matches_the_header():
     names = re.findall(r"\b(?:double|int)\s+([a-z_0-9]+)(?:\[[A-Z_]+\])?;", body)
     assert names == [f for f, _ in frmg.fr_stats._fields_]
     assert frmg.FR_HIST == int(re.search(r"#define FR_HIST (\d+)", src).group(1))
+
+
+def test_no_gpu_fails_loudly(lib):
+    """Without a usable GPU the library refuses to create a context (FR_ECUDA
+    with the CUDA error in the message) instead of computing anywhere else."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1110_1379_gb300 import frmg
+    with pytest.raises(frmg.FRError) as ei:
+        frmg.Context(0)
+    assert ei.value.status == frmg.FR_ECUDA
+    assert "fr_ctx_create" in str(ei.value)
