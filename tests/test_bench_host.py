@@ -55,3 +55,30 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     s = bench.ClockSampler(0)
     s.start()
     assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_reference_arm_reports_the_headline_config(monkeypatch, capsys):
+    """Both arms print the same metric, unit and config, so the two lines can
+    be compared; the reference arm's bounded sample is named in cpu_baseline.
+    The oracle solve is replaced by a stand-in (this checks the line, not the
+    oracle)."""
+    import json
+    import types
+    import bench
+    from oracle import oracle as O
+    calls = []
+
+    def fake_solve(rho, **kw):
+        calls.append(rho.shape)
+        return types.SimpleNamespace(converged=True)
+
+    monkeypatch.setattr(O, "solve", fake_solve)
+    monkeypatch.delenv("RANK", raising=False)
+    args = types.SimpleNamespace(gpus=2, steps=2, warmup=1, n=bench.N)
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "cells/s" and line["higher_is_better"] is True
+    assert line["config"] == bench.headline_config(bench.N, 2)
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
+    assert calls == [(bench.SAMPLE_N,) * 3] * 3
