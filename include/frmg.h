@@ -24,7 +24,9 @@
  *    staged through library-owned device buffers (copies in both directions
  *    are part of the call).  The caller keeps ownership of every array.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
- *    is synchronous on return: results and stats are valid when it returns.
+ *    that takes a context is synchronous on return: results and stats are
+ *    valid when it returns (fr_residual_norm_noalloc, which takes none, is
+ *    asynchronous on its stream).
  *  - Return values are fr_status codes.  On FR_ENOCONV / FR_EDIVERGED the last
  *    iterate is still written to u.  fr_status_string() names a code;
  *    fr_last_error() returns a message for the last failing call on the
