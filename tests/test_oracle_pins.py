@@ -255,6 +255,25 @@ def test_prolongation_exact_for_linear_fields():
     assert np.abs(const - 3.0).max() < 1e-15
 
 
+def test_prolongation_on_a_patch_drops_outside_cells():
+    """On a patch (Sec. V.A.3: a coarse cell outside the patch is no multigrid
+    cell and adds nothing; the remaining weights are not renormalised, reading
+    D15) a constant correction c reaches a fine cell scaled by 3/4 for every
+    axis along which the cell touches the patch boundary, since the 27/9/3/1
+    weights factor into 3/4 (own coarse cell) and 1/4 (neighbour) per axis;
+    periodic grids wrap and reproduce c everywhere."""
+    shape = (6, 10, 8)                                # (n2, n1, n0)
+    cs = tuple(v // 2 for v in shape)
+    c = 2.5
+    uf = O.prolong_correct(np.zeros(shape), np.full(cs, c), np.zeros(cs), dirichlet=True)
+    k, j, i = np.indices(shape)
+    nb = sum(((ix == 0) | (ix == n - 1)).astype(int) for ix, n in ((i, shape[2]), (j, shape[1]),
+                                                                  (k, shape[0])))
+    assert np.abs(uf - c * 0.75 ** nb).max() < 1e-15
+    up = O.prolong_correct(np.zeros(shape), np.full(cs, c), np.zeros(cs), dirichlet=False)
+    assert np.abs(up - c).max() < 1e-15
+
+
 def test_face_restriction_exact_for_linear_faces():
     """Coarse patch boundary values (Sec. V.B.2 reading: the mean of the 4 fine
     face values covering a coarse face cell) reproduce a field linear along
