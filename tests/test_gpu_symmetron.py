@@ -44,6 +44,25 @@ def test_symmetron_matches_oracle(C, shape, sigma, seed, prec):
         assert s.hist[0] == pytest.approx(ref.hist[0], rel=1e-9)
 
 
+@pytest.mark.parametrize("ncyc", [1, 3])
+@pytest.mark.parametrize("shape,sigma,seed", [((32, 32, 32), 2.0, 91), ((16, 24, 40), 1.5, 92)])
+def test_fp64_vcycles_match_oracle_iterates(C, shape, sigma, seed, ncyc):
+    """After exactly ncyc FP64 V-cycles the GPU iterate equals the oracle's up
+    to rounding: the same sweeps, restriction (the coarse density included),
+    coarse operator, prolongation and coarsest rule, not only the same
+    fixed point."""
+    rho = synth.lognormal_density(shape, seed, sigma=sigma)
+    box = 0.5 * shape[2]
+    ref = S.solve(rho, box=box, tol=1e-30, max_cycles=ncyc, **P)
+    assert ref.cycles == ncyc and not ref.converged
+    chi = torch.empty(shape, dtype=torch.float64, device="cuda")
+    st, s = C.symmetron(dev(rho), chi, box=box, tol=1e-30, prec="fp64", initial_guess=0,
+                        max_vcycles=ncyc, **P)
+    assert st == 4 and s.vcycles == ncyc, s.as_dict()  # FR_ENOCONV: the iterate is returned
+    assert float(np.abs(host(chi) - ref.chi).max()) < 1e-10
+    assert s.res_rms == pytest.approx(ref.hist[-1], rel=1e-6)
+
+
 @pytest.mark.parametrize("tiling", [1, -1])
 @pytest.mark.parametrize("shape,sigma,seed", [((32, 32, 32), 2.0, 81), ((48, 34, 66), 1.5, 82),
                                               ((16, 130, 20), 1.0, 83)])

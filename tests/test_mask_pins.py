@@ -231,3 +231,48 @@ def test_ghost_relation_returns_the_ghost_value():
         assert np.abs(back - ug[ghost]).max() < 1e-12
         n += int(ghost.sum())
     assert n > 0
+
+
+def test_level_count_rule_by_hand():
+    """Masked level rule (reading of Sec. V.A.2: halve while every size stays
+    even and the halved size is >= 4, the coarser mask, the mean of the 8
+    children, keeps its outer layer masked and has an active cell), on cases
+    counted by hand."""
+    def block(n, lo, hi):
+        m = -np.ones((n, n, n))
+        m[lo:hi, lo:hi, lo:hi] = 1.0
+        return m
+    # 12^3 with the central 4^3 active: 12 -> 6 (6^3 has the central 2^3
+    # active); halving 6 would give 3 < 4
+    assert M.num_levels(block(12, 4, 8)) == 2
+    # 16^3 with a 2-cell masked margin: 16 -> 8 -> 4 (4^3: faces average to 0)
+    assert M.num_levels(block(16, 2, 14)) == 3
+    # 16^3 with a 1-cell margin: the 4^3 level would have active outer cells
+    assert M.num_levels(block(16, 1, 15)) == 2
+    # 10 -> 5 and 14 -> 7 (odd sizes end the series); 6 would halve to 3 < 4
+    assert M.num_levels(block(10, 1, 9)) == 2 and M.num_levels(block(14, 1, 13)) == 2
+    assert M.num_levels(block(6, 1, 5)) == 1
+
+
+def test_coarse_ghosts_keep_their_initial_values():
+    """On every coarse level the ghost cells (mask <= 0) hold the restriction of
+    the initial fine values for the whole solve (reading of Sec. V.B.2 for
+    masked levels): a V-cycle changes only active coarse cells."""
+    shape = (16, 16, 16)
+    rng = np.random.default_rng(8)
+    k, j, i = np.indices(shape)
+    r2 = ((i - 7.5) ** 2 + (j - 7.5) ** 2 + (k - 7.5) ** 2) / 20.0
+    m = np.clip(2.0 * np.exp(-r2) - 0.3, -1.0, 1.0)
+    m[[0, -1]], m[:, [0, -1]], m[:, :, [0, -1]] = -1.0, -1.0, -1.0
+    from oracle import oracle as _O
+    model = _O.Model(P["box"], 1, P["a"], P["omega_m"], P["fr0"])
+    u0 = 0.3 * np.sin(0.4 * i) + 0.2 * rng.uniform(-1, 1, shape) + model.ubar
+    rho = np.exp(rng.normal(0, 0.5, shape))
+    H = M.Hierarchy(u0, m, rho, 1.0 / 64, model)
+    assert len(H.lev) >= 2
+    before = [L.u.copy() for L in H.lev]
+    for _ in range(2):
+        M.vcycle(H, 0, 2, 2, 1e-10)
+    for L, b in zip(H.lev, before):
+        assert np.array_equal(L.u[~L.act], b[~L.act])
+    assert not np.array_equal(H.lev[1].u[H.lev[1].act], before[1][H.lev[1].act])
