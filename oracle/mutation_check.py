@@ -2,7 +2,7 @@
 library).
 
 Each entry plants one plausible mistake in an oracle file (``fr_oracle.c``,
-``symmetron.py``, ``masked.py``, ``poisson.py``, ``particles.py``: a wrong
+``oracle.py``, ``symmetron.py``, ``masked.py``, ``poisson.py``, ``particles.py``: a wrong
 constant, sign, index, weight or a dropped term) in a scratch copy of
 ``oracle/`` and ``tests/`` and runs that file's pin tests against it; a
 mistake that no pin catches is reported as a survivor.  Two survivors are
@@ -157,9 +157,19 @@ MUT_PARTICLES = [
  ("pa force sign", "out[:, d] -= w * g[d][iz[:, c], iy[:, b], ix[:, a]]", "out[:, d] += w * g[d][iz[:, c], iy[:, b], ix[:, a]]"),
 ]
 
+MUT_ORACLE_PY = [
+ ("tau coarse h", "return (residual(restrict(u), restrict(rho), h=2.0 * h, **P)", "return (residual(restrict(u), restrict(rho), h=h, **P)"),
+ ("tau sign", "            - restrict(residual(u, rho, h=h, **P)))", "            + restrict(residual(u, rho, h=h, **P)))"),
+ ("tau coarse rho", "return (residual(restrict(u), restrict(rho), h=2.0 * h, **P)", "return (residual(restrict(u), rho[::2, ::2, ::2], h=2.0 * h, **P)"),
+ ("levels patch h", "max_cycles=max_cycles, pre=pre, post=post, cap=cap, u0=u0, h=hp / 2.0,", "max_cycles=max_cycles, pre=pre, post=post, cap=cap, u0=u0, h=hp,"),
+ ("levels parent", "up, periodic, hp = out[p[\"parent\"]].u, False, hs[p[\"parent\"]]", "up, periodic, hp = dom.u, False, hs[p[\"parent\"]]"),
+ ("levels patch rho", "r = solve(p[\"rho\"], box=box,", "r = solve(np.ones_like(p[\"rho\"]), box=box,"),
+]
+
 # oracle file -> (pin tests, mutants)
 TARGETS = {
     "fr_oracle.c": (["tests/test_oracle_pins.py"], MUT_C),
+    "oracle.py": (["tests/test_oracle_pins.py"], MUT_ORACLE_PY),
     "symmetron.py": (["tests/test_symmetron_pins.py"], MUT_SYMMETRON),
     "masked.py": (["tests/test_mask_pins.py"], MUT_MASKED),
     "poisson.py": (["tests/test_poisson_pins.py"], MUT_POISSON),

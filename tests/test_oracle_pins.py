@@ -14,7 +14,8 @@ sign, a wrong index or a transposed operand.
 * FAS solution equals a dense-Jacobian Newton root (8^3, periodic and patch).
 * restriction / prolongation identities; weights 27/9/3/1 over 64.
 * multigrid convergence vs single-grid relaxation (Sec. VI.D.1).
-* refinement patches (Sec. VI.B.1): edge error and peak improvement.
+* refinement patches (Sec. VI.B.1): edge error and peak improvement, two and
+  three levels.
 * CIC (Sec. VI.C): mean density 1, centred particle, translation, brute force.
 """
 import os
@@ -353,6 +354,29 @@ def test_two_level_gaussian_patch():
     # boundary interpolation error: small, as the paper reports at refinement edges
     assert err_p.max() < 0.02
     assert err_p[0].max() < 20 * golden("refinement_edge_error")
+
+
+def test_three_level_gaussian_patch():
+    """Sec. VI.B's nested refinement on the spherical Gaussian: a level-2
+    patch inside the level-1 patch takes its boundary from that patch (not
+    from the domain grid) and is more accurate at the peak than its parent,
+    with a small error at its edges."""
+    P = dict(box=256.0, a=1.0, omega_m=0.24, fr0=1e-5)
+    G = dict(amp=0.99, width=0.06, centre=(0.5, 0.5, 0.5))
+    N, n, o1, o2 = 32, 16, 12, 4                   # level-2 patch over level-1 cells 4..11
+    rho0, _ = PF.spherical_gaussian_field(N, **P, **G)
+    rho1, ue1 = PF.spherical_gaussian_patch(2 * o1, n, 2 * N, **P, **G)
+    lo2 = 2 * (2 * o1 + o2)
+    rho2, ue2 = PF.spherical_gaussian_patch(lo2, n, 4 * N, **P, **G)
+    dom, (p1, p2) = O.solve_levels(
+        rho0, [dict(parent=-1, origin=(o1, o1, o1), rho=rho1),
+               dict(parent=0, origin=(o2, o2, o2), rho=rho2)], tol=1e-10, **P)
+    assert p1.converged and p2.converged
+    e1, e2 = np.abs(p1.u - ue1), np.abs(p2.u - ue2)
+    c = n // 2
+    assert e2[c - 1:c + 1, c - 1:c + 1, c - 1:c + 1].max() < \
+        e1[c - 1:c + 1, c - 1:c + 1, c - 1:c + 1].max()
+    assert e2.max() < 0.02
 
 
 def _faces_from(u, lo, n):
