@@ -86,6 +86,11 @@ MUT_C = [
  ("cic weight", "w *= hi ? t[d] : (1.0 - t[d]);", "w *= hi ? (1.0 - t[d]) : t[d];"),
  ("cic mass", "double mass = (double)nc / (double)np;", "double mass = 1.0;"),
  ("face_axes", "*q = (ax == 2) ? 1 : 2;", "*q = (ax == 1) ? 1 : 2;"),
+ ("rms norm", "return n > 0 ? sqrt(s / (double)n) : 0.0;", "return n > 0 ? sqrt(s) : 0.0;"),
+ ("cap clamp sign", "                    if (du > cap)\n                        du = cap;", "                    if (du > cap)\n                        du = -cap;"),
+ ("residual drops f", "d[ci] = lv - (L->f ? L->f[ci] : 0.0);", "d[ci] = lv;"),
+ ("pinterp no wrap", "cc[d] = ((cc[d] % np_[d]) + np_[d]) % np_[d];", "cc[d] = cc[d] < 0 ? 0 : np_[d] - 1;"),
+ ("cic truncation", "double fl = floor(x);", "double fl = (double)(long)x;"),
  ("face_value idx", "return L->ub[L->foff[f] + (long)c[q] * L->n[p] + c[p]];", "return L->ub[L->foff[f] + (long)c[p] * L->n[q] + c[q]];"),
 ]
 

@@ -440,6 +440,23 @@ def test_patch_bc_exact_for_linear_parent():
         O.patch_bc(up, (0, 2, 4), n, parent_periodic=False)
 
 
+def test_patch_bc_wraps_a_periodic_parent():
+    """A patch on a periodic parent that crosses the domain edge is set up
+    from the periodic continuation of the parent: the same as a non-periodic
+    parent padded by one layer of wrapped cells, with the origin shifted by
+    one parent cell."""
+    rng = np.random.default_rng(12)
+    npar = (8, 10, 12)                            # (n2, n1, n0)
+    up = rng.normal(size=npar)
+    n = (6, 8, 10)
+    for org in [(0, 0, 0), (9, 7, 5), (8, 1, 6)]:   # (x, y, z); past the upper edge too
+        u0, ub = O.patch_bc(up, org, n, parent_periodic=True)
+        o2 = (org[0] % npar[2] + 1, org[1] % npar[1] + 1, org[2] % npar[0] + 1)
+        big = np.pad(up, ((1, n[0]), (1, n[1]), (1, n[2])), mode="wrap")  # index 0 = cell -1
+        v0, vb = O.patch_bc(big, o2, n, parent_periodic=False)
+        assert np.array_equal(u0, v0) and np.array_equal(ub, vb)
+
+
 # ---------------------------------------------------------------- CIC
 def test_cic_mean_density_is_one():
     pos = synth.uniform_positions(5000, 3)
