@@ -5,11 +5,12 @@ Each entry plants one plausible mistake in an oracle file (``fr_oracle.c``,
 ``oracle.py``, ``symmetron.py``, ``masked.py``, ``poisson.py``, ``particles.py``: a wrong
 constant, sign, index, weight or a dropped term) in a scratch copy of
 ``oracle/`` and ``tests/`` and runs that file's pin tests against it; a
-mistake that no pin catches is reported as a survivor.  Two survivors are
+mistake that no pin catches is reported as a survivor.  One survivor is
 expected (``EXPECTED_SURVIVORS``): the f(R) coarse density set to 1, whose
 terms cancel between L^H(u^H) and L^H(R u^h) in the FAS right-hand side
-(Sec. V.B.2), and the symmetron's coarse density taken by injection, which
-changes the iteration path but not the converged solution.
+(Sec. V.B.2), so that mutant computes the same result.  Mistakes that change
+only the iteration path (level rules, sweep order, clamps, coarse-level set-up)
+are caught by pins that write those steps out by hand.
 
     python oracle/mutation_check.py --workdir <scratch folder> [name ...]
 """
@@ -110,6 +111,9 @@ MUT_SYMMETRON = [
  ("sy coarse A", "AH = 0.25 * A", "AH = 0.5 * A"),
  ("sy fas rhs sign", "fH = operator(uR, rhoH, AH, s) - restrict(d)", "fH = operator(uR, rhoH, AH, s) + restrict(d)"),
  ("sy correction sign", "chi = chi + prolong(uH - uR)", "chi = chi + prolong(uR - uH)"),
+ ("sy levels >= 4", "while all(v % 2 == 0 and v // 2 >= 4 for v in n):", "while all(v % 2 == 0 and v // 2 >= 2 for v in n):"),
+ ("sy cap clamp", "d = np.clip(d, -cap, cap)\n            chi[m] += d[m]", "d = np.clip(d, -cap, 0.5 * cap)\n            chi[m] += d[m]"),
+ ("sy coarsest rule", "lim = max(1e-3 * r0, 0.1 * tol)", "lim = max(1e-1 * r0, 0.1 * tol)"),
  ("sy coarse rho injection", "rhoH = restrict(rho)", "rhoH = rho[::2, ::2, ::2]"),
 ]
 
@@ -131,6 +135,9 @@ MUT_MASKED = [
  ("ma prolong masked fine", "return np.where(fine_act, out, 0.0)", "return out"),
  ("ma coarse ghosts overwritten", "uR = np.where(C.act, restrict_mean(L.u), C.u)", "uR = restrict_mean(L.u)"),
  ("ma fas rhs sign", "C.f = np.where(C.act, LH - restrict_active(d, L.act), 0.0)", "C.f = np.where(C.act, LH + restrict_active(d, L.act), 0.0)"),
+ ("ma coarse masks by injection", "u0, mm, rr, hh = restrict_mean(u0), restrict_mean(mm), restrict_mean(rr), 2 * hh", "u0, mm, rr, hh = restrict_mean(u0), mm[::2, ::2, ::2], restrict_mean(rr), 2 * hh"),
+ ("ma coarse h", "u0, mm, rr, hh = restrict_mean(u0), restrict_mean(mm), restrict_mean(rr), 2 * hh", "u0, mm, rr, hh = restrict_mean(u0), restrict_mean(mm), restrict_mean(rr), hh"),
+ ("ma colour order", "for colour in (0, 1):\n        Lv, dL = cell_terms(L, model)", "for colour in (1, 0):\n        Lv, dL = cell_terms(L, model)"),
  ("ma levels >= 4", "while all(s % 2 == 0 and s // 2 >= 4 for s in m.shape):", "while all(s % 2 == 0 and s // 2 >= 2 for s in m.shape):"),
 ]
 
@@ -185,10 +192,6 @@ TARGETS = {
 EXPECTED_SURVIVORS = {
     # equivalent: the coarse density terms cancel in the FAS right-hand side
     "coarse rho = 1",
-    # the coarse density of the symmetron enters only the coarse correction's
-    # linearisation: the iteration path changes, the converged solution does
-    # not (the GPU is held to the oracle's path by fixed-cycle iterate tests)
-    "sy coarse rho injection",
 }
 
 

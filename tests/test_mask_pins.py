@@ -276,3 +276,45 @@ def test_coarse_ghosts_keep_their_initial_values():
     for L, b in zip(H.lev, before):
         assert np.array_equal(L.u[~L.act], b[~L.act])
     assert not np.array_equal(H.lev[1].u[H.lev[1].act], before[1][H.lev[1].act])
+
+
+def test_hierarchy_masks_cell_sizes_and_sweep_by_hand():
+    """Masked levels (reading of Sec. V.A.2): each coarse mask, density and
+    initial u is the mean of the 8 children (written out as loops), and the
+    cell size doubles per level.  One vectorised Newton-Gauss-Seidel sweep
+    equals the sweep written cell by cell over the active cells, red
+    ((i + j + k) even) in index order first, then black."""
+    from oracle import oracle as _O
+    shape = (8, 12, 16)
+    rng = np.random.default_rng(14)
+    m = _irregular_mask(shape, 15, frac=0.7)
+    model = _O.Model(P["box"], 1, P["a"], P["omega_m"], P["fr0"])
+    u0 = 0.2 * rng.standard_normal(shape) + model.ubar
+    rho = np.exp(rng.normal(0, 0.5, shape))
+    H = M.Hierarchy(u0, m, rho, 1.0 / 64, model, nlevels=2)
+    F, C = H.lev
+    assert C.h == 2 * F.h and C.pre == pytest.approx(F.pre / 4, rel=1e-15)
+    for K in range(shape[0] // 2):
+        for J in range(shape[1] // 2):
+            for I in range(shape[2] // 2):
+                blk = (slice(2 * K, 2 * K + 2), slice(2 * J, 2 * J + 2), slice(2 * I, 2 * I + 2))
+                assert C.m[K, J, I] == pytest.approx(m[blk].sum() / 8, abs=1e-15)
+                assert C.rho[K, J, I] == pytest.approx(rho[blk].sum() / 8, rel=1e-14)
+                assert C.u[K, J, I] == pytest.approx(u0[blk].sum() / 8, rel=1e-14)
+    # the sweep, cell by cell
+    F.f = 1e-3 * rng.standard_normal(shape)
+    ref = F.u.copy()
+    n2, n1, n0 = shape
+    for colour in (0, 1):
+        for k in range(n2):
+            for j in range(n1):
+                for i in range(n0):
+                    if (i + j + k) % 2 != colour or not F.act[k, j, i]:
+                        continue
+                    F.u, keep = ref, F.u
+                    Lv, dL = M.cell_terms(F, model)
+                    F.u = keep
+                    du = -(Lv[k, j, i] - F.f[k, j, i]) / dL[k, j, i]
+                    ref[k, j, i] += min(max(du, -1.0), 1.0)
+    M.ngs_sweep(F, model)
+    assert np.abs(F.u - ref).max() < 1e-13

@@ -175,3 +175,90 @@ def test_manufactured_solution_through_the_multigrid():
     r = S.solve(rho, box=16.0, tol=1e-13, **P)
     assert r.converged and r.cycles <= 15
     assert np.abs(r.chi - chi_s).max() < 1e-11
+
+
+def test_sweep_equals_cell_by_cell_red_then_black():
+    """One vectorised sweep equals Newton-Gauss-Seidel written cell by cell,
+    red cells ((i + j + k) even) in index order first, then black, each
+    update clamped to |d chi| <= cap; a large start makes the clamp act."""
+    rng = np.random.default_rng(21)
+    shape = (4, 6, 8)
+    rho = synth.lognormal_density(shape, 5, sigma=1.0)
+    A, s = S.coefficients(4.0, shape[2], **P)
+    chi0 = rng.uniform(-2.0, 3.0, shape)
+    f = 0.1 * rng.standard_normal(shape)
+    cap = 0.25
+    got = S.smooth(chi0, rho, f, A, s, 1, cap=cap)
+    ref = chi0.copy()
+    n2, n1, n0 = shape
+    hit = 0
+    for colour in (0, 1):
+        for k in range(n2):
+            for j in range(n1):
+                for i in range(n0):
+                    if (i + j + k) % 2 != colour:
+                        continue
+                    nb = sum(ref[(k + dk) % n2, (j + dj) % n1, (i + di) % n0]
+                             for dk, dj, di in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                                                (0, 0, 1), (0, 0, -1)))
+                    c = ref[k, j, i]
+                    L = A * (nb - 6.0 * c) - ((s * rho[k, j, i] - 1.0) * c + c ** 3)
+                    dL = -6.0 * A - ((s * rho[k, j, i] - 1.0) + 3.0 * c * c)
+                    d = -(L - f[k, j, i]) / dL
+                    hit += abs(d) > cap
+                    ref[k, j, i] = c + min(max(d, -cap), cap)
+    assert hit > 10
+    assert np.abs(got - ref).max() < 1e-12
+
+
+def test_level_rule_and_coarsest_rule_by_hand():
+    """Readings stated in the oracle: levels halve while every size is even and
+    the halved size is >= 4 (16 -> 8 -> 4; 12 -> 6, since 6 would halve to 3;
+    odd sizes stop); the coarsest level is relaxed until its rms residual is
+    <= max(1e-3 x its initial rms, 0.1 tol), and stops at the first sweep that
+    reaches it."""
+    assert S.num_levels((16, 16, 16)) == 3
+    assert S.num_levels((12, 12, 12)) == 2
+    assert S.num_levels((16, 8, 24)) == 2 and S.num_levels((10, 16, 16)) == 2
+    assert S.num_levels((6, 16, 16)) == 1
+    rho = synth.lognormal_density((4, 4, 4), 9, sigma=1.0)
+    A, s = S.coefficients(2.0, 4, **P)
+    chi = np.full((4, 4, 4), 2.0)
+    f = np.zeros_like(rho)
+    rms = lambda c: float(np.sqrt(np.mean((S.operator(c, rho, A, s) - f) ** 2)))  # noqa: E731
+    r0 = rms(chi)
+    out = S._coarsest(chi, rho, f, A, s, 1e-8, 1.0)
+    lim = max(1e-3 * r0, 1e-9)
+    assert rms(out) <= lim
+    c, n = chi.copy(), 0
+    while rms(c) > lim:
+        c = S.smooth(c, rho, f, A, s, 1, 1.0)
+        n += 1
+    assert n >= 2 and np.array_equal(c, out)
+
+
+def test_two_level_cycle_by_hand():
+    """One two-level FAS cycle (Sec. V.B.2) written out step by step: pre
+    sweeps; d = L(chi) - f; coarse chi = R chi, coarse density = the mean of
+    the 8 children (loops), coarse A = A / 4 (twice the cell size); coarse
+    right-hand side L^H(R chi) - R d; coarse solve; chi += P(chi^H - R chi);
+    post sweeps."""
+    rng = np.random.default_rng(31)
+    shape = (8, 8, 12)
+    rho = synth.lognormal_density(shape, 6, sigma=1.0)
+    A, s = S.coefficients(6.0, shape[2], **P)
+    chi0 = 0.9 + 0.1 * rng.standard_normal(shape)
+    f = np.zeros(shape)
+    got = S.vcycle(chi0, rho, f, A, s, 2, pre=2, post=1, cap=1.0, tol=1e-10)
+    c = S.smooth(chi0, rho, f, A, s, 2)
+    d = S.operator(c, rho, A, s) - f
+    rhoH = np.zeros((4, 4, 6))
+    for K in range(4):
+        for J in range(4):
+            for I in range(6):
+                rhoH[K, J, I] = rho[2 * K:2 * K + 2, 2 * J:2 * J + 2, 2 * I:2 * I + 2].mean()
+    uR = S.restrict(c)
+    fH = S.operator(uR, rhoH, A / 4.0, s) - S.restrict(d)
+    uH = S._coarsest(uR.copy(), rhoH, fH, A / 4.0, s, 1e-10, 1.0)
+    ref = S.smooth(c + S.prolong(uH - uR), rho, f, A, s, 1)
+    assert np.abs(got - ref).max() < 1e-13
