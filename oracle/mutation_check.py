@@ -92,6 +92,9 @@ MUT_C = [
  ("residual drops f", "d[ci] = lv - (L->f ? L->f[ci] : 0.0);", "d[ci] = lv;"),
  ("pinterp no wrap", "cc[d] = ((cc[d] % np_[d]) + np_[d]) % np_[d];", "cc[d] = cc[d] < 0 ? 0 : np_[d] - 1;"),
  ("cic truncation", "double fl = floor(x);", "double fl = (double)(long)x;"),
+ ("ngs black first", "                    if ((i + j + k) % 2 != colour)\n                        continue;\n                    long ci = idx3(L->n, i, j, k);\n                    double lv, dl;", "                    if ((i + j + k + 1) % 2 != colour)\n                        continue;\n                    long ci = idx3(L->n, i, j, k);\n                    double lv, dl;"),
+ ("coarsest rule", "double thr = fmax(1e-3 * r0, 0.1 * H->tol);", "double thr = fmax(1e-1 * r0, 0.1 * H->tol);"),
+ ("post count", "    for (int s = 0; s < H->post_sw; s++)\n        ngs_sweep(L, &H->m, H->cap);\n}", "    for (int s = 0; s < H->pre_sw; s++)\n        ngs_sweep(L, &H->m, H->cap);\n}"),
  ("face_value idx", "return L->ub[L->foff[f] + (long)c[q] * L->n[p] + c[p]];", "return L->ub[L->foff[f] + (long)c[p] * L->n[q] + c[q]];"),
 ]
 

@@ -304,6 +304,63 @@ def test_face_restriction_exact_for_linear_faces():
     assert np.abs(coarse - expect).max() < 1e-14
 
 
+def test_sweep_equals_cell_by_cell_red_then_black():
+    """One oracle sweep equals Newton-Gauss-Seidel written cell by cell from
+    the single-cell operator: red cells ((i + j + k) even) in index order
+    first, then black, u <- u - (L - f) / (dL/du) clamped to |du| <= cap (the
+    clamp acts from this start)."""
+    rng = np.random.default_rng(41)
+    shape = (4, 4, 6)
+    rho = synth.lognormal_density(shape, 3, sigma=1.0)
+    u0 = rng.uniform(-2.0, 1.0, shape)
+    f = 0.01 * rng.standard_normal(shape)
+    h, cap = 1.0 / 16, 0.25
+    got = O.smooth(u0, rho, 1, h=h, f=f, cap=cap, **F5_64)
+    ref = u0.copy()
+    hit = 0
+    for colour in (0, 1):
+        for k in range(shape[0]):
+            for j in range(shape[1]):
+                for i in range(shape[2]):
+                    if (i + j + k) % 2 != colour:
+                        continue
+                    L, dL = O.cell_op(ref, rho, i, j, k, h=h, **F5_64)
+                    du = -(L - f[k, j, i]) / dL
+                    hit += abs(du) > cap
+                    ref[k, j, i] += min(max(du, -cap), cap)
+    assert hit > 5
+    assert np.abs(got - ref).max() < 1e-12
+
+
+def test_two_level_vcycle_by_hand():
+    """One two-level FAS V-cycle of the oracle (Sec. V.B.2) equals its steps
+    written out with the single-step entry points: pre sweeps; d = L(u);
+    u^H = R u, f^H = L^H(R u) - R d at twice the cell size with density R rho;
+    coarsest solve (sweeps until rms(L^H - f^H) <= max(1e-3 x its initial
+    rms, 0.1 tol), at least one); u += P(u^H - R u); post sweeps."""
+    rng = np.random.default_rng(42)
+    shape = (8, 8, 12)
+    assert O.num_levels(shape) == 2
+    rho = synth.lognormal_density(shape, 4, sigma=1.0)
+    u0 = 0.3 * rng.standard_normal(shape)
+    h, tol, pre, post = 1.0 / 24, 1e-9, 2, 1
+    got = O.solve(rho, u0=u0, h=h, tol=tol, pre=pre, post=post, ncycles=1, **F5_64).u
+    rms = lambda d: float(np.sqrt(np.mean(d * d)))  # noqa: E731
+    u = O.smooth(u0, rho, pre, h=h, **F5_64)
+    d = O.residual(u, rho, h=h, **F5_64)
+    uR, rhoH = O.restrict(u), O.restrict(rho)
+    fH = O.residual(uR, rhoH, h=2 * h, **F5_64) - O.restrict(d)
+    thr = max(1e-3 * rms(O.residual(uR, rhoH, h=2 * h, f=fH, **F5_64)), 0.1 * tol)
+    uH = uR.copy()
+    for _ in range(500):
+        uH = O.smooth(uH, rhoH, 1, h=2 * h, f=fH, **F5_64)
+        if rms(O.residual(uH, rhoH, h=2 * h, f=fH, **F5_64)) <= thr:
+            break
+    u = O.prolong_correct(u, uH, uR)
+    ref = O.smooth(u, rho, post, h=h, **F5_64)
+    assert np.abs(got - ref).max() < 1e-11
+
+
 def test_level_count_rule():
     assert O.num_levels((32, 32, 32)) == 4  # 32 16 8 4
     assert O.num_levels((512, 512, 512)) == 8
