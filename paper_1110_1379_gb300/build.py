@@ -47,22 +47,28 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
               "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
     procs = []
     objs = []
-    for s in SOURCES:
-        obj = os.path.join(BUILD, s.replace(".cu", f".{os.getpid()}.o"))
-        objs.append(obj)
-        cmd = common + ["-c", os.path.join(CSRC, s), "-o", obj]
-        if verbose:
-            print(" ".join(cmd))
-        procs.append(subprocess.Popen(cmd))
-    for p in procs:
-        if p.wait() != 0:
+    try:
+        for s in SOURCES:
+            obj = os.path.join(BUILD, s.replace(".cu", f".{os.getpid()}.o"))
+            objs.append(obj)
+            cmd = common + ["-c", os.path.join(CSRC, s), "-o", obj]
+            if verbose:
+                print(" ".join(cmd))
+            procs.append(subprocess.Popen(cmd))
+        failed = [p.wait() != 0 for p in procs]
+        if any(failed):
             raise RuntimeError("nvcc failed")
-    tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
-    subprocess.run(link, check=True)
-    os.replace(tmp, LIB)
-    for o in objs:
-        os.remove(o)
+        tmp = LIB + f".tmp{os.getpid()}"
+        link = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        subprocess.run(link, check=True)
+        os.replace(tmp, LIB)
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.wait()
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 
