@@ -214,11 +214,16 @@ int fr_cic_assign(frmg_ctx *ctx, const double *pos, long long np, const int dims
                   double *density_out, void *stream);
 
 /* ---- Single-step entry points (one level, FP64, the same kernels as the
- *      solver uses); parity checks call these step by step. ---- */
+ *      solver uses); parity checks call these step by step.  Arrays follow
+ *      the conventions above (caller-owned, device or host, [n2][n1][n0]);
+ *      bad dims, sizes or model parameters give FR_EINVAL, checked before
+ *      anything is written. ---- */
 
-/* nsweeps red-black Newton-Gauss-Seidel sweeps (red = (i+j+k) even first) on
- * L(u) = f (f NULL = 0); cell size h; ub NULL = periodic, else the six packed
- * boundary faces (-x,+x,-y,+y,-z,+z; face normal to axis a indexed by the other
+/* nsweeps red-black Newton-Gauss-Seidel sweeps (Sec. V.B.1: u <- u - (L - f) /
+ * (dL/du), the step clamped to |du| <= step_cap; red = (i+j+k) even first) on
+ * L(u) = f (f NULL = 0), u updated in place; cell size h; ub NULL = periodic,
+ * else the six packed boundary faces of a patch (Eq. u_i-1jk with mask ratio
+ * -1; faces -x,+x,-y,+y,-z,+z; the face normal to axis a indexed by the other
  * axes p < q as c[q]*n[p] + c[p]). */
 int fr_smooth(frmg_ctx *ctx, double *u, const double *density, const double *f,
               const int dims[3], double h, double box_mpc_h, double a, double omega_m,
@@ -236,7 +241,8 @@ int fr_smooth_f32(frmg_ctx *ctx, float *u, const float *bg, const float *f, cons
                   double h, double box_mpc_h, double a, double omega_m, double fr0_abs,
                   const float *ub, int nsweeps, double step_cap, int tiled, void *stream);
 
-/* d = L(u) - f on one level (arguments as fr_smooth). */
+/* d = L(u) - f on one level (Sec. IV Eq. discrete_fR, with patch faces
+ * Eq. bc_modified_fR_op; arguments as fr_smooth); d: dims cells, overwritten. */
 int fr_residual(frmg_ctx *ctx, const double *u, const double *density, const double *f,
                 const int dims[3], double h, double box_mpc_h, double a, double omega_m,
                 double fr0_abs, const double *ub, double *d, void *stream);
@@ -249,23 +255,32 @@ int fr_residual_df(frmg_ctx *ctx, const double *u, const double *density, const 
                    double h, double box_mpc_h, double a, double omega_m, double fr0_abs,
                    const double *ub, double *d, void *stream);
 
-/* coarse = average of the 8 children of each coarse cell (full weighting on a
- * cell-centred grid); fine dims even. */
+/* Restriction of Sec. V.B.2 (read as the average of the 8 children of each
+ * coarse cell): coarse [n2/2][n1/2][n0/2] from fine [n2][n1][n0], overwritten;
+ * every fine dim even and >= 2. */
 int fr_restrict(frmg_ctx *ctx, const double *fine, const int dims_fine[3], double *coarse,
                 void *stream);
 
 /* u_fine += P(uH - uR), trilinear 27/9/3/1 over 64 (Sec. V.A.3, V.B.3);
- * dirichlet != 0: coarse neighbours outside the grid contribute 0. */
+ * uH and uR have dims_fine / 2; periodic wrap, or with dirichlet != 0 coarse
+ * neighbours outside the grid contribute 0 (no renormalisation). */
 int fr_prolong_correct(frmg_ctx *ctx, double *u_fine, const int dims_fine[3], const double *uH,
                        const double *uR, int dirichlet, void *stream);
 
-/* Patch boundary set-up: u_init (patch cells) and ub (packed faces) from the
- * parent solution uparent (dims_parent; periodic != 0 wraps). */
+/* Patch boundary set-up (Sec. V.A.1, V.B.1: ghost values from the parent):
+ * a patch of n[3] fine cells (refinement factor 2) whose lower corner is
+ * parent cell origin[3] (x, y, z).  u_init (n cells) and every ghost value are
+ * the trilinear 27/9/3/1 interpolation of uparent (dims_parent); ub (packed
+ * faces as fr_smooth) receives u_b = (ghost + first interior) / 2.  periodic
+ * != 0 wraps the parent; otherwise a stencil leaving it gives FR_EINVAL
+ * (found while interpolating: device outputs may then hold partial values,
+ * host outputs are left unchanged). */
 int fr_patch_bc(frmg_ctx *ctx, const double *uparent, const int dims_parent[3], int periodic,
                 const int origin[3], const int n[3], double *u_init, double *ub, void *stream);
 
-/* Run exactly ncycles FAS V-cycles (no convergence test) on one periodic grid
- * in the given precision; stats->res_rms is the FP64 residual afterwards. */
+/* Run exactly ncycles FAS V-cycles of Sec. V.B.2 (no convergence test) on one
+ * periodic grid in the precision of opts, u_inout updated in place;
+ * stats->res_rms is the FP64 residual afterwards. */
 int fr_vcycles(frmg_ctx *ctx, const double *density, const int dims[3], double box_mpc_h,
                double a, double omega_m, double fr0_abs, double *u_inout, int ncycles,
                const fr_opts *opts, fr_stats *stats, void *stream);
