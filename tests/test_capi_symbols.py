@@ -106,3 +106,20 @@ def test_no_gpu_fails_loudly(lib):
         frmg.Context(0)
     assert ei.value.status == frmg.FR_ECUDA
     assert "fr_ctx_create" in str(ei.value)
+
+
+def test_status_strings_name_every_code(lib):
+    """fr_status_string names each fr_status code of the header and falls back
+    for unknown values; the binding's constants match the header's enum."""
+    from paper_1110_1379_gb300 import frmg
+    h = frmg.load()
+    src = open(os.path.join(ROOT, "include", "frmg.h")).read()
+    codes = dict((n, int(v)) for n, v in re.findall(r"\b(FR_E?[A-Z]+) = (\d+)", src))
+    assert codes["FR_OK"] == 0 and len(codes) >= 7
+    for name, v in codes.items():
+        if name in ("FR_FP64", "FR_MIXED"):
+            continue
+        assert getattr(frmg, name) == v
+        assert h.fr_status_string(v).decode().startswith(name)
+    for v in (-1, 99):
+        assert h.fr_status_string(v) == b"unknown status"
