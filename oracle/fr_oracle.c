@@ -23,6 +23,30 @@
  * Readings where the paper is silent (restriction operator, level count,
  * coarsest solve, Newton step cap, norm) are marked "Reading:" below.
  *
+ * Pins (tests/test_oracle_pins.py; no function here is unpinned):
+ *   model_init        test_minus_rbar_41, test_background_matches_paper_fields,
+ *                     test_homogeneous_converges_to_background
+ *   cell_op           test_algebraic_limit, test_linear_limit_fft,
+ *                     test_point_mass_far_field_is_linear_yukawa,
+ *                     test_sine_closed_form_second_order, test_gaussian_closed_form_converges,
+ *                     test_flux_terms_telescope, test_newton_derivative_central_difference
+ *   ngs_sweep         test_sweep_equals_cell_by_cell_red_then_black
+ *   restrict_avg      test_restriction_identities
+ *   restrict_faces    test_face_restriction_exact_for_linear_faces
+ *   prolong_add       test_prolongation_weights_are_the_papers,
+ *                     test_prolongation_exact_for_linear_fields,
+ *                     test_prolongation_on_a_patch_drops_outside_cells
+ *   count_levels      test_level_count_rule
+ *   vcycle, coarsest  test_two_level_vcycle_by_hand, test_vcycle_beats_single_grid,
+ *                     test_dense_newton_matches_fas_periodic / _patch
+ *   orc_patch_bc      test_patch_bc_exact_for_linear_parent,
+ *                     test_patch_bc_wraps_a_periodic_parent,
+ *                     test_two_level_gaussian_patch, test_three_level_gaussian_patch,
+ *                     test_patch_with_exact_boundary_reproduces_full_grid
+ *   orc_cic           test_cic_mean_density_is_one,
+ *                     test_cic_centred_particle_and_translation, test_cic_brute_force
+ * oracle/mutation_check.py plants mistakes in this file and checks that a pin fails.
+ *
  * Layout: every field is [n2][n1][n0], x (index 0) fastest.
  * Boundary values of a patch are six packed faces in the order
  * -x, +x, -y, +y, -z, +z; the face normal to axis `ax` is indexed by the two

@@ -32,6 +32,19 @@ code).  Every cell of the box's outer layer must be a ghost.
 Values in and out are the shifted variable u = ln(f_R / fbar_R) of ``oracle.py``;
 the arithmetic is in the paper's u~ = u + ubar.  Vectorised over one colour of
 the red-black ordering at a time (cells of one colour do not couple).
+
+Pins (tests/test_mask_pins.py; no function here is unpinned): cell_terms and
+boundary_values by test_box_mask_is_the_patch_operator,
+test_zero_ghost_mask_is_the_unmodified_operator,
+test_derivative_matches_finite_differences_for_any_ratio,
+test_homogeneous_state_is_exact_for_any_mask and
+test_ghost_relation_returns_the_ghost_value; restrict_active and
+prolong_masked by test_masked_transfers_by_brute_force; num_levels, the
+hierarchy and ngs_sweep by test_level_count_rule_by_hand and
+test_hierarchy_masks_cell_sizes_and_sweep_by_hand; vcycle and solve by
+test_coarse_ghosts_keep_their_initial_values,
+test_multigrid_equals_brute_force_newton and
+test_spherical_region_converges_at_second_order.
 """
 from __future__ import annotations
 

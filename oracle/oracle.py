@@ -14,6 +14,13 @@ u~ = ln(-a^2 f_R) internally.
 ``dense_newton`` is an independent brute force (Sec. V.B.1's Newton step on the
 whole grid at once): it solves L(u) = 0 with the full Jacobian and
 ``numpy.linalg.solve``; it shares only the residual evaluation with the FAS path.
+
+Pins (tests/test_oracle_pins.py; the C functions' pins are listed in
+fr_oracle.c): truncation_error by test_truncation_error_vanishes_on_homogeneous_solution
+and test_truncation_error_is_second_order; solve_levels by
+test_two_level_gaussian_patch and test_three_level_gaussian_patch; dense_newton
+by test_dense_newton_matches_fas_periodic / _patch (two independent routes to
+the same root).
 """
 from __future__ import annotations
 

@@ -21,6 +21,12 @@ are the standard ones it refers to (Hockney & Eastwood):
   with the assignment weights.
 
 ``numpy.add.at`` (an unbuffered scatter-add) performs the deposits.
+
+Pins (tests/test_particle_pins.py; no function here is unpinned): assign by
+test_mass_conservation, test_cell_centre_weights, test_translation_by_one_cell
+and test_tsc_is_cic_widened_by_a_cell; gradient by test_gradient_of_cosine_mode;
+forces by test_force_at_cell_centre_closed_form and
+test_no_self_force_and_equal_opposite_pair.
 """
 from __future__ import annotations
 

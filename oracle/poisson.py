@@ -25,6 +25,12 @@ Everything here follows Li, Zhao, Teyssier & Koyama (arXiv:1110.1379):
 
 Values in and out are the shifted f(R) variable u = ln(f_R / fbar_R) (as in
 ``oracle.py``) and Phi in code units (box side 1, h = 1/N).
+
+Pins (tests/test_poisson_pins.py; no function here is unpinned): source by
+test_source_limits and test_source_mean_at_converged_fR_solution; laplacian
+by test_stencil_explicit_sums and test_patch_ghost_rule_exact_for_linear_fields;
+eigenvalues and solve_periodic by test_fft_solution_satisfies_stencil;
+solve_patch by test_patch_solver_against_dense_stencil_matrix.
 """
 from __future__ import annotations
 

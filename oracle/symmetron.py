@@ -44,6 +44,19 @@ by 1e-3 (or below 0.1 tol), at most 500 sweeps.
 Vectorised red-black sweeps are exact: a cell's update reads only its own
 value and neighbours of the other colour, so updating every cell of one
 colour at once equals updating them one by one.
+
+Pins (tests/test_symmetron_pins.py; no function here is unpinned):
+coefficients and background by test_coefficients_closed_form and
+test_homogeneous_solution_from_random_start; operator and derivative by
+test_operator_sums_to_the_local_terms,
+test_newton_derivative_by_finite_differences,
+test_linear_limit_matches_fft_solution, test_short_range_limit_is_the_local_minimum
+and test_screening_in_dense_cells; smooth by
+test_sweep_equals_cell_by_cell_red_then_black; restrict and prolong by
+test_transfer_operators; num_levels and the coarsest rule by
+test_level_rule_and_coarsest_rule_by_hand; vcycle and solve by
+test_two_level_cycle_by_hand, test_fas_matches_dense_newton_brute_force and
+test_manufactured_solution_through_the_multigrid.
 """
 from __future__ import annotations
 
