@@ -51,3 +51,20 @@ def test_named_paths_exist(doc):
         if not any(os.path.exists(c) for c in cands):
             missing.append(n)
     assert not missing, missing
+
+
+def test_oracle_pin_maps_name_existing_tests():
+    """The pin maps in the oracle files' headers name pin tests that exist."""
+    tests = ""
+    for path in glob.glob(os.path.join(ROOT, "tests", "test_*.py")):
+        tests += open(path).read()
+    defined = set(re.findall(r"^def (test_\w+)", tests, flags=re.M))
+    for name in ("fr_oracle.c", "oracle.py", "masked.py", "symmetron.py", "poisson.py",
+                 "particles.py"):
+        head = open(os.path.join(ROOT, "oracle", name)).read()[:6000]
+        named = set(re.findall(r"\b(test_\w+)(?!\.py)\b", head))
+        named = {n for n in named if not n.endswith("_") and not n.endswith("_pins")}
+        assert named, name
+        missing = sorted(n for n in named if n not in defined
+                         and not any(d.startswith(n) for d in defined))
+        assert not missing, (name, missing)
